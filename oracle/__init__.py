@@ -1,0 +1,198 @@
+"""FP64 CPU oracle for IVF + ADSampling (Gao & Long, SIGMOD 2023).
+
+TEST INFRASTRUCTURE ONLY.  The product library never imports, links or runs
+anything here; only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` do.  It shares no
+code with the CUDA path: the arithmetic lives in ``adsx_oracle.c`` (plain C,
+double precision, no intrinsics), this module only marshals numpy arrays.
+
+Functions (each follows the passage named in its docstring):
+  rotate(P, X)                      Sec. 3.1, y := P' x
+  knn_exact(Y, Qr, K)               Sec. 2.1, exact KNN
+  probe(Cr, Qr, nprobe)             Sec. 2.2.2, nearest N_probe centroids
+  ivf_exact(...)                    Sec. 2.2.2, IVF with FDScanning
+  dco(o, q, r2, eps0, delta_d)      Algorithm 1 with the Sec. 3.2 test
+  ivf_ads(...)                      Sec. 4, IVF+ (Algorithm 1 inside IVF)
+  dco_fixed_r(Y, Qr, r2, ...)       Sec. 6.2.5 fixed-threshold linear scan
+  recall_at(...), avg_dist_ratio()  Sec. 6.1 accuracy metrics
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "adsx_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+REJECTED, POSITIVE, NEGATIVE_AT_D = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile adsx_oracle.c into liboracle.so beside it (gcc, -O2, OpenMP)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            i32, i64, f64, cint = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+            lib.orc_max_threads.restype = cint
+            lib.orc_rotate.argtypes = [P, i32, P, i64, P, cint]
+            lib.orc_knn_exact.argtypes = [P, i64, i32, P, i64, i32, P, P, cint]
+            lib.orc_probe.argtypes = [P, i32, i32, P, i64, i32, P, P, cint]
+            lib.orc_ivf_exact.argtypes = [P, i64, i32, P, i32, P, P, i64, i32, i32, P, P, cint]
+            lib.orc_dco.argtypes = [P, P, i32, f64, f64, i32, P, P, P]
+            lib.orc_dco.restype = cint
+            lib.orc_ivf_ads.argtypes = [P, i64, i32, P, i32, P, P, i64, i32, i32,
+                                        f64, i32, P, P, P, P, cint]
+            lib.orc_dco_fixed_r.argtypes = [P, i64, i32, P, i64, P, f64, i32, P, P, P, cint]
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())
+
+
+def rotate(P, X, nthreads: int = 0):
+    """Sec. 3.1: rows of X (float32 values) mapped to y = P x in FP64."""
+    P = _c(P, np.float32)
+    X = _c(X, np.float32)
+    D = P.shape[0]
+    assert P.shape == (D, D) and X.shape[1] == D
+    Y = np.empty((X.shape[0], D), np.float64)
+    _load().orc_rotate(_p(P), D, _p(X), X.shape[0], _p(Y), nthreads)
+    return Y
+
+
+def knn_exact(Y, Qr, K: int, nthreads: int = 0):
+    """Sec. 2.1: exact KNN by brute force, ordered by (squared dist, id)."""
+    Y = _c(Y, np.float64)
+    Qr = _c(Qr, np.float64)
+    nq, D = Qr.shape
+    ids = np.empty((nq, K), np.int64)
+    d2 = np.empty((nq, K), np.float64)
+    _load().orc_knn_exact(_p(Y), Y.shape[0], D, _p(Qr), nq, K, _p(ids), _p(d2), nthreads)
+    return ids, d2
+
+
+def probe(Cr, Qr, nprobe: int, nthreads: int = 0):
+    """Sec. 2.2.2: the nprobe nearest centroids by (squared dist, cluster id)."""
+    Cr = _c(Cr, np.float64)
+    Qr = _c(Qr, np.float64)
+    nq, D = Qr.shape
+    probes = np.empty((nq, nprobe), np.int32)
+    pd2 = np.empty((nq, nprobe), np.float64)
+    _load().orc_probe(_p(Cr), Cr.shape[0], D, _p(Qr), nq, nprobe, _p(probes), _p(pd2), nthreads)
+    return probes, pd2
+
+
+def ivf_exact(Y, Cr, assign, Qr, K: int, nprobe: int, nthreads: int = 0):
+    """Sec. 2.2.2: IVF with exact (FDScanning) distances over the candidates."""
+    Y = _c(Y, np.float64)
+    Cr = _c(Cr, np.float64)
+    assign = _c(assign, np.int32)
+    Qr = _c(Qr, np.float64)
+    nq, D = Qr.shape
+    ids = np.empty((nq, K), np.int64)
+    d2 = np.empty((nq, K), np.float64)
+    _load().orc_ivf_exact(_p(Y), Y.shape[0], D, _p(Cr), Cr.shape[0], _p(assign), _p(Qr),
+                          nq, K, nprobe, _p(ids), _p(d2), nthreads)
+    return ids, d2
+
+
+def dco(o, q, r2: float, eps0: float, delta_d: int):
+    """Algorithm 1 on one pair.  Returns (decision, dims, S, margin)."""
+    o = _c(o, np.float64)
+    q = _c(q, np.float64)
+    dims = ctypes.c_int32(0)
+    S = ctypes.c_double(0.0)
+    m = ctypes.c_double(0.0)
+    res = _load().orc_dco(_p(o), _p(q), o.shape[0], float(r2), float(eps0), int(delta_d),
+                          ctypes.byref(dims), ctypes.byref(S), ctypes.byref(m))
+    return int(res), int(dims.value), float(S.value), float(m.value)
+
+
+def ivf_ads(Y, Cr, assign, Qr, K: int, nprobe: int, eps0: float, delta_d: int,
+            nthreads: int = 0):
+    """Sec. 4 (IVF+): sequential IVF with Algorithm 1 DCOs.
+
+    Returns ids (nq,K), squared distances (nq,K), dims sampled per query,
+    candidates per query."""
+    Y = _c(Y, np.float64)
+    Cr = _c(Cr, np.float64)
+    assign = _c(assign, np.int32)
+    Qr = _c(Qr, np.float64)
+    nq, D = Qr.shape
+    ids = np.empty((nq, K), np.int64)
+    d2 = np.empty((nq, K), np.float64)
+    dims = np.empty(nq, np.int64)
+    ncand = np.empty(nq, np.int64)
+    _load().orc_ivf_ads(_p(Y), Y.shape[0], D, _p(Cr), Cr.shape[0], _p(assign), _p(Qr), nq,
+                        K, nprobe, float(eps0), int(delta_d), _p(ids), _p(d2), _p(dims),
+                        _p(ncand), nthreads)
+    return ids, d2, dims, ncand
+
+
+def dco_fixed_r(Y, Qr, r2, eps0: float, delta_d: int, nthreads: int = 0):
+    """Sec. 6.2.5: Algorithm 1 for every (query, object) of a linear scan with a
+    fixed per-query threshold r2.  Returns decisions, dims, margins (nq x N)."""
+    Y = _c(Y, np.float64)
+    Qr = _c(Qr, np.float64)
+    r2 = _c(r2, np.float64)
+    nq, D = Qr.shape
+    N = Y.shape[0]
+    dec = np.empty((nq, N), np.uint8)
+    dims = np.empty((nq, N), np.int32)
+    mar = np.empty((nq, N), np.float64)
+    _load().orc_dco_fixed_r(_p(Y), N, D, _p(Qr), nq, _p(r2), float(eps0), int(delta_d),
+                            _p(dec), _p(dims), _p(mar), nthreads)
+    return dec, dims, mar
+
+
+# ---------------------------------------------------------------- metrics
+def recall_at(ids, gt_ids, k: int) -> float:
+    """Sec. 6.1: |first k returned  intersect  true top-k| / k, averaged."""
+    ids = np.asarray(ids)[:, :k]
+    gt = np.asarray(gt_ids)[:, :k]
+    hit = 0
+    for a, b in zip(ids, gt):
+        hit += len(set(int(x) for x in a if x >= 0) & set(int(x) for x in b))
+    return hit / float(k * ids.shape[0])
+
+
+def avg_dist_ratio(d2, gt_d2) -> float:
+    """Sec. 6.1: mean over rank-aligned pairs of dist(returned)/dist(true),
+    Euclidean (square roots of the squared distances); pairs whose true
+    distance is 0 or whose returned slot is empty are skipped."""
+    a = np.sqrt(np.asarray(d2, np.float64))
+    b = np.sqrt(np.asarray(gt_d2, np.float64))
+    ok = (b > 0) & np.isfinite(a)
+    return float(np.mean(a[ok] / b[ok])) if ok.any() else 1.0

@@ -1,0 +1,397 @@
+/*
+ * adsx_oracle.c -- plain FP64 CPU reference for IVF + ADSampling
+ * (Gao & Long, "High-Dimensional Approximate Nearest Neighbor Search: with
+ * Reliable and Efficient Distance Comparison Operations", SIGMOD 2023).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark do.  It shares no code, header or table with the CUDA path.
+ *
+ * Everything is computed in double precision from the float32 inputs the GPU
+ * library receives (the same X, P, centroids, assignments and queries), in the
+ * order the paper states, with no blocking or reordering:
+ *   - orc_rotate          Sec. 3.1: the transformed vector y := P' x.
+ *   - orc_knn_exact       Sec. 2.1: exact KNN by brute force.
+ *   - orc_probe           Sec. 2.2.2 (IVF): the N_probe nearest centroids.
+ *   - orc_ivf_exact       Sec. 2.2.2 (IVF) with FDScanning DCOs.
+ *   - orc_dco             Algorithm 1 (ADSampling) with the test of Sec. 3.2.
+ *   - orc_ivf_ads         Sec. 4 (IVF+): IVF whose DCOs run Algorithm 1
+ *                         against the current K-th distance of the KNN set.
+ *   - orc_dco_fixed_r     Sec. 6.2.5: Algorithm 1 over a linear scan with a
+ *                         fixed threshold per query (verification protocol).
+ *
+ * Conventions (readings of points the paper leaves open):
+ *   - distances are SQUARED Euclidean distances in the rotated space;
+ *   - the hypothesis test is used in its squared form,
+ *       reject  iff  D * S_d  >  r^2 * d * (1 + eps0/sqrt(d))^2,
+ *     which equals dis' > (1 + eps0/sqrt(d)) r for dis', r >= 0 (Sec. 3.2);
+ *   - d grows by delta_d per step, the last step may be shorter
+ *     (d_j = min(j*delta_d, D)); no test at d = D (Algorithm 1, Case 3);
+ *   - eps0 = +inf or r = +inf means "never reject" (no 0*inf);
+ *   - the KNN set is totally ordered by (distance, id); a candidate enters
+ *     iff it is positive and (dist, id) < the set's maximum (or the set has
+ *     fewer than K members, whose maximum is +inf; Sec. 2.2.2);
+ *   - clusters are visited in ascending (centroid distance, cluster id),
+ *     members of a cluster in ascending id.
+ *
+ * Parity pins (see tests/test_oracle_*.py): brute force on tiny inputs,
+ * permutation and orthogonal rotations, IVF with nprobe = nlist equals
+ * exact KNN, eps0 = inf and delta_d >= D reduce IVF+ to IVF exactly, the
+ * Beta law of a single rejection step (Lemma 3.1 made exact), hand-worked
+ * boundary cases of the strict test, the Lemma 3.2 / 3.3 trends.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_REJECTED 0      /* Case 1: H0 rejected at some d < D            */
+#define ORC_POSITIVE 1      /* Case 3: d = D and dis <= r                    */
+#define ORC_NEGATIVE_AT_D 2 /* Case 3: d = D and dis > r                     */
+
+static void set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ---------------------------------------------------------------------- */
+/* Sec. 3.1: y := P' x, with P' a D x D orthogonal matrix, row-major.      */
+void orc_rotate(const float *P, int32_t D, const float *X, int64_t N,
+                double *Y, int nthreads)
+{
+    set_threads(nthreads);
+#pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < N; ++n) {
+        const float *x = X + n * (int64_t)D;
+        for (int32_t i = 0; i < D; ++i) {
+            double s = 0.0;
+            for (int32_t j = 0; j < D; ++j)
+                s += (double)P[(int64_t)i * D + j] * (double)x[j];
+            Y[n * (int64_t)D + i] = s;
+        }
+    }
+}
+
+static double sqdist(const double *a, const double *b, int32_t D)
+{
+    double s = 0.0;
+    for (int32_t i = 0; i < D; ++i) {
+        double t = a[i] - b[i];
+        s += t * t;
+    }
+    return s;
+}
+
+typedef struct {
+    double d;
+    int64_t id;
+} orc_pair;
+
+static int pair_cmp(const void *pa, const void *pb)
+{
+    const orc_pair *a = (const orc_pair *)pa, *b = (const orc_pair *)pb;
+    if (a->d < b->d) return -1;
+    if (a->d > b->d) return 1;
+    if (a->id < b->id) return -1;
+    if (a->id > b->id) return 1;
+    return 0;
+}
+
+/* (d1,i1) < (d2,i2) in the total order used for the KNN set. */
+static int pair_less(double d1, int64_t i1, double d2, int64_t i2)
+{
+    return d1 < d2 || (d1 == d2 && i1 < i2);
+}
+
+static void write_sorted(orc_pair *pairs, int64_t n, int32_t K,
+                         int64_t *ids, double *d2)
+{
+    qsort(pairs, (size_t)n, sizeof(orc_pair), pair_cmp);
+    for (int32_t k = 0; k < K; ++k) {
+        if (k < n) {
+            ids[k] = pairs[k].id;
+            d2[k] = pairs[k].d;
+        } else {
+            ids[k] = -1;
+            d2[k] = INFINITY;
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Sec. 2.1: exact KNN -- all N distances, K smallest by (distance, id).   */
+void orc_knn_exact(const double *Y, int64_t N, int32_t D, const double *Qr,
+                   int64_t nq, int32_t K, int64_t *ids, double *d2,
+                   int nthreads)
+{
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t q = 0; q < nq; ++q) {
+        orc_pair *pairs = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(N > 0 ? N : 1));
+        for (int64_t n = 0; n < N; ++n) {
+            pairs[n].d = sqdist(Y + n * D, Qr + q * D, D);
+            pairs[n].id = n;
+        }
+        write_sorted(pairs, N, K, ids + q * K, d2 + q * K);
+        free(pairs);
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Sec. 2.2.2: the N_probe clusters whose centroids are nearest to q,     */
+/* ordered by (centroid distance, cluster id).                            */
+static void probe_one(const double *Cr, int32_t nlist, int32_t D,
+                      const double *qr, int32_t nprobe, int32_t *probes,
+                      double *pd2)
+{
+    orc_pair *pairs = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)nlist);
+    for (int32_t c = 0; c < nlist; ++c) {
+        pairs[c].d = sqdist(Cr + (int64_t)c * D, qr, D);
+        pairs[c].id = c;
+    }
+    qsort(pairs, (size_t)nlist, sizeof(orc_pair), pair_cmp);
+    for (int32_t p = 0; p < nprobe; ++p) {
+        probes[p] = (int32_t)pairs[p].id;
+        if (pd2) pd2[p] = pairs[p].d;
+    }
+    free(pairs);
+}
+
+void orc_probe(const double *Cr, int32_t nlist, int32_t D, const double *Qr,
+               int64_t nq, int32_t nprobe, int32_t *probes, double *pd2,
+               int nthreads)
+{
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t q = 0; q < nq; ++q)
+        probe_one(Cr, nlist, D, Qr + q * D, nprobe, probes + q * nprobe,
+                  pd2 ? pd2 + q * nprobe : NULL);
+}
+
+/* Buckets of the inverted file: members of each cluster in ascending id. */
+typedef struct {
+    int64_t *start; /* nlist + 1 */
+    int64_t *member;
+} orc_buckets;
+
+static orc_buckets make_buckets(const int32_t *assign, int64_t N, int32_t nlist)
+{
+    orc_buckets b;
+    b.start = (int64_t *)calloc((size_t)nlist + 1, sizeof(int64_t));
+    b.member = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    for (int64_t n = 0; n < N; ++n) b.start[assign[n] + 1] += 1;
+    for (int32_t c = 0; c < nlist; ++c) b.start[c + 1] += b.start[c];
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)nlist);
+    for (int32_t c = 0; c < nlist; ++c) fill[c] = b.start[c];
+    for (int64_t n = 0; n < N; ++n) b.member[fill[assign[n]]++] = n;
+    free(fill);
+    return b;
+}
+
+static void free_buckets(orc_buckets *b)
+{
+    free(b->start);
+    free(b->member);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Sec. 2.2.2 with FDScanning (Sec. 2.1): exact distance of every         */
+/* candidate of the probed clusters, K smallest by (distance, id).        */
+void orc_ivf_exact(const double *Y, int64_t N, int32_t D, const double *Cr,
+                   int32_t nlist, const int32_t *assign, const double *Qr,
+                   int64_t nq, int32_t K, int32_t nprobe, int64_t *ids,
+                   double *d2, int nthreads)
+{
+    orc_buckets b = make_buckets(assign, N, nlist);
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t q = 0; q < nq; ++q) {
+        const double *qr = Qr + q * D;
+        int32_t *probes = (int32_t *)malloc(sizeof(int32_t) * (size_t)nprobe);
+        probe_one(Cr, nlist, D, qr, nprobe, probes, NULL);
+        int64_t ncand = 0;
+        for (int32_t p = 0; p < nprobe; ++p)
+            ncand += b.start[probes[p] + 1] - b.start[probes[p]];
+        orc_pair *pairs = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(ncand > 0 ? ncand : 1));
+        int64_t k = 0;
+        for (int32_t p = 0; p < nprobe; ++p)
+            for (int64_t m = b.start[probes[p]]; m < b.start[probes[p] + 1]; ++m) {
+                int64_t id = b.member[m];
+                pairs[k].d = sqdist(Y + id * D, qr, D);
+                pairs[k].id = id;
+                ++k;
+            }
+        write_sorted(pairs, ncand, K, ids + q * K, d2 + q * K);
+        free(pairs);
+        free(probes);
+    }
+    free_buckets(&b);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Algorithm 1 (ADSampling) for one DCO: object o', query q', threshold   */
+/* r^2.  Samples delta_d more dimensions per step, updates the partial    */
+/* squared distance S_d (so dis' = sqrt(D/d * S_d), Eq. 3), and tests     */
+/* H0: dis <= r at every d < D (Sec. 3.2).  At d = D the comparison is    */
+/* exact (Case 3).                                                         */
+/*   returns ORC_REJECTED / ORC_POSITIVE / ORC_NEGATIVE_AT_D              */
+/*   *dims   = number of dimensions sampled                                */
+/*   *S_out  = S_d at termination (the exact squared distance if d = D)    */
+/*   *margin = smallest |lhs/rhs - 1| over every comparison made, where    */
+/*             lhs/rhs are the two sides of the test (or S_D vs r^2)      */
+int orc_dco(const double *o, const double *q, int32_t D, double r2,
+            double eps0, int32_t delta_d, int32_t *dims, double *S_out,
+            double *margin)
+{
+    int32_t d = 0;
+    double S = 0.0;
+    double closest = INFINITY;
+    int test_on = isfinite(eps0) && isfinite(r2);
+    while (d < D) {
+        int32_t dn = d + delta_d;
+        if (dn > D) dn = D;
+        for (int32_t i = d; i < dn; ++i) {
+            double t = o[i] - q[i];
+            S += t * t;
+        }
+        d = dn;
+        if (d < D) {
+            if (test_on) {
+                double g = 1.0 + eps0 / sqrt((double)d);
+                double lhs = (double)D * S;
+                double rhs = r2 * (double)d * g * g;
+                if (rhs > 0.0) {
+                    double m = fabs(lhs / rhs - 1.0);
+                    if (m < closest) closest = m;
+                } else if (lhs == 0.0) {
+                    closest = 0.0;
+                }
+                if (lhs > rhs) { /* Case 1 */
+                    if (dims) *dims = d;
+                    if (S_out) *S_out = S;
+                    if (margin) *margin = closest;
+                    return ORC_REJECTED;
+                }
+            }
+            /* Case 2: continue sampling */
+        }
+    }
+    /* Case 3: d = D, S is the exact squared distance. */
+    if (isfinite(r2)) {
+        if (r2 > 0.0) {
+            double m = fabs(S / r2 - 1.0);
+            if (m < closest) closest = m;
+        } else if (S == 0.0) {
+            closest = 0.0;
+        }
+    }
+    if (dims) *dims = D;
+    if (S_out) *S_out = S;
+    if (margin) *margin = closest;
+    return (S <= r2) ? ORC_POSITIVE : ORC_NEGATIVE_AT_D;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Sec. 4 (IVF+): IVF whose DCOs are Algorithm 1 against r = the current   */
+/* K-th distance of the KNN set (r = +inf until it holds K objects).      */
+/* Outputs ids/d2 sorted by (distance, id), -1/+inf padded, the total     */
+/* number of dimensions sampled per query, and the number of candidates.  */
+void orc_ivf_ads(const double *Y, int64_t N, int32_t D, const double *Cr,
+                 int32_t nlist, const int32_t *assign, const double *Qr,
+                 int64_t nq, int32_t K, int32_t nprobe, double eps0,
+                 int32_t delta_d, int64_t *ids, double *d2,
+                 int64_t *dims_total, int64_t *ncand_out, int nthreads)
+{
+    orc_buckets b = make_buckets(assign, N, nlist);
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t q = 0; q < nq; ++q) {
+        const double *qr = Qr + q * D;
+        int32_t *probes = (int32_t *)malloc(sizeof(int32_t) * (size_t)nprobe);
+        probe_one(Cr, nlist, D, qr, nprobe, probes, NULL);
+        /* KNN set: unordered array, its maximum found by a linear scan. */
+        double *hd = (double *)malloc(sizeof(double) * (size_t)K);
+        int64_t *hi = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
+        int32_t count = 0;
+        int64_t dims_sum = 0, ncand = 0;
+        for (int32_t p = 0; p < nprobe; ++p) {
+            for (int64_t m = b.start[probes[p]]; m < b.start[probes[p] + 1]; ++m) {
+                int64_t id = b.member[m];
+                int32_t imax = 0;
+                double r2 = INFINITY;
+                if (count == K) {
+                    for (int32_t k = 1; k < K; ++k)
+                        if (pair_less(hd[imax], hi[imax], hd[k], hi[k])) imax = k;
+                    r2 = hd[imax];
+                }
+                int32_t dims = 0;
+                double S = 0.0;
+                int res = orc_dco(Y + id * D, qr, D, r2, eps0, delta_d, &dims, &S, NULL);
+                dims_sum += dims;
+                ncand += 1;
+                if (res != ORC_POSITIVE) continue;
+                if (count < K) {
+                    hd[count] = S;
+                    hi[count] = id;
+                    ++count;
+                } else if (pair_less(S, id, hd[imax], hi[imax])) {
+                    hd[imax] = S;
+                    hi[imax] = id;
+                }
+            }
+        }
+        orc_pair *pairs = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(count > 0 ? count : 1));
+        for (int32_t k = 0; k < count; ++k) {
+            pairs[k].d = hd[k];
+            pairs[k].id = hi[k];
+        }
+        write_sorted(pairs, count, K, ids + q * K, d2 + q * K);
+        if (dims_total) dims_total[q] = dims_sum;
+        if (ncand_out) ncand_out[q] = ncand;
+        free(pairs);
+        free(hd);
+        free(hi);
+        free(probes);
+    }
+    free_buckets(&b);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Sec. 6.2.5 verification protocol: Algorithm 1 on every (query, object)  */
+/* pair of a linear scan with a FIXED threshold r2[q] per query, so the    */
+/* DCOs are independent.  decisions/dims/margins are nq x N, object order. */
+void orc_dco_fixed_r(const double *Y, int64_t N, int32_t D, const double *Qr,
+                     int64_t nq, const double *r2, double eps0,
+                     int32_t delta_d, uint8_t *decisions, int32_t *dims,
+                     double *margins, int nthreads)
+{
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t q = 0; q < nq; ++q) {
+        for (int64_t n = 0; n < N; ++n) {
+            int32_t dd = 0;
+            double m = 0.0;
+            int res = orc_dco(Y + n * D, Qr + q * D, D, r2[q], eps0, delta_d,
+                              &dd, NULL, &m);
+            decisions[q * N + n] = (uint8_t)res;
+            if (dims) dims[q * N + n] = dd;
+            if (margins) margins[q * N + n] = m;
+        }
+    }
+}
