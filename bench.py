@@ -1,0 +1,395 @@
+"""Benchmark: QPS at recall@10 >= 0.95 of IVF+ADSampling vs the full-D (FDScanning)
+DCO scan, on one GB300, SIFT-shaped synthetic workload (1M x 128 non-negative
+integer-valued floats, 10k queries, nlist 4096, K 100, eps0 2.1, delta_d 32).
+
+One step = one adsx_search call over the whole query batch (query rotation,
+centroid distances, top-nprobe, candidate scan, top-K), queries resident in
+HBM.  nprobe is calibrated before the timed region: the smallest nprobe in
+{8,16,32,64,128,256} whose recall@10 >= 0.95 (ground truth by exact brute
+force).  Prints ONE JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl adsx|reference]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QPS at recall@10>=0.95: ADSampling-IVF vs full-D DCO scan, 1 GB300; HBM GB/s"
+UNIT = "queries/s"
+NPROBE_GRID = [8, 16, 32, 64, 128, 256]
+TARGET_RECALL = 0.95
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="adsx", choices=["adsx", "reference"])
+    ap.add_argument("--workload", default="sift", choices=["sift", "gauss"])
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink N and nq (quick checks)")
+    ap.add_argument("--K", type=int, default=100)
+    ap.add_argument("--eps0", type=float, default=2.1)
+    ap.add_argument("--delta-d", type=int, default=32)
+    ap.add_argument("--nprobe", type=int, default=0, help="0 = calibrate")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(args, device):
+    from paper_2303_09855_gb300 import workloads as W
+    if args.workload == "sift":
+        N = int(1_000_000 * args.scale)
+        nq = int(10_000 * args.scale)
+        nlist = 4096 if args.scale >= 0.5 else max(64, int(4096 * args.scale))
+        return W.gen_sift_like(N=N, nq=max(nq, 100), nlist=nlist, device=device)
+    return W.gen_gaussian_mixture(device=device)
+
+
+def ground_truth(X, Q, k, device):
+    """Exact k nearest ids by brute force (torch FP32 on the device, TF32 off);
+    a measurement helper, not part of the library."""
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = False
+    Xt = torch.from_numpy(X).to(device)
+    xn = (Xt * Xt).sum(1)
+    out = []
+    for s in range(0, Q.shape[0], 1024):
+        q = torch.from_numpy(Q[s:s + 1024]).to(device)
+        d = xn[None, :] - 2.0 * (q @ Xt.T)
+        out.append(torch.topk(d, k, dim=1, largest=False).indices.cpu().numpy())
+    del Xt
+    return np.concatenate(out)
+
+
+def recall10(ids, gt):
+    ids = np.asarray(ids)[:, :10]
+    hit = sum(len(set(a.tolist()) & set(b.tolist())) for a, b in zip(ids, gt[:, :10]))
+    return hit / (10.0 * ids.shape[0])
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        rows = []
+        for l in getattr(self, "lines", []):
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                rows.append((float(p[0]), float(p[1]), p[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        load = [s for s in sm if s > 0.5 * max(sm)] or sm
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[2])
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def scan_traffic():
+    """DRAM bytes per scan launch from the committed ncu summary, if it was
+    taken on the current scan source (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "scan_traffic.json")
+    src = os.path.join(ROOT, "paper_2303_09855_gb300", "csrc", "scan.cu")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if t.get("scan_cu_sha256_16") != h:
+            return None
+        return t
+    except Exception:
+        return None
+
+
+def cpu_baseline_oracle(wl, K, nprobe, eps0, dd, seconds):
+    """The FP64 oracle's IVF+ (sequential Algorithm 1) on the host cores, on a
+    bounded sample of the same queries; index-phase rotation untimed."""
+    import oracle
+    threads = oracle.max_threads()
+    Y = oracle.rotate(wl.P, wl.X, threads)
+    Cr = oracle.rotate(wl.P, wl.centroids, threads)
+    Qr = oracle.rotate(wl.P, wl.Q, threads)
+    n = max(threads, 8)
+    t0 = time.perf_counter()
+    oracle.ivf_ads(Y, Cr, wl.assign, Qr[:n], K, nprobe, eps0, dd, threads)
+    dt = time.perf_counter() - t0
+    total_q, total_t = n, dt
+    if dt < seconds:
+        m = int(min(Qr.shape[0] - n, max(threads, n * (seconds - dt) / max(dt, 1e-3))))
+        if m > 0:
+            t0 = time.perf_counter()
+            oracle.ivf_ads(Y, Cr, wl.assign, Qr[n:n + m], K, nprobe, eps0, dd, threads)
+            total_t += time.perf_counter() - t0
+            total_q += m
+    return {"value": total_q / total_t, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d of %d queries, FP64 sequential IVF+ (Algorithm 1), nprobe %d, K %d, "
+                      "OpenMP over queries; data rotation untimed" % (total_q, Qr.shape[0],
+                                                                       nprobe, K)}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle timed on the host cores."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    import torch
+    import oracle
+    device = "cuda:%d" % local if torch.cuda.is_available() else "cpu"
+    wl = make_workload(args, device)
+    threads = oracle.max_threads()
+    Y = oracle.rotate(wl.P, wl.X, threads)
+    Cr = oracle.rotate(wl.P, wl.centroids, threads)
+    Qr = oracle.rotate(wl.P, wl.Q, threads)
+    ns = 32
+    gt, _ = oracle.knn_exact(Y, Qr[:ns], 10, threads)
+    nprobe = args.nprobe
+    if not nprobe:
+        nprobe = NPROBE_GRID[-1]
+        for npb in NPROBE_GRID:
+            ids, _, _, _ = oracle.ivf_ads(Y, Cr, wl.assign, Qr[:ns], args.K, npb, args.eps0,
+                                          args.delta_d, threads)
+            if recall10(ids, gt) >= TARGET_RECALL:
+                nprobe = npb
+                break
+    per_step = max(threads, 16)
+    times = []
+    for step in range(args.warmup + args.steps):
+        lo = (step * per_step) % max(1, Qr.shape[0] - per_step)
+        t0 = time.perf_counter()
+        oracle.ivf_ads(Y, Cr, wl.assign, Qr[lo:lo + per_step], args.K, nprobe, args.eps0,
+                       args.delta_d, threads)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    v = per_step * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "nq_per_step": per_step, "K": args.K,
+                       "nprobe": nprobe, "eps0": args.eps0, "delta_d": args.delta_d},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "%d queries per step, FP64 sequential IVF+" % per_step},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    device = "cuda:%d" % local
+    from paper_2303_09855_gb300 import adsx
+    from paper_2303_09855_gb300 import build as libbuild
+    libbuild.build()
+
+    wl = make_workload(args, device)
+    ix = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign)
+    Qd = torch.from_numpy(wl.Q).to(device)
+    nq = Qd.shape[0]
+    gt = ground_truth(wl.X, wl.Q, 10, device)
+
+    def search(nprobe, eps0, dims=False):
+        return ix.search(Qd, args.K, nprobe, eps0=eps0, delta_d=args.delta_d, return_dims=dims)
+
+    # ---- calibration (untimed): smallest nprobe with recall@10 >= 0.95
+    sweep = []
+    np_fd = np_ads = None
+    for npb in NPROBE_GRID:
+        if npb > wl.nlist:
+            break
+        ids, _ = search(npb, math.inf)
+        r_fd = recall10(ids.cpu().numpy(), gt)
+        ids, _, dims = search(npb, args.eps0, True)
+        r_ads = recall10(ids.cpu().numpy(), gt)
+        sweep.append({"nprobe": npb, "recall10_fd": r_fd, "recall10_ads": r_ads})
+        if np_fd is None and r_fd >= TARGET_RECALL:
+            np_fd = npb
+        if np_ads is None and r_ads >= TARGET_RECALL:
+            np_ads = npb
+        if np_fd is not None and np_ads is not None:
+            break
+    if args.nprobe:
+        np_fd = np_ads = args.nprobe
+    np_fd = np_fd or NPROBE_GRID[-1]
+    np_ads = np_ads or NPROBE_GRID[-1]
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)   # 256 MB > L2
+    adsx.set_stage_timing(ix, True)
+    stream = torch.cuda.current_stream()
+
+    def timed(nprobe, eps0, steps, warmup):
+        tot, scan_ms, dims_sum = 0.0, 0.0, 0
+        for s in range(warmup + steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            ids, d2, dims = search(nprobe, eps0, True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if s >= warmup:
+                tot += e0.elapsed_time(e1)
+                scan_ms += adsx.stage_ms(ix)[3]
+                dims_sum += int(dims.sum().item())
+        return tot / steps, scan_ms / steps, dims_sum / steps, ids
+
+    # FDScanning arm (the baseline the metric compares against)
+    fd_ms, fd_scan_ms, fd_dims, _ = timed(np_fd, math.inf, max(3, args.steps // 2), 2)
+
+    # ADSampling arm (the headline), clocks sampled during it
+    import torch.distributed as dist
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    gpu_idx = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local if ws > 1 else 0]
+    with Clocks(gpu_idx) as clk:
+        ads_ms, ads_scan_ms, ads_dims, ids = timed(np_ads, args.eps0, args.steps, args.warmup)
+    torch.cuda.synchronize()
+    stage = adsx.stage_ms(ix)
+    if ws > 1:
+        t = torch.tensor([ads_ms])
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ads_ms = float(t.item())
+        dist.barrier()
+    recall_ads = recall10(ids.cpu().numpy(), gt)
+
+    # end to end through host (pinned) buffers, copies inside the timed region
+    Qh = torch.from_numpy(wl.Q).pin_memory()
+    e2e_t = []
+    for s in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hid, hd = ix.search(Qh, args.K, np_ads, eps0=args.eps0, delta_d=args.delta_d)
+        if s >= args.warmup:
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_qps = nq * ws / (sum(e2e_t) / len(e2e_t))
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return 0
+
+    hbm, peak_kind = peaks()
+    algo_bytes = 4.0 * ads_dims            # FP32 dims actually sampled per scan launch
+    achieved = algo_bytes / (ads_scan_ms * 1e-3) / 1e9
+    tr = scan_traffic()
+    fd_frac = ads_dims / fd_dims if fd_dims else None
+    line = {
+        "metric": METRIC, "value": nq * ws / (ads_ms * 1e-3), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ads_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (SIFT-shaped seeded mixture; random orthogonal P; seeded k-means)",
+        "config": {"workload": wl.name, "nq": nq, "nlist": wl.nlist, "K": args.K,
+                   "eps0": args.eps0, "delta_d": args.delta_d, "nprobe": np_ads,
+                   "l2": "256 MB flush between steps; index 512 MB > L2",
+                   "recall10": recall_ads},
+        "fd_scan": {"qps": nq * ws / (fd_ms * 1e-3), "nprobe": np_fd, "ms_per_step": fd_ms,
+                    "scan_ms": fd_scan_ms},
+        "speedup_vs_fd": fd_ms / ads_ms,
+        "dims_fraction_vs_fd_at_ads_nprobe": None,
+        "stage_ms_last": {"rotate": stage[0], "centroid_dist": stage[1], "select": stage[2],
+                          "scan": stage[3]},
+        "calibration": sweep,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_kind": peak_kind,
+                     "kernel": "ads_scan_kernel",
+                     "traffic": (tr["dram_bytes_per_launch"] * ads_dims / tr["dims_per_launch"])
+                     if tr else None,
+                     "algorithmic_bytes_per_launch": algo_bytes},
+        "e2e": {"value": e2e_qps, "unit": UNIT, "h2d_bytes_per_step": int(nq * wl.D * 4),
+                "d2h_bytes_per_step": int(nq * args.K * 12)},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk.summary(),
+    }
+    # dims fraction of ADS vs FD at the same nprobe (Sec. 6.1 evaluated-dims metric)
+    if np_fd == np_ads:
+        line["dims_fraction_vs_fd_at_ads_nprobe"] = fd_frac
+    else:
+        _, _, d_fd = search(np_ads, math.inf, True)
+        line["dims_fraction_vs_fd_at_ads_nprobe"] = ads_dims / float(d_fd.sum().item())
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline_oracle(wl, args.K, np_ads, args.eps0,
+                                                   args.delta_d, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    ix.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,178 @@
+/*
+ * adsx.h -- C ABI of libadsx.so: IVF + ADSampling distance comparison
+ * operations on one GB300 GPU (sm_103a).
+ *
+ * Method: Gao & Long, "High-Dimensional Approximate Nearest Neighbor Search:
+ * with Reliable and Efficient Distance Comparison Operations", SIGMOD 2023.
+ *   - Sec. 2.1    KNN query; DCO = "is dis <= r, and if so return dis".
+ *   - Sec. 2.2.2  IVF: probe the N_probe nearest centroids, scan their members
+ *                 against the K-th distance of a KNN set (+inf until full).
+ *   - Sec. 3.1    random orthogonal transform y = P x; dis' = sqrt(D/d)||y|_d||.
+ *   - Sec. 3.2    hypothesis test: reject dis <= r iff dis' > (1+eps0/sqrt d) r.
+ *   - Algorithm 1 incremental sampling, delta_d dims per step, exact at d = D.
+ *   - Sec. 4      IVF+ = IVF whose DCOs run Algorithm 1.
+ *   - Sec. 5.2    IVF++ = a data layout that stores the first dims of all
+ *                 candidates together (generalised here to 16-dim blocks).
+ *   - Sec. 6.2.5  fixed-threshold linear-scan verification protocol.
+ *
+ * Conventions for every entry point:
+ *   - Return value: ADSX_OK (0) or a negative ADSX_E* code; the message of
+ *     the last failure on the calling thread is adsx_last_error().  No C++
+ *     exception crosses this ABI.
+ *   - Vectors are float32, row-major, D contiguous floats per vector, in the
+ *     RAW (unrotated) space; the library applies P itself.
+ *   - Distances are SQUARED Euclidean distances (in the rotated space, which
+ *     equals the raw space up to the float32 rounding of P).
+ *   - Pointers marked "host or device" may point to host memory (pageable or
+ *     pinned) or to device memory of the current CUDA device; the library
+ *     inspects each pointer.  When any output is in host memory the call
+ *     copies results back and synchronises `stream` before returning; when
+ *     all of them are in device memory the call only enqueues work on
+ *     `stream` and returns (query results are valid once `stream` reaches
+ *     that point; use adsx_stream_status for the device-side error word).
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   - The caller owns every buffer it passes; the library never retains a
+ *     caller pointer after a call returns.
+ *   - Thread safety: searches on one index may run concurrently on different
+ *     streams; build and free must not overlap any other call on the index.
+ */
+#ifndef ADSX_H
+#define ADSX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct adsx_index adsx_index;
+
+enum {
+    ADSX_OK = 0,
+    ADSX_EINVAL = -1,   /* invalid argument (sizes, ranges, null pointers)   */
+    ADSX_ENOMEM = -2,   /* device memory could not be allocated             */
+    ADSX_ECUDA = -3,    /* a CUDA runtime call failed                       */
+    ADSX_ETIMEOUT = -4  /* a bounded device-side wait gave up (results bad)  */
+};
+
+/* Storage type of the dimension-blocked vector layout. */
+typedef enum { ADSX_F32 = 0, ADSX_BF16 = 1, ADSX_F16 = 2 } adsx_dtype;
+
+/* Limits of the current kernels (checked; ADSX_EINVAL beyond them). */
+#define ADSX_MAX_D 4080       /* dimensions (padded to a multiple of 16)   */
+#define ADSX_MAX_K 1024       /* neighbours per query                        */
+#define ADSX_MAX_NPROBE 1024  /* probed clusters per query                   */
+#define ADSX_MAX_NLIST 16384  /* clusters                                    */
+
+/*
+ * adsx_build_index -- index phase (Sec. 6.1 "Implementation", Sec. 4, Sec. 5.2).
+ *   X          host, N x D float32, raw data vectors; N in [1, 2^31).
+ *   P          host, D x D float32 row-major, the random orthogonal matrix
+ *              (y = P x).  Orthogonality is checked: max |P^T P - I| <= 1e-4.
+ *   centroids  host, nlist x D float32, IVF centroids in the raw space.
+ *   assign     host, N int32, cluster of each vector, each in [0, nlist).
+ *   storage    ADSX_F32 (the only storage type accepted by this version).
+ *   stream     work is enqueued on it and the call synchronises it.
+ *   out        receives an opaque handle owning all of the index's device
+ *              memory (rotated vectors in the dim-blocked per-cluster layout,
+ *              ids, CSR offsets, rotated centroids, P).
+ * Errors: ADSX_EINVAL (bad sizes, non-orthogonal P, assign out of range),
+ * ADSX_ENOMEM, ADSX_ECUDA.  On error *out is NULL and nothing leaks.
+ */
+int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
+                     const float *centroids, int32_t nlist,
+                     const int32_t *assign, int32_t storage, void *stream,
+                     adsx_index **out);
+
+/* Frees the index and all of its device memory (synchronises the device). */
+int adsx_free_index(adsx_index *index);
+
+/* Shape of an index: any output pointer may be NULL. */
+int adsx_index_info(const adsx_index *index, int64_t *N, int32_t *D,
+                    int32_t *nlist, int32_t *storage, int64_t *device_bytes);
+
+/*
+ * adsx_search -- IVF+ query phase (Sec. 4 with Algorithm 1 DCOs, Sec. 2.2.2).
+ * For each query: q' = P q; the nprobe clusters with the smallest
+ * (||q' - c'||^2, cluster id); every member is scanned in delta_d-dim steps
+ * and rejected as soon as D * S_d > r^2 * d * (1 + eps0/sqrt(d))^2 with
+ * d < D, where r^2 is the query's current K-th squared distance (+inf until
+ * K exact distances are known); members reaching d = D with S_D <= r^2
+ * enter the query's top-K, ordered by (distance, id).
+ *   Qv         host or device, nq x D float32 raw queries; nq >= 0.
+ *   K          1..ADSX_MAX_K.   nprobe 1..min(nlist, ADSX_MAX_NPROBE).
+ *   eps0       >= 0; +INFINITY disables the test (FDScanning, exact IVF).
+ *   delta_d    multiple of 16, >= 16 (a value >= D also disables the test).
+ *   ids        host or device, nq x K int64 output; -1 pads missing slots.
+ *   dists      host or device, nq x K float32 squared distances; +INF pads.
+ *   dims_read  host or device, nq int64 (may be NULL): dimensions sampled
+ *              per query, summed over its candidates (Sec. 6.1 metric).
+ * The threshold r is shared among the warps scanning a query, so which
+ * candidates are rejected depends on scheduling; every returned distance is
+ * exact and every true top-K member of the probed clusters that would pass
+ * its DCO at the final K-th distance is returned.
+ * Errors: ADSX_EINVAL, ADSX_ENOMEM, ADSX_ECUDA, ADSX_ETIMEOUT.
+ */
+int adsx_search(const adsx_index *index, const float *Qv, int64_t nq,
+                int32_t K, int32_t nprobe, float eps0, int32_t delta_d,
+                int64_t *ids, float *dists, int64_t *dims_read, void *stream);
+
+/*
+ * adsx_probe -- the query rotation and centroid selection steps of
+ * adsx_search alone (Sec. 3.1, Sec. 2.2.2), for inspection and tests.
+ *   probes     host or device, nq x nprobe int32, ascending (dist, id).
+ *   probe_d2   host or device, nq x nprobe float32 (may be NULL).
+ */
+int adsx_probe(const adsx_index *index, const float *Qv, int64_t nq,
+               int32_t nprobe, int32_t *probes, float *probe_d2, void *stream);
+
+/*
+ * adsx_rotate -- q' = P q for each query (Sec. 3.1).
+ *   out        host or device, nq x D float32.
+ */
+int adsx_rotate(const adsx_index *index, const float *Qv, int64_t nq,
+                float *out, void *stream);
+
+/*
+ * adsx_dco_fixed_r -- Algorithm 1 for every (query, indexed vector) pair with
+ * a FIXED squared threshold per query: the verification protocol of
+ * Sec. 6.2.5 (linear scan, independent DCOs), run by the same device DCO
+ * code as adsx_search.
+ *   r2         host or device, nq float32 squared thresholds (+INF allowed).
+ *   decisions  host or device, nq x N uint8, indexed by original vector id:
+ *              0 = rejected at some d < D (Case 1), 1 = reached d = D with
+ *              S_D <= r2 (positive), 2 = reached d = D with S_D > r2.
+ *   dims       host or device, nq x N int32 dims sampled (may be NULL).
+ */
+int adsx_dco_fixed_r(const adsx_index *index, const float *Qv, int64_t nq,
+                     const float *r2, float eps0, int32_t delta_d,
+                     uint8_t *decisions, int32_t *dims, void *stream);
+
+/*
+ * adsx_stream_status -- synchronises `stream`, then reads and clears the
+ * index's device-side error word (set when a bounded wait inside a kernel
+ * gave up).  Returns ADSX_OK, ADSX_ETIMEOUT or ADSX_ECUDA.
+ */
+int adsx_stream_status(const adsx_index *index, void *stream);
+
+/*
+ * adsx_set_stage_timing -- when `enable` is non-zero, every later
+ * adsx_search on this index records CUDA events on its stream between its
+ * stages (query rotation, centroid distances, top-nprobe select, candidate
+ * scan).  Timing is per index: do not enable it while searches on the index
+ * run concurrently on several streams.
+ * adsx_stage_ms -- waits for the last timed search and writes the device
+ * time of its four stages, in milliseconds, to ms[0..3] (in the order above).
+ * Returns ADSX_EINVAL if no timed search has run.
+ */
+int adsx_set_stage_timing(adsx_index *index, int32_t enable);
+int adsx_stage_ms(const adsx_index *index, float *ms);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *adsx_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADSX_H */

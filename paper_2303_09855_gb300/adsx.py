@@ -1,0 +1,246 @@
+"""Thin ctypes binding of libadsx.so (include/adsx.h).  Argument marshalling
+only: every step of the path runs in the library's CUDA kernels.
+
+Each function has the name of the C entry point without the ``adsx_`` prefix.
+Inputs may be numpy arrays (host memory: outputs come back as numpy arrays
+and the call synchronises) or torch CUDA tensors (outputs are allocated as
+torch CUDA tensors and the work is enqueued on torch's current stream).
+
+The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_2303_09855_gb300.build``); loading fails loudly otherwise.
+There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libadsx.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4
+F32, BF16, F16 = 0, 1, 2
+REJECTED, POSITIVE, NEGATIVE_AT_D = 0, 1, 2
+
+_lib = None
+
+
+class AdsxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("adsx error %d: %s" % (code, msg))
+        self.code = code
+
+
+def load():
+    """Loads libadsx.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libadsx.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    try:
+        import torch  # noqa: F401  (loads the CUDA runtime the library links against)
+    except Exception:
+        pass
+    lib = ctypes.CDLL(LIB_PATH)
+    V, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+    lib.adsx_build_index.argtypes = [V, i64, i32, V, V, i32, V, i32, V, ctypes.POINTER(V)]
+    lib.adsx_free_index.argtypes = [V]
+    lib.adsx_index_info.argtypes = [V, V, V, V, V, V]
+    lib.adsx_search.argtypes = [V, V, i64, i32, i32, f32, i32, V, V, V, V]
+    lib.adsx_probe.argtypes = [V, V, i64, i32, V, V, V]
+    lib.adsx_rotate.argtypes = [V, V, i64, V, V]
+    lib.adsx_dco_fixed_r.argtypes = [V, V, i64, V, f32, i32, V, V, V]
+    lib.adsx_stream_status.argtypes = [V, V]
+    lib.adsx_set_stage_timing.argtypes = [V, i32]
+    lib.adsx_stage_ms.argtypes = [V, V]
+    lib.adsx_last_error.restype = ctypes.c_char_p
+    for fn in ("adsx_build_index", "adsx_free_index", "adsx_index_info", "adsx_search",
+               "adsx_probe", "adsx_rotate", "adsx_dco_fixed_r", "adsx_stream_status",
+               "adsx_set_stage_timing", "adsx_stage_ms"):
+        getattr(lib, fn).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().adsx_last_error().decode()
+
+
+def _check(rc):
+    if rc != OK:
+        raise AdsxError(rc, last_error())
+
+
+def _is_torch_cuda(a):
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _stream_of(a, stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    if _is_torch_cuda(a):
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _host(a, dtype):
+    if hasattr(a, "detach"):
+        a = a.detach().cpu().numpy()
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _prep_queries(Q):
+    if hasattr(Q, "data_ptr"):          # torch tensor: device, or (pinned) host memory
+        import torch
+        return Q.to(torch.float32).contiguous()
+    return _host(Q, np.float32)
+
+
+def _out(like, shape, np_dtype, torch_name):
+    if hasattr(like, "data_ptr"):
+        import torch
+        if like.is_cuda:
+            return torch.empty(shape, dtype=getattr(torch, torch_name), device=like.device)
+        return torch.empty(shape, dtype=getattr(torch, torch_name),
+                           pin_memory=like.is_pinned())
+    return np.empty(shape, np_dtype)
+
+
+class Index:
+    """Owns an adsx_index handle (freed by close() or garbage collection)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        N, D, nl, st, by = (ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(),
+                            ctypes.c_int32(), ctypes.c_int64())
+        _check(load().adsx_index_info(handle, ctypes.byref(N), ctypes.byref(D),
+                                      ctypes.byref(nl), ctypes.byref(st), ctypes.byref(by)))
+        self.N, self.D, self.nlist, self.storage, self.device_bytes = (
+            N.value, D.value, nl.value, st.value, by.value)
+
+    def close(self):
+        if self.handle:
+            load().adsx_free_index(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # method forms of the module functions
+    def search(self, Q, K, nprobe, eps0=2.1, delta_d=32, return_dims=False, stream=None):
+        return search(self, Q, K, nprobe, eps0, delta_d, return_dims, stream)
+
+    def probe(self, Q, nprobe, stream=None):
+        return probe(self, Q, nprobe, stream)
+
+    def rotate(self, Q, stream=None):
+        return rotate(self, Q, stream)
+
+    def dco_fixed_r(self, Q, r2, eps0, delta_d, stream=None):
+        return dco_fixed_r(self, Q, r2, eps0, delta_d, stream)
+
+
+def build_index(X, P, centroids, assign, storage=F32, stream=None) -> Index:
+    """adsx_build_index: host arrays X (N x D), P (D x D), centroids, assign."""
+    X = _host(X, np.float32)
+    P = _host(P, np.float32)
+    C = _host(centroids, np.float32)
+    a = _host(assign, np.int32)
+    h = ctypes.c_void_p()
+    _check(load().adsx_build_index(_ptr(X), X.shape[0], X.shape[1], _ptr(P), _ptr(C), C.shape[0],
+                                   _ptr(a), int(storage), _stream_of(None, stream),
+                                   ctypes.byref(h)))
+    return Index(h)
+
+
+def free_index(index: Index):
+    index.close()
+
+
+def index_info(index: Index):
+    """adsx_index_info: (N, D, nlist, storage, device_bytes)."""
+    return index.N, index.D, index.nlist, index.storage, index.device_bytes
+
+
+def search(index: Index, Q, K: int, nprobe: int, eps0: float = 2.1, delta_d: int = 32,
+           return_dims: bool = False, stream=None):
+    """adsx_search: returns (ids int64 nq x K, squared dists float32 nq x K[, dims nq])."""
+    Q = _prep_queries(Q)
+    nq = Q.shape[0]
+    ids = _out(Q, (nq, K), np.int64, "int64")
+    d2 = _out(Q, (nq, K), np.float32, "float32")
+    dims = _out(Q, (nq,), np.int64, "int64") if return_dims else None
+    _check(load().adsx_search(index.handle, _ptr(Q), nq, int(K), int(nprobe),
+                              float(eps0) if math.isfinite(eps0) else float("inf"),
+                              int(delta_d), _ptr(ids), _ptr(d2), _ptr(dims),
+                              _stream_of(Q, stream)))
+    return (ids, d2, dims) if return_dims else (ids, d2)
+
+
+def probe(index: Index, Q, nprobe: int, stream=None):
+    """adsx_probe: (cluster ids int32 nq x nprobe, squared centroid distances)."""
+    Q = _prep_queries(Q)
+    nq = Q.shape[0]
+    pr = _out(Q, (nq, nprobe), np.int32, "int32")
+    pd = _out(Q, (nq, nprobe), np.float32, "float32")
+    _check(load().adsx_probe(index.handle, _ptr(Q), nq, int(nprobe), _ptr(pr), _ptr(pd),
+                             _stream_of(Q, stream)))
+    return pr, pd
+
+
+def rotate(index: Index, Q, stream=None):
+    """adsx_rotate: q' = P q for each row."""
+    Q = _prep_queries(Q)
+    out = _out(Q, tuple(Q.shape), np.float32, "float32")
+    _check(load().adsx_rotate(index.handle, _ptr(Q), Q.shape[0], _ptr(out), _stream_of(Q, stream)))
+    return out
+
+
+def dco_fixed_r(index: Index, Q, r2, eps0: float, delta_d: int, stream=None):
+    """adsx_dco_fixed_r: (decisions uint8 nq x N, dims int32 nq x N)."""
+    Q = _prep_queries(Q)
+    nq = Q.shape[0]
+    if _is_torch_cuda(Q):
+        import torch
+        r2 = torch.as_tensor(r2, dtype=torch.float32, device=Q.device).contiguous()
+    else:
+        r2 = _host(r2, np.float32)
+    dec = _out(Q, (nq, index.N), np.uint8, "uint8")
+    dims = _out(Q, (nq, index.N), np.int32, "int32")
+    _check(load().adsx_dco_fixed_r(index.handle, _ptr(Q), nq, _ptr(r2), float(eps0),
+                                   int(delta_d), _ptr(dec), _ptr(dims), _stream_of(Q, stream)))
+    return dec, dims
+
+
+def set_stage_timing(index: Index, enable: bool = True):
+    """adsx_set_stage_timing: record CUDA events between search stages."""
+    _check(load().adsx_set_stage_timing(index.handle, 1 if enable else 0))
+
+
+def stage_ms(index: Index):
+    """adsx_stage_ms: device ms of (rotate, centroid distances, select, scan)
+    of the last timed search."""
+    out = (ctypes.c_float * 4)()
+    _check(load().adsx_stage_ms(index.handle, out))
+    return [float(x) for x in out]
+
+
+def stream_status(index: Index, stream=None):
+    """adsx_stream_status: synchronise and raise if a device wait gave up."""
+    _check(load().adsx_stream_status(index.handle, _stream_of(None, stream)))

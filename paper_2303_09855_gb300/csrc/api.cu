@@ -1,0 +1,555 @@
+// api.cu -- the C ABI declared in include/adsx.h: argument checks, index
+// construction (host CSR build + device rotation and layout scatter) and the
+// search pipeline (rotate -> centroid distances -> top-nprobe -> scan), all
+// enqueued on the caller's stream.  Temporary device buffers come from the
+// stream-ordered allocator (cudaMallocAsync / cudaFreeAsync).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "adsx_internal.cuh"
+
+using adsx::Index;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    cudaGetLastError();
+    if (e == cudaErrorMemoryAllocation)
+        return fail(ADSX_ENOMEM, "%s: out of device memory", what);
+    return fail(ADSX_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Stream-ordered scratch buffers, released on the stream when the scope ends.
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void *> bufs;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    ~Scratch()
+    {
+        for (void *p : bufs) cudaFreeAsync(p, s);
+    }
+    template <typename T>
+    cudaError_t get(T **out, size_t count)
+    {
+        void *p = nullptr;
+        cudaError_t e = cudaMallocAsync(&p, std::max<size_t>(count * sizeof(T), 16), s);
+        if (e != cudaSuccess) return e;
+        bufs.push_back(p);
+        *out = static_cast<T *>(p);
+        return cudaSuccess;
+    }
+};
+
+// A caller buffer of `count` T: used in place when it is device memory, else
+// staged through a scratch buffer (inputs copied in now, outputs copied out by
+// finish()).
+template <typename T>
+struct Buf {
+    T *dev = nullptr;
+    T *host = nullptr;
+    size_t count = 0;
+};
+
+template <typename T>
+cudaError_t stage_in(Scratch &sc, const T *user, size_t count, Buf<T> &b)
+{
+    b.count = count;
+    if (is_device_ptr(user)) {
+        b.dev = const_cast<T *>(user);
+        return cudaSuccess;
+    }
+    cudaError_t e = sc.get(&b.dev, count);
+    if (e != cudaSuccess) return e;
+    if (count) e = cudaMemcpyAsync(b.dev, user, count * sizeof(T), cudaMemcpyHostToDevice, sc.s);
+    return e;
+}
+
+template <typename T>
+cudaError_t stage_out(Scratch &sc, T *user, size_t count, Buf<T> &b)
+{
+    b.count = count;
+    if (!user) return cudaSuccess;
+    if (is_device_ptr(user)) {
+        b.dev = user;
+        return cudaSuccess;
+    }
+    b.host = user;
+    return sc.get(&b.dev, count);
+}
+
+template <typename T>
+cudaError_t copy_back(const Buf<T> &b, cudaStream_t s)
+{
+    if (!b.host || !b.count) return cudaSuccess;
+    return cudaMemcpyAsync(b.host, b.dev, b.count * sizeof(T), cudaMemcpyDeviceToHost, s);
+}
+
+int check_index(const Index *ix)
+{
+    if (!ix) return fail(ADSX_EINVAL, "index is NULL");
+    cudaError_t e = cudaSetDevice(ix->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return ADSX_OK;
+}
+
+// q' = P q for nq raw queries into a Dp-strided buffer (zero padded dims).
+cudaError_t rotate_queries(const Index *ix, const float *q_dev, int64_t nq, float *qrot,
+                           cudaStream_t s)
+{
+    return adsx::launch_nt_gemm(q_dev, nq, ix->D, ix->P, ix->D, ix->Dp, ix->D, qrot, ix->Dp,
+                                ix->Dp, false, s);
+}
+
+cudaError_t mark(const Index *ix, int i, cudaStream_t s)
+{
+    if (!ix->timing) return cudaSuccess;
+    return cudaEventRecord(ix->ev[i], s);
+}
+
+cudaError_t probe_queries(const Index *ix, const float *qrot, int64_t nq, int nprobe,
+                          int32_t *probes, float *pd2, Scratch &sc)
+{
+    float *dist = nullptr;
+    cudaError_t e = sc.get(&dist, (size_t)nq * ix->nlist);
+    if (e != cudaSuccess) return e;
+    e = adsx::launch_nt_gemm(qrot, nq, ix->Dp, ix->cents, ix->nlist, ix->Dp, ix->Dp, dist,
+                             ix->nlist, ix->nlist, true, sc.s);
+    if (e != cudaSuccess) return e;
+    if ((e = mark(ix, 2, sc.s)) != cudaSuccess) return e;
+    return adsx::launch_select_nprobe(dist, nq, ix->nlist, nprobe, probes, pd2, sc.s);
+}
+
+int finish(cudaStream_t s, bool any_host, const char *what)
+{
+    if (!any_host) return ADSX_OK;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return ADSX_OK;
+}
+
+int check_blocks(int32_t delta_d, float eps0)
+{
+    if (delta_d < 16 || (delta_d % 16) != 0)
+        return fail(ADSX_EINVAL, "delta_d must be a positive multiple of 16 (got %d)", delta_d);
+    if (!(eps0 >= 0.f)) return fail(ADSX_EINVAL, "eps0 must be >= 0 (got %g)", (double)eps0);
+    return ADSX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *adsx_last_error(void) { return g_last_error.c_str(); }
+
+int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
+                     const float *centroids, int32_t nlist, const int32_t *assign,
+                     int32_t storage, void *stream, adsx_index **out)
+{
+    if (!out) return fail(ADSX_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!X || !P || !centroids || !assign) return fail(ADSX_EINVAL, "NULL input pointer");
+    if (N < 1 || N >= (int64_t)1 << 31) return fail(ADSX_EINVAL, "N out of range");
+    if (D < 1 || D > ADSX_MAX_D) return fail(ADSX_EINVAL, "D out of range (1..%d)", ADSX_MAX_D);
+    if (nlist < 1 || nlist > ADSX_MAX_NLIST || nlist > N)
+        return fail(ADSX_EINVAL, "nlist out of range (1..min(N, %d))", ADSX_MAX_NLIST);
+    if (storage != ADSX_F32) return fail(ADSX_EINVAL, "storage type %d not supported", storage);
+    if (is_device_ptr(X) || is_device_ptr(P) || is_device_ptr(centroids) || is_device_ptr(assign))
+        return fail(ADSX_EINVAL, "adsx_build_index takes host pointers");
+
+    // P must be orthogonal (Sec. 3.1): max |P^T P - I| <= 1e-4.
+    {
+        std::vector<double> G((size_t)D * D, 0.0);
+        for (int32_t k = 0; k < D; ++k) {
+            const float *row = P + (size_t)k * D;
+            for (int32_t i = 0; i < D; ++i) {
+                const double pi = row[i];
+                double *g = &G[(size_t)i * D];
+                for (int32_t j = 0; j < D; ++j) g[j] += pi * (double)row[j];
+            }
+        }
+        double worst = 0.0;
+        for (int32_t i = 0; i < D; ++i)
+            for (int32_t j = 0; j < D; ++j)
+                worst = std::max(worst, fabs(G[(size_t)i * D + j] - (i == j ? 1.0 : 0.0)));
+        if (!(worst <= 1e-4)) return fail(ADSX_EINVAL, "P is not orthogonal (max|P^T P - I| = %g)", worst);
+    }
+    // Inverted file (Sec. 2.2.2): stable counting sort by cluster.
+    std::vector<int64_t> off((size_t)nlist + 1, 0), pos((size_t)N);
+    for (int64_t n = 0; n < N; ++n) {
+        int32_t c = assign[n];
+        if (c < 0 || c >= nlist) return fail(ADSX_EINVAL, "assign[%lld] = %d out of range", (long long)n, c);
+        off[(size_t)c + 1]++;
+    }
+    for (int32_t c = 0; c < nlist; ++c) off[(size_t)c + 1] += off[(size_t)c];
+    std::vector<int32_t> ids((size_t)N);
+    {
+        std::vector<int64_t> fill(off.begin(), off.end() - 1);
+        for (int64_t n = 0; n < N; ++n) {
+            int64_t p = fill[(size_t)assign[n]]++;
+            pos[(size_t)n] = p;
+            ids[(size_t)p] = (int32_t)n;
+        }
+    }
+    std::vector<int32_t> tile_off((size_t)nlist + 1, 0);
+    for (int32_t c = 0; c < nlist; ++c) {
+        int64_t t = tile_off[(size_t)c] + (off[(size_t)c + 1] - off[(size_t)c] + 31) / 32;
+        if (t >= (int64_t)1 << 31) return fail(ADSX_EINVAL, "too many tiles");
+        tile_off[(size_t)c + 1] = (int32_t)t;
+    }
+
+    Index *ix = new Index();
+    ix->N = N;
+    ix->D = D;
+    ix->Dp = (D + 15) / 16 * 16;
+    ix->nlist = nlist;
+    ix->storage = storage;
+    ix->h_off = off;
+    ix->total_tiles = tile_off[(size_t)nlist];
+    cudaGetDevice(&ix->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int Dp = ix->Dp;
+
+    auto cleanup = [&](int rc) {
+        adsx_free_index(reinterpret_cast<adsx_index *>(ix));
+        return rc;
+    };
+    auto dalloc = [&](void **p, size_t bytes) -> cudaError_t {
+        cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+        if (e == cudaSuccess) ix->bytes += (int64_t)bytes;
+        return e;
+    };
+    cudaError_t e;
+#define BCK(call, what)                                        \
+    do {                                                       \
+        e = (call);                                            \
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, what)); \
+    } while (0)
+
+    BCK(dalloc((void **)&ix->P, sizeof(float) * Dp * Dp), "alloc P");
+    BCK(dalloc((void **)&ix->cents, sizeof(float) * (size_t)nlist * Dp), "alloc centroids");
+    BCK(dalloc((void **)&ix->data, sizeof(float) * (size_t)N * Dp), "alloc data");
+    BCK(dalloc((void **)&ix->ids, sizeof(int32_t) * (size_t)N), "alloc ids");
+    BCK(dalloc((void **)&ix->off, sizeof(int64_t) * ((size_t)nlist + 1)), "alloc offsets");
+    BCK(dalloc((void **)&ix->tile_off, sizeof(int32_t) * ((size_t)nlist + 1)), "alloc tiles");
+    BCK(dalloc((void **)&ix->err, sizeof(unsigned)), "alloc error word");
+
+    // P padded to Dp x Dp with zeros: padded rotated dims are exactly 0.
+    {
+        std::vector<float> Pp((size_t)Dp * Dp, 0.f);
+        for (int32_t i = 0; i < D; ++i) memcpy(&Pp[(size_t)i * Dp], P + (size_t)i * D, sizeof(float) * D);
+        BCK(cudaMemcpyAsync(ix->P, Pp.data(), sizeof(float) * Dp * Dp, cudaMemcpyHostToDevice, s), "copy P");
+        BCK(cudaStreamSynchronize(s), "sync");
+    }
+    BCK(cudaMemcpyAsync(ix->ids, ids.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, s), "copy ids");
+    BCK(cudaMemcpyAsync(ix->off, off.data(), sizeof(int64_t) * (nlist + 1), cudaMemcpyHostToDevice, s), "copy off");
+    BCK(cudaMemcpyAsync(ix->tile_off, tile_off.data(), sizeof(int32_t) * (nlist + 1), cudaMemcpyHostToDevice, s), "copy tiles");
+    BCK(cudaMemsetAsync(ix->err, 0, sizeof(unsigned), s), "clear error word");
+
+    {
+        Scratch sc(s);
+        float *xd = nullptr, *yd = nullptr, *cd = nullptr;
+        int32_t *ad = nullptr;
+        int64_t *pd = nullptr;
+        BCK(sc.get(&xd, (size_t)N * D), "alloc X");
+        BCK(sc.get(&yd, (size_t)N * Dp), "alloc Y");
+        BCK(sc.get(&ad, (size_t)N), "alloc assign");
+        BCK(sc.get(&pd, (size_t)N), "alloc positions");
+        BCK(sc.get(&cd, (size_t)nlist * D), "alloc C");
+        BCK(cudaMemcpyAsync(xd, X, sizeof(float) * N * D, cudaMemcpyHostToDevice, s), "copy X");
+        BCK(cudaMemcpyAsync(ad, assign, sizeof(int32_t) * N, cudaMemcpyHostToDevice, s), "copy assign");
+        BCK(cudaMemcpyAsync(pd, pos.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, s), "copy positions");
+        BCK(cudaMemcpyAsync(cd, centroids, sizeof(float) * (size_t)nlist * D, cudaMemcpyHostToDevice, s), "copy C");
+        // Sec. 3.1 / Sec. 6.1: rotate every data vector and centroid once.
+        BCK(adsx::launch_nt_gemm(xd, N, D, ix->P, D, Dp, D, yd, Dp, Dp, false, s), "rotate data");
+        BCK(adsx::launch_nt_gemm(cd, nlist, D, ix->P, D, Dp, D, ix->cents, Dp, Dp, false, s), "rotate centroids");
+        BCK(adsx::launch_scatter_layout(yd, N, Dp, ad, pd, ix->off, ix->data, s), "scatter layout");
+        BCK(cudaStreamSynchronize(s), "build sync");
+    }
+    BCK(cudaStreamSynchronize(s), "build sync");
+#undef BCK
+    *out = reinterpret_cast<adsx_index *>(ix);
+    return ADSX_OK;
+}
+
+int adsx_free_index(adsx_index *index)
+{
+    Index *ix = reinterpret_cast<Index *>(index);
+    if (!ix) return ADSX_OK;
+    cudaSetDevice(ix->device);
+    cudaDeviceSynchronize();
+    cudaFree(ix->P);
+    cudaFree(ix->cents);
+    cudaFree(ix->data);
+    cudaFree(ix->ids);
+    cudaFree(ix->off);
+    cudaFree(ix->tile_off);
+    cudaFree(ix->err);
+    for (cudaEvent_t e : ix->ev)
+        if (e) cudaEventDestroy(e);
+    delete ix;
+    return ADSX_OK;
+}
+
+int adsx_index_info(const adsx_index *index, int64_t *N, int32_t *D, int32_t *nlist,
+                    int32_t *storage, int64_t *device_bytes)
+{
+    const Index *ix = reinterpret_cast<const Index *>(index);
+    if (!ix) return fail(ADSX_EINVAL, "index is NULL");
+    if (N) *N = ix->N;
+    if (D) *D = ix->D;
+    if (nlist) *nlist = ix->nlist;
+    if (storage) *storage = ix->storage;
+    if (device_bytes) *device_bytes = ix->bytes;
+    return ADSX_OK;
+}
+
+int adsx_rotate(const adsx_index *index, const float *Qv, int64_t nq, float *out, void *stream)
+{
+    const Index *ix = reinterpret_cast<const Index *>(index);
+    int rc = check_index(ix);
+    if (rc) return rc;
+    if (nq < 0 || (nq > 0 && (!Qv || !out))) return fail(ADSX_EINVAL, "bad query arguments");
+    if (nq == 0) return ADSX_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    Buf<float> q, o;
+    float *qrot = nullptr;
+    CK(stage_in(sc, Qv, (size_t)nq * ix->D, q), "stage queries");
+    CK(stage_out(sc, out, (size_t)nq * ix->D, o), "stage output");
+    CK(sc.get(&qrot, (size_t)nq * ix->Dp), "alloc q'");
+    CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
+    CK(cudaMemcpy2DAsync(o.dev, sizeof(float) * ix->D, qrot, sizeof(float) * ix->Dp,
+                         sizeof(float) * ix->D, (size_t)nq, cudaMemcpyDeviceToDevice, s), "copy q'");
+    CK(copy_back(o, s), "copy back");
+    return finish(s, o.host != nullptr, "rotate");
+}
+
+int adsx_probe(const adsx_index *index, const float *Qv, int64_t nq, int32_t nprobe,
+               int32_t *probes, float *probe_d2, void *stream)
+{
+    const Index *ix = reinterpret_cast<const Index *>(index);
+    int rc = check_index(ix);
+    if (rc) return rc;
+    if (nq < 0 || (nq > 0 && (!Qv || !probes))) return fail(ADSX_EINVAL, "bad query arguments");
+    if (nprobe < 1 || nprobe > ix->nlist || nprobe > ADSX_MAX_NPROBE)
+        return fail(ADSX_EINVAL, "nprobe out of range (1..min(nlist, %d))", ADSX_MAX_NPROBE);
+    if (nq == 0) return ADSX_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    Buf<float> q, pd;
+    Buf<int32_t> pr;
+    float *qrot = nullptr;
+    CK(stage_in(sc, Qv, (size_t)nq * ix->D, q), "stage queries");
+    CK(stage_out(sc, probes, (size_t)nq * nprobe, pr), "stage probes");
+    CK(stage_out(sc, probe_d2, (size_t)nq * nprobe, pd), "stage probe distances");
+    CK(sc.get(&qrot, (size_t)nq * ix->Dp), "alloc q'");
+    CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
+    CK(probe_queries(ix, qrot, nq, nprobe, pr.dev, pd.dev, sc), "probe");
+    CK(copy_back(pr, s), "copy back");
+    CK(copy_back(pd, s), "copy back");
+    return finish(s, pr.host || pd.host, "probe");
+}
+
+int adsx_search(const adsx_index *index, const float *Qv, int64_t nq, int32_t K, int32_t nprobe,
+                float eps0, int32_t delta_d, int64_t *ids, float *dists, int64_t *dims_read,
+                void *stream)
+{
+    const Index *ix = reinterpret_cast<const Index *>(index);
+    int rc = check_index(ix);
+    if (rc) return rc;
+    if (nq < 0 || (nq > 0 && (!Qv || !ids || !dists))) return fail(ADSX_EINVAL, "bad query arguments");
+    if (K < 1 || K > ADSX_MAX_K) return fail(ADSX_EINVAL, "K out of range (1..%d)", ADSX_MAX_K);
+    if (nprobe < 1 || nprobe > ix->nlist || nprobe > ADSX_MAX_NPROBE)
+        return fail(ADSX_EINVAL, "nprobe out of range (1..min(nlist, %d))", ADSX_MAX_NPROBE);
+    if ((rc = check_blocks(delta_d, eps0))) return rc;
+    if (nq == 0) return ADSX_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    Buf<float> q, od;
+    Buf<int64_t> oi, odims;
+    float *qrot = nullptr;
+    int32_t *probes = nullptr;
+    unsigned *counter = nullptr;
+    CK(stage_in(sc, Qv, (size_t)nq * ix->D, q), "stage queries");
+    CK(stage_out(sc, ids, (size_t)nq * K, oi), "stage ids");
+    CK(stage_out(sc, dists, (size_t)nq * K, od), "stage dists");
+    CK(stage_out(sc, dims_read, (size_t)nq, odims), "stage dims");
+    CK(sc.get(&qrot, (size_t)nq * ix->Dp), "alloc q'");
+    CK(sc.get(&probes, (size_t)nq * nprobe), "alloc probes");
+    CK(sc.get(&counter, 1), "alloc counter");
+    CK(mark(ix, 0, s), "event");
+    CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
+    CK(mark(ix, 1, s), "event");
+    CK(probe_queries(ix, qrot, nq, nprobe, probes, nullptr, sc), "probe");
+    CK(mark(ix, 3, s), "event");
+
+    adsx::ScanArgs a;
+    a.data = ix->data;
+    a.ids = ix->ids;
+    a.off = ix->off;
+    a.qrot = qrot;
+    a.probes = probes;
+    a.nq = nq;
+    a.D = ix->D;
+    a.Dp = ix->Dp;
+    a.nblk = ix->Dp / adsx::BLK;
+    a.nprobe = nprobe;
+    a.K = K;
+    a.Kp = 1;
+    while (a.Kp < K) a.Kp <<= 1;
+    a.db = delta_d / adsx::BLK;
+    a.test_on = isinf(eps0) ? 0 : 1;
+    if (a.db >= a.nblk) a.test_on = 0;
+    a.eps0 = a.test_on ? eps0 : 0.f;
+    a.out_ids = oi.dev;
+    a.out_d2 = od.dev;
+    a.out_dims = odims.dev;
+    a.work_counter = counter;
+    a.err = ix->err;
+    CK(cudaMemsetAsync(counter, 0, sizeof(unsigned), s), "clear counter");
+    CK(adsx::launch_ads_scan(a, adsx::ads_scan_grid(a, ix->device), s), "scan");
+    CK(mark(ix, 4, s), "event");
+    if (ix->timing) const_cast<Index *>(ix)->timed_once = true;
+    CK(copy_back(oi, s), "copy back");
+    CK(copy_back(od, s), "copy back");
+    CK(copy_back(odims, s), "copy back");
+    bool any_host = oi.host || od.host || odims.host;
+    rc = finish(s, any_host, "search");
+    if (rc) return rc;
+    if (any_host) {
+        unsigned err = 0;
+        CK(cudaMemcpy(&err, ix->err, sizeof err, cudaMemcpyDeviceToHost), "read error word");
+        if (err) {
+            cudaMemset(ix->err, 0, sizeof(unsigned));
+            return fail(ADSX_ETIMEOUT, "a bounded device wait gave up (error word 0x%x)", err);
+        }
+    }
+    return ADSX_OK;
+}
+
+int adsx_dco_fixed_r(const adsx_index *index, const float *Qv, int64_t nq, const float *r2,
+                     float eps0, int32_t delta_d, uint8_t *decisions, int32_t *dims, void *stream)
+{
+    const Index *ix = reinterpret_cast<const Index *>(index);
+    int rc = check_index(ix);
+    if (rc) return rc;
+    if (nq < 0 || (nq > 0 && (!Qv || !r2 || !decisions))) return fail(ADSX_EINVAL, "bad arguments");
+    if (nq > 65535) return fail(ADSX_EINVAL, "nq > 65535 in one fixed-r call");
+    if ((rc = check_blocks(delta_d, eps0))) return rc;
+    if (nq == 0) return ADSX_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    Buf<float> q, rr;
+    Buf<uint8_t> dec;
+    Buf<int32_t> dm;
+    float *qrot = nullptr;
+    CK(stage_in(sc, Qv, (size_t)nq * ix->D, q), "stage queries");
+    CK(stage_in(sc, r2, (size_t)nq, rr), "stage r2");
+    CK(stage_out(sc, decisions, (size_t)nq * ix->N, dec), "stage decisions");
+    CK(stage_out(sc, dims, (size_t)nq * ix->N, dm), "stage dims");
+    CK(sc.get(&qrot, (size_t)nq * ix->Dp), "alloc q'");
+    CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
+    adsx::FixedRArgs a;
+    a.data = ix->data;
+    a.ids = ix->ids;
+    a.off = ix->off;
+    a.tile_off = ix->tile_off;
+    a.nlist = ix->nlist;
+    a.total_tiles = ix->total_tiles;
+    a.N = ix->N;
+    a.qrot = qrot;
+    a.r2 = rr.dev;
+    a.nq = nq;
+    a.D = ix->D;
+    a.Dp = ix->Dp;
+    a.nblk = ix->Dp / adsx::BLK;
+    a.db = delta_d / adsx::BLK;
+    a.test_on = isinf(eps0) ? 0 : 1;
+    if (a.db >= a.nblk) a.test_on = 0;
+    a.eps0 = a.test_on ? eps0 : 0.f;
+    a.decisions = dec.dev;
+    a.dims = dm.dev;
+    CK(adsx::launch_dco_fixed_r(a, s), "fixed-r scan");
+    CK(copy_back(dec, s), "copy back");
+    CK(copy_back(dm, s), "copy back");
+    return finish(s, dec.host || dm.host, "fixed-r");
+}
+
+int adsx_set_stage_timing(adsx_index *index, int32_t enable)
+{
+    Index *ix = reinterpret_cast<Index *>(index);
+    int rc = check_index(ix);
+    if (rc) return rc;
+    if (enable && !ix->ev[0])
+        for (cudaEvent_t &e : ix->ev) CK(cudaEventCreate(&e), "create event");
+    ix->timing = enable != 0;
+    return ADSX_OK;
+}
+
+int adsx_stage_ms(const adsx_index *index, float *ms)
+{
+    const Index *ix = reinterpret_cast<const Index *>(index);
+    int rc = check_index(ix);
+    if (rc) return rc;
+    if (!ms) return fail(ADSX_EINVAL, "ms is NULL");
+    if (!ix->timed_once || !ix->ev[0]) return fail(ADSX_EINVAL, "no timed search has run");
+    CK(cudaEventSynchronize(ix->ev[4]), "event sync");
+    for (int i = 0; i < 4; ++i) CK(cudaEventElapsedTime(&ms[i], ix->ev[i], ix->ev[i + 1]), "elapsed");
+    return ADSX_OK;
+}
+
+int adsx_stream_status(const adsx_index *index, void *stream)
+{
+    const Index *ix = reinterpret_cast<const Index *>(index);
+    int rc = check_index(ix);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize((cudaStream_t)stream), "sync");
+    unsigned err = 0;
+    CK(cudaMemcpy(&err, ix->err, sizeof err, cudaMemcpyDeviceToHost), "read error word");
+    if (err) {
+        cudaMemset(ix->err, 0, sizeof(unsigned));
+        return fail(ADSX_ETIMEOUT, "a bounded device wait gave up (error word 0x%x)", err);
+    }
+    return ADSX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,236 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Acceptance (FP32 storage):
+  - rotation within 1e-5 relative of the FP64 rotation of the same inputs;
+  - probed clusters identical except selection near-ties (the nprobe-th and
+    (nprobe+1)-th centroid distances within 1e-5 relative in FP64);
+  - fixed-r DCO decisions bit-exact except boundary cases whose oracle
+    margin is below 1e-5 relative (counted), dims equal where decisions agree;
+  - eps0 = inf: ids identical to exact IVF except near-tie queries, distances
+    within 1e-5 relative;
+  - eps0 = 2.1: every returned distance exact to 1e-5, the bracket invariant
+    (every true IVF top-K member that passes its DCO at the exact K-th
+    distance is returned), recall@K no worse than the sequential oracle's
+    IVF+ recall minus 0.002;
+  - FDScanning (eps0 = inf) and delta_d >= D bit-identical.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_09855_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def adsx_mod():
+    from paper_2303_09855_gb300 import adsx, build
+    build.build()
+    return adsx
+
+
+@pytest.fixture(scope="module")
+def c1(adsx_mod):
+    """10k x 128 Gaussian mixture, 100 queries, nlist 100 (the small
+    correctness configuration), with its oracle-side rotated arrays."""
+    wl = W.gen_gaussian_mixture()
+    ix = adsx_mod.build_index(wl.X, wl.P, wl.centroids, wl.assign)
+    Y = oracle.rotate(wl.P, wl.X)
+    Cr = oracle.rotate(wl.P, wl.centroids)
+    Qr = oracle.rotate(wl.P, wl.Q)
+    yield wl, ix, Y, Cr, Qr
+    ix.close()
+
+
+def _near_tie_queries(Cr, Qr, nprobe):
+    """Queries whose nprobe-th and (nprobe+1)-th centroid distances are within
+    REL in FP64 (their probe sets are not determined at FP32 precision)."""
+    if nprobe >= Cr.shape[0]:
+        return np.zeros(Qr.shape[0], bool)
+    _, pd = oracle.probe(Cr, Qr, nprobe + 1)
+    a, b = pd[:, nprobe - 1], pd[:, nprobe]
+    return (b - a) <= REL * np.maximum(b, 1e-30)
+
+
+def _kth_near_tie(d2, K):
+    if d2.shape[1] <= K:
+        return np.zeros(d2.shape[0], bool)
+    a, b = d2[:, K - 1], d2[:, K]
+    return (b - a) <= REL * np.maximum(b, 1e-30)
+
+
+def test_rotation_matches_fp64(c1):
+    wl, ix, Y, Cr, Qr = c1
+    got = ix.rotate(wl.Q)
+    scale = np.linalg.norm(Qr, axis=1, keepdims=True)
+    assert np.max(np.abs(got - Qr) / scale) < REL
+
+
+def test_probe_matches_oracle(c1):
+    wl, ix, Y, Cr, Qr = c1
+    for nprobe in (1, 10, 37, 100):
+        pr, pd = ix.probe(wl.Q, nprobe)
+        epr, epd = oracle.probe(Cr, Qr, nprobe)
+        tie = _near_tie_queries(Cr, Qr, nprobe)
+        assert tie.mean() < 0.05
+        ok = ~tie
+        # ordering inside the set may differ only between near-equal distances
+        assert all(set(pr[q]) == set(epr[q]) for q in np.nonzero(ok)[0])
+        assert np.max(np.abs(pd[ok] - epd[ok]) / np.maximum(epd[ok], 1e-30)) < 1e-4
+
+
+def test_fixed_r_decisions_bit_exact(c1):
+    wl, ix, Y, Cr, Qr = c1
+    _, kd = oracle.knn_exact(Y, Qr, 10)
+    for scale, eps0, dd in ((1.0, 2.1, 32), (1.0, 1.0, 16), (1.5, 2.1, 48), (0.7, 0.5, 16),
+                            (1.0, math.inf, 32), (1.0, 2.1, 128), (1.0, 0.0, 64)):
+        r2 = kd[:, -1] * scale
+        dec, dims = ix.dco_fixed_r(wl.Q, r2.astype(np.float32), eps0, dd)
+        edec, edims, emar = oracle.dco_fixed_r(Y, Qr, r2.astype(np.float32).astype(np.float64),
+                                               eps0, dd)
+        boundary = emar < REL
+        agree = dec == edec
+        assert np.all(agree | boundary), (scale, eps0, dd, int((~agree & ~boundary).sum()))
+        assert np.all(dims[agree] == edims[agree])
+        assert boundary.mean() < 1e-3
+
+
+def test_fd_scan_matches_exact_ivf(c1):
+    wl, ix, Y, Cr, Qr = c1
+    for K, nprobe in ((10, 10), (1, 3), (100, 25), (10, 100)):
+        ids, d2, dims = ix.search(wl.Q, K, nprobe, eps0=math.inf, delta_d=32, return_dims=True)
+        eids, ed2 = oracle.ivf_exact(Y, Cr, wl.assign, Qr, K + 1, nprobe)
+        skip = _near_tie_queries(Cr, Qr, nprobe) | _kth_near_tie(ed2, K)
+        ok = ~skip
+        assert skip.mean() < 0.05
+        assert np.array_equal(ids[ok], eids[ok, :K])
+        assert np.max(np.abs(d2[ok] - ed2[ok, :K]) / ed2[ok, :K]) < REL
+        _, _, _, ncand = oracle.ivf_ads(Y, Cr, wl.assign, Qr, K, nprobe, math.inf, 32)
+        assert np.array_equal(dims[ok], (ncand * wl.D)[ok])
+
+
+def test_fd_equals_full_step_bit_identical(c1):
+    wl, ix, *_ = c1
+    a = ix.search(wl.Q, 10, 10, eps0=math.inf, delta_d=32)
+    b = ix.search(wl.Q, 10, 10, eps0=2.1, delta_d=128)
+    c = ix.search(wl.Q, 10, 10, eps0=0.5, delta_d=256)
+    for x, y in ((a, b), (a, c)):
+        assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+
+
+@pytest.mark.parametrize("K,nprobe,eps0,dd", [(10, 10, 2.1, 32), (10, 20, 2.1, 16),
+                                              (100, 10, 2.1, 32), (1, 5, 1.5, 32),
+                                              (10, 10, 0.5, 16)])
+def test_ads_search_bracket_and_recall(c1, K, nprobe, eps0, dd):
+    wl, ix, Y, Cr, Qr = c1
+    ids, d2, dims = ix.search(wl.Q, K, nprobe, eps0=eps0, delta_d=dd, return_dims=True)
+    eids, ed2 = oracle.ivf_exact(Y, Cr, wl.assign, Qr, K + 1, nprobe)
+    oids, od2, odims, ncand = oracle.ivf_ads(Y, Cr, wl.assign, Qr, K, nprobe, eps0, dd)
+    gt_ids, _ = oracle.knn_exact(Y, Qr, K)
+    tie = _near_tie_queries(Cr, Qr, nprobe)
+    ok = ~tie
+    # every returned distance is the exact distance of that id
+    for q in np.nonzero(ok)[0]:
+        for i, d in zip(ids[q], d2[q]):
+            if i < 0:
+                continue
+            ex = np.sum((Y[i] - Qr[q]) ** 2)
+            assert abs(d - ex) <= REL * ex + 1e-6
+    # bracket: members passing their DCO at r* (the exact K-th candidate distance)
+    rstar = ed2[:, K - 1]
+    for q in np.nonzero(ok)[0]:
+        top = eids[q, :K]
+        top = top[top >= 0]
+        dec, _, mar = oracle.dco_fixed_r(Y[top], Qr[q:q + 1], np.array([rstar[q]]), eps0, dd)
+        must = set(top[(dec[0] == oracle.POSITIVE) & (mar[0] >= REL)].tolist())
+        assert must <= set(ids[q].tolist()), q
+    # recall no worse than the sequential oracle (the shared r is never below it
+    # at the same candidate set, so the GPU rejects no more true neighbours)
+    r_gpu = oracle.recall_at(ids[ok], gt_ids[ok], K)
+    r_orc = oracle.recall_at(oids[ok], gt_ids[ok], K)
+    assert r_gpu >= r_orc - 0.002, (r_gpu, r_orc)
+    # dims accounting: at least the first step of every candidate, at most all
+    first = min(dd, wl.D)
+    assert np.all(dims >= ncand * first) and np.all(dims <= ncand * wl.D)
+
+
+def test_device_pointer_path_matches_host_path(c1):
+    import torch
+    wl, ix, *_ = c1
+    a_ids, a_d = ix.search(wl.Q, 10, 10, eps0=math.inf)
+    Qd = torch.from_numpy(wl.Q).cuda()
+    b_ids, b_d = ix.search(Qd, 10, 10, eps0=math.inf)
+    torch.cuda.synchronize()
+    assert np.array_equal(a_ids, b_ids.cpu().numpy())
+    assert np.array_equal(a_d, b_d.cpu().numpy())
+    pr_h, _ = ix.probe(wl.Q, 10)
+    pr_d, _ = ix.probe(Qd, 10)
+    assert np.array_equal(pr_h, pr_d.cpu().numpy())
+
+
+def test_ragged_shapes_and_padding(adsx_mod):
+    """D not a multiple of 16 (zero-padded to 112), N not a multiple of 32,
+    empty and single-member clusters, K above the candidate count, nprobe =
+    nlist, one query and zero queries."""
+    rng = np.random.default_rng(5)
+    N, D, nlist = 1001, 100, 40
+    X = rng.standard_normal((N, D)).astype(np.float32)
+    Q = rng.standard_normal((7, D)).astype(np.float32)
+    P = W.make_P(D, 77).astype(np.float32)
+    C = rng.standard_normal((nlist, D)).astype(np.float32)
+    assign = rng.integers(0, nlist - 3, size=N).astype(np.int32)   # 3 empty clusters
+    assign[0] = nlist - 3                                            # a 1-member cluster
+    ix = adsx_mod.build_index(X, P, C, assign)
+    Y, Cr, Qr = (oracle.rotate(P, a) for a in (X, C, Q))
+    try:
+        for K, nprobe, eps0, dd in ((2000, 2, math.inf, 32), (5, nlist, math.inf, 16),
+                                    (5, 4, 2.1, 16), (3, 1, 1.0, 112), (7, 3, 2.1, 48)):
+            ids, d2 = ix.search(Q, K, nprobe, eps0=eps0, delta_d=dd)
+            eids, ed2 = oracle.ivf_exact(Y, Cr, assign, Qr, K, nprobe)
+            if math.isinf(eps0) or dd >= D:
+                ok = ~_near_tie_queries(Cr, Qr, nprobe)
+                assert np.array_equal(ids[ok], eids[ok])
+                fin = np.isfinite(ed2[ok])
+                assert np.array_equal(np.isfinite(d2[ok]), fin)
+                assert np.max(np.abs(d2[ok][fin] - ed2[ok][fin]) / ed2[ok][fin]) < REL
+            else:
+                for q in range(Q.shape[0]):
+                    got = [i for i in ids[q] if i >= 0]
+                    assert len(set(got)) == len(got)
+                    assert set(got) <= set(np.nonzero(np.isin(assign, oracle.probe(Cr, Qr[q:q+1], nprobe)[0][0]))[0])
+        one_ids, _ = ix.search(Q[:1], 5, 4, eps0=math.inf)
+        assert one_ids.shape == (1, 5)
+        z_ids, z_d = ix.search(Q[:0], 5, 4)
+        assert z_ids.shape == (0, 5)
+        dec, dims = ix.dco_fixed_r(Q[:2], np.array([np.inf, 0.0], np.float32), 2.1, 16)
+        assert np.all(dec[0] == oracle.POSITIVE) and np.all(dims[0] == D)
+        assert np.all(dec[1] != oracle.POSITIVE)
+    finally:
+        ix.close()
+
+
+def test_invalid_arguments_are_rejected(adsx_mod, c1):
+    wl, ix, *_ = c1
+    bad = [dict(K=0, nprobe=10, delta_d=32), dict(K=10, nprobe=0, delta_d=32),
+           dict(K=10, nprobe=101, delta_d=32), dict(K=10, nprobe=10, delta_d=24),
+           dict(K=2000, nprobe=10, delta_d=32), dict(K=10, nprobe=10, delta_d=0)]
+    for kw in bad:
+        with pytest.raises(adsx_mod.AdsxError) as e:
+            ix.search(wl.Q, kw["K"], kw["nprobe"], eps0=2.1, delta_d=kw["delta_d"])
+        assert e.value.code == adsx_mod.EINVAL
+    with pytest.raises(adsx_mod.AdsxError):
+        ix.search(wl.Q, 10, 10, eps0=-1.0)
+    P = wl.P.copy()
+    P[0, 0] += 0.01
+    with pytest.raises(adsx_mod.AdsxError) as e:
+        adsx_mod.build_index(wl.X, P, wl.centroids, wl.assign)
+    assert e.value.code == adsx_mod.EINVAL
+    a = wl.assign.copy()
+    a[3] = wl.nlist
+    with pytest.raises(adsx_mod.AdsxError):
+        adsx_mod.build_index(wl.X, wl.P, wl.centroids, a)
