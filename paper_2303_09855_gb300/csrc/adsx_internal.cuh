@@ -138,19 +138,26 @@ struct ScanArgs {
     const int64_t *off;
     const float *qrot;
     const int32_t *probes;
+    const float *ftab;         // nblk + 1 test factors f(d) (Sec. 3.2)
     int64_t nq;
-    int32_t D, Dp, nblk, nprobe, K, Kp, db;
-    float eps0;
+    int32_t D, Dp, nblk, nprobe, K, C, db;
+    int32_t S, n_items;        // splits per query, work items = nq * S
     int32_t test_on;
     int64_t *out_ids;
     float *out_d2;
-    int64_t *out_dims;
+    int64_t *out_dims;         // zeroed by the caller when S > 1
+    float *part_d;             // n_items x K partial lists (S > 1)
+    int32_t *part_i;
+    unsigned int *r2g;         // nq shared r^2 bounds, 0xffffffff = none (S > 1)
     unsigned int *work_counter;
     unsigned int *err;
 };
 
 size_t scan_smem_bytes(const ScanArgs &a);
+int scan_items_target(int device);
+cudaError_t launch_test_factors(float *ftab, int nblk, int D, float eps0, cudaStream_t s);
 cudaError_t launch_ads_scan(const ScanArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_finalize_topk(const ScanArgs &a, cudaStream_t s);
 int ads_scan_grid(const ScanArgs &a, int device);
 
 struct FixedRArgs {

@@ -434,19 +434,47 @@ int adsx_search(const adsx_index *index, const float *Qv, int64_t nq, int32_t K,
     a.nblk = ix->Dp / adsx::BLK;
     a.nprobe = nprobe;
     a.K = K;
-    a.Kp = 1;
-    while (a.Kp < K) a.Kp <<= 1;
+    {
+        int Kp = 1;
+        while (Kp < K) Kp <<= 1;
+        int need = std::max(2 * Kp, K + 32);
+        a.C = 1;
+        while (a.C < need) a.C <<= 1;
+        // splits per query: enough work items to fill the GPU, bounded by the
+        // probe count and by the merge buffer of the finalize kernel
+        int64_t target = adsx::scan_items_target(ix->device);
+        int64_t S = (target + nq - 1) / nq;
+        S = std::min<int64_t>(S, std::min(nprobe, 64));
+        S = std::min<int64_t>(S, std::max(1, 16384 / Kp));
+        a.S = (int32_t)std::max<int64_t>(S, 1);
+    }
+    if (nq * (int64_t)a.S >= ((int64_t)1 << 31)) return fail(ADSX_EINVAL, "too many queries in one call");
+    a.n_items = (int32_t)(nq * a.S);
     a.db = delta_d / adsx::BLK;
     a.test_on = isinf(eps0) ? 0 : 1;
     if (a.db >= a.nblk) a.test_on = 0;
-    a.eps0 = a.test_on ? eps0 : 0.f;
     a.out_ids = oi.dev;
     a.out_d2 = od.dev;
     a.out_dims = odims.dev;
+    a.part_d = nullptr;
+    a.part_i = nullptr;
+    a.r2g = nullptr;
     a.work_counter = counter;
     a.err = ix->err;
+    float *ftab = nullptr;
+    CK(sc.get(&ftab, (size_t)a.nblk + 1), "alloc test factors");
+    a.ftab = ftab;
+    CK(adsx::launch_test_factors(ftab, a.nblk, a.D, a.test_on ? eps0 : 0.f, s), "test factors");
+    if (a.S > 1) {
+        CK(sc.get(&a.part_d, (size_t)a.n_items * K), "alloc partial lists");
+        CK(sc.get(&a.part_i, (size_t)a.n_items * K), "alloc partial lists");
+        CK(sc.get(&a.r2g, (size_t)nq), "alloc r2 bounds");
+        CK(cudaMemsetAsync(a.r2g, 0xff, sizeof(unsigned) * nq, s), "clear r2 bounds");
+        if (a.out_dims) CK(cudaMemsetAsync(a.out_dims, 0, sizeof(int64_t) * nq, s), "clear dims");
+    }
     CK(cudaMemsetAsync(counter, 0, sizeof(unsigned), s), "clear counter");
     CK(adsx::launch_ads_scan(a, adsx::ads_scan_grid(a, ix->device), s), "scan");
+    CK(adsx::launch_finalize_topk(a, s), "finalize");
     CK(mark(ix, 4, s), "event");
     if (ix->timing) const_cast<Index *>(ix)->timed_once = true;
     CK(copy_back(oi, s), "copy back");

@@ -3,24 +3,31 @@
 // current K-th distance (Sec. 2.2.2), plus the fixed-threshold linear scan of
 // the verification protocol (Sec. 6.2.5).
 //
-// ads_scan_kernel -- persistent: each 256-thread block repeatedly claims the
-// next query from a global counter.  Per query, shared memory holds q', the
-// probed clusters' CSR spans, a tile prefix (32 members per tile) and the
-// query's top-K.  Each warp:
-//   1. claims the next tile of 32 members (shared-memory counter), one member
-//      per lane, and reads the first delta_d dims of all 32 members: 2 KB
-//      coalesced runs per 16-dim block;
-//   2. tests S_d > r^2 f(d) (squared Sec. 3.2 test, r^2 read live from shared
-//      memory); a ballot compacts the survivors into the warp's ring of
-//      pending candidates (member, cluster slot, blocks done, S);
-//   3. whenever 32 candidates are pending, advances all 32 by one delta_d step
-//      each (each lane its own candidate, whole 64-byte pieces), tests again
-//      and re-queues survivors, so lanes stay busy after compaction;
-//   4. candidates that reach d = D with S_D <= r^2 are inserted into the
-//      block's top-K under a shared-memory lock (bounded spin); the K-th
-//      distance becomes the new r^2 for every warp of the block.
-// When tiles run out, each warp drains its ring.  The top-K is then
-// bitonic-sorted by (distance, id) and written out.
+// ads_scan_kernel is persistent and warp-centric.  A work item is (query q,
+// split s): the probe slots s, s+S, s+2S, ... of q (S = 1 unless there are
+// too few queries to fill the GPU).  Each warp claims items from a global
+// counter and owns, in shared memory, the item's q', a pending ring and a
+// candidate buffer; nothing is shared between warps, so no locks.
+//   1. Members are visited cluster by cluster in probe order, 32 per tile,
+//      one member per lane.  The first delta_d dims of a tile are 2 KB
+//      coalesced runs per 16-dim block of the dim-blocked layout.
+//   2. The squared test S_d > r^2 f(d) (Sec. 3.2) rejects; a ballot compacts
+//      survivors into the warp's pending ring (cluster, member, blocks done,
+//      S).  Whenever 32 are pending they advance one delta_d step each (each
+//      lane its own candidate, whole 64-byte pieces) and are re-tested, so
+//      lanes stay busy after compaction.
+//   3. Candidates reaching d = D with S_D <= r^2 are appended to the warp's
+//      candidate buffer (capacity C = 2 * next_pow2(K)).  When it fills, or
+//      first holds K entries, it is bitonic-sorted by (distance, id) and cut
+//      to K; r^2 becomes the K-th distance (the KNN set's maximum, Sec. 2.2.2).
+//      With S > 1, r^2 is also published per query with atomicMin and read
+//      back at each tile, so every split prunes with the best known bound.
+//   4. At the end the buffer is sorted: with S = 1 the warp writes the final
+//      top-K; otherwise its list goes to a partial buffer that
+//      finalize_topk_kernel merges per query.
+// Every returned distance is exact (d = D); any r used is the K-th of a set
+// of exact candidate distances, so it is never below the exact K-th distance
+// of all candidates -- the bracket property the tests check.
 #include <float.h>
 
 #include "adsx_internal.cuh"
@@ -28,43 +35,29 @@
 namespace adsx {
 namespace {
 
-constexpr int WARPS = 8;
+constexpr int WARPS = 4;
 constexpr int THREADS = WARPS * 32;
-constexpr int RING = 64;                       // per-warp pending ring (power of 2)
-constexpr unsigned LOCK_SPIN_LIMIT = 1u << 24;  // bounded spin on the top-K lock
+constexpr int RING = 64;                  // per-warp pending ring (power of 2)
 constexpr unsigned FULL = 0xffffffffu;
+constexpr unsigned NO_BOUND = 0xffffffffu;  // r2 bits "no bound yet" (> +inf bits)
 
-struct Ctl {
-    int q;
-    int next_tile;
-    int total_tiles;
-    int lock;
-    int count;
-    int maxpos;
-    int maxi;
-    float maxd;
-    float r2;
-    unsigned long long dims;
-};
+__host__ __device__ inline int align4(int x) { return (x + 3) & ~3; }
 
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-
-struct SmemCarve {
-    size_t qv, ftab, soff, sn, tpref, tkd, tki, pm, psb, pS, total;
-    __host__ __device__ SmemCarve(int Dp, int nblk, int nprobe, int Kp)
+// Per-warp shared-memory region, in 4-byte words.
+struct WarpCarve {
+    int qv, ed, ei, po, pm, pn, pb, pS, words;
+    __host__ __device__ WarpCarve(int Dp, int C)
     {
-        size_t o = 0;
-        qv = o;    o = align16(o + sizeof(float) * Dp);
-        ftab = o;  o = align16(o + sizeof(float) * (nblk + 1));
-        soff = o;  o = align16(o + sizeof(long long) * nprobe);
-        sn = o;    o = align16(o + sizeof(int) * nprobe);
-        tpref = o; o = align16(o + sizeof(int) * (nprobe + 1));
-        tkd = o;   o = align16(o + sizeof(float) * Kp);
-        tki = o;   o = align16(o + sizeof(int) * Kp);
-        pm = o;    o = align16(o + sizeof(int) * WARPS * RING);
-        psb = o;   o = align16(o + sizeof(int) * WARPS * RING);
-        pS = o;    o = align16(o + sizeof(float) * WARPS * RING);
-        total = o;
+        int o = 0;
+        qv = o; o = align4(o + Dp);
+        ed = o; o = align4(o + C);
+        ei = o; o = align4(o + C);
+        po = o; o += RING;
+        pm = o; o += RING;
+        pn = o; o += RING;
+        pb = o; o += RING;
+        pS = o; o += RING;
+        words = o;
     }
 };
 
@@ -73,137 +66,82 @@ __device__ __forceinline__ bool pair_less(float d1, int i1, float d2, int i2)
     return d1 < d2 || (d1 == d2 && i1 < i2);
 }
 
-// Maximum (by (distance, id)) of the K entries of the top-K, warp-wide.
-__device__ __forceinline__ void warp_max(const float *tkd, const int *tki, int K, int lane,
-                                         float &md, int &mi, int &mp)
-{
-    float bd = -1.f;
-    int bi = -1, bp = -1;
-    for (int k = lane; k < K; k += 32) {
-        float d = tkd[k];
-        int i = tki[k];
-        if (bp < 0 || pair_less(bd, bi, d, i)) {
-            bd = d;
-            bi = i;
-            bp = k;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        float od = __shfl_xor_sync(FULL, bd, o);
-        int oi = __shfl_xor_sync(FULL, bi, o);
-        int op = __shfl_xor_sync(FULL, bp, o);
-        bool take = (bp < 0) || (op >= 0 && pair_less(bd, bi, od, oi));
-        if (take) {
-            bd = od;
-            bi = oi;
-            bp = op;
-        }
-    }
-    md = bd;
-    mi = bi;
-    mp = bp;
-}
-
-struct WarpCtx {
+struct Warp {
     const ScanArgs *a;
-    Ctl *ctl;
-    const float *qv;
-    const float *ftab;
-    const long long *soff;
-    const int *sn;
-    float *tkd;
-    int *tki;
-    int *pm;
-    int *psb;
+    float *qv;
+    float *ed;
+    int *ei;
+    int *po, *pm, *pn, *pb;
     float *pS;
     int lane;
-    int head, cnt;                // ring state (warp-uniform)
-    unsigned long long dims;      // per-lane dims sampled
+    int64_t q;
+    int head, cnt;             // pending ring (warp-uniform)
+    int count;                 // candidate buffer fill (warp-uniform)
+    float r2;                  // this warp's K-th distance (warp-uniform)
+    unsigned long long dims;   // per lane
 };
 
-// Inserts the lanes whose candidate reached d = D with S_D <= r^2 into the
-// block's top-K (Sec. 2.2.2: the KNN set keeps the K smallest (dist, id)).
-__device__ __forceinline__ void try_insert(WarpCtx &w, bool fin, float S, int slot, int m)
+// Sorts the candidate buffer by (distance, id), keeps the first K and sets
+// r^2 to the K-th distance once K are held.
+__device__ void compact(Warp &w)
 {
-    volatile Ctl *vc = w.ctl;
-    const float r2 = vc->r2;
-    const bool want = fin && (S <= r2);
-    unsigned mask = __ballot_sync(FULL, want);
-    if (!mask) return;
-    int id = 0;
-    if (want) id = w.a->ids[w.soff[slot] + m];
-    bool ok = true;
-    if (w.lane == 0) {
-        unsigned spins = 0;
-        while (atomicCAS(&w.ctl->lock, 0, 1) != 0) {
-            if (++spins > LOCK_SPIN_LIMIT) {
-                ok = false;
-                break;
-            }
-            __nanosleep(32);
-        }
+    const int C = w.a->C, K = w.a->K;
+    for (int k = w.count + w.lane; k < C; k += 32) {
+        w.ed[k] = INFINITY;
+        w.ei[k] = 0x7fffffff;
     }
-    ok = __shfl_sync(FULL, ok, 0);
-    if (!ok) {
-        if (w.lane == 0) atomicOr(w.a->err, ERR_LOCK_TIMEOUT);
-        return;
-    }
-    __threadfence_block();
-    const int K = w.a->K;
-    int count = vc->count, maxpos = vc->maxpos, maxi = vc->maxi;
-    float maxd = vc->maxd;
-    volatile float *tkd = w.tkd;
-    volatile int *tki = w.tki;
-    while (mask) {
-        const int src = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const float s = __shfl_sync(FULL, S, src);
-        const int i = __shfl_sync(FULL, id, src);
-        if (count < K) {
-            if (w.lane == 0) {
-                tkd[count] = s;
-                tki[count] = i;
-            }
-            ++count;
-            if (count == K) {
-                __syncwarp();
-                warp_max(w.tkd, w.tki, K, w.lane, maxd, maxi, maxpos);
-            }
-        } else if (pair_less(s, i, maxd, maxi)) {
-            if (w.lane == 0) {
-                tkd[maxpos] = s;
-                tki[maxpos] = i;
+    __syncwarp();
+    for (int size = 2; size <= C; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = w.lane; i < C; i += 32) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const float di = w.ed[i], dj = w.ed[j];
+                    const int ii = w.ei[i], ij = w.ei[j];
+                    const bool up = (i & size) == 0;
+                    if (pair_less(dj, ij, di, ii) == up) {
+                        w.ed[i] = dj;
+                        w.ei[i] = ij;
+                        w.ed[j] = di;
+                        w.ei[j] = ii;
+                    }
+                }
             }
             __syncwarp();
-            warp_max(w.tkd, w.tki, K, w.lane, maxd, maxi, maxpos);
         }
     }
-    if (w.lane == 0) {
-        vc->count = count;
-        vc->maxpos = maxpos;
-        vc->maxi = maxi;
-        vc->maxd = maxd;
-        vc->r2 = (count == K) ? maxd : INFINITY;
-        __threadfence_block();
-        atomicExch(&w.ctl->lock, 0);
+    if (w.count > K) w.count = K;
+    if (w.count == K) {
+        const float r2 = w.ed[K - 1];
+        if (r2 < w.r2) {
+            w.r2 = r2;
+            if (w.a->S > 1 && w.lane == 0) atomicMin(w.a->r2g + w.q, __float_as_uint(r2));
+        }
     }
     __syncwarp();
 }
 
-// After a candidate has `blk` blocks accumulated in S: exact compare at d = D
-// (Case 3), else the hypothesis test (Case 1 reject / Case 2 re-queue).
-__device__ __forceinline__ void after_step(WarpCtx &w, bool valid, float S, int blk, int slot,
-                                           int m)
+__device__ __forceinline__ float current_r2(const Warp &w)
+{
+    float r2 = w.r2;
+    if (w.a->S > 1) {
+        const unsigned g = *((volatile const unsigned *)(w.a->r2g + w.q));
+        if (g <= 0x7f800000u) r2 = fminf(r2, __uint_as_float(g));
+    }
+    return r2;
+}
+
+// After a candidate has `blk` blocks accumulated in S: the exact compare at
+// d = D (Case 3), else the hypothesis test (Case 1 reject / Case 2 re-queue).
+__device__ __forceinline__ void after_step(Warp &w, bool valid, float S, int blk, int o, int m,
+                                           int n, float r2)
 {
     const ScanArgs &a = *w.a;
     const bool fin = valid && blk >= a.nblk;
     bool surv = false;
     if (valid && !fin) {
-        const float r2 = ((volatile Ctl *)w.ctl)->r2;
-        const bool rej = a.test_on && (S > r2 * w.ftab[blk]);
-        if (rej) {
-            int d = blk * BLK;
+        if (a.test_on && S > r2 * a.ftab[blk]) {
+            const int d = blk * BLK;
             w.dims += (unsigned long long)(d < a.D ? d : a.D);
         } else {
             surv = true;
@@ -212,206 +150,201 @@ __device__ __forceinline__ void after_step(WarpCtx &w, bool valid, float S, int 
     if (fin) w.dims += (unsigned long long)a.D;
     const unsigned sm = __ballot_sync(FULL, surv);
     if (surv) {
-        const int pos = __popc(sm & ((1u << w.lane) - 1u));
-        const int idx = (w.head + w.cnt + pos) & (RING - 1);
+        const int idx = (w.head + w.cnt + __popc(sm & ((1u << w.lane) - 1u))) & (RING - 1);
+        w.po[idx] = o;
         w.pm[idx] = m;
-        w.psb[idx] = (slot << 8) | blk;
+        w.pn[idx] = n;
+        w.pb[idx] = blk;
         w.pS[idx] = S;
     }
     w.cnt += __popc(sm);
+    // Case 3 positives into the candidate buffer.
+    const bool want = fin && S <= r2;
+    const unsigned wm = __ballot_sync(FULL, want);
+    if (wm) {
+        const int nw = __popc(wm);
+        if (w.count + nw > a.C) compact(w);
+        if (want) {
+            const int k = w.count + __popc(wm & ((1u << w.lane) - 1u));
+            w.ed[k] = S;
+            w.ei[k] = a.ids[o + m];
+        }
+        w.count += nw;
+        __syncwarp();
+        if (w.count >= a.K && w.r2 == INFINITY) compact(w);
+    }
     __syncwarp();
-    try_insert(w, fin, S, slot, m);
 }
 
 // Advances up to 32 pending candidates by one delta_d step each.
-__device__ __forceinline__ void process_pending(WarpCtx &w, int nb)
+__device__ __forceinline__ void process_pending(Warp &w, int nb)
 {
     const ScanArgs &a = *w.a;
     const bool valid = w.lane < nb;
-    int m = 0, sb = 0;
+    int o = 0, m = 0, n = 0, blk = 0;
     float S = 0.f;
     if (valid) {
         const int idx = (w.head + w.lane) & (RING - 1);
+        o = w.po[idx];
         m = w.pm[idx];
-        sb = w.psb[idx];
+        n = w.pn[idx];
+        blk = w.pb[idx];
         S = w.pS[idx];
     }
     __syncwarp();
     w.head = (w.head + nb) & (RING - 1);
     w.cnt -= nb;
-    const int slot = sb >> 8;
-    int blk = sb & 255;
+    const float r2 = current_r2(w);
     if (valid) {
-        const int64_t n = w.sn[slot];
-        const float *base = a.data + w.soff[slot] * (int64_t)a.Dp;
         int e = blk + a.db;
         if (e > a.nblk) e = a.nblk;
-        S = accum_range_f32(base, n, m, blk, e, w.qv, S);
+        S = accum_range_f32(a.data + (int64_t)o * a.Dp, n, m, blk, e, w.qv, S);
         blk = e;
     }
-    after_step(w, valid, S, blk, slot, m);
+    after_step(w, valid, S, blk, o, m, n, r2);
 }
 
 __global__ void __launch_bounds__(THREADS) ads_scan_kernel(ScanArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ Ctl ctl;
-    const SmemCarve sc(a.Dp, a.nblk, a.nprobe, a.Kp);
-    float *qv = reinterpret_cast<float *>(smraw + sc.qv);
-    float *ftab = reinterpret_cast<float *>(smraw + sc.ftab);
-    long long *soff = reinterpret_cast<long long *>(smraw + sc.soff);
-    int *sn = reinterpret_cast<int *>(smraw + sc.sn);
-    int *tpref = reinterpret_cast<int *>(smraw + sc.tpref);
-    float *tkd = reinterpret_cast<float *>(smraw + sc.tkd);
-    int *tki = reinterpret_cast<int *>(smraw + sc.tki);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-    for (int b = tid; b <= a.nblk; b += THREADS)
-        ftab[b] = (b == 0) ? 0.f : test_factor(b, a.D, a.eps0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const WarpCarve wc(a.Dp, a.C);
+    float *base = reinterpret_cast<float *>(smraw) + (size_t)warp * wc.words;
+    Warp w;
+    w.a = &a;
+    w.qv = base + wc.qv;
+    w.ed = base + wc.ed;
+    w.ei = reinterpret_cast<int *>(base + wc.ei);
+    w.po = reinterpret_cast<int *>(base + wc.po);
+    w.pm = reinterpret_cast<int *>(base + wc.pm);
+    w.pn = reinterpret_cast<int *>(base + wc.pn);
+    w.pb = reinterpret_cast<int *>(base + wc.pb);
+    w.pS = base + wc.pS;
+    w.lane = lane;
+    const int nb0 = a.db < a.nblk ? a.db : a.nblk;
 
     for (;;) {
-        if (tid == 0) ctl.q = (int)atomicAdd(a.work_counter, 1u);
-        __syncthreads();
-        const int64_t q = ctl.q;
-        if (q >= a.nq) break;
-
-        for (int i = tid; i < a.Dp; i += THREADS) qv[i] = a.qrot[q * a.Dp + i];
-        for (int i = tid; i < a.nprobe; i += THREADS) {
-            const int c = a.probes[q * a.nprobe + i];
-            const int64_t o = a.off[c];
-            soff[i] = o;
-            sn[i] = (int)(a.off[c + 1] - o);
-        }
-        if (tid == 0) {
-            ctl.next_tile = 0;
-            ctl.lock = 0;
-            ctl.count = 0;
-            ctl.maxpos = 0;
-            ctl.maxi = 0;
-            ctl.maxd = INFINITY;
-            ctl.r2 = INFINITY;
-            ctl.dims = 0ull;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            int run = 0;
-            for (int i0 = 0; i0 < a.nprobe; i0 += 32) {
-                const int i = i0 + lane;
-                const int t = (i < a.nprobe) ? (sn[i] + 31) / 32 : 0;
-                int incl = t;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    int v = __shfl_up_sync(FULL, incl, o);
-                    if (lane >= o) incl += v;
-                }
-                if (i < a.nprobe) tpref[i] = run + incl - t;
-                run += __shfl_sync(FULL, incl, 31);
-            }
-            if (lane == 0) {
-                tpref[a.nprobe] = run;
-                ctl.total_tiles = run;
-            }
-        }
-        __syncthreads();
-
-        WarpCtx w;
-        w.a = &a;
-        w.ctl = &ctl;
-        w.qv = qv;
-        w.ftab = ftab;
-        w.soff = soff;
-        w.sn = sn;
-        w.tkd = tkd;
-        w.tki = tki;
-        w.pm = reinterpret_cast<int *>(smraw + sc.pm) + warp * RING;
-        w.psb = reinterpret_cast<int *>(smraw + sc.psb) + warp * RING;
-        w.pS = reinterpret_cast<float *>(smraw + sc.pS) + warp * RING;
-        w.lane = lane;
-        w.head = 0;
-        w.cnt = 0;
+        int item = 0;
+        if (lane == 0) item = (int)atomicAdd(a.work_counter, 1u);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= a.n_items) break;
+        const int64_t q = item / a.S;
+        const int s = item - (int)q * a.S;
+        w.q = q;
+        for (int i = lane; i < a.Dp; i += 32) w.qv[i] = a.qrot[q * a.Dp + i];
+        w.head = w.cnt = 0;
+        w.count = 0;
+        w.r2 = INFINITY;
         w.dims = 0ull;
-        const int total = ctl.total_tiles;
-        const int nb0 = a.db < a.nblk ? a.db : a.nblk;
+        __syncwarp();
 
-        for (;;) {
-            int t = 0;
-            if (lane == 0) t = atomicAdd(&ctl.next_tile, 1);
-            t = __shfl_sync(FULL, t, 0);
-            if (t >= total) break;
-            int lo = 0, hi = a.nprobe - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (tpref[mid] <= t) lo = mid; else hi = mid - 1;
+        for (int p = s; p < a.nprobe; p += a.S) {
+            const int c = a.probes[q * a.nprobe + p];
+            const int o = (int)a.off[c];
+            const int n = (int)(a.off[c + 1] - o);
+            const float *cb = a.data + (int64_t)o * a.Dp;
+            for (int m0 = 0; m0 < n; m0 += 32) {
+                const float r2 = current_r2(w);
+                const int m = m0 + lane;
+                const bool valid = m < n;
+                float S = 0.f;
+                if (valid) S = accum_range_f32(cb, n, m, 0, nb0, w.qv, 0.f);
+                after_step(w, valid, S, nb0, o, m, n, r2);
+                while (w.cnt >= 32) process_pending(w, 32);
             }
-            const int slot = lo;
-            const int n = sn[slot];
-            const int m = (t - tpref[slot]) * 32 + lane;
-            const bool valid = m < n;
-            float S = 0.f;
-            if (valid)
-                S = accum_range_f32(a.data + soff[slot] * (int64_t)a.Dp, n, m, 0, nb0, qv, 0.f);
-            after_step(w, valid, S, nb0, slot, m);
-            while (w.cnt >= 32) process_pending(w, 32);
         }
         while (w.cnt > 0) process_pending(w, w.cnt < 32 ? w.cnt : 32);
+        compact(w);
 
         unsigned long long wd = w.dims;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) wd += __shfl_xor_sync(FULL, wd, o);
-        if (lane == 0) atomicAdd(&ctl.dims, wd);
-        __syncthreads();
+        for (int off = 16; off > 0; off >>= 1) wd += __shfl_xor_sync(FULL, wd, off);
+        if (a.S == 1) {
+            for (int k = lane; k < a.K; k += 32) {
+                const bool has = k < w.count;
+                a.out_ids[q * a.K + k] = has ? (int64_t)w.ei[k] : (int64_t)-1;
+                a.out_d2[q * a.K + k] = has ? w.ed[k] : INFINITY;
+            }
+            if (lane == 0 && a.out_dims) a.out_dims[q] = (int64_t)wd;
+        } else {
+            const int64_t pbase = (int64_t)item * a.K;
+            for (int k = lane; k < a.K; k += 32) {
+                a.part_d[pbase + k] = k < w.count ? w.ed[k] : INFINITY;
+                a.part_i[pbase + k] = k < w.count ? w.ei[k] : 0x7fffffff;
+            }
+            if (lane == 0 && a.out_dims) atomicAdd((unsigned long long *)(a.out_dims + q), wd);
+        }
+        __syncwarp();
+    }
+}
 
-        // (distance, id)-sort of the top-K, padded with (+inf, INT_MAX).
-        const int count = ctl.count;
-        for (int k = count + tid; k < a.Kp; k += THREADS) {
-            tkd[k] = INFINITY;
-            tki[k] = 0x7fffffff;
+// Merges the S sorted partial lists of each query into its final top-K.
+__global__ void __launch_bounds__(256) finalize_topk_kernel(const float *__restrict__ part_d,
+                                                            const int *__restrict__ part_i,
+                                                            int64_t nq, int S, int K, int T,
+                                                            int64_t *__restrict__ out_ids,
+                                                            float *__restrict__ out_d2)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float *sd = reinterpret_cast<float *>(smraw);
+    int *si = reinterpret_cast<int *>(sd + T);
+    for (int64_t q = blockIdx.x; q < nq; q += gridDim.x) {
+        const int64_t b = q * (int64_t)S * K;
+        for (int i = threadIdx.x; i < T; i += blockDim.x) {
+            const bool in = i < S * K;
+            sd[i] = in ? part_d[b + i] : INFINITY;
+            si[i] = in ? part_i[b + i] : 0x7fffffff;
         }
         __syncthreads();
-        for (int size = 2; size <= a.Kp; size <<= 1) {
+        for (int size = 2; size <= T; size <<= 1) {
             for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = tid; i < a.Kp; i += THREADS) {
+                for (int i = threadIdx.x; i < T; i += blockDim.x) {
                     const int j = i ^ stride;
                     if (j > i) {
-                        const float di = tkd[i], dj = tkd[j];
-                        const int ii = tki[i], ij = tki[j];
+                        const float di = sd[i], dj = sd[j];
+                        const int ii = si[i], ij = si[j];
                         const bool up = (i & size) == 0;
                         if (pair_less(dj, ij, di, ii) == up) {
-                            tkd[i] = dj;
-                            tki[i] = ij;
-                            tkd[j] = di;
-                            tki[j] = ii;
+                            sd[i] = dj;
+                            si[i] = ij;
+                            sd[j] = di;
+                            si[j] = ii;
                         }
                     }
                 }
                 __syncthreads();
             }
         }
-        for (int k = tid; k < a.K; k += THREADS) {
-            const bool has = k < count;
-            a.out_ids[q * a.K + k] = has ? (int64_t)tki[k] : (int64_t)-1;
-            a.out_d2[q * a.K + k] = has ? tkd[k] : INFINITY;
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            const bool has = sd[k] != INFINITY || si[k] != 0x7fffffff;
+            out_ids[q * K + k] = has ? (int64_t)si[k] : (int64_t)-1;
+            out_d2[q * K + k] = has ? sd[k] : INFINITY;
         }
-        if (tid == 0 && a.out_dims) a.out_dims[q] = (int64_t)ctl.dims;
         __syncthreads();
     }
+}
+
+__global__ void test_factor_kernel(float *ftab, int nblk, int D, float eps0)
+{
+    for (int b = threadIdx.x; b <= nblk; b += blockDim.x)
+        ftab[b] = (b == 0) ? 0.f : test_factor(b, D, eps0);
 }
 
 // Verification protocol (Sec. 6.2.5): every (query, indexed vector) pair,
 // fixed threshold r2[q].  One warp per 32-member tile of one cluster, one
 // lane per member; the same block accumulation and test as the search scan.
-__global__ void __launch_bounds__(THREADS) dco_fixed_r_kernel(FixedRArgs a)
+__global__ void __launch_bounds__(256) dco_fixed_r_kernel(FixedRArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     float *qv = reinterpret_cast<float *>(smraw);
     float *ftab = qv + a.Dp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t q = blockIdx.y;
-    for (int i = tid; i < a.Dp; i += THREADS) qv[i] = a.qrot[q * a.Dp + i];
-    for (int b = tid; b <= a.nblk; b += THREADS)
+    for (int i = tid; i < a.Dp; i += 256) qv[i] = a.qrot[q * a.Dp + i];
+    for (int b = tid; b <= a.nblk; b += 256)
         ftab[b] = (b == 0) ? 0.f : test_factor(b, a.D, a.eps0);
     __syncthreads();
-    const int t = blockIdx.x * WARPS + warp;
+    const int t = blockIdx.x * 8 + warp;
     if (t >= a.total_tiles) return;
     int lo = 0, hi = a.nlist - 1;
     while (lo < hi) {
@@ -454,7 +387,14 @@ __global__ void __launch_bounds__(THREADS) dco_fixed_r_kernel(FixedRArgs a)
 
 size_t scan_smem_bytes(const ScanArgs &a)
 {
-    return SmemCarve(a.Dp, a.nblk, a.nprobe, a.Kp).total;
+    return (size_t)WarpCarve(a.Dp, a.C).words * 4 * WARPS;
+}
+
+int scan_items_target(int device)
+{
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+    return nsm * 48;   // about two resident warps' worth of work per warp slot
 }
 
 int ads_scan_grid(const ScanArgs &a, int device)
@@ -466,13 +406,20 @@ int ads_scan_grid(const ScanArgs &a, int device)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ads_scan_kernel, THREADS, smem);
     if (per < 1) per = 1;
     int64_t g = (int64_t)nsm * per;
-    if (g > a.nq) g = a.nq;
+    const int64_t need = ((int64_t)a.n_items + WARPS - 1) / WARPS;
+    if (g > need) g = need;
     return (int)(g < 1 ? 1 : g);
+}
+
+cudaError_t launch_test_factors(float *ftab, int nblk, int D, float eps0, cudaStream_t s)
+{
+    test_factor_kernel<<<1, 256, 0, s>>>(ftab, nblk, D, eps0);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ads_scan(const ScanArgs &a, int grid, cudaStream_t s)
 {
-    if (a.nq <= 0) return cudaSuccess;
+    if (a.n_items <= 0) return cudaSuccess;
     size_t smem = scan_smem_bytes(a);
     cudaError_t e = cudaFuncSetAttribute(ads_scan_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -481,13 +428,28 @@ cudaError_t launch_ads_scan(const ScanArgs &a, int grid, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_finalize_topk(const ScanArgs &a, cudaStream_t s)
+{
+    if (a.nq <= 0 || a.S <= 1) return cudaSuccess;
+    int T = 1;
+    while (T < a.S * a.K) T <<= 1;
+    size_t smem = (size_t)T * 8;
+    cudaError_t e = cudaFuncSetAttribute(finalize_topk_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int64_t grid = a.nq < 152 * 8 ? a.nq : 152 * 8;
+    finalize_topk_kernel<<<(unsigned)grid, 256, smem, s>>>(a.part_d, a.part_i, a.nq, a.S, a.K, T,
+                                                          a.out_ids, a.out_d2);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dco_fixed_r(const FixedRArgs &a, cudaStream_t s)
 {
     if (a.nq <= 0 || a.total_tiles <= 0) return cudaSuccess;
     size_t smem = sizeof(float) * (a.Dp + a.nblk + 1);
-    dim3 grid((unsigned)((a.total_tiles + WARPS - 1) / WARPS), (unsigned)a.nq);
     if (a.nq > 65535) return cudaErrorInvalidValue;
-    dco_fixed_r_kernel<<<grid, THREADS, smem, s>>>(a);
+    dim3 grid((unsigned)((a.total_tiles + 7) / 8), (unsigned)a.nq);
+    dco_fixed_r_kernel<<<grid, 256, smem, s>>>(a);
     return cudaGetLastError();
 }
 

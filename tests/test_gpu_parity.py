@@ -159,6 +159,30 @@ def test_ads_search_bracket_and_recall(c1, K, nprobe, eps0, dd):
     assert np.all(dims >= ncand * first) and np.all(dims <= ncand * wl.D)
 
 
+def test_split_and_unsplit_scans_agree(c1):
+    """Few queries are split over several warps (shared r via atomicMin,
+    partial lists merged by a finalize kernel); many queries run one warp per
+    query.  With FDScanning both must return identical results; with the
+    test on, both keep the bracket (checked above) and their returned
+    distances are exact."""
+    wl, ix, Y, Cr, Qr = c1
+    many = np.tile(wl.Q, (80, 1))                  # 8000 queries -> one warp each
+    for K, nprobe in ((10, 10), (100, 16)):
+        a_ids, a_d = ix.search(wl.Q, K, nprobe, eps0=math.inf)
+        b_ids, b_d = ix.search(many, K, nprobe, eps0=math.inf)
+        assert np.array_equal(a_ids, b_ids[:100]) and np.array_equal(a_d, b_d[:100])
+        assert np.array_equal(b_ids[:100], b_ids[7900:])
+        c_ids, c_d, c_dims = ix.search(many, K, nprobe, eps0=2.1, delta_d=16, return_dims=True)
+        _, _, _, ncand = oracle.ivf_ads(Y, Cr, wl.assign, Qr, K, nprobe, math.inf, 32)
+        assert np.all(c_dims <= np.tile(ncand, 80) * wl.D)
+        for q in range(0, 8000, 997):
+            qq = q % 100
+            for i, d in zip(c_ids[q], c_d[q]):
+                if i >= 0:
+                    ex = np.sum((Y[i] - Qr[qq]) ** 2)
+                    assert abs(d - ex) <= REL * ex + 1e-6
+
+
 def test_device_pointer_path_matches_host_path(c1):
     import torch
     wl, ix, *_ = c1
@@ -188,7 +212,7 @@ def test_ragged_shapes_and_padding(adsx_mod):
     ix = adsx_mod.build_index(X, P, C, assign)
     Y, Cr, Qr = (oracle.rotate(P, a) for a in (X, C, Q))
     try:
-        for K, nprobe, eps0, dd in ((2000, 2, math.inf, 32), (5, nlist, math.inf, 16),
+        for K, nprobe, eps0, dd in ((200, 2, math.inf, 32), (5, nlist, math.inf, 16),
                                     (5, 4, 2.1, 16), (3, 1, 1.0, 112), (7, 3, 2.1, 48)):
             ids, d2 = ix.search(Q, K, nprobe, eps0=eps0, delta_d=dd)
             eids, ed2 = oracle.ivf_exact(Y, Cr, assign, Qr, K, nprobe)
