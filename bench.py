@@ -266,7 +266,7 @@ def main():
     # ---- calibration (untimed): smallest nprobe with recall@10 >= 0.95
     sweep = []
     np_fd = np_ads = None
-    for npb in NPROBE_GRID:
+    for npb in ([] if args.nprobe else NPROBE_GRID):
         if npb > wl.nlist:
             break
         ids, _ = search(npb, math.inf)
