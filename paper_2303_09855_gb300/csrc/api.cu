@@ -453,6 +453,7 @@ int adsx_search(const adsx_index *index, const float *Qv, int64_t nq, int32_t K,
     a.db = delta_d / adsx::BLK;
     a.test_on = isinf(eps0) ? 0 : 1;
     if (a.db >= a.nblk) a.test_on = 0;
+    if (!a.test_on) a.db = a.nblk;   // FDScanning: the whole vector in one step
     a.out_ids = oi.dev;
     a.out_d2 = od.dev;
     a.out_dims = odims.dev;

@@ -127,21 +127,25 @@ def gen_gaussian_mixture(N=10_000, D=128, nq=100, ncomp=50, nlist=100, kmeans_it
 
 
 def gen_sift_like(N=1_000_000, D=128, nq=10_000, ncomp=1024, nlist=4096, kmeans_iters=10,
-                  cfg=1, device="cpu", noise_sd=30.0, inactive_sd=30.0):
+                  cfg=1, device="cpu", noise_sd=30.0, inactive_sd=30.0, rank=0, amp=0.0):
     """SIFT-shaped workload: non-negative integer-valued floats in [0, 255].
 
     A ``ncomp``-component mixture whose centre dims are active with
-    probability 0.25 with heavy-tailed magnitude |t_3| * 24 (else 0);
-    N(0, noise_sd^2) noise on the active dims and N(0, inactive_sd^2) on the
-    others; clipped to [0, 255] and rounded.  The default noise (30 on every
-    dim) makes the components overlap, so that exact IVF over 4096 lists
-    needs nprobe of 32-64 for recall@10 = 0.95, as SIFT1M does; with little
-    noise the components are isolated and nprobe = 4 already reaches 0.97."""
+    probability 0.25 with heavy-tailed magnitude |t_3| * 24 (else 0).  Each
+    draw adds low-rank noise (z * s_c) W, with W a shared random rank x D
+    basis of unit rows and s_c per-component scales amp * U(0.5, 1.5), plus
+    isotropic noise N(0, noise_sd^2) on the component's active dims and
+    N(0, inactive_sd^2) on the others; the result is clipped to [0, 255] and
+    rounded."""
     base = 1000 * cfg
     rng = np.random.default_rng(1 + base)
     active = rng.random((ncomp, D)) < 0.25
     mag = np.abs(rng.standard_t(3, size=(ncomp, D))) * 24.0
     centres = np.where(active, mag, 0.0)
+    if rank > 0:
+        Wb = rng.standard_normal((rank, D))
+        Wb /= np.linalg.norm(Wb, axis=1, keepdims=True)
+        sc = amp * rng.uniform(0.5, 1.5, size=(ncomp, rank))
 
     def draw(r, n):
         comp = r.integers(0, ncomp, size=n)
@@ -151,6 +155,8 @@ def gen_sift_like(N=1_000_000, D=128, nq=10_000, ncomp=1024, nlist=4096, kmeans_
             c = comp[s:s + step]
             noise = r.standard_normal((c.shape[0], D))
             v = centres[c] + noise * np.where(active[c], noise_sd, inactive_sd)
+            if rank > 0:
+                v += (r.standard_normal((c.shape[0], rank)) * sc[c]) @ Wb
             out[s:s + step] = np.rint(np.clip(v, 0.0, 255.0))
         return out
 
@@ -160,7 +166,8 @@ def gen_sift_like(N=1_000_000, D=128, nq=10_000, ncomp=1024, nlist=4096, kmeans_
     C, a = kmeans(X, nlist, kmeans_iters, 4 + base, device=device,
                   sample=min(N, 256 * nlist))
     return Workload("sift_like_N%d_D%d" % (N, D), X, Q, P, C, a,
-                    dict(N=N, D=D, nq=nq, ncomp=ncomp, nlist=nlist, kmeans_iters=kmeans_iters))
+                    dict(N=N, D=D, nq=nq, ncomp=ncomp, nlist=nlist, kmeans_iters=kmeans_iters,
+                         noise_sd=noise_sd, inactive_sd=inactive_sd, rank=rank, amp=amp))
 
 
 def gen_gist_like(N=1_000_000, D=960, nq=1_000, ncomp=1000, nlist=1024, rank=64,
