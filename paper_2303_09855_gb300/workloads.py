@@ -127,7 +127,7 @@ def gen_gaussian_mixture(N=10_000, D=128, nq=100, ncomp=50, nlist=100, kmeans_it
 
 
 def gen_sift_like(N=1_000_000, D=128, nq=10_000, ncomp=1024, nlist=4096, kmeans_iters=10,
-                  cfg=1, device="cpu", noise_sd=30.0, inactive_sd=30.0, rank=0, amp=0.0):
+                  cfg=1, device="cpu", noise_sd=6.0, inactive_sd=3.0, rank=16, amp=70.0):
     """SIFT-shaped workload: non-negative integer-valued floats in [0, 255].
 
     A ``ncomp``-component mixture whose centre dims are active with
@@ -136,7 +136,12 @@ def gen_sift_like(N=1_000_000, D=128, nq=10_000, ncomp=1024, nlist=4096, kmeans_
     basis of unit rows and s_c per-component scales amp * U(0.5, 1.5), plus
     isotropic noise N(0, noise_sd^2) on the component's active dims and
     N(0, inactive_sd^2) on the others; the result is clipped to [0, 255] and
-    rounded."""
+    rounded.  The defaults give each component a low intrinsic dimension
+    (rank 16) and make components overlap, so exact IVF over 4096 lists
+    reaches recall@10 = 0.95 between nprobe 32 and 64, as SIFT1M does
+    (measured: 0.937 at 32, 0.971 at 64); isotropic-only noise either
+    isolates the components (nprobe 4 suffices) or concentrates distances
+    (no early rejection is possible), neither of which resembles SIFT."""
     base = 1000 * cfg
     rng = np.random.default_rng(1 + base)
     active = rng.random((ncomp, D)) < 0.25
