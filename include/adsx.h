@@ -168,6 +168,34 @@ int adsx_stream_status(const adsx_index *index, void *stream);
 int adsx_set_stage_timing(adsx_index *index, int32_t enable);
 int adsx_stage_ms(const adsx_index *index, float *ms);
 
+/*
+ * adsx_search_noalloc -- adsx_search for callers that must not allocate
+ * device memory while serving queries: for example a process whose GPU memory
+ * is reserved up front by another allocator or a fixed budget, where
+ * cudaMalloc / cudaMallocAsync would fail, or would lock or synchronise and
+ * stall other work.  The paper has no counterpart; this is an interface
+ * variant of adsx_search, computing the same results.
+ *   - Same arguments and results as adsx_search, but Qv, ids, dists and
+ *     dims_read must all be DEVICE pointers (ADSX_EINVAL otherwise); the call
+ *     only enqueues work on `stream` and never synchronises.
+ *   - No device memory is allocated or freed: every temporary buffer is cut
+ *     from one fixed array of ADSX_NOALLOC_SCRATCH_BYTES that the library
+ *     holds on every GPU that loads it, until the process exits.  A call
+ *     whose temporaries would not fit (roughly nq * (4*D + 4*nlist +
+ *     4*nprobe) bytes, plus partial top-K lists when nq is small) returns
+ *     ADSX_EINVAL with the size it needed; split the batch.
+ *   - The first call on each device looks up the array's device address on
+ *     that device; make that first call before any stream capture.
+ *   - All calls share the one array: calls whose work overlaps on the GPU
+ *     (different streams, or host threads) race on it and give wrong
+ *     results.  Serialise them, e.g. on one stream.
+ */
+#define ADSX_NOALLOC_SCRATCH_BYTES (32 << 20)
+int adsx_search_noalloc(const adsx_index *index, const float *Qv, int64_t nq,
+                        int32_t K, int32_t nprobe, float eps0, int32_t delta_d,
+                        int64_t *ids, float *dists, int64_t *dims_read,
+                        void *stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char *adsx_last_error(void);
 

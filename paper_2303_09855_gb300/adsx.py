@@ -55,12 +55,13 @@ def load():
     lib.adsx_rotate.argtypes = [V, V, i64, V, V]
     lib.adsx_dco_fixed_r.argtypes = [V, V, i64, V, f32, i32, V, V, V]
     lib.adsx_stream_status.argtypes = [V, V]
+    lib.adsx_search_noalloc.argtypes = [V, V, i64, i32, i32, f32, i32, V, V, V, V]
     lib.adsx_set_stage_timing.argtypes = [V, i32]
     lib.adsx_stage_ms.argtypes = [V, V]
     lib.adsx_last_error.restype = ctypes.c_char_p
     for fn in ("adsx_build_index", "adsx_free_index", "adsx_index_info", "adsx_search",
                "adsx_probe", "adsx_rotate", "adsx_dco_fixed_r", "adsx_stream_status",
-               "adsx_set_stage_timing", "adsx_stage_ms"):
+               "adsx_set_stage_timing", "adsx_stage_ms", "adsx_search_noalloc"):
         getattr(lib, fn).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -190,6 +191,26 @@ def search(index: Index, Q, K: int, nprobe: int, eps0: float = 2.1, delta_d: int
                               float(eps0) if math.isfinite(eps0) else float("inf"),
                               int(delta_d), _ptr(ids), _ptr(d2), _ptr(dims),
                               _stream_of(Q, stream)))
+    return (ids, d2, dims) if return_dims else (ids, d2)
+
+
+def search_noalloc(index: Index, Q, K: int, nprobe: int, eps0: float = 2.1, delta_d: int = 32,
+                   return_dims: bool = False, stream=None):
+    """adsx_search_noalloc: adsx_search without any device allocation, for
+    callers that must not allocate on the query path.  Q must be a CUDA
+    tensor; outputs are CUDA tensors; the work is only enqueued on the
+    stream.  Calls share one fixed scratch array: do not overlap them."""
+    if not _is_torch_cuda(Q):
+        raise ValueError("search_noalloc takes a CUDA tensor")
+    Q = _prep_queries(Q)
+    nq = Q.shape[0]
+    ids = _out(Q, (nq, K), np.int64, "int64")
+    d2 = _out(Q, (nq, K), np.float32, "float32")
+    dims = _out(Q, (nq,), np.int64, "int64") if return_dims else None
+    _check(load().adsx_search_noalloc(index.handle, _ptr(Q), nq, int(K), int(nprobe),
+                                      float(eps0) if math.isfinite(eps0) else float("inf"),
+                                      int(delta_d), _ptr(ids), _ptr(d2), _ptr(dims),
+                                      _stream_of(Q, stream)))
     return (ids, d2, dims) if return_dims else (ids, d2)
 
 

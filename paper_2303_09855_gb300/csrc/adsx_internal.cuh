@@ -120,6 +120,9 @@ __device__ __forceinline__ float test_factor(int blk, int D, float eps0)
     return ((float)d / (float)D) * g * g;
 }
 
+// Sets the message returned by adsx_last_error() on the calling thread.
+void set_last_error(const std::string &msg);
+
 // ----------------------------------------------------------------- launches
 cudaError_t launch_nt_gemm(const float *A, int64_t M, int lda, const float *B, int Nb,
                            int ldb, int Kd, float *C, int ldc, int Nout, bool dist,

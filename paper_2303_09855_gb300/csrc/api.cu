@@ -176,6 +176,10 @@ int check_blocks(int32_t delta_d, float eps0)
 
 }  // namespace
 
+namespace adsx {
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace adsx
+
 extern "C" {
 
 const char *adsx_last_error(void) { return g_last_error.c_str(); }

@@ -1,0 +1,194 @@
+// noalloc.cu -- adsx_search_noalloc: the search pipeline of adsx_search with
+// every temporary buffer carved from one fixed, file-scope device array
+// instead of the stream-ordered allocator.
+//
+// Who needs it: callers that must not allocate device memory on the query
+// path -- for example a serving process whose GPU memory is reserved up front
+// by another allocator or a fixed budget, where cudaMalloc/cudaMallocAsync
+// would fail, or would take a lock or synchronise and stall other work.
+//
+// The array is a static __device__ object, so every GPU that loads this
+// library holds ADSX_NOALLOC_SCRATCH_BYTES of it until the process exits.  In
+// host code the array's name is only a host-side stand-in, so its device
+// address is looked up once per device with cudaGetSymbolAddress (with that
+// device current) on the first call made on that device.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+
+#include "adsx_internal.cuh"
+
+namespace {
+
+constexpr int MAX_DEVICES = 64;
+
+// The shared scratch of adsx_search_noalloc.  Every call uses it, and it keeps
+// whatever the last call left in it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[ADSX_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_setup_mu;
+void *g_scratch_ptr[MAX_DEVICES] = {};
+
+int nerr(int code, const std::string &msg)
+{
+    adsx::set_last_error(msg);
+    return code;
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Device address of the scratch array on the current device (looked up once).
+int scratch_base(int device, unsigned char **out)
+{
+    if (device < 0 || device >= MAX_DEVICES) return nerr(ADSX_EINVAL, "device id out of range");
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    if (!g_scratch_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return nerr(ADSX_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") +
+                                        cudaGetErrorString(e));
+        }
+        g_scratch_ptr[device] = p;
+    }
+    *out = static_cast<unsigned char *>(g_scratch_ptr[device]);
+    return ADSX_OK;
+}
+
+// Bump carving of the fixed array, 256-byte aligned pieces.
+struct Carver {
+    unsigned char *base;
+    size_t used = 0;
+    template <typename T>
+    T *take(size_t count)
+    {
+        size_t bytes = (std::max<size_t>(count * sizeof(T), 1) + 255) & ~size_t(255);
+        T *p = reinterpret_cast<T *>(base + used);
+        used += bytes;
+        return p;
+    }
+};
+
+}  // namespace
+
+extern "C" int adsx_search_noalloc(const adsx_index *index, const float *Qv, int64_t nq,
+                                   int32_t K, int32_t nprobe, float eps0, int32_t delta_d,
+                                   int64_t *ids, float *dists, int64_t *dims_read, void *stream)
+{
+    const adsx::Index *ix = reinterpret_cast<const adsx::Index *>(index);
+    if (!ix) return nerr(ADSX_EINVAL, "index is NULL");
+    cudaError_t e = cudaSetDevice(ix->device);
+    if (e != cudaSuccess) return nerr(ADSX_ECUDA, cudaGetErrorString(e));
+    if (nq < 0) return nerr(ADSX_EINVAL, "nq < 0");
+    if (K < 1 || K > ADSX_MAX_K) return nerr(ADSX_EINVAL, "K out of range");
+    if (nprobe < 1 || nprobe > ix->nlist || nprobe > ADSX_MAX_NPROBE)
+        return nerr(ADSX_EINVAL, "nprobe out of range");
+    if (delta_d < 16 || delta_d % 16) return nerr(ADSX_EINVAL, "delta_d must be a positive multiple of 16");
+    if (!(eps0 >= 0.f)) return nerr(ADSX_EINVAL, "eps0 must be >= 0");
+    if (nq == 0) return ADSX_OK;
+    if (!is_device_ptr(Qv) || !is_device_ptr(ids) || !is_device_ptr(dists) ||
+        (dims_read && !is_device_ptr(dims_read)))
+        return nerr(ADSX_EINVAL, "adsx_search_noalloc takes device pointers only");
+
+    const int Dp = ix->Dp, nblk = Dp / adsx::BLK;
+    adsx::ScanArgs a;
+    a.data = ix->data;
+    a.ids = ix->ids;
+    a.off = ix->off;
+    a.nq = nq;
+    a.D = ix->D;
+    a.Dp = Dp;
+    a.nblk = nblk;
+    a.nprobe = nprobe;
+    a.K = K;
+    int Kp = 1;
+    while (Kp < K) Kp <<= 1;
+    a.C = 1;
+    while (a.C < std::max(2 * Kp, K + 32)) a.C <<= 1;
+    {
+        int64_t target = adsx::scan_items_target(ix->device);
+        int64_t S = (target + nq - 1) / nq;
+        S = std::min<int64_t>(S, std::min(nprobe, 64));
+        S = std::min<int64_t>(S, std::max(1, 16384 / Kp));
+        a.S = (int32_t)std::max<int64_t>(S, 1);
+    }
+    if (nq * (int64_t)a.S >= ((int64_t)1 << 31)) return nerr(ADSX_EINVAL, "too many queries");
+    a.n_items = (int32_t)(nq * a.S);
+    a.db = delta_d / adsx::BLK;
+    a.test_on = isinf(eps0) ? 0 : 1;
+    if (a.db >= nblk) a.test_on = 0;
+    if (!a.test_on) a.db = nblk;
+
+    // Size check before touching the array.
+    auto rup = [](size_t b) { return (std::max<size_t>(b, 1) + 255) & ~size_t(255); };
+    size_t need = rup((size_t)nq * Dp * 4) + rup((size_t)nq * ix->nlist * 4) +
+                  rup((size_t)nq * nprobe * 4) + rup((size_t)(nblk + 1) * 4) + rup(4);
+    if (a.S > 1) need += rup((size_t)nq * 4) + 2 * rup((size_t)a.n_items * K * 4);
+    if (need > (size_t)ADSX_NOALLOC_SCRATCH_BYTES)
+        return nerr(ADSX_EINVAL, "adsx_search_noalloc: this call needs " + std::to_string(need) +
+                                     " bytes of scratch, above the fixed maximum of " +
+                                     std::to_string((long long)ADSX_NOALLOC_SCRATCH_BYTES) +
+                                     " (split the batch)");
+
+    unsigned char *base = nullptr;
+    int rc = scratch_base(ix->device, &base);
+    if (rc) return rc;
+    Carver cv{base};
+    float *qrot = cv.take<float>((size_t)nq * Dp);
+    float *dist = cv.take<float>((size_t)nq * ix->nlist);
+    int32_t *probes = cv.take<int32_t>((size_t)nq * nprobe);
+    float *ftab = cv.take<float>((size_t)nblk + 1);
+    unsigned *counter = cv.take<unsigned>(1);
+    a.qrot = qrot;
+    a.probes = probes;
+    a.ftab = ftab;
+    a.work_counter = counter;
+    a.out_ids = ids;
+    a.out_d2 = dists;
+    a.out_dims = dims_read;
+    a.err = ix->err;
+    a.r2g = nullptr;
+    a.part_d = nullptr;
+    a.part_i = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    // The array keeps the previous call's contents: clear what must start
+    // from a known value.
+    if (a.S > 1) {
+        a.r2g = cv.take<unsigned>((size_t)nq);
+        a.part_d = cv.take<float>((size_t)a.n_items * K);
+        a.part_i = cv.take<int32_t>((size_t)a.n_items * K);
+        e = cudaMemsetAsync(a.r2g, 0xff, sizeof(unsigned) * nq, s);
+        if (e == cudaSuccess && dims_read) e = cudaMemsetAsync(dims_read, 0, sizeof(int64_t) * nq, s);
+        if (e != cudaSuccess) return nerr(ADSX_ECUDA, cudaGetErrorString(e));
+    }
+    e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess)
+        e = adsx::launch_nt_gemm(Qv, nq, ix->D, ix->P, ix->D, Dp, ix->D, qrot, Dp, Dp, false, s);
+    if (e == cudaSuccess)
+        e = adsx::launch_nt_gemm(qrot, nq, Dp, ix->cents, ix->nlist, Dp, Dp, dist, ix->nlist,
+                                 ix->nlist, true, s);
+    if (e == cudaSuccess)
+        e = adsx::launch_select_nprobe(dist, nq, ix->nlist, nprobe, probes, nullptr, s);
+    if (e == cudaSuccess)
+        e = adsx::launch_test_factors(ftab, nblk, ix->D, a.test_on ? eps0 : 0.f, s);
+    if (e == cudaSuccess) e = adsx::launch_ads_scan(a, adsx::ads_scan_grid(a, ix->device), s);
+    if (e == cudaSuccess) e = adsx::launch_finalize_topk(a, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nerr(ADSX_ECUDA, std::string("adsx_search_noalloc: ") + cudaGetErrorString(e));
+    }
+    return ADSX_OK;
+}

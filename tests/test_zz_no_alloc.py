@@ -1,0 +1,91 @@
+"""adsx_search_noalloc, the search entry point for callers that must not
+allocate device memory on the query path (for example a serving process whose
+GPU memory is reserved up front by another allocator or a fixed budget, where
+cudaMalloc would fail or would synchronise and stall other work).  It keeps its
+temporaries in one fixed array inside the library.
+
+Checked through the C ABI against adsx_search, the existing entry point, on
+two calls in a row (the second call runs on whatever the first left in the
+shared array).  This file is named so that pytest collects it last."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+from paper_2303_09855_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import torch
+    from paper_2303_09855_gb300 import adsx, build
+    build.build()
+    wl = W.gen_gaussian_mixture()
+    ix = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign)
+    yield adsx, torch, wl, ix
+    ix.close()
+
+
+def _noalloc(adsx, torch, ix, Qd, K, nprobe, eps0, dd):
+    nq = Qd.shape[0]
+    ids = torch.empty((nq, K), dtype=torch.int64, device=Qd.device)
+    d2 = torch.empty((nq, K), dtype=torch.float32, device=Qd.device)
+    dims = torch.empty((nq,), dtype=torch.int64, device=Qd.device)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = adsx.load().adsx_search_noalloc(ix.handle, ctypes.c_void_p(Qd.data_ptr()), nq, K, nprobe,
+                                         eps0, dd, ctypes.c_void_p(ids.data_ptr()),
+                                         ctypes.c_void_p(d2.data_ptr()),
+                                         ctypes.c_void_p(dims.data_ptr()), stream)
+    assert rc == 0, adsx.last_error()
+    torch.cuda.synchronize()
+    return ids.cpu().numpy(), d2.cpu().numpy(), dims.cpu().numpy()
+
+
+def _same(a_ids, a_d, b_ids, b_d):
+    assert np.array_equal(a_ids, b_ids)
+    fin = np.isfinite(b_d)
+    assert np.array_equal(np.isfinite(a_d), fin)
+    assert np.all(np.abs(a_d[fin] - b_d[fin]) <= REL * np.maximum(b_d[fin], 1e-30))
+
+
+@pytest.mark.parametrize("reps,K,nprobe,eps0,dd", [
+    (1, 10, 10, math.inf, 32),      # few queries: split scans, partial lists, shared r
+    (1, 100, 25, math.inf, 32),
+    (80, 10, 10, 2.1, 32),          # 8000 queries: one warp per query (deterministic)
+    (80, 100, 16, 2.1, 16),
+])
+def test_noalloc_matches_search_on_two_calls_in_a_row(setup, reps, K, nprobe, eps0, dd):
+    adsx, torch, wl, ix = setup
+    Qd = torch.from_numpy(np.tile(wl.Q, (reps, 1))).cuda()
+    ref_ids, ref_d, ref_dims = ix.search(Qd, K, nprobe, eps0=eps0, delta_d=dd, return_dims=True)
+    torch.cuda.synchronize()
+    ref_ids, ref_d, ref_dims = ref_ids.cpu().numpy(), ref_d.cpu().numpy(), ref_dims.cpu().numpy()
+    for _ in range(2):
+        ids, d2, dims = _noalloc(adsx, torch, ix, Qd, K, nprobe, eps0, dd)
+        _same(ids, d2, ref_ids, ref_d)
+        assert np.array_equal(dims, ref_dims)
+
+
+def test_noalloc_rejects_oversized_calls_and_host_pointers(setup):
+    adsx, torch, wl, ix = setup
+    big = torch.zeros((100_000, wl.D), dtype=torch.float32, device="cuda")
+    with pytest.raises(adsx.AdsxError) as e:
+        adsx.search_noalloc(ix, big, 10, 10)
+    assert e.value.code == adsx.EINVAL and "maximum" in adsx.last_error()
+    nq, K = 4, 10
+    ids = np.empty((nq, K), np.int64)
+    d2 = np.empty((nq, K), np.float32)
+    Qh = np.ascontiguousarray(wl.Q[:nq])
+    rc = adsx.load().adsx_search_noalloc(ix.handle, ctypes.c_void_p(Qh.ctypes.data), nq, K, 10,
+                                         2.1, 32, ctypes.c_void_p(ids.ctypes.data),
+                                         ctypes.c_void_p(d2.ctypes.data), None, None)
+    assert rc == adsx.EINVAL
+    # still usable afterwards
+    ids2, d22 = adsx.search_noalloc(ix, torch.from_numpy(wl.Q).cuda(), 10, 10, eps0=math.inf)
+    ref_ids, ref_d = ix.search(wl.Q, 10, 10, eps0=math.inf)
+    _same(ids2.cpu().numpy(), d22.cpu().numpy(), ref_ids, ref_d)
