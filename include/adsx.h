@@ -71,7 +71,12 @@ typedef enum { ADSX_F32 = 0, ADSX_BF16 = 1, ADSX_F16 = 2 } adsx_dtype;
  *              (y = P x).  Orthogonality is checked: max |P^T P - I| <= 1e-4.
  *   centroids  host, nlist x D float32, IVF centroids in the raw space.
  *   assign     host, N int32, cluster of each vector, each in [0, nlist).
- *   storage    ADSX_F32 (the only storage type accepted by this version).
+ *   storage    ADSX_F32, ADSX_BF16 or ADSX_F16: the type of the dim-blocked
+ *              layout the scan reads.  16-bit types halve the bytes per
+ *              dimension; partial sums stay FP32, and the index also keeps an
+ *              FP32 copy of every rotated vector and its norm, from which each
+ *              candidate that reaches d = D and may be positive gets its exact
+ *              FP32 distance, so low precision moves only reject decisions.
  *   stream     work is enqueued on it and the call synchronises it.
  *   out        receives an opaque handle owning all of the index's device
  *              memory (rotated vectors in the dim-blocked per-cluster layout,

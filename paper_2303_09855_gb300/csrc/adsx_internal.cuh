@@ -10,6 +10,8 @@
 //   2 KB runs (FP32), and a single member's step is whole 64-byte pieces.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,7 +31,9 @@ struct Index {
     int device = 0;
     float *P = nullptr;        // Dp x Dp, zero padded, row-major (y = P x)
     float *cents = nullptr;    // nlist x Dp rotated centroids
-    float *data = nullptr;     // N x Dp, dim-blocked per cluster
+    void *data = nullptr;      // N x Dp of the storage type, dim-blocked per cluster
+    float *rows32 = nullptr;   // N x Dp FP32 rotated rows in CSR order (16-bit storage only)
+    float *norms = nullptr;    // N FP32 norms ||y|| in CSR order (16-bit storage only)
     int32_t *ids = nullptr;    // N: CSR position -> original id
     int64_t *off = nullptr;    // nlist + 1 CSR offsets
     int32_t *tile_off = nullptr;  // nlist + 1 prefix of ceil(n_c/32)
@@ -108,6 +112,100 @@ __device__ __forceinline__ float accum_range_f32(const float *__restrict__ base,
     return S;
 }
 
+// 16-bit storage: a 16-dim block is 32 bytes (one sector), converted to FP32
+// and accumulated in FP32 in dimension order.
+__device__ __forceinline__ void unpack8(uint4 w, float *v, __nv_bfloat16)
+{
+    const unsigned u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        v[2 * i] = __uint_as_float(u[i] << 16);
+        v[2 * i + 1] = __uint_as_float(u[i] & 0xffff0000u);
+    }
+}
+
+__device__ __forceinline__ void unpack8(uint4 w, float *v, __half)
+{
+    const unsigned u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __half2 h = *reinterpret_cast<const __half2 *>(&u[i]);
+        float2 f = __half22float2(h);
+        v[2 * i] = f.x;
+        v[2 * i + 1] = f.y;
+    }
+}
+
+template <typename H>
+__device__ __forceinline__ float accum_8h(uint4 w, const float *__restrict__ q, float S)
+{
+    float v[8];
+    unpack8(w, v, H());
+    const float4 q0 = reinterpret_cast<const float4 *>(q)[0];
+    const float4 q1 = reinterpret_cast<const float4 *>(q)[1];
+    float t;
+    t = v[0] - q0.x; S = fmaf(t, t, S);
+    t = v[1] - q0.y; S = fmaf(t, t, S);
+    t = v[2] - q0.z; S = fmaf(t, t, S);
+    t = v[3] - q0.w; S = fmaf(t, t, S);
+    t = v[4] - q1.x; S = fmaf(t, t, S);
+    t = v[5] - q1.y; S = fmaf(t, t, S);
+    t = v[6] - q1.z; S = fmaf(t, t, S);
+    t = v[7] - q1.w; S = fmaf(t, t, S);
+    return S;
+}
+
+// Blocks [b0, b1) of member m, 16-bit storage, two blocks per load batch.
+template <typename H>
+__device__ __forceinline__ float accum_range_h(const H *__restrict__ base, int64_t n, int64_t m,
+                                               int b0, int b1, const float *__restrict__ qv,
+                                               float S)
+{
+    const int64_t stride = n * BLK;
+    const H *x = base + (int64_t)b0 * stride + m * BLK;
+    int b = b0;
+    for (; b + 2 <= b1; b += 2, x += 2 * stride) {
+        const uint4 *p0 = reinterpret_cast<const uint4 *>(x);
+        const uint4 *p1 = reinterpret_cast<const uint4 *>(x + stride);
+        uint4 w0 = __ldg(p0), w1 = __ldg(p0 + 1), w2 = __ldg(p1), w3 = __ldg(p1 + 1);
+        const float *q = qv + b * BLK;
+        S = accum_8h<H>(w0, q, S);
+        S = accum_8h<H>(w1, q + 8, S);
+        S = accum_8h<H>(w2, q + 16, S);
+        S = accum_8h<H>(w3, q + 24, S);
+    }
+    if (b < b1) {
+        const uint4 *p0 = reinterpret_cast<const uint4 *>(x);
+        uint4 w0 = __ldg(p0), w1 = __ldg(p0 + 1);
+        const float *q = qv + b * BLK;
+        S = accum_8h<H>(w0, q, S);
+        S = accum_8h<H>(w1, q + 8, S);
+    }
+    return S;
+}
+
+__device__ __forceinline__ float accum_range(const float *base, int64_t n, int64_t m, int b0,
+                                             int b1, const float *qv, float S)
+{
+    return accum_range_f32(base, n, m, b0, b1, qv, S);
+}
+__device__ __forceinline__ float accum_range(const __nv_bfloat16 *base, int64_t n, int64_t m,
+                                             int b0, int b1, const float *qv, float S)
+{
+    return accum_range_h(base, n, m, b0, b1, qv, S);
+}
+__device__ __forceinline__ float accum_range(const __half *base, int64_t n, int64_t m, int b0,
+                                             int b1, const float *qv, float S)
+{
+    return accum_range_h(base, n, m, b0, b1, qv, S);
+}
+
+// Unit roundoff of the storage type (round to nearest): |x~ - x| <= u |x|.
+template <typename T> struct Roundoff;
+template <> struct Roundoff<float> { static constexpr float u = 0.f; };
+template <> struct Roundoff<__nv_bfloat16> { static constexpr float u = 1.0f / 256.0f; };
+template <> struct Roundoff<__half> { static constexpr float u = 1.0f / 2048.0f; };
+
 // Threshold factor of the squared test after `blk` blocks (Sec. 3.2):
 //   reject  iff  D*S_d > r^2 * d * (1+eps0/sqrt(d))^2
 //          iff  S_d > r^2 * f(d),   f(d) = (d/D) (1 + eps0/sqrt(d))^2,
@@ -128,15 +226,21 @@ cudaError_t launch_nt_gemm(const float *A, int64_t M, int lda, const float *B, i
                            int ldb, int Kd, float *C, int ldc, int Nout, bool dist,
                            cudaStream_t s);
 
+// Rotated rows Y (N x Dp, FP32) into the dim-blocked layout of `storage`
+// (ADSX_F32 / ADSX_BF16 / ADSX_F16); for 16-bit storage also the FP32 row copy
+// and the norms, both in CSR order.
 cudaError_t launch_scatter_layout(const float *Y, int64_t N, int Dp, const int32_t *assign,
-                                  const int64_t *pos_of_id, const int64_t *off, float *data,
-                                  cudaStream_t s);
+                                  const int64_t *pos_of_id, const int64_t *off, void *data,
+                                  int storage, float *rows32, float *norms, cudaStream_t s);
 
 cudaError_t launch_select_nprobe(const float *dist, int64_t nq, int nlist, int nprobe,
                                  int32_t *probes, float *probe_d2, cudaStream_t s);
 
 struct ScanArgs {
-    const float *data;
+    const void *data;          // storage type per `storage`
+    const float *rows32;       // FP32 rows (16-bit storage: exact recheck at d = D)
+    const float *norms;
+    int32_t storage;
     const int32_t *ids;
     const int64_t *off;
     const float *qrot;
@@ -164,7 +268,9 @@ cudaError_t launch_finalize_topk(const ScanArgs &a, cudaStream_t s);
 int ads_scan_grid(const ScanArgs &a, int device);
 
 struct FixedRArgs {
-    const float *data;
+    const void *data;
+    const float *rows32;
+    int32_t storage;
     const int32_t *ids;
     const int64_t *off;
     const int32_t *tile_off;

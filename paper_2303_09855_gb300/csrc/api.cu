@@ -195,7 +195,8 @@ int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
     if (D < 1 || D > ADSX_MAX_D) return fail(ADSX_EINVAL, "D out of range (1..%d)", ADSX_MAX_D);
     if (nlist < 1 || nlist > ADSX_MAX_NLIST || nlist > N)
         return fail(ADSX_EINVAL, "nlist out of range (1..min(N, %d))", ADSX_MAX_NLIST);
-    if (storage != ADSX_F32) return fail(ADSX_EINVAL, "storage type %d not supported", storage);
+    if (storage != ADSX_F32 && storage != ADSX_BF16 && storage != ADSX_F16)
+        return fail(ADSX_EINVAL, "storage type %d not supported", storage);
     if (is_device_ptr(X) || is_device_ptr(P) || is_device_ptr(centroids) || is_device_ptr(assign))
         return fail(ADSX_EINVAL, "adsx_build_index takes host pointers");
 
@@ -270,7 +271,12 @@ int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
 
     BCK(dalloc((void **)&ix->P, sizeof(float) * Dp * Dp), "alloc P");
     BCK(dalloc((void **)&ix->cents, sizeof(float) * (size_t)nlist * Dp), "alloc centroids");
-    BCK(dalloc((void **)&ix->data, sizeof(float) * (size_t)N * Dp), "alloc data");
+    const size_t esz = storage == ADSX_F32 ? 4 : 2;
+    BCK(dalloc((void **)&ix->data, esz * (size_t)N * Dp), "alloc data");
+    if (storage != ADSX_F32) {
+        BCK(dalloc((void **)&ix->rows32, sizeof(float) * (size_t)N * Dp), "alloc FP32 rows");
+        BCK(dalloc((void **)&ix->norms, sizeof(float) * (size_t)N), "alloc norms");
+    }
     BCK(dalloc((void **)&ix->ids, sizeof(int32_t) * (size_t)N), "alloc ids");
     BCK(dalloc((void **)&ix->off, sizeof(int64_t) * ((size_t)nlist + 1)), "alloc offsets");
     BCK(dalloc((void **)&ix->tile_off, sizeof(int32_t) * ((size_t)nlist + 1)), "alloc tiles");
@@ -305,7 +311,8 @@ int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
         // Sec. 3.1 / Sec. 6.1: rotate every data vector and centroid once.
         BCK(adsx::launch_nt_gemm(xd, N, D, ix->P, D, Dp, D, yd, Dp, Dp, false, s), "rotate data");
         BCK(adsx::launch_nt_gemm(cd, nlist, D, ix->P, D, Dp, D, ix->cents, Dp, Dp, false, s), "rotate centroids");
-        BCK(adsx::launch_scatter_layout(yd, N, Dp, ad, pd, ix->off, ix->data, s), "scatter layout");
+        BCK(adsx::launch_scatter_layout(yd, N, Dp, ad, pd, ix->off, ix->data, storage, ix->rows32,
+                                        ix->norms, s), "scatter layout");
         BCK(cudaStreamSynchronize(s), "build sync");
     }
     BCK(cudaStreamSynchronize(s), "build sync");
@@ -323,6 +330,8 @@ int adsx_free_index(adsx_index *index)
     cudaFree(ix->P);
     cudaFree(ix->cents);
     cudaFree(ix->data);
+    cudaFree(ix->rows32);
+    cudaFree(ix->norms);
     cudaFree(ix->ids);
     cudaFree(ix->off);
     cudaFree(ix->tile_off);
@@ -428,6 +437,9 @@ int adsx_search(const adsx_index *index, const float *Qv, int64_t nq, int32_t K,
 
     adsx::ScanArgs a;
     a.data = ix->data;
+    a.rows32 = ix->rows32;
+    a.norms = ix->norms;
+    a.storage = ix->storage;
     a.ids = ix->ids;
     a.off = ix->off;
     a.qrot = qrot;
@@ -523,6 +535,8 @@ int adsx_dco_fixed_r(const adsx_index *index, const float *Qv, int64_t nq, const
     CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
     adsx::FixedRArgs a;
     a.data = ix->data;
+    a.rows32 = ix->rows32;
+    a.storage = ix->storage;
     a.ids = ix->ids;
     a.off = ix->off;
     a.tile_off = ix->tile_off;

@@ -2,18 +2,49 @@
 // dimension-blocked per-cluster layout (Sec. 5.2 IVF++: the first dims of all
 // candidates stored together; here every 16-dim block of a cluster is stored
 // together, so any delta_d that is a multiple of 16 reads contiguous runs).
+// 16-bit storage types also get an FP32 copy of each rotated row and its
+// norm, in CSR order, for the exact recheck of candidates reaching d = D.
 #include "adsx_internal.cuh"
 
 namespace adsx {
 namespace {
 
-// One thread per (vector, 16-dim block): a 64-byte row piece read from the
-// row-major rotated matrix Y (coalesced along the row) and written to its
-// block of its cluster.
+__device__ __forceinline__ void store16(float *dst, const float *v)
+{
+    float4 *d = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) d[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+}
+
+__device__ __forceinline__ void store16(__nv_bfloat16 *dst, const float *v)
+{
+    __nv_bfloat162 h[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+    d[0] = *reinterpret_cast<uint4 *>(&h[0]);
+    d[1] = *reinterpret_cast<uint4 *>(&h[4]);
+}
+
+__device__ __forceinline__ void store16(__half *dst, const float *v)
+{
+    __half2 h[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) h[i] = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+    d[0] = *reinterpret_cast<uint4 *>(&h[0]);
+    d[1] = *reinterpret_cast<uint4 *>(&h[4]);
+}
+
+// One thread per (vector, 16-dim block): a 64-byte piece of the row-major
+// rotated matrix Y (coalesced along the row) written to its block of its
+// cluster (converted to the storage type).
+template <typename T>
 __global__ void scatter_layout_kernel(const float *__restrict__ Y, int64_t N, int Dp,
                                       const int32_t *__restrict__ assign,
                                       const int64_t *__restrict__ pos_of_id,
-                                      const int64_t *__restrict__ off, float *__restrict__ data)
+                                      const int64_t *__restrict__ off, T *__restrict__ data,
+                                      float *__restrict__ rows32)
 {
     const int nblk = Dp / BLK;
     const int64_t total = N * nblk;
@@ -24,26 +55,65 @@ __global__ void scatter_layout_kernel(const float *__restrict__ Y, int64_t N, in
         const int c = assign[id];
         const int64_t o = off[c];
         const int64_t n = off[c + 1] - o;
-        const int64_t m = pos_of_id[id] - o;
+        const int64_t p = pos_of_id[id];
+        const int64_t m = p - o;
+        float v[16];
         const float4 *src = reinterpret_cast<const float4 *>(Y + id * Dp + b * BLK);
-        float4 *dst = reinterpret_cast<float4 *>(data + o * Dp + (int64_t)b * n * BLK + m * BLK);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) dst[i] = src[i];
+        for (int i = 0; i < 4; ++i) {
+            float4 t = src[i];
+            v[4 * i] = t.x;
+            v[4 * i + 1] = t.y;
+            v[4 * i + 2] = t.z;
+            v[4 * i + 3] = t.w;
+        }
+        store16(data + o * Dp + (int64_t)b * n * BLK + m * BLK, v);
+        if (rows32) store16(rows32 + p * Dp + b * BLK, v);
+    }
+}
+
+// ||y|| of each FP32 row (CSR order), one warp per row.
+__global__ void row_norms_kernel(const float *__restrict__ rows32, int64_t N, int Dp,
+                                 float *__restrict__ norms)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < N;
+         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        float s = 0.f;
+        for (int j = lane; j < Dp; j += 32) {
+            float x = rows32[r * Dp + j];
+            s = fmaf(x, x, s);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) norms[r] = sqrtf(s);
     }
 }
 
 }  // namespace
 
 cudaError_t launch_scatter_layout(const float *Y, int64_t N, int Dp, const int32_t *assign,
-                                  const int64_t *pos_of_id, const int64_t *off, float *data,
-                                  cudaStream_t s)
+                                  const int64_t *pos_of_id, const int64_t *off, void *data,
+                                  int storage, float *rows32, float *norms, cudaStream_t s)
 {
     if (N <= 0) return cudaSuccess;
     int64_t total = N * (Dp / BLK);
     int64_t blocks = (total + 255) / 256;
     if (blocks > 152 * 64) blocks = 152 * 64;
-    scatter_layout_kernel<<<(unsigned)blocks, 256, 0, s>>>(Y, N, Dp, assign, pos_of_id, off,
-                                                           data);
+    if (storage == ADSX_F32)
+        scatter_layout_kernel<float><<<(unsigned)blocks, 256, 0, s>>>(
+            Y, N, Dp, assign, pos_of_id, off, static_cast<float *>(data), nullptr);
+    else if (storage == ADSX_BF16)
+        scatter_layout_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, s>>>(
+            Y, N, Dp, assign, pos_of_id, off, static_cast<__nv_bfloat16 *>(data), rows32);
+    else
+        scatter_layout_kernel<__half><<<(unsigned)blocks, 256, 0, s>>>(
+            Y, N, Dp, assign, pos_of_id, off, static_cast<__half *>(data), rows32);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || storage == ADSX_F32) return e;
+    int64_t nb = (N * 32 + 255) / 256;
+    if (nb > 152 * 64) nb = 152 * 64;
+    row_norms_kernel<<<(unsigned)nb, 256, 0, s>>>(rows32, N, Dp, norms);
     return cudaGetLastError();
 }
 

@@ -106,6 +106,9 @@ extern "C" int adsx_search_noalloc(const adsx_index *index, const float *Qv, int
     const int Dp = ix->Dp, nblk = Dp / adsx::BLK;
     adsx::ScanArgs a;
     a.data = ix->data;
+    a.rows32 = ix->rows32;
+    a.norms = ix->norms;
+    a.storage = ix->storage;
     a.ids = ix->ids;
     a.off = ix->off;
     a.nq = nq;

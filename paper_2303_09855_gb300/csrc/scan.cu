@@ -39,7 +39,6 @@ constexpr int WARPS = 4;
 constexpr int THREADS = WARPS * 32;
 constexpr int RING = 64;                  // per-warp pending ring (power of 2)
 constexpr unsigned FULL = 0xffffffffu;
-constexpr unsigned NO_BOUND = 0xffffffffu;  // r2 bits "no bound yet" (> +inf bits)
 
 __host__ __device__ inline int align4(int x) { return (x + 3) & ~3; }
 
@@ -66,6 +65,7 @@ __device__ __forceinline__ bool pair_less(float d1, int i1, float d2, int i2)
     return d1 < d2 || (d1 == d2 && i1 < i2);
 }
 
+template <typename T>
 struct Warp {
     const ScanArgs *a;
     float *qv;
@@ -83,7 +83,8 @@ struct Warp {
 
 // Sorts the candidate buffer by (distance, id), keeps the first K and sets
 // r^2 to the K-th distance once K are held.
-__device__ void compact(Warp &w)
+template <typename T>
+__device__ void compact(Warp<T> &w)
 {
     const int C = w.a->C, K = w.a->K;
     for (int k = w.count + w.lane; k < C; k += 32) {
@@ -121,7 +122,8 @@ __device__ void compact(Warp &w)
     __syncwarp();
 }
 
-__device__ __forceinline__ float current_r2(const Warp &w)
+template <typename T>
+__device__ __forceinline__ float current_r2(const Warp<T> &w)
 {
     float r2 = w.r2;
     if (w.a->S > 1) {
@@ -131,9 +133,40 @@ __device__ __forceinline__ float current_r2(const Warp &w)
     return r2;
 }
 
+// 16-bit storage: exact FP32 distance of every lane with `need`, recomputed
+// from the FP32 row copy, one candidate at a time by the whole warp (each lane
+// a 4-dim slice, then a butterfly sum whose result is the same on all lanes).
+template <typename T>
+__device__ __forceinline__ float recheck_exact(const Warp<T> &w, bool need, int pos, float S)
+{
+    const ScanArgs &a = *w.a;
+    unsigned mask = __ballot_sync(FULL, need);
+    while (mask) {
+        const int src = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int p = __shfl_sync(FULL, pos, src);
+        const float *row = a.rows32 + (int64_t)p * a.Dp;
+        float part = 0.f;
+        for (int j = w.lane * 4; j < a.Dp; j += 128) {
+            const float4 x = __ldg(reinterpret_cast<const float4 *>(row + j));
+            const float4 q = *reinterpret_cast<const float4 *>(w.qv + j);
+            float t;
+            t = x.x - q.x; part = fmaf(t, t, part);
+            t = x.y - q.y; part = fmaf(t, t, part);
+            t = x.z - q.z; part = fmaf(t, t, part);
+            t = x.w - q.w; part = fmaf(t, t, part);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+        if (w.lane == src) S = part;
+    }
+    return S;
+}
+
 // After a candidate has `blk` blocks accumulated in S: the exact compare at
 // d = D (Case 3), else the hypothesis test (Case 1 reject / Case 2 re-queue).
-__device__ __forceinline__ void after_step(Warp &w, bool valid, float S, int blk, int o, int m,
+template <typename T>
+__device__ __forceinline__ void after_step(Warp<T> &w, bool valid, float S, int blk, int o, int m,
                                            int n, float r2)
 {
     const ScanArgs &a = *w.a;
@@ -158,8 +191,25 @@ __device__ __forceinline__ void after_step(Warp &w, bool valid, float S, int blk
         w.pS[idx] = S;
     }
     w.cnt += __popc(sm);
+    bool cand = fin;
+    if constexpr (Roundoff<T>::u > 0.f) {
+        // S is a sum over rounded coordinates x~ with |x~ - x| <= u|x|, so
+        // ||x~ - q|| <= ||x - q|| + u||x||: a candidate with S_D <= r^2 has
+        // sqrt(S~) <= r + u||x||.  Only those are recomputed exactly in FP32;
+        // the low precision moves reject decisions only, never a result.
+        bool need = false;
+        if (fin) {
+            need = !(r2 < INFINITY);
+            if (!need) {
+                const float bound = (sqrtf(r2) + Roundoff<T>::u * a.norms[o + m]) * 1.0001f;
+                need = sqrtf(S) <= bound;
+            }
+        }
+        S = recheck_exact(w, need, o + m, S);
+        cand = need;
+    }
     // Case 3 positives into the candidate buffer.
-    const bool want = fin && S <= r2;
+    const bool want = cand && S <= r2;
     const unsigned wm = __ballot_sync(FULL, want);
     if (wm) {
         const int nw = __popc(wm);
@@ -177,7 +227,8 @@ __device__ __forceinline__ void after_step(Warp &w, bool valid, float S, int blk
 }
 
 // Advances up to 32 pending candidates by one delta_d step each.
-__device__ __forceinline__ void process_pending(Warp &w, int nb)
+template <typename T>
+__device__ __forceinline__ void process_pending(Warp<T> &w, int nb)
 {
     const ScanArgs &a = *w.a;
     const bool valid = w.lane < nb;
@@ -198,19 +249,25 @@ __device__ __forceinline__ void process_pending(Warp &w, int nb)
     if (valid) {
         int e = blk + a.db;
         if (e > a.nblk) e = a.nblk;
-        S = accum_range_f32(a.data + (int64_t)o * a.Dp, n, m, blk, e, w.qv, S);
+        S = accum_range(static_cast<const T *>(a.data) + (int64_t)o * a.Dp, n, m, blk, e, w.qv, S);
         blk = e;
     }
     after_step(w, valid, S, blk, o, m, n, r2);
 }
 
-__global__ void __launch_bounds__(THREADS) ads_scan_kernel(ScanArgs a)
+// Resident blocks per SM the register budget is sized for (FP32: 48
+// registers, 40 warps per SM; 16-bit storage with its recheck: 64).
+template <typename T> struct MinBlocks { static constexpr int value = 8; };
+template <> struct MinBlocks<float> { static constexpr int value = 10; };
+
+template <typename T>
+__global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(ScanArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const WarpCarve wc(a.Dp, a.C);
     float *base = reinterpret_cast<float *>(smraw) + (size_t)warp * wc.words;
-    Warp w;
+    Warp<T> w;
     w.a = &a;
     w.qv = base + wc.qv;
     w.ed = base + wc.ed;
@@ -242,13 +299,13 @@ __global__ void __launch_bounds__(THREADS) ads_scan_kernel(ScanArgs a)
             const int c = a.probes[q * a.nprobe + p];
             const int o = (int)a.off[c];
             const int n = (int)(a.off[c + 1] - o);
-            const float *cb = a.data + (int64_t)o * a.Dp;
+            const T *cb = static_cast<const T *>(a.data) + (int64_t)o * a.Dp;
             for (int m0 = 0; m0 < n; m0 += 32) {
                 const float r2 = current_r2(w);
                 const int m = m0 + lane;
                 const bool valid = m < n;
                 float S = 0.f;
-                if (valid) S = accum_range_f32(cb, n, m, 0, nb0, w.qv, 0.f);
+                if (valid) S = accum_range(cb, n, m, 0, nb0, w.qv, 0.f);
                 after_step(w, valid, S, nb0, o, m, n, r2);
                 while (w.cnt >= 32) process_pending(w, 32);
             }
@@ -332,7 +389,9 @@ __global__ void test_factor_kernel(float *ftab, int nblk, int D, float eps0)
 
 // Verification protocol (Sec. 6.2.5): every (query, indexed vector) pair,
 // fixed threshold r2[q].  One warp per 32-member tile of one cluster, one
-// lane per member; the same block accumulation and test as the search scan.
+// lane per member; the same block accumulation and test as the search scan
+// (and, for 16-bit storage, the exact FP32 distance at d = D).
+template <typename T>
 __global__ void __launch_bounds__(256) dco_fixed_r_kernel(FixedRArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -345,7 +404,7 @@ __global__ void __launch_bounds__(256) dco_fixed_r_kernel(FixedRArgs a)
         ftab[b] = (b == 0) ? 0.f : test_factor(b, a.D, a.eps0);
     __syncthreads();
     const int t = blockIdx.x * 8 + warp;
-    if (t >= a.total_tiles) return;
+    if (t >= a.total_tiles) return;      // whole warp
     int lo = 0, hi = a.nlist - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -355,29 +414,56 @@ __global__ void __launch_bounds__(256) dco_fixed_r_kernel(FixedRArgs a)
     const int64_t o = a.off[c];
     const int64_t n = a.off[c + 1] - o;
     const int64_t m = (int64_t)(t - a.tile_off[c]) * 32 + lane;
-    if (m >= n) return;
+    const bool valid = m < n;
     const float r2 = a.r2[q];
-    const float *base = a.data + o * a.Dp;
+    const T *base = static_cast<const T *>(a.data) + o * a.Dp;
     float S = 0.f;
     int blk = 0;
     uint8_t dec = 0;
     int dims = 0;
-    for (;;) {
-        int e = blk + a.db;
-        if (e > a.nblk) e = a.nblk;
-        S = accum_range_f32(base, n, m, blk, e, qv, S);
-        blk = e;
-        if (blk >= a.nblk) {
-            dec = (S <= r2) ? 1 : 2;
-            dims = a.D;
-            break;
-        }
-        if (a.test_on && S > r2 * ftab[blk]) {
-            dec = 0;
-            dims = blk * BLK < a.D ? blk * BLK : a.D;
-            break;
+    bool at_D = false;
+    if (valid) {
+        for (;;) {
+            int e = blk + a.db;
+            if (e > a.nblk) e = a.nblk;
+            S = accum_range(base, n, m, blk, e, qv, S);
+            blk = e;
+            if (blk >= a.nblk) {
+                at_D = true;
+                dims = a.D;
+                break;
+            }
+            if (a.test_on && S > r2 * ftab[blk]) {
+                dec = 0;
+                dims = blk * BLK < a.D ? blk * BLK : a.D;
+                break;
+            }
         }
     }
+    if constexpr (Roundoff<T>::u > 0.f) {
+        unsigned mask = __ballot_sync(0xffffffffu, at_D);
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int64_t p = o + __shfl_sync(0xffffffffu, (int)m, src);
+            const float *row = a.rows32 + p * a.Dp;
+            float part = 0.f;
+            for (int j = lane * 4; j < a.Dp; j += 128) {
+                const float4 x = __ldg(reinterpret_cast<const float4 *>(row + j));
+                const float4 qq = *reinterpret_cast<const float4 *>(qv + j);
+                float d;
+                d = x.x - qq.x; part = fmaf(d, d, part);
+                d = x.y - qq.y; part = fmaf(d, d, part);
+                d = x.z - qq.z; part = fmaf(d, d, part);
+                d = x.w - qq.w; part = fmaf(d, d, part);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+            if (lane == src) S = part;
+        }
+    }
+    if (!valid) return;
+    if (at_D) dec = (S <= r2) ? 1 : 2;
     const int64_t id = a.ids[o + m];
     a.decisions[q * a.N + id] = dec;
     if (a.dims) a.dims[q * a.N + id] = dims;
@@ -397,13 +483,22 @@ int scan_items_target(int device)
     return nsm * 48;   // about two resident warps' worth of work per warp slot
 }
 
+template <typename T>
+static int occupancy(size_t smem)
+{
+    int per = 0;
+    cudaFuncSetAttribute(ads_scan_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ads_scan_kernel<T>, THREADS, smem);
+    return per;
+}
+
 int ads_scan_grid(const ScanArgs &a, int device)
 {
     int nsm = 0, per = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
     size_t smem = scan_smem_bytes(a);
-    cudaFuncSetAttribute(ads_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ads_scan_kernel, THREADS, smem);
+    per = a.storage == ADSX_F32 ? occupancy<float>(smem)
+        : a.storage == ADSX_BF16 ? occupancy<__nv_bfloat16>(smem) : occupancy<__half>(smem);
     if (per < 1) per = 1;
     int64_t g = (int64_t)nsm * per;
     const int64_t need = ((int64_t)a.n_items + WARPS - 1) / WARPS;
@@ -421,10 +516,22 @@ cudaError_t launch_ads_scan(const ScanArgs &a, int grid, cudaStream_t s)
 {
     if (a.n_items <= 0) return cudaSuccess;
     size_t smem = scan_smem_bytes(a);
-    cudaError_t e = cudaFuncSetAttribute(ads_scan_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    ads_scan_kernel<<<grid, THREADS, smem, s>>>(a);
+    if (a.storage == ADSX_F32) {
+        cudaError_t e = cudaFuncSetAttribute(ads_scan_kernel<float>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        ads_scan_kernel<float><<<grid, THREADS, smem, s>>>(a);
+    } else if (a.storage == ADSX_BF16) {
+        cudaError_t e = cudaFuncSetAttribute(ads_scan_kernel<__nv_bfloat16>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        ads_scan_kernel<__nv_bfloat16><<<grid, THREADS, smem, s>>>(a);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(ads_scan_kernel<__half>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        ads_scan_kernel<__half><<<grid, THREADS, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -449,7 +556,12 @@ cudaError_t launch_dco_fixed_r(const FixedRArgs &a, cudaStream_t s)
     size_t smem = sizeof(float) * (a.Dp + a.nblk + 1);
     if (a.nq > 65535) return cudaErrorInvalidValue;
     dim3 grid((unsigned)((a.total_tiles + 7) / 8), (unsigned)a.nq);
-    dco_fixed_r_kernel<<<grid, 256, smem, s>>>(a);
+    if (a.storage == ADSX_F32)
+        dco_fixed_r_kernel<float><<<grid, 256, smem, s>>>(a);
+    else if (a.storage == ADSX_BF16)
+        dco_fixed_r_kernel<__nv_bfloat16><<<grid, 256, smem, s>>>(a);
+    else
+        dco_fixed_r_kernel<__half><<<grid, 256, smem, s>>>(a);
     return cudaGetLastError();
 }
 
