@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--eps0", type=float, default=2.1)
     ap.add_argument("--delta-d", type=int, default=32)
     ap.add_argument("--nprobe", type=int, default=0, help="0 = calibrate")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -255,7 +256,8 @@ def main():
     libbuild.build()
 
     wl = make_workload(args, device)
-    ix = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign)
+    storage = {"f32": adsx.F32, "bf16": adsx.BF16, "f16": adsx.F16}[args.storage]
+    ix = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign, storage=storage)
     Qd = torch.from_numpy(wl.Q).to(device)
     nq = Qd.shape[0]
     gt = ground_truth(wl.X, wl.Q, 10, device)
@@ -344,19 +346,23 @@ def main():
         return 0
 
     hbm, peak_kind = peaks()
-    algo_bytes = 4.0 * ads_dims            # FP32 dims actually sampled per scan launch
+    # dims actually sampled per scan launch x bytes per stored dim (the FP32
+    # rechecks of 16-bit storage are not counted: a lower bound on bytes)
+    esz = 4.0 if args.storage == "f32" else 2.0
+    algo_bytes = esz * ads_dims
     achieved = algo_bytes / (ads_scan_ms * 1e-3) / 1e9
     tr = scan_traffic()
     fd_frac = ads_dims / fd_dims if fd_dims else None
     line = {
         "metric": METRIC, "value": nq * ws / (ads_ms * 1e-3), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ads_ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.storage == "f32" else args.storage + " storage, f32 accumulate",
         "data": "synthetic (SIFT-shaped seeded mixture; random orthogonal P; seeded k-means)",
         "config": {"workload": wl.name, "nq": nq, "nlist": wl.nlist, "K": args.K,
                    "eps0": args.eps0, "delta_d": args.delta_d, "nprobe": np_ads,
                    "l2": "256 MB flush between steps; index 512 MB > L2",
-                   "recall10": recall_ads},
+                   "recall10": recall_ads, "storage": args.storage},
         "fd_scan": {"qps": nq * ws / (fd_ms * 1e-3), "nprobe": np_fd, "ms_per_step": fd_ms,
                     "scan_ms": fd_scan_ms},
         "speedup_vs_fd": fd_ms / ads_ms,
