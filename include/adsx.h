@@ -107,7 +107,8 @@ int adsx_index_info(const adsx_index *index, int64_t *N, int32_t *D,
  *   Qv         host or device, nq x D float32 raw queries; nq >= 0.
  *   K          1..ADSX_MAX_K.   nprobe 1..min(nlist, ADSX_MAX_NPROBE).
  *   eps0       >= 0; +INFINITY disables the test (FDScanning, exact IVF).
- *   delta_d    multiple of 16, >= 16 (a value >= D also disables the test).
+ *   delta_d    multiple of 16, >= 16 (a value >= D also disables the test);
+ *              0 uses the index's tuned step (adsx_autotune; 32 until tuned).
  *   ids        host or device, nq x K int64 output; -1 pads missing slots.
  *   dists      host or device, nq x K float32 squared distances; +INF pads.
  *   dims_read  host or device, nq int64 (may be NULL): dimensions sampled
@@ -121,6 +122,39 @@ int adsx_index_info(const adsx_index *index, int64_t *N, int32_t *D,
 int adsx_search(const adsx_index *index, const float *Qv, int64_t nq,
                 int32_t K, int32_t nprobe, float eps0, int32_t delta_d,
                 int64_t *ids, float *dists, int64_t *dims_read, void *stream);
+
+/*
+ * adsx_search_batched -- the IVF+ query phase for a batch whose queries each
+ * have their own K and nprobe (same method as adsx_search, Sec. 4), in one
+ * persistent scan launch: a device-side planner validates the per-query
+ * values, splits long queries into several work items and orders the
+ * queries longest-first; split queries share their r through the device.
+ *   Qv           host or device, nq x D float32 raw queries.
+ *   K, nprobe    host or device, nq int32 each; K[q] in [1, max_K],
+ *                nprobe[q] in [1, max_nprobe].  Host arrays are checked
+ *                before any work (ADSX_EINVAL); device arrays are checked by
+ *                the planner, which clamps bad values and sets the index's
+ *                error word (reported as ADSX_EINVAL by this call when it
+ *                synchronises, else by adsx_stream_status).
+ *   max_K        1..ADSX_MAX_K; max_nprobe 1..min(nlist, ADSX_MAX_NPROBE).
+ *   eps0, delta_d  as adsx_search; delta_d = 0 uses the index's tuned step
+ *                (adsx_autotune; 32 until tuned).
+ *   out_offsets  host or device, nq int64 (may be NULL): query q's results
+ *                go to ids/dists[out_offsets[q] .. + K[q]); NULL means the
+ *                prefix sums of K (results packed in query order).
+ *   out_total    length of ids and dists; a query whose slice does not fit
+ *                is skipped and flagged in the error word.
+ *   ids, dists   host or device, out_total entries; -1 / +INF padding.
+ *   dims_read    host or device, nq int64 (may be NULL).
+ * With all pointers in device memory the call only enqueues work, and the
+ * sequence can be captured in a CUDA graph.
+ */
+int adsx_search_batched(const adsx_index *index, const float *Qv, int64_t nq,
+                        const int32_t *K, const int32_t *nprobe, int32_t max_K,
+                        int32_t max_nprobe, float eps0, int32_t delta_d,
+                        const int64_t *out_offsets, int64_t out_total,
+                        int64_t *ids, float *dists, int64_t *dims_read,
+                        void *stream);
 
 /*
  * adsx_probe -- the query rotation and centroid selection steps of
@@ -155,10 +189,28 @@ int adsx_dco_fixed_r(const adsx_index *index, const float *Qv, int64_t nq,
 
 /*
  * adsx_stream_status -- synchronises `stream`, then reads and clears the
- * index's device-side error word (set when a bounded wait inside a kernel
- * gave up).  Returns ADSX_OK, ADSX_ETIMEOUT or ADSX_ECUDA.
+ * index's device-side error word (set by device-side argument checks of the
+ * batched form, or when a bounded wait inside a kernel gives up).  Returns
+ * ADSX_OK, ADSX_EINVAL (argument check), ADSX_ETIMEOUT or ADSX_ECUDA.
  */
 int adsx_stream_status(const adsx_index *index, void *stream);
+
+/*
+ * adsx_autotune -- picks the step delta_d (Sec. 6.2.4: 16..64 give the best
+ * trade-off; the candidates are 16, 32, 48, 64, up to the padded D) and the
+ * work-item granularity used when queries are split (24, 48 or 96 items per
+ * SM) by timing adsx_search on a caller-supplied query sample (one warm-up
+ * and three timed runs each, CUDA events on `stream`).  The winner is stored
+ * in the index and used by searches that pass delta_d = 0; the item
+ * granularity applies to every later search on the index.
+ *   Qv               host or device, nq x D sample queries (nq >= 1).
+ *   K, nprobe, eps0  the search parameters to tune for.
+ *   best_delta_d, best_items_per_sm, best_ms  outputs (each may be NULL).
+ * Not thread-safe with other calls on the same index.
+ */
+int adsx_autotune(adsx_index *index, const float *Qv, int64_t nq, int32_t K,
+                  int32_t nprobe, float eps0, int32_t *best_delta_d,
+                  int32_t *best_items_per_sm, float *best_ms, void *stream);
 
 /*
  * adsx_set_stage_timing -- when `enable` is non-zero, every later

@@ -56,12 +56,15 @@ def load():
     lib.adsx_dco_fixed_r.argtypes = [V, V, i64, V, f32, i32, V, V, V]
     lib.adsx_stream_status.argtypes = [V, V]
     lib.adsx_search_noalloc.argtypes = [V, V, i64, i32, i32, f32, i32, V, V, V, V]
+    lib.adsx_search_batched.argtypes = [V, V, i64, V, V, i32, i32, f32, i32, V, i64, V, V, V, V]
+    lib.adsx_autotune.argtypes = [V, V, i64, i32, i32, f32, V, V, V, V]
     lib.adsx_set_stage_timing.argtypes = [V, i32]
     lib.adsx_stage_ms.argtypes = [V, V]
     lib.adsx_last_error.restype = ctypes.c_char_p
     for fn in ("adsx_build_index", "adsx_free_index", "adsx_index_info", "adsx_search",
                "adsx_probe", "adsx_rotate", "adsx_dco_fixed_r", "adsx_stream_status",
-               "adsx_set_stage_timing", "adsx_stage_ms", "adsx_search_noalloc"):
+               "adsx_set_stage_timing", "adsx_stage_ms", "adsx_search_noalloc",
+               "adsx_search_batched", "adsx_autotune"):
         getattr(lib, fn).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -194,6 +197,57 @@ def search(index: Index, Q, K: int, nprobe: int, eps0: float = 2.1, delta_d: int
     return (ids, d2, dims) if return_dims else (ids, d2)
 
 
+def _i32(a, like):
+    if _is_torch_cuda(like):
+        import torch
+        return torch.as_tensor(a, dtype=torch.int32, device=like.device).contiguous()
+    return _host(a, np.int32)
+
+
+def search_batched(index: Index, Q, K, nprobe, eps0: float = 2.1, delta_d: int = 32,
+                   max_K: int = 0, max_nprobe: int = 0, out_offsets=None, out_total: int = -1,
+                   return_dims: bool = False, stream=None):
+    """adsx_search_batched: per-query K and nprobe (arrays of length nq).
+
+    Returns (ids, dists[, dims]) as flat arrays: query q's K[q] results start
+    at out_offsets[q], or at the prefix sum of K when out_offsets is None.
+    With CUDA tensors for Q, K and nprobe and max_K, max_nprobe and out_total
+    given, nothing is read back to the host, so the call can be captured in a
+    CUDA graph."""
+    Q = _prep_queries(Q)
+    nq = Q.shape[0]
+    on_dev = _is_torch_cuda(Q)
+    if not (max_K and max_nprobe and out_total >= 0):
+        Kh = np.asarray(K.cpu() if hasattr(K, "cpu") else K, np.int64)
+        Ph = np.asarray(nprobe.cpu() if hasattr(nprobe, "cpu") else nprobe, np.int64)
+        max_K = int(max_K or (Kh.max() if nq else 1))
+        max_nprobe = int(max_nprobe or (Ph.max() if nq else 1))
+        if out_total < 0:
+            if out_offsets is None:
+                out_total = int(Kh.sum())
+            else:
+                oh = np.asarray(out_offsets.cpu() if hasattr(out_offsets, "cpu") else out_offsets)
+                out_total = int(np.max(oh + Kh)) if nq else 0
+    Kd = _i32(K, Q)
+    Pd = _i32(nprobe, Q)
+    offs = None
+    if out_offsets is not None:
+        if on_dev:
+            import torch
+            offs = torch.as_tensor(out_offsets, dtype=torch.int64, device=Q.device).contiguous()
+        else:
+            offs = _host(out_offsets, np.int64)
+    ids = _out(Q, (out_total,), np.int64, "int64")
+    d2 = _out(Q, (out_total,), np.float32, "float32")
+    dims = _out(Q, (nq,), np.int64, "int64") if return_dims else None
+    _check(load().adsx_search_batched(index.handle, _ptr(Q), nq, _ptr(Kd), _ptr(Pd), int(max_K),
+                                      int(max_nprobe),
+                                      float(eps0) if math.isfinite(eps0) else float("inf"),
+                                      int(delta_d), _ptr(offs), int(out_total), _ptr(ids),
+                                      _ptr(d2), _ptr(dims), _stream_of(Q, stream)))
+    return (ids, d2, dims) if return_dims else (ids, d2)
+
+
 def search_noalloc(index: Index, Q, K: int, nprobe: int, eps0: float = 2.1, delta_d: int = 32,
                    return_dims: bool = False, stream=None):
     """adsx_search_noalloc: adsx_search without any device allocation, for
@@ -247,6 +301,18 @@ def dco_fixed_r(index: Index, Q, r2, eps0: float, delta_d: int, stream=None):
     _check(load().adsx_dco_fixed_r(index.handle, _ptr(Q), nq, _ptr(r2), float(eps0),
                                    int(delta_d), _ptr(dec), _ptr(dims), _stream_of(Q, stream)))
     return dec, dims
+
+
+def autotune(index: Index, Q, K: int, nprobe: int, eps0: float = 2.1, stream=None):
+    """adsx_autotune: returns (delta_d, items_per_sm, ms) of the fastest
+    configuration on the sample Q; searches with delta_d=0 then use it."""
+    Q = _prep_queries(Q)
+    dd, ip, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(load().adsx_autotune(index.handle, _ptr(Q), Q.shape[0], int(K), int(nprobe),
+                                float(eps0) if math.isfinite(eps0) else float("inf"),
+                                ctypes.byref(dd), ctypes.byref(ip), ctypes.byref(ms),
+                                _stream_of(Q, stream)))
+    return dd.value, ip.value, ms.value
 
 
 def set_stage_timing(index: Index, enable: bool = True):

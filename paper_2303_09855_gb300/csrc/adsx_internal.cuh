@@ -41,6 +41,8 @@ struct Index {
     std::vector<int64_t> h_off;
     int32_t total_tiles = 0;
     int64_t bytes = 0;
+    int32_t tuned_delta_d = 32;   // used when a search passes delta_d = 0
+    int32_t items_per_sm = 48;    // work items per SM targeted when splitting queries
     // stage timing (adsx_set_stage_timing): events between search stages
     bool timing = false;
     bool timed_once = false;
@@ -234,7 +236,8 @@ cudaError_t launch_scatter_layout(const float *Y, int64_t N, int Dp, const int32
                                   int storage, float *rows32, float *norms, cudaStream_t s);
 
 cudaError_t launch_select_nprobe(const float *dist, int64_t nq, int nlist, int nprobe,
-                                 int32_t *probes, float *probe_d2, cudaStream_t s);
+                                 int32_t *probes, float *probe_d2, cudaStream_t s,
+                                 const int32_t *nprobe_q = nullptr);
 
 struct ScanArgs {
     const void *data;          // storage type per `storage`
@@ -258,13 +261,37 @@ struct ScanArgs {
     unsigned int *r2g;         // nq shared r^2 bounds, 0xffffffff = none (S > 1)
     unsigned int *work_counter;
     unsigned int *err;
+    // batched form (all NULL for a uniform search): per-query K and nprobe,
+    // output offsets, the planned items (x = query, y = split << 16 | splits),
+    // each query's first item, and the item count (device)
+    const int32_t *Kq = nullptr;
+    const int32_t *nprobe_q = nullptr;
+    const int64_t *out_off = nullptr;
+    const int2 *items = nullptr;
+    const int32_t *item_first = nullptr;
+    const int32_t *n_items_dev = nullptr;
+    int64_t out_total = 0;       // length of out_ids/out_d2 when out_off is set
+    int32_t Kmax = 0;            // stride of partial lists (>= every K)
+    int32_t probe_stride = 0;    // row stride of `probes` (>= every nprobe)
+    int32_t finalize_T = 0;
 };
 
 size_t scan_smem_bytes(const ScanArgs &a);
-int scan_items_target(int device);
+int scan_items_target(int device, int items_per_sm = 48);
 cudaError_t launch_test_factors(float *ftab, int nblk, int D, float eps0, cudaStream_t s);
 cudaError_t launch_ads_scan(const ScanArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_finalize_topk(const ScanArgs &a, cudaStream_t s);
+
+// Batched form: validates per-query K / nprobe, chooses splits, orders the
+// queries longest-first and writes the item list (capacity nq * 64 items).
+cudaError_t launch_plan_batched(const int32_t *Kq, const int32_t *nprobe_q, int64_t nq,
+                                int maxK, int maxP, int target_items, int2 *items,
+                                int32_t *item_first, int32_t *n_items, int32_t *qperm,
+                                const int64_t *out_off_in, int64_t *out_off,
+                                unsigned *err, cudaStream_t s);
+constexpr unsigned ERR_BATCH_ARGS = 2u;   // a per-query K or nprobe was out of range
+constexpr unsigned ERR_OUT_RANGE = 4u;    // an output offset + K exceeded the output length
+constexpr int BATCH_MAX_SPLITS = 16;
 int ads_scan_grid(const ScanArgs &a, int device);
 
 struct FixedRArgs {

@@ -413,6 +413,7 @@ int adsx_search(const adsx_index *index, const float *Qv, int64_t nq, int32_t K,
     if (K < 1 || K > ADSX_MAX_K) return fail(ADSX_EINVAL, "K out of range (1..%d)", ADSX_MAX_K);
     if (nprobe < 1 || nprobe > ix->nlist || nprobe > ADSX_MAX_NPROBE)
         return fail(ADSX_EINVAL, "nprobe out of range (1..min(nlist, %d))", ADSX_MAX_NPROBE);
+    if (delta_d == 0) delta_d = ix->tuned_delta_d;
     if ((rc = check_blocks(delta_d, eps0))) return rc;
     if (nq == 0) return ADSX_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -458,7 +459,7 @@ int adsx_search(const adsx_index *index, const float *Qv, int64_t nq, int32_t K,
         while (a.C < need) a.C <<= 1;
         // splits per query: enough work items to fill the GPU, bounded by the
         // probe count and by the merge buffer of the finalize kernel
-        int64_t target = adsx::scan_items_target(ix->device);
+        int64_t target = adsx::scan_items_target(ix->device, ix->items_per_sm);
         int64_t S = (target + nq - 1) / nq;
         S = std::min<int64_t>(S, std::min(nprobe, 64));
         S = std::min<int64_t>(S, std::max(1, 16384 / Kp));
@@ -506,6 +507,152 @@ int adsx_search(const adsx_index *index, const float *Qv, int64_t nq, int32_t K,
         if (err) {
             cudaMemset(ix->err, 0, sizeof(unsigned));
             return fail(ADSX_ETIMEOUT, "a bounded device wait gave up (error word 0x%x)", err);
+        }
+    }
+    return ADSX_OK;
+}
+
+int adsx_search_batched(const adsx_index *index, const float *Qv, int64_t nq, const int32_t *K,
+                        const int32_t *nprobe, int32_t max_K, int32_t max_nprobe, float eps0,
+                        int32_t delta_d, const int64_t *out_offsets, int64_t out_total,
+                        int64_t *ids, float *dists, int64_t *dims_read, void *stream)
+{
+    const Index *ix = reinterpret_cast<const Index *>(index);
+    int rc = check_index(ix);
+    if (rc) return rc;
+    if (nq < 0 || (nq > 0 && (!Qv || !K || !nprobe || !ids || !dists)))
+        return fail(ADSX_EINVAL, "bad query arguments");
+    if (max_K < 1 || max_K > ADSX_MAX_K) return fail(ADSX_EINVAL, "max_K out of range (1..%d)", ADSX_MAX_K);
+    if (max_nprobe < 1 || max_nprobe > ix->nlist || max_nprobe > ADSX_MAX_NPROBE)
+        return fail(ADSX_EINVAL, "max_nprobe out of range (1..min(nlist, %d))", ADSX_MAX_NPROBE);
+    if (delta_d == 0) delta_d = ix->tuned_delta_d;
+    if ((rc = check_blocks(delta_d, eps0))) return rc;
+    if (out_total < 0) return fail(ADSX_EINVAL, "out_total < 0");
+    if (nq == 0) return ADSX_OK;
+    if (nq >= ((int64_t)1 << 31) / adsx::BATCH_MAX_SPLITS) return fail(ADSX_EINVAL, "too many queries in one call");
+    // Host copies of K / nprobe are checked here when the caller passes host
+    // arrays; device arrays are checked by the planner (error word).
+    if (!is_device_ptr(K) && !is_device_ptr(nprobe)) {
+        int64_t sumK = 0;
+        for (int64_t q = 0; q < nq; ++q) {
+            if (K[q] < 1 || K[q] > max_K) return fail(ADSX_EINVAL, "K[%lld] = %d outside [1, max_K]", (long long)q, K[q]);
+            if (nprobe[q] < 1 || nprobe[q] > max_nprobe)
+                return fail(ADSX_EINVAL, "nprobe[%lld] = %d outside [1, max_nprobe]", (long long)q, nprobe[q]);
+            sumK += K[q];
+        }
+        if (!out_offsets && out_total < sumK) return fail(ADSX_EINVAL, "out_total below the sum of K");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    Buf<float> q, od;
+    Buf<int32_t> kq, pq;
+    Buf<int64_t> oo, oi, odims;
+    CK(stage_in(sc, Qv, (size_t)nq * ix->D, q), "stage queries");
+    CK(stage_in(sc, K, (size_t)nq, kq), "stage K");
+    CK(stage_in(sc, nprobe, (size_t)nq, pq), "stage nprobe");
+    if (out_offsets) CK(stage_in(sc, out_offsets, (size_t)nq, oo), "stage offsets");
+    CK(stage_out(sc, ids, (size_t)out_total, oi), "stage ids");
+    CK(stage_out(sc, dists, (size_t)out_total, od), "stage dists");
+    CK(stage_out(sc, dims_read, (size_t)nq, odims), "stage dims");
+    float *qrot = nullptr;
+    int32_t *probes = nullptr, *item_first = nullptr, *n_items = nullptr, *qperm = nullptr;
+    int2 *items = nullptr;
+    int64_t *out_off = nullptr;
+    unsigned *counter = nullptr;
+    const int64_t items_cap = nq * adsx::BATCH_MAX_SPLITS;
+    CK(sc.get(&qrot, (size_t)nq * ix->Dp), "alloc q'");
+    CK(sc.get(&probes, (size_t)nq * max_nprobe), "alloc probes");
+    CK(sc.get(&items, (size_t)items_cap), "alloc items");
+    CK(sc.get(&item_first, (size_t)nq), "alloc items");
+    CK(sc.get(&n_items, 1), "alloc items");
+    CK(sc.get(&qperm, (size_t)nq), "alloc order");
+    CK(sc.get(&out_off, (size_t)nq), "alloc offsets");
+    CK(sc.get(&counter, 1), "alloc counter");
+    CK(mark(ix, 0, s), "event");
+    CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
+    CK(mark(ix, 1, s), "event");
+    {
+        float *dist = nullptr;
+        CK(sc.get(&dist, (size_t)nq * ix->nlist), "alloc distances");
+        CK(adsx::launch_nt_gemm(qrot, nq, ix->Dp, ix->cents, ix->nlist, ix->Dp, ix->Dp, dist,
+                                ix->nlist, ix->nlist, true, s), "centroid distances");
+        CK(mark(ix, 2, s), "event");
+        CK(adsx::launch_select_nprobe(dist, nq, ix->nlist, max_nprobe, probes, nullptr, s, pq.dev),
+           "select");
+    }
+    const int target = adsx::scan_items_target(ix->device, ix->items_per_sm);
+    CK(adsx::launch_plan_batched(kq.dev, pq.dev, nq, max_K, max_nprobe, target, items, item_first,
+                                 n_items, qperm, oo.dev, out_off, ix->err, s), "plan");
+    CK(mark(ix, 3, s), "event");
+
+    adsx::ScanArgs a;
+    a.data = ix->data;
+    a.rows32 = ix->rows32;
+    a.norms = ix->norms;
+    a.storage = ix->storage;
+    a.ids = ix->ids;
+    a.off = ix->off;
+    a.qrot = qrot;
+    a.probes = probes;
+    a.nq = nq;
+    a.D = ix->D;
+    a.Dp = ix->Dp;
+    a.nblk = ix->Dp / adsx::BLK;
+    a.nprobe = max_nprobe;
+    a.K = max_K;
+    {
+        int Kp = 1;
+        while (Kp < max_K) Kp <<= 1;
+        a.C = 1;
+        while (a.C < std::max(2 * Kp, max_K + 32)) a.C <<= 1;
+    }
+    a.S = 1;
+    a.n_items = (int32_t)items_cap;       // upper bound; the kernel reads the planned count
+    a.db = delta_d / adsx::BLK;
+    a.test_on = isinf(eps0) ? 0 : 1;
+    if (a.db >= a.nblk) a.test_on = 0;
+    if (!a.test_on) a.db = a.nblk;
+    a.out_ids = oi.dev;
+    a.out_d2 = od.dev;
+    a.out_dims = odims.dev;
+    a.work_counter = counter;
+    a.err = ix->err;
+    a.Kq = kq.dev;
+    a.nprobe_q = pq.dev;
+    a.out_off = out_off;
+    a.out_total = out_total;
+    a.items = items;
+    a.item_first = item_first;
+    a.n_items_dev = n_items;
+    a.Kmax = max_K;
+    a.probe_stride = max_nprobe;
+    float *ftab = nullptr;
+    CK(sc.get(&ftab, (size_t)a.nblk + 1), "alloc test factors");
+    a.ftab = ftab;
+    CK(adsx::launch_test_factors(ftab, a.nblk, a.D, a.test_on ? eps0 : 0.f, s), "test factors");
+    CK(sc.get(&a.part_d, (size_t)items_cap * max_K), "alloc partial lists");
+    CK(sc.get(&a.part_i, (size_t)items_cap * max_K), "alloc partial lists");
+    CK(sc.get(&a.r2g, (size_t)nq), "alloc r2 bounds");
+    CK(cudaMemsetAsync(a.r2g, 0xff, sizeof(unsigned) * nq, s), "clear r2 bounds");
+    if (a.out_dims) CK(cudaMemsetAsync(a.out_dims, 0, sizeof(int64_t) * nq, s), "clear dims");
+    CK(cudaMemsetAsync(counter, 0, sizeof(unsigned), s), "clear counter");
+    CK(adsx::launch_ads_scan(a, adsx::ads_scan_grid(a, ix->device), s), "scan");
+    CK(adsx::launch_finalize_topk(a, s), "finalize");
+    CK(mark(ix, 4, s), "event");
+    if (ix->timing) const_cast<Index *>(ix)->timed_once = true;
+    CK(copy_back(oi, s), "copy back");
+    CK(copy_back(od, s), "copy back");
+    CK(copy_back(odims, s), "copy back");
+    bool any_host = oi.host || od.host || odims.host;
+    rc = finish(s, any_host, "batched search");
+    if (rc) return rc;
+    if (any_host) {
+        unsigned err = 0;
+        CK(cudaMemcpy(&err, ix->err, sizeof err, cudaMemcpyDeviceToHost), "read error word");
+        if (err) {
+            cudaMemset(ix->err, 0, sizeof(unsigned));
+            return fail((err & (adsx::ERR_BATCH_ARGS | adsx::ERR_OUT_RANGE)) ? ADSX_EINVAL : ADSX_ETIMEOUT,
+                        "device-side check failed (error word 0x%x)", err);
         }
     }
     return ADSX_OK;
@@ -561,6 +708,74 @@ int adsx_dco_fixed_r(const adsx_index *index, const float *Qv, int64_t nq, const
     return finish(s, dec.host || dm.host, "fixed-r");
 }
 
+int adsx_autotune(adsx_index *index, const float *Qv, int64_t nq, int32_t K, int32_t nprobe,
+                  float eps0, int32_t *best_delta_d, int32_t *best_items_per_sm, float *best_ms,
+                  void *stream)
+{
+    Index *ix = reinterpret_cast<Index *>(index);
+    int rc = check_index(ix);
+    if (rc) return rc;
+    if (nq < 1 || !Qv) return fail(ADSX_EINVAL, "autotune needs a non-empty query sample");
+    if (K < 1 || K > ADSX_MAX_K || nprobe < 1 || nprobe > ix->nlist || nprobe > ADSX_MAX_NPROBE)
+        return fail(ADSX_EINVAL, "K or nprobe out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc(s);
+    Buf<float> q;
+    float *d2 = nullptr;
+    int64_t *ids = nullptr;
+    CK(stage_in(sc, Qv, (size_t)nq * ix->D, q), "stage queries");
+    CK(sc.get(&d2, (size_t)nq * K), "alloc outputs");
+    CK(sc.get(&ids, (size_t)nq * K), "alloc outputs");
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    const bool timing = ix->timing;
+    ix->timing = false;
+    const int dds[4] = {16, 32, 48, 64};
+    const int ips[3] = {24, 48, 96};
+    float best = INFINITY;
+    int bdd = ix->tuned_delta_d, bip = ix->items_per_sm;
+    const int saved_ip = ix->items_per_sm;
+    for (int di = 0; di < 4 && rc == ADSX_OK; ++di) {
+        if (dds[di] > ix->Dp) continue;
+        for (int ii = 0; ii < 3 && rc == ADSX_OK; ++ii) {
+            ix->items_per_sm = ips[ii];
+            float tot = 0.f;
+            for (int rep = 0; rep < 4 && rc == ADSX_OK; ++rep) {
+                cudaEventRecord(e0, s);
+                rc = adsx_search(index, q.dev, nq, K, nprobe, eps0, dds[di], ids, d2, nullptr, stream);
+                cudaEventRecord(e1, s);
+                if (rc) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = fail(ADSX_ECUDA, "autotune sync failed");
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tot += ms;          // first run is a warm-up
+            }
+            if (rc == ADSX_OK && tot / 3.f < best) {
+                best = tot / 3.f;
+                bdd = dds[di];
+                bip = ips[ii];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ix->timing = timing;
+    if (rc) {
+        ix->items_per_sm = saved_ip;
+        return rc;
+    }
+    ix->tuned_delta_d = bdd;
+    ix->items_per_sm = bip;
+    if (best_delta_d) *best_delta_d = bdd;
+    if (best_items_per_sm) *best_items_per_sm = bip;
+    if (best_ms) *best_ms = best;
+    return ADSX_OK;
+}
+
 int adsx_set_stage_timing(adsx_index *index, int32_t enable)
 {
     Index *ix = reinterpret_cast<Index *>(index);
@@ -594,6 +809,8 @@ int adsx_stream_status(const adsx_index *index, void *stream)
     CK(cudaMemcpy(&err, ix->err, sizeof err, cudaMemcpyDeviceToHost), "read error word");
     if (err) {
         cudaMemset(ix->err, 0, sizeof(unsigned));
+        if (err & (adsx::ERR_BATCH_ARGS | adsx::ERR_OUT_RANGE))
+            return fail(ADSX_EINVAL, "device-side argument check failed (error word 0x%x)", err);
         return fail(ADSX_ETIMEOUT, "a bounded device wait gave up (error word 0x%x)", err);
     }
     return ADSX_OK;

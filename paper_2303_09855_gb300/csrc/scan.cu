@@ -75,6 +75,7 @@ struct Warp {
     float *pS;
     int lane;
     int64_t q;
+    int K, C, S;               // this item's K, buffer capacity, splits of its query
     int head, cnt;             // pending ring (warp-uniform)
     int count;                 // candidate buffer fill (warp-uniform)
     float r2;                  // this warp's K-th distance (warp-uniform)
@@ -86,7 +87,7 @@ struct Warp {
 template <typename T>
 __device__ void compact(Warp<T> &w)
 {
-    const int C = w.a->C, K = w.a->K;
+    const int C = w.C, K = w.K;
     for (int k = w.count + w.lane; k < C; k += 32) {
         w.ed[k] = INFINITY;
         w.ei[k] = 0x7fffffff;
@@ -116,7 +117,7 @@ __device__ void compact(Warp<T> &w)
         const float r2 = w.ed[K - 1];
         if (r2 < w.r2) {
             w.r2 = r2;
-            if (w.a->S > 1 && w.lane == 0) atomicMin(w.a->r2g + w.q, __float_as_uint(r2));
+            if (w.S > 1 && w.lane == 0) atomicMin(w.a->r2g + w.q, __float_as_uint(r2));
         }
     }
     __syncwarp();
@@ -126,7 +127,7 @@ template <typename T>
 __device__ __forceinline__ float current_r2(const Warp<T> &w)
 {
     float r2 = w.r2;
-    if (w.a->S > 1) {
+    if (w.S > 1) {
         const unsigned g = *((volatile const unsigned *)(w.a->r2g + w.q));
         if (g <= 0x7f800000u) r2 = fminf(r2, __uint_as_float(g));
     }
@@ -213,7 +214,7 @@ __device__ __forceinline__ void after_step(Warp<T> &w, bool valid, float S, int 
     const unsigned wm = __ballot_sync(FULL, want);
     if (wm) {
         const int nw = __popc(wm);
-        if (w.count + nw > a.C) compact(w);
+        if (w.count + nw > w.C) compact(w);
         if (want) {
             const int k = w.count + __popc(wm & ((1u << w.lane) - 1u));
             w.ed[k] = S;
@@ -221,7 +222,7 @@ __device__ __forceinline__ void after_step(Warp<T> &w, bool valid, float S, int 
         }
         w.count += nw;
         __syncwarp();
-        if (w.count >= a.K && w.r2 == INFINITY) compact(w);
+        if (w.count >= w.K && w.r2 == INFINITY) compact(w);
     }
     __syncwarp();
 }
@@ -279,15 +280,38 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
     w.pS = base + wc.pS;
     w.lane = lane;
     const int nb0 = a.db < a.nblk ? a.db : a.nblk;
+    const int n_items = a.n_items_dev ? *a.n_items_dev : a.n_items;
 
     for (;;) {
         int item = 0;
         if (lane == 0) item = (int)atomicAdd(a.work_counter, 1u);
         item = __shfl_sync(FULL, item, 0);
-        if (item >= a.n_items) break;
-        const int64_t q = item / a.S;
-        const int s = item - (int)q * a.S;
+        if (item >= n_items) break;
+        int64_t q;
+        int s, S;
+        if (a.items) {                       // batched: planned (query, split, splits)
+            const int2 it = a.items[item];
+            q = it.x;
+            s = it.y >> 16;
+            S = it.y & 0xffff;
+        } else {
+            q = item / a.S;
+            s = item - (int)q * a.S;
+            S = a.S;
+        }
+        const int K = a.Kq ? a.Kq[q] : a.K;
+        const int nprobe = a.nprobe_q ? a.nprobe_q[q] : a.nprobe;
+        int C = 1;
+        {
+            int Kp = 1;
+            while (Kp < K) Kp <<= 1;
+            const int need = 2 * Kp > K + 32 ? 2 * Kp : K + 32;
+            while (C < need) C <<= 1;
+        }
         w.q = q;
+        w.K = K;
+        w.C = C;
+        w.S = S;
         for (int i = lane; i < a.Dp; i += 32) w.qv[i] = a.qrot[q * a.Dp + i];
         w.head = w.cnt = 0;
         w.count = 0;
@@ -295,8 +319,8 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
         w.dims = 0ull;
         __syncwarp();
 
-        for (int p = s; p < a.nprobe; p += a.S) {
-            const int c = a.probes[q * a.nprobe + p];
+        for (int p = s; p < nprobe; p += S) {
+            const int c = a.probes[q * (a.probe_stride ? a.probe_stride : a.nprobe) + p];
             const int o = (int)a.off[c];
             const int n = (int)(a.off[c + 1] - o);
             const T *cb = static_cast<const T *>(a.data) + (int64_t)o * a.Dp;
@@ -304,9 +328,9 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
                 const float r2 = current_r2(w);
                 const int m = m0 + lane;
                 const bool valid = m < n;
-                float S = 0.f;
-                if (valid) S = accum_range(cb, n, m, 0, nb0, w.qv, 0.f);
-                after_step(w, valid, S, nb0, o, m, n, r2);
+                float Sd = 0.f;
+                if (valid) Sd = accum_range(cb, n, m, 0, nb0, w.qv, 0.f);
+                after_step(w, valid, Sd, nb0, o, m, n, r2);
                 while (w.cnt >= 32) process_pending(w, 32);
             }
         }
@@ -316,16 +340,21 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
         unsigned long long wd = w.dims;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) wd += __shfl_xor_sync(FULL, wd, off);
-        if (a.S == 1) {
-            for (int k = lane; k < a.K; k += 32) {
+        if (S == 1) {
+            const int64_t ob = a.out_off ? a.out_off[q] : q * (int64_t)K;
+            if (a.out_off && (ob < 0 || ob + K > a.out_total)) {
+                if (lane == 0) atomicOr(a.err, ERR_OUT_RANGE);
+                continue;
+            }
+            for (int k = lane; k < K; k += 32) {
                 const bool has = k < w.count;
-                a.out_ids[q * a.K + k] = has ? (int64_t)w.ei[k] : (int64_t)-1;
-                a.out_d2[q * a.K + k] = has ? w.ed[k] : INFINITY;
+                a.out_ids[ob + k] = has ? (int64_t)w.ei[k] : (int64_t)-1;
+                a.out_d2[ob + k] = has ? w.ed[k] : INFINITY;
             }
             if (lane == 0 && a.out_dims) a.out_dims[q] = (int64_t)wd;
         } else {
-            const int64_t pbase = (int64_t)item * a.K;
-            for (int k = lane; k < a.K; k += 32) {
+            const int64_t pbase = (int64_t)item * (a.Kmax ? a.Kmax : a.K);
+            for (int k = lane; k < K; k += 32) {
                 a.part_d[pbase + k] = k < w.count ? w.ed[k] : INFINITY;
                 a.part_i[pbase + k] = k < w.count ? w.ei[k] : 0x7fffffff;
             }
@@ -335,22 +364,34 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
     }
 }
 
-// Merges the S sorted partial lists of each query into its final top-K.
-__global__ void __launch_bounds__(256) finalize_topk_kernel(const float *__restrict__ part_d,
-                                                            const int *__restrict__ part_i,
-                                                            int64_t nq, int S, int K, int T,
-                                                            int64_t *__restrict__ out_ids,
-                                                            float *__restrict__ out_d2)
+// Merges the S_q sorted partial lists of each split query into its final
+// top-K (queries with one item were written by the scan itself).
+__global__ void __launch_bounds__(256) finalize_topk_kernel(ScanArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
+    const int Tmax = a.finalize_T;
     float *sd = reinterpret_cast<float *>(smraw);
-    int *si = reinterpret_cast<int *>(sd + T);
-    for (int64_t q = blockIdx.x; q < nq; q += gridDim.x) {
-        const int64_t b = q * (int64_t)S * K;
+    int *si = reinterpret_cast<int *>(sd + Tmax);
+    for (int64_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
+        int64_t first;
+        int S;
+        if (a.items) {
+            first = a.item_first[q];
+            S = a.items[first].y & 0xffff;
+        } else {
+            first = q * a.S;
+            S = a.S;
+        }
+        if (S <= 1) continue;                 // uniform per block
+        const int K = a.Kq ? a.Kq[q] : a.K;
+        int T = 1;
+        while (T < S * K) T <<= 1;
         for (int i = threadIdx.x; i < T; i += blockDim.x) {
-            const bool in = i < S * K;
-            sd[i] = in ? part_d[b + i] : INFINITY;
-            si[i] = in ? part_i[b + i] : 0x7fffffff;
+            const int s = i / K, k = i - s * K;
+            const bool in = s < S;
+            const int64_t src = (first + s) * (int64_t)(a.Kmax ? a.Kmax : a.K) + k;
+            sd[i] = in ? a.part_d[src] : INFINITY;
+            si[i] = in ? a.part_i[src] : 0x7fffffff;
         }
         __syncthreads();
         for (int size = 2; size <= T; size <<= 1) {
@@ -372,10 +413,16 @@ __global__ void __launch_bounds__(256) finalize_topk_kernel(const float *__restr
                 __syncthreads();
             }
         }
+        const int64_t ob = a.out_off ? a.out_off[q] : q * (int64_t)K;
+        if (a.out_off && (ob < 0 || ob + K > a.out_total)) {
+            if (threadIdx.x == 0) atomicOr(a.err, ERR_OUT_RANGE);
+            __syncthreads();
+            continue;
+        }
         for (int k = threadIdx.x; k < K; k += blockDim.x) {
             const bool has = sd[k] != INFINITY || si[k] != 0x7fffffff;
-            out_ids[q * K + k] = has ? (int64_t)si[k] : (int64_t)-1;
-            out_d2[q * K + k] = has ? sd[k] : INFINITY;
+            a.out_ids[ob + k] = has ? (int64_t)si[k] : (int64_t)-1;
+            a.out_d2[ob + k] = has ? sd[k] : INFINITY;
         }
         __syncthreads();
     }
@@ -476,11 +523,11 @@ size_t scan_smem_bytes(const ScanArgs &a)
     return (size_t)WarpCarve(a.Dp, a.C).words * 4 * WARPS;
 }
 
-int scan_items_target(int device)
+int scan_items_target(int device, int items_per_sm)
 {
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
-    return nsm * 48;   // about two resident warps' worth of work per warp slot
+    return nsm * items_per_sm;   // default 48: about one item per resident warp slot
 }
 
 template <typename T>
@@ -537,16 +584,18 @@ cudaError_t launch_ads_scan(const ScanArgs &a, int grid, cudaStream_t s)
 
 cudaError_t launch_finalize_topk(const ScanArgs &a, cudaStream_t s)
 {
-    if (a.nq <= 0 || a.S <= 1) return cudaSuccess;
-    int T = 1;
-    while (T < a.S * a.K) T <<= 1;
-    size_t smem = (size_t)T * 8;
+    if (a.nq <= 0 || (!a.items && a.S <= 1)) return cudaSuccess;
+    // a split query has S_q * next_pow2(K_q) <= 16384 entries (the planner's cap)
+    int Tmax = 1;
+    while (Tmax < (a.items ? 16384 : a.S * a.K)) Tmax <<= 1;
+    ScanArgs b = a;
+    b.finalize_T = Tmax;
+    size_t smem = (size_t)Tmax * 8;
     cudaError_t e = cudaFuncSetAttribute(finalize_topk_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int64_t grid = a.nq < 152 * 8 ? a.nq : 152 * 8;
-    finalize_topk_kernel<<<(unsigned)grid, 256, smem, s>>>(a.part_d, a.part_i, a.nq, a.S, a.K, T,
-                                                          a.out_ids, a.out_d2);
+    finalize_topk_kernel<<<(unsigned)grid, 256, smem, s>>>(b);
     return cudaGetLastError();
 }
 

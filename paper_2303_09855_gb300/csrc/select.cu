@@ -25,9 +25,10 @@ __device__ __forceinline__ unsigned dist_key(float v)
 }
 
 __global__ void __launch_bounds__(ST) select_nprobe_kernel(const float *__restrict__ dist,
-                                                           int64_t nq, int nlist, int nprobe,
+                                                           int64_t nq, int nlist, int pstride,
                                                            int P2, int32_t *__restrict__ probes,
-                                                           float *__restrict__ pd2)
+                                                           float *__restrict__ pd2,
+                                                           const int32_t *__restrict__ nprobe_q)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned long long *sel = reinterpret_cast<unsigned long long *>(smraw);   // P2
@@ -37,6 +38,11 @@ __global__ void __launch_bounds__(ST) select_nprobe_kernel(const float *__restri
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     for (int64_t q = blockIdx.x; q < nq; q += gridDim.x) {
+        int nprobe = pstride;
+        if (nprobe_q) {                     // per-query count, clamped to [1, pstride]
+            nprobe = nprobe_q[q];
+            nprobe = nprobe < 1 ? 1 : (nprobe > pstride ? pstride : nprobe);
+        }
         const float *row = dist + q * nlist;
         for (int i = tid; i < nlist; i += ST) key[i] = dist_key(row[i]);
         if (tid == 0) {
@@ -115,8 +121,8 @@ __global__ void __launch_bounds__(ST) select_nprobe_kernel(const float *__restri
         }
         for (int p = tid; p < nprobe; p += ST) {
             unsigned long long v = sel[p];
-            probes[q * nprobe + p] = (int32_t)(v & 0xffffffffu);
-            if (pd2) pd2[q * nprobe + p] = __uint_as_float((unsigned)(v >> 32));
+            probes[q * pstride + p] = (int32_t)(v & 0xffffffffu);
+            if (pd2) pd2[q * pstride + p] = __uint_as_float((unsigned)(v >> 32));
         }
         __syncthreads();
     }
@@ -125,7 +131,8 @@ __global__ void __launch_bounds__(ST) select_nprobe_kernel(const float *__restri
 }  // namespace
 
 cudaError_t launch_select_nprobe(const float *dist, int64_t nq, int nlist, int nprobe,
-                                 int32_t *probes, float *probe_d2, cudaStream_t s)
+                                 int32_t *probes, float *probe_d2, cudaStream_t s,
+                                 const int32_t *nprobe_q)
 {
     if (nq <= 0) return cudaSuccess;
     int P2 = 1;
@@ -137,7 +144,7 @@ cudaError_t launch_select_nprobe(const float *dist, int64_t nq, int nlist, int n
     if (e != cudaSuccess) return e;
     int64_t grid = nq < 152 * 8 ? nq : 152 * 8;
     select_nprobe_kernel<<<(unsigned)grid, ST, smem, s>>>(dist, nq, nlist, nprobe, P2, probes,
-                                                          probe_d2);
+                                                          probe_d2, nprobe_q);
     return cudaGetLastError();
 }
 
