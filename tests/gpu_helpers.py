@@ -13,14 +13,16 @@ def near_tie_queries(Cr, Qr, nprobe):
         return np.zeros(Qr.shape[0], bool)
     _, pd = oracle.probe(Cr, Qr, nprobe + 1)
     a, b = pd[:, nprobe - 1], pd[:, nprobe]
-    return (b - a) <= REL * np.maximum(b, 1e-30)
+    with np.errstate(invalid="ignore"):
+        return (b - a) <= REL * np.maximum(b, 1e-30)
 
 
 def kth_near_tie(d2, K):
     if d2.shape[1] <= K:
         return np.zeros(d2.shape[0], bool)
     a, b = d2[:, K - 1], d2[:, K]
-    return (b - a) <= REL * np.maximum(b, 1e-30)
+    with np.errstate(invalid="ignore"):
+        return (b - a) <= REL * np.maximum(b, 1e-30)
 
 
 def topk_row_mismatch(ids, d2, eids, ed2):

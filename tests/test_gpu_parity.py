@@ -275,7 +275,7 @@ def test_invalid_arguments_are_rejected(adsx_mod, c1):
     wl, ix, *_ = c1
     bad = [dict(K=0, nprobe=10, delta_d=32), dict(K=10, nprobe=0, delta_d=32),
            dict(K=10, nprobe=101, delta_d=32), dict(K=10, nprobe=10, delta_d=24),
-           dict(K=2000, nprobe=10, delta_d=32), dict(K=10, nprobe=10, delta_d=0)]
+           dict(K=2000, nprobe=10, delta_d=32), dict(K=10, nprobe=10, delta_d=-16)]
     for kw in bad:
         with pytest.raises(adsx_mod.AdsxError) as e:
             ix.search(wl.Q, kw["K"], kw["nprobe"], eps0=2.1, delta_d=kw["delta_d"])
