@@ -253,6 +253,46 @@ int adsx_search_noalloc(const adsx_index *index, const float *Qv, int64_t nq,
                         int64_t *ids, float *dists, int64_t *dims_read,
                         void *stream);
 
+/*
+ * Serving: a continuous-batching request loop over adsx_search_batched.
+ * A worker thread keeps up to n_streams batches in flight (one per CUDA
+ * stream, so their work overlaps on the device).  Whenever a stream is free
+ * it forms the next batch from the queue head: requests sharing the head's
+ * (eps0, delta_d), as many as the free query slots (max_slots in flight),
+ * max_batch and the device-memory budget allow (admission by memory: each
+ * request is charged the device bytes its search needs).  The index stays
+ * resident; per-request results return through pinned host buffers.
+ *
+ * adsx_server_create   index must outlive the server.  max_K / max_nprobe
+ *                      bound every request.  ADSX_ENOMEM if staging fails.
+ * adsx_server_submit   q: host, D float32 (copied).  Returns a ticket.
+ *                      ADSX_ENOMEM if the request alone exceeds the budget.
+ * adsx_server_wait     blocks up to timeout_ms (host wait, bounded) for the
+ *                      ticket; copies K ids / dists (host) and dims_read (may
+ *                      be NULL) and forgets the ticket.  ADSX_ETIMEOUT if not
+ *                      done in time (the ticket stays valid), ADSX_EINVAL if
+ *                      it was cancelled.
+ * adsx_server_cancel   cancels a request that is still queued.
+ * adsx_server_stats    latency percentiles (submit -> results on the host)
+ *                      and throughput of completed requests since the last
+ *                      reset, batches launched, the largest number of batches
+ *                      and of queries in flight at once.
+ */
+typedef struct adsx_server adsx_server;
+int adsx_server_create(const adsx_index *index, int32_t max_slots, int32_t max_batch,
+                       int32_t n_streams, int64_t mem_budget_bytes, int32_t max_K,
+                       int32_t max_nprobe, adsx_server **out);
+int adsx_server_submit(adsx_server *server, const float *q, int32_t K, int32_t nprobe,
+                       float eps0, int32_t delta_d, int64_t *ticket);
+int adsx_server_wait(adsx_server *server, int64_t ticket, int32_t timeout_ms,
+                     int64_t *ids, float *dists, int64_t *dims_read);
+int adsx_server_cancel(adsx_server *server, int64_t ticket);
+int adsx_server_stats(adsx_server *server, double *p50_ms, double *p99_ms, double *qps,
+                      int64_t *completed, int64_t *batches,
+                      int64_t *max_inflight_batches, int64_t *max_inflight_queries);
+int adsx_server_reset_stats(adsx_server *server);
+int adsx_server_destroy(adsx_server *server);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char *adsx_last_error(void);
 

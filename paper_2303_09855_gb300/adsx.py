@@ -58,13 +58,22 @@ def load():
     lib.adsx_search_noalloc.argtypes = [V, V, i64, i32, i32, f32, i32, V, V, V, V]
     lib.adsx_search_batched.argtypes = [V, V, i64, V, V, i32, i32, f32, i32, V, i64, V, V, V, V]
     lib.adsx_autotune.argtypes = [V, V, i64, i32, i32, f32, V, V, V, V]
+    lib.adsx_server_create.argtypes = [V, i32, i32, i32, i64, i32, i32, ctypes.POINTER(V)]
+    lib.adsx_server_submit.argtypes = [V, V, i32, i32, f32, i32, V]
+    lib.adsx_server_wait.argtypes = [V, i64, i32, V, V, V]
+    lib.adsx_server_cancel.argtypes = [V, i64]
+    lib.adsx_server_stats.argtypes = [V, V, V, V, V, V, V, V]
+    lib.adsx_server_reset_stats.argtypes = [V]
+    lib.adsx_server_destroy.argtypes = [V]
     lib.adsx_set_stage_timing.argtypes = [V, i32]
     lib.adsx_stage_ms.argtypes = [V, V]
     lib.adsx_last_error.restype = ctypes.c_char_p
     for fn in ("adsx_build_index", "adsx_free_index", "adsx_index_info", "adsx_search",
                "adsx_probe", "adsx_rotate", "adsx_dco_fixed_r", "adsx_stream_status",
                "adsx_set_stage_timing", "adsx_stage_ms", "adsx_search_noalloc",
-               "adsx_search_batched", "adsx_autotune"):
+               "adsx_search_batched", "adsx_autotune", "adsx_server_create",
+               "adsx_server_submit", "adsx_server_wait", "adsx_server_cancel",
+               "adsx_server_stats", "adsx_server_reset_stats", "adsx_server_destroy"):
         getattr(lib, fn).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -331,3 +340,90 @@ def stage_ms(index: Index):
 def stream_status(index: Index, stream=None):
     """adsx_stream_status: synchronise and raise if a device wait gave up."""
     _check(load().adsx_stream_status(index.handle, _stream_of(None, stream)))
+
+
+# ---------------------------------------------------------------- serving
+class Server:
+    """adsx_server_*: continuous-batching request loop (see include/adsx.h)."""
+
+    def __init__(self, index: Index, max_slots=1024, max_batch=256, n_streams=4,
+                 mem_budget_bytes=1 << 30, max_K=100, max_nprobe=64):
+        self.index = index
+        self.max_K = max_K
+        h = ctypes.c_void_p()
+        _check(load().adsx_server_create(index.handle, int(max_slots), int(max_batch),
+                                         int(n_streams), int(mem_budget_bytes), int(max_K),
+                                         int(max_nprobe), ctypes.byref(h)))
+        self.handle = h
+
+    def submit(self, q, K, nprobe, eps0=2.1, delta_d=32):
+        q = _host(q, np.float32).reshape(-1)
+        t = ctypes.c_int64()
+        _check(load().adsx_server_submit(self.handle, _ptr(q), int(K), int(nprobe),
+                                         float(eps0) if math.isfinite(eps0) else float("inf"),
+                                         int(delta_d), ctypes.byref(t)))
+        return t.value, int(K)
+
+    def wait(self, ticket, timeout_ms=10000):
+        t, K = ticket
+        ids = np.empty(K, np.int64)
+        d2 = np.empty(K, np.float32)
+        dims = ctypes.c_int64()
+        _check(load().adsx_server_wait(self.handle, t, int(timeout_ms), _ptr(ids), _ptr(d2),
+                                       ctypes.byref(dims)))
+        return ids, d2, dims.value
+
+    def cancel(self, ticket):
+        _check(load().adsx_server_cancel(self.handle, ticket[0]))
+
+    def stats(self):
+        p50, p99, qps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        c, b, mib, miq = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().adsx_server_stats(self.handle, ctypes.byref(p50), ctypes.byref(p99),
+                                        ctypes.byref(qps), ctypes.byref(c), ctypes.byref(b),
+                                        ctypes.byref(mib), ctypes.byref(miq)))
+        return dict(p50_ms=p50.value, p99_ms=p99.value, qps=qps.value, completed=c.value,
+                    batches=b.value, max_inflight_batches=mib.value,
+                    max_inflight_queries=miq.value)
+
+    def reset_stats(self):
+        _check(load().adsx_server_reset_stats(self.handle))
+
+    def close(self):
+        if self.handle:
+            load().adsx_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def server_create(index, **kw):
+    return Server(index, **kw)
+
+
+def server_submit(server, q, K, nprobe, eps0=2.1, delta_d=32):
+    return server.submit(q, K, nprobe, eps0, delta_d)
+
+
+def server_wait(server, ticket, timeout_ms=10000):
+    return server.wait(ticket, timeout_ms)
+
+
+def server_cancel(server, ticket):
+    server.cancel(ticket)
+
+
+def server_stats(server):
+    return server.stats()
+
+
+def server_reset_stats(server):
+    server.reset_stats()
+
+
+def server_destroy(server):
+    server.close()
