@@ -31,6 +31,7 @@ struct Index {
     int device = 0;
     float *P = nullptr;        // Dp x Dp, zero padded, row-major (y = P x)
     float *cents = nullptr;    // nlist x Dp rotated centroids
+    float *cnorm = nullptr;    // nlist ||c'||^2
     void *data = nullptr;      // N x Dp of the storage type, dim-blocked per cluster
     float *rows32 = nullptr;   // N x Dp FP32 rotated rows in CSR order (16-bit storage only)
     float *norms = nullptr;    // N FP32 norms ||y|| in CSR order (16-bit storage only)
@@ -224,9 +225,14 @@ __device__ __forceinline__ float test_factor(int blk, int D, float eps0)
 void set_last_error(const std::string &msg);
 
 // ----------------------------------------------------------------- launches
-cudaError_t launch_nt_gemm(const float *A, int64_t M, int lda, const float *B, int Nb,
-                           int ldb, int Kd, float *C, int ldc, int Nout, bool dist,
-                           cudaStream_t s);
+// C = A B^T on tcgen05 tensor cores, FP32-accurate (3-term TF32 split), A
+// M x Kd (row stride lda), B Nb x Kd (row stride ldb; rows >= Nb read as 0),
+// C M x Nout (row stride ldc).  With an and bn (squared row norms of A and B)
+// C[i][j] = max(an[i] + bn[j] - 2 (A B^T)[i][j], 0) instead.
+cudaError_t launch_tc_gemm(const float *A, int64_t M, int lda, const float *B, int Nb, int ldb,
+                           int Kd, float *C, int ldc, int Nout, const float *an, const float *bn,
+                           unsigned *err, cudaStream_t s);
+cudaError_t launch_row_sqnorm(const float *X, int64_t M, int ld, int K, float *out, cudaStream_t s);
 
 // Rotated rows Y (N x Dp, FP32) into the dim-blocked layout of `storage`
 // (ADSX_F32 / ADSX_BF16 / ADSX_F16); for 16-bit storage also the FP32 row copy

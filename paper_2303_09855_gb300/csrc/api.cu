@@ -135,8 +135,21 @@ int check_index(const Index *ix)
 cudaError_t rotate_queries(const Index *ix, const float *q_dev, int64_t nq, float *qrot,
                            cudaStream_t s)
 {
-    return adsx::launch_nt_gemm(q_dev, nq, ix->D, ix->P, ix->D, ix->Dp, ix->D, qrot, ix->Dp,
-                                ix->Dp, false, s);
+    return adsx::launch_tc_gemm(q_dev, nq, ix->D, ix->P, ix->D, ix->Dp, ix->D, qrot, ix->Dp,
+                                ix->Dp, nullptr, nullptr, ix->err, s);
+}
+
+// ||q'-c'||^2 for every (query, centroid) as ||q'||^2 + ||c'||^2 - 2 q'.c'.
+cudaError_t centroid_distances(const Index *ix, const float *qrot, int64_t nq, float *dist,
+                               Scratch &sc)
+{
+    float *qn = nullptr;
+    cudaError_t e = sc.get(&qn, (size_t)nq);
+    if (e != cudaSuccess) return e;
+    e = adsx::launch_row_sqnorm(qrot, nq, ix->Dp, ix->Dp, qn, sc.s);
+    if (e != cudaSuccess) return e;
+    return adsx::launch_tc_gemm(qrot, nq, ix->Dp, ix->cents, ix->nlist, ix->Dp, ix->Dp, dist,
+                                ix->nlist, ix->nlist, qn, ix->cnorm, ix->err, sc.s);
 }
 
 cudaError_t mark(const Index *ix, int i, cudaStream_t s)
@@ -151,8 +164,7 @@ cudaError_t probe_queries(const Index *ix, const float *qrot, int64_t nq, int np
     float *dist = nullptr;
     cudaError_t e = sc.get(&dist, (size_t)nq * ix->nlist);
     if (e != cudaSuccess) return e;
-    e = adsx::launch_nt_gemm(qrot, nq, ix->Dp, ix->cents, ix->nlist, ix->Dp, ix->Dp, dist,
-                             ix->nlist, ix->nlist, true, sc.s);
+    e = centroid_distances(ix, qrot, nq, dist, sc);
     if (e != cudaSuccess) return e;
     if ((e = mark(ix, 2, sc.s)) != cudaSuccess) return e;
     return adsx::launch_select_nprobe(dist, nq, ix->nlist, nprobe, probes, pd2, sc.s);
@@ -271,6 +283,7 @@ int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
 
     BCK(dalloc((void **)&ix->P, sizeof(float) * Dp * Dp), "alloc P");
     BCK(dalloc((void **)&ix->cents, sizeof(float) * (size_t)nlist * Dp), "alloc centroids");
+    BCK(dalloc((void **)&ix->cnorm, sizeof(float) * (size_t)nlist), "alloc centroid norms");
     const size_t esz = storage == ADSX_F32 ? 4 : 2;
     BCK(dalloc((void **)&ix->data, esz * (size_t)N * Dp), "alloc data");
     if (storage != ADSX_F32) {
@@ -309,8 +322,11 @@ int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
         BCK(cudaMemcpyAsync(pd, pos.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, s), "copy positions");
         BCK(cudaMemcpyAsync(cd, centroids, sizeof(float) * (size_t)nlist * D, cudaMemcpyHostToDevice, s), "copy C");
         // Sec. 3.1 / Sec. 6.1: rotate every data vector and centroid once.
-        BCK(adsx::launch_nt_gemm(xd, N, D, ix->P, D, Dp, D, yd, Dp, Dp, false, s), "rotate data");
-        BCK(adsx::launch_nt_gemm(cd, nlist, D, ix->P, D, Dp, D, ix->cents, Dp, Dp, false, s), "rotate centroids");
+        BCK(adsx::launch_tc_gemm(xd, N, D, ix->P, D, Dp, D, yd, Dp, Dp, nullptr, nullptr, ix->err, s),
+            "rotate data");
+        BCK(adsx::launch_tc_gemm(cd, nlist, D, ix->P, D, Dp, D, ix->cents, Dp, Dp, nullptr, nullptr,
+                                 ix->err, s), "rotate centroids");
+        BCK(adsx::launch_row_sqnorm(ix->cents, nlist, Dp, Dp, ix->cnorm, s), "centroid norms");
         BCK(adsx::launch_scatter_layout(yd, N, Dp, ad, pd, ix->off, ix->data, storage, ix->rows32,
                                         ix->norms, s), "scatter layout");
         BCK(cudaStreamSynchronize(s), "build sync");
@@ -329,6 +345,7 @@ int adsx_free_index(adsx_index *index)
     cudaDeviceSynchronize();
     cudaFree(ix->P);
     cudaFree(ix->cents);
+    cudaFree(ix->cnorm);
     cudaFree(ix->data);
     cudaFree(ix->rows32);
     cudaFree(ix->norms);
@@ -574,8 +591,7 @@ int adsx_search_batched(const adsx_index *index, const float *Qv, int64_t nq, co
     {
         float *dist = nullptr;
         CK(sc.get(&dist, (size_t)nq * ix->nlist), "alloc distances");
-        CK(adsx::launch_nt_gemm(qrot, nq, ix->Dp, ix->cents, ix->nlist, ix->Dp, ix->Dp, dist,
-                                ix->nlist, ix->nlist, true, s), "centroid distances");
+        CK(centroid_distances(ix, qrot, nq, dist, sc), "centroid distances");
         CK(mark(ix, 2, s), "event");
         CK(adsx::launch_select_nprobe(dist, nq, ix->nlist, max_nprobe, probes, nullptr, s, pq.dev),
            "select");

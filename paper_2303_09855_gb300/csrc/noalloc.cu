@@ -137,7 +137,7 @@ extern "C" int adsx_search_noalloc(const adsx_index *index, const float *Qv, int
 
     // Size check before touching the array.
     auto rup = [](size_t b) { return (std::max<size_t>(b, 1) + 255) & ~size_t(255); };
-    size_t need = rup((size_t)nq * Dp * 4) + rup((size_t)nq * ix->nlist * 4) +
+    size_t need = rup((size_t)nq * Dp * 4) + rup((size_t)nq * 4) + rup((size_t)nq * ix->nlist * 4) +
                   rup((size_t)nq * nprobe * 4) + rup((size_t)(nblk + 1) * 4) + rup(4);
     if (a.S > 1) need += rup((size_t)nq * 4) + 2 * rup((size_t)a.n_items * K * 4);
     if (need > (size_t)ADSX_NOALLOC_SCRATCH_BYTES)
@@ -151,6 +151,7 @@ extern "C" int adsx_search_noalloc(const adsx_index *index, const float *Qv, int
     if (rc) return rc;
     Carver cv{base};
     float *qrot = cv.take<float>((size_t)nq * Dp);
+    float *qn = cv.take<float>((size_t)nq);
     float *dist = cv.take<float>((size_t)nq * ix->nlist);
     int32_t *probes = cv.take<int32_t>((size_t)nq * nprobe);
     float *ftab = cv.take<float>((size_t)nblk + 1);
@@ -179,10 +180,12 @@ extern "C" int adsx_search_noalloc(const adsx_index *index, const float *Qv, int
     }
     e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
     if (e == cudaSuccess)
-        e = adsx::launch_nt_gemm(Qv, nq, ix->D, ix->P, ix->D, Dp, ix->D, qrot, Dp, Dp, false, s);
+        e = adsx::launch_tc_gemm(Qv, nq, ix->D, ix->P, ix->D, Dp, ix->D, qrot, Dp, Dp, nullptr,
+                                 nullptr, ix->err, s);
+    if (e == cudaSuccess) e = adsx::launch_row_sqnorm(qrot, nq, Dp, Dp, qn, s);
     if (e == cudaSuccess)
-        e = adsx::launch_nt_gemm(qrot, nq, Dp, ix->cents, ix->nlist, Dp, Dp, dist, ix->nlist,
-                                 ix->nlist, true, s);
+        e = adsx::launch_tc_gemm(qrot, nq, Dp, ix->cents, ix->nlist, Dp, Dp, dist, ix->nlist,
+                                 ix->nlist, qn, ix->cnorm, ix->err, s);
     if (e == cudaSuccess)
         e = adsx::launch_select_nprobe(dist, nq, ix->nlist, nprobe, probes, nullptr, s);
     if (e == cudaSuccess)
