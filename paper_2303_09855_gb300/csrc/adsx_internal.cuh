@@ -234,6 +234,11 @@ cudaError_t launch_tc_gemm(const float *A, int64_t M, int lda, const float *B, i
                            unsigned *err, cudaStream_t s);
 cudaError_t launch_row_sqnorm(const float *X, int64_t M, int ld, int K, float *out, cudaStream_t s);
 
+// Index-phase rotation Y = X P^T (N x D times D x D, P row stride ldp) with
+// FP64 accumulation, written as N x Dp FP32 (columns >= D are 0).
+cudaError_t launch_rotate_f64(const float *X, int64_t N, int D, const float *P, int ldp, float *Y,
+                              int Dp, cudaStream_t s);
+
 // Rotated rows Y (N x Dp, FP32) into the dim-blocked layout of `storage`
 // (ADSX_F32 / ADSX_BF16 / ADSX_F16); for 16-bit storage also the FP32 row copy
 // and the norms, both in CSR order.

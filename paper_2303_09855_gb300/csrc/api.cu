@@ -322,10 +322,10 @@ int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
         BCK(cudaMemcpyAsync(pd, pos.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, s), "copy positions");
         BCK(cudaMemcpyAsync(cd, centroids, sizeof(float) * (size_t)nlist * D, cudaMemcpyHostToDevice, s), "copy C");
         // Sec. 3.1 / Sec. 6.1: rotate every data vector and centroid once.
-        BCK(adsx::launch_tc_gemm(xd, N, D, ix->P, D, Dp, D, yd, Dp, Dp, nullptr, nullptr, ix->err, s),
-            "rotate data");
-        BCK(adsx::launch_tc_gemm(cd, nlist, D, ix->P, D, Dp, D, ix->cents, Dp, Dp, nullptr, nullptr,
-                                 ix->err, s), "rotate centroids");
+        // Index phase: exact-rounded rotation (FP64 accumulation) of the data
+        // and the centroids, once per index.
+        BCK(adsx::launch_rotate_f64(xd, N, D, ix->P, Dp, yd, Dp, s), "rotate data");
+        BCK(adsx::launch_rotate_f64(cd, nlist, D, ix->P, Dp, ix->cents, Dp, s), "rotate centroids");
         BCK(adsx::launch_row_sqnorm(ix->cents, nlist, Dp, Dp, ix->cnorm, s), "centroid norms");
         BCK(adsx::launch_scatter_layout(yd, N, Dp, ad, pd, ix->off, ix->data, storage, ix->rows32,
                                         ix->norms, s), "scatter layout");

@@ -118,3 +118,63 @@ cudaError_t launch_scatter_layout(const float *Y, int64_t N, int Dp, const int32
 }
 
 }  // namespace adsx
+
+namespace adsx {
+namespace {
+
+// Index-phase rotation Y = X P^T with FP64 accumulation (each y rounded once
+// to FP32), so the stored vectors carry no error beyond their own rounding.
+// 64 x 64 output tile per 256-thread block, 4 x 4 per thread, k-steps of 16.
+__global__ void __launch_bounds__(256) rotate_f64_kernel(const float *__restrict__ X, int64_t N,
+                                                         int D, const float *__restrict__ P,
+                                                         int ldp, float *__restrict__ Y, int Dp)
+{
+    __shared__ double Xs[16][64 + 1];
+    __shared__ double Ps[16][64 + 1];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t r0 = (int64_t)blockIdx.x * 64;
+    const int c0 = blockIdx.y * 64;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < D; k0 += 16) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int e = tid + i * 256, r = e >> 4, kk = e & 15;
+            const int64_t gr = r0 + r;
+            const int gk = k0 + kk, gc = c0 + r;
+            Xs[kk][r] = (gr < N && gk < D) ? (double)X[gr * D + gk] : 0.0;
+            Ps[kk][r] = (gc < D && gk < D) ? (double)P[(int64_t)gc * ldp + gk] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    acc[i][j] = fma(Xs[kk][ty * 4 + i], Ps[kk][tx * 4 + j], acc[i][j]);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t gr = r0 + ty * 4 + i;
+        if (gr >= N) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gc = c0 + tx * 4 + j;
+            if (gc < Dp) Y[gr * Dp + gc] = (float)acc[i][j];
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_rotate_f64(const float *X, int64_t N, int D, const float *P, int ldp, float *Y,
+                              int Dp, cudaStream_t s)
+{
+    if (N <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((N + 63) / 64), (unsigned)((Dp + 63) / 64));
+    rotate_f64_kernel<<<grid, 256, 0, s>>>(X, N, D, P, ldp, Y, Dp);
+    return cudaGetLastError();
+}
+
+}  // namespace adsx
