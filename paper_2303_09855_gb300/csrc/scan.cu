@@ -43,14 +43,11 @@ constexpr unsigned FULL = 0xffffffffu;
 __host__ __device__ inline int align4(int x) { return (x + 3) & ~3; }
 
 // Per-warp shared-memory region, in 4-byte words.
-constexpr int PF_BLOCKS = 2;            // first-step blocks staged ahead per tile
-
 struct WarpCarve {
-    int pf, qv, ed, ei, po, pm, pn, pb, pS, words;
+    int qv, ed, ei, po, pm, pn, pb, pS, words;
     __host__ __device__ WarpCarve(int Dp, int C)
     {
         int o = 0;
-        pf = o; o += PF_BLOCKS * 32 * 16;    // 16 words = 64 bytes per lane per block
         qv = o; o = align4(o + Dp);
         ed = o; o = align4(o + C);
         ei = o; o = align4(o + C);
@@ -76,15 +73,13 @@ struct Warp {
     int *ei;
     int *po, *pm, *pn, *pb;
     float *pS;
-    unsigned char *pf;         // staged first step of the next tile
-    const float *ftab;         // test factors (shared memory)
     int lane;
     int64_t q;
     int K, C, S;               // this item's K, buffer capacity, splits of its query
     int head, cnt;             // pending ring (warp-uniform)
     int count;                 // candidate buffer fill (warp-uniform)
     float r2;                  // this warp's K-th distance (warp-uniform)
-    unsigned dims;             // per lane, dims sampled by this item
+    unsigned long long dims;   // per lane
 };
 
 // Sorts the candidate buffer by (distance, id), keeps the first K and sets
@@ -179,14 +174,14 @@ __device__ __forceinline__ void after_step(Warp<T> &w, bool valid, float S, int 
     const bool fin = valid && blk >= a.nblk;
     bool surv = false;
     if (valid && !fin) {
-        if (a.test_on && S > r2 * w.ftab[blk]) {
+        if (a.test_on && S > r2 * a.ftab[blk]) {
             const int d = blk * BLK;
-            w.dims += (unsigned)(d < a.D ? d : a.D);
+            w.dims += (unsigned long long)(d < a.D ? d : a.D);
         } else {
             surv = true;
         }
     }
-    if (fin) w.dims += (unsigned)a.D;
+    if (fin) w.dims += (unsigned long long)a.D;
     const unsigned sm = __ballot_sync(FULL, surv);
     if (surv) {
         const int idx = (w.head + w.cnt + __popc(sm & ((1u << w.lane) - 1u))) & (RING - 1);
@@ -261,80 +256,6 @@ __device__ __forceinline__ void process_pending(Warp<T> &w, int nb)
     after_step(w, valid, S, blk, o, m, n, r2);
 }
 
-// ---- first step of the next tile staged in shared memory with cp.async ----
-// Each lane copies its own candidate's first PF_BLOCKS blocks (16-byte pieces)
-// and reads them back itself.  Piece i of a lane's block sits at a rotated
-// slot so that a warp-wide 16-byte read touches every bank once per 8 lanes.
-template <typename T> struct Pieces { static constexpr int Q = 2; };   // 16-bit: 32 B / block
-template <> struct Pieces<float> { static constexpr int Q = 4; };       // FP32: 64 B / block
-
-template <typename T>
-__device__ __forceinline__ int pf_off(int b, int lane, int i)
-{
-    constexpr int Q = Pieces<T>::Q, LPR = 8 / Q;     // lanes per 128-byte bank row
-    return (b * 32 + lane) * Q * 16 + ((i + lane / LPR) % Q) * 16;
-}
-
-template <typename T>
-__device__ __forceinline__ void prefetch_first(unsigned char *pf, const T *cb, int n, int m,
-                                               bool valid, int nbp, int lane)
-{
-    constexpr int Q = Pieces<T>::Q;
-    if (valid) {
-        const int64_t stride = (int64_t)n * BLK;
-        for (int b = 0; b < nbp; ++b) {
-            const unsigned char *src =
-                reinterpret_cast<const unsigned char *>(cb + b * stride + (int64_t)m * BLK);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const unsigned dst = (unsigned)__cvta_generic_to_shared(pf + pf_off<T>(b, lane, i));
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + i * 16)
-                             : "memory");
-            }
-        }
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-// The staged blocks, accumulated in dimension order (the same arithmetic as
-// the global-memory path).
-__device__ __forceinline__ float accum_staged(const unsigned char *pf, int nbp, int lane,
-                                              const float *qv, float S, float)
-{
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    for (int b = 0; b < nbp; ++b) {
-        float4 v[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            v[i] = *reinterpret_cast<const float4 *>(pf + pf_off<float>(b, lane, i));
-        const float4 *q4 = reinterpret_cast<const float4 *>(qv + b * BLK);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float4 qq = q4[i];
-            float t;
-            t = v[i].x - qq.x; S = fmaf(t, t, S);
-            t = v[i].y - qq.y; S = fmaf(t, t, S);
-            t = v[i].z - qq.z; S = fmaf(t, t, S);
-            t = v[i].w - qq.w; S = fmaf(t, t, S);
-        }
-    }
-    return S;
-}
-
-template <typename H>
-__device__ __forceinline__ float accum_staged(const unsigned char *pf, int nbp, int lane,
-                                              const float *qv, float S, H)
-{
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    for (int b = 0; b < nbp; ++b) {
-        const uint4 w0 = *reinterpret_cast<const uint4 *>(pf + pf_off<H>(b, lane, 0));
-        const uint4 w1 = *reinterpret_cast<const uint4 *>(pf + pf_off<H>(b, lane, 1));
-        S = accum_8h<H>(w0, qv + b * BLK, S);
-        S = accum_8h<H>(w1, qv + b * BLK + 8, S);
-    }
-    return S;
-}
-
 // Resident blocks per SM the register budget is sized for (FP32: 48
 // registers, 40 warps per SM; 16-bit storage with its recheck: 64).
 template <typename T> struct MinBlocks { static constexpr int value = 8; };
@@ -347,13 +268,8 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const WarpCarve wc(a.Dp, a.C);
     float *base = reinterpret_cast<float *>(smraw) + (size_t)warp * wc.words;
-    __shared__ float s_ftab[256];
-    for (int b = threadIdx.x; b <= a.nblk && b < 256; b += THREADS) s_ftab[b] = a.ftab[b];
-    __syncthreads();
     Warp<T> w;
     w.a = &a;
-    w.ftab = s_ftab;
-    w.pf = reinterpret_cast<unsigned char *>(base + wc.pf);
     w.qv = base + wc.qv;
     w.ed = base + wc.ed;
     w.ei = reinterpret_cast<int *>(base + wc.ei);
@@ -400,52 +316,23 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
         w.head = w.cnt = 0;
         w.count = 0;
         w.r2 = INFINITY;
-        w.dims = 0u;
+        w.dims = 0ull;
         __syncwarp();
 
-        // Tiles of 32 members, cluster by cluster in probe order.  The first
-        // step of tile t+1 is staged (cp.async) before tile t's test and
-        // pending steps run, so its latency overlaps them.
-        const int32_t *prow = a.probes + q * (a.probe_stride ? a.probe_stride : a.nprobe);
-        int cp = s, co = 0, cn = 0, cm0 = 0;
-        for (; cp < nprobe; cp += S) {                 // first non-empty cluster
-            const int c = prow[cp];
-            co = (int)a.off[c];
-            cn = (int)(a.off[c + 1] - co);
-            if (cn > 0) break;
-        }
-        const int nbp = nb0 < PF_BLOCKS ? nb0 : PF_BLOCKS;
-        if (cp < nprobe)
-            prefetch_first(w.pf, static_cast<const T *>(a.data) + (int64_t)co * a.Dp, cn,
-                           lane, lane < cn, nbp, lane);
-        while (cp < nprobe) {
-            // the tile after (cp, cm0)
-            int np_ = cp, no = co, nn = cn, nm0 = cm0 + 32;
-            if (nm0 >= cn) {
-                nm0 = 0;
-                for (np_ = cp + S; np_ < nprobe; np_ += S) {
-                    const int c = prow[np_];
-                    no = (int)a.off[c];
-                    nn = (int)(a.off[c + 1] - no);
-                    if (nn > 0) break;
-                }
+        for (int p = s; p < nprobe; p += S) {
+            const int c = a.probes[q * (a.probe_stride ? a.probe_stride : a.nprobe) + p];
+            const int o = (int)a.off[c];
+            const int n = (int)(a.off[c + 1] - o);
+            const T *cb = static_cast<const T *>(a.data) + (int64_t)o * a.Dp;
+            for (int m0 = 0; m0 < n; m0 += 32) {
+                const float r2 = current_r2(w);
+                const int m = m0 + lane;
+                const bool valid = m < n;
+                float Sd = 0.f;
+                if (valid) Sd = accum_range(cb, n, m, 0, nb0, w.qv, 0.f);
+                after_step(w, valid, Sd, nb0, o, m, n, r2);
+                while (w.cnt >= 32) process_pending(w, 32);
             }
-            const float r2 = current_r2(w);
-            const int m = cm0 + lane;
-            const bool valid = m < cn;
-            const T *cb = static_cast<const T *>(a.data) + (int64_t)co * a.Dp;
-            float Sd = accum_staged(w.pf, valid ? nbp : 0, lane, w.qv, 0.f, T());
-            if (valid && nb0 > nbp) Sd = accum_range(cb, cn, m, nbp, nb0, w.qv, Sd);
-            __syncwarp();
-            if (np_ < nprobe)
-                prefetch_first(w.pf, static_cast<const T *>(a.data) + (int64_t)no * a.Dp, nn,
-                               nm0 + lane, nm0 + lane < nn, nbp, lane);
-            after_step(w, valid, Sd, nb0, co, m, cn, r2);
-            while (w.cnt >= 32) process_pending(w, 32);
-            cp = np_;
-            co = no;
-            cn = nn;
-            cm0 = nm0;
         }
         while (w.cnt > 0) process_pending(w, w.cnt < 32 ? w.cnt : 32);
         compact(w);
