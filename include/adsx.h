@@ -284,6 +284,11 @@ int adsx_server_create(const adsx_index *index, int32_t max_slots, int32_t max_b
                        int32_t max_nprobe, adsx_server **out);
 int adsx_server_submit(adsx_server *server, const float *q, int32_t K, int32_t nprobe,
                        float eps0, int32_t delta_d, int64_t *ticket);
+/* adsx_server_submit_many: n requests at once (host Q n x D, K[n], nprobe[n]),
+ * all with one arrival time; tickets[n] receives their tickets. */
+int adsx_server_submit_many(adsx_server *server, const float *Q, int64_t n, const int32_t *K,
+                            const int32_t *nprobe, float eps0, int32_t delta_d,
+                            int64_t *tickets);
 int adsx_server_wait(adsx_server *server, int64_t ticket, int32_t timeout_ms,
                      int64_t *ids, float *dists, int64_t *dims_read);
 int adsx_server_cancel(adsx_server *server, int64_t ticket);

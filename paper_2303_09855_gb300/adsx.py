@@ -61,6 +61,7 @@ def load():
     lib.adsx_server_create.argtypes = [V, i32, i32, i32, i64, i32, i32, ctypes.POINTER(V)]
     lib.adsx_server_submit.argtypes = [V, V, i32, i32, f32, i32, V]
     lib.adsx_server_wait.argtypes = [V, i64, i32, V, V, V]
+    lib.adsx_server_submit_many.argtypes = [V, V, i64, V, V, f32, i32, V]
     lib.adsx_server_cancel.argtypes = [V, i64]
     lib.adsx_server_stats.argtypes = [V, V, V, V, V, V, V, V]
     lib.adsx_server_reset_stats.argtypes = [V]
@@ -72,7 +73,8 @@ def load():
                "adsx_probe", "adsx_rotate", "adsx_dco_fixed_r", "adsx_stream_status",
                "adsx_set_stage_timing", "adsx_stage_ms", "adsx_search_noalloc",
                "adsx_search_batched", "adsx_autotune", "adsx_server_create",
-               "adsx_server_submit", "adsx_server_wait", "adsx_server_cancel",
+               "adsx_server_submit", "adsx_server_submit_many", "adsx_server_wait",
+               "adsx_server_cancel",
                "adsx_server_stats", "adsx_server_reset_stats", "adsx_server_destroy"):
         getattr(lib, fn).restype = ctypes.c_int
     _lib = lib
@@ -364,6 +366,17 @@ class Server:
                                          int(delta_d), ctypes.byref(t)))
         return t.value, int(K)
 
+    def submit_many(self, Q, K, nprobe, eps0=2.1, delta_d=32):
+        Q = _host(Q, np.float32)
+        n = Q.shape[0]
+        Kh = np.ascontiguousarray(np.broadcast_to(np.asarray(K, np.int32), (n,)))
+        Ph = np.ascontiguousarray(np.broadcast_to(np.asarray(nprobe, np.int32), (n,)))
+        t = np.empty(n, np.int64)
+        _check(load().adsx_server_submit_many(self.handle, _ptr(Q), n, _ptr(Kh), _ptr(Ph),
+                                              float(eps0) if math.isfinite(eps0) else float("inf"),
+                                              int(delta_d), _ptr(t)))
+        return [(int(x), int(k)) for x, k in zip(t, Kh)]
+
     def wait(self, ticket, timeout_ms=10000):
         t, K = ticket
         ids = np.empty(K, np.int64)
@@ -407,6 +420,10 @@ def server_create(index, **kw):
 
 def server_submit(server, q, K, nprobe, eps0=2.1, delta_d=32):
     return server.submit(q, K, nprobe, eps0, delta_d)
+
+
+def server_submit_many(server, Q, K, nprobe, eps0=2.1, delta_d=32):
+    return server.submit_many(Q, K, nprobe, eps0, delta_d)
 
 
 def server_wait(server, ticket, timeout_ms=10000):

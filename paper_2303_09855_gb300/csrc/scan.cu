@@ -73,13 +73,14 @@ struct Warp {
     int *ei;
     int *po, *pm, *pn, *pb;
     float *pS;
+    const float *ftab;         // test factors (shared memory)
     int lane;
     int64_t q;
     int K, C, S;               // this item's K, buffer capacity, splits of its query
     int head, cnt;             // pending ring (warp-uniform)
     int count;                 // candidate buffer fill (warp-uniform)
     float r2;                  // this warp's K-th distance (warp-uniform)
-    unsigned long long dims;   // per lane
+    unsigned dims;             // per lane, dims sampled by this item
 };
 
 // Sorts the candidate buffer by (distance, id), keeps the first K and sets
@@ -174,14 +175,14 @@ __device__ __forceinline__ void after_step(Warp<T> &w, bool valid, float S, int 
     const bool fin = valid && blk >= a.nblk;
     bool surv = false;
     if (valid && !fin) {
-        if (a.test_on && S > r2 * a.ftab[blk]) {
+        if (a.test_on && S > r2 * w.ftab[blk]) {
             const int d = blk * BLK;
-            w.dims += (unsigned long long)(d < a.D ? d : a.D);
+            w.dims += (unsigned)(d < a.D ? d : a.D);
         } else {
             surv = true;
         }
     }
-    if (fin) w.dims += (unsigned long long)a.D;
+    if (fin) w.dims += (unsigned)a.D;
     const unsigned sm = __ballot_sync(FULL, surv);
     if (surv) {
         const int idx = (w.head + w.cnt + __popc(sm & ((1u << w.lane) - 1u))) & (RING - 1);
@@ -268,8 +269,12 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const WarpCarve wc(a.Dp, a.C);
     float *base = reinterpret_cast<float *>(smraw) + (size_t)warp * wc.words;
+    __shared__ float s_ftab[256];
+    for (int b = threadIdx.x; b <= a.nblk && b < 256; b += THREADS) s_ftab[b] = a.ftab[b];
+    __syncthreads();
     Warp<T> w;
     w.a = &a;
+    w.ftab = s_ftab;
     w.qv = base + wc.qv;
     w.ed = base + wc.ed;
     w.ei = reinterpret_cast<int *>(base + wc.ei);
@@ -316,7 +321,7 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
         w.head = w.cnt = 0;
         w.count = 0;
         w.r2 = INFINITY;
-        w.dims = 0ull;
+        w.dims = 0u;
         __syncwarp();
 
         for (int p = s; p < nprobe; p += S) {

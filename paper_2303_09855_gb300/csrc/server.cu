@@ -344,6 +344,45 @@ int adsx_server_submit(adsx_server *server, const float *q, int32_t K, int32_t n
     return ADSX_OK;
 }
 
+int adsx_server_submit_many(adsx_server *server, const float *Q, int64_t n, const int32_t *K,
+                            const int32_t *nprobe, float eps0, int32_t delta_d, int64_t *tickets)
+{
+    Server *sv = reinterpret_cast<Server *>(server);
+    if (!sv || (n > 0 && (!Q || !K || !nprobe || !tickets)) || n < 0)
+        return sfail(ADSX_EINVAL, "bad submit arguments");
+    if (!(eps0 >= 0.f)) return sfail(ADSX_EINVAL, "eps0 must be >= 0");
+    if (delta_d != 0 && (delta_d < 16 || delta_d % 16)) return sfail(ADSX_EINVAL, "bad delta_d");
+    const int D = sv->ix->D;
+    std::vector<Req> rs((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        if (K[i] < 1 || K[i] > sv->max_K || nprobe[i] < 1 || nprobe[i] > sv->max_nprobe)
+            return sfail(ADSX_EINVAL, "K / nprobe outside the server's limits");
+        Req &r = rs[(size_t)i];
+        r.q.assign(Q + i * D, Q + (i + 1) * D);
+        r.K = K[i];
+        r.nprobe = nprobe[i];
+        r.eps0 = eps0;
+        r.delta_d = delta_d;
+        r.cost = request_cost(sv->ix, K[i], sv->max_nprobe, sv->max_K);
+        if (r.cost > sv->budget) return sfail(ADSX_ENOMEM, "a request exceeds the whole budget");
+    }
+    const auto now = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (sv->completed == 0 && sv->reqs.empty()) sv->t_first = now;
+        for (int64_t i = 0; i < n; ++i) {
+            Req &r = rs[(size_t)i];
+            r.t_submit = now;
+            r.ticket = sv->next_ticket++;
+            tickets[i] = r.ticket;
+            sv->queue.push_back(r.ticket);
+            sv->reqs.emplace(r.ticket, std::move(r));
+        }
+    }
+    sv->cv_work.notify_one();
+    return ADSX_OK;
+}
+
 int adsx_server_wait(adsx_server *server, int64_t ticket, int32_t timeout_ms, int64_t *ids,
                      float *dists, int64_t *dims_read)
 {
