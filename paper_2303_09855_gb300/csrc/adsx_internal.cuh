@@ -225,19 +225,19 @@ __device__ __forceinline__ float test_factor(int blk, int D, float eps0)
 void set_last_error(const std::string &msg);
 
 // ----------------------------------------------------------------- launches
-// C = A B^T on tcgen05 tensor cores, FP32-accurate (3-term TF32 split), A
-// M x Kd (row stride lda), B Nb x Kd (row stride ldb; rows >= Nb read as 0),
-// C M x Nout (row stride ldc).  With an and bn (squared row norms of A and B)
-// C[i][j] = max(an[i] + bn[j] - 2 (A B^T)[i][j], 0) instead.
+// C[i][j] = max(an[i] + bn[j] - 2 (A B^T)[i][j], 0) on tcgen05 tensor cores
+// (3-term TF32 split, FP32 accumulation in TMEM): A M x Kd (row stride lda),
+// B Nb x Kd (row stride ldb; rows >= Nb read as 0), C M x Nout (row stride
+// ldc), an / bn the squared row norms of A / B.
 cudaError_t launch_tc_gemm(const float *A, int64_t M, int lda, const float *B, int Nb, int ldb,
                            int Kd, float *C, int ldc, int Nout, const float *an, const float *bn,
                            unsigned *err, cudaStream_t s);
 cudaError_t launch_row_sqnorm(const float *X, int64_t M, int ld, int K, float *out, cudaStream_t s);
 
-// Index-phase rotation Y = X P^T (N x D times D x D, P row stride ldp) with
-// FP64 accumulation, written as N x Dp FP32 (columns >= D are 0).
-cudaError_t launch_rotate_f64(const float *X, int64_t N, int D, const float *P, int ldp, float *Y,
-                              int Dp, cudaStream_t s);
+// Rotation Y = X P^T (N x D times D x D, P row stride ldp) with compensated
+// (Dot2) FP32 dot products, written as N x Dp FP32 (columns >= D are 0).
+cudaError_t launch_rotate(const float *X, int64_t N, int D, const float *P, int ldp, float *Y,
+                          int Dp, cudaStream_t s);
 
 // Rotated rows Y (N x Dp, FP32) into the dim-blocked layout of `storage`
 // (ADSX_F32 / ADSX_BF16 / ADSX_F16); for 16-bit storage also the FP32 row copy

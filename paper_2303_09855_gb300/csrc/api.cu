@@ -135,8 +135,7 @@ int check_index(const Index *ix)
 cudaError_t rotate_queries(const Index *ix, const float *q_dev, int64_t nq, float *qrot,
                            cudaStream_t s)
 {
-    return adsx::launch_tc_gemm(q_dev, nq, ix->D, ix->P, ix->D, ix->Dp, ix->D, qrot, ix->Dp,
-                                ix->Dp, nullptr, nullptr, ix->err, s);
+    return adsx::launch_rotate(q_dev, nq, ix->D, ix->P, ix->Dp, qrot, ix->Dp, s);
 }
 
 // ||q'-c'||^2 for every (query, centroid) as ||q'||^2 + ||c'||^2 - 2 q'.c'.
@@ -322,10 +321,9 @@ int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
         BCK(cudaMemcpyAsync(pd, pos.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, s), "copy positions");
         BCK(cudaMemcpyAsync(cd, centroids, sizeof(float) * (size_t)nlist * D, cudaMemcpyHostToDevice, s), "copy C");
         // Sec. 3.1 / Sec. 6.1: rotate every data vector and centroid once.
-        // Index phase: exact-rounded rotation (FP64 accumulation) of the data
-        // and the centroids, once per index.
-        BCK(adsx::launch_rotate_f64(xd, N, D, ix->P, Dp, yd, Dp, s), "rotate data");
-        BCK(adsx::launch_rotate_f64(cd, nlist, D, ix->P, Dp, ix->cents, Dp, s), "rotate centroids");
+        // Index phase: rotation of the data and the centroids, once per index.
+        BCK(adsx::launch_rotate(xd, N, D, ix->P, Dp, yd, Dp, s), "rotate data");
+        BCK(adsx::launch_rotate(cd, nlist, D, ix->P, Dp, ix->cents, Dp, s), "rotate centroids");
         BCK(adsx::launch_row_sqnorm(ix->cents, nlist, Dp, Dp, ix->cnorm, s), "centroid norms");
         BCK(adsx::launch_scatter_layout(yd, N, Dp, ad, pd, ix->off, ix->data, storage, ix->rows32,
                                         ix->norms, s), "scatter layout");

@@ -3,9 +3,9 @@
 //   x = x_hi + x_lo with x_hi = tf32(x), x_lo = tf32(x - x_hi), and
 //   A B^T ~= A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T   (the lo*lo term, of
 //   relative size 2^-22, is dropped), all accumulated in FP32 in TMEM.
-// Uses:
-//   rotation   Y = X P^T        (Sec. 3.1: y = P x; index vectors, centroids, queries)
-//   distances  D2[q][c] = ||q'||^2 + ||c'||^2 - 2 q'.c'   (Sec. 2.2.2 centroid ranking)
+// Use: the query-centroid distances of the probe step (Sec. 2.2.2),
+//   D2[q][c] = ||q'||^2 + ||c'||^2 - 2 q'.c'  (clamped at 0),
+// a dense nq x nlist x Dp contraction.
 //
 // One 128-thread CTA computes a 128 x 128 output tile.  Per 32-wide k-step
 // every thread converts one row of A and one row of B (fp32 from global) into
@@ -126,8 +126,7 @@ __device__ __forceinline__ void stage_row(const float *__restrict__ src, bool va
     }
 }
 
-// MODE 0: C = A B^T.  MODE 1: C = an[i] + bn[j] - 2 (A B^T) clamped at 0.
-template <int MODE>
+// C[i][j] = max(an[i] + bn[j] - 2 (A B^T)[i][j], 0).
 __global__ void __launch_bounds__(128, 1)
     tc_gemm_kernel(const float *__restrict__ A, int64_t M, int lda, const float *__restrict__ B,
                    int Nb, int ldb, int Kd, float *__restrict__ C, int ldc, int Nout,
@@ -196,7 +195,7 @@ __global__ void __launch_bounds__(128, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int64_t row = m0 + warp * 32 + lane;
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-        const float rn = (MODE == 1 && row < M) ? an[row] : 0.f;
+        const float rn = (row < M) ? an[row] : 0.f;
 #pragma unroll 1
         for (int c0 = 0; c0 < TN; c0 += 16) {
             uint32_t v[16];
@@ -213,9 +212,8 @@ __global__ void __launch_bounds__(128, 1)
                 for (int j = 0; j < 16; ++j) {
                     const int col = n0 + c0 + j;
                     if (col < Nout) {
-                        float acc = __uint_as_float(v[j]);
-                        if (MODE == 1) acc = fmaxf(rn + bn[col] - 2.f * acc, 0.f);
-                        C[row * ldc + col] = acc;
+                        const float acc = __uint_as_float(v[j]);
+                        C[row * ldc + col] = fmaxf(rn + bn[col] - 2.f * acc, 0.f);
                     }
                 }
             }
@@ -256,20 +254,12 @@ cudaError_t launch_tc_gemm(const float *A, int64_t M, int lda, const float *B, i
 {
     if (M <= 0 || Nout <= 0) return cudaSuccess;
     if ((M + TM - 1) / TM > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (!an || !bn) return cudaErrorInvalidValue;
     dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)((Nout + TN - 1) / TN));
-    if (an && bn) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<1>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        tc_gemm_kernel<1><<<grid, 128, SMEM_BYTES, s>>>(A, M, lda, B, Nb, ldb, Kd, C, ldc, Nout, an,
-                                                         bn, err);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<0>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        tc_gemm_kernel<0><<<grid, 128, SMEM_BYTES, s>>>(A, M, lda, B, Nb, ldb, Kd, C, ldc, Nout,
-                                                         nullptr, nullptr, err);
-    }
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    tc_gemm_kernel<<<grid, 128, SMEM_BYTES, s>>>(A, M, lda, B, Nb, ldb, Kd, C, ldc, Nout, an, bn, err);
     return cudaGetLastError();
 }
 

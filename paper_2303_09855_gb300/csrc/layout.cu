@@ -122,36 +122,63 @@ cudaError_t launch_scatter_layout(const float *Y, int64_t N, int Dp, const int32
 namespace adsx {
 namespace {
 
-// Index-phase rotation Y = X P^T with FP64 accumulation (each y rounded once
-// to FP32), so the stored vectors carry no error beyond their own rounding.
+// Rotation Y = X P^T (y = P x, Sec. 3.1) with compensated FP32 dot products:
+// Dot2 of Ogita, Rump & Oishi ("Accurate sum and dot product", SIAM J. Sci.
+// Comput. 2005).  Each product is split exactly by TwoProduct (h = a*b,
+// r = fma(a, b, -h)), the running sum by TwoSum (Knuth), and the errors are
+// summed separately, so y is as accurate as if computed in twice the working
+// precision and then rounded once to FP32.
 // 64 x 64 output tile per 256-thread block, 4 x 4 per thread, k-steps of 16.
-__global__ void __launch_bounds__(256) rotate_f64_kernel(const float *__restrict__ X, int64_t N,
-                                                         int D, const float *__restrict__ P,
-                                                         int ldp, float *__restrict__ Y, int Dp)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
-    __shared__ double Xs[16][64 + 1];
-    __shared__ double Ps[16][64 + 1];
+    s = a + b;
+    const float z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+
+__global__ void __launch_bounds__(256) rotate_dot2_kernel(const float *__restrict__ X, int64_t N,
+                                                          int D, const float *__restrict__ P,
+                                                          int ldp, float *__restrict__ Y, int Dp)
+{
+    __shared__ float Xs[16][64 + 4];
+    __shared__ float Ps[16][64 + 4];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t r0 = (int64_t)blockIdx.x * 64;
     const int c0 = blockIdx.y * 64;
-    double acc[4][4] = {};
+    float hi[4][4], lo[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) hi[i][j] = lo[i][j] = 0.f;
     for (int k0 = 0; k0 < D; k0 += 16) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int e = tid + i * 256, r = e >> 4, kk = e & 15;
             const int64_t gr = r0 + r;
             const int gk = k0 + kk, gc = c0 + r;
-            Xs[kk][r] = (gr < N && gk < D) ? (double)X[gr * D + gk] : 0.0;
-            Ps[kk][r] = (gc < D && gk < D) ? (double)P[(int64_t)gc * ldp + gk] : 0.0;
+            Xs[kk][r] = (gr < N && gk < D) ? X[gr * D + gk] : 0.f;
+            Ps[kk][r] = (gc < D && gk < D) ? P[(int64_t)gc * ldp + gk] : 0.f;
         }
         __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], b[4];
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk)
+            for (int i = 0; i < 4; ++i) a[i] = Xs[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Ps[kk][tx * 4 + j];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    acc[i][j] = fma(Xs[kk][ty * 4 + i], Ps[kk][tx * 4 + j], acc[i][j]);
+                for (int j = 0; j < 4; ++j) {
+                    const float h = a[i] * b[j];
+                    const float r = fmaf(a[i], b[j], -h);
+                    float s, q;
+                    two_sum(hi[i][j], h, s, q);
+                    hi[i][j] = s;
+                    lo[i][j] += q + r;
+                }
+        }
         __syncthreads();
     }
 #pragma unroll
@@ -161,19 +188,20 @@ __global__ void __launch_bounds__(256) rotate_f64_kernel(const float *__restrict
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int gc = c0 + tx * 4 + j;
-            if (gc < Dp) Y[gr * Dp + gc] = (float)acc[i][j];
+            if (gc < Dp) Y[gr * Dp + gc] = hi[i][j] + lo[i][j];
         }
     }
 }
 
 }  // namespace
 
-cudaError_t launch_rotate_f64(const float *X, int64_t N, int D, const float *P, int ldp, float *Y,
-                              int Dp, cudaStream_t s)
+cudaError_t launch_rotate(const float *X, int64_t N, int D, const float *P, int ldp, float *Y,
+                          int Dp, cudaStream_t s)
 {
     if (N <= 0) return cudaSuccess;
+    if ((N + 63) / 64 > 0x7fffffffLL) return cudaErrorInvalidValue;
     dim3 grid((unsigned)((N + 63) / 64), (unsigned)((Dp + 63) / 64));
-    rotate_f64_kernel<<<grid, 256, 0, s>>>(X, N, D, P, ldp, Y, Dp);
+    rotate_dot2_kernel<<<grid, 256, 0, s>>>(X, N, D, P, ldp, Y, Dp);
     return cudaGetLastError();
 }
 
