@@ -153,9 +153,10 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def scan_traffic():
-    """DRAM bytes per scan launch from the committed ncu summary, if it was
-    taken on the current scan source (else None)."""
+def scan_traffic(workload=None, nprobe=None, storage="f32"):
+    """DRAM bytes per scan launch from the committed 1-pass ncu capture
+    (profiles/scan_traffic.json), if it was taken on the current scan source,
+    the same workload and nprobe (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "scan_traffic.json")
     src = os.path.join(ROOT, "paper_2303_09855_gb300", "csrc", "scan.cu")
@@ -164,6 +165,9 @@ def scan_traffic():
             t = json.load(f)
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         if t.get("scan_cu_sha256_16") != h:
+            return None
+        if workload is not None and (t.get("workload") != workload or t.get("nprobe") != nprobe
+                                     or storage != "f32"):
             return None
         return t
     except Exception:
@@ -587,7 +591,7 @@ def main():
     esz = 4.0 if args.storage == "f32" else 2.0
     algo_bytes = esz * ads_dims
     achieved = algo_bytes / (ads_scan_ms * 1e-3) / 1e9
-    tr = scan_traffic()
+    tr = scan_traffic(wl.name, np_ads, args.storage)
     fd_frac = ads_dims / fd_dims if fd_dims else None
     line = {
         "metric": METRIC, "value": nq * ws / (ads_ms * 1e-3), "unit": UNIT, "n_gpus": ws,
@@ -611,6 +615,8 @@ def main():
                      "kernel": "ads_scan_kernel",
                      "traffic": (tr["dram_bytes_per_launch"] * ads_dims / tr["dims_per_launch"])
                      if tr else None,
+                     "dram_frac": ((tr["dram_bytes_per_launch"] * ads_dims / tr["dims_per_launch"])
+                                   / (ads_scan_ms * 1e-3) / 1e9 / hbm) if tr else None,
                      "algorithmic_bytes_per_launch": algo_bytes},
         "e2e": {"value": e2e_qps, "unit": UNIT, "h2d_bytes_per_step": int(nq * wl.D * 4),
                 "d2h_bytes_per_step": int(nq * args.K * 12)},
