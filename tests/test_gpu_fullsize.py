@@ -1,0 +1,94 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times, on outputs sampled for the oracle.
+
+SIFT-shaped 1M x 128, 10k queries, nlist 4096, nprobe 64, K 100, eps0 2.1,
+delta_d 32 (one warp per query): for a sample of queries the oracle computes
+exact IVF and the DCO decisions of the true top-K at the exact K-th distance;
+FDScanning must return exact IVF, ADSampling every returned distance exact and
+the bracket invariant, and recall@10 over the sample within 0.01 of the
+sequential oracle's IVF+.  GIST-shaped 1M x 960 in BF16 storage (1000 queries,
+nprobe 16, K 10): the same checks with the 16-bit allowance; the oracle rotates
+only the sampled queries' candidates (other rows are never read)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_09855_gb300 import workloads as W
+from gpu_helpers import REL, kth_near_tie, near_tie_queries, topk_row_mismatch
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def _check_sample(ids, d2, wl, Y, Cr, Qr, qs, K, nprobe, eps0, dd, allow, fd_ids=None,
+                  fd_d2=None):
+    got_ids, got_d2 = ids[qs], d2[qs]
+    eids, ed2 = oracle.ivf_exact(Y, Cr, wl.assign, Qr, K + 1, nprobe)
+    oids, _, _, _ = oracle.ivf_ads(Y, Cr, wl.assign, Qr, K, nprobe, eps0, dd)
+    skip = near_tie_queries(Cr, Qr, nprobe) | kth_near_tie(ed2, K)
+    checked = 0
+    for j in range(len(qs)):
+        if skip[j]:
+            continue
+        checked += 1
+        if fd_ids is not None:
+            assert not topk_row_mismatch(fd_ids[qs[j]], fd_d2[qs[j]], eids[j, :K], ed2[j, :K]), j
+        for i, d in zip(got_ids[j], got_d2[j]):
+            if i >= 0:
+                ex = float(np.sum((Y[i] - Qr[j]) ** 2))
+                assert abs(d - ex) <= REL * ex + 1e-6, (j, i, d, ex)
+        top = eids[j, :K][eids[j, :K] >= 0]
+        dec, _, mar = oracle.dco_fixed_r(Y[top], Qr[j:j + 1], np.array([ed2[j, K - 1]]), eps0, dd)
+        must = set(top[(dec[0] == oracle.POSITIVE) & (mar[0] >= allow)].tolist())
+        assert must <= set(got_ids[j].tolist()), j
+    assert checked >= len(qs) // 2
+    # recall@10 of the sample against exact IVF's top 10 (the probed candidates)
+    r_gpu = np.mean([len(set(got_ids[j, :10]) & set(eids[j, :10])) / 10 for j in range(len(qs))])
+    r_orc = np.mean([len(set(oids[j, :10]) & set(eids[j, :10])) / 10 for j in range(len(qs))])
+    assert r_gpu >= r_orc - 0.01, (r_gpu, r_orc)
+
+
+def test_sift_shaped_1M_headline_configuration():
+    import torch
+    from paper_2303_09855_gb300 import adsx, build
+    build.build()
+    wl = W.gen_sift_like(device="cuda")
+    ix = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign)
+    try:
+        Qd = torch.from_numpy(wl.Q).cuda()
+        K, nprobe, eps0, dd = 100, 64, 2.1, 32
+        ids, d2 = (t.cpu().numpy() for t in ix.search(Qd, K, nprobe, eps0=eps0, delta_d=dd))
+        fd_ids, fd_d2 = (t.cpu().numpy() for t in ix.search(Qd, K, nprobe, eps0=math.inf))
+        qs = np.random.default_rng(0).choice(wl.Q.shape[0], size=24, replace=False)
+        threads = oracle.max_threads()
+        Y = oracle.rotate(wl.P, wl.X, threads)
+        Cr = oracle.rotate(wl.P, wl.centroids, threads)
+        Qr = oracle.rotate(wl.P, wl.Q[qs], threads)
+        _check_sample(ids, d2, wl, Y, Cr, Qr, qs, K, nprobe, eps0, dd, REL, fd_ids, fd_d2)
+    finally:
+        ix.close()
+
+
+def test_gist_shaped_1M_bf16():
+    import torch
+    from paper_2303_09855_gb300 import adsx, build
+    build.build()
+    wl = W.gen_gist_like(device="cuda")
+    ix = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign, storage=adsx.BF16)
+    try:
+        Qd = torch.from_numpy(wl.Q).cuda()
+        K, nprobe, eps0, dd = 10, 16, 2.1, 32
+        ids, d2 = (t.cpu().numpy() for t in ix.search(Qd, K, nprobe, eps0=eps0, delta_d=dd))
+        fd_ids, fd_d2 = (t.cpu().numpy() for t in ix.search(Qd, K, nprobe, eps0=math.inf))
+        qs = np.random.default_rng(1).choice(wl.Q.shape[0], size=6, replace=False)
+        threads = oracle.max_threads()
+        Cr = oracle.rotate(wl.P, wl.centroids, threads)
+        Qr = oracle.rotate(wl.P, wl.Q[qs], threads)
+        probes, _ = oracle.probe(Cr, Qr, nprobe + 1, threads)
+        rows = np.nonzero(np.isin(wl.assign, np.unique(probes)))[0]
+        Y = np.zeros((wl.N, wl.D))
+        Y[rows] = oracle.rotate(wl.P, wl.X[rows], threads)
+        _check_sample(ids, d2, wl, Y, Cr, Qr, qs, K, nprobe, eps0, dd, 0.1, fd_ids, fd_d2)
+    finally:
+        ix.close()
