@@ -259,8 +259,11 @@ __device__ __forceinline__ void process_pending(Warp<T> &w, int nb)
 
 // Resident blocks per SM the register budget is sized for (FP32: 48
 // registers, 40 warps per SM; 16-bit storage with its recheck: 64).
+#ifndef ADSX_SCAN_MINBLOCKS_F32
+#define ADSX_SCAN_MINBLOCKS_F32 10
+#endif
 template <typename T> struct MinBlocks { static constexpr int value = 8; };
-template <> struct MinBlocks<float> { static constexpr int value = 10; };
+template <> struct MinBlocks<float> { static constexpr int value = ADSX_SCAN_MINBLOCKS_F32; };
 
 template <typename T>
 __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(ScanArgs a)
