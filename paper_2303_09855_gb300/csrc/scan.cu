@@ -257,13 +257,14 @@ __device__ __forceinline__ void process_pending(Warp<T> &w, int nb)
     after_step(w, valid, S, blk, o, m, n, r2);
 }
 
-// Resident blocks per SM the register budget is sized for (FP32: 48
-// registers, 40 warps per SM; 16-bit storage with its recheck: 64).
-#ifndef ADSX_SCAN_MINBLOCKS_F32
-#define ADSX_SCAN_MINBLOCKS_F32 10
+// Resident blocks per SM the register budget is sized for: 6 (up to 85
+// registers, 24 warps per SM).  Measured on the SIFT-shaped 1M x 128
+// benchmark: bounds of 12 or more spill in the inner loop and halve the scan
+// rate; 6 (no spills) beats 10 (48 registers, 40 warps) by 10%.
+#ifndef ADSX_SCAN_MINBLOCKS
+#define ADSX_SCAN_MINBLOCKS 6
 #endif
-template <typename T> struct MinBlocks { static constexpr int value = 8; };
-template <> struct MinBlocks<float> { static constexpr int value = ADSX_SCAN_MINBLOCKS_F32; };
+template <typename T> struct MinBlocks { static constexpr int value = ADSX_SCAN_MINBLOCKS; };
 
 template <typename T>
 __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(ScanArgs a)
