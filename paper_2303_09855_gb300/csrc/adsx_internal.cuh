@@ -117,26 +117,32 @@ __device__ __forceinline__ float accum_range_f32(const float *__restrict__ base,
 
 // 16-bit storage: a 16-dim block is 32 bytes (one sector), converted to FP32
 // and accumulated in FP32 in dimension order.
-__device__ __forceinline__ void unpack8(uint4 w, float *v, __nv_bfloat16)
+__device__ __forceinline__ void unpack2(unsigned x, float &lo, float &hi, __nv_bfloat16)
 {
-    const unsigned u[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        v[2 * i] = __uint_as_float(u[i] << 16);
-        v[2 * i + 1] = __uint_as_float(u[i] & 0xffff0000u);
-    }
+    lo = __uint_as_float(x << 16);
+    hi = __uint_as_float(x & 0xffff0000u);
 }
 
-__device__ __forceinline__ void unpack8(uint4 w, float *v, __half)
+__device__ __forceinline__ void unpack2(unsigned x, float &lo, float &hi, __half)
 {
-    const unsigned u[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        __half2 h = *reinterpret_cast<const __half2 *>(&u[i]);
-        float2 f = __half22float2(h);
-        v[2 * i] = f.x;
-        v[2 * i + 1] = f.y;
-    }
+    lo = __half2float(__ushort_as_half((unsigned short)(x & 0xffffu)));
+    hi = __half2float(__ushort_as_half((unsigned short)(x >> 16)));
+}
+
+__device__ __forceinline__ void unpack8(uint4 w, float *v, __nv_bfloat16 t)
+{
+    unpack2(w.x, v[0], v[1], t);
+    unpack2(w.y, v[2], v[3], t);
+    unpack2(w.z, v[4], v[5], t);
+    unpack2(w.w, v[6], v[7], t);
+}
+
+__device__ __forceinline__ void unpack8(uint4 w, float *v, __half t)
+{
+    unpack2(w.x, v[0], v[1], t);
+    unpack2(w.y, v[2], v[3], t);
+    unpack2(w.z, v[4], v[5], t);
+    unpack2(w.w, v[6], v[7], t);
 }
 
 template <typename H>
