@@ -570,6 +570,25 @@ def main():
     fd_ms, fd_scan_ms, fd_dims, _ = timed(np_fd, math.inf, max(3, args.steps // 2), 2)
     fd_ms = max_over_ranks(fd_ms)
 
+    # PDScanning on raw vectors (an index with P = I): the paper's IVF** baseline
+    ix_raw = adsx.build_index(wl.X, np.eye(wl.D, dtype=np.float32), wl.centroids, wl.assign,
+                              storage=storage)
+    adsx.set_stage_timing(ix_raw, True)
+    pd_t, pd_dims = [], 0.0
+    for st in range(2 + max(3, args.steps // 2)):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, _, pdd = adsx.search_pdscan(ix_raw, Qd, args.K, np_fd, args.delta_d, return_dims=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if st >= 2:
+            pd_t.append(e0.elapsed_time(e1))
+            pd_dims = float(pdd.sum().item())
+    pd_ms = max_over_ranks(sum(pd_t) / len(pd_t))
+    ix_raw.close()
+
     # ADSampling arm (the headline), clocks sampled during it
     import torch.distributed as dist
     if ws > 1:
@@ -622,6 +641,9 @@ def main():
                    "recall10": recall_ads, "storage": args.storage},
         "fd_scan": {"qps": job_throughput(nq, ws, fd_ms), "nprobe": np_fd, "ms_per_step": fd_ms,
                     "scan_ms": fd_scan_ms},
+        "pd_scan_raw": {"qps": job_throughput(nq, ws, pd_ms), "nprobe": np_fd, "ms_per_step": pd_ms,
+                        "dims_fraction_vs_fd": pd_dims / fd_dims if fd_dims else None,
+                        "what": "PDScanning (exact) on raw vectors, dim-blocked layout (IVF**)"},
         "speedup_vs_fd": fd_ms / ads_ms,
         "dims_fraction_vs_fd_at_ads_nprobe": None,
         "stage_ms_last": {"rotate": stage[0], "centroid_dist": stage[1], "select": stage[2],

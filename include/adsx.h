@@ -124,6 +124,19 @@ int adsx_search(const adsx_index *index, const float *Qv, int64_t nq,
                 int64_t *ids, float *dists, int64_t *dims_read, void *stream);
 
 /*
+ * adsx_search_pdscan -- the IVF* baseline of Sec. 6.1: IVF whose DCOs are
+ * PDScanning -- dimensions scanned in delta_d steps, a candidate stopped as
+ * soon as its partial squared distance S_d exceeds r^2 (strictly).  An exact
+ * DCO: results equal exact IVF; only the dimensions read differ.  On an
+ * index built with P = I the partial sums are over raw coordinates, which
+ * with the dim-blocked layout is the paper's IVF** (Sec. 6.1).  Arguments and
+ * outputs as adsx_search (no eps0).
+ */
+int adsx_search_pdscan(const adsx_index *index, const float *Qv, int64_t nq,
+                       int32_t K, int32_t nprobe, int32_t delta_d, int64_t *ids,
+                       float *dists, int64_t *dims_read, void *stream);
+
+/*
  * adsx_search_batched -- the IVF+ query phase for a batch whose queries each
  * have their own K and nprobe (same method as adsx_search, Sec. 4), in one
  * persistent scan launch: a device-side planner validates the per-query

@@ -14,6 +14,8 @@ Functions (each follows the passage named in its docstring):
   dco(o, q, r2, eps0, delta_d)      Algorithm 1 with the Sec. 3.2 test
   ivf_ads(...)                      Sec. 4, IVF+ (Algorithm 1 inside IVF)
   dco_fixed_r(Y, Qr, r2, ...)       Sec. 6.2.5 fixed-threshold linear scan
+  dco_pd(o, q, r2, delta_d)         Sec. 6.1 PDScanning (exact partial-distance DCO)
+  ivf_pd(...)                       Sec. 6.1 IVF* (IVF with PDScanning DCOs)
   recall_at(...), avg_dist_ratio()  Sec. 6.1 accuracy metrics
 """
 from __future__ import annotations
@@ -65,6 +67,9 @@ def _load():
             lib.orc_ivf_ads.argtypes = [P, i64, i32, P, i32, P, P, i64, i32, i32,
                                         f64, i32, P, P, P, P, cint]
             lib.orc_dco_fixed_r.argtypes = [P, i64, i32, P, i64, P, f64, i32, P, P, P, cint]
+            lib.orc_dco_pd.argtypes = [P, P, i32, f64, i32, P, P]
+            lib.orc_dco_pd.restype = cint
+            lib.orc_ivf_pd.argtypes = [P, i64, i32, P, i32, P, P, i64, i32, i32, i32, P, P, P, cint]
             _lib = lib
     return _lib
 
@@ -175,6 +180,33 @@ def dco_fixed_r(Y, Qr, r2, eps0: float, delta_d: int, nthreads: int = 0):
     _load().orc_dco_fixed_r(_p(Y), N, D, _p(Qr), nq, _p(r2), float(eps0), int(delta_d),
                             _p(dec), _p(dims), _p(mar), nthreads)
     return dec, dims, mar
+
+
+def dco_pd(o, q, r2: float, delta_d: int):
+    """Sec. 6.1 PDScanning on one pair.  Returns (decision, dims, S)."""
+    o = _c(o, np.float64)
+    q = _c(q, np.float64)
+    dims = ctypes.c_int32(0)
+    S = ctypes.c_double(0.0)
+    res = _load().orc_dco_pd(_p(o), _p(q), o.shape[0], float(r2), int(delta_d),
+                             ctypes.byref(dims), ctypes.byref(S))
+    return int(res), int(dims.value), float(S.value)
+
+
+def ivf_pd(Y, Cr, assign, Qr, K: int, nprobe: int, delta_d: int, nthreads: int = 0):
+    """Sec. 6.1 IVF*: sequential IVF with PDScanning DCOs.  Returns ids,
+    squared distances and dims sampled per query."""
+    Y = _c(Y, np.float64)
+    Cr = _c(Cr, np.float64)
+    assign = _c(assign, np.int32)
+    Qr = _c(Qr, np.float64)
+    nq, D = Qr.shape
+    ids = np.empty((nq, K), np.int64)
+    d2 = np.empty((nq, K), np.float64)
+    dims = np.empty(nq, np.int64)
+    _load().orc_ivf_pd(_p(Y), Y.shape[0], D, _p(Cr), Cr.shape[0], _p(assign), _p(Qr), nq, K,
+                       nprobe, int(delta_d), _p(ids), _p(d2), _p(dims), nthreads)
+    return ids, d2, dims
 
 
 # ---------------------------------------------------------------- metrics

@@ -19,6 +19,8 @@
  *                         against the current K-th distance of the KNN set.
  *   - orc_dco_fixed_r     Sec. 6.2.5: Algorithm 1 over a linear scan with a
  *                         fixed threshold per query (verification protocol).
+ *   - orc_dco_pd,         Sec. 6.1: PDScanning, the exact partial-distance
+ *     orc_ivf_pd          DCO of the IVF* / IVF** baselines.
  *
  * Conventions (readings of points the paper leaves open):
  *   - distances are SQUARED Euclidean distances in the rotated space;
@@ -394,4 +396,91 @@ void orc_dco_fixed_r(const double *Y, int64_t N, int32_t D, const double *Qr,
             if (margins) margins[q * N + n] = m;
         }
     }
+}
+
+/* ---------------------------------------------------------------------- */
+/* PDScanning (Sec. 6.1, the IVF* / IVF** baseline): scan dimensions in     */
+/* steps of delta_d and stop as soon as the partial squared distance S_d    */
+/* exceeds r^2 -- an exact DCO (S_d <= S_D, so a positive is never          */
+/* stopped).  Same outputs as orc_dco (decision, dims, S, margin).          */
+int orc_dco_pd(const double *o, const double *q, int32_t D, double r2, int32_t delta_d,
+               int32_t *dims, double *S_out)
+{
+    int32_t d = 0;
+    double S = 0.0;
+    while (d < D) {
+        int32_t dn = d + delta_d;
+        if (dn > D) dn = D;
+        for (int32_t i = d; i < dn; ++i) {
+            double t = o[i] - q[i];
+            S += t * t;
+        }
+        d = dn;
+        if (d < D && S > r2) {
+            if (dims) *dims = d;
+            if (S_out) *S_out = S;
+            return ORC_REJECTED;
+        }
+    }
+    if (dims) *dims = D;
+    if (S_out) *S_out = S;
+    return (S <= r2) ? ORC_POSITIVE : ORC_NEGATIVE_AT_D;
+}
+
+/* IVF* (Sec. 6.1): IVF whose DCOs are PDScanning against the current K-th  */
+/* distance; returns exactly the IVF result, with fewer dimensions read.    */
+void orc_ivf_pd(const double *Y, int64_t N, int32_t D, const double *Cr, int32_t nlist,
+                const int32_t *assign, const double *Qr, int64_t nq, int32_t K,
+                int32_t nprobe, int32_t delta_d, int64_t *ids, double *d2,
+                int64_t *dims_total, int nthreads)
+{
+    orc_buckets b = make_buckets(assign, N, nlist);
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t q = 0; q < nq; ++q) {
+        const double *qr = Qr + q * D;
+        int32_t *probes = (int32_t *)malloc(sizeof(int32_t) * (size_t)nprobe);
+        probe_one(Cr, nlist, D, qr, nprobe, probes, NULL);
+        double *hd = (double *)malloc(sizeof(double) * (size_t)K);
+        int64_t *hi = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
+        int32_t count = 0;
+        int64_t dims_sum = 0;
+        for (int32_t p = 0; p < nprobe; ++p) {
+            for (int64_t m = b.start[probes[p]]; m < b.start[probes[p] + 1]; ++m) {
+                int64_t id = b.member[m];
+                int32_t imax = 0;
+                double r2 = INFINITY;
+                if (count == K) {
+                    for (int32_t k = 1; k < K; ++k)
+                        if (pair_less(hd[imax], hi[imax], hd[k], hi[k])) imax = k;
+                    r2 = hd[imax];
+                }
+                int32_t dims = 0;
+                double S = 0.0;
+                int res = orc_dco_pd(Y + id * D, qr, D, r2, delta_d, &dims, &S);
+                dims_sum += dims;
+                if (res != ORC_POSITIVE) continue;
+                if (count < K) {
+                    hd[count] = S;
+                    hi[count] = id;
+                    ++count;
+                } else if (pair_less(S, id, hd[imax], hi[imax])) {
+                    hd[imax] = S;
+                    hi[imax] = id;
+                }
+            }
+        }
+        orc_pair *pairs = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(count > 0 ? count : 1));
+        for (int32_t k = 0; k < count; ++k) {
+            pairs[k].d = hd[k];
+            pairs[k].id = hi[k];
+        }
+        write_sorted(pairs, count, K, ids + q * K, d2 + q * K);
+        if (dims_total) dims_total[q] = dims_sum;
+        free(pairs);
+        free(hd);
+        free(hi);
+        free(probes);
+    }
+    free_buckets(&b);
 }

@@ -57,6 +57,7 @@ def load():
     lib.adsx_stream_status.argtypes = [V, V]
     lib.adsx_search_noalloc.argtypes = [V, V, i64, i32, i32, f32, i32, V, V, V, V]
     lib.adsx_search_batched.argtypes = [V, V, i64, V, V, i32, i32, f32, i32, V, i64, V, V, V, V]
+    lib.adsx_search_pdscan.argtypes = [V, V, i64, i32, i32, i32, V, V, V, V]
     lib.adsx_autotune.argtypes = [V, V, i64, i32, i32, f32, V, V, V, V]
     lib.adsx_server_create.argtypes = [V, i32, i32, i32, i64, i32, i32, ctypes.POINTER(V)]
     lib.adsx_server_submit.argtypes = [V, V, i32, i32, f32, i32, V]
@@ -72,7 +73,8 @@ def load():
     for fn in ("adsx_build_index", "adsx_free_index", "adsx_index_info", "adsx_search",
                "adsx_probe", "adsx_rotate", "adsx_dco_fixed_r", "adsx_stream_status",
                "adsx_set_stage_timing", "adsx_stage_ms", "adsx_search_noalloc",
-               "adsx_search_batched", "adsx_autotune", "adsx_server_create",
+               "adsx_search_batched", "adsx_search_pdscan", "adsx_autotune",
+               "adsx_server_create",
                "adsx_server_submit", "adsx_server_submit_many", "adsx_server_wait",
                "adsx_server_cancel",
                "adsx_server_stats", "adsx_server_reset_stats", "adsx_server_destroy"):
@@ -276,6 +278,19 @@ def search_noalloc(index: Index, Q, K: int, nprobe: int, eps0: float = 2.1, delt
                                       float(eps0) if math.isfinite(eps0) else float("inf"),
                                       int(delta_d), _ptr(ids), _ptr(d2), _ptr(dims),
                                       _stream_of(Q, stream)))
+    return (ids, d2, dims) if return_dims else (ids, d2)
+
+
+def search_pdscan(index: Index, Q, K: int, nprobe: int, delta_d: int = 32,
+                  return_dims: bool = False, stream=None):
+    """adsx_search_pdscan: IVF* (PDScanning DCOs, exact results)."""
+    Q = _prep_queries(Q)
+    nq = Q.shape[0]
+    ids = _out(Q, (nq, K), np.int64, "int64")
+    d2 = _out(Q, (nq, K), np.float32, "float32")
+    dims = _out(Q, (nq,), np.int64, "int64") if return_dims else None
+    _check(load().adsx_search_pdscan(index.handle, _ptr(Q), nq, int(K), int(nprobe), int(delta_d),
+                                     _ptr(ids), _ptr(d2), _ptr(dims), _stream_of(Q, stream)))
     return (ids, d2, dims) if return_dims else (ids, d2)
 
 

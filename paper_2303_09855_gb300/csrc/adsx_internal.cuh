@@ -295,7 +295,8 @@ struct ScanArgs {
 
 size_t scan_smem_bytes(const ScanArgs &a);
 int scan_items_target(int device, int items_per_sm = 48);
-cudaError_t launch_test_factors(float *ftab, int nblk, int D, float eps0, cudaStream_t s);
+cudaError_t launch_test_factors(float *ftab, int nblk, int D, float eps0, cudaStream_t s,
+                                int pd = 0);
 cudaError_t launch_ads_scan(const ScanArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_finalize_topk(const ScanArgs &a, cudaStream_t s);
 

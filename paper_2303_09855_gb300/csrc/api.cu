@@ -417,9 +417,11 @@ int adsx_probe(const adsx_index *index, const float *Qv, int64_t nq, int32_t npr
     return finish(s, pr.host || pd.host, "probe");
 }
 
-int adsx_search(const adsx_index *index, const float *Qv, int64_t nq, int32_t K, int32_t nprobe,
-                float eps0, int32_t delta_d, int64_t *ids, float *dists, int64_t *dims_read,
-                void *stream)
+}  // extern "C"
+
+static int search_impl(const adsx_index *index, const float *Qv, int64_t nq, int32_t K,
+                       int32_t nprobe, float eps0, int32_t delta_d, int64_t *ids, float *dists,
+                       int64_t *dims_read, void *stream, int pd)
 {
     const Index *ix = reinterpret_cast<const Index *>(index);
     int rc = check_index(ix);
@@ -483,7 +485,7 @@ int adsx_search(const adsx_index *index, const float *Qv, int64_t nq, int32_t K,
     if (nq * (int64_t)a.S >= ((int64_t)1 << 31)) return fail(ADSX_EINVAL, "too many queries in one call");
     a.n_items = (int32_t)(nq * a.S);
     a.db = delta_d / adsx::BLK;
-    a.test_on = isinf(eps0) ? 0 : 1;
+    a.test_on = (isinf(eps0) && !pd) ? 0 : 1;
     if (a.db >= a.nblk) a.test_on = 0;
     if (!a.test_on) a.db = a.nblk;   // FDScanning: the whole vector in one step
     a.out_ids = oi.dev;
@@ -497,7 +499,8 @@ int adsx_search(const adsx_index *index, const float *Qv, int64_t nq, int32_t K,
     float *ftab = nullptr;
     CK(sc.get(&ftab, (size_t)a.nblk + 1), "alloc test factors");
     a.ftab = ftab;
-    CK(adsx::launch_test_factors(ftab, a.nblk, a.D, a.test_on ? eps0 : 0.f, s), "test factors");
+    CK(adsx::launch_test_factors(ftab, a.nblk, a.D, (a.test_on && !pd) ? eps0 : 0.f, s, pd),
+       "test factors");
     if (a.S > 1) {
         CK(sc.get(&a.part_d, (size_t)a.n_items * K), "alloc partial lists");
         CK(sc.get(&a.part_i, (size_t)a.n_items * K), "alloc partial lists");
@@ -525,6 +528,22 @@ int adsx_search(const adsx_index *index, const float *Qv, int64_t nq, int32_t K,
         }
     }
     return ADSX_OK;
+}
+
+extern "C" {
+
+int adsx_search(const adsx_index *index, const float *Qv, int64_t nq, int32_t K, int32_t nprobe,
+                float eps0, int32_t delta_d, int64_t *ids, float *dists, int64_t *dims_read,
+                void *stream)
+{
+    return search_impl(index, Qv, nq, K, nprobe, eps0, delta_d, ids, dists, dims_read, stream, 0);
+}
+
+int adsx_search_pdscan(const adsx_index *index, const float *Qv, int64_t nq, int32_t K,
+                       int32_t nprobe, int32_t delta_d, int64_t *ids, float *dists,
+                       int64_t *dims_read, void *stream)
+{
+    return search_impl(index, Qv, nq, K, nprobe, 0.f, delta_d, ids, dists, dims_read, stream, 1);
 }
 
 int adsx_search_batched(const adsx_index *index, const float *Qv, int64_t nq, const int32_t *K,

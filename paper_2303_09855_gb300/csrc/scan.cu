@@ -437,10 +437,12 @@ __global__ void __launch_bounds__(256) finalize_topk_kernel(ScanArgs a)
     }
 }
 
-__global__ void test_factor_kernel(float *ftab, int nblk, int D, float eps0)
+// f(d) per step: ADSampling's (d/D)(1+eps0/sqrt d)^2 (Sec. 3.2), or 1 for
+// PDScanning (reject as soon as the partial distance exceeds r, Sec. 6.1).
+__global__ void test_factor_kernel(float *ftab, int nblk, int D, float eps0, int pd)
 {
     for (int b = threadIdx.x; b <= nblk; b += blockDim.x)
-        ftab[b] = (b == 0) ? 0.f : test_factor(b, D, eps0);
+        ftab[b] = (b == 0) ? 0.f : (pd ? 1.f : test_factor(b, D, eps0));
 }
 
 // Verification protocol (Sec. 6.2.5): every (query, indexed vector) pair,
@@ -562,9 +564,9 @@ int ads_scan_grid(const ScanArgs &a, int device)
     return (int)(g < 1 ? 1 : g);
 }
 
-cudaError_t launch_test_factors(float *ftab, int nblk, int D, float eps0, cudaStream_t s)
+cudaError_t launch_test_factors(float *ftab, int nblk, int D, float eps0, cudaStream_t s, int pd)
 {
-    test_factor_kernel<<<1, 256, 0, s>>>(ftab, nblk, D, eps0);
+    test_factor_kernel<<<1, 256, 0, s>>>(ftab, nblk, D, eps0, pd);
     return cudaGetLastError();
 }
 

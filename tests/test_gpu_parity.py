@@ -138,6 +138,23 @@ def test_fd_scan_matches_exact_ivf(c1):
         assert np.array_equal(dims[ok], (ncand * wl.D)[ok])
 
 
+def test_pdscanning_is_exact_ivf_with_fewer_dims(adsx_mod, c1):
+    """Sec. 6.1 PDScanning (IVF*): exact DCOs, so the results equal exact IVF;
+    the dims read match the sequential oracle's IVF* only in total order of
+    magnitude (r is shared differently), so they are bounded by FDScanning's
+    and by the first step's."""
+    wl, ix, Y, Cr, Qr = c1
+    for K, nprobe, dd in ((10, 10, 16), (100, 20, 32)):
+        ids, d2, dims = adsx_mod.search_pdscan(ix, wl.Q, K, nprobe, dd, return_dims=True)
+        eids, ed2 = oracle.ivf_exact(Y, Cr, wl.assign, Qr, K + 1, nprobe)
+        skip = _near_tie_queries(Cr, Qr, nprobe) | _kth_near_tie(ed2, K)
+        assert not _topk_mismatch(ids[~skip], d2[~skip], eids[~skip, :K], ed2[~skip, :K])
+        _, _, fdims, ncand = oracle.ivf_ads(Y, Cr, wl.assign, Qr, K, nprobe, math.inf, dd)
+        assert np.all(dims <= fdims) and np.all(dims >= ncand * dd)
+        _, _, odims = oracle.ivf_pd(Y, Cr, wl.assign, Qr, K, nprobe, dd)
+        assert 0.5 < dims.sum() / odims.sum() < 2.0
+
+
 def test_fd_equals_full_step_bit_identical(c1):
     wl, ix, *_ = c1
     a = ix.search(wl.Q, 10, 10, eps0=math.inf, delta_d=32)

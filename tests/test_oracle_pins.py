@@ -307,3 +307,20 @@ def test_recall_and_ratio_metrics():
     assert oracle.recall_at([[1, 2, 3]], [[3, 2, 9]], 3) == pytest.approx(2 / 3)
     assert oracle.recall_at([[1, -1, -1]], [[1, 2, 3]], 3) == pytest.approx(1 / 3)
     assert oracle.avg_dist_ratio([[4.0, 16.0]], [[1.0, 16.0]]) == pytest.approx(1.5)
+
+
+# ------------------------------------------------------------ Sec. 6.1 PDScanning
+def test_pdscanning_hand_cases_and_exactness(small_wl):
+    """PDScanning stops when the partial squared distance exceeds r^2
+    (strictly): o - q = (2, 1, 1, 0), delta_d 1, r2 = 4: S_1 = 4 (not > 4),
+    S_2 = 5 > 4 -> stopped with 2 dims; r2 = 6: S = 4, 5, 6, 6 -> positive."""
+    o, q = np.array([2.0, 1, 1, 0]), np.zeros(4)
+    assert oracle.dco_pd(o, q, 4.0, 1)[:2] == (oracle.REJECTED, 2)
+    assert oracle.dco_pd(o, q, 6.0, 1)[:2] == (oracle.POSITIVE, 4)
+    assert oracle.dco_pd(o, q, 5.5, 2)[:2] == (oracle.NEGATIVE_AT_D, 4)
+    wl, Y, Cr, Qr = small_wl
+    e_ids, e_d = oracle.ivf_exact(Y, Cr, wl.assign, Qr, 10, 6)
+    ids, d2, dims = oracle.ivf_pd(Y, Cr, wl.assign, Qr, 10, 6, 16)
+    assert np.array_equal(ids, e_ids) and np.array_equal(d2, e_d)   # exact DCO
+    _, _, full, ncand = oracle.ivf_ads(Y, Cr, wl.assign, Qr, 10, 6, math.inf, 16)
+    assert np.all(dims <= full) and np.any(dims < full)
