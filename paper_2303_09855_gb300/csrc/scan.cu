@@ -13,9 +13,9 @@
 //      coalesced runs per 16-dim block of the dim-blocked layout.
 //   2. The squared test S_d > r^2 f(d) (Sec. 3.2) rejects; a ballot compacts
 //      survivors into the warp's pending ring (cluster, member, blocks done,
-//      S).  Whenever 32 are pending they advance one delta_d step each (each
-//      lane its own candidate, whole 64-byte pieces) and are re-tested, so
-//      lanes stay busy after compaction.
+//      S).  Whenever 64 are pending they advance one delta_d step each (two
+//      per lane, whole 64-byte pieces, all loads issued first) and are
+//      re-tested, so lanes stay busy after compaction.
 //   3. Candidates reaching d = D with S_D <= r^2 are appended to the warp's
 //      candidate buffer (capacity C = 2 * next_pow2(K)).  When it fills, or
 //      first holds K entries, it is bitonic-sorted by (distance, id) and cut
@@ -37,7 +37,7 @@ namespace {
 
 constexpr int WARPS = 4;
 constexpr int THREADS = WARPS * 32;
-constexpr int RING = 64;                  // per-warp pending ring (power of 2)
+constexpr int RING = 128;                 // per-warp pending ring (power of 2)
 constexpr unsigned FULL = 0xffffffffu;
 
 __host__ __device__ inline int align4(int x) { return (x + 3) & ~3; }
@@ -266,6 +266,32 @@ __device__ __forceinline__ void process_pending(Warp<T> &w, int nb)
 #endif
 template <typename T> struct MinBlocks { static constexpr int value = ADSX_SCAN_MINBLOCKS; };
 
+// Advances 64 pending candidates (two per lane, cnt >= 64) by one step each,
+// with the loads of both issued before their arithmetic.
+template <typename T>
+__device__ __forceinline__ void process_pending2(Warp<T> &w)
+{
+    const ScanArgs &a = *w.a;
+    const int i0 = (w.head + w.lane) & (RING - 1), i1 = (w.head + 32 + w.lane) & (RING - 1);
+    const int o0 = w.po[i0], m0 = w.pm[i0], n0 = w.pn[i0], blk0 = w.pb[i0];
+    const int o1 = w.po[i1], m1 = w.pm[i1], n1 = w.pn[i1], blk1 = w.pb[i1];
+    float S0 = w.pS[i0], S1 = w.pS[i1];
+    __syncwarp();
+    w.head = (w.head + 64) & (RING - 1);
+    w.cnt -= 64;
+    const float r2 = current_r2(w);
+    int e0 = blk0 + a.db, e1 = blk1 + a.db;
+    if (e0 > a.nblk) e0 = a.nblk;
+    if (e1 > a.nblk) e1 = a.nblk;
+    const T *d = static_cast<const T *>(a.data);
+    const int64_t st0 = (int64_t)n0 * BLK, st1 = (int64_t)n1 * BLK;
+    accum_pair(d + (int64_t)o0 * a.Dp + blk0 * st0 + (int64_t)m0 * BLK, st0, blk0, e0 - blk0,
+               d + (int64_t)o1 * a.Dp + blk1 * st1 + (int64_t)m1 * BLK, st1, blk1, e1 - blk1, w.qv,
+               S0, S1);
+    after_step(w, true, S0, e0, o0, m0, n0, r2);
+    after_step(w, true, S1, e1, o1, m1, n1, r2);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(ScanArgs a)
 {
@@ -340,7 +366,7 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
                 float Sd = 0.f;
                 if (valid) Sd = accum_range(cb, n, m, 0, nb0, w.qv, 0.f);
                 after_step(w, valid, Sd, nb0, o, m, n, r2);
-                while (w.cnt >= 32) process_pending(w, 32);
+                while (w.cnt >= 64) process_pending2(w);
             }
         }
         while (w.cnt > 0) process_pending(w, w.cnt < 32 ? w.cnt : 32);
