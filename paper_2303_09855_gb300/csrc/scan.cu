@@ -257,12 +257,12 @@ __device__ __forceinline__ void process_pending(Warp<T> &w, int nb)
     after_step(w, valid, S, blk, o, m, n, r2);
 }
 
-// Resident blocks per SM the register budget is sized for: 6 (up to 85
-// registers, 24 warps per SM).  Measured on the SIFT-shaped 1M x 128
+// Resident blocks per SM the register budget is sized for: 4 (up to 128
+// registers, 16 warps per SM).  Measured on the SIFT-shaped 1M x 128
 // benchmark: bounds of 12 or more spill in the inner loop and halve the scan
-// rate; 6 (no spills) beats 10 (48 registers, 40 warps) by 10%.
+// rate; with two pending candidates per lane, 4 beats 6 and 10.
 #ifndef ADSX_SCAN_MINBLOCKS
-#define ADSX_SCAN_MINBLOCKS 6
+#define ADSX_SCAN_MINBLOCKS 4
 #endif
 template <typename T> struct MinBlocks { static constexpr int value = ADSX_SCAN_MINBLOCKS; };
 

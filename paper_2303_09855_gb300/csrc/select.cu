@@ -60,16 +60,34 @@ __global__ void __launch_bounds__(ST) select_nprobe_kernel(const float *__restri
                 if ((u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
             }
             __syncthreads();
-            if (tid == 0) {
-                unsigned rem = s_remaining, cum = 0;
-                for (int b = 0; b < 256; ++b) {
-                    unsigned h = hist[b];
-                    if (cum + h >= rem) {
-                        s_prefix = prefix | ((unsigned)b << shift);
-                        s_remaining = rem - cum;
-                        break;
+            if (warp == 0) {
+                // warp-wide search of the bin holding the rem-th key: each lane
+                // owns 8 consecutive bins, a shuffle scan gives the counts before
+                // them, and the one lane whose range crosses rem finds the bin.
+                const unsigned rem = s_remaining;
+                unsigned h[8], own = 0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    h[j] = hist[lane * 8 + j];
+                    own += h[j];
+                }
+                unsigned incl = own;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                unsigned cum = incl - own;
+                if (cum < rem && incl >= rem) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (cum + h[j] >= rem) {
+                            s_prefix = prefix | ((unsigned)(lane * 8 + j) << shift);
+                            s_remaining = rem - cum;
+                            break;
+                        }
+                        cum += h[j];
                     }
-                    cum += h;
                 }
             }
             mask |= 255u << shift;
