@@ -68,7 +68,8 @@ typedef enum { ADSX_F32 = 0, ADSX_BF16 = 1, ADSX_F16 = 2 } adsx_dtype;
  * adsx_build_index -- index phase (Sec. 6.1 "Implementation", Sec. 4, Sec. 5.2).
  *   X          host, N x D float32, raw data vectors; N in [1, 2^31).
  *   P          host, D x D float32 row-major, the random orthogonal matrix
- *              (y = P x).  Orthogonality is checked: max |P^T P - I| <= 1e-4.
+ *              (y = P x).  Orthogonality is checked on the device:
+ *              max |P P^T - I| <= 1e-4.
  *   centroids  host, nlist x D float32, IVF centroids in the raw space.
  *   assign     host, N int32, cluster of each vector, each in [0, nlist).
  *   storage    ADSX_F32, ADSX_BF16 or ADSX_F16: the type of the dim-blocked

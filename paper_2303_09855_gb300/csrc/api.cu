@@ -211,23 +211,6 @@ int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
     if (is_device_ptr(X) || is_device_ptr(P) || is_device_ptr(centroids) || is_device_ptr(assign))
         return fail(ADSX_EINVAL, "adsx_build_index takes host pointers");
 
-    // P must be orthogonal (Sec. 3.1): max |P^T P - I| <= 1e-4.
-    {
-        std::vector<double> G((size_t)D * D, 0.0);
-        for (int32_t k = 0; k < D; ++k) {
-            const float *row = P + (size_t)k * D;
-            for (int32_t i = 0; i < D; ++i) {
-                const double pi = row[i];
-                double *g = &G[(size_t)i * D];
-                for (int32_t j = 0; j < D; ++j) g[j] += pi * (double)row[j];
-            }
-        }
-        double worst = 0.0;
-        for (int32_t i = 0; i < D; ++i)
-            for (int32_t j = 0; j < D; ++j)
-                worst = std::max(worst, fabs(G[(size_t)i * D + j] - (i == j ? 1.0 : 0.0)));
-        if (!(worst <= 1e-4)) return fail(ADSX_EINVAL, "P is not orthogonal (max|P^T P - I| = %g)", worst);
-    }
     // Inverted file (Sec. 2.2.2): stable counting sort by cluster.
     std::vector<int64_t> off((size_t)nlist + 1, 0), pos((size_t)N);
     for (int64_t n = 0; n < N; ++n) {
@@ -300,6 +283,32 @@ int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
         for (int32_t i = 0; i < D; ++i) memcpy(&Pp[(size_t)i * Dp], P + (size_t)i * D, sizeof(float) * D);
         BCK(cudaMemcpyAsync(ix->P, Pp.data(), sizeof(float) * Dp * Dp, cudaMemcpyHostToDevice, s), "copy P");
         BCK(cudaStreamSynchronize(s), "sync");
+    }
+    // P must be orthogonal (Sec. 3.1): max |P P^T - I| <= 1e-4, checked with
+    // the compensated rotation kernel on the device (P P^T = rotating P's rows).
+    {
+        float *pd = nullptr, *gd = nullptr;
+        BCK(cudaMalloc(&pd, sizeof(float) * (size_t)D * D), "alloc P check");
+        e = cudaMalloc(&gd, sizeof(float) * (size_t)D * Dp);
+        if (e != cudaSuccess) {
+            cudaFree(pd);
+            return cleanup(cuda_fail(e, "alloc P check"));
+        }
+        std::vector<float> G((size_t)D * Dp);
+        e = cudaMemcpyAsync(pd, P, sizeof(float) * (size_t)D * D, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = adsx::launch_rotate(pd, D, D, ix->P, Dp, gd, Dp, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(G.data(), gd, sizeof(float) * (size_t)D * Dp, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(pd);
+        cudaFree(gd);
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "P check"));
+        double worst = 0.0;
+        for (int32_t i = 0; i < D; ++i)
+            for (int32_t j = 0; j < D; ++j)
+                worst = std::max(worst, fabs((double)G[(size_t)i * Dp + j] - (i == j ? 1.0 : 0.0)));
+        if (!(worst <= 1e-4))
+            return cleanup(fail(ADSX_EINVAL, "P is not orthogonal (max|P P^T - I| = %g)", worst));
     }
     BCK(cudaMemcpyAsync(ix->ids, ids.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, s), "copy ids");
     BCK(cudaMemcpyAsync(ix->off, off.data(), sizeof(int64_t) * (nlist + 1), cudaMemcpyHostToDevice, s), "copy off");
