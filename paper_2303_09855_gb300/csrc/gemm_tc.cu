@@ -25,7 +25,9 @@ namespace {
 constexpr int TM = 128, TN = 128, BK = 32;
 constexpr int SLAB = 4096;                     // bytes of one K = 8 slab of 128 rows
 constexpr int OPER = (BK / 8) * SLAB;          // bytes of one operand (hi or lo) per k-step
-constexpr int SMEM_BYTES = 4 * OPER;           // A_hi, A_lo, B_hi, B_lo
+constexpr int OPER_BYTES = 4 * OPER;           // A_hi, A_lo, B_hi, B_lo
+constexpr int STAGE_BYTES = 4 * 32 * (TN + 4) * 4;  // epilogue: 4 warps x 32 rows x 132 floats
+constexpr int SMEM_BYTES = OPER_BYTES > STAGE_BYTES ? OPER_BYTES : STAGE_BYTES;
 constexpr uint32_t TMEM_COLS = 128;
 constexpr unsigned WAIT_LIMIT = 1u << 22;
 constexpr unsigned ERR_MMA_TIMEOUT = 8u;
@@ -193,9 +195,14 @@ __global__ void __launch_bounds__(128, 1)
         mbar_wait(bar, phase ^ 1u);            // bounded: let in-flight MMAs drain
     } else {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // Each warp reads its 32 accumulator rows (lane = row) and stages the
+        // finished 32 x 128 distances in the (now idle) operand shared memory,
+        // rows 132 floats apart (float4 writes of 8 lanes hit distinct banks),
+        // then writes every row as one coalesced 512-byte run.
         const int64_t row = m0 + warp * 32 + lane;
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         const float rn = (row < M) ? an[row] : 0.f;
+        float *stage = reinterpret_cast<float *>(sm) + warp * 32 * (TN + 4);
 #pragma unroll 1
         for (int c0 = 0; c0 < TN; c0 += 16) {
             uint32_t v[16];
@@ -207,15 +214,34 @@ __global__ void __launch_bounds__(128, 1)
                   "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
                 : "r"(trow + (uint32_t)c0));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < M) {
+            float o[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = n0 + c0 + j;
-                    if (col < Nout) {
-                        const float acc = __uint_as_float(v[j]);
-                        C[row * ldc + col] = fmaxf(rn + bn[col] - 2.f * acc, 0.f);
-                    }
-                }
+            for (int j = 0; j < 16; ++j) {
+                const int col = n0 + c0 + j;
+                const float cn = (col < Nout) ? bn[col] : 0.f;
+                o[j] = fmaxf(rn + cn - 2.f * __uint_as_float(v[j]), 0.f);
+            }
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+                *reinterpret_cast<float4 *>(stage + lane * (TN + 4) + c0 + j) =
+                    make_float4(o[j], o[j + 1], o[j + 2], o[j + 3]);
+        }
+        __syncwarp();
+        const int col = n0 + lane * 4;
+        const bool vec_ok = (ldc % 4 == 0) && (col + 4 <= Nout);
+#pragma unroll 4
+        for (int r = 0; r < 32; ++r) {
+            const int64_t grow = m0 + warp * 32 + r;
+            if (grow >= M) break;
+            const float4 x = *reinterpret_cast<const float4 *>(stage + r * (TN + 4) + lane * 4);
+            float *dst = C + grow * ldc + col;
+            if (vec_ok) {
+                *reinterpret_cast<float4 *>(dst) = x;
+            } else {
+                if (col < Nout) dst[0] = x.x;
+                if (col + 1 < Nout) dst[1] = x.y;
+                if (col + 2 < Nout) dst[2] = x.z;
+                if (col + 3 < Nout) dst[3] = x.w;
             }
         }
     }
