@@ -55,9 +55,19 @@ __global__ void __launch_bounds__(ST) select_nprobe_kernel(const float *__restri
             hist[tid] = 0;
             __syncthreads();
             const unsigned prefix = s_prefix;
-            for (int i = tid; i < nlist; i += ST) {
-                unsigned u = key[i];
-                if ((u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
+            // Keys that still match the prefix vote for their digit; lanes of a
+            // warp with the same digit are merged (match.any) into one atomic,
+            // since most keys share the high digits of the float's exponent.
+            for (int i0 = warp * 32; i0 < nlist; i0 += ST) {
+                const int i = i0 + lane;
+                unsigned bin = 256u;                    // no vote
+                if (i < nlist) {
+                    const unsigned u = key[i];
+                    if ((u & mask) == prefix) bin = (u >> shift) & 255u;
+                }
+                const unsigned peers = __match_any_sync(0xffffffffu, bin);
+                if (bin < 256u && lane == __ffs(peers) - 1)
+                    atomicAdd(&hist[bin], (unsigned)__popc(peers));
             }
             __syncthreads();
             if (warp == 0) {
