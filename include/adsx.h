@@ -63,6 +63,8 @@ typedef enum { ADSX_F32 = 0, ADSX_BF16 = 1, ADSX_F16 = 2 } adsx_dtype;
 #define ADSX_MAX_K 1024       /* neighbours per query                        */
 #define ADSX_MAX_NPROBE 1024  /* probed clusters per query                   */
 #define ADSX_MAX_NLIST 16384  /* clusters                                    */
+#define ADSX_MAX_CLUSTER ((1 << 27) - 1)  /* members of one cluster (16 x this
+                                           indexes a 32-bit block stride)    */
 
 /*
  * adsx_build_index -- index phase (Sec. 6.1 "Implementation", Sec. 4, Sec. 5.2).
@@ -82,8 +84,9 @@ typedef enum { ADSX_F32 = 0, ADSX_BF16 = 1, ADSX_F16 = 2 } adsx_dtype;
  *   out        receives an opaque handle owning all of the index's device
  *              memory (rotated vectors in the dim-blocked per-cluster layout,
  *              ids, CSR offsets, rotated centroids, P).
- * Errors: ADSX_EINVAL (bad sizes, non-orthogonal P, assign out of range),
- * ADSX_ENOMEM, ADSX_ECUDA.  On error *out is NULL and nothing leaks.
+ * Errors: ADSX_EINVAL (bad sizes, non-orthogonal P, assign out of range, a
+ * cluster above ADSX_MAX_CLUSTER members), ADSX_ENOMEM, ADSX_ECUDA.  On
+ * error *out is NULL and nothing leaks.
  */
 int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
                      const float *centroids, int32_t nlist,

@@ -6,8 +6,9 @@
 //   the 16 dims [16b, 16b+16) of all n_c members are contiguous, member after
 //   member.  Element (cluster c, member m, dim j) sits at
 //       data[off[c]*Dp + (j/16)*n_c*16 + m*16 + (j%16)]
-//   so one delta_d step of 32 consecutive members is a few fully coalesced
-//   2 KB runs (FP32), and a single member's step is whole 64-byte pieces.
+//   so one block of 8 (FP32) or 16 (16-bit) consecutive members is a single
+//   contiguous 512-byte run, and a single member's block is one 64- or
+//   32-byte piece.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -207,90 +208,6 @@ __device__ __forceinline__ float accum_range(const __half *base, int64_t n, int6
                                              int b1, const float *qv, float S)
 {
     return accum_range_h(base, n, m, b0, b1, qv, S);
-}
-
-// ---- two candidates advanced together: every load of a step is issued
-// before any arithmetic, so a lane has twice the bytes in flight; each
-// candidate's sum keeps the dimension order of accum_range.
-struct Blk32 { float4 v[4]; };
-struct Blk16 { uint4 v[2]; };
-
-__device__ __forceinline__ Blk32 load_blk(const float *x)
-{
-    Blk32 b;
-    const float4 *p = reinterpret_cast<const float4 *>(x);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) b.v[i] = __ldg(p + i);
-    return b;
-}
-template <typename H>
-__device__ __forceinline__ Blk16 load_blk(const H *x)
-{
-    Blk16 b;
-    const uint4 *p = reinterpret_cast<const uint4 *>(x);
-    b.v[0] = __ldg(p);
-    b.v[1] = __ldg(p + 1);
-    return b;
-}
-__device__ __forceinline__ float add_blk(const Blk32 &b, const float *q, float S)
-{
-    const float4 *q4 = reinterpret_cast<const float4 *>(q);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float4 qq = q4[i];
-        float t;
-        t = b.v[i].x - qq.x; S = fmaf(t, t, S);
-        t = b.v[i].y - qq.y; S = fmaf(t, t, S);
-        t = b.v[i].z - qq.z; S = fmaf(t, t, S);
-        t = b.v[i].w - qq.w; S = fmaf(t, t, S);
-    }
-    return S;
-}
-template <typename H>
-__device__ __forceinline__ float add_blk(const Blk16 &b, const float *q, float S, H)
-{
-    S = accum_8h<H>(b.v[0], q, S);
-    return accum_8h<H>(b.v[1], q + 8, S);
-}
-
-template <typename T> struct BlkOf { typedef Blk16 type; };
-template <> struct BlkOf<float> { typedef Blk32 type; };
-
-__device__ __forceinline__ float add_any(const Blk32 &b, const float *q, float S, float)
-{
-    return add_blk(b, q, S);
-}
-template <typename H>
-__device__ __forceinline__ float add_any(const Blk16 &b, const float *q, float S, H h)
-{
-    return add_blk(b, q, S, h);
-}
-
-// Blocks [b0, b0+k0) of candidate 0 and [b1, b1+k1) of candidate 1 (block j
-// of a candidate at p + j*stride; query slice qv + b*16).
-template <typename T>
-__device__ __forceinline__ void accum_pair(const T *p0, int64_t st0, int b0, int k0, const T *p1,
-                                           int64_t st1, int b1, int k1,
-                                           const float *__restrict__ qv, float &S0, float &S1)
-{
-    typedef typename BlkOf<T>::type B;
-    while (k0 >= 2 && k1 >= 2) {
-        const B x0 = load_blk(p0), x1 = load_blk(p0 + st0);
-        const B y0 = load_blk(p1), y1 = load_blk(p1 + st1);
-        S0 = add_any(x0, qv + b0 * BLK, S0, T());
-        S0 = add_any(x1, qv + (b0 + 1) * BLK, S0, T());
-        S1 = add_any(y0, qv + b1 * BLK, S1, T());
-        S1 = add_any(y1, qv + (b1 + 1) * BLK, S1, T());
-        p0 += 2 * st0; p1 += 2 * st1; b0 += 2; b1 += 2; k0 -= 2; k1 -= 2;
-    }
-    while (k0 >= 1 && k1 >= 1) {
-        const B x0 = load_blk(p0), y0 = load_blk(p1);
-        S0 = add_any(x0, qv + b0 * BLK, S0, T());
-        S1 = add_any(y0, qv + b1 * BLK, S1, T());
-        p0 += st0; p1 += st1; ++b0; ++b1; --k0; --k1;
-    }
-    for (; k0 > 0; --k0, p0 += st0, ++b0) S0 = add_any(load_blk(p0), qv + b0 * BLK, S0, T());
-    for (; k1 > 0; --k1, p1 += st1, ++b1) S1 = add_any(load_blk(p1), qv + b1 * BLK, S1, T());
 }
 
 // Unit roundoff of the storage type (round to nearest): |x~ - x| <= u |x|.

@@ -230,6 +230,8 @@ int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
     }
     std::vector<int32_t> tile_off((size_t)nlist + 1, 0);
     for (int32_t c = 0; c < nlist; ++c) {
+        if (off[(size_t)c + 1] - off[(size_t)c] > ADSX_MAX_CLUSTER)
+            return fail(ADSX_EINVAL, "cluster %d has more than %d members", c, ADSX_MAX_CLUSTER);
         int64_t t = tile_off[(size_t)c] + (off[(size_t)c + 1] - off[(size_t)c] + 31) / 32;
         if (t >= (int64_t)1 << 31) return fail(ADSX_EINVAL, "too many tiles");
         tile_off[(size_t)c + 1] = (int32_t)t;

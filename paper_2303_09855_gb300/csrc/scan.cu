@@ -8,14 +8,20 @@
 // too few queries to fill the GPU).  Each warp claims items from a global
 // counter and owns, in shared memory, the item's q', a pending ring and a
 // candidate buffer; nothing is shared between warps, so no locks.
-//   1. Members are visited cluster by cluster in probe order, 32 per tile,
-//      one member per lane.  The first delta_d dims of a tile are 2 KB
-//      coalesced runs per 16-dim block of the dim-blocked layout.
-//   2. The squared test S_d > r^2 f(d) (Sec. 3.2) rejects; a ballot compacts
-//      survivors into the warp's pending ring (cluster, member, blocks done,
-//      S).  Whenever 64 are pending they advance one delta_d step each (two
-//      per lane, whole 64-byte pieces, all loads issued first) and are
-//      re-tested, so lanes stay busy after compaction.
+//   1. Members are visited cluster by cluster in probe order, 32 per tile.
+//      Each 16-dim block of a member is split over NL lanes (4 for FP32, 2
+//      for 16-bit storage; 16 bytes each), so one load instruction of the
+//      warp reads whole blocks of 32/NL members -- a contiguous 512-byte run
+//      of the dim-blocked layout -- and a shuffle transpose gives every lane
+//      the complete partial distance of one member.
+//   2. The squared test S_d > r^2 f(d) (Sec. 3.2) rejects.  While at least
+//      DENSE_MIN members of a tile are live, the tile advances as a whole
+//      (all live members sit at the same block: contiguous loads, broadcast
+//      query reads); then a ballot compacts the survivors into the warp's
+//      pending ring (next-block offset, block stride, blocks done, CSR row,
+//      S).  Whenever 32 are pending they advance one delta_d step each (NL
+//      lanes per candidate again, all loads issued before the arithmetic)
+//      and are re-tested, so lanes stay busy after compaction.
 //   3. Candidates reaching d = D with S_D <= r^2 are appended to the warp's
 //      candidate buffer (capacity C = 2 * next_pow2(K)).  When it fills, or
 //      first holds K entries, it is bitonic-sorted by (distance, id) and cut
@@ -38,23 +44,29 @@ namespace {
 constexpr int WARPS = 4;
 constexpr int THREADS = WARPS * 32;
 constexpr int RING = 128;                 // per-warp pending ring (power of 2)
+// Live members that keep a tile stepping as a whole (measured on the
+// SIFT-shaped benchmark: 16-20 best; 8 and 32 -- never dense -- about 8% slower).
+#ifndef ADSX_DENSE_MIN
+#define ADSX_DENSE_MIN 20
+#endif
+constexpr int DENSE_MIN = ADSX_DENSE_MIN;
 constexpr unsigned FULL = 0xffffffffu;
 
 __host__ __device__ inline int align4(int x) { return (x + 3) & ~3; }
 
 // Per-warp shared-memory region, in 4-byte words.
 struct WarpCarve {
-    int qv, ed, ei, po, pm, pn, pb, pS, words;
+    int qv, ed, ei, pof, pst, pb, pp, pS, words;
     __host__ __device__ WarpCarve(int Dp, int C)
     {
         int o = 0;
         qv = o; o = align4(o + Dp);
         ed = o; o = align4(o + C);
         ei = o; o = align4(o + C);
-        po = o; o += RING;
-        pm = o; o += RING;
-        pn = o; o += RING;
+        pof = o; o += 2 * RING;             // 8-byte aligned (o is a multiple of 4)
+        pst = o; o += RING;
         pb = o; o += RING;
+        pp = o; o += RING;
         pS = o; o += RING;
         words = o;
     }
@@ -71,7 +83,10 @@ struct Warp {
     float *qv;
     float *ed;
     int *ei;
-    int *po, *pm, *pn, *pb;
+    // pending ring: element offset of the candidate's next block, its block
+    // stride (16 * cluster size), blocks done, CSR row, partial distance
+    long long *pof;
+    int *pst, *pb, *pp;
     float *pS;
     const float *ftab;         // test factors (shared memory)
     int lane;
@@ -165,11 +180,31 @@ __device__ __forceinline__ float recheck_exact(const Warp<T> &w, bool need, int 
     return S;
 }
 
-// After a candidate has `blk` blocks accumulated in S: the exact compare at
-// d = D (Case 3), else the hypothesis test (Case 1 reject / Case 2 re-queue).
+// Appends the lanes with `surv` to the pending ring (lane order).
 template <typename T>
-__device__ __forceinline__ void after_step(Warp<T> &w, bool valid, float S, int blk, int o, int m,
-                                           int n, float r2)
+__device__ __forceinline__ void enqueue(Warp<T> &w, bool surv, float S, int blk, int pos,
+                                        long long off, int st)
+{
+    const unsigned sm = __ballot_sync(FULL, surv);
+    if (surv) {
+        const int idx = (w.head + w.cnt + __popc(sm & ((1u << w.lane) - 1u))) & (RING - 1);
+        w.pof[idx] = off;
+        w.pst[idx] = st;
+        w.pb[idx] = blk;
+        w.pp[idx] = pos;
+        w.pS[idx] = S;
+    }
+    w.cnt += __popc(sm);
+}
+
+// After a candidate has `blk` blocks accumulated in S: the exact compare at
+// d = D (Case 3), else the hypothesis test (Case 1 reject / Case 2 continue).
+// `pos` is the candidate's CSR row, `off` the element offset of its block
+// `blk` and `st` its block stride.  Returns whether the candidate continues;
+// with `push` it is also queued.
+template <typename T>
+__device__ __forceinline__ bool after_step(Warp<T> &w, bool valid, float S, int blk, int pos,
+                                           long long off, int st, float r2, bool push)
 {
     const ScanArgs &a = *w.a;
     const bool fin = valid && blk >= a.nblk;
@@ -183,16 +218,7 @@ __device__ __forceinline__ void after_step(Warp<T> &w, bool valid, float S, int 
         }
     }
     if (fin) w.dims += (unsigned)a.D;
-    const unsigned sm = __ballot_sync(FULL, surv);
-    if (surv) {
-        const int idx = (w.head + w.cnt + __popc(sm & ((1u << w.lane) - 1u))) & (RING - 1);
-        w.po[idx] = o;
-        w.pm[idx] = m;
-        w.pn[idx] = n;
-        w.pb[idx] = blk;
-        w.pS[idx] = S;
-    }
-    w.cnt += __popc(sm);
+    if (push) enqueue(w, surv, S, blk, pos, off, st);
     bool cand = fin;
     if constexpr (Roundoff<T>::u > 0.f) {
         // S is a sum over rounded coordinates x~ with |x~ - x| <= u|x|, so
@@ -203,11 +229,11 @@ __device__ __forceinline__ void after_step(Warp<T> &w, bool valid, float S, int 
         if (fin) {
             need = !(r2 < INFINITY);
             if (!need) {
-                const float bound = (sqrtf(r2) + Roundoff<T>::u * a.norms[o + m]) * 1.0001f;
+                const float bound = (sqrtf(r2) + Roundoff<T>::u * a.norms[pos]) * 1.0001f;
                 need = sqrtf(S) <= bound;
             }
         }
-        S = recheck_exact(w, need, o + m, S);
+        S = recheck_exact(w, need, pos, S);
         cand = need;
     }
     // Case 3 positives into the candidate buffer.
@@ -219,78 +245,265 @@ __device__ __forceinline__ void after_step(Warp<T> &w, bool valid, float S, int 
         if (want) {
             const int k = w.count + __popc(wm & ((1u << w.lane) - 1u));
             w.ed[k] = S;
-            w.ei[k] = a.ids[o + m];
+            w.ei[k] = a.ids[pos];
         }
         w.count += nw;
         __syncwarp();
         if (w.count >= w.K && w.r2 == INFINITY) compact(w);
     }
     __syncwarp();
+    return surv;
 }
 
-// Advances up to 32 pending candidates by one delta_d step each.
+// ---- several lanes per candidate.  One 16-dim block of a candidate is 64
+// bytes (FP32) or 32 bytes (16-bit); NL = 4 or 2 lanes split it into 16-byte
+// pieces.  The warp is 32/NL groups of NL lanes, and lane l (group g = l / NL,
+// piece j = l % NL) works on the NL candidates g + (32/NL) k, k < NL, of a set
+// of 32.  One load instruction of the warp thus reads whole blocks of 32/NL
+// candidates -- a single contiguous 512-byte run when they are consecutive
+// members -- instead of 16-byte slices of 32 candidates spread over 16 or more
+// cache lines.  Each lane keeps a partial sum per candidate (its piece, two
+// FP32 chains: even and odd dims); group_sum then combines the NL pieces so
+// that lane l holds the complete sum of candidate own_slot(l).
+template <typename T> struct Split {           // 16-bit: 2 lanes x 8 values
+    static constexpr int NL = 2;
+    typedef uint4 V;
+};
+template <> struct Split<float> {              // FP32: 4 lanes x 4 values
+    static constexpr int NL = 4;
+    typedef float4 V;
+};
+
+__device__ __forceinline__ float4 ld_piece(const float *p)
+{
+    return __ldg(reinterpret_cast<const float4 *>(p));
+}
+template <typename H>
+__device__ __forceinline__ uint4 ld_piece(const H *p)
+{
+    return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+__device__ __forceinline__ void zero_piece(float4 &v) { v = make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ void zero_piece(uint4 &v) { v = make_uint4(0u, 0u, 0u, 0u); }
+
+// The query values matching a lane's piece (4 or 8 floats, shared memory).
+template <int NL> struct QPiece;
+template <> struct QPiece<4> { float4 a; };
+template <> struct QPiece<2> { float4 a, b; };
+template <int NL>
+__device__ __forceinline__ QPiece<NL> ld_qpiece(const float *q)
+{
+    QPiece<NL> r;
+    r.a = *reinterpret_cast<const float4 *>(q);
+    if constexpr (NL == 2) r.b = *reinterpret_cast<const float4 *>(q + 4);
+    return r;
+}
+
+// S + (x - q)^2 over the piece, even dims into S.x and odd dims into S.y.
+// (The packed f32x2 subtract/FMA of sm_100+ gives the same values but
+// measured about 12% slower in this loop, so the chains stay scalar.)
+__device__ __forceinline__ float2 add_piece(float4 x, const QPiece<4> &q, float2 S, float)
+{
+    float t;
+    t = x.x - q.a.x; S.x = fmaf(t, t, S.x);
+    t = x.y - q.a.y; S.y = fmaf(t, t, S.y);
+    t = x.z - q.a.z; S.x = fmaf(t, t, S.x);
+    t = x.w - q.a.w; S.y = fmaf(t, t, S.y);
+    return S;
+}
+template <typename H>
+__device__ __forceinline__ float2 add_piece(uint4 x, const QPiece<2> &q, float2 S, H h)
+{
+    float v0, v1, t;
+    unpack2(x.x, v0, v1, h);
+    t = v0 - q.a.x; S.x = fmaf(t, t, S.x);
+    t = v1 - q.a.y; S.y = fmaf(t, t, S.y);
+    unpack2(x.y, v0, v1, h);
+    t = v0 - q.a.z; S.x = fmaf(t, t, S.x);
+    t = v1 - q.a.w; S.y = fmaf(t, t, S.y);
+    unpack2(x.z, v0, v1, h);
+    t = v0 - q.b.x; S.x = fmaf(t, t, S.x);
+    t = v1 - q.b.y; S.y = fmaf(t, t, S.y);
+    unpack2(x.w, v0, v1, h);
+    t = v0 - q.b.z; S.x = fmaf(t, t, S.x);
+    t = v1 - q.b.w; S.y = fmaf(t, t, S.y);
+    return S;
+}
+
+// The candidate (of the set of 32) whose complete sum lane l receives from
+// group_sum, and the lane that receives candidate g + (32/NL) k.
+template <int NL>
+__device__ __forceinline__ int own_slot(int lane)
+{
+    if constexpr (NL == 4) return (lane >> 2) + 8 * (2 * (lane & 1) + ((lane >> 1) & 1));
+    else return (lane >> 1) + 16 * (lane & 1);
+}
+template <int NL>
+__device__ __forceinline__ int owner_lane(int g, int k)
+{
+    if constexpr (NL == 4) return 4 * g + (k >> 1) + 2 * (k & 1);
+    else return 2 * g + k;
+}
+
+// Transpose-and-add over the NL lanes of a group: lane l enters with the
+// partial sums p[k] of its piece for candidates g + (32/NL) k and leaves with
+// the sum over all pieces of candidate own_slot(l).  With NL = 4, lanes l, l^1
+// split the four candidates into {0, 1} and {2, 3}, then lanes l, l^2 split
+// each pair; with NL = 2, lanes l, l^1 split {0, 1}.
+template <int NL>
+__device__ __forceinline__ float group_sum(const float2 (&pp)[NL], int lane)
+{
+    float p[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) p[k] = pp[k].x + pp[k].y;
+    const bool hi1 = lane & 1;
+    if constexpr (NL == 4) {
+        const bool hi2 = lane & 2;
+        const float u0 = (hi1 ? p[2] : p[0]) + __shfl_xor_sync(FULL, hi1 ? p[0] : p[2], 1);
+        const float u1 = (hi1 ? p[3] : p[1]) + __shfl_xor_sync(FULL, hi1 ? p[1] : p[3], 1);
+        return (hi2 ? u1 : u0) + __shfl_xor_sync(FULL, hi2 ? u0 : u1, 2);
+    } else {
+        return (hi1 ? p[1] : p[0]) + __shfl_xor_sync(FULL, hi1 ? p[0] : p[1], 1);
+    }
+}
+
+// One step of a dense tile: blocks [b0, b1) of the live members among
+// m0 .. m0+31 of a cluster laid out from `cb` (block stride n*16); member
+// m0 + g + (32/NL) k is loaded iff bit owner_lane(g, k) of `live` is set.
+// Returns, on lane l, the step's partial distance of member m0 + own_slot(l)
+// (meaningless if that member is dead: its loads are skipped, its sum unused).
+template <typename T>
+__device__ __forceinline__ float tile_step(const T *cb, int64_t stride, int m0, int b0, int b1,
+                                           unsigned live, const float *qv, int lane)
+{
+    constexpr int NL = Split<T>::NL, NG = 32 / NL, PW = BLK / NL;
+    typedef typename Split<T>::V V;
+    const int g = lane / NL, jo = (lane % NL) * PW;
+    const T *x = cb + (int64_t)b0 * stride + (int64_t)(m0 + g) * BLK + jo;
+    bool ok[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) ok[k] = (live >> owner_lane<NL>(g, k)) & 1u;
+    float2 p[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) p[k] = make_float2(0.f, 0.f);
+    int b = b0;
+    for (; b + 2 <= b1; b += 2, x += 2 * stride) {
+        V v[2 * NL];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            zero_piece(v[k]);
+            zero_piece(v[NL + k]);
+            if (ok[k]) {
+                v[k] = ld_piece(x + k * NG * BLK);
+                v[NL + k] = ld_piece(x + stride + k * NG * BLK);
+            }
+        }
+        const QPiece<NL> q0 = ld_qpiece<NL>(qv + b * BLK + jo);
+        const QPiece<NL> q1 = ld_qpiece<NL>(qv + (b + 1) * BLK + jo);
+#pragma unroll
+        for (int k = 0; k < NL; ++k)
+            p[k] = add_piece(v[NL + k], q1, add_piece(v[k], q0, p[k], T()), T());
+    }
+    if (b < b1) {
+        V v[NL];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            zero_piece(v[k]);
+            if (ok[k]) v[k] = ld_piece(x + k * NG * BLK);
+        }
+        const QPiece<NL> q0 = ld_qpiece<NL>(qv + b * BLK + jo);
+#pragma unroll
+        for (int k = 0; k < NL; ++k) p[k] = add_piece(v[k], q0, p[k], T());
+    }
+    return group_sum<NL>(p, lane);
+}
+
+// Advances the first nb (<= 32) pending candidates by one delta_d step each,
+// NL lanes per candidate, then tests them (after_step) one per lane.
 template <typename T>
 __device__ __forceinline__ void process_pending(Warp<T> &w, int nb)
 {
+    constexpr int NL = Split<T>::NL, NG = 32 / NL, PW = BLK / NL;
+    typedef typename Split<T>::V V;
     const ScanArgs &a = *w.a;
-    const bool valid = w.lane < nb;
-    int o = 0, m = 0, n = 0, blk = 0;
+    const int g = w.lane / NL, jo = (w.lane % NL) * PW, mine = own_slot<NL>(w.lane);
+    const T *data = static_cast<const T *>(a.data) + jo;
+    const T *x[NL];
+    int st[NL], bk[NL], kb[NL];
+    long long off_own = 0;
+    int st_own = 0, e_own = 0, kmax = 0;
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+        const int t = g + NG * k;
+        long long off = 0;
+        int s = 0, blk = 0, e = 0;
+        if (t < nb) {
+            const int idx = (w.head + t) & (RING - 1);
+            off = w.pof[idx];
+            s = w.pst[idx];
+            blk = w.pb[idx];
+            e = blk + a.db < a.nblk ? blk + a.db : a.nblk;
+        }
+        x[k] = data + off;
+        st[k] = s;
+        bk[k] = blk;
+        kb[k] = e - blk;
+        kmax = kb[k] > kmax ? kb[k] : kmax;
+        if (t == mine) {
+            off_own = off + (long long)(e - blk) * s;
+            st_own = s;
+            e_own = e;
+        }
+    }
+    const bool valid = mine < nb;
     float S = 0.f;
+    int pos = 0;
     if (valid) {
-        const int idx = (w.head + w.lane) & (RING - 1);
-        o = w.po[idx];
-        m = w.pm[idx];
-        n = w.pn[idx];
-        blk = w.pb[idx];
+        const int idx = (w.head + mine) & (RING - 1);
         S = w.pS[idx];
+        pos = w.pp[idx];
     }
     __syncwarp();
     w.head = (w.head + nb) & (RING - 1);
     w.cnt -= nb;
     const float r2 = current_r2(w);
-    if (valid) {
-        int e = blk + a.db;
-        if (e > a.nblk) e = a.nblk;
-        S = accum_range(static_cast<const T *>(a.data) + (int64_t)o * a.Dp, n, m, blk, e, w.qv, S);
-        blk = e;
+    float2 p[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) p[k] = make_float2(0.f, 0.f);
+    for (int s = 0; s < kmax; s += 2) {
+        V v[2 * NL];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            zero_piece(v[k]);
+            zero_piece(v[NL + k]);
+            if (s < kb[k]) v[k] = ld_piece(x[k]);
+            if (s + 1 < kb[k]) v[NL + k] = ld_piece(x[k] + st[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            if (s < kb[k])
+                p[k] = add_piece(v[k], ld_qpiece<NL>(w.qv + (bk[k] + s) * BLK + jo), p[k], T());
+            if (s + 1 < kb[k])
+                p[k] = add_piece(v[NL + k], ld_qpiece<NL>(w.qv + (bk[k] + s + 1) * BLK + jo), p[k],
+                                 T());
+            x[k] += 2 * st[k];
+        }
     }
-    after_step(w, valid, S, blk, o, m, n, r2);
+    S += group_sum<NL>(p, w.lane);
+    after_step(w, valid, S, e_own, pos, off_own, st_own, r2, true);
 }
 
-// Resident blocks per SM the register budget is sized for: 4 (up to 128
-// registers, 16 warps per SM).  Measured on the SIFT-shaped 1M x 128
-// benchmark: bounds of 12 or more spill in the inner loop and halve the scan
-// rate; with two pending candidates per lane, 4 beats 6 and 10.
+// Resident blocks per SM the register budget is sized for (FP32 storage;
+// 16-bit storage).  Measured on the SIFT-shaped 1M x 128 benchmark (FP32) and
+// the GIST-shaped 1M x 960 one (16-bit): 5 beats 4 and 6 for both.
 #ifndef ADSX_SCAN_MINBLOCKS
-#define ADSX_SCAN_MINBLOCKS 4
+#define ADSX_SCAN_MINBLOCKS 5
 #endif
-template <typename T> struct MinBlocks { static constexpr int value = ADSX_SCAN_MINBLOCKS; };
-
-// Advances 64 pending candidates (two per lane, cnt >= 64) by one step each,
-// with the loads of both issued before their arithmetic.
-template <typename T>
-__device__ __forceinline__ void process_pending2(Warp<T> &w)
-{
-    const ScanArgs &a = *w.a;
-    const int i0 = (w.head + w.lane) & (RING - 1), i1 = (w.head + 32 + w.lane) & (RING - 1);
-    const int o0 = w.po[i0], m0 = w.pm[i0], n0 = w.pn[i0], blk0 = w.pb[i0];
-    const int o1 = w.po[i1], m1 = w.pm[i1], n1 = w.pn[i1], blk1 = w.pb[i1];
-    float S0 = w.pS[i0], S1 = w.pS[i1];
-    __syncwarp();
-    w.head = (w.head + 64) & (RING - 1);
-    w.cnt -= 64;
-    const float r2 = current_r2(w);
-    int e0 = blk0 + a.db, e1 = blk1 + a.db;
-    if (e0 > a.nblk) e0 = a.nblk;
-    if (e1 > a.nblk) e1 = a.nblk;
-    const T *d = static_cast<const T *>(a.data);
-    const int64_t st0 = (int64_t)n0 * BLK, st1 = (int64_t)n1 * BLK;
-    accum_pair(d + (int64_t)o0 * a.Dp + blk0 * st0 + (int64_t)m0 * BLK, st0, blk0, e0 - blk0,
-               d + (int64_t)o1 * a.Dp + blk1 * st1 + (int64_t)m1 * BLK, st1, blk1, e1 - blk1, w.qv,
-               S0, S1);
-    after_step(w, true, S0, e0, o0, m0, n0, r2);
-    after_step(w, true, S1, e1, o1, m1, n1, r2);
-}
+#ifndef ADSX_SCAN_MINBLOCKS_H
+#define ADSX_SCAN_MINBLOCKS_H 5
+#endif
+template <typename T> struct MinBlocks { static constexpr int value = ADSX_SCAN_MINBLOCKS_H; };
+template <> struct MinBlocks<float> { static constexpr int value = ADSX_SCAN_MINBLOCKS; };
 
 template <typename T>
 __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(ScanArgs a)
@@ -308,13 +521,12 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
     w.qv = base + wc.qv;
     w.ed = base + wc.ed;
     w.ei = reinterpret_cast<int *>(base + wc.ei);
-    w.po = reinterpret_cast<int *>(base + wc.po);
-    w.pm = reinterpret_cast<int *>(base + wc.pm);
-    w.pn = reinterpret_cast<int *>(base + wc.pn);
+    w.pof = reinterpret_cast<long long *>(base + wc.pof);
+    w.pst = reinterpret_cast<int *>(base + wc.pst);
     w.pb = reinterpret_cast<int *>(base + wc.pb);
+    w.pp = reinterpret_cast<int *>(base + wc.pp);
     w.pS = base + wc.pS;
     w.lane = lane;
-    const int nb0 = a.db < a.nblk ? a.db : a.nblk;
     const int n_items = a.n_items_dev ? *a.n_items_dev : a.n_items;
 
     for (;;) {
@@ -359,14 +571,32 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
             const int o = (int)a.off[c];
             const int n = (int)(a.off[c + 1] - o);
             const T *cb = static_cast<const T *>(a.data) + (int64_t)o * a.Dp;
+            const int64_t stride = (int64_t)n * BLK;
+            const long long cbase = (long long)o * a.Dp;
             for (int m0 = 0; m0 < n; m0 += 32) {
-                const float r2 = current_r2(w);
-                const int m = m0 + lane;
-                const bool valid = m < n;
-                float Sd = 0.f;
-                if (valid) Sd = accum_range(cb, n, m, 0, nb0, w.qv, 0.f);
-                after_step(w, valid, Sd, nb0, o, m, n, r2);
-                while (w.cnt >= 64) process_pending2(w);
+                // The tile advances step by step while at least DENSE_MIN of
+                // its members are live (all at the same block, contiguous
+                // loads); the rest go to the pending ring.
+                const int m = m0 + own_slot<Split<T>::NL>(lane);
+                bool live = m < n;
+                unsigned lm = __ballot_sync(FULL, live);
+                float S = 0.f;
+                int blk = 0;
+                for (;;) {
+                    const float r2 = current_r2(w);
+                    const int e = blk + a.db < a.nblk ? blk + a.db : a.nblk;
+                    S += tile_step(cb, stride, m0, blk, e, lm, w.qv, lane);
+                    blk = e;
+                    const long long off = cbase + blk * stride + (long long)m * BLK;
+                    live = after_step(w, live, S, blk, o + m, off, (int)stride, r2, false);
+                    lm = __ballot_sync(FULL, live);
+                    if (lm == 0u) break;
+                    if (__popc(lm) < DENSE_MIN) {
+                        enqueue(w, live, S, blk, o + m, off, (int)stride);
+                        break;
+                    }
+                }
+                while (w.cnt >= 32) process_pending(w, 32);
             }
         }
         while (w.cnt > 0) process_pending(w, w.cnt < 32 ? w.cnt : 32);
