@@ -566,14 +566,20 @@ def main():
                 dims_sum += int(dims.sum().item())
         return tot / steps, scan_ms / steps, dims_sum / steps, ids
 
-    # FDScanning arm (the baseline the metric compares against)
+    # FDScanning arm (the baseline the metric compares against).  Each arm is an
+    # NVTX range, so a profiler can select its launches (e.g. ncu --nvtx
+    # --nvtx-include "ads_arm/").
+    nvtx = torch.cuda.nvtx
+    nvtx.range_push("fd_arm")
     fd_ms, fd_scan_ms, fd_dims, _ = timed(np_fd, math.inf, max(3, args.steps // 2), 2)
+    nvtx.range_pop()
     fd_ms = max_over_ranks(fd_ms)
 
     # PDScanning on raw vectors (an index with P = I): the paper's IVF** baseline
     ix_raw = adsx.build_index(wl.X, np.eye(wl.D, dtype=np.float32), wl.centroids, wl.assign,
                               storage=storage)
     adsx.set_stage_timing(ix_raw, True)
+    nvtx.range_push("pd_arm")
     pd_t, pd_dims = [], 0.0
     for st in range(2 + max(3, args.steps // 2)):
         flush.zero_()
@@ -586,6 +592,7 @@ def main():
         if st >= 2:
             pd_t.append(e0.elapsed_time(e1))
             pd_dims = float(pdd.sum().item())
+    nvtx.range_pop()
     pd_ms = max_over_ranks(sum(pd_t) / len(pd_t))
     ix_raw.close()
 
@@ -595,8 +602,10 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     gpu_idx = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local if ws > 1 else 0]
+    nvtx.range_push("ads_arm")
     with Clocks(gpu_idx) as clk:
         ads_ms, ads_scan_ms, ads_dims, ids = timed(np_ads, args.eps0, args.steps, args.warmup)
+    nvtx.range_pop()
     torch.cuda.synchronize()
     stage = adsx.stage_ms(ix)
     ads_ms = max_over_ranks(ads_ms)
