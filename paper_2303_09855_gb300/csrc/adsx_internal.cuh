@@ -303,10 +303,29 @@ cudaError_t launch_finalize_topk(const ScanArgs &a, cudaStream_t s);
 
 // Batched form: validates per-query K / nprobe, chooses splits, orders the
 // queries longest-first and writes the item list (capacity nq * 64 items).
+// Splits per query of the uniform search: enough work items to fill the GPU
+// (`target`), but each split should expect at least 2K candidates (a split
+// prunes only once it holds K exact distances), and at most 64 and the
+// finalize kernel's merge buffer (S * next_pow2(K) <= 16384).
+// members_per_list = N / nlist.
+inline int32_t uniform_splits(int64_t nq, int nprobe, int K, int64_t target,
+                              int64_t members_per_list)
+{
+    int Kp = 1;
+    while (Kp < K) Kp <<= 1;
+    int64_t S = (target + nq - 1) / (nq > 0 ? nq : 1);
+    const int64_t by_cand = (int64_t)nprobe * members_per_list / (2 * (int64_t)K);
+    if (S > by_cand) S = by_cand;
+    if (S > 64) S = 64;
+    const int64_t cap = 16384 / Kp > 1 ? 16384 / Kp : 1;
+    if (S > cap) S = cap;
+    return (int32_t)(S > 1 ? S : 1);
+}
+
 cudaError_t launch_plan_batched(const int32_t *Kq, const int32_t *nprobe_q, int64_t nq,
-                                int maxK, int maxP, int target_items, int2 *items,
-                                int32_t *item_first, int32_t *n_items, int32_t *qperm,
-                                const int64_t *out_off_in, int64_t *out_off,
+                                int maxK, int maxP, int target_items, int64_t members_per_list,
+                                int2 *items, int32_t *item_first, int32_t *n_items,
+                                int32_t *qperm, const int64_t *out_off_in, int64_t *out_off,
                                 unsigned *err, cudaStream_t s);
 constexpr unsigned ERR_BATCH_ARGS = 2u;   // a per-query K or nprobe was out of range
 constexpr unsigned ERR_OUT_RANGE = 4u;    // an output offset + K exceeded the output length

@@ -485,13 +485,9 @@ static int search_impl(const adsx_index *index, const float *Qv, int64_t nq, int
         int need = std::max(2 * Kp, K + 32);
         a.C = 1;
         while (a.C < need) a.C <<= 1;
-        // splits per query: enough work items to fill the GPU, bounded by the
-        // probe count and by the merge buffer of the finalize kernel
-        int64_t target = adsx::scan_items_target(ix->device, ix->items_per_sm);
-        int64_t S = (target + nq - 1) / nq;
-        S = std::min<int64_t>(S, std::min(nprobe, 64));
-        S = std::min<int64_t>(S, std::max(1, 16384 / Kp));
-        a.S = (int32_t)std::max<int64_t>(S, 1);
+        a.S = adsx::uniform_splits(nq, nprobe, K,
+                                   adsx::scan_items_target(ix->device, ix->items_per_sm),
+                                   ix->N / ix->nlist);
     }
     if (nq * (int64_t)a.S >= ((int64_t)1 << 31)) return fail(ADSX_EINVAL, "too many queries in one call");
     a.n_items = (int32_t)(nq * a.S);
@@ -625,8 +621,9 @@ int adsx_search_batched(const adsx_index *index, const float *Qv, int64_t nq, co
            "select");
     }
     const int target = adsx::scan_items_target(ix->device, ix->items_per_sm);
-    CK(adsx::launch_plan_batched(kq.dev, pq.dev, nq, max_K, max_nprobe, target, items, item_first,
-                                 n_items, qperm, oo.dev, out_off, ix->err, s), "plan");
+    CK(adsx::launch_plan_batched(kq.dev, pq.dev, nq, max_K, max_nprobe, target,
+                                 ix->N / ix->nlist, items, item_first, n_items,
+                                 qperm, oo.dev, out_off, ix->err, s), "plan");
     CK(mark(ix, 3, s), "event");
 
     adsx::ScanArgs a;

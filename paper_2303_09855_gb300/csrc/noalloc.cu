@@ -121,13 +121,8 @@ extern "C" int adsx_search_noalloc(const adsx_index *index, const float *Qv, int
     while (Kp < K) Kp <<= 1;
     a.C = 1;
     while (a.C < std::max(2 * Kp, K + 32)) a.C <<= 1;
-    {
-        int64_t target = adsx::scan_items_target(ix->device);
-        int64_t S = (target + nq - 1) / nq;
-        S = std::min<int64_t>(S, std::min(nprobe, 64));
-        S = std::min<int64_t>(S, std::max(1, 16384 / Kp));
-        a.S = (int32_t)std::max<int64_t>(S, 1);
-    }
+    a.S = adsx::uniform_splits(nq, nprobe, K, adsx::scan_items_target(ix->device, ix->items_per_sm),
+                               ix->N / ix->nlist);
     if (nq * (int64_t)a.S >= ((int64_t)1 << 31)) return nerr(ADSX_EINVAL, "too many queries");
     a.n_items = (int32_t)(nq * a.S);
     a.db = delta_d / adsx::BLK;

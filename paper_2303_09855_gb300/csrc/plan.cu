@@ -6,8 +6,9 @@
 //      values set ERR_BATCH_ARGS in the index's error word and are clamped);
 //   2. picks the splits S_q of each query: enough items to fill the GPU
 //      (target_items / nq), at least one item per 64 probe slots for long
-//      queries, capped by nprobe_q, 16 and 16384 / next_pow2(K_q) (the
-//      finalize merge buffer);
+//      queries, capped by nprobe_q * (N / nlist) / (2 K_q) (each split should
+//      expect 2K candidates: it prunes only once it holds K exact
+//      distances), 16 and 16384 / next_pow2(K_q) (the finalize merge buffer);
 //   3. orders the queries longest-first (counting sort on nprobe_q) so the
 //      longest items start first and short ones fill the tail;
 //   4. lays out the items of each query contiguously in that order
@@ -20,14 +21,16 @@ namespace {
 
 constexpr int PT = 1024;
 
-__device__ __forceinline__ int splits_of(int K, int np, int64_t nq, int target)
+__device__ __forceinline__ int splits_of(int K, int np, int64_t nq, int target,
+                                         int64_t members_per_list)
 {
     int Kp = 1;
     while (Kp < K) Kp <<= 1;
     int64_t S = (target + nq - 1) / nq;
     const int by_len = (np + 63) / 64;
     if (S < by_len) S = by_len;
-    if (S > np) S = np;
+    const int64_t by_cand = (int64_t)np * members_per_list / (2 * (int64_t)K);
+    if (S > by_cand) S = by_cand;
     if (S > 16) S = 16;
     const int cap = 16384 / Kp;
     if (S > cap) S = cap;
@@ -65,7 +68,8 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *warp_tot,
 
 __global__ void __launch_bounds__(PT) plan_batched_kernel(
     const int32_t *__restrict__ Kq, const int32_t *__restrict__ npq, int64_t nq, int maxK, int maxP,
-    int target, int2 *__restrict__ items, int32_t *__restrict__ item_first,
+    int target, int64_t members_per_list, int2 *__restrict__ items,
+    int32_t *__restrict__ item_first,
     int32_t *__restrict__ n_items, int32_t *__restrict__ qperm,
     const int64_t *__restrict__ out_off_in, int64_t *__restrict__ out_off, unsigned *err)
 {
@@ -113,7 +117,7 @@ __global__ void __launch_bounds__(PT) plan_batched_kernel(
             int np = npq[q], K = Kq[q];
             np = np < 1 ? 1 : (np > maxP ? maxP : np);
             K = K < 1 ? 1 : (K > maxK ? maxK : K);
-            S = splits_of(K, np, nq, target);
+            S = splits_of(K, np, nq, target, members_per_list);
         }
         int64_t total;
         const int64_t before = block_excl_scan(S, warp_tot, &total);
@@ -152,14 +156,15 @@ __global__ void __launch_bounds__(PT) plan_batched_kernel(
 }  // namespace
 
 cudaError_t launch_plan_batched(const int32_t *Kq, const int32_t *nprobe_q, int64_t nq,
-                                int maxK, int maxP, int target_items, int2 *items,
-                                int32_t *item_first, int32_t *n_items, int32_t *qperm,
-                                const int64_t *out_off_in, int64_t *out_off,
+                                int maxK, int maxP, int target_items, int64_t members_per_list,
+                                int2 *items, int32_t *item_first, int32_t *n_items,
+                                int32_t *qperm, const int64_t *out_off_in, int64_t *out_off,
                                 unsigned *err, cudaStream_t s)
 {
     if (nq <= 0) return cudaSuccess;
     size_t smem = sizeof(int) * (size_t)(maxP + 2);
-    plan_batched_kernel<<<1, PT, smem, s>>>(Kq, nprobe_q, nq, maxK, maxP, target_items, items,
+    plan_batched_kernel<<<1, PT, smem, s>>>(Kq, nprobe_q, nq, maxK, maxP, target_items,
+                                            members_per_list, items,
                                             item_first, n_items, qperm, out_off_in, out_off, err);
     return cudaGetLastError();
 }

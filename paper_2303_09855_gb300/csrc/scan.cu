@@ -4,8 +4,9 @@
 // the verification protocol (Sec. 6.2.5).
 //
 // ads_scan_kernel is persistent and warp-centric.  A work item is (query q,
-// split s): the probe slots s, s+S, s+2S, ... of q (S = 1 unless there are
-// too few queries to fill the GPU).  Each warp claims items from a global
+// split s): the probe slots s, s+S, s+2S, ... of q, or with more splits than
+// slots every js-th tile of one slot (S = 1 unless there are too few queries
+// to fill the GPU).  Each warp claims items from a global
 // counter and owns, in shared memory, the item's q', a pending ring and a
 // candidate buffer; nothing is shared between warps, so no locks.
 //   1. Members are visited cluster by cluster in probe order, 32 per tile.
@@ -566,14 +567,24 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
         w.dims = 0u;
         __syncwarp();
 
-        for (int p = s; p < nprobe; p += S) {
+        // With S <= nprobe, split s owns the probe slots s, s + S, ... (the
+        // split holding the nearest cluster finds a tight r early and shares
+        // it).  With S > nprobe (e.g. nlist = 1, a linear scan), split s works
+        // on slot s % nprobe alone, taking every js-th 32-member tile of it
+        // from tile s / nprobe, js being the number of splits on that slot.
+        const bool wide = S > nprobe;
+        const int p0 = wide ? s % nprobe : s;
+        const int pstep = wide ? nprobe : S;
+        const int j0 = wide ? s / nprobe : 0;
+        const int js = wide ? (S - 1 - p0) / nprobe + 1 : 1;
+        for (int p = p0; p < nprobe; p += pstep) {
             const int c = a.probes[q * (a.probe_stride ? a.probe_stride : a.nprobe) + p];
             const int o = (int)a.off[c];
             const int n = (int)(a.off[c + 1] - o);
             const T *cb = static_cast<const T *>(a.data) + (int64_t)o * a.Dp;
             const int64_t stride = (int64_t)n * BLK;
             const long long cbase = (long long)o * a.Dp;
-            for (int m0 = 0; m0 < n; m0 += 32) {
+            for (int m0 = j0 * 32; m0 < n; m0 += 32 * js) {
                 // The tile advances step by step while at least DENSE_MIN of
                 // its members are live (all at the same block, contiguous
                 // loads); the rest go to the pending ring.
