@@ -17,6 +17,11 @@ Functions (each follows the passage named in its docstring):
   dco_pd(o, q, r2, delta_d)         Sec. 6.1 PDScanning (exact partial-distance DCO)
   ivf_pd(...)                       Sec. 6.1 IVF* (IVF with PDScanning DCOs)
   recall_at(...), avg_dist_ratio()  Sec. 6.1 accuracy metrics
+  normalize_rows(A)                 Sec. 8 ext. (1): cosine similarity is the
+                                    Euclidean case on normalised vectors
+  dco_ip(o, q, r, eps0, delta_d)    Sec. 8 ext. (1): inner-product DCO reduced
+                                    to Algorithm 1 on normalised vectors
+  ivf_exact_ip(...), ivf_ads_ip(...) IVF / IVF+ for inner products
 """
 from __future__ import annotations
 
@@ -70,6 +75,11 @@ def _load():
             lib.orc_dco_pd.argtypes = [P, P, i32, f64, i32, P, P]
             lib.orc_dco_pd.restype = cint
             lib.orc_ivf_pd.argtypes = [P, i64, i32, P, i32, P, P, i64, i32, i32, i32, P, P, P, cint]
+            lib.orc_dco_ip.argtypes = [P, P, i32, f64, f64, i32, P, P, P]
+            lib.orc_dco_ip.restype = cint
+            lib.orc_ivf_exact_ip.argtypes = [P, i64, i32, P, i32, P, P, i64, i32, i32, P, P, cint]
+            lib.orc_ivf_ads_ip.argtypes = [P, i64, i32, P, i32, P, P, i64, i32, i32,
+                                           f64, i32, P, P, P, P, cint]
             _lib = lib
     return _lib
 
@@ -207,6 +217,66 @@ def ivf_pd(Y, Cr, assign, Qr, K: int, nprobe: int, delta_d: int, nthreads: int =
     _load().orc_ivf_pd(_p(Y), Y.shape[0], D, _p(Cr), Cr.shape[0], _p(assign), _p(Qr), nq, K,
                        nprobe, int(delta_d), _p(ids), _p(d2), _p(dims), nthreads)
     return ids, d2, dims
+
+
+# ------------------------------------------- cosine and inner product
+def normalize_rows(A):
+    """Sec. 8, extension (1): cosine-similarity search is Euclidean search on
+    the normalised vectors.  Rows of A scaled to unit norm in FP64 (a zero row
+    stays zero)."""
+    A = np.asarray(A, np.float64)
+    n = np.sqrt(np.sum(A * A, axis=1, keepdims=True))
+    return np.where(n > 0, A / np.where(n > 0, n, 1.0), 0.0)
+
+
+def dco_ip(o, q, r: float, eps0: float, delta_d: int):
+    """Sec. 8, extension (1): is <o, q> >= r?  Algorithm 1 on o/||o|| and
+    q/||q|| against the squared threshold 2 - 2 r / (||o|| ||q||).  Returns
+    (decision, dims, <o, q>, margin)."""
+    o = _c(o, np.float64)
+    q = _c(q, np.float64)
+    dims = ctypes.c_int32(0)
+    ip = ctypes.c_double(0.0)
+    m = ctypes.c_double(0.0)
+    res = _load().orc_dco_ip(_p(o), _p(q), o.shape[0], float(r), float(eps0), int(delta_d),
+                             ctypes.byref(dims), ctypes.byref(ip), ctypes.byref(m))
+    return int(res), int(dims.value), float(ip.value), float(m.value)
+
+
+def ivf_exact_ip(Y, Cr, assign, Qr, K: int, nprobe: int, nthreads: int = 0):
+    """IVF for inner products with exact scoring: the nprobe clusters of
+    largest <c, q> (ties by id), the K largest <o, q> (ties by id) among their
+    members.  Returns ids (nq,K) and inner products (nq,K), -1 / -inf padded."""
+    Y = _c(Y, np.float64)
+    Cr = _c(Cr, np.float64)
+    assign = _c(assign, np.int32)
+    Qr = _c(Qr, np.float64)
+    nq, D = Qr.shape
+    ids = np.empty((nq, K), np.int64)
+    ips = np.empty((nq, K), np.float64)
+    _load().orc_ivf_exact_ip(_p(Y), Y.shape[0], D, _p(Cr), Cr.shape[0], _p(assign), _p(Qr),
+                             nq, K, nprobe, _p(ids), _p(ips), nthreads)
+    return ids, ips
+
+
+def ivf_ads_ip(Y, Cr, assign, Qr, K: int, nprobe: int, eps0: float, delta_d: int,
+               nthreads: int = 0):
+    """IVF+ for inner products: sequential IVF whose DCOs are dco_ip against
+    the K-th largest inner product held.  Returns ids, inner products, dims
+    sampled per query, candidates per query."""
+    Y = _c(Y, np.float64)
+    Cr = _c(Cr, np.float64)
+    assign = _c(assign, np.int32)
+    Qr = _c(Qr, np.float64)
+    nq, D = Qr.shape
+    ids = np.empty((nq, K), np.int64)
+    ips = np.empty((nq, K), np.float64)
+    dims = np.empty(nq, np.int64)
+    ncand = np.empty(nq, np.int64)
+    _load().orc_ivf_ads_ip(_p(Y), Y.shape[0], D, _p(Cr), Cr.shape[0], _p(assign), _p(Qr), nq,
+                           K, nprobe, float(eps0), int(delta_d), _p(ids), _p(ips), _p(dims),
+                           _p(ncand), nthreads)
+    return ids, ips, dims, ncand
 
 
 # ---------------------------------------------------------------- metrics

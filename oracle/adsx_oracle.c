@@ -21,6 +21,11 @@
  *                         fixed threshold per query (verification protocol).
  *   - orc_dco_pd,         Sec. 6.1: PDScanning, the exact partial-distance
  *     orc_ivf_pd          DCO of the IVF* / IVF** baselines.
+ *   - orc_dco_ip,         Sec. 8, extension (1): inner-product DCOs reduced
+ *     orc_ivf_exact_ip,   to Algorithm 1 on normalised vectors with a
+ *     orc_ivf_ads_ip      per-object threshold; IVF for inner products.
+ *     (Cosine similarity is the Euclidean case on normalised vectors, done
+ *     in the Python wrapper.)
  *
  * Conventions (readings of points the paper leaves open):
  *   - distances are SQUARED Euclidean distances in the rotated space;
@@ -477,6 +482,171 @@ void orc_ivf_pd(const double *Y, int64_t N, int32_t D, const double *Cr, int32_t
         }
         write_sorted(pairs, count, K, ids + q * K, d2 + q * K);
         if (dims_total) dims_total[q] = dims_sum;
+        free(pairs);
+        free(hd);
+        free(hi);
+        free(probes);
+    }
+    free_buckets(&b);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Inner product (Sec. 8, extension (1)).  <o,q> >= r holds iff            */
+/*     || o/||o|| - q/||q|| ||^2  <=  2 - 2 r / (||o|| ||q||),              */
+/* so the DCO "is <o,q> at least r?" is Algorithm 1 on the normalised      */
+/* vectors against the per-object squared threshold                        */
+/*     tau = 2 - 2 r / (||o|| ||q||).                                       */
+/* Readings: r = -inf (fewer than K objects held) gives tau = +inf (never  */
+/* reject); tau < 0 means <o,q> <= ||o|| ||q|| < r, a negative decided     */
+/* without sampling (dims 0); a zero-norm o or q has <o,q> = 0, decided    */
+/* exactly (positive iff 0 >= r, dims D).  *ip_out is <o,q> computed       */
+/* directly; o, q are rotated vectors (rotation preserves both norms and   */
+/* inner products).                                                        */
+static double dot(const double *a, const double *b, int32_t D)
+{
+    double s = 0.0;
+    for (int32_t i = 0; i < D; ++i) s += a[i] * b[i];
+    return s;
+}
+
+int orc_dco_ip(const double *o, const double *q, int32_t D, double r,
+               double eps0, int32_t delta_d, int32_t *dims, double *ip_out,
+               double *margin)
+{
+    const double no = sqrt(dot(o, o, D)), nq = sqrt(dot(q, q, D));
+    const double ip = dot(o, q, D);
+    if (ip_out) *ip_out = ip;
+    if (no == 0.0 || nq == 0.0) {
+        if (dims) *dims = D;
+        if (margin) *margin = INFINITY;
+        return (0.0 >= r) ? ORC_POSITIVE : ORC_NEGATIVE_AT_D;
+    }
+    const double tau = isinf(r) && r < 0 ? INFINITY : 2.0 - 2.0 * r / (no * nq);
+    if (tau < 0.0) {
+        if (dims) *dims = 0;
+        if (margin) *margin = INFINITY;
+        return ORC_REJECTED;
+    }
+    double *oh = (double *)malloc(sizeof(double) * (size_t)D);
+    double *qh = (double *)malloc(sizeof(double) * (size_t)D);
+    for (int32_t i = 0; i < D; ++i) {
+        oh[i] = o[i] / no;
+        qh[i] = q[i] / nq;
+    }
+    int res = orc_dco(oh, qh, D, tau, eps0, delta_d, dims, NULL, margin);
+    free(oh);
+    free(qh);
+    return res;
+}
+
+/* IVF for inner products: the N_probe clusters with the largest <c, q>    */
+/* (ties by cluster id), then the K largest <o, q> (ties by id) among     */
+/* their members.  Pairs hold -<.,q> so the ascending order of orc_pair   */
+/* is the descending order of inner products.                             */
+static void probe_one_ip(const double *Cr, int32_t nlist, int32_t D,
+                         const double *qr, int32_t nprobe, int32_t *probes)
+{
+    orc_pair *pairs = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)nlist);
+    for (int32_t c = 0; c < nlist; ++c) {
+        pairs[c].d = -dot(Cr + (int64_t)c * D, qr, D);
+        pairs[c].id = c;
+    }
+    qsort(pairs, (size_t)nlist, sizeof(orc_pair), pair_cmp);
+    for (int32_t p = 0; p < nprobe; ++p) probes[p] = (int32_t)pairs[p].id;
+    free(pairs);
+}
+
+static void write_sorted_ip(orc_pair *pairs, int64_t n, int32_t K, int64_t *ids, double *ips)
+{
+    write_sorted(pairs, n, K, ids, ips);
+    for (int32_t k = 0; k < K; ++k) ips[k] = (k < n) ? -ips[k] : -INFINITY;
+}
+
+void orc_ivf_exact_ip(const double *Y, int64_t N, int32_t D, const double *Cr,
+                      int32_t nlist, const int32_t *assign, const double *Qr,
+                      int64_t nq, int32_t K, int32_t nprobe, int64_t *ids,
+                      double *ips, int nthreads)
+{
+    orc_buckets b = make_buckets(assign, N, nlist);
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t q = 0; q < nq; ++q) {
+        const double *qr = Qr + q * D;
+        int32_t *probes = (int32_t *)malloc(sizeof(int32_t) * (size_t)nprobe);
+        probe_one_ip(Cr, nlist, D, qr, nprobe, probes);
+        int64_t ncand = 0;
+        for (int32_t p = 0; p < nprobe; ++p)
+            ncand += b.start[probes[p] + 1] - b.start[probes[p]];
+        orc_pair *pairs = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(ncand > 0 ? ncand : 1));
+        int64_t k = 0;
+        for (int32_t p = 0; p < nprobe; ++p)
+            for (int64_t m = b.start[probes[p]]; m < b.start[probes[p] + 1]; ++m) {
+                int64_t id = b.member[m];
+                pairs[k].d = -dot(Y + id * D, qr, D);
+                pairs[k].id = id;
+                ++k;
+            }
+        write_sorted_ip(pairs, ncand, K, ids + q * K, ips + q * K);
+        free(pairs);
+        free(probes);
+    }
+    free_buckets(&b);
+}
+
+/* IVF+ for inner products: sequential IVF whose DCOs are orc_dco_ip       */
+/* against r = the K-th largest inner product held (-inf until K are).    */
+void orc_ivf_ads_ip(const double *Y, int64_t N, int32_t D, const double *Cr,
+                    int32_t nlist, const int32_t *assign, const double *Qr,
+                    int64_t nq, int32_t K, int32_t nprobe, double eps0,
+                    int32_t delta_d, int64_t *ids, double *ips,
+                    int64_t *dims_total, int64_t *ncand_out, int nthreads)
+{
+    orc_buckets b = make_buckets(assign, N, nlist);
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t q = 0; q < nq; ++q) {
+        const double *qr = Qr + q * D;
+        int32_t *probes = (int32_t *)malloc(sizeof(int32_t) * (size_t)nprobe);
+        probe_one_ip(Cr, nlist, D, qr, nprobe, probes);
+        /* KNN set of (-<o,q>, id): unordered array, maximum by linear scan. */
+        double *hd = (double *)malloc(sizeof(double) * (size_t)K);
+        int64_t *hi = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
+        int32_t count = 0;
+        int64_t dims_sum = 0, ncand = 0;
+        for (int32_t p = 0; p < nprobe; ++p) {
+            for (int64_t m = b.start[probes[p]]; m < b.start[probes[p] + 1]; ++m) {
+                int64_t id = b.member[m];
+                int32_t imax = 0;
+                double r = -INFINITY;
+                if (count == K) {
+                    for (int32_t k = 1; k < K; ++k)
+                        if (pair_less(hd[imax], hi[imax], hd[k], hi[k])) imax = k;
+                    r = -hd[imax];
+                }
+                int32_t dims = 0;
+                double ip = 0.0;
+                int res = orc_dco_ip(Y + id * D, qr, D, r, eps0, delta_d, &dims, &ip, NULL);
+                dims_sum += dims;
+                ncand += 1;
+                if (res != ORC_POSITIVE) continue;
+                if (count < K) {
+                    hd[count] = -ip;
+                    hi[count] = id;
+                    ++count;
+                } else if (pair_less(-ip, id, hd[imax], hi[imax])) {
+                    hd[imax] = -ip;
+                    hi[imax] = id;
+                }
+            }
+        }
+        orc_pair *pairs = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(count > 0 ? count : 1));
+        for (int32_t k = 0; k < count; ++k) {
+            pairs[k].d = hd[k];
+            pairs[k].id = hi[k];
+        }
+        write_sorted_ip(pairs, count, K, ids + q * K, ips + q * K);
+        if (dims_total) dims_total[q] = dims_sum;
+        if (ncand_out) ncand_out[q] = ncand;
         free(pairs);
         free(hd);
         free(hi);
