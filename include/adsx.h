@@ -58,6 +58,9 @@ enum {
 /* Storage type of the dimension-blocked vector layout. */
 typedef enum { ADSX_F32 = 0, ADSX_BF16 = 1, ADSX_F16 = 2 } adsx_dtype;
 
+/* Similarity of an index (adsx_build_index_metric; Sec. 8, extension (1)). */
+typedef enum { ADSX_L2 = 0, ADSX_IP = 1, ADSX_COSINE = 2 } adsx_metric;
+
 /* Limits of the current kernels (checked; ADSX_EINVAL beyond them). */
 #define ADSX_MAX_D 4080       /* dimensions (padded to a multiple of 16)   */
 #define ADSX_MAX_K 1024       /* neighbours per query                        */
@@ -93,8 +96,37 @@ int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
                      const int32_t *assign, int32_t storage, void *stream,
                      adsx_index **out);
 
+/*
+ * adsx_build_index_metric -- adsx_build_index for cosine similarity or inner
+ * product, through the reductions of Sec. 8, extension (1):
+ *   ADSX_L2      exactly adsx_build_index.
+ *   ADSX_COSINE  data rows, centroids and (at search) queries are scaled to
+ *                unit norm, so cosine search is Euclidean search on them;
+ *                searches return cosine similarities (1 - ||x^ - q^||^2 / 2),
+ *                largest first.  A zero data row is ADSX_EINVAL; a zero query
+ *                row stays zero (its results are unspecified).
+ *   ADSX_IP      data rows are stored normalised with their norms ||o||;
+ *                "is <o,q> at least r" is Algorithm 1 on o/||o||, q/||q||
+ *                against the per-object squared threshold
+ *                2 - 2 r / (||o|| ||q||) (a negative threshold rejects at
+ *                once: <o,q> <= ||o|| ||q|| < r); r is the query's current
+ *                K-th largest inner product.  Clusters are probed by the
+ *                largest <c, q> with the given (raw) centroids.  Searches
+ *                return inner products, largest first.
+ * For both, padding slots hold -INF (ids -1); ties are ordered by id.  Other
+ * arguments and errors as adsx_build_index.  adsx_dco_fixed_r and
+ * adsx_search_noalloc accept ADSX_L2 indexes only (ADSX_EINVAL otherwise).
+ */
+int adsx_build_index_metric(const float *X, int64_t N, int32_t D, const float *P,
+                            const float *centroids, int32_t nlist,
+                            const int32_t *assign, int32_t storage, int32_t metric,
+                            void *stream, adsx_index **out);
+
 /* Frees the index and all of its device memory (synchronises the device). */
 int adsx_free_index(adsx_index *index);
+
+/* The metric an index was built with (ADSX_L2, ADSX_IP or ADSX_COSINE). */
+int adsx_index_metric(const adsx_index *index, int32_t *metric);
 
 /* Shape of an index: any output pointer may be NULL. */
 int adsx_index_info(const adsx_index *index, int64_t *N, int32_t *D,
@@ -114,7 +146,8 @@ int adsx_index_info(const adsx_index *index, int64_t *N, int32_t *D,
  *   delta_d    multiple of 16, >= 16 (a value >= D also disables the test);
  *              0 uses the index's tuned step (adsx_autotune; 32 until tuned).
  *   ids        host or device, nq x K int64 output; -1 pads missing slots.
- *   dists      host or device, nq x K float32 squared distances; +INF pads.
+ *   dists      host or device, nq x K float32 squared distances; +INF pads
+ *              (cosine / inner-product indexes: similarities, -INF pads).
  *   dims_read  host or device, nq int64 (may be NULL): dimensions sampled
  *              per query, summed over its candidates (Sec. 6.1 metric).
  * The threshold r is shared among the warps scanning a query, so which
@@ -161,7 +194,8 @@ int adsx_search_pdscan(const adsx_index *index, const float *Qv, int64_t nq,
  *                prefix sums of K (results packed in query order).
  *   out_total    length of ids and dists; a query whose slice does not fit
  *                is skipped and flagged in the error word.
- *   ids, dists   host or device, out_total entries; -1 / +INF padding.
+ *   ids, dists   host or device, out_total entries; -1 / +INF padding
+ *                (cosine / inner-product indexes: similarities, -INF).
  *   dims_read    host or device, nq int64 (may be NULL).
  * With all pointers in device memory the call only enqueues work, and the
  * sequence can be captured in a CUDA graph.
@@ -177,7 +211,10 @@ int adsx_search_batched(const adsx_index *index, const float *Qv, int64_t nq,
  * adsx_probe -- the query rotation and centroid selection steps of
  * adsx_search alone (Sec. 3.1, Sec. 2.2.2), for inspection and tests.
  *   probes     host or device, nq x nprobe int32, ascending (dist, id).
- *   probe_d2   host or device, nq x nprobe float32 (may be NULL).
+ *   probe_d2   host or device, nq x nprobe float32 (may be NULL): the
+ *              ranking key ||q' - c'||^2; for cosine indexes on normalised
+ *              q and c; for inner-product indexes ||q'||^2 + max ||c'||^2 -
+ *              2 <q', c'> (ascending = largest inner product first).
  */
 int adsx_probe(const adsx_index *index, const float *Qv, int64_t nq,
                int32_t nprobe, int32_t *probes, float *probe_d2, void *stream);

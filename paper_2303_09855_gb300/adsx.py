@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libadsx.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4
 F32, BF16, F16 = 0, 1, 2
+L2, IP, COSINE = 0, 1, 2
 REJECTED, POSITIVE, NEGATIVE_AT_D = 0, 1, 2
 
 _lib = None
@@ -48,6 +49,9 @@ def load():
     lib = ctypes.CDLL(LIB_PATH)
     V, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
     lib.adsx_build_index.argtypes = [V, i64, i32, V, V, i32, V, i32, V, ctypes.POINTER(V)]
+    lib.adsx_build_index_metric.argtypes = [V, i64, i32, V, V, i32, V, i32, i32, V,
+                                            ctypes.POINTER(V)]
+    lib.adsx_index_metric.argtypes = [V, V]
     lib.adsx_free_index.argtypes = [V]
     lib.adsx_index_info.argtypes = [V, V, V, V, V, V]
     lib.adsx_search.argtypes = [V, V, i64, i32, i32, f32, i32, V, V, V, V]
@@ -70,7 +74,8 @@ def load():
     lib.adsx_set_stage_timing.argtypes = [V, i32]
     lib.adsx_stage_ms.argtypes = [V, V]
     lib.adsx_last_error.restype = ctypes.c_char_p
-    for fn in ("adsx_build_index", "adsx_free_index", "adsx_index_info", "adsx_search",
+    for fn in ("adsx_build_index", "adsx_build_index_metric", "adsx_index_metric",
+               "adsx_free_index", "adsx_index_info", "adsx_search",
                "adsx_probe", "adsx_rotate", "adsx_dco_fixed_r", "adsx_stream_status",
                "adsx_set_stage_timing", "adsx_stage_ms", "adsx_search_noalloc",
                "adsx_search_batched", "adsx_search_pdscan", "adsx_autotune",
@@ -147,6 +152,9 @@ class Index:
                                       ctypes.byref(nl), ctypes.byref(st), ctypes.byref(by)))
         self.N, self.D, self.nlist, self.storage, self.device_bytes = (
             N.value, D.value, nl.value, st.value, by.value)
+        m = ctypes.c_int32()
+        _check(load().adsx_index_metric(handle, ctypes.byref(m)))
+        self.metric = m.value
 
     def close(self):
         if self.handle:
@@ -173,17 +181,34 @@ class Index:
         return dco_fixed_r(self, Q, r2, eps0, delta_d, stream)
 
 
-def build_index(X, P, centroids, assign, storage=F32, stream=None) -> Index:
-    """adsx_build_index: host arrays X (N x D), P (D x D), centroids, assign."""
+def build_index(X, P, centroids, assign, storage=F32, stream=None, metric=L2) -> Index:
+    """adsx_build_index (metric L2) or adsx_build_index_metric (IP, COSINE):
+    host arrays X (N x D), P (D x D), centroids, assign.  With IP / COSINE,
+    searches return inner products / cosine similarities, largest first."""
     X = _host(X, np.float32)
     P = _host(P, np.float32)
     C = _host(centroids, np.float32)
     a = _host(assign, np.int32)
     h = ctypes.c_void_p()
-    _check(load().adsx_build_index(_ptr(X), X.shape[0], X.shape[1], _ptr(P), _ptr(C), C.shape[0],
-                                   _ptr(a), int(storage), _stream_of(None, stream),
-                                   ctypes.byref(h)))
+    if metric == L2:
+        _check(load().adsx_build_index(_ptr(X), X.shape[0], X.shape[1], _ptr(P), _ptr(C),
+                                       C.shape[0], _ptr(a), int(storage),
+                                       _stream_of(None, stream), ctypes.byref(h)))
+    else:
+        _check(load().adsx_build_index_metric(_ptr(X), X.shape[0], X.shape[1], _ptr(P), _ptr(C),
+                                              C.shape[0], _ptr(a), int(storage), int(metric),
+                                              _stream_of(None, stream), ctypes.byref(h)))
     return Index(h)
+
+
+def build_index_metric(X, P, centroids, assign, storage=F32, metric=L2, stream=None) -> Index:
+    """adsx_build_index_metric (Sec. 8, extension (1))."""
+    return build_index(X, P, centroids, assign, storage, stream, metric)
+
+
+def index_metric(index: Index) -> int:
+    """adsx_index_metric."""
+    return index.metric
 
 
 def free_index(index: Index):

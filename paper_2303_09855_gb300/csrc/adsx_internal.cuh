@@ -36,6 +36,8 @@ struct Index {
     void *data = nullptr;      // N x Dp of the storage type, dim-blocked per cluster
     float *rows32 = nullptr;   // N x Dp FP32 rotated rows in CSR order (16-bit storage only)
     float *norms = nullptr;    // N FP32 norms ||y|| in CSR order (16-bit storage only)
+    float *onorm = nullptr;    // N raw norms ||o|| in CSR order (inner-product indexes)
+    int32_t metric = ADSX_L2;  // ADSX_L2 / ADSX_IP / ADSX_COSINE
     int32_t *ids = nullptr;    // N: CSR position -> original id
     int64_t *off = nullptr;    // nlist + 1 CSR offsets
     int32_t *tile_off = nullptr;  // nlist + 1 prefix of ceil(n_c/32)
@@ -249,6 +251,17 @@ cudaError_t launch_rotate(const float *X, int64_t N, int D, const float *P, int 
 // Rotated rows Y (N x Dp, FP32) into the dim-blocked layout of `storage`
 // (ADSX_F32 / ADSX_BF16 / ADSX_F16); for 16-bit storage also the FP32 row copy
 // and the norms, both in CSR order.
+// Scales each of the N rows (D values, row stride ld) to unit norm in place
+// (norm accumulated in FP64; a zero row stays zero and, with zero_err, sets
+// ERR_ZERO_ROW in *zero_err); norms (may be NULL) receives the original norms.
+cudaError_t launch_normalize_rows(float *X, int64_t N, int ld, int D, float *norms,
+                                  unsigned *zero_err, cudaStream_t s);
+// v[0..n) := max(v): the inner-product index's constant centroid term.
+cudaError_t launch_fill_max(float *v, int n, cudaStream_t s);
+// dst[pos[i]] = src[i] for i < N (row order -> CSR order).
+cudaError_t launch_scatter_f32(const float *src, const int64_t *pos, int64_t N, float *dst,
+                               cudaStream_t s);
+
 cudaError_t launch_scatter_layout(const float *Y, int64_t N, int Dp, const int32_t *assign,
                                   const int64_t *pos_of_id, const int64_t *off, void *data,
                                   int storage, float *rows32, float *norms, cudaStream_t s);
@@ -292,6 +305,13 @@ struct ScanArgs {
     int32_t Kmax = 0;            // stride of partial lists (>= every K)
     int32_t probe_stride = 0;    // row stride of `probes` (>= every nprobe)
     int32_t finalize_T = 0;
+    // similarity (Sec. 8, extension (1)): ADSX_L2 keys are squared distances;
+    // ADSX_COSINE keys are squared distances of normalised vectors; ADSX_IP
+    // keys are -<o,q> with per-object thresholds 2 - 2 r / (||o|| ||q||) on
+    // the normalised vectors (onorm: ||o|| per CSR row, qnorm: ||q|| per query)
+    int32_t metric = ADSX_L2;
+    const float *onorm = nullptr;
+    const float *qnorm = nullptr;
 };
 
 size_t scan_smem_bytes(const ScanArgs &a);
@@ -301,8 +321,6 @@ cudaError_t launch_test_factors(float *ftab, int nblk, int D, float eps0, cudaSt
 cudaError_t launch_ads_scan(const ScanArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_finalize_topk(const ScanArgs &a, cudaStream_t s);
 
-// Batched form: validates per-query K / nprobe, chooses splits, orders the
-// queries longest-first and writes the item list (capacity nq * 64 items).
 // Splits per query of the uniform search: enough work items to fill the GPU
 // (`target`), but each split should expect at least 2K candidates (a split
 // prunes only once it holds K exact distances), and at most 64 and the
@@ -322,6 +340,8 @@ inline int32_t uniform_splits(int64_t nq, int nprobe, int K, int64_t target,
     return (int32_t)(S > 1 ? S : 1);
 }
 
+// Batched form: validates per-query K / nprobe, chooses splits, orders the
+// queries longest-first and writes the item list (capacity nq * 64 items).
 cudaError_t launch_plan_batched(const int32_t *Kq, const int32_t *nprobe_q, int64_t nq,
                                 int maxK, int maxP, int target_items, int64_t members_per_list,
                                 int2 *items, int32_t *item_first, int32_t *n_items,
@@ -329,6 +349,7 @@ cudaError_t launch_plan_batched(const int32_t *Kq, const int32_t *nprobe_q, int6
                                 unsigned *err, cudaStream_t s);
 constexpr unsigned ERR_BATCH_ARGS = 2u;   // a per-query K or nprobe was out of range
 constexpr unsigned ERR_OUT_RANGE = 4u;    // an output offset + K exceeded the output length
+constexpr unsigned ERR_ZERO_ROW = 16u;    // a zero-norm row where a unit row is required
 constexpr int BATCH_MAX_SPLITS = 16;
 int ads_scan_grid(const ScanArgs &a, int device);
 

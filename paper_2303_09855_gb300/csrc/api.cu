@@ -169,6 +169,26 @@ cudaError_t probe_queries(const Index *ix, const float *qrot, int64_t nq, int np
     return adsx::launch_select_nprobe(dist, nq, ix->nlist, nprobe, probes, pd2, sc.s);
 }
 
+// Sec. 8, extension (1): cosine queries are scaled to unit norm before the
+// centroid ranking (the centroids are); inner-product queries are ranked raw
+// (largest <c, q>) and scaled afterwards, keeping ||q|| for the per-object
+// thresholds and the returned inner products.
+cudaError_t queries_before_probe(const Index *ix, float *qrot, int64_t nq, cudaStream_t s)
+{
+    if (ix->metric != ADSX_COSINE) return cudaSuccess;
+    return adsx::launch_normalize_rows(qrot, nq, ix->Dp, ix->Dp, nullptr, nullptr, s);
+}
+
+cudaError_t queries_after_probe(const Index *ix, float *qrot, int64_t nq, Scratch &sc,
+                                float **qnorm)
+{
+    *qnorm = nullptr;
+    if (ix->metric != ADSX_IP) return cudaSuccess;
+    cudaError_t e = sc.get(qnorm, (size_t)nq);
+    if (e != cudaSuccess) return e;
+    return adsx::launch_normalize_rows(qrot, nq, ix->Dp, ix->Dp, *qnorm, nullptr, sc.s);
+}
+
 int finish(cudaStream_t s, bool any_host, const char *what)
 {
     if (!any_host) return ADSX_OK;
@@ -195,12 +215,14 @@ extern "C" {
 
 const char *adsx_last_error(void) { return g_last_error.c_str(); }
 
-int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
-                     const float *centroids, int32_t nlist, const int32_t *assign,
-                     int32_t storage, void *stream, adsx_index **out)
+static int build_impl(const float *X, int64_t N, int32_t D, const float *P,
+                      const float *centroids, int32_t nlist, const int32_t *assign,
+                      int32_t storage, int32_t metric, void *stream, adsx_index **out)
 {
     if (!out) return fail(ADSX_EINVAL, "out is NULL");
     *out = nullptr;
+    if (metric != ADSX_L2 && metric != ADSX_IP && metric != ADSX_COSINE)
+        return fail(ADSX_EINVAL, "metric %d not supported", metric);
     if (!X || !P || !centroids || !assign) return fail(ADSX_EINVAL, "NULL input pointer");
     if (N < 1 || N >= (int64_t)1 << 31) return fail(ADSX_EINVAL, "N out of range");
     if (D < 1 || D > ADSX_MAX_D) return fail(ADSX_EINVAL, "D out of range (1..%d)", ADSX_MAX_D);
@@ -239,6 +261,7 @@ int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
 
     Index *ix = new Index();
     ix->N = N;
+    ix->metric = metric;
     ix->D = D;
     ix->Dp = (D + 15) / 16 * 16;
     ix->nlist = nlist;
@@ -274,6 +297,7 @@ int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
         BCK(dalloc((void **)&ix->rows32, sizeof(float) * (size_t)N * Dp), "alloc FP32 rows");
         BCK(dalloc((void **)&ix->norms, sizeof(float) * (size_t)N), "alloc norms");
     }
+    if (metric == ADSX_IP) BCK(dalloc((void **)&ix->onorm, sizeof(float) * (size_t)N), "alloc norms");
     BCK(dalloc((void **)&ix->ids, sizeof(int32_t) * (size_t)N), "alloc ids");
     BCK(dalloc((void **)&ix->off, sizeof(int64_t) * ((size_t)nlist + 1)), "alloc offsets");
     BCK(dalloc((void **)&ix->tile_off, sizeof(int32_t) * ((size_t)nlist + 1)), "alloc tiles");
@@ -331,18 +355,63 @@ int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
         BCK(cudaMemcpyAsync(ad, assign, sizeof(int32_t) * N, cudaMemcpyHostToDevice, s), "copy assign");
         BCK(cudaMemcpyAsync(pd, pos.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, s), "copy positions");
         BCK(cudaMemcpyAsync(cd, centroids, sizeof(float) * (size_t)nlist * D, cudaMemcpyHostToDevice, s), "copy C");
+        // Sec. 8, extension (1): cosine and inner-product indexes store the
+        // data rows normalised (inner product keeps their norms); cosine
+        // centroids are normalised too, inner-product ones stay raw.
+        float *xnorm = nullptr;
+        if (metric != ADSX_L2) {
+            if (metric == ADSX_IP) BCK(sc.get(&xnorm, (size_t)N), "alloc norms");
+            BCK(adsx::launch_normalize_rows(xd, N, D, D, xnorm,
+                                            metric == ADSX_COSINE ? ix->err : nullptr, s),
+                "normalise data");
+            if (metric == ADSX_COSINE)
+                BCK(adsx::launch_normalize_rows(cd, nlist, D, D, nullptr, nullptr, s),
+                    "normalise centroids");
+        }
         // Sec. 3.1 / Sec. 6.1: rotate every data vector and centroid once.
         // Index phase: rotation of the data and the centroids, once per index.
         BCK(adsx::launch_rotate(xd, N, D, ix->P, Dp, yd, Dp, s), "rotate data");
         BCK(adsx::launch_rotate(cd, nlist, D, ix->P, Dp, ix->cents, Dp, s), "rotate centroids");
         BCK(adsx::launch_row_sqnorm(ix->cents, nlist, Dp, Dp, ix->cnorm, s), "centroid norms");
+        // inner product: ||q'||^2 + max ||c'||^2 - 2 q'.c' >= 0 ranks clusters
+        // by the largest <c, q> with the distance GEMM unchanged
+        if (metric == ADSX_IP) BCK(adsx::launch_fill_max(ix->cnorm, nlist, s), "centroid term");
         BCK(adsx::launch_scatter_layout(yd, N, Dp, ad, pd, ix->off, ix->data, storage, ix->rows32,
                                         ix->norms, s), "scatter layout");
+        if (metric == ADSX_IP) BCK(adsx::launch_scatter_f32(xnorm, pd, N, ix->onorm, s), "scatter norms");
         BCK(cudaStreamSynchronize(s), "build sync");
+    }
+    if (metric == ADSX_COSINE) {
+        unsigned err = 0;
+        BCK(cudaMemcpy(&err, ix->err, sizeof(unsigned), cudaMemcpyDeviceToHost), "read error word");
+        if (err & adsx::ERR_ZERO_ROW)
+            return cleanup(fail(ADSX_EINVAL, "a data row has zero norm (cosine similarity undefined)"));
     }
     BCK(cudaStreamSynchronize(s), "build sync");
 #undef BCK
     *out = reinterpret_cast<adsx_index *>(ix);
+    return ADSX_OK;
+}
+
+int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
+                     const float *centroids, int32_t nlist, const int32_t *assign,
+                     int32_t storage, void *stream, adsx_index **out)
+{
+    return build_impl(X, N, D, P, centroids, nlist, assign, storage, ADSX_L2, stream, out);
+}
+
+int adsx_build_index_metric(const float *X, int64_t N, int32_t D, const float *P,
+                            const float *centroids, int32_t nlist, const int32_t *assign,
+                            int32_t storage, int32_t metric, void *stream, adsx_index **out)
+{
+    return build_impl(X, N, D, P, centroids, nlist, assign, storage, metric, stream, out);
+}
+
+int adsx_index_metric(const adsx_index *index, int32_t *metric)
+{
+    const Index *ix = reinterpret_cast<const Index *>(index);
+    if (!ix || !metric) return fail(ADSX_EINVAL, "NULL argument");
+    *metric = ix->metric;
     return ADSX_OK;
 }
 
@@ -358,6 +427,7 @@ int adsx_free_index(adsx_index *index)
     cudaFree(ix->data);
     cudaFree(ix->rows32);
     cudaFree(ix->norms);
+    cudaFree(ix->onorm);
     cudaFree(ix->ids);
     cudaFree(ix->off);
     cudaFree(ix->tile_off);
@@ -422,6 +492,7 @@ int adsx_probe(const adsx_index *index, const float *Qv, int64_t nq, int32_t npr
     CK(stage_out(sc, probe_d2, (size_t)nq * nprobe, pd), "stage probe distances");
     CK(sc.get(&qrot, (size_t)nq * ix->Dp), "alloc q'");
     CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
+    CK(queries_before_probe(ix, qrot, nq, s), "normalise queries");
     CK(probe_queries(ix, qrot, nq, nprobe, pr.dev, pd.dev, sc), "probe");
     CK(copy_back(pr, s), "copy back");
     CK(copy_back(pd, s), "copy back");
@@ -461,10 +532,16 @@ static int search_impl(const adsx_index *index, const float *Qv, int64_t nq, int
     CK(mark(ix, 0, s), "event");
     CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
     CK(mark(ix, 1, s), "event");
+    CK(queries_before_probe(ix, qrot, nq, s), "normalise queries");
     CK(probe_queries(ix, qrot, nq, nprobe, probes, nullptr, sc), "probe");
     CK(mark(ix, 3, s), "event");
+    float *qnorm = nullptr;
+    CK(queries_after_probe(ix, qrot, nq, sc, &qnorm), "normalise queries");
 
     adsx::ScanArgs a;
+    a.metric = ix->metric;
+    a.onorm = ix->onorm;
+    a.qnorm = qnorm;
     a.data = ix->data;
     a.rows32 = ix->rows32;
     a.norms = ix->norms;
@@ -612,6 +689,7 @@ int adsx_search_batched(const adsx_index *index, const float *Qv, int64_t nq, co
     CK(mark(ix, 0, s), "event");
     CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
     CK(mark(ix, 1, s), "event");
+    CK(queries_before_probe(ix, qrot, nq, s), "normalise queries");
     {
         float *dist = nullptr;
         CK(sc.get(&dist, (size_t)nq * ix->nlist), "alloc distances");
@@ -625,8 +703,13 @@ int adsx_search_batched(const adsx_index *index, const float *Qv, int64_t nq, co
                                  ix->N / ix->nlist, items, item_first, n_items,
                                  qperm, oo.dev, out_off, ix->err, s), "plan");
     CK(mark(ix, 3, s), "event");
+    float *qnorm = nullptr;
+    CK(queries_after_probe(ix, qrot, nq, sc, &qnorm), "normalise queries");
 
     adsx::ScanArgs a;
+    a.metric = ix->metric;
+    a.onorm = ix->onorm;
+    a.qnorm = qnorm;
     a.data = ix->data;
     a.rows32 = ix->rows32;
     a.norms = ix->norms;
@@ -705,6 +788,7 @@ int adsx_dco_fixed_r(const adsx_index *index, const float *Qv, int64_t nq, const
     const Index *ix = reinterpret_cast<const Index *>(index);
     int rc = check_index(ix);
     if (rc) return rc;
+    if (ix->metric != ADSX_L2) return fail(ADSX_EINVAL, "adsx_dco_fixed_r supports L2 indexes only");
     if (nq < 0 || (nq > 0 && (!Qv || !r2 || !decisions))) return fail(ADSX_EINVAL, "bad arguments");
     if (nq > 65535) return fail(ADSX_EINVAL, "nq > 65535 in one fixed-r call");
     if ((rc = check_blocks(delta_d, eps0))) return rc;

@@ -206,3 +206,92 @@ cudaError_t launch_rotate(const float *X, int64_t N, int D, const float *P, int 
 }
 
 }  // namespace adsx
+
+// ---- cosine / inner-product support (Sec. 8, extension (1)): rows scaled
+// to unit norm, the constant centroid term of inner-product probing, and a
+// row-order -> CSR-order scatter of per-row values.
+namespace adsx {
+namespace {
+
+// One warp per row: the squared norm is accumulated in FP64, the row is
+// scaled by the FP32 value of 1/||x||.
+__global__ void __launch_bounds__(256) normalize_rows_kernel(float *X, int64_t N, int ld, int D,
+                                                             float *norms, unsigned *zero_err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < N; r += nw) {
+        float *x = X + r * ld;
+        double s = 0.0;
+        for (int j = lane; j < D; j += 32) s += (double)x[j] * (double)x[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const double n = sqrt(s);
+        if (lane == 0 && norms) norms[r] = (float)n;
+        if (n > 0.0) {
+            const float inv = (float)(1.0 / n);
+            for (int j = lane; j < D; j += 32) x[j] *= inv;
+        } else if (lane == 0 && zero_err) {
+            atomicOr(zero_err, ERR_ZERO_ROW);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(1024) fill_max_kernel(float *v, int n)
+{
+    __shared__ float wmax[32];
+    float m = -INFINITY;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmaxf(m, v[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : -INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) wmax[0] = m;
+    }
+    __syncthreads();
+    m = wmax[0];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = m;
+}
+
+__global__ void scatter_f32_kernel(const float *__restrict__ src, const int64_t *__restrict__ pos,
+                                   int64_t N, float *__restrict__ dst)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[pos[i]] = src[i];
+}
+
+}  // namespace
+
+cudaError_t launch_normalize_rows(float *X, int64_t N, int ld, int D, float *norms,
+                                  unsigned *zero_err, cudaStream_t s)
+{
+    if (N <= 0) return cudaSuccess;
+    const int64_t blocks = (N + 7) / 8;
+    normalize_rows_kernel<<<(unsigned)(blocks < 152 * 64 ? blocks : 152 * 64), 256, 0, s>>>(
+        X, N, ld, D, norms, zero_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_max(float *v, int n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    fill_max_kernel<<<1, 1024, 0, s>>>(v, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_f32(const float *src, const int64_t *pos, int64_t N, float *dst,
+                               cudaStream_t s)
+{
+    if (N <= 0) return cudaSuccess;
+    const int64_t blocks = (N + 255) / 256;
+    scatter_f32_kernel<<<(unsigned)(blocks < 152 * 32 ? blocks : 152 * 32), 256, 0, s>>>(src, pos,
+                                                                                       N, dst);
+    return cudaGetLastError();
+}
+
+}  // namespace adsx

@@ -90,6 +90,7 @@ extern "C" int adsx_search_noalloc(const adsx_index *index, const float *Qv, int
 {
     const adsx::Index *ix = reinterpret_cast<const adsx::Index *>(index);
     if (!ix) return nerr(ADSX_EINVAL, "index is NULL");
+    if (ix->metric != ADSX_L2) return nerr(ADSX_EINVAL, "adsx_search_noalloc supports L2 indexes only");
     cudaError_t e = cudaSetDevice(ix->device);
     if (e != cudaSuccess) return nerr(ADSX_ECUDA, cudaGetErrorString(e));
     if (nq < 0) return nerr(ADSX_EINVAL, "nq < 0");

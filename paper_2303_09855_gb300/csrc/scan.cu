@@ -78,7 +78,30 @@ __device__ __forceinline__ bool pair_less(float d1, int i1, float d2, int i2)
     return d1 < d2 || (d1 == d2 && i1 < i2);
 }
 
-template <typename T>
+// Order-preserving map of a float key to unsigned (inner-product keys are
+// negative), for the atomicMin that shares r between the splits of a query;
+// 0xffffffff (the cleared value) means "no bound yet".
+__device__ __forceinline__ unsigned key_to_ord(float k)
+{
+    const unsigned u = __float_as_uint(k);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord_to_key(unsigned m)
+{
+    return __uint_as_float((m & 0x80000000u) ? (m & 0x7fffffffu) : ~m);
+}
+
+// The value returned for a key: L2 the squared distance; cosine the
+// similarity 1 - ||x^ - q^||^2 / 2; inner product <o,q> (key = -<o,q>).
+// Empty slots: +inf for L2, -inf for similarities.
+__device__ __forceinline__ float out_value(int metric, float key, bool has)
+{
+    if (metric == ADSX_L2) return has ? key : INFINITY;
+    if (!has) return -INFINITY;
+    return metric == ADSX_COSINE ? fmaf(-0.5f, key, 1.f) : -key;
+}
+
+template <typename T, bool IP>
 struct Warp {
     const ScanArgs *a;
     float *qv;
@@ -95,14 +118,16 @@ struct Warp {
     int K, C, S;               // this item's K, buffer capacity, splits of its query
     int head, cnt;             // pending ring (warp-uniform)
     int count;                 // candidate buffer fill (warp-uniform)
-    float r2;                  // this warp's K-th distance (warp-uniform)
+    float r2;                  // this warp's K-th key (warp-uniform; squared distance, or
+                               // -<o,q> for inner products)
+    float qn;                  // ||q|| (inner-product indexes)
     unsigned dims;             // per lane, dims sampled by this item
 };
 
 // Sorts the candidate buffer by (distance, id), keeps the first K and sets
 // r^2 to the K-th distance once K are held.
-template <typename T>
-__device__ void compact(Warp<T> &w)
+template <typename T, bool IP>
+__device__ void compact(Warp<T, IP> &w)
 {
     const int C = w.C, K = w.K;
     for (int k = w.count + w.lane; k < C; k += 32) {
@@ -134,19 +159,19 @@ __device__ void compact(Warp<T> &w)
         const float r2 = w.ed[K - 1];
         if (r2 < w.r2) {
             w.r2 = r2;
-            if (w.S > 1 && w.lane == 0) atomicMin(w.a->r2g + w.q, __float_as_uint(r2));
+            if (w.S > 1 && w.lane == 0) atomicMin(w.a->r2g + w.q, key_to_ord(r2));
         }
     }
     __syncwarp();
 }
 
-template <typename T>
-__device__ __forceinline__ float current_r2(const Warp<T> &w)
+template <typename T, bool IP>
+__device__ __forceinline__ float current_r2(const Warp<T, IP> &w)
 {
     float r2 = w.r2;
     if (w.S > 1) {
         const unsigned g = *((volatile const unsigned *)(w.a->r2g + w.q));
-        if (g <= 0x7f800000u) r2 = fminf(r2, __uint_as_float(g));
+        if (g != 0xffffffffu) r2 = fminf(r2, ord_to_key(g));
     }
     return r2;
 }
@@ -154,8 +179,8 @@ __device__ __forceinline__ float current_r2(const Warp<T> &w)
 // 16-bit storage: exact FP32 distance of every lane with `need`, recomputed
 // from the FP32 row copy, one candidate at a time by the whole warp (each lane
 // a 4-dim slice, then a butterfly sum whose result is the same on all lanes).
-template <typename T>
-__device__ __forceinline__ float recheck_exact(const Warp<T> &w, bool need, int pos, float S)
+template <typename T, bool IP>
+__device__ __forceinline__ float recheck_exact(const Warp<T, IP> &w, bool need, int pos, float S)
 {
     const ScanArgs &a = *w.a;
     unsigned mask = __ballot_sync(FULL, need);
@@ -182,8 +207,8 @@ __device__ __forceinline__ float recheck_exact(const Warp<T> &w, bool need, int 
 }
 
 // Appends the lanes with `surv` to the pending ring (lane order).
-template <typename T>
-__device__ __forceinline__ void enqueue(Warp<T> &w, bool surv, float S, int blk, int pos,
+template <typename T, bool IP>
+__device__ __forceinline__ void enqueue(Warp<T, IP> &w, bool surv, float S, int blk, int pos,
                                         long long off, int st)
 {
     const unsigned sm = __ballot_sync(FULL, surv);
@@ -203,15 +228,24 @@ __device__ __forceinline__ void enqueue(Warp<T> &w, bool surv, float S, int blk,
 // `pos` is the candidate's CSR row, `off` the element offset of its block
 // `blk` and `st` its block stride.  Returns whether the candidate continues;
 // with `push` it is also queued.
-template <typename T>
-__device__ __forceinline__ bool after_step(Warp<T> &w, bool valid, float S, int blk, int pos,
+template <typename T, bool IP>
+__device__ __forceinline__ bool after_step(Warp<T, IP> &w, bool valid, float S, int blk, int pos,
                                            long long off, int st, float r2, bool push)
 {
     const ScanArgs &a = *w.a;
     const bool fin = valid && blk >= a.nblk;
+    // Squared threshold on the stored vectors: r^2 itself (L2, cosine), or
+    // for inner products the per-object 2 - 2 r / (||o|| ||q||) on the
+    // normalised vectors, r = -r2 the K-th largest inner product held
+    // (Sec. 8, extension (1)); a negative threshold rejects at once.
+    float thr = r2, onq = 0.f;
+    if (IP && valid) {
+        onq = a.onorm[pos] * w.qn;
+        thr = 2.f + 2.f * r2 / onq;
+    }
     bool surv = false;
     if (valid && !fin) {
-        if (a.test_on && S > r2 * w.ftab[blk]) {
+        if (a.test_on && S > thr * w.ftab[blk]) {
             const int d = blk * BLK;
             w.dims += (unsigned)(d < a.D ? d : a.D);
         } else {
@@ -228,24 +262,26 @@ __device__ __forceinline__ bool after_step(Warp<T> &w, bool valid, float S, int 
         // the low precision moves reject decisions only, never a result.
         bool need = false;
         if (fin) {
-            need = !(r2 < INFINITY);
-            if (!need) {
-                const float bound = (sqrtf(r2) + Roundoff<T>::u * a.norms[pos]) * 1.0001f;
+            need = !(thr < INFINITY);
+            if (!need && thr >= 0.f) {
+                const float bound = (sqrtf(thr) + Roundoff<T>::u * a.norms[pos]) * 1.0001f;
                 need = sqrtf(S) <= bound;
             }
         }
         S = recheck_exact(w, need, pos, S);
         cand = need;
     }
-    // Case 3 positives into the candidate buffer.
-    const bool want = cand && S <= r2;
+    // Case 3 positives into the candidate buffer; the key is the squared
+    // distance, or -<o,q> = -||o|| ||q|| (1 - S/2) for inner products.
+    const float key = IP ? -(onq * fmaf(-0.5f, S, 1.f)) : S;
+    const bool want = cand && key <= r2;
     const unsigned wm = __ballot_sync(FULL, want);
     if (wm) {
         const int nw = __popc(wm);
         if (w.count + nw > w.C) compact(w);
         if (want) {
             const int k = w.count + __popc(wm & ((1u << w.lane) - 1u));
-            w.ed[k] = S;
+            w.ed[k] = key;
             w.ei[k] = a.ids[pos];
         }
         w.count += nw;
@@ -421,8 +457,8 @@ __device__ __forceinline__ float tile_step(const T *cb, int64_t stride, int m0, 
 
 // Advances the first nb (<= 32) pending candidates by one delta_d step each,
 // NL lanes per candidate, then tests them (after_step) one per lane.
-template <typename T>
-__device__ __forceinline__ void process_pending(Warp<T> &w, int nb)
+template <typename T, bool IP>
+__device__ __forceinline__ void process_pending(Warp<T, IP> &w, int nb)
 {
     constexpr int NL = Split<T>::NL, NG = 32 / NL, PW = BLK / NL;
     typedef typename Split<T>::V V;
@@ -506,7 +542,7 @@ __device__ __forceinline__ void process_pending(Warp<T> &w, int nb)
 template <typename T> struct MinBlocks { static constexpr int value = ADSX_SCAN_MINBLOCKS_H; };
 template <> struct MinBlocks<float> { static constexpr int value = ADSX_SCAN_MINBLOCKS; };
 
-template <typename T>
+template <typename T, bool IP>
 __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(ScanArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -516,7 +552,7 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
     __shared__ float s_ftab[256];
     for (int b = threadIdx.x; b <= a.nblk && b < 256; b += THREADS) s_ftab[b] = a.ftab[b];
     __syncthreads();
-    Warp<T> w;
+    Warp<T, IP> w;
     w.a = &a;
     w.ftab = s_ftab;
     w.qv = base + wc.qv;
@@ -564,6 +600,7 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
         w.head = w.cnt = 0;
         w.count = 0;
         w.r2 = INFINITY;
+        w.qn = IP ? a.qnorm[q] : 1.f;
         w.dims = 0u;
         __syncwarp();
 
@@ -572,13 +609,10 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
         // it).  With S > nprobe (e.g. nlist = 1, a linear scan), split s works
         // on slot s % nprobe alone, taking every js-th 32-member tile of it
         // from tile s / nprobe, js being the number of splits on that slot.
-        const bool wide = S > nprobe;
-        const int p0 = wide ? s % nprobe : s;
-        const int pstep = wide ? nprobe : S;
-        const int j0 = wide ? s / nprobe : 0;
-        const int js = wide ? (S - 1 - p0) / nprobe + 1 : 1;
-        for (int p = p0; p < nprobe; p += pstep) {
-            const int c = a.probes[q * (a.probe_stride ? a.probe_stride : a.nprobe) + p];
+        // (Two inlined copies: the common one has constant tile steps.)
+        const int pstride = a.probe_stride ? a.probe_stride : a.nprobe;
+        auto scan_slot = [&](int p, int j0, int js) {
+            const int c = a.probes[q * pstride + p];
             const int o = (int)a.off[c];
             const int n = (int)(a.off[c + 1] - o);
             const T *cb = static_cast<const T *>(a.data) + (int64_t)o * a.Dp;
@@ -591,24 +625,30 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
                 const int m = m0 + own_slot<Split<T>::NL>(lane);
                 bool live = m < n;
                 unsigned lm = __ballot_sync(FULL, live);
-                float S = 0.f;
+                float Sd = 0.f;
                 int blk = 0;
                 for (;;) {
                     const float r2 = current_r2(w);
                     const int e = blk + a.db < a.nblk ? blk + a.db : a.nblk;
-                    S += tile_step(cb, stride, m0, blk, e, lm, w.qv, lane);
+                    Sd += tile_step(cb, stride, m0, blk, e, lm, w.qv, lane);
                     blk = e;
                     const long long off = cbase + blk * stride + (long long)m * BLK;
-                    live = after_step(w, live, S, blk, o + m, off, (int)stride, r2, false);
+                    live = after_step(w, live, Sd, blk, o + m, off, (int)stride, r2, false);
                     lm = __ballot_sync(FULL, live);
                     if (lm == 0u) break;
                     if (__popc(lm) < DENSE_MIN) {
-                        enqueue(w, live, S, blk, o + m, off, (int)stride);
+                        enqueue(w, live, Sd, blk, o + m, off, (int)stride);
                         break;
                     }
                 }
                 while (w.cnt >= 32) process_pending(w, 32);
             }
+        };
+        if (S <= nprobe) {
+            for (int p = s; p < nprobe; p += S) scan_slot(p, 0, 1);
+        } else {
+            const int p0 = s % nprobe;
+            scan_slot(p0, s / nprobe, (S - 1 - p0) / nprobe + 1);
         }
         while (w.cnt > 0) process_pending(w, w.cnt < 32 ? w.cnt : 32);
         compact(w);
@@ -625,7 +665,7 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
             for (int k = lane; k < K; k += 32) {
                 const bool has = k < w.count;
                 a.out_ids[ob + k] = has ? (int64_t)w.ei[k] : (int64_t)-1;
-                a.out_d2[ob + k] = has ? w.ed[k] : INFINITY;
+                a.out_d2[ob + k] = out_value(a.metric, has ? w.ed[k] : 0.f, has);
             }
             if (lane == 0 && a.out_dims) a.out_dims[q] = (int64_t)wd;
         } else {
@@ -698,7 +738,7 @@ __global__ void __launch_bounds__(256) finalize_topk_kernel(ScanArgs a)
         for (int k = threadIdx.x; k < K; k += blockDim.x) {
             const bool has = sd[k] != INFINITY || si[k] != 0x7fffffff;
             a.out_ids[ob + k] = has ? (int64_t)si[k] : (int64_t)-1;
-            a.out_d2[ob + k] = has ? sd[k] : INFINITY;
+            a.out_d2[ob + k] = out_value(a.metric, sd[k], has);
         }
         __syncthreads();
     }
@@ -809,11 +849,12 @@ int scan_items_target(int device, int items_per_sm)
 }
 
 template <typename T>
-static int occupancy(size_t smem)
+static int occupancy(size_t smem, bool ip)
 {
     int per = 0;
-    cudaFuncSetAttribute(ads_scan_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ads_scan_kernel<T>, THREADS, smem);
+    auto k = ip ? ads_scan_kernel<T, true> : ads_scan_kernel<T, false>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, THREADS, smem);
     return per;
 }
 
@@ -822,8 +863,9 @@ int ads_scan_grid(const ScanArgs &a, int device)
     int nsm = 0, per = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
     size_t smem = scan_smem_bytes(a);
-    per = a.storage == ADSX_F32 ? occupancy<float>(smem)
-        : a.storage == ADSX_BF16 ? occupancy<__nv_bfloat16>(smem) : occupancy<__half>(smem);
+    const bool ip = a.metric == ADSX_IP;
+    per = a.storage == ADSX_F32 ? occupancy<float>(smem, ip)
+        : a.storage == ADSX_BF16 ? occupancy<__nv_bfloat16>(smem, ip) : occupancy<__half>(smem, ip);
     if (per < 1) per = 1;
     int64_t g = (int64_t)nsm * per;
     const int64_t need = ((int64_t)a.n_items + WARPS - 1) / WARPS;
@@ -841,22 +883,15 @@ cudaError_t launch_ads_scan(const ScanArgs &a, int grid, cudaStream_t s)
 {
     if (a.n_items <= 0) return cudaSuccess;
     size_t smem = scan_smem_bytes(a);
-    if (a.storage == ADSX_F32) {
-        cudaError_t e = cudaFuncSetAttribute(ads_scan_kernel<float>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        ads_scan_kernel<float><<<grid, THREADS, smem, s>>>(a);
-    } else if (a.storage == ADSX_BF16) {
-        cudaError_t e = cudaFuncSetAttribute(ads_scan_kernel<__nv_bfloat16>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        ads_scan_kernel<__nv_bfloat16><<<grid, THREADS, smem, s>>>(a);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(ads_scan_kernel<__half>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        ads_scan_kernel<__half><<<grid, THREADS, smem, s>>>(a);
-    }
+    const bool ip = a.metric == ADSX_IP;
+    void (*k)(ScanArgs);
+    if (a.storage == ADSX_F32) k = ip ? ads_scan_kernel<float, true> : ads_scan_kernel<float, false>;
+    else if (a.storage == ADSX_BF16)
+        k = ip ? ads_scan_kernel<__nv_bfloat16, true> : ads_scan_kernel<__nv_bfloat16, false>;
+    else k = ip ? ads_scan_kernel<__half, true> : ads_scan_kernel<__half, false>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
