@@ -2,19 +2,23 @@
 // N_probe clusters whose centroids are nearest to the query), ordered by
 // (squared centroid distance, cluster id).
 //
-// One 256-thread block per query row.  The row's distances are turned into
-// order-preserving 32-bit keys (bit patterns of non-negative floats) in shared
-// memory; a 4-pass, 8-bit radix select finds the exact key T of the
-// nprobe-th smallest distance and how many keys equal to T are still needed;
-// keys below T are gathered, keys equal to T are taken in ascending cluster id
-// by one warp (ballot order), and the nprobe winners are bitonic-sorted as
-// 64-bit (key, id) words.
+// One warp per query row, several per block, no block barriers.  The row's
+// distances become order-preserving 32-bit keys (bit patterns of non-negative
+// floats) in the warp's shared memory; the row's smallest and largest key
+// give the high bits every key shares, and radix passes of up to 8 bits over
+// the remaining bits (warp-aggregated shared-memory histograms) find the
+// exact key T of the nprobe-th smallest distance and how many keys equal to T
+// are needed (or stop early when a digit's bin is needed whole).  Keys below
+// T and the needed keys equal to T (ascending cluster id) are gathered by
+// ballot in index order, and the warp bitonic-sorts the
+// nprobe winners as 64-bit (key, id) words.
 #include "adsx_internal.cuh"
 
 namespace adsx {
 namespace {
 
-constexpr int ST = 256;
+constexpr int MAXW = 4;                 // warps per block (fewer for large rows)
+constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ unsigned dist_key(float v)
 {
@@ -24,57 +28,106 @@ __device__ __forceinline__ unsigned dist_key(float v)
     return __float_as_uint(v);
 }
 
-__global__ void __launch_bounds__(ST) select_nprobe_kernel(const float *__restrict__ dist,
-                                                           int64_t nq, int nlist, int pstride,
-                                                           int P2, int32_t *__restrict__ probes,
-                                                           float *__restrict__ pd2,
-                                                           const int32_t *__restrict__ nprobe_q)
+// One warp's shared-memory region: winners (P2 x 8 bytes), histogram
+// (256 x 4), keys (nlist x 4); each part starts on a 16-byte boundary (the
+// keys are written with 16-byte stores).
+__host__ __device__ inline size_t sel_bytes(int P2) { return ((size_t)P2 * 8 + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t warp_region(int nlist, int P2)
+{
+    return sel_bytes(P2) + 1024 + (size_t)((nlist + 3) & ~3) * 4;
+}
+
+__global__ void __launch_bounds__(MAXW * 32) select_nprobe_kernel(
+    const float *__restrict__ dist, int64_t nq, int nlist, int pstride, int P2, int W,
+    int32_t *__restrict__ probes, float *__restrict__ pd2, const int32_t *__restrict__ nprobe_q)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    unsigned long long *sel = reinterpret_cast<unsigned long long *>(smraw);   // P2
-    unsigned *key = reinterpret_cast<unsigned *>(sel + P2);                    // nlist
-    __shared__ unsigned hist[256];
-    __shared__ unsigned s_prefix, s_remaining, s_nsel;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char *base = smraw + warp_region(nlist, P2) * warp;
+    unsigned long long *sel = reinterpret_cast<unsigned long long *>(base);
+    unsigned *hist = reinterpret_cast<unsigned *>(base + sel_bytes(P2));
+    unsigned *key = hist + 256;
+    const unsigned below = (1u << lane) - 1u;
 
-    for (int64_t q = blockIdx.x; q < nq; q += gridDim.x) {
+    for (int64_t q = (int64_t)blockIdx.x * W + warp; q < nq; q += (int64_t)gridDim.x * W) {
         int nprobe = pstride;
         if (nprobe_q) {                     // per-query count, clamped to [1, pstride]
             nprobe = nprobe_q[q];
             nprobe = nprobe < 1 ? 1 : (nprobe > pstride ? pstride : nprobe);
         }
         const float *row = dist + q * nlist;
-        for (int i = tid; i < nlist; i += ST) key[i] = dist_key(row[i]);
-        if (tid == 0) {
-            s_prefix = 0;
-            s_remaining = (unsigned)nprobe;
-        }
-        __syncthreads();
-        unsigned mask = 0;
-        for (int shift = 24; shift >= 0; shift -= 8) {
-            hist[tid] = 0;
-            __syncthreads();
-            const unsigned prefix = s_prefix;
-            // Keys that still match the prefix vote for their digit; lanes of a
-            // warp with the same digit are merged (match.any) into one atomic,
-            // since most keys share the high digits of the float's exponent.
-            for (int i0 = warp * 32; i0 < nlist; i0 += ST) {
-                const int i = i0 + lane;
-                unsigned bin = 256u;                    // no vote
-                if (i < nlist) {
-                    const unsigned u = key[i];
-                    if ((u & mask) == prefix) bin = (u >> shift) & 255u;
+        unsigned kmin = 0xffffffffu, kmax = 0u;
+        if ((nlist & 3) == 0) {
+            // 16-byte loads, eight in flight per lane before any use
+            const float4 *r4 = reinterpret_cast<const float4 *>(row);
+            const int n4 = nlist >> 2;
+            for (int i0 = lane; i0 < n4; i0 += 32 * 8) {
+                float4 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (i0 + 32 * u < n4) v[u] = __ldg(r4 + i0 + 32 * u);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = i0 + 32 * u;
+                    if (i < n4) {
+                        const uint4 k4 = make_uint4(dist_key(v[u].x), dist_key(v[u].y),
+                                                    dist_key(v[u].z), dist_key(v[u].w));
+                        reinterpret_cast<uint4 *>(key)[i] = k4;
+                        kmin = min(min(kmin, min(k4.x, k4.y)), min(k4.z, k4.w));
+                        kmax = max(max(kmax, max(k4.x, k4.y)), max(k4.z, k4.w));
+                    }
                 }
-                const unsigned peers = __match_any_sync(0xffffffffu, bin);
-                if (bin < 256u && lane == __ffs(peers) - 1)
-                    atomicAdd(&hist[bin], (unsigned)__popc(peers));
             }
-            __syncthreads();
-            if (warp == 0) {
-                // warp-wide search of the bin holding the rem-th key: each lane
-                // owns 8 consecutive bins, a shuffle scan gives the counts before
-                // them, and the one lane whose range crosses rem finds the bin.
-                const unsigned rem = s_remaining;
+        } else {
+            for (int i0 = lane; i0 < nlist; i0 += 32 * 8) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (i0 + 32 * u < nlist) v[u] = __ldg(row + i0 + 32 * u);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = i0 + 32 * u;
+                    if (i < nlist) {
+                        const unsigned k = dist_key(v[u]);
+                        key[i] = k;
+                        kmin = k < kmin ? k : kmin;
+                        kmax = k > kmax ? k : kmax;
+                    }
+                }
+            }
+        }
+        kmin = __reduce_min_sync(FULL, kmin);
+        kmax = __reduce_max_sync(FULL, kmax);
+        __syncwarp();
+
+        // Radix select over the bits below the common prefix of all keys.
+        unsigned prefix = kmin, rem = (unsigned)nprobe;
+        int cut = -1;     // >= 0: every key whose bits above `cut` are <= prefix's is taken
+        if (kmin != kmax) {
+            const int hb = 31 - __clz(kmin ^ kmax);             // highest differing bit
+            unsigned mask = hb == 31 ? 0u : ~((2u << hb) - 1u);  // bits already fixed
+            prefix = kmin & mask;
+            for (int top = hb; top >= 0; top -= 8) {
+                const int shift = top >= 7 ? top - 7 : 0;
+                const unsigned dmask = (2u << (top - shift)) - 1u;  // <= 8 bits
+#pragma unroll
+                for (int j = 0; j < 8; ++j) hist[lane * 8 + j] = 0u;
+                __syncwarp();
+                for (int i0 = 0; i0 < nlist; i0 += 32) {
+                    const int i = i0 + lane;
+                    unsigned bin = 256u;                        // no vote
+                    if (i < nlist) {
+                        const unsigned u = key[i];
+                        if ((u & mask) == prefix) bin = (u >> shift) & dmask;
+                    }
+                    // lanes with the same digit merge into one atomic
+                    const unsigned peers = __match_any_sync(FULL, bin);
+                    if (bin < 256u && lane == __ffs(peers) - 1)
+                        atomicAdd(&hist[bin], (unsigned)__popc(peers));
+                }
+                __syncwarp();
+                // the bin holding the rem-th key: each lane owns 8 bins, a
+                // shuffle scan gives the counts before them
                 unsigned h[8], own = 0;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
@@ -84,75 +137,77 @@ __global__ void __launch_bounds__(ST) select_nprobe_kernel(const float *__restri
                 unsigned incl = own;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
-                    const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+                    const unsigned v = __shfl_up_sync(FULL, incl, o);
                     if (lane >= o) incl += v;
                 }
-                unsigned cum = incl - own;
-                if (cum < rem && incl >= rem) {
+                unsigned cum = incl - own, bin = 0, nrem = 0, cnt = 0;
+                const bool found = cum < rem && incl >= rem;
+                if (found) {
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         if (cum + h[j] >= rem) {
-                            s_prefix = prefix | ((unsigned)(lane * 8 + j) << shift);
-                            s_remaining = rem - cum;
+                            bin = (unsigned)(lane * 8 + j);
+                            nrem = rem - cum;
+                            cnt = h[j];
                             break;
                         }
                         cum += h[j];
                     }
                 }
-            }
-            mask |= 255u << shift;
-            __syncthreads();
-        }
-        const unsigned T = s_prefix;
-        const unsigned need_eq = s_remaining;
-        if (tid == 0) s_nsel = 0;
-        __syncthreads();
-        for (int i = tid; i < nlist; i += ST) {
-            unsigned u = key[i];
-            if (u < T) {
-                unsigned p = atomicAdd(&s_nsel, 1u);
-                sel[p] = ((unsigned long long)u << 32) | (unsigned)i;
-            }
-        }
-        __syncthreads();
-        if (warp == 0) {
-            const unsigned base = s_nsel;
-            unsigned taken = 0;
-            for (int i0 = 0; i0 < nlist && taken < need_eq; i0 += 32) {
-                int i = i0 + lane;
-                bool eq = (i < nlist) && key[i] == T;
-                unsigned b = __ballot_sync(0xffffffffu, eq);
-                unsigned r = __popc(b & ((1u << lane) - 1u));
-                if (eq && taken + r < need_eq)
-                    sel[base + taken + r] = ((unsigned long long)T << 32) | (unsigned)i;
-                taken += __popc(b);
+                const int src = __ffs(__ballot_sync(FULL, found)) - 1;
+                bin = __shfl_sync(FULL, bin, src);
+                rem = __shfl_sync(FULL, nrem, src);
+                cnt = __shfl_sync(FULL, cnt, src);
+                prefix |= bin << shift;
+                mask |= dmask << shift;
+                __syncwarp();
+                if (shift == 0) break;
+                if (cnt == rem) {       // the whole bin is needed: no further digits
+                    cut = shift;
+                    break;
+                }
             }
         }
-        __syncthreads();
-        for (int i = nprobe + tid; i < P2; i += ST) sel[i] = ~0ull;
-        __syncthreads();
+        const unsigned T = prefix;          // key of the nprobe-th smallest distance
+        const unsigned need_eq = rem;       // keys equal to T still needed (>= 1)
+
+        // Gather in index order: keys below T, and the first need_eq keys == T.
+        unsigned nsel = 0, eq_seen = 0;
+        for (int i0 = 0; i0 < nlist; i0 += 32) {
+            const int i = i0 + lane;
+            const unsigned u = i < nlist ? key[i] : 0xffffffffu;
+            const bool lt = i < nlist && (cut >= 0 ? (u >> cut) <= (T >> cut) : u < T);
+            const bool eq = i < nlist && cut < 0 && u == T;
+            const unsigned be = __ballot_sync(FULL, eq);
+            const bool take = lt || (eq && eq_seen + __popc(be & below) < need_eq);
+            const unsigned bt = __ballot_sync(FULL, take);
+            if (take) sel[nsel + __popc(bt & below)] = ((unsigned long long)u << 32) | (unsigned)i;
+            nsel += __popc(bt);
+            eq_seen += __popc(be);
+        }
+        for (int i = (int)nsel + lane; i < P2; i += 32) sel[i] = ~0ull;
+        __syncwarp();
         for (int size = 2; size <= P2; size <<= 1) {
             for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = tid; i < P2; i += ST) {
-                    int j = i ^ stride;
+                for (int i = lane; i < P2; i += 32) {
+                    const int j = i ^ stride;
                     if (j > i) {
-                        unsigned long long a = sel[i], b = sel[j];
-                        bool up = (i & size) == 0;
-                        if ((a > b) == up) {
-                            sel[i] = b;
-                            sel[j] = a;
+                        const unsigned long long x = sel[i], y = sel[j];
+                        if ((x > y) == ((i & size) == 0)) {
+                            sel[i] = y;
+                            sel[j] = x;
                         }
                     }
                 }
-                __syncthreads();
+                __syncwarp();
             }
         }
-        for (int p = tid; p < nprobe; p += ST) {
-            unsigned long long v = sel[p];
+        for (int p = lane; p < nprobe; p += 32) {
+            const unsigned long long v = sel[p];
             probes[q * pstride + p] = (int32_t)(v & 0xffffffffu);
             if (pd2) pd2[q * pstride + p] = __uint_as_float((unsigned)(v >> 32));
         }
-        __syncthreads();
+        __syncwarp();                       // before the next row reuses the region
     }
 }
 
@@ -165,14 +220,17 @@ cudaError_t launch_select_nprobe(const float *dist, int64_t nq, int nlist, int n
     if (nq <= 0) return cudaSuccess;
     int P2 = 1;
     while (P2 < nprobe) P2 <<= 1;
-    size_t smem = (size_t)P2 * 8 + (size_t)nlist * 4;
+    const size_t per = warp_region(nlist, P2);
+    int W = (int)((200u << 10) / per);
+    W = W > MAXW ? MAXW : (W < 1 ? 1 : W);
+    const size_t smem = per * W;
     cudaError_t e = cudaFuncSetAttribute(select_nprobe_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int64_t grid = nq < 152 * 8 ? nq : 152 * 8;
-    select_nprobe_kernel<<<(unsigned)grid, ST, smem, s>>>(dist, nq, nlist, nprobe, P2, probes,
-                                                          probe_d2, nprobe_q);
+    int64_t grid = (nq + W - 1) / W;
+    if (grid > 152 * 16) grid = 152 * 16;
+    select_nprobe_kernel<<<(unsigned)grid, W * 32, smem, s>>>(dist, nq, nlist, nprobe, P2, W, probes,
+                                                              probe_d2, nprobe_q);
     return cudaGetLastError();
 }
 
