@@ -2,7 +2,9 @@
 // N_probe clusters whose centroids are nearest to the query), ordered by
 // (squared centroid distance, cluster id).
 //
-// One warp per query row, several per block, no block barriers.  The row's
+// One warp per query row, several per block, no block barriers.  For
+// nprobe <= 64 a bound-and-gather path is taken (see the kernel); otherwise,
+// or when ties overflow it, a radix select runs: the row's
 // distances become order-preserving 32-bit keys (bit patterns of non-negative
 // floats) in the warp's shared memory; the row's smallest and largest key
 // give the high bits every key shares, and radix passes of up to 8 bits over
@@ -28,10 +30,46 @@ __device__ __forceinline__ unsigned dist_key(float v)
     return __float_as_uint(v);
 }
 
+// Keeps t0 <= t1 <= t2 <= t3, the lane's four smallest keys so far.
+__device__ __forceinline__ void keep4(unsigned x, unsigned &t0, unsigned &t1, unsigned &t2,
+                                      unsigned &t3)
+{
+    unsigned m;
+    m = min(t0, x); x = max(t0, x); t0 = m;
+    m = min(t1, x); x = max(t1, x); t1 = m;
+    m = min(t2, x); x = max(t2, x); t2 = m;
+    t3 = min(t3, x);
+}
+
+// Bitonic sort of n (a power of two) entries of `v` by the warp.
+template <typename K>
+__device__ __forceinline__ void warp_sort(K *v, int n, int lane)
+{
+    for (int size = 2; size <= n; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = lane; i < n; i += 32) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const K x = v[i], y = v[j];
+                    if ((x > y) == ((i & size) == 0)) {
+                        v[i] = y;
+                        v[j] = x;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
 // One warp's shared-memory region: winners (P2 x 8 bytes), histogram
 // (256 x 4), keys (nlist x 4); each part starts on a 16-byte boundary (the
 // keys are written with 16-byte stores).
-__host__ __device__ inline size_t sel_bytes(int P2) { return ((size_t)P2 * 8 + 15) & ~(size_t)15; }
+constexpr int FAST_CAP = 128;   // candidate capacity of the bound-and-gather path (nprobe <= 64)
+__host__ __device__ inline size_t sel_bytes(int P2)
+{
+    return ((size_t)(P2 > FAST_CAP ? P2 : FAST_CAP) * 8 + 15) & ~(size_t)15;
+}
 __host__ __device__ inline size_t warp_region(int nlist, int P2)
 {
     return sel_bytes(P2) + 1024 + (size_t)((nlist + 3) & ~3) * 4;
@@ -57,6 +95,12 @@ __global__ void __launch_bounds__(MAXW * 32) select_nprobe_kernel(
         }
         const float *row = dist + q * nlist;
         unsigned kmin = 0xffffffffu, kmax = 0u;
+        // nprobe <= 64: the nprobe-th smallest of the 128 lane-wise four
+        // smallest keys bounds the nprobe-th smallest key from above (it is
+        // the nprobe-th of a subset), so gathering every key up to it and
+        // sorting those by (key, id) gives the exact answer.
+        const bool fast = nprobe <= 64;
+        unsigned t0 = 0xffffffffu, t1 = 0xffffffffu, t2 = 0xffffffffu, t3 = 0xffffffffu;
         if ((nlist & 3) == 0) {
             // 16-byte loads, eight in flight per lane before any use
             const float4 *r4 = reinterpret_cast<const float4 *>(row);
@@ -75,6 +119,12 @@ __global__ void __launch_bounds__(MAXW * 32) select_nprobe_kernel(
                         reinterpret_cast<uint4 *>(key)[i] = k4;
                         kmin = min(min(kmin, min(k4.x, k4.y)), min(k4.z, k4.w));
                         kmax = max(max(kmax, max(k4.x, k4.y)), max(k4.z, k4.w));
+                        if (fast) {
+                            keep4(k4.x, t0, t1, t2, t3);
+                            keep4(k4.y, t0, t1, t2, t3);
+                            keep4(k4.z, t0, t1, t2, t3);
+                            keep4(k4.w, t0, t1, t2, t3);
+                        }
                     }
                 }
             }
@@ -92,6 +142,7 @@ __global__ void __launch_bounds__(MAXW * 32) select_nprobe_kernel(
                         key[i] = k;
                         kmin = k < kmin ? k : kmin;
                         kmax = k > kmax ? k : kmax;
+                        if (fast) keep4(k, t0, t1, t2, t3);
                     }
                 }
             }
@@ -99,6 +150,41 @@ __global__ void __launch_bounds__(MAXW * 32) select_nprobe_kernel(
         kmin = __reduce_min_sync(FULL, kmin);
         kmax = __reduce_max_sync(FULL, kmax);
         __syncwarp();
+        if (fast) {
+            hist[lane * 4 + 0] = t0;
+            hist[lane * 4 + 1] = t1;
+            hist[lane * 4 + 2] = t2;
+            hist[lane * 4 + 3] = t3;
+            __syncwarp();
+            warp_sort(hist, 128, lane);
+            const unsigned Tb = hist[nprobe - 1];
+            unsigned c = 0;
+            for (int i0 = 0; i0 < nlist && c <= (unsigned)FAST_CAP; i0 += 32) {
+                const int i = i0 + lane;
+                const unsigned u = i < nlist ? key[i] : 0xffffffffu;
+                const bool take = i < nlist && u <= Tb;
+                const unsigned bt = __ballot_sync(FULL, take);
+                const unsigned at = c + __popc(bt & below);
+                if (take && at < (unsigned)FAST_CAP)
+                    sel[at] = ((unsigned long long)u << 32) | (unsigned)i;
+                c += __popc(bt);
+            }
+            if (c <= (unsigned)FAST_CAP) {
+                int n2 = 32;
+                while (n2 < (int)c) n2 <<= 1;
+                for (int i = (int)c + lane; i < n2; i += 32) sel[i] = ~0ull;
+                __syncwarp();
+                warp_sort(sel, n2, lane);
+                for (int p = lane; p < nprobe; p += 32) {
+                    const unsigned long long v = sel[p];
+                    probes[q * pstride + p] = (int32_t)(v & 0xffffffffu);
+                    if (pd2) pd2[q * pstride + p] = __uint_as_float((unsigned)(v >> 32));
+                }
+                __syncwarp();
+                continue;
+            }
+            __syncwarp();                   // too many ties: the radix path below
+        }
 
         // Radix select over the bits below the common prefix of all keys.
         unsigned prefix = kmin, rem = (unsigned)nprobe;
@@ -187,21 +273,7 @@ __global__ void __launch_bounds__(MAXW * 32) select_nprobe_kernel(
         }
         for (int i = (int)nsel + lane; i < P2; i += 32) sel[i] = ~0ull;
         __syncwarp();
-        for (int size = 2; size <= P2; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = lane; i < P2; i += 32) {
-                    const int j = i ^ stride;
-                    if (j > i) {
-                        const unsigned long long x = sel[i], y = sel[j];
-                        if ((x > y) == ((i & size) == 0)) {
-                            sel[i] = y;
-                            sel[j] = x;
-                        }
-                    }
-                }
-                __syncwarp();
-            }
-        }
+        warp_sort(sel, P2, lane);
         for (int p = lane; p < nprobe; p += 32) {
             const unsigned long long v = sel[p];
             probes[q * pstride + p] = (int32_t)(v & 0xffffffffu);

@@ -108,6 +108,31 @@ def test_probe_matches_oracle(c1):
         assert np.max(np.abs(pd[ok] - epd[ok]) / np.maximum(epd[ok], 1e-30)) < 1e-4
 
 
+def test_probe_duplicate_centroids_take_lowest_ids(adsx_mod):
+    """Exact ties in the centroid ranking: 4 distinct centroids, each repeated
+    150 times under shuffled ids.  Equal rows give bit-identical distances on
+    both sides, so the probe lists must equal the oracle's exactly (ties by
+    ascending cluster id), for nprobe below and above 64 and with tie groups
+    larger than the selection's fast-path capacity."""
+    rng = np.random.default_rng(81)
+    D = 32
+    base = rng.normal(0.0, 3.0, size=(4, D)).astype(np.float32)
+    C = np.repeat(base, 150, axis=0)[rng.permutation(600)]
+    X = (C[rng.integers(0, 600, 5000)] + rng.normal(0, 0.1, (5000, D))).astype(np.float32)
+    assign = rng.integers(0, 600, 5000).astype(np.int32)
+    P = W.make_P(D, 82).astype(np.float32)
+    Q = (base[rng.integers(0, 4, 12)] + rng.normal(0, 0.5, (12, D))).astype(np.float32)
+    ix = adsx_mod.build_index(X, P, C, assign)
+    try:
+        Cr, Qr = oracle.rotate(P, C), oracle.rotate(P, Q)
+        for nprobe in (1, 20, 64, 150, 200, 600):
+            pr, _ = ix.probe(Q, nprobe)
+            epr, _ = oracle.probe(Cr, Qr, nprobe)
+            assert np.array_equal(pr, epr), nprobe
+    finally:
+        ix.close()
+
+
 def test_fixed_r_decisions_bit_exact(c1):
     wl, ix, Y, Cr, Qr = c1
     _, kd = oracle.knn_exact(Y, Qr, 10)
