@@ -312,7 +312,12 @@ def run_batched(args):
         return g, out
 
     res = {}
-    for name, eps0 in (("ads", args.eps0), ("fd", math.inf)):
+    arms = [("ads", args.eps0, ix), ("fd", math.inf, ix)]
+    ix16 = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign, storage=adsx.BF16)
+    dd16, ip16, _ = adsx.autotune(ix16, wl.Q[:2000], 10, 64, args.eps0)
+    arms.append(("ads_bf16", args.eps0, ix16))
+    for name, eps0, index in arms:
+        ix = index
         g, (ids, d2, dims) = graph_for(eps0)
         ts = []
         for st in range(args.warmup + args.steps):
@@ -342,12 +347,14 @@ def run_batched(args):
             "config": {"workload": wl.name, "nq": nq, "nlist": wl.nlist, "K": "{1,10,100}",
                        "nprobe": "round(exp(U[ln 8, ln 512]))", "eps0": args.eps0,
                        "autotuned_delta_d": dd, "autotuned_items_per_sm": ip,
+                       "bf16_autotuned_delta_d": dd16, "bf16_autotuned_items_per_sm": ip16,
                        "l2": "256 MB flush between steps"},
-            "ads": res["ads"], "fd_scan": res["fd"],
+            "ads": res["ads"], "fd_scan": res["fd"], "ads_bf16": res["ads_bf16"],
             "speedup_vs_fd": res["fd"]["ms"] / res["ads"]["ms"],
             "dims_fraction_vs_fd": res["ads"]["dims"] / res["fd"]["dims"]}
     print(json.dumps(line), flush=True)
-    ix.close()
+    for _, _, index in arms[1:]:
+        index.close()
     return 0
 
 
@@ -463,6 +470,20 @@ def run_precision(args):
                     nprobe = npb
                     break
         adsx.set_stage_timing(ix, True)
+        if name == "f32":
+            # FDScanning (full-D scan) on the same index: the high-D comparison
+            fts = []
+            for s_ in range(args.warmup + max(args.steps, 20)):
+                _flush_l2(flush)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                ix.search(Qd, 10, nprobe, eps0=math.inf)
+                e1.record()
+                torch.cuda.synchronize()
+                if s_ >= args.warmup:
+                    fts.append(e0.elapsed_time(e1))
+            fd_f32 = dict(qps=1000 / (np.median(fts) * 1e-3), ms=float(np.median(fts)))
         ts, scan = [], []
         steps = max(args.steps, 20)     # one search is ~6 ms: medians over >= 20 steps
         for s_ in range(args.warmup + steps):
@@ -496,7 +517,8 @@ def run_precision(args):
             "dtype": "bf16 storage, f32 accumulate, f32 recheck", "data": "synthetic (GIST-shaped)",
             "config": {"workload": wl.name, "nq": 1000, "nlist": wl.nlist, "K": 10,
                        "nprobe": nprobe, "eps0": args.eps0, "delta_d": 32},
-            "per_storage": res}
+            "per_storage": res, "fd_scan_f32": fd_f32,
+            "speedup_f32_vs_fd": fd_f32["ms"] / res["f32"]["ms"]}
     print(json.dumps(line), flush=True)
     return 0
 

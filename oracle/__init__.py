@@ -22,6 +22,8 @@ Functions (each follows the passage named in its docstring):
   dco_ip(o, q, r, eps0, delta_d)    Sec. 8 ext. (1): inner-product DCO reduced
                                     to Algorithm 1 on normalised vectors
   ivf_exact_ip(...), ivf_ads_ip(...) IVF / IVF+ for inner products
+  kac_apply(pairs, cs, X)           Sec. 6.2.3: the layered Kac walk as a
+  kac_matrix(pairs, cs, D)          rotation, and its dense matrix
 """
 from __future__ import annotations
 
@@ -217,6 +219,31 @@ def ivf_pd(Y, Cr, assign, Qr, K: int, nprobe: int, delta_d: int, nthreads: int =
     _load().orc_ivf_pd(_p(Y), Y.shape[0], D, _p(Cr), Cr.shape[0], _p(assign), _p(Qr), nq, K,
                        nprobe, int(delta_d), _p(ids), _p(d2), _p(dims), nthreads)
     return ids, d2, dims
+
+
+# ------------------------------------------------------ Kac's walk
+def kac_apply(pairs, cs, X):
+    """Sec. 6.2.3 (fast rotation by Kac's walk): applies the layered walk to
+    every row of X in FP64, layer after layer; in layer l the pair
+    (i, j) = (pairs[l, 2t], pairs[l, 2t+1]) with (c, s) = (cs[l, 2t],
+    cs[l, 2t+1]) becomes (c x_i - s x_j, s x_i + c x_j).  Returns y = W x for
+    each row (W the product of the layers)."""
+    pairs = np.asarray(pairs)
+    cs = np.asarray(cs, np.float64)
+    Y = np.array(X, dtype=np.float64, copy=True)
+    for l in range(pairs.shape[0]):
+        i, j = pairs[l, 0::2], pairs[l, 1::2]
+        c, s = cs[l, 0::2], cs[l, 1::2]
+        xi, xj = Y[:, i].copy(), Y[:, j].copy()
+        Y[:, i] = c * xi - s * xj
+        Y[:, j] = s * xi + c * xj
+    return Y
+
+
+def kac_matrix(pairs, cs, D: int):
+    """The dense D x D matrix W of a Kac walk (y = W x), built by walking the
+    unit vectors; the IVF / ADSampling oracles then use it as P."""
+    return kac_apply(pairs, cs, np.eye(D)).T
 
 
 # ------------------------------------------- cosine and inner product

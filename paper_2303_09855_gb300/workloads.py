@@ -58,6 +58,26 @@ def make_P(D: int, seed: int) -> np.ndarray:
     return Qm * s[None, :]
 
 
+def make_kac_walk(D: int, L: int, seed: int):
+    """A seeded layered Kac walk (the O(D log D) random rotation named in
+    Sec. 6.2.3): L layers, each a random perfect matching of the D coordinates
+    (a seeded permutation read as consecutive pairs; with D odd one coordinate
+    rests) with an angle theta ~ U[0, 2 pi) per pair.  Returns pairs (L x 2m
+    int32, m = D // 2) and cs (L x 2m float32: cos theta, sin theta per pair).
+    Only random draws -- applying the walk is the library's and the oracle's
+    business."""
+    rng = np.random.default_rng(seed)
+    m = D // 2
+    pairs = np.empty((L, 2 * m), np.int32)
+    cs = np.empty((L, 2 * m), np.float32)
+    for l in range(L):
+        pairs[l] = rng.permutation(D)[:2 * m]
+        th = rng.uniform(0.0, 2.0 * np.pi, size=m)
+        cs[l, 0::2] = np.cos(th)
+        cs[l, 1::2] = np.sin(th)
+    return pairs, cs
+
+
 def kmeans(X: np.ndarray, nlist: int, iters: int, seed: int, device: str = "cpu",
            sample: int | None = None):
     """Lloyd's k-means in float32 (index phase; the paper uses Faiss).
