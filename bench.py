@@ -510,6 +510,38 @@ def run_precision(args):
                          dims_fraction=float(dims.sum().item()) / (1000 * nprobe * 0 + 1),
                          max_rel_err_vs_fp64=float(rel.max()), device_bytes=ix.device_bytes)
         ix.close()
+    # the same FP32 search with the rotation as a Kac walk (Sec. 6.2.3):
+    # 2 ceil(log2 D) layers; the query rotation stage is timed for both
+    L = 2 * int(math.ceil(math.log2(wl.D)))
+    pairs, cs = W.make_kac_walk(wl.D, L, 5)
+    t0 = time.perf_counter()
+    ixk = adsx.build_index_kac(wl.X, pairs, cs, wl.centroids, wl.assign)
+    build_kac_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ixd = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign)
+    build_dense_s = time.perf_counter() - t0
+    Qd = torch.from_numpy(wl.Q).to(dev)
+    rot = {}
+    for nm, index in (("dense", ixd), ("kac", ixk)):
+        adsx.set_stage_timing(index, True)
+        ts, rs = [], []
+        for s_ in range(args.warmup + max(args.steps, 20)):
+            _flush_l2(flush)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            ids, _ = index.search(Qd, 10, nprobe, eps0=args.eps0, delta_d=32)
+            e1.record()
+            torch.cuda.synchronize()
+            if s_ >= args.warmup:
+                ts.append(e0.elapsed_time(e1))
+                rs.append(adsx.stage_ms(index)[0])
+        rot[nm] = dict(qps=1000 / (np.median(ts) * 1e-3), rotate_ms=float(np.median(rs)),
+                       recall10=recall10(ids.cpu().numpy(), gt))
+        index.close()
+    rot["kac"]["layers"] = L
+    rot["kac"]["build_s"] = build_kac_s
+    rot["dense"]["build_s"] = build_dense_s
     for v in res.values():
         v.pop("dims_fraction")
     line = {"metric": "QPS of the precision form (GIST-shaped, K 10) per storage type",
@@ -517,7 +549,7 @@ def run_precision(args):
             "dtype": "bf16 storage, f32 accumulate, f32 recheck", "data": "synthetic (GIST-shaped)",
             "config": {"workload": wl.name, "nq": 1000, "nlist": wl.nlist, "K": 10,
                        "nprobe": nprobe, "eps0": args.eps0, "delta_d": 32},
-            "per_storage": res, "fd_scan_f32": fd_f32,
+            "per_storage": res, "fd_scan_f32": fd_f32, "rotation_f32": rot,
             "speedup_f32_vs_fd": fd_f32["ms"] / res["f32"]["ms"]}
     print(json.dumps(line), flush=True)
     return 0

@@ -68,6 +68,7 @@ typedef enum { ADSX_L2 = 0, ADSX_IP = 1, ADSX_COSINE = 2 } adsx_metric;
 #define ADSX_MAX_NLIST 16384  /* clusters                                    */
 #define ADSX_MAX_CLUSTER ((1 << 27) - 1)  /* members of one cluster (16 x this
                                            indexes a 32-bit block stride)    */
+#define ADSX_MAX_KAC_LAYERS 1024  /* layers of a Kac-walk rotation           */
 
 /*
  * adsx_build_index -- index phase (Sec. 6.1 "Implementation", Sec. 4, Sec. 5.2).
@@ -121,6 +122,27 @@ int adsx_build_index_metric(const float *X, int64_t N, int32_t D, const float *P
                             const float *centroids, int32_t nlist,
                             const int32_t *assign, int32_t storage, int32_t metric,
                             void *stream, adsx_index **out);
+
+/*
+ * adsx_build_index_kac -- adsx_build_index_metric with the random rotation
+ * given as a layered Kac walk instead of a dense P: the O(D log D) transform
+ * the paper names for this step (Sec. 6.2.3).  With m = D / 2, layer l
+ * (l < L) replaces each coordinate pair (i, j) = (pairs[2m l + 2t],
+ * pairs[2m l + 2t + 1]), t < m, by (c y_i - s y_j, s y_i + c y_j) with
+ * (c, s) = (cs[2m l + 2t], cs[2m l + 2t + 1]); the layers apply in order.
+ * Data, centroids and queries are rotated by the same walk, an orthogonal
+ * map, so distances and inner products are kept.  The walk must mix well
+ * enough for the hypothesis test (Sec. 3); about 2-3 log2(D) layers of
+ * random matchings and angles do.
+ *   pairs   host, L x 2m int32 in [0, D), each index at most once per layer.
+ *   cs      host, L x 2m float32 (c, s) per pair, |c^2 + s^2 - 1| <= 1e-5.
+ *   L       1..ADSX_MAX_KAC_LAYERS.
+ * Other arguments, results and errors as adsx_build_index_metric.
+ */
+int adsx_build_index_kac(const float *X, int64_t N, int32_t D, const int32_t *pairs,
+                         const float *cs, int32_t L, const float *centroids,
+                         int32_t nlist, const int32_t *assign, int32_t storage,
+                         int32_t metric, void *stream, adsx_index **out);
 
 /* Frees the index and all of its device memory (synchronises the device). */
 int adsx_free_index(adsx_index *index);
@@ -220,7 +242,8 @@ int adsx_probe(const adsx_index *index, const float *Qv, int64_t nq,
                int32_t nprobe, int32_t *probes, float *probe_d2, void *stream);
 
 /*
- * adsx_rotate -- q' = P q for each query (Sec. 3.1).
+ * adsx_rotate -- q' = P q for each query (Sec. 3.1), or the Kac walk of an
+ * index built with adsx_build_index_kac.
  *   out        host or device, nq x D float32.
  */
 int adsx_rotate(const adsx_index *index, const float *Qv, int64_t nq,

@@ -52,6 +52,8 @@ def load():
     lib.adsx_build_index_metric.argtypes = [V, i64, i32, V, V, i32, V, i32, i32, V,
                                             ctypes.POINTER(V)]
     lib.adsx_index_metric.argtypes = [V, V]
+    lib.adsx_build_index_kac.argtypes = [V, i64, i32, V, V, i32, V, i32, V, i32, i32, V,
+                                         ctypes.POINTER(V)]
     lib.adsx_free_index.argtypes = [V]
     lib.adsx_index_info.argtypes = [V, V, V, V, V, V]
     lib.adsx_search.argtypes = [V, V, i64, i32, i32, f32, i32, V, V, V, V]
@@ -75,6 +77,7 @@ def load():
     lib.adsx_stage_ms.argtypes = [V, V]
     lib.adsx_last_error.restype = ctypes.c_char_p
     for fn in ("adsx_build_index", "adsx_build_index_metric", "adsx_index_metric",
+               "adsx_build_index_kac",
                "adsx_free_index", "adsx_index_info", "adsx_search",
                "adsx_probe", "adsx_rotate", "adsx_dco_fixed_r", "adsx_stream_status",
                "adsx_set_stage_timing", "adsx_stage_ms", "adsx_search_noalloc",
@@ -204,6 +207,23 @@ def build_index(X, P, centroids, assign, storage=F32, stream=None, metric=L2) ->
 def build_index_metric(X, P, centroids, assign, storage=F32, metric=L2, stream=None) -> Index:
     """adsx_build_index_metric (Sec. 8, extension (1))."""
     return build_index(X, P, centroids, assign, storage, stream, metric)
+
+
+def build_index_kac(X, pairs, cs, centroids, assign, storage=F32, metric=L2, stream=None) -> Index:
+    """adsx_build_index_kac: the rotation given as a layered Kac walk (Sec. 6.2.3),
+    pairs and cs host arrays of shape (L, 2 * (D // 2)) (int32 / float32)."""
+    X = _host(X, np.float32)
+    pairs = _host(pairs, np.int32)
+    cs = _host(cs, np.float32)
+    C = _host(centroids, np.float32)
+    a = _host(assign, np.int32)
+    L = pairs.shape[0] if pairs.ndim == 2 else 0
+    assert pairs.shape == cs.shape and (L == 0 or pairs.shape[1] == 2 * (X.shape[1] // 2))
+    h = ctypes.c_void_p()
+    _check(load().adsx_build_index_kac(_ptr(X), X.shape[0], X.shape[1], _ptr(pairs), _ptr(cs), L,
+                                       _ptr(C), C.shape[0], _ptr(a), int(storage), int(metric),
+                                       _stream_of(None, stream), ctypes.byref(h)))
+    return Index(h)
 
 
 def index_metric(index: Index) -> int:

@@ -37,6 +37,9 @@ struct Index {
     float *rows32 = nullptr;   // N x Dp FP32 rotated rows in CSR order (16-bit storage only)
     float *norms = nullptr;    // N FP32 norms ||y|| in CSR order (16-bit storage only)
     float *onorm = nullptr;    // N raw norms ||o|| in CSR order (inner-product indexes)
+    int32_t *kac_pairs = nullptr;  // Kac-walk rotation (instead of P): L x 2(D/2) pairs
+    float *kac_cs = nullptr;       //   and their (cos, sin)
+    int32_t kac_L = 0;
     int32_t metric = ADSX_L2;  // ADSX_L2 / ADSX_IP / ADSX_COSINE
     int32_t *ids = nullptr;    // N: CSR position -> original id
     int64_t *off = nullptr;    // nlist + 1 CSR offsets
@@ -247,6 +250,22 @@ cudaError_t launch_row_sqnorm(const float *X, int64_t M, int ld, int K, float *o
 // (Dot2) FP32 dot products, written as N x Dp FP32 (columns >= D are 0).
 cudaError_t launch_rotate(const float *X, int64_t N, int D, const float *P, int ldp, float *Y,
                           int Dp, cudaStream_t s);
+
+// Layered Kac walk (Sec. 6.2.3): Y = W X for N rows of D values (row stride
+// ldx), written as N x Dp FP32 (columns >= D are 0); pairs / cs are L x 2(D/2).
+cudaError_t launch_kac_rotate(const float *X, int64_t N, int D, int ldx, const int32_t *pairs,
+                              const float *cs, int L, float *Y, int Dp, cudaStream_t s);
+
+// The index's rotation of N raw rows (D values each, contiguous) into an
+// N x Dp buffer: the dense P (compensated FP32) or the Kac walk.
+inline cudaError_t rotate_rows(const Index *ix, const float *X, int64_t N, float *Y,
+                               cudaStream_t s)
+{
+    if (ix->kac_L > 0)
+        return launch_kac_rotate(X, N, ix->D, ix->D, ix->kac_pairs, ix->kac_cs, ix->kac_L, Y,
+                                 ix->Dp, s);
+    return launch_rotate(X, N, ix->D, ix->P, ix->Dp, Y, ix->Dp, s);
+}
 
 // Rotated rows Y (N x Dp, FP32) into the dim-blocked layout of `storage`
 // (ADSX_F32 / ADSX_BF16 / ADSX_F16); for 16-bit storage also the FP32 row copy

@@ -135,7 +135,7 @@ int check_index(const Index *ix)
 cudaError_t rotate_queries(const Index *ix, const float *q_dev, int64_t nq, float *qrot,
                            cudaStream_t s)
 {
-    return adsx::launch_rotate(q_dev, nq, ix->D, ix->P, ix->Dp, qrot, ix->Dp, s);
+    return adsx::rotate_rows(ix, q_dev, nq, qrot, s);
 }
 
 // ||q'-c'||^2 for every (query, centroid) as ||q'||^2 + ||c'||^2 - 2 q'.c'.
@@ -215,7 +215,9 @@ extern "C" {
 
 const char *adsx_last_error(void) { return g_last_error.c_str(); }
 
+// The rotation is either a dense P (kac_L = 0) or a layered Kac walk.
 static int build_impl(const float *X, int64_t N, int32_t D, const float *P,
+                      const int32_t *kac_pairs, const float *kac_cs, int32_t kac_L,
                       const float *centroids, int32_t nlist, const int32_t *assign,
                       int32_t storage, int32_t metric, void *stream, adsx_index **out)
 {
@@ -223,14 +225,38 @@ static int build_impl(const float *X, int64_t N, int32_t D, const float *P,
     *out = nullptr;
     if (metric != ADSX_L2 && metric != ADSX_IP && metric != ADSX_COSINE)
         return fail(ADSX_EINVAL, "metric %d not supported", metric);
-    if (!X || !P || !centroids || !assign) return fail(ADSX_EINVAL, "NULL input pointer");
+    const bool kac = kac_L != 0;
+    if (!X || (!kac && !P) || !centroids || !assign) return fail(ADSX_EINVAL, "NULL input pointer");
+    if (kac) {
+        if (kac_L < 1 || kac_L > ADSX_MAX_KAC_LAYERS)
+            return fail(ADSX_EINVAL, "Kac walk layers out of range (1..%d)", ADSX_MAX_KAC_LAYERS);
+        if (!kac_pairs || !kac_cs) return fail(ADSX_EINVAL, "NULL Kac walk");
+        if (is_device_ptr(kac_pairs) || is_device_ptr(kac_cs))
+            return fail(ADSX_EINVAL, "the Kac walk takes host pointers");
+        if (D >= 1 && D <= ADSX_MAX_D) {
+            const int m = D / 2;
+            std::vector<int32_t> stamp((size_t)D, -1);
+            for (int32_t l = 0; l < kac_L; ++l)
+                for (int t = 0; t < 2 * m; ++t) {
+                    const int32_t i = kac_pairs[(size_t)l * 2 * m + t];
+                    if (i < 0 || i >= D || stamp[(size_t)i] == l)
+                        return fail(ADSX_EINVAL, "Kac walk layer %d: index %d out of range or repeated", l, i);
+                    stamp[(size_t)i] = l;
+                }
+            for (size_t k = 0; k < (size_t)kac_L * m; ++k) {
+                const double c = kac_cs[2 * k], sn = kac_cs[2 * k + 1];
+                if (!(fabs(c * c + sn * sn - 1.0) <= 1e-5))
+                    return fail(ADSX_EINVAL, "Kac walk pair %zu: c^2 + s^2 != 1", k);
+            }
+        }
+    }
     if (N < 1 || N >= (int64_t)1 << 31) return fail(ADSX_EINVAL, "N out of range");
     if (D < 1 || D > ADSX_MAX_D) return fail(ADSX_EINVAL, "D out of range (1..%d)", ADSX_MAX_D);
     if (nlist < 1 || nlist > ADSX_MAX_NLIST || nlist > N)
         return fail(ADSX_EINVAL, "nlist out of range (1..min(N, %d))", ADSX_MAX_NLIST);
     if (storage != ADSX_F32 && storage != ADSX_BF16 && storage != ADSX_F16)
         return fail(ADSX_EINVAL, "storage type %d not supported", storage);
-    if (is_device_ptr(X) || is_device_ptr(P) || is_device_ptr(centroids) || is_device_ptr(assign))
+    if (is_device_ptr(X) || (P && is_device_ptr(P)) || is_device_ptr(centroids) || is_device_ptr(assign))
         return fail(ADSX_EINVAL, "adsx_build_index takes host pointers");
 
     // Inverted file (Sec. 2.2.2): stable counting sort by cluster.
@@ -288,7 +314,7 @@ static int build_impl(const float *X, int64_t N, int32_t D, const float *P,
         if (e != cudaSuccess) return cleanup(cuda_fail(e, what)); \
     } while (0)
 
-    BCK(dalloc((void **)&ix->P, sizeof(float) * Dp * Dp), "alloc P");
+    if (!kac) BCK(dalloc((void **)&ix->P, sizeof(float) * Dp * Dp), "alloc P");
     BCK(dalloc((void **)&ix->cents, sizeof(float) * (size_t)nlist * Dp), "alloc centroids");
     BCK(dalloc((void **)&ix->cnorm, sizeof(float) * (size_t)nlist), "alloc centroid norms");
     const size_t esz = storage == ADSX_F32 ? 4 : 2;
@@ -303,38 +329,51 @@ static int build_impl(const float *X, int64_t N, int32_t D, const float *P,
     BCK(dalloc((void **)&ix->tile_off, sizeof(int32_t) * ((size_t)nlist + 1)), "alloc tiles");
     BCK(dalloc((void **)&ix->err, sizeof(unsigned)), "alloc error word");
 
-    // P padded to Dp x Dp with zeros: padded rotated dims are exactly 0.
-    {
-        std::vector<float> Pp((size_t)Dp * Dp, 0.f);
-        for (int32_t i = 0; i < D; ++i) memcpy(&Pp[(size_t)i * Dp], P + (size_t)i * D, sizeof(float) * D);
-        BCK(cudaMemcpyAsync(ix->P, Pp.data(), sizeof(float) * Dp * Dp, cudaMemcpyHostToDevice, s), "copy P");
-        BCK(cudaStreamSynchronize(s), "sync");
-    }
-    // P must be orthogonal (Sec. 3.1): max |P P^T - I| <= 1e-4, checked with
-    // the compensated rotation kernel on the device (P P^T = rotating P's rows).
-    {
-        float *pd = nullptr, *gd = nullptr;
-        BCK(cudaMalloc(&pd, sizeof(float) * (size_t)D * D), "alloc P check");
-        e = cudaMalloc(&gd, sizeof(float) * (size_t)D * Dp);
-        if (e != cudaSuccess) {
-            cudaFree(pd);
-            return cleanup(cuda_fail(e, "alloc P check"));
+    if (kac) {
+        // Kac-walk rotation (Sec. 6.2.3) instead of a dense P: orthogonal by
+        // construction (products of Givens rotations with c^2 + s^2 = 1).
+        const size_t cnt = (size_t)kac_L * 2 * (D / 2);
+        BCK(dalloc((void **)&ix->kac_pairs, sizeof(int32_t) * cnt), "alloc Kac walk");
+        BCK(dalloc((void **)&ix->kac_cs, sizeof(float) * cnt), "alloc Kac walk");
+        ix->kac_L = kac_L;
+        if (cnt) {
+            BCK(cudaMemcpyAsync(ix->kac_pairs, kac_pairs, sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, s), "copy Kac walk");
+            BCK(cudaMemcpyAsync(ix->kac_cs, kac_cs, sizeof(float) * cnt, cudaMemcpyHostToDevice, s), "copy Kac walk");
         }
-        std::vector<float> G((size_t)D * Dp);
-        e = cudaMemcpyAsync(pd, P, sizeof(float) * (size_t)D * D, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = adsx::launch_rotate(pd, D, D, ix->P, Dp, gd, Dp, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(G.data(), gd, sizeof(float) * (size_t)D * Dp, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        cudaFree(pd);
-        cudaFree(gd);
-        if (e != cudaSuccess) return cleanup(cuda_fail(e, "P check"));
-        double worst = 0.0;
-        for (int32_t i = 0; i < D; ++i)
-            for (int32_t j = 0; j < D; ++j)
-                worst = std::max(worst, fabs((double)G[(size_t)i * Dp + j] - (i == j ? 1.0 : 0.0)));
-        if (!(worst <= 1e-4))
-            return cleanup(fail(ADSX_EINVAL, "P is not orthogonal (max|P P^T - I| = %g)", worst));
+    } else {
+        // P padded to Dp x Dp with zeros: padded rotated dims are exactly 0.
+        {
+            std::vector<float> Pp((size_t)Dp * Dp, 0.f);
+            for (int32_t i = 0; i < D; ++i) memcpy(&Pp[(size_t)i * Dp], P + (size_t)i * D, sizeof(float) * D);
+            BCK(cudaMemcpyAsync(ix->P, Pp.data(), sizeof(float) * Dp * Dp, cudaMemcpyHostToDevice, s), "copy P");
+            BCK(cudaStreamSynchronize(s), "sync");
+        }
+        // P must be orthogonal (Sec. 3.1): max |P P^T - I| <= 1e-4, checked with
+        // the compensated rotation kernel on the device (P P^T = rotating P's rows).
+        {
+            float *pd = nullptr, *gd = nullptr;
+            BCK(cudaMalloc(&pd, sizeof(float) * (size_t)D * D), "alloc P check");
+            e = cudaMalloc(&gd, sizeof(float) * (size_t)D * Dp);
+            if (e != cudaSuccess) {
+                cudaFree(pd);
+                return cleanup(cuda_fail(e, "alloc P check"));
+            }
+            std::vector<float> G((size_t)D * Dp);
+            e = cudaMemcpyAsync(pd, P, sizeof(float) * (size_t)D * D, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = adsx::launch_rotate(pd, D, D, ix->P, Dp, gd, Dp, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(G.data(), gd, sizeof(float) * (size_t)D * Dp, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            cudaFree(pd);
+            cudaFree(gd);
+            if (e != cudaSuccess) return cleanup(cuda_fail(e, "P check"));
+            double worst = 0.0;
+            for (int32_t i = 0; i < D; ++i)
+                for (int32_t j = 0; j < D; ++j)
+                    worst = std::max(worst, fabs((double)G[(size_t)i * Dp + j] - (i == j ? 1.0 : 0.0)));
+            if (!(worst <= 1e-4))
+                return cleanup(fail(ADSX_EINVAL, "P is not orthogonal (max|P P^T - I| = %g)", worst));
+        }
     }
     BCK(cudaMemcpyAsync(ix->ids, ids.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, s), "copy ids");
     BCK(cudaMemcpyAsync(ix->off, off.data(), sizeof(int64_t) * (nlist + 1), cudaMemcpyHostToDevice, s), "copy off");
@@ -370,8 +409,8 @@ static int build_impl(const float *X, int64_t N, int32_t D, const float *P,
         }
         // Sec. 3.1 / Sec. 6.1: rotate every data vector and centroid once.
         // Index phase: rotation of the data and the centroids, once per index.
-        BCK(adsx::launch_rotate(xd, N, D, ix->P, Dp, yd, Dp, s), "rotate data");
-        BCK(adsx::launch_rotate(cd, nlist, D, ix->P, Dp, ix->cents, Dp, s), "rotate centroids");
+        BCK(adsx::rotate_rows(ix, xd, N, yd, s), "rotate data");
+        BCK(adsx::rotate_rows(ix, cd, nlist, ix->cents, s), "rotate centroids");
         BCK(adsx::launch_row_sqnorm(ix->cents, nlist, Dp, Dp, ix->cnorm, s), "centroid norms");
         // inner product: ||q'||^2 + max ||c'||^2 - 2 q'.c' >= 0 ranks clusters
         // by the largest <c, q> with the distance GEMM unchanged
@@ -397,14 +436,26 @@ int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
                      const float *centroids, int32_t nlist, const int32_t *assign,
                      int32_t storage, void *stream, adsx_index **out)
 {
-    return build_impl(X, N, D, P, centroids, nlist, assign, storage, ADSX_L2, stream, out);
+    return build_impl(X, N, D, P, nullptr, nullptr, 0, centroids, nlist, assign, storage, ADSX_L2,
+                      stream, out);
 }
 
 int adsx_build_index_metric(const float *X, int64_t N, int32_t D, const float *P,
                             const float *centroids, int32_t nlist, const int32_t *assign,
                             int32_t storage, int32_t metric, void *stream, adsx_index **out)
 {
-    return build_impl(X, N, D, P, centroids, nlist, assign, storage, metric, stream, out);
+    return build_impl(X, N, D, P, nullptr, nullptr, 0, centroids, nlist, assign, storage, metric,
+                      stream, out);
+}
+
+int adsx_build_index_kac(const float *X, int64_t N, int32_t D, const int32_t *pairs,
+                         const float *cs, int32_t L, const float *centroids, int32_t nlist,
+                         const int32_t *assign, int32_t storage, int32_t metric, void *stream,
+                         adsx_index **out)
+{
+    if (L == 0) return fail(ADSX_EINVAL, "Kac walk layers out of range (1..%d)", ADSX_MAX_KAC_LAYERS);
+    return build_impl(X, N, D, nullptr, pairs, cs, L, centroids, nlist, assign, storage, metric,
+                      stream, out);
 }
 
 int adsx_index_metric(const adsx_index *index, int32_t *metric)
@@ -428,6 +479,8 @@ int adsx_free_index(adsx_index *index)
     cudaFree(ix->rows32);
     cudaFree(ix->norms);
     cudaFree(ix->onorm);
+    cudaFree(ix->kac_pairs);
+    cudaFree(ix->kac_cs);
     cudaFree(ix->ids);
     cudaFree(ix->off);
     cudaFree(ix->tile_off);

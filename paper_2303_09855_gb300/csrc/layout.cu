@@ -295,3 +295,75 @@ cudaError_t launch_scatter_f32(const float *src, const int64_t *pos, int64_t N, 
 }
 
 }  // namespace adsx
+
+// ---- Kac-walk rotation (Sec. 6.2.3: the random rotation in O(D log D)).
+namespace adsx {
+namespace {
+
+// R rows per block live in shared memory; for each layer the block stages the
+// layer's pairs and (c, s) and applies its disjoint Givens rotations to every
+// row: (x_i, x_j) <- (c x_i - s x_j, s x_i + c x_j).
+__global__ void __launch_bounds__(256) kac_rotate_kernel(const float *__restrict__ X, int64_t N,
+                                                         int D, int ldx,
+                                                         const int32_t *__restrict__ pairs,
+                                                         const float *__restrict__ cs, int L,
+                                                         float *__restrict__ Y, int ldy, int R)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int m = D / 2;
+    float *xs = reinterpret_cast<float *>(smraw);               // R x D
+    int *pr = reinterpret_cast<int *>(xs + (size_t)R * D);      // 2m
+    float *cv = reinterpret_cast<float *>(pr + 2 * m);          // 2m
+    for (int64_t r0 = (int64_t)blockIdx.x * R; r0 < N; r0 += (int64_t)gridDim.x * R) {
+        const int nr = (int)(N - r0 < R ? N - r0 : R);
+        for (int idx = threadIdx.x; idx < nr * D; idx += blockDim.x) {
+            const int r = idx / D, j = idx - r * D;
+            xs[idx] = X[(r0 + r) * ldx + j];
+        }
+        for (int l = 0; l < L; ++l) {
+            __syncthreads();            // rows loaded / previous layer applied
+            for (int t = threadIdx.x; t < 2 * m; t += blockDim.x) {
+                pr[t] = pairs[(size_t)l * 2 * m + t];
+                cv[t] = cs[(size_t)l * 2 * m + t];
+            }
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < nr * m; idx += blockDim.x) {
+                const int r = idx / m, t = idx - r * m;
+                const int i = pr[2 * t], j = pr[2 * t + 1];
+                const float c = cv[2 * t], s = cv[2 * t + 1];
+                float *x = xs + (size_t)r * D;
+                const float xi = x[i], xj = x[j];
+                x[i] = fmaf(c, xi, -s * xj);
+                x[j] = fmaf(s, xi, c * xj);
+            }
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nr * ldy; idx += blockDim.x) {
+            const int r = idx / ldy, j = idx - r * ldy;
+            Y[(r0 + r) * ldy + j] = j < D ? xs[(size_t)r * D + j] : 0.f;
+        }
+        __syncthreads();                // before the next rows overwrite xs
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_kac_rotate(const float *X, int64_t N, int D, int ldx, const int32_t *pairs,
+                              const float *cs, int L, float *Y, int Dp, cudaStream_t s)
+{
+    if (N <= 0) return cudaSuccess;
+    const int m = D / 2;
+    const size_t params = (size_t)2 * m * 8;
+    int R = (int)(((size_t)64 << 10) > params ? (((size_t)64 << 10) - params) / ((size_t)D * 4) : 1);
+    R = R < 1 ? 1 : (R > 64 ? 64 : R);
+    const size_t smem = (size_t)R * D * 4 + params;
+    cudaError_t e = cudaFuncSetAttribute(kac_rotate_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int64_t grid = (N + R - 1) / R;
+    if (grid > 152 * 8) grid = 152 * 8;
+    kac_rotate_kernel<<<(unsigned)grid, 256, smem, s>>>(X, N, D, ldx, pairs, cs, L, Y, Dp, R);
+    return cudaGetLastError();
+}
+
+}  // namespace adsx

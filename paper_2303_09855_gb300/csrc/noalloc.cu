@@ -176,7 +176,7 @@ extern "C" int adsx_search_noalloc(const adsx_index *index, const float *Qv, int
     }
     e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
     if (e == cudaSuccess)
-        e = adsx::launch_rotate(Qv, nq, ix->D, ix->P, Dp, qrot, Dp, s);
+        e = adsx::rotate_rows(ix, Qv, nq, qrot, s);
     if (e == cudaSuccess) e = adsx::launch_row_sqnorm(qrot, nq, Dp, Dp, qn, s);
     if (e == cudaSuccess)
         e = adsx::launch_tc_gemm(qrot, nq, Dp, ix->cents, ix->nlist, Dp, Dp, dist, ix->nlist,
