@@ -581,8 +581,9 @@ def main():
     nq = Qd.shape[0]
     gt = ground_truth(wl.X, wl.Q, 10, device)
 
-    def search(nprobe, eps0, dims=False):
-        return ix.search(Qd, args.K, nprobe, eps0=eps0, delta_d=args.delta_d, return_dims=dims)
+    def search(nprobe, eps0, dims=False, dd=None):
+        return ix.search(Qd, args.K, nprobe, eps0=eps0, delta_d=dd or args.delta_d,
+                         return_dims=dims)
 
     # ---- calibration (untimed): smallest nprobe with recall@10 >= 0.95
     sweep = []
@@ -610,7 +611,7 @@ def main():
     adsx.set_stage_timing(ix, True)
     stream = torch.cuda.current_stream()
 
-    def timed(nprobe, eps0, steps, warmup):
+    def timed(nprobe, eps0, steps, warmup, dd=None):
         tot, scan_ms, dims_sum = 0.0, 0.0, 0
         for s in range(warmup + steps):
             flush.zero_()
@@ -618,7 +619,7 @@ def main():
             e1 = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
-            ids, d2, dims = search(nprobe, eps0, True)
+            ids, d2, dims = search(nprobe, eps0, True, dd)
             e1.record(stream)
             torch.cuda.synchronize()
             if s >= warmup:
@@ -740,6 +741,13 @@ def main():
     else:
         _, _, d_fd = search(np_ads, math.inf, True)
         line["dims_fraction_vs_fd_at_ads_nprobe"] = ads_dims / float(d_fd.sum().item())
+    # the same search with delta_d = 16 (a finer first step than 32 / 128 dims)
+    if args.delta_d != 16:
+        ms16, _, dims16, ids16 = timed(np_ads, args.eps0, max(3, args.steps // 2), 2, dd=16)
+        ms16 = max_over_ranks(ms16)
+        line["ads_delta_d16"] = {"qps": job_throughput(nq, ws, ms16), "ms_per_step": ms16,
+                                 "recall10": recall10(ids16.cpu().numpy(), gt),
+                                 "dims_fraction_vs_fd": dims16 / fd_dims if fd_dims else None}
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline_oracle(wl, args.K, np_ads, args.eps0,
                                                    args.delta_d, args.cpu_seconds)
