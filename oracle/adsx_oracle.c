@@ -26,6 +26,9 @@
  *     orc_ivf_ads_ip      per-object threshold; IVF for inner products.
  *     (Cosine similarity is the Euclidean case on normalised vectors, done
  *     in the Python wrapper.)
+ *   - orc_graph_search    Sec. 2.2.1 / Sec. 4 (HNSW+): greedy beam search on
+ *                         a proximity graph with Algorithm 1 DCOs against the
+ *                         largest distance of the result set.
  *
  * Conventions (readings of points the paper leaves open):
  *   - distances are SQUARED Euclidean distances in the rotated space;
@@ -653,4 +656,102 @@ void orc_ivf_ads_ip(const double *Y, int64_t N, int32_t D, const double *Cr,
         free(probes);
     }
     free_buckets(&b);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Sec. 2.2.1 / Sec. 4 (HNSW+): greedy beam search on a proximity graph    */
+/* whose DCOs run Algorithm 1 against the largest distance of the result  */
+/* set R (size N_ef).  The search set S is the set of R's entries not yet */
+/* expanded (an entry leaving R can never be expanded usefully again).    */
+/* Reading of batch semantics: the threshold r is the largest distance in */
+/* R when a node's expansion starts and stays fixed while its neighbours  */
+/* are tested (in adjacency order, skipping visited ones); the neighbours */
+/* that pass and precede R's maximum in (distance, id) order then merge   */
+/* into R, which keeps its N_ef smallest.  The search stops when every    */
+/* entry of R has been expanded (or after max_iter expansions).           */
+/*   graph     N x Rg int32 neighbour ids (-1 = none), by original id      */
+/*   entries   nq int64 start vertices                                     */
+/* Outputs ids/d2 (K smallest of R by (distance, id); -1/+inf padded),    */
+/* the dims sampled and the expansions per query.                          */
+void orc_graph_search(const double *Y, int64_t N, int32_t D, const int32_t *graph,
+                      int32_t Rg, const int64_t *entries, const double *Qr, int64_t nq,
+                      int32_t K, int32_t ef, int32_t max_iter, double eps0,
+                      int32_t delta_d, int64_t *ids, double *d2, int64_t *dims_total,
+                      int64_t *iters_out, int nthreads)
+{
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t q = 0; q < nq; ++q) {
+        const double *qr = Qr + q * D;
+        unsigned char *visited = (unsigned char *)calloc((size_t)(N > 0 ? N : 1), 1);
+        orc_pair *R = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(ef + Rg));
+        unsigned char *expd = (unsigned char *)malloc((size_t)(ef + Rg));
+        orc_pair *cand = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(Rg > 0 ? Rg : 1));
+        int32_t nR = 0, it = 0;
+        int64_t dims_sum = 0;
+        const int64_t e = entries[q];
+        visited[e] = 1;
+        R[0].d = sqdist(Y + e * D, qr, D);
+        R[0].id = e;
+        expd[0] = 0;
+        nR = 1;
+        dims_sum += D;
+        while (it < max_iter) {
+            int32_t u = -1;
+            for (int32_t k = 0; k < nR; ++k)
+                if (!expd[k]) { u = k; break; }
+            if (u < 0) break;
+            expd[u] = 1;
+            const int64_t node = R[u].id;
+            const int full = nR == ef;
+            const double r2 = full ? R[nR - 1].d : INFINITY;
+            const int64_t rid = full ? R[nR - 1].id : INT64_MAX;
+            int32_t nc = 0;
+            for (int32_t j = 0; j < Rg; ++j) {
+                const int32_t v = graph[node * Rg + j];
+                if (v < 0 || visited[v]) continue;
+                visited[v] = 1;
+                int32_t dims = 0;
+                double S = 0.0;
+                const int res = orc_dco(Y + (int64_t)v * D, qr, D, r2, eps0, delta_d, &dims, &S, NULL);
+                dims_sum += dims;
+                if (res == ORC_POSITIVE && (!full || pair_less(S, v, r2, rid))) {
+                    cand[nc].d = S;
+                    cand[nc].id = v;
+                    ++nc;
+                }
+            }
+            /* merge: R and the candidates, keep the ef smallest by (d, id) */
+            for (int32_t k = 0; k < nc; ++k) {
+                R[nR + k] = cand[k];
+                expd[nR + k] = 0;
+            }
+            const int32_t tot = nR + nc;
+            /* insertion sort carrying the expanded flags (tot <= ef + Rg) */
+            for (int32_t a = 1; a < tot; ++a) {
+                orc_pair x = R[a];
+                unsigned char fx = expd[a];
+                int32_t b = a - 1;
+                while (b >= 0 && pair_less(x.d, x.id, R[b].d, R[b].id)) {
+                    R[b + 1] = R[b];
+                    expd[b + 1] = expd[b];
+                    --b;
+                }
+                R[b + 1] = x;
+                expd[b + 1] = fx;
+            }
+            nR = tot < ef ? tot : ef;
+            ++it;
+        }
+        for (int32_t k = 0; k < K; ++k) {
+            ids[q * K + k] = k < nR ? R[k].id : -1;
+            d2[q * K + k] = k < nR ? R[k].d : INFINITY;
+        }
+        if (dims_total) dims_total[q] = dims_sum;
+        if (iters_out) iters_out[q] = it;
+        free(cand);
+        free(expd);
+        free(R);
+        free(visited);
+    }
 }
