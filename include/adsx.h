@@ -69,6 +69,8 @@ typedef enum { ADSX_L2 = 0, ADSX_IP = 1, ADSX_COSINE = 2 } adsx_metric;
 #define ADSX_MAX_CLUSTER ((1 << 27) - 1)  /* members of one cluster (16 x this
                                            indexes a 32-bit block stride)    */
 #define ADSX_MAX_KAC_LAYERS 1024  /* layers of a Kac-walk rotation           */
+#define ADSX_MAX_DEGREE 32    /* neighbours per vertex of a proximity graph  */
+#define ADSX_MAX_EF 512       /* result-set size of a graph search           */
 
 /*
  * adsx_build_index -- index phase (Sec. 6.1 "Implementation", Sec. 4, Sec. 5.2).
@@ -377,6 +379,61 @@ int adsx_server_destroy(adsx_server *server);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char *adsx_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Graph-based search with ADSampling DCOs: HNSW+ (Sec. 4) -- the greedy beam
+ * search HNSW runs on its base layer (Sec. 2.2.1) with Algorithm 1 as every
+ * DCO -- on a kNN proximity graph over the vectors of an FP32 L2 index.
+ * ---------------------------------------------------------------------- */
+typedef struct adsx_graph adsx_graph;
+
+/*
+ * adsx_build_graph -- vertex x's neighbours are its `degree` nearest other
+ * vectors among the members of its nprobe nearest clusters (ties by id),
+ * found with the library's own exact IVF search (adsx_search, eps0 = +INF);
+ * each cluster's entry vertex is its member nearest to the centroid.  HNSW's
+ * upper layers only locate a start vertex: a search starts at the entry of
+ * the query's nearest cluster instead.  The vectors themselves are read in
+ * place from the index, which must outlive the graph.
+ *   index    an FP32 index built with the L2 metric (ADSX_EINVAL otherwise).
+ *   X        host or device, N x D float32: the vectors the index was built from.
+ *   degree   1..ADSX_MAX_DEGREE.   nprobe 1..min(nlist, ADSX_MAX_NPROBE).
+ *   out      receives the graph (owns its device memory).
+ * Errors: ADSX_EINVAL, ADSX_ENOMEM, ADSX_ECUDA.
+ */
+int adsx_build_graph(const adsx_index *index, const float *X, int32_t degree,
+                     int32_t nprobe, void *stream, adsx_graph **out);
+
+/* Frees the graph and its device memory (synchronises the device). */
+int adsx_free_graph(adsx_graph *graph);
+
+/* Shape of a graph: any output pointer may be NULL. */
+int adsx_graph_info(const adsx_graph *graph, int64_t *N, int32_t *degree, int32_t *nlist);
+
+/* Copies the neighbour lists (N x degree int32, -1 = none) and the per-cluster
+ * entry vertices (nlist int64, -1 = empty cluster) to host or device memory
+ * (either pointer may be NULL). */
+int adsx_graph_export(const adsx_graph *graph, int32_t *neighbors, int64_t *entries);
+
+/*
+ * adsx_search_graph -- HNSW+: greedy beam search with a result set R of ef
+ * entries (Sec. 2.2.1).  From the entry vertex, repeatedly expand the
+ * nearest not-yet-expanded entry of R: every neighbour not visited before
+ * runs Algorithm 1 against r = the largest distance in R (+INF while R holds
+ * fewer than ef; fixed during one expansion) and, if it reaches d = D with
+ * (distance, id) below R's largest, joins R, which keeps its ef smallest.
+ * The search stops when every entry of R is expanded, or after 4 ef
+ * expansions.  The K smallest entries of R are returned, by (distance, id).
+ *   Qv, nq, ids, dists, dims_read, eps0, delta_d   as adsx_search
+ *                (eps0 = +INF: exact DCOs, i.e. HNSW's own search).
+ *   K          1..ef.     ef 1..ADSX_MAX_EF.
+ * The graph keeps per-warp scratch for the visited test: searches on one
+ * graph must not overlap on the GPU.
+ * Errors: ADSX_EINVAL, ADSX_ENOMEM, ADSX_ECUDA.
+ */
+int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const float *Qv,
+                      int64_t nq, int32_t K, int32_t ef, float eps0, int32_t delta_d,
+                      int64_t *ids, float *dists, int64_t *dims_read, void *stream);
 
 #ifdef __cplusplus
 }

@@ -52,6 +52,11 @@ def load():
     lib.adsx_build_index_metric.argtypes = [V, i64, i32, V, V, i32, V, i32, i32, V,
                                             ctypes.POINTER(V)]
     lib.adsx_index_metric.argtypes = [V, V]
+    lib.adsx_build_graph.argtypes = [V, V, i32, i32, V, ctypes.POINTER(V)]
+    lib.adsx_free_graph.argtypes = [V]
+    lib.adsx_graph_info.argtypes = [V, V, V, V]
+    lib.adsx_graph_export.argtypes = [V, V, V]
+    lib.adsx_search_graph.argtypes = [V, V, V, i64, i32, i32, f32, i32, V, V, V, V]
     lib.adsx_build_index_kac.argtypes = [V, i64, i32, V, V, i32, V, i32, V, i32, i32, V,
                                          ctypes.POINTER(V)]
     lib.adsx_free_index.argtypes = [V]
@@ -77,7 +82,8 @@ def load():
     lib.adsx_stage_ms.argtypes = [V, V]
     lib.adsx_last_error.restype = ctypes.c_char_p
     for fn in ("adsx_build_index", "adsx_build_index_metric", "adsx_index_metric",
-               "adsx_build_index_kac",
+               "adsx_build_index_kac", "adsx_build_graph", "adsx_free_graph",
+               "adsx_graph_info", "adsx_graph_export", "adsx_search_graph",
                "adsx_free_index", "adsx_index_info", "adsx_search",
                "adsx_probe", "adsx_rotate", "adsx_dco_fixed_r", "adsx_stream_status",
                "adsx_set_stage_timing", "adsx_stage_ms", "adsx_search_noalloc",
@@ -224,6 +230,73 @@ def build_index_kac(X, pairs, cs, centroids, assign, storage=F32, metric=L2, str
                                        _ptr(C), C.shape[0], _ptr(a), int(storage), int(metric),
                                        _stream_of(None, stream), ctypes.byref(h)))
     return Index(h)
+
+
+class Graph:
+    """Owns an adsx_graph handle (freed by close() or garbage collection)."""
+
+    def __init__(self, handle, index):
+        self.handle = handle
+        self.index = index                 # the graph reads the index's vectors
+        N, deg, nl = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().adsx_graph_info(handle, ctypes.byref(N), ctypes.byref(deg), ctypes.byref(nl)))
+        self.N, self.degree, self.nlist = N.value, deg.value, nl.value
+
+    def close(self):
+        if self.handle:
+            load().adsx_free_graph(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def search(self, Q, K, ef, eps0=2.1, delta_d=32, return_dims=False, stream=None):
+        return search_graph(self.index, self, Q, K, ef, eps0, delta_d, return_dims, stream)
+
+
+def build_graph(index: Index, X, degree: int = 32, nprobe: int = 16, stream=None) -> Graph:
+    """adsx_build_graph: a kNN proximity graph over the index's vectors (X: the
+    raw vectors the index was built from)."""
+    X = _host(X, np.float32) if not _is_torch_cuda(X) else X.contiguous()
+    h = ctypes.c_void_p()
+    _check(load().adsx_build_graph(index.handle, _ptr(X), int(degree), int(nprobe),
+                                   _stream_of(None, stream), ctypes.byref(h)))
+    return Graph(h, index)
+
+
+def free_graph(graph: Graph):
+    graph.close()
+
+
+def graph_info(graph: Graph):
+    """adsx_graph_info: (N, degree, nlist)."""
+    return graph.N, graph.degree, graph.nlist
+
+
+def graph_export(graph: Graph):
+    """adsx_graph_export: (neighbours N x degree int32, entries nlist int64) as numpy."""
+    nbr = np.empty((graph.N, graph.degree), np.int32)
+    ent = np.empty(graph.nlist, np.int64)
+    _check(load().adsx_graph_export(graph.handle, _ptr(nbr), _ptr(ent)))
+    return nbr, ent
+
+
+def search_graph(index: Index, graph: Graph, Q, K: int, ef: int, eps0: float = 2.1,
+                 delta_d: int = 32, return_dims: bool = False, stream=None):
+    """adsx_search_graph (HNSW+): returns (ids, squared dists[, dims])."""
+    Q = _prep_queries(Q)
+    nq = Q.shape[0]
+    ids = _out(Q, (nq, K), np.int64, "int64")
+    d2 = _out(Q, (nq, K), np.float32, "float32")
+    dims = _out(Q, (nq,), np.int64, "int64") if return_dims else None
+    _check(load().adsx_search_graph(index.handle, graph.handle, _ptr(Q), nq, int(K), int(ef),
+                                    float(eps0) if math.isfinite(eps0) else float("inf"),
+                                    int(delta_d), _ptr(ids), _ptr(d2), _ptr(dims),
+                                    _stream_of(Q, stream)))
+    return (ids, d2, dims) if return_dims else (ids, d2)
 
 
 def index_metric(index: Index) -> int:

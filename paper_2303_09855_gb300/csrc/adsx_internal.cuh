@@ -333,6 +333,39 @@ struct ScanArgs {
     const float *qnorm = nullptr;
 };
 
+// Graph search with ADSampling DCOs (HNSW+, graph.cu).
+struct GraphArgs {
+    const float *data;          // the index's FP32 dim-blocked vectors
+    const int64_t *vbase;       // per vertex: element offset of its block 0
+    const int32_t *vstride;     // per vertex: block stride (16 * cluster size)
+    const int32_t *nbr;         // N x degree neighbour ids (-1 = none)
+    int32_t degree;
+    const int64_t *entry;       // per cluster: start vertex (-1 = empty)
+    const float *qrot;          // nq x Dp rotated queries
+    const int32_t *probes;      // nq nearest clusters
+    const float *ftab;          // nblk + 1 test factors
+    int64_t nq;
+    int32_t D, Dp, nblk, db, test_on, K, ef, max_iter;
+    int64_t *out_ids;
+    float *out_d2;
+    int64_t *out_dims;          // may be NULL
+    unsigned *bitmap;           // warps x bm_words visited bits (all zero between queries)
+    int64_t bm_words;
+    int32_t *vlist;             // warps x vcap visited ids of the current query
+    int64_t vcap;               // >= 1 + max_iter * degree
+    int32_t warps;
+};
+size_t graph_search_smem(int Dp, int ef);
+int graph_search_warps_per_block();
+cudaError_t launch_knn_to_graph(const int64_t *knn, int64_t N, int64_t row0, int Kk, int degree,
+                                int32_t *nbr, cudaStream_t s);
+cudaError_t launch_vertex_map(const int64_t *off, int nlist, const int32_t *ids, int Dp,
+                              int64_t *vbase, int32_t *vstride, cudaStream_t s);
+cudaError_t launch_cluster_entries(const float *data, const int64_t *off, const int32_t *ids,
+                                   const float *cents, int nlist, int Dp, int64_t *entry,
+                                   cudaStream_t s);
+cudaError_t launch_graph_search(const GraphArgs &g, cudaStream_t s);
+
 size_t scan_smem_bytes(const ScanArgs &a);
 int scan_items_target(int device, int items_per_sm = 48);
 cudaError_t launch_test_factors(float *ftab, int nblk, int D, float eps0, cudaStream_t s,

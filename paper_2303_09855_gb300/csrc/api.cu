@@ -995,3 +995,235 @@ int adsx_stream_status(const adsx_index *index, void *stream)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- graph search
+// HNSW+ (Sec. 4) on a kNN proximity graph over an FP32 L2 index; kernels in
+// graph.cu.  The graph owns its device memory and, once a search has run, the
+// per-warp scratch of the visited test (reused by later searches).
+struct Graph {
+    int64_t N = 0;
+    int32_t degree = 0, nlist = 0, device = 0;
+    int32_t *nbr = nullptr;      // N x degree
+    int64_t *entry = nullptr;    // nlist
+    int64_t *vbase = nullptr;    // N
+    int32_t *vstride = nullptr;  // N
+    unsigned *bitmap = nullptr;  // warps x bm_words (all zero between queries)
+    int32_t *vlist = nullptr;    // warps x vcap
+    int64_t bm_words = 0, vcap = 0;
+    int32_t warps = 0;
+};
+
+extern "C" {
+
+int adsx_free_graph(adsx_graph *graph)
+{
+    Graph *g = reinterpret_cast<Graph *>(graph);
+    if (!g) return ADSX_OK;
+    cudaSetDevice(g->device);
+    cudaDeviceSynchronize();
+    cudaFree(g->nbr);
+    cudaFree(g->entry);
+    cudaFree(g->vbase);
+    cudaFree(g->vstride);
+    cudaFree(g->bitmap);
+    cudaFree(g->vlist);
+    delete g;
+    return ADSX_OK;
+}
+
+int adsx_build_graph(const adsx_index *index, const float *X, int32_t degree, int32_t nprobe,
+                     void *stream, adsx_graph **out)
+{
+    const Index *ix = reinterpret_cast<const Index *>(index);
+    if (!out) return fail(ADSX_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = check_index(ix);
+    if (rc) return rc;
+    if (ix->storage != ADSX_F32 || ix->metric != ADSX_L2)
+        return fail(ADSX_EINVAL, "graph search needs an FP32 L2 index");
+    if (!X) return fail(ADSX_EINVAL, "X is NULL");
+    if (degree < 1 || degree > ADSX_MAX_DEGREE)
+        return fail(ADSX_EINVAL, "degree out of range (1..%d)", ADSX_MAX_DEGREE);
+    if (nprobe < 1 || nprobe > ix->nlist || nprobe > ADSX_MAX_NPROBE)
+        return fail(ADSX_EINVAL, "nprobe out of range (1..min(nlist, %d))", ADSX_MAX_NPROBE);
+    cudaStream_t s = (cudaStream_t)stream;
+    Graph *g = new Graph();
+    g->N = ix->N;
+    g->degree = degree;
+    g->nlist = ix->nlist;
+    g->device = ix->device;
+    auto cleanup = [&](int r) {
+        adsx_free_graph(reinterpret_cast<adsx_graph *>(g));
+        return r;
+    };
+    cudaError_t e;
+#define GCK(call, what)                                          \
+    do {                                                         \
+        e = (call);                                              \
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, what)); \
+    } while (0)
+    GCK(cudaMalloc(&g->nbr, sizeof(int32_t) * (size_t)g->N * degree), "alloc graph");
+    GCK(cudaMalloc(&g->entry, sizeof(int64_t) * (size_t)g->nlist), "alloc graph");
+    GCK(cudaMalloc(&g->vbase, sizeof(int64_t) * (size_t)g->N), "alloc graph");
+    GCK(cudaMalloc(&g->vstride, sizeof(int32_t) * (size_t)g->N), "alloc graph");
+    {
+        // Each vertex's degree nearest others among its nprobe nearest
+        // clusters: the library's exact IVF search with every vertex as a
+        // query, in chunks (its centroid-distance matrix is chunk x nlist).
+        const int Kk = degree + 1;
+        const int64_t chunk = 65536;
+        int64_t *knn = nullptr;
+        float *kd = nullptr;
+        GCK(cudaMalloc(&knn, sizeof(int64_t) * (size_t)std::min(chunk, g->N) * Kk), "alloc kNN");
+        e = cudaMalloc(&kd, sizeof(float) * (size_t)std::min(chunk, g->N) * Kk);
+        if (e != cudaSuccess) {
+            cudaFree(knn);
+            return cleanup(cuda_fail(e, "alloc kNN"));
+        }
+        for (int64_t r0 = 0; r0 < g->N && rc == 0; r0 += chunk) {
+            const int64_t n = std::min(chunk, g->N - r0);
+            rc = search_impl(index, X + r0 * ix->D, n, Kk, nprobe, INFINITY, 32, knn, kd, nullptr,
+                             stream, 0);
+            if (rc == 0) {
+                e = adsx::launch_knn_to_graph(knn, n, r0, Kk, degree, g->nbr + r0 * degree, s);
+                if (e != cudaSuccess) rc = cuda_fail(e, "graph rows");
+            }
+        }
+        cudaStreamSynchronize(s);
+        cudaFree(knn);
+        cudaFree(kd);
+        if (rc) return cleanup(rc);
+    }
+    GCK(adsx::launch_vertex_map(ix->off, ix->nlist, ix->ids, ix->Dp, g->vbase, g->vstride, s), "vertex map");
+    GCK(adsx::launch_cluster_entries(static_cast<const float *>(ix->data), ix->off, ix->ids, ix->cents,
+                                     ix->nlist, ix->Dp, g->entry, s), "cluster entries");
+    GCK(cudaStreamSynchronize(s), "graph sync");
+#undef GCK
+    *out = reinterpret_cast<adsx_graph *>(g);
+    return ADSX_OK;
+}
+
+int adsx_graph_export(const adsx_graph *graph, int32_t *neighbors, int64_t *entries)
+{
+    const Graph *g = reinterpret_cast<const Graph *>(graph);
+    if (!g) return fail(ADSX_EINVAL, "graph is NULL");
+    cudaSetDevice(g->device);
+    cudaError_t e = cudaSuccess;
+    if (neighbors)
+        e = cudaMemcpy(neighbors, g->nbr, sizeof(int32_t) * (size_t)g->N * g->degree, cudaMemcpyDefault);
+    if (e == cudaSuccess && entries)
+        e = cudaMemcpy(entries, g->entry, sizeof(int64_t) * (size_t)g->nlist, cudaMemcpyDefault);
+    return e == cudaSuccess ? ADSX_OK : cuda_fail(e, "graph export");
+}
+
+int adsx_graph_info(const adsx_graph *graph, int64_t *N, int32_t *degree, int32_t *nlist)
+{
+    const Graph *g = reinterpret_cast<const Graph *>(graph);
+    if (!g) return fail(ADSX_EINVAL, "graph is NULL");
+    if (N) *N = g->N;
+    if (degree) *degree = g->degree;
+    if (nlist) *nlist = g->nlist;
+    return ADSX_OK;
+}
+
+int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const float *Qv,
+                      int64_t nq, int32_t K, int32_t ef, float eps0, int32_t delta_d,
+                      int64_t *ids, float *dists, int64_t *dims_read, void *stream)
+{
+    const Index *ix = reinterpret_cast<const Index *>(index);
+    Graph *g = const_cast<Graph *>(reinterpret_cast<const Graph *>(graph));
+    int rc = check_index(ix);
+    if (rc) return rc;
+    if (!g || g->N != ix->N || g->nlist != ix->nlist) return fail(ADSX_EINVAL, "graph does not match the index");
+    if (ix->storage != ADSX_F32 || ix->metric != ADSX_L2)
+        return fail(ADSX_EINVAL, "graph search needs an FP32 L2 index");
+    if (nq < 0 || (nq > 0 && (!Qv || !ids || !dists))) return fail(ADSX_EINVAL, "bad query arguments");
+    if (ef < 1 || ef > ADSX_MAX_EF) return fail(ADSX_EINVAL, "ef out of range (1..%d)", ADSX_MAX_EF);
+    if (K < 1 || K > ef) return fail(ADSX_EINVAL, "K out of range (1..ef)");
+    if (delta_d == 0) delta_d = ix->tuned_delta_d;
+    if ((rc = check_blocks(delta_d, eps0))) return rc;
+    if (nq == 0) return ADSX_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int max_iter = 4 * ef;
+    // per-warp scratch of the visited test, kept with the graph
+    {
+        int nsm = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ix->device);
+        const int32_t warps = nsm * 16;
+        const int64_t bm_words = (g->N + 31) / 32;
+        const int64_t vcap = 1 + (int64_t)max_iter * g->degree;
+        if (g->warps != warps || g->bm_words != bm_words || g->vcap < vcap) {
+            cudaStreamSynchronize(s);
+            cudaFree(g->bitmap);
+            cudaFree(g->vlist);
+            g->bitmap = nullptr;
+            g->vlist = nullptr;
+            g->warps = 0;
+            cudaError_t e = cudaMalloc(&g->bitmap, sizeof(unsigned) * (size_t)warps * bm_words);
+            if (e == cudaSuccess) e = cudaMalloc(&g->vlist, sizeof(int32_t) * (size_t)warps * vcap);
+            if (e == cudaSuccess) e = cudaMemset(g->bitmap, 0, sizeof(unsigned) * (size_t)warps * bm_words);
+            if (e != cudaSuccess) {
+                cudaFree(g->bitmap);
+                cudaFree(g->vlist);
+                g->bitmap = nullptr;
+                g->vlist = nullptr;
+                return cuda_fail(e, "alloc graph search scratch");
+            }
+            g->warps = warps;
+            g->bm_words = bm_words;
+            g->vcap = vcap;
+        }
+    }
+    Scratch sc(s);
+    Buf<float> q, od;
+    Buf<int64_t> oi, odims;
+    float *qrot = nullptr, *ftab = nullptr;
+    int32_t *probes = nullptr;
+    const int nblk = ix->Dp / adsx::BLK;
+    CK(stage_in(sc, Qv, (size_t)nq * ix->D, q), "stage queries");
+    CK(stage_out(sc, ids, (size_t)nq * K, oi), "stage ids");
+    CK(stage_out(sc, dists, (size_t)nq * K, od), "stage dists");
+    CK(stage_out(sc, dims_read, (size_t)nq, odims), "stage dims");
+    CK(sc.get(&qrot, (size_t)nq * ix->Dp), "alloc q'");
+    CK(sc.get(&probes, (size_t)nq), "alloc probes");
+    CK(sc.get(&ftab, (size_t)nblk + 1), "alloc test factors");
+    CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
+    CK(probe_queries(ix, qrot, nq, 1, probes, nullptr, sc), "entry cluster");
+    adsx::GraphArgs a;
+    a.data = static_cast<const float *>(ix->data);
+    a.vbase = g->vbase;
+    a.vstride = g->vstride;
+    a.nbr = g->nbr;
+    a.degree = g->degree;
+    a.entry = g->entry;
+    a.qrot = qrot;
+    a.probes = probes;
+    a.ftab = ftab;
+    a.nq = nq;
+    a.D = ix->D;
+    a.Dp = ix->Dp;
+    a.nblk = nblk;
+    a.db = delta_d / adsx::BLK;
+    a.test_on = isinf(eps0) ? 0 : 1;
+    if (a.db >= nblk) a.test_on = 0;
+    if (!a.test_on) a.db = nblk;
+    a.K = K;
+    a.ef = ef;
+    a.max_iter = max_iter;
+    a.out_ids = oi.dev;
+    a.out_d2 = od.dev;
+    a.out_dims = odims.dev;
+    a.bitmap = g->bitmap;
+    a.bm_words = g->bm_words;
+    a.vlist = g->vlist;
+    a.vcap = g->vcap;
+    a.warps = g->warps;
+    CK(adsx::launch_test_factors(ftab, nblk, ix->D, a.test_on ? eps0 : 0.f, s, 0), "test factors");
+    CK(adsx::launch_graph_search(a, s), "graph search");
+    CK(copy_back(oi, s), "copy back");
+    CK(copy_back(od, s), "copy back");
+    CK(copy_back(odims, s), "copy back");
+    return finish(s, oi.host || od.host || odims.host, "graph search");
+}
+
+}  // extern "C"

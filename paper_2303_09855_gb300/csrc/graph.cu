@@ -1,0 +1,315 @@
+// graph.cu -- graph-based search with ADSampling DCOs (HNSW+, Sec. 4): the
+// greedy beam search HNSW runs on its base layer (Sec. 2.2.1), each DCO
+// being Algorithm 1 against the largest distance of the result set R.
+//
+// The proximity graph is a kNN graph of fixed degree <= 32 (one neighbour per
+// lane) over the vectors of an FP32 index, read in place from its
+// dim-blocked layout through a per-vertex address map.  HNSW's upper layers
+// only find a start vertex; here each query starts at the entry vertex (the
+// member nearest to the centroid) of its nearest cluster.
+//
+// graph_search_kernel: one warp per query, persistent.  R (capacity ef) is a
+// sorted array of (distance, id) with an "expanded" flag; the search set S is
+// R's unexpanded entries (an entry evicted from R cannot matter again).  Each
+// iteration expands the first unexpanded entry: its neighbours (one per lane)
+// pass an exact visited test (a per-warp bitmap over all vertices, its set
+// bits cleared after the query), then the fresh ones run Algorithm 1 against
+// r = R's largest distance, fixed for the expansion; the accepted ones are
+// sorted by a warp bitonic network and merged into R by rank.
+#include <climits>
+
+#include "adsx_internal.cuh"
+
+namespace adsx {
+namespace {
+
+constexpr int GW = 4;                       // warps per block
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ bool pless(float d1, int i1, float d2, int i2)
+{
+    return d1 < d2 || (d1 == d2 && i1 < i2);
+}
+
+// number of entries of the sorted (d, i)[0..n) that precede (x, xi)
+__device__ __forceinline__ int rank_in(const float *d, const int *i, int n, float x, int xi)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (pless(d[mid], i[mid], x, xi)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Row r of a chunk of kNN lists is vertex row0 + r: its neighbours are the
+// listed ids other than itself, -1 padded.
+__global__ void knn_to_graph_kernel(const int64_t *__restrict__ knn, int64_t N, int64_t row0,
+                                    int Kk, int degree, int32_t *__restrict__ nbr)
+{
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int k = 0;
+        for (int j = 0; j < Kk && k < degree; ++j) {
+            const int64_t v = knn[r * Kk + j];
+            if (v >= 0 && v != row0 + r) nbr[r * degree + k++] = (int32_t)v;
+        }
+        for (; k < degree; ++k) nbr[r * degree + k] = -1;
+    }
+}
+
+// vbase[id] = element offset of the vertex's block 0, vstride[id] = 16 n_c.
+__global__ void vertex_map_kernel(const int64_t *__restrict__ off, int nlist,
+                                  const int32_t *__restrict__ ids, int Dp,
+                                  int64_t *__restrict__ vbase, int32_t *__restrict__ vstride)
+{
+    for (int c = blockIdx.x; c < nlist; c += gridDim.x) {
+        const int64_t o = off[c], n = off[c + 1] - o;
+        for (int64_t m = threadIdx.x; m < n; m += blockDim.x) {
+            const int32_t id = ids[o + m];
+            vbase[id] = o * Dp + m * BLK;
+            vstride[id] = (int32_t)(n * BLK);
+        }
+    }
+}
+
+// One warp per cluster: the member nearest to the (rotated) centroid, ties
+// by id; -1 for an empty cluster.
+__global__ void cluster_entry_kernel(const float *__restrict__ data, const int64_t *__restrict__ off,
+                                     const int32_t *__restrict__ ids, const float *__restrict__ cents,
+                                     int nlist, int Dp, int64_t *__restrict__ entry)
+{
+    const int lane = threadIdx.x & 31;
+    const int nblk = Dp / BLK;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nlist; c += nw) {
+        const int64_t o = off[c], n = off[c + 1] - o;
+        const float *cb = data + o * Dp;
+        const float *cq = cents + c * Dp;
+        float best = INFINITY;
+        int bid = INT_MAX;
+        for (int64_t m = lane; m < n; m += 32) {
+            float S = 0.f;
+            for (int b = 0; b < nblk; ++b) S = accum_block_f32(cb + b * n * BLK + m * BLK, cq + b * BLK, S);
+            const int id = ids[o + m];
+            if (pless(S, id, best, bid)) {
+                best = S;
+                bid = id;
+            }
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+            const float ob = __shfl_xor_sync(FULL, best, s);
+            const int oi = __shfl_xor_sync(FULL, bid, s);
+            if (pless(ob, oi, best, bid)) {
+                best = ob;
+                bid = oi;
+            }
+        }
+        if (lane == 0) entry[c] = n > 0 ? (int64_t)bid : -1;
+    }
+}
+
+__host__ __device__ __forceinline__ size_t graph_warp_bytes(int Dp, int ef)
+{
+    const size_t cap = (size_t)ef + 32;
+    return (((size_t)Dp * 4 + cap * 4 * 6 + 32 * 8) + 15) & ~(size_t)15;
+}
+
+__global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    const int cap = g.ef + 32;
+    unsigned char *base = smraw + graph_warp_bytes(g.Dp, g.ef) * warp;
+    float *qv = reinterpret_cast<float *>(base);
+    float *rd = qv + g.Dp, *nd = rd + cap;
+    int *ri = reinterpret_cast<int *>(nd + cap), *ni = ri + cap;
+    int *rx = ni + cap, *nx = rx + cap;
+    float *ad = reinterpret_cast<float *>(nx + cap);
+    int *ai = reinterpret_cast<int *>(ad + 32);
+    const int64_t gw = (int64_t)blockIdx.x * GW + warp;
+    if (gw >= g.warps) return;
+    unsigned *bm = g.bitmap + gw * g.bm_words;
+    int32_t *vl = g.vlist + gw * g.vcap;
+
+    for (int64_t q = gw; q < g.nq; q += g.warps) {
+        for (int i = lane; i < g.Dp; i += 32) qv[i] = g.qrot[q * g.Dp + i];
+        int64_t e = g.entry[g.probes[q]];
+        if (e < 0) e = 0;
+        __syncwarp();
+        // exact distance of the start vertex (warp-cooperative over blocks)
+        float part = 0.f;
+        {
+            const float *x = g.data + g.vbase[e];
+            const int64_t st = g.vstride[e];
+            for (int b = lane; b < g.nblk; b += 32) part = accum_block_f32(x + b * st, qv + b * BLK, part);
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) part += __shfl_xor_sync(FULL, part, s);
+        unsigned long long dims = lane == 0 ? (unsigned long long)g.D : 0ull;
+        if (lane == 0) {
+            bm[e >> 5] |= 1u << (e & 31);
+            vl[0] = (int32_t)e;
+            rd[0] = part;
+            ri[0] = (int)e;
+            rx[0] = 0;
+        }
+        int vcount = 1, nR = 1;
+        __syncwarp();
+        for (int it = 0; it < g.max_iter; ++it) {
+            int u = -1;
+            for (int b0 = 0; b0 < nR; b0 += 32) {
+                const int k = b0 + lane;
+                const unsigned bb = __ballot_sync(FULL, k < nR && rx[k] == 0);
+                if (bb) {
+                    u = b0 + __ffs(bb) - 1;
+                    break;
+                }
+            }
+            if (u < 0) break;
+            const int node = ri[u];
+            const bool full = nR == g.ef;
+            const float r2 = full ? rd[nR - 1] : INFINITY;
+            const int rid = full ? ri[nR - 1] : INT_MAX;
+            __syncwarp();
+            if (lane == 0) rx[u] = 1;
+            // neighbours, one per lane, exact visited test
+            int v = -1;
+            if (lane < g.degree) v = g.nbr[(int64_t)node * g.degree + lane];
+            bool fresh = false;
+            if (v >= 0) {
+                const unsigned bit = 1u << (v & 31);
+                fresh = !(atomicOr(bm + (v >> 5), bit) & bit);
+            }
+            const unsigned fb = __ballot_sync(FULL, fresh);
+            if (fresh) vl[vcount + __popc(fb & below)] = v;
+            vcount += __popc(fb);
+            // Algorithm 1 per fresh neighbour against r2 (squared test of Sec. 3.2)
+            float S = 0.f;
+            int blk = 0;
+            bool alive = fresh, acc = false;
+            const float *x = g.data + (fresh ? g.vbase[v] : 0);
+            const int64_t st = fresh ? g.vstride[v] : 0;
+            while (__ballot_sync(FULL, alive)) {
+                if (alive) {
+                    const int e2 = blk + g.db < g.nblk ? blk + g.db : g.nblk;
+                    for (int b = blk; b < e2; ++b) S = accum_block_f32(x + b * st, qv + b * BLK, S);
+                    blk = e2;
+                    if (blk >= g.nblk) {
+                        alive = false;
+                        dims += (unsigned long long)g.D;
+                        acc = S <= r2 && (!full || pless(S, v, r2, rid));
+                    } else if (g.test_on && S > r2 * g.ftab[blk]) {
+                        alive = false;
+                        dims += (unsigned long long)(blk * BLK < g.D ? blk * BLK : g.D);
+                    }
+                }
+            }
+            const int na = __popc(__ballot_sync(FULL, acc));
+            if (na) {
+                // warp bitonic sort of the accepted (distance, id) as 64-bit keys
+                unsigned long long key = acc ? ((unsigned long long)__float_as_uint(S) << 32) | (unsigned)v
+                                             : ~0ull;
+#pragma unroll
+                for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+                    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                        const unsigned long long o = __shfl_xor_sync(FULL, key, stride);
+                        const bool lower = (lane & stride) == 0;
+                        const bool up = (lane & size) == 0;
+                        key = (lower == up) ? (o < key ? o : key) : (o > key ? o : key);
+                    }
+                }
+                if (lane < na) {
+                    ad[lane] = __uint_as_float((unsigned)(key >> 32));
+                    ai[lane] = (int)(key & 0xffffffffu);
+                }
+                __syncwarp();
+                // merge by rank into the other buffer, keeping the first ef
+                for (int k = lane; k < nR; k += 32) {
+                    const int pos = k + rank_in(ad, ai, na, rd[k], ri[k]);
+                    if (pos < g.ef) {
+                        nd[pos] = rd[k];
+                        ni[pos] = ri[k];
+                        nx[pos] = rx[k];
+                    }
+                }
+                if (lane < na) {
+                    const int pos = lane + rank_in(rd, ri, nR, ad[lane], ai[lane]);
+                    if (pos < g.ef) {
+                        nd[pos] = ad[lane];
+                        ni[pos] = ai[lane];
+                        nx[pos] = 0;
+                    }
+                }
+                __syncwarp();
+                float *tf = rd; rd = nd; nd = tf;
+                int *ti = ri; ri = ni; ni = ti;
+                ti = rx; rx = nx; nx = ti;
+                nR = nR + na < g.ef ? nR + na : g.ef;
+            }
+        }
+        for (int k = lane; k < g.K; k += 32) {
+            const bool has = k < nR;
+            g.out_ids[q * g.K + k] = has ? (int64_t)ri[k] : (int64_t)-1;
+            g.out_d2[q * g.K + k] = has ? rd[k] : INFINITY;
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) dims += __shfl_xor_sync(FULL, dims, s);
+        if (lane == 0 && g.out_dims) g.out_dims[q] = (int64_t)dims;
+        // leave the bitmap all-zero for the next query
+        __syncwarp();
+        for (int k = lane; k < vcount; k += 32) bm[vl[k] >> 5] = 0u;
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+size_t graph_search_smem(int Dp, int ef) { return graph_warp_bytes(Dp, ef) * GW; }
+int graph_search_warps_per_block() { return GW; }
+
+cudaError_t launch_knn_to_graph(const int64_t *knn, int64_t N, int64_t row0, int Kk, int degree,
+                                int32_t *nbr, cudaStream_t s)
+{
+    if (N <= 0) return cudaSuccess;
+    const int64_t blocks = (N + 255) / 256;
+    knn_to_graph_kernel<<<(unsigned)(blocks < 152 * 32 ? blocks : 152 * 32), 256, 0, s>>>(
+        knn, N, row0, Kk, degree, nbr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vertex_map(const int64_t *off, int nlist, const int32_t *ids, int Dp,
+                              int64_t *vbase, int32_t *vstride, cudaStream_t s)
+{
+    vertex_map_kernel<<<nlist < 152 * 16 ? nlist : 152 * 16, 256, 0, s>>>(off, nlist, ids, Dp, vbase,
+                                                                          vstride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cluster_entries(const float *data, const int64_t *off, const int32_t *ids,
+                                   const float *cents, int nlist, int Dp, int64_t *entry,
+                                   cudaStream_t s)
+{
+    const int blocks = (nlist + 7) / 8;
+    cluster_entry_kernel<<<blocks < 152 * 16 ? blocks : 152 * 16, 256, 0, s>>>(data, off, ids, cents,
+                                                                               nlist, Dp, entry);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_graph_search(const GraphArgs &g, cudaStream_t s)
+{
+    if (g.nq <= 0) return cudaSuccess;
+    const size_t smem = graph_search_smem(g.Dp, g.ef);
+    cudaError_t e = cudaFuncSetAttribute(graph_search_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = (g.warps + GW - 1) / GW;
+    graph_search_kernel<<<blocks, GW * 32, smem, s>>>(g);
+    return cudaGetLastError();
+}
+
+}  // namespace adsx

@@ -1,0 +1,106 @@
+"""Graph search with ADSampling DCOs (HNSW+, Sec. 4; the base-layer greedy
+beam search of Sec. 2.2.1) through the C ABI, against the FP64 oracle running
+the same algorithm on the same (exported) graph and start vertices:
+  - the kNN graph: every vertex's neighbour list equals the oracle's exact
+    IVF list (self excluded) except near-ties; the entry vertex of a cluster
+    is its member nearest to the centroid;
+  - eps0 = inf (exact DCOs: HNSW's own search) and eps0 = 2.1: returned
+    distances exact to 1e-5, no duplicates, results identical to the
+    oracle's for most queries (a beam search can take another path after one
+    FP32 near-tie), recall no worse than the oracle's minus 0.02;
+  - argument checks (K > ef, a 16-bit index).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import REL, kth_near_tie, near_tie_queries
+
+pytestmark = pytest.mark.gpu
+
+K, EF = 10, 64
+
+
+@pytest.fixture(scope="module")
+def gr():
+    from paper_2303_09855_gb300 import adsx, build
+    from paper_2303_09855_gb300 import workloads as W
+    build.build()
+    wl = W.gen_gaussian_mixture()
+    ix = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign)
+    g = adsx.build_graph(ix, wl.X, degree=32, nprobe=10)
+    Y, Cr, Qr = (oracle.rotate(wl.P, a) for a in (wl.X, wl.centroids, wl.Q))
+    nbr, ent = adsx.graph_export(g)
+    yield adsx, wl, ix, g, Y, Cr, Qr, nbr, ent
+    g.close()
+    ix.close()
+
+
+def test_graph_lists_and_entries_match_oracle(gr):
+    adsx, wl, ix, g, Y, Cr, Qr, nbr, ent = gr
+    assert nbr.shape == (wl.N, 32)
+    rows = np.random.default_rng(7).choice(wl.N, 300, replace=False)
+    eids, ed2 = oracle.ivf_exact(Y, Cr, wl.assign, Y[rows], 34, 10)
+    skip = near_tie_queries(Cr, Y[rows], 10) | kth_near_tie(ed2, 33)
+    checked = 0
+    for j, r in enumerate(rows):
+        if skip[j]:
+            continue
+        want = [v for v in eids[j] if v != r][:32]
+        assert set(nbr[r].tolist()) == set(want), r
+        checked += 1
+    assert checked >= 250
+    for c in range(wl.nlist):
+        mem = np.nonzero(wl.assign == c)[0]
+        if len(mem) == 0:
+            assert ent[c] == -1
+            continue
+        d = np.sum((Y[mem] - Cr[c]) ** 2, axis=1)
+        order = np.lexsort((mem, d))
+        if len(mem) > 1 and d[order[1]] - d[order[0]] <= REL * d[order[1]]:
+            continue
+        assert ent[c] == mem[order[0]], c
+
+
+@pytest.mark.parametrize("eps0,dd,min_same", [(math.inf, 32, 0.95), (2.1, 32, 0.9), (2.1, 16, 0.9)])
+def test_graph_search_matches_oracle(gr, eps0, dd, min_same):
+    adsx, wl, ix, g, Y, Cr, Qr, nbr, ent = gr
+    ids, d2, dims = g.search(wl.Q, K, EF, eps0=eps0, delta_d=dd, return_dims=True)
+    probes, _ = oracle.probe(Cr, Qr, 1)
+    starts = ent[probes[:, 0]]
+    oids, od2, odims, iters = oracle.graph_search(Y, nbr, starts, Qr, K, EF, eps0, dd,
+                                                  max_iter=4 * EF)
+    ok = ~near_tie_queries(Cr, Qr, 1)
+    same = 0
+    for q in range(wl.Q.shape[0]):
+        row = ids[q][ids[q] >= 0]
+        assert len(set(row.tolist())) == len(row), q
+        for i, d in zip(ids[q], d2[q]):
+            if i >= 0:
+                ex = float(np.sum((Y[i] - Qr[q]) ** 2))
+                assert abs(d - ex) <= REL * ex + 1e-6, (q, i, d, ex)
+        assert np.all(np.diff(d2[q][ids[q] >= 0]) >= -1e-6 * (1 + d2[q][0]))
+        if ok[q] and np.array_equal(ids[q], oids[q]):
+            same += 1
+    assert same >= min_same * ok.sum(), (same, int(ok.sum()))
+    gt, _ = oracle.knn_exact(Y, Qr, K)
+    assert oracle.recall_at(ids, gt, K) >= oracle.recall_at(oids, gt, K) - 0.02
+    if math.isfinite(eps0):
+        _, _, fdims = g.search(wl.Q, K, EF, eps0=math.inf, return_dims=True)
+        assert dims.sum() < fdims.sum()                      # early rejections happen
+
+
+def test_graph_argument_checks(gr):
+    adsx, wl, ix, g, Y, Cr, Qr, nbr, ent = gr
+    with pytest.raises(adsx.AdsxError):
+        g.search(wl.Q, 65, 64)                               # K > ef
+    with pytest.raises(adsx.AdsxError):
+        g.search(wl.Q, 10, 10_000)                           # ef > ADSX_MAX_EF
+    ix16 = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign, storage=adsx.BF16)
+    try:
+        with pytest.raises(adsx.AdsxError):
+            adsx.build_graph(ix16, wl.X)
+    finally:
+        ix16.close()
