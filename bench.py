@@ -85,6 +85,8 @@ def make_workload(args, device):
         nq = int(10_000 * args.scale)
         nlist = 4096 if args.scale >= 0.5 else max(64, int(4096 * args.scale))
         return W.gen_sift_like(N=N, nq=max(nq, 100), nlist=nlist, device=device)
+    if args.workload == "gist":
+        return W.gen_gist_like(N=int(1_000_000 * args.scale), nq=1000, device=device)
     return W.gen_gaussian_mixture(device=device)
 
 
