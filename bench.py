@@ -583,7 +583,7 @@ def run_graph(args):
     for name, eps0 in (("hnsw_plus", args.eps0), ("hnsw", math.inf)):
         sweep, ef_sel = [], None
         for ef in (16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512):
-            ids, _ = g.search(Qd, 10, ef, eps0=eps0, delta_d=args.delta_d)
+            ids, _ = g.search(Qd, 10, ef, eps0=eps0, delta_d=args.delta_d, n_entry=8)
             r = recall10(ids.cpu().numpy(), gt)
             sweep.append({"ef": ef, "recall10": r})
             if r >= TARGET_RECALL:
@@ -597,7 +597,7 @@ def run_graph(args):
             torch.cuda.synchronize()
             e0.record()
             ids, _, dims = g.search(Qd, 10, ef_sel, eps0=eps0, delta_d=args.delta_d,
-                                    return_dims=True)
+                                    return_dims=True, n_entry=8)
             e1.record()
             torch.cuda.synchronize()
             if st >= args.warmup:
@@ -609,6 +609,7 @@ def run_graph(args):
             "value": res["hnsw_plus"]["qps"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
             "dtype": "f32", "data": "synthetic (SIFT-shaped seeded mixture)",
             "config": {"workload": wl.name, "nq": nq, "K": 10, "degree": 32, "graph_nprobe": 16,
+                       "start_clusters": 8,
                        "eps0": args.eps0, "delta_d": args.delta_d, "graph_build_s": build_s,
                        "l2": "256 MB flush between steps"},
             "hnsw_plus": res["hnsw_plus"], "hnsw": res["hnsw"],

@@ -71,6 +71,7 @@ typedef enum { ADSX_L2 = 0, ADSX_IP = 1, ADSX_COSINE = 2 } adsx_metric;
 #define ADSX_MAX_KAC_LAYERS 1024  /* layers of a Kac-walk rotation           */
 #define ADSX_MAX_DEGREE 32    /* neighbours per vertex of a proximity graph  */
 #define ADSX_MAX_EF 512       /* result-set size of a graph search           */
+#define ADSX_MAX_GRAPH_ENTRIES 16  /* start vertices of a graph search        */
 
 /*
  * adsx_build_index -- index phase (Sec. 6.1 "Implementation", Sec. 4, Sec. 5.2).
@@ -417,7 +418,9 @@ int adsx_graph_export(const adsx_graph *graph, int32_t *neighbors, int64_t *entr
 
 /*
  * adsx_search_graph -- HNSW+: greedy beam search with a result set R of ef
- * entries (Sec. 2.2.1).  From the entry vertex, repeatedly expand the
+ * entries (Sec. 2.2.1).  R starts as the entry vertices of the query's
+ * n_entry nearest clusters (exact distances, the ef nearest kept).  Then
+ * repeatedly expand the
  * nearest not-yet-expanded entry of R: every neighbour not visited before
  * runs Algorithm 1 against r = the largest distance in R (+INF while R holds
  * fewer than ef; fixed during one expansion) and, if it reaches d = D with
@@ -427,13 +430,15 @@ int adsx_graph_export(const adsx_graph *graph, int32_t *neighbors, int64_t *entr
  *   Qv, nq, ids, dists, dims_read, eps0, delta_d   as adsx_search
  *                (eps0 = +INF: exact DCOs, i.e. HNSW's own search).
  *   K          1..ef.     ef 1..ADSX_MAX_EF.
+ *   n_entry    1..min(nlist, ADSX_MAX_GRAPH_ENTRIES).
  * The graph keeps per-warp scratch for the visited test: searches on one
  * graph must not overlap on the GPU.
  * Errors: ADSX_EINVAL, ADSX_ENOMEM, ADSX_ECUDA.
  */
 int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const float *Qv,
-                      int64_t nq, int32_t K, int32_t ef, float eps0, int32_t delta_d,
-                      int64_t *ids, float *dists, int64_t *dims_read, void *stream);
+                      int64_t nq, int32_t K, int32_t ef, int32_t n_entry, float eps0,
+                      int32_t delta_d, int64_t *ids, float *dists, int64_t *dims_read,
+                      void *stream);
 
 #ifdef __cplusplus
 }

@@ -84,7 +84,7 @@ def _load():
             lib.orc_ivf_exact_ip.argtypes = [P, i64, i32, P, i32, P, P, i64, i32, i32, P, P, cint]
             lib.orc_ivf_ads_ip.argtypes = [P, i64, i32, P, i32, P, P, i64, i32, i32,
                                            f64, i32, P, P, P, P, cint]
-            lib.orc_graph_search.argtypes = [P, i64, i32, P, i32, P, P, i64, i32, i32, i32,
+            lib.orc_graph_search.argtypes = [P, i64, i32, P, i32, P, i32, P, i64, i32, i32, i32,
                                              f64, i32, P, P, P, P, cint]
             _lib = lib
     return _lib
@@ -230,22 +230,23 @@ def graph_search(Y, graph, entries, Qr, K: int, ef: int, eps0: float, delta_d: i
                  max_iter: int = 0, nthreads: int = 0):
     """Sec. 2.2.1 / Sec. 4 (HNSW+): greedy beam search on a proximity graph
     (graph: N x Rg int32 neighbour ids, -1 = none; entries: start vertex per
-    query) whose DCOs run Algorithm 1 against the largest distance of the
-    result set of size ef, fixed for the duration of one node's expansion.
+    query, or nq x E start vertices, -1 = none) whose DCOs run Algorithm 1
+    against the largest distance of the result set of size ef, fixed for the
+    duration of one node's expansion.
     max_iter = 0 means 16 * ef expansions at most.  Returns ids, squared
     distances (K smallest of the result set), dims sampled and expansions per
     query."""
     Y = _c(Y, np.float64)
     graph = _c(graph, np.int32)
-    entries = _c(entries, np.int64)
     Qr = _c(Qr, np.float64)
     nq, D = Qr.shape
+    entries = _c(np.asarray(entries).reshape(nq, -1), np.int64)
     ids = np.empty((nq, K), np.int64)
     d2 = np.empty((nq, K), np.float64)
     dims = np.empty(nq, np.int64)
     iters = np.empty(nq, np.int64)
     _load().orc_graph_search(_p(Y), Y.shape[0], D, _p(graph), graph.shape[1], _p(entries),
-                             _p(Qr), nq, K, ef, int(max_iter or 16 * ef), float(eps0),
+                             entries.shape[1], _p(Qr), nq, K, ef, int(max_iter or 16 * ef), float(eps0),
                              int(delta_d), _p(ids), _p(d2), _p(dims), _p(iters), nthreads)
     return ids, d2, dims, iters
 

@@ -670,12 +670,12 @@ void orc_ivf_ads_ip(const double *Y, int64_t N, int32_t D, const double *Cr,
 /* into R, which keeps its N_ef smallest.  The search stops when every    */
 /* entry of R has been expanded (or after max_iter expansions).           */
 /*   graph     N x Rg int32 neighbour ids (-1 = none), by original id      */
-/*   entries   nq int64 start vertices                                     */
+/*   entries   nq x E int64 start vertices (-1 = none)                    */
 /* Outputs ids/d2 (K smallest of R by (distance, id); -1/+inf padded),    */
 /* the dims sampled and the expansions per query.                          */
 void orc_graph_search(const double *Y, int64_t N, int32_t D, const int32_t *graph,
-                      int32_t Rg, const int64_t *entries, const double *Qr, int64_t nq,
-                      int32_t K, int32_t ef, int32_t max_iter, double eps0,
+                      int32_t Rg, const int64_t *entries, int32_t E, const double *Qr,
+                      int64_t nq, int32_t K, int32_t ef, int32_t max_iter, double eps0,
                       int32_t delta_d, int64_t *ids, double *d2, int64_t *dims_total,
                       int64_t *iters_out, int nthreads)
 {
@@ -684,18 +684,26 @@ void orc_graph_search(const double *Y, int64_t N, int32_t D, const int32_t *grap
     for (int64_t q = 0; q < nq; ++q) {
         const double *qr = Qr + q * D;
         unsigned char *visited = (unsigned char *)calloc((size_t)(N > 0 ? N : 1), 1);
-        orc_pair *R = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(ef + Rg));
-        unsigned char *expd = (unsigned char *)malloc((size_t)(ef + Rg));
+        const int32_t cap = ef + (Rg > E ? Rg : E);
+        orc_pair *R = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)cap);
+        unsigned char *expd = (unsigned char *)malloc((size_t)cap);
         orc_pair *cand = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(Rg > 0 ? Rg : 1));
         int32_t nR = 0, it = 0;
         int64_t dims_sum = 0;
-        const int64_t e = entries[q];
-        visited[e] = 1;
-        R[0].d = sqdist(Y + e * D, qr, D);
-        R[0].id = e;
-        expd[0] = 0;
-        nR = 1;
-        dims_sum += D;
+        /* the start vertices (exact distances, duplicates and -1 skipped),
+           sorted by (distance, id), the ef smallest kept */
+        for (int32_t k = 0; k < E; ++k) {
+            const int64_t e = entries[q * E + k];
+            if (e < 0 || visited[e]) continue;
+            visited[e] = 1;
+            R[nR].d = sqdist(Y + e * D, qr, D);
+            R[nR].id = e;
+            expd[nR] = 0;
+            ++nR;
+            dims_sum += D;
+        }
+        qsort(R, (size_t)nR, sizeof(orc_pair), pair_cmp);
+        if (nR > ef) nR = ef;
         while (it < max_iter) {
             int32_t u = -1;
             for (int32_t k = 0; k < nR; ++k)

@@ -342,7 +342,8 @@ struct GraphArgs {
     int32_t degree;
     const int64_t *entry;       // per cluster: start vertex (-1 = empty)
     const float *qrot;          // nq x Dp rotated queries
-    const int32_t *probes;      // nq nearest clusters
+    const int32_t *probes;      // nq x n_entry nearest clusters
+    int32_t n_entry;
     const float *ftab;          // nblk + 1 test factors
     int64_t nq;
     int32_t D, Dp, nblk, db, test_on, K, ef, max_iter;
@@ -352,7 +353,7 @@ struct GraphArgs {
     unsigned *bitmap;           // warps x bm_words visited bits (all zero between queries)
     int64_t bm_words;
     int32_t *vlist;             // warps x vcap visited ids of the current query
-    int64_t vcap;               // >= 1 + max_iter * degree
+    int64_t vcap;               // >= n_entry + 1 + max_iter * degree
     int32_t warps;
 };
 size_t graph_search_smem(int Dp, int ef);

@@ -1127,8 +1127,9 @@ int adsx_graph_info(const adsx_graph *graph, int64_t *N, int32_t *degree, int32_
 }
 
 int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const float *Qv,
-                      int64_t nq, int32_t K, int32_t ef, float eps0, int32_t delta_d,
-                      int64_t *ids, float *dists, int64_t *dims_read, void *stream)
+                      int64_t nq, int32_t K, int32_t ef, int32_t n_entry, float eps0,
+                      int32_t delta_d, int64_t *ids, float *dists, int64_t *dims_read,
+                      void *stream)
 {
     const Index *ix = reinterpret_cast<const Index *>(index);
     Graph *g = const_cast<Graph *>(reinterpret_cast<const Graph *>(graph));
@@ -1140,6 +1141,8 @@ int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const fl
     if (nq < 0 || (nq > 0 && (!Qv || !ids || !dists))) return fail(ADSX_EINVAL, "bad query arguments");
     if (ef < 1 || ef > ADSX_MAX_EF) return fail(ADSX_EINVAL, "ef out of range (1..%d)", ADSX_MAX_EF);
     if (K < 1 || K > ef) return fail(ADSX_EINVAL, "K out of range (1..ef)");
+    if (n_entry < 1 || n_entry > ADSX_MAX_GRAPH_ENTRIES || n_entry > ix->nlist)
+        return fail(ADSX_EINVAL, "n_entry out of range (1..min(nlist, %d))", ADSX_MAX_GRAPH_ENTRIES);
     if (delta_d == 0) delta_d = ix->tuned_delta_d;
     if ((rc = check_blocks(delta_d, eps0))) return rc;
     if (nq == 0) return ADSX_OK;
@@ -1151,7 +1154,7 @@ int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const fl
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ix->device);
         const int32_t warps = nsm * 16;
         const int64_t bm_words = (g->N + 31) / 32;
-        const int64_t vcap = 1 + (int64_t)max_iter * g->degree;
+        const int64_t vcap = 1 + ADSX_MAX_GRAPH_ENTRIES + (int64_t)max_iter * g->degree;
         if (g->warps != warps || g->bm_words != bm_words || g->vcap < vcap) {
             cudaStreamSynchronize(s);
             cudaFree(g->bitmap);
@@ -1185,10 +1188,10 @@ int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const fl
     CK(stage_out(sc, dists, (size_t)nq * K, od), "stage dists");
     CK(stage_out(sc, dims_read, (size_t)nq, odims), "stage dims");
     CK(sc.get(&qrot, (size_t)nq * ix->Dp), "alloc q'");
-    CK(sc.get(&probes, (size_t)nq), "alloc probes");
+    CK(sc.get(&probes, (size_t)nq * n_entry), "alloc probes");
     CK(sc.get(&ftab, (size_t)nblk + 1), "alloc test factors");
     CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
-    CK(probe_queries(ix, qrot, nq, 1, probes, nullptr, sc), "entry cluster");
+    CK(probe_queries(ix, qrot, nq, n_entry, probes, nullptr, sc), "entry clusters");
     adsx::GraphArgs a;
     a.data = static_cast<const float *>(ix->data);
     a.vbase = g->vbase;
@@ -1198,6 +1201,7 @@ int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const fl
     a.entry = g->entry;
     a.qrot = qrot;
     a.probes = probes;
+    a.n_entry = n_entry;
     a.ftab = ftab;
     a.nq = nq;
     a.D = ix->D;

@@ -5,8 +5,8 @@
 // The proximity graph is a kNN graph of fixed degree <= 32 (one neighbour per
 // lane) over the vectors of an FP32 index, read in place from its
 // dim-blocked layout through a per-vertex address map.  HNSW's upper layers
-// only find a start vertex; here each query starts at the entry vertex (the
-// member nearest to the centroid) of its nearest cluster.
+// only find a start vertex; here each query starts from the entry vertices
+// (members nearest to the centroids) of its n_entry nearest clusters.
 //
 // graph_search_kernel: one warp per query, persistent.  R (capacity ef) is a
 // sorted array of (distance, id) with an "expanded" flag; the search set S is
@@ -137,27 +137,60 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
 
     for (int64_t q = gw; q < g.nq; q += g.warps) {
         for (int i = lane; i < g.Dp; i += 32) qv[i] = g.qrot[q * g.Dp + i];
-        int64_t e = g.entry[g.probes[q]];
-        if (e < 0) e = 0;
         __syncwarp();
-        // exact distance of the start vertex (warp-cooperative over blocks)
-        float part = 0.f;
-        {
+        // Start vertices: the entries of the query's n_entry nearest clusters
+        // (distinct, exact distances), sorted by (distance, id), ef kept.
+        unsigned long long dims = 0ull;
+        int vcount = 0, nR = 0;
+        for (int k = 0; k <= g.n_entry; ++k) {
+            int64_t e;
+            if (k < g.n_entry) e = g.entry[g.probes[q * g.n_entry + k]];
+            else e = nR == 0 ? 0 : -1;      // no entry at all: vertex 0
+            if (e < 0) continue;
+            bool fresh = false;
+            if (lane == 0) {
+                const unsigned bit = 1u << (e & 31);
+                fresh = !(atomicOr(bm + (e >> 5), bit) & bit);
+            }
+            if (!__shfl_sync(FULL, fresh, 0)) continue;
+            float part = 0.f;
             const float *x = g.data + g.vbase[e];
             const int64_t st = g.vstride[e];
             for (int b = lane; b < g.nblk; b += 32) part = accum_block_f32(x + b * st, qv + b * BLK, part);
-        }
 #pragma unroll
-        for (int s = 16; s > 0; s >>= 1) part += __shfl_xor_sync(FULL, part, s);
-        unsigned long long dims = lane == 0 ? (unsigned long long)g.D : 0ull;
-        if (lane == 0) {
-            bm[e >> 5] |= 1u << (e & 31);
-            vl[0] = (int32_t)e;
-            rd[0] = part;
-            ri[0] = (int)e;
-            rx[0] = 0;
+            for (int s = 16; s > 0; s >>= 1) part += __shfl_xor_sync(FULL, part, s);
+            if (lane == 0) {
+                vl[vcount] = (int32_t)e;
+                rd[nR] = part;
+                ri[nR] = (int)e;
+                dims += (unsigned long long)g.D;
+            }
+            ++vcount;
+            ++nR;
         }
-        int vcount = 1, nR = 1;
+        __syncwarp();
+        {
+            // nR <= n_entry + 1 <= 17: one warp bitonic sort of (distance, id)
+            unsigned long long key = lane < nR
+                ? ((unsigned long long)__float_as_uint(rd[lane]) << 32) | (unsigned)ri[lane] : ~0ull;
+#pragma unroll
+            for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    const unsigned long long o = __shfl_xor_sync(FULL, key, stride);
+                    const bool lower = (lane & stride) == 0;
+                    const bool up = (lane & size) == 0;
+                    key = (lower == up) ? (o < key ? o : key) : (o > key ? o : key);
+                }
+            }
+            __syncwarp();
+            if (lane < nR) {
+                rd[lane] = __uint_as_float((unsigned)(key >> 32));
+                ri[lane] = (int)(key & 0xffffffffu);
+                rx[lane] = 0;
+            }
+            if (nR > g.ef) nR = g.ef;
+        }
         __syncwarp();
         for (int it = 0; it < g.max_iter; ++it) {
             int u = -1;

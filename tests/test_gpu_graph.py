@@ -20,7 +20,7 @@ from gpu_helpers import REL, kth_near_tie, near_tie_queries
 
 pytestmark = pytest.mark.gpu
 
-K, EF = 10, 64
+K, EF, NE = 10, 64, 3
 
 
 @pytest.fixture(scope="module")
@@ -67,12 +67,12 @@ def test_graph_lists_and_entries_match_oracle(gr):
 @pytest.mark.parametrize("eps0,dd,min_same", [(math.inf, 32, 0.95), (2.1, 32, 0.9), (2.1, 16, 0.9)])
 def test_graph_search_matches_oracle(gr, eps0, dd, min_same):
     adsx, wl, ix, g, Y, Cr, Qr, nbr, ent = gr
-    ids, d2, dims = g.search(wl.Q, K, EF, eps0=eps0, delta_d=dd, return_dims=True)
-    probes, _ = oracle.probe(Cr, Qr, 1)
-    starts = ent[probes[:, 0]]
+    ids, d2, dims = g.search(wl.Q, K, EF, eps0=eps0, delta_d=dd, return_dims=True, n_entry=NE)
+    probes, _ = oracle.probe(Cr, Qr, NE)
+    starts = ent[probes]
     oids, od2, odims, iters = oracle.graph_search(Y, nbr, starts, Qr, K, EF, eps0, dd,
                                                   max_iter=4 * EF)
-    ok = ~near_tie_queries(Cr, Qr, 1)
+    ok = ~near_tie_queries(Cr, Qr, NE)
     same = 0
     for q in range(wl.Q.shape[0]):
         row = ids[q][ids[q] >= 0]
@@ -88,7 +88,7 @@ def test_graph_search_matches_oracle(gr, eps0, dd, min_same):
     gt, _ = oracle.knn_exact(Y, Qr, K)
     assert oracle.recall_at(ids, gt, K) >= oracle.recall_at(oids, gt, K) - 0.02
     if math.isfinite(eps0):
-        _, _, fdims = g.search(wl.Q, K, EF, eps0=math.inf, return_dims=True)
+        _, _, fdims = g.search(wl.Q, K, EF, eps0=math.inf, return_dims=True, n_entry=NE)
         assert dims.sum() < fdims.sum()                      # early rejections happen
 
 
@@ -98,6 +98,8 @@ def test_graph_argument_checks(gr):
         g.search(wl.Q, 65, 64)                               # K > ef
     with pytest.raises(adsx.AdsxError):
         g.search(wl.Q, 10, 10_000)                           # ef > ADSX_MAX_EF
+    with pytest.raises(adsx.AdsxError):
+        g.search(wl.Q, 10, 64, n_entry=17)                   # n_entry > ADSX_MAX_GRAPH_ENTRIES
     ix16 = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign, storage=adsx.BF16)
     try:
         with pytest.raises(adsx.AdsxError):

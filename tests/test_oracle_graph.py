@@ -2,7 +2,8 @@
 base-layer search of Sec. 2.2.1 with Algorithm 1 as its DCO, Sec. 4):
 
   - a hand-worked chain graph (points on a line, ef = 1) walks greedily to
-    the nearest point and stops there;
+    the nearest point and stops there; with two start vertices it keeps the
+    nearer one;
   - on a complete graph one expansion sees every vertex, so the result is the
     exact KNN (brute force) for any ef >= K;
   - eps0 = inf and delta_d >= D give identical results (exact DCOs);
@@ -30,6 +31,11 @@ def test_chain_graph_greedy_walk():
     assert np.allclose(d2[:, 0], [0.3 ** 2, 0.2 ** 2, 36.0])
     # ef = 1 expands exactly the vertices on the walk 0 -> 1 -> ... -> 10
     assert iters[0] == 11 and iters[1] == 1 and iters[2] == 20
+    # several start vertices: R starts as the ef nearest of them (here 19 of
+    # {0, 19}); 19's other neighbour 18 is farther, so one expansion ends it
+    ids, _, _, iters = oracle.graph_search(Y, graph, np.array([[0, 19]], np.int64),
+                                           np.array([[18.6]]), 1, 1, math.inf, 16)
+    assert ids[0, 0] == 19 and iters[0] == 1
     # the expansion cap stops the walk where it is (default 16 ef = 16 here)
     ids, _, _, iters = oracle.graph_search(Y, graph, np.zeros(1, np.int64), Q[2:], 1, 1,
                                            math.inf, 16)
