@@ -393,8 +393,8 @@ typedef struct adsx_graph adsx_graph;
  * vectors among the members of its nprobe nearest clusters (ties by id),
  * found with the library's own exact IVF search (adsx_search, eps0 = +INF);
  * each cluster's entry vertex is its member nearest to the centroid.  HNSW's
- * upper layers only locate a start vertex: a search starts at the entry of
- * the query's nearest cluster instead.  The vectors themselves are read in
+ * upper layers only locate a start vertex: a search starts from the entries
+ * of the query's nearest clusters instead.  The vectors themselves are read in
  * place from the index, which must outlive the graph.
  *   index    an FP32 index built with the L2 metric (ADSX_EINVAL otherwise).
  *   X        host or device, N x D float32: the vectors the index was built from.
