@@ -85,7 +85,7 @@ def _load():
             lib.orc_ivf_ads_ip.argtypes = [P, i64, i32, P, i32, P, P, i64, i32, i32,
                                            f64, i32, P, P, P, P, cint]
             lib.orc_graph_search.argtypes = [P, i64, i32, P, i32, P, i32, P, i64, i32, i32, i32,
-                                             f64, i32, P, P, P, P, cint]
+                                             f64, i32, i32, P, P, P, P, cint]
             _lib = lib
     return _lib
 
@@ -227,15 +227,17 @@ def ivf_pd(Y, Cr, assign, Qr, K: int, nprobe: int, delta_d: int, nthreads: int =
 
 # ------------------------------------------------------ graph search
 def graph_search(Y, graph, entries, Qr, K: int, ef: int, eps0: float, delta_d: int,
-                 max_iter: int = 0, nthreads: int = 0):
+                 max_iter: int = 0, nthreads: int = 0, pp: bool = False):
     """Sec. 2.2.1 / Sec. 4 (HNSW+): greedy beam search on a proximity graph
     (graph: N x Rg int32 neighbour ids, -1 = none; entries: start vertex per
     query, or nq x E start vertices, -1 = none) whose DCOs run Algorithm 1
     against the largest distance of the result set of size ef, fixed for the
     duration of one node's expansion.
-    max_iter = 0 means 16 * ef expansions at most.  Returns ids, squared
-    distances (K smallest of the result set), dims sampled and expansions per
-    query."""
+    max_iter = 0 means 16 * ef expansions at most.  pp: HNSW++ (Sec. 5.1),
+    the result set's roles decoupled -- the DCO threshold and the output come
+    from the K smallest exact distances, the beam (size ef) is kept with each
+    DCO's observed distance (exact at d = D, else (D/d) S_d).  Returns ids,
+    squared distances (K smallest), dims sampled and expansions per query."""
     Y = _c(Y, np.float64)
     graph = _c(graph, np.int32)
     Qr = _c(Qr, np.float64)
@@ -247,7 +249,8 @@ def graph_search(Y, graph, entries, Qr, K: int, ef: int, eps0: float, delta_d: i
     iters = np.empty(nq, np.int64)
     _load().orc_graph_search(_p(Y), Y.shape[0], D, _p(graph), graph.shape[1], _p(entries),
                              entries.shape[1], _p(Qr), nq, K, ef, int(max_iter or 16 * ef), float(eps0),
-                             int(delta_d), _p(ids), _p(d2), _p(dims), _p(iters), nthreads)
+                             int(delta_d), int(bool(pp)), _p(ids), _p(d2), _p(dims), _p(iters),
+                             nthreads)
     return ids, d2, dims, iters
 
 

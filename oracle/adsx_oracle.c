@@ -28,7 +28,8 @@
  *     in the Python wrapper.)
  *   - orc_graph_search    Sec. 2.2.1 / Sec. 4 (HNSW+): greedy beam search on
  *                         a proximity graph with Algorithm 1 DCOs against the
- *                         largest distance of the result set.
+ *                         largest distance of the result set; Sec. 5.1
+ *                         (HNSW++) with the result set's roles decoupled.
  *
  * Conventions (readings of points the paper leaves open):
  *   - distances are SQUARED Euclidean distances in the rotated space;
@@ -673,11 +674,16 @@ void orc_ivf_ads_ip(const double *Y, int64_t N, int32_t D, const double *Cr,
 /*   entries   nq x E int64 start vertices (-1 = none)                    */
 /* Outputs ids/d2 (K smallest of R by (distance, id); -1/+inf padded),    */
 /* the dims sampled and the expansions per query.                          */
+/* pp = 1: HNSW++ (Sec. 5.1) -- R's two roles decoupled: R1 (size K, exact  */
+/* distances) holds the results and gives every DCO its threshold (R1's   */
+/* largest distance); R (size N_ef) and S are kept with the observed      */
+/* distance of each DCO: exact if it reached d = D, else the estimate     */
+/* (D/d) S_d at the d where Algorithm 1 stopped.  The output is R1.       */
 void orc_graph_search(const double *Y, int64_t N, int32_t D, const int32_t *graph,
                       int32_t Rg, const int64_t *entries, int32_t E, const double *Qr,
                       int64_t nq, int32_t K, int32_t ef, int32_t max_iter, double eps0,
-                      int32_t delta_d, int64_t *ids, double *d2, int64_t *dims_total,
-                      int64_t *iters_out, int nthreads)
+                      int32_t delta_d, int32_t pp, int64_t *ids, double *d2,
+                      int64_t *dims_total, int64_t *iters_out, int nthreads)
 {
     set_threads(nthreads);
 #pragma omp parallel for schedule(dynamic)
@@ -688,7 +694,9 @@ void orc_graph_search(const double *Y, int64_t N, int32_t D, const int32_t *grap
         orc_pair *R = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)cap);
         unsigned char *expd = (unsigned char *)malloc((size_t)cap);
         orc_pair *cand = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(Rg > 0 ? Rg : 1));
-        int32_t nR = 0, it = 0;
+        orc_pair *R1 = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(K + (Rg > E ? Rg : E)));
+        orc_pair *add1 = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(Rg > 0 ? Rg : 1));
+        int32_t nR = 0, n1 = 0, it = 0;
         int64_t dims_sum = 0;
         /* the start vertices (exact distances, duplicates and -1 skipped),
            sorted by (distance, id), the ef smallest kept */
@@ -703,6 +711,7 @@ void orc_graph_search(const double *Y, int64_t N, int32_t D, const int32_t *grap
             dims_sum += D;
         }
         qsort(R, (size_t)nR, sizeof(orc_pair), pair_cmp);
+        for (int32_t k = 0; k < nR && k < K; ++k) R1[n1++] = R[k];   /* exact already */
         if (nR > ef) nR = ef;
         while (it < max_iter) {
             int32_t u = -1;
@@ -712,9 +721,13 @@ void orc_graph_search(const double *Y, int64_t N, int32_t D, const int32_t *grap
             expd[u] = 1;
             const int64_t node = R[u].id;
             const int full = nR == ef;
-            const double r2 = full ? R[nR - 1].d : INFINITY;
+            const double rmax = full ? R[nR - 1].d : INFINITY;
             const int64_t rid = full ? R[nR - 1].id : INT64_MAX;
-            int32_t nc = 0;
+            const int full1 = n1 == K;
+            const double r1max = full1 ? R1[n1 - 1].d : INFINITY;
+            const int64_t r1id = full1 ? R1[n1 - 1].id : INT64_MAX;
+            const double r2 = pp ? r1max : rmax;        /* the DCO threshold */
+            int32_t nc = 0, nc1 = 0;
             for (int32_t j = 0; j < Rg; ++j) {
                 const int32_t v = graph[node * Rg + j];
                 if (v < 0 || visited[v]) continue;
@@ -723,11 +736,30 @@ void orc_graph_search(const double *Y, int64_t N, int32_t D, const int32_t *grap
                 double S = 0.0;
                 const int res = orc_dco(Y + (int64_t)v * D, qr, D, r2, eps0, delta_d, &dims, &S, NULL);
                 dims_sum += dims;
-                if (res == ORC_POSITIVE && (!full || pair_less(S, v, r2, rid))) {
-                    cand[nc].d = S;
-                    cand[nc].id = v;
-                    ++nc;
+                if (!pp) {
+                    if (res == ORC_POSITIVE && (!full || pair_less(S, v, rmax, rid))) {
+                        cand[nc].d = S;
+                        cand[nc].id = v;
+                        ++nc;
+                    }
+                } else {
+                    const double obs = dims == D ? S : S * (double)D / (double)dims;
+                    if (res == ORC_POSITIVE && (!full1 || pair_less(S, v, r1max, r1id))) {
+                        add1[nc1].d = S;
+                        add1[nc1].id = v;
+                        ++nc1;
+                    }
+                    if (!full || pair_less(obs, v, rmax, rid)) {
+                        cand[nc].d = obs;
+                        cand[nc].id = v;
+                        ++nc;
+                    }
                 }
+            }
+            if (pp && nc1) {            /* R1: the K smallest exact distances */
+                for (int32_t k = 0; k < nc1; ++k) R1[n1 + k] = add1[k];
+                qsort(R1, (size_t)(n1 + nc1), sizeof(orc_pair), pair_cmp);
+                n1 = n1 + nc1 < K ? n1 + nc1 : K;
             }
             /* merge: R and the candidates, keep the ef smallest by (d, id) */
             for (int32_t k = 0; k < nc; ++k) {
@@ -751,12 +783,16 @@ void orc_graph_search(const double *Y, int64_t N, int32_t D, const int32_t *grap
             nR = tot < ef ? tot : ef;
             ++it;
         }
+        const orc_pair *res = pp ? R1 : R;
+        const int32_t nres = pp ? n1 : nR;
         for (int32_t k = 0; k < K; ++k) {
-            ids[q * K + k] = k < nR ? R[k].id : -1;
-            d2[q * K + k] = k < nR ? R[k].d : INFINITY;
+            ids[q * K + k] = k < nres ? res[k].id : -1;
+            d2[q * K + k] = k < nres ? res[k].d : INFINITY;
         }
         if (dims_total) dims_total[q] = dims_sum;
         if (iters_out) iters_out[q] = it;
+        free(add1);
+        free(R1);
         free(cand);
         free(expd);
         free(R);

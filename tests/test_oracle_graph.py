@@ -79,3 +79,30 @@ def test_exact_modes_agree_and_adsampling_is_exact():
         for i, d in zip(ids[q], d2[q]):
             if i >= 0:
                 assert abs(d - float(np.sum((Y[i] - Q[q]) ** 2))) <= 1e-12 * (1 + d)
+
+
+def test_hnsw_pp_reduces_to_hnsw_and_samples_fewer_dims():
+    """Sec. 5.1 (HNSW++): with exact DCOs every observed distance is exact, so
+    the beam evolves exactly as HNSW's and R1 is its first K: identical
+    results.  With ADSampling, R1's K-th distance is a tighter threshold than
+    the beam's N_ef-th, so fewer dimensions are sampled than by HNSW+;
+    returned distances stay exact and distinct."""
+    rng = np.random.default_rng(5)
+    N, D = 2000, 32
+    C = rng.normal(0, 3, size=(20, D))
+    Y = C[rng.integers(0, 20, N)] + rng.normal(size=(N, D))
+    Q = C[rng.integers(0, 20, 15)] + rng.normal(size=(15, D))
+    graph = _knn_graph(Y, 12)
+    ent = np.stack([np.zeros(15, np.int64), np.full(15, 7, np.int64)], axis=1)
+    a = oracle.graph_search(Y, graph, ent, Q, 10, 40, math.inf, 8)
+    b = oracle.graph_search(Y, graph, ent, Q, 10, 40, math.inf, 8, pp=True)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[3], b[3])
+    plus = oracle.graph_search(Y, graph, ent, Q, 10, 40, 2.1, 8)
+    ids, d2, dims, _ = oracle.graph_search(Y, graph, ent, Q, 10, 40, 2.1, 8, pp=True)
+    assert dims.sum() < plus[2].sum()
+    for q in range(15):
+        row = ids[q][ids[q] >= 0]
+        assert len(set(row.tolist())) == len(row)
+        for i, d in zip(ids[q], d2[q]):
+            if i >= 0:
+                assert abs(d - float(np.sum((Y[i] - Q[q]) ** 2))) <= 1e-12 * (1 + d)
