@@ -582,10 +582,12 @@ def run_graph(args):
     nq = Qd.shape[0]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     res = {}
-    for name, eps0 in (("hnsw_plus", args.eps0), ("hnsw", math.inf)):
+    for name, eps0, pp in (("hnsw_plus", args.eps0, False), ("hnsw_pp", args.eps0, True),
+                           ("hnsw", math.inf, False)):
         sweep, ef_sel = [], None
         for ef in (16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512):
-            ids, _ = g.search(Qd, 10, ef, eps0=eps0, delta_d=args.delta_d, n_entry=8)
+            ids, _ = g.search(Qd, 10, ef, eps0=eps0, delta_d=args.delta_d, n_entry=8,
+                              decoupled=pp)
             r = recall10(ids.cpu().numpy(), gt)
             sweep.append({"ef": ef, "recall10": r})
             if r >= TARGET_RECALL:
@@ -599,7 +601,7 @@ def run_graph(args):
             torch.cuda.synchronize()
             e0.record()
             ids, _, dims = g.search(Qd, 10, ef_sel, eps0=eps0, delta_d=args.delta_d,
-                                    return_dims=True, n_entry=8)
+                                    return_dims=True, n_entry=8, decoupled=pp)
             e1.record()
             torch.cuda.synchronize()
             if st >= args.warmup:
@@ -607,15 +609,16 @@ def run_graph(args):
         res[name] = {"ef": ef_sel, "qps": nq / (np.median(ts) * 1e-3), "ms": float(np.median(ts)),
                      "recall10": recall10(ids.cpu().numpy(), gt), "dims": float(dims.sum().item()),
                      "sweep": sweep}
-    line = {"metric": "QPS at recall@10>=0.95, graph search on a kNN graph: HNSW+ (ADSampling DCOs) vs HNSW (exact DCOs)",
+    line = {"metric": "QPS at recall@10>=0.95, graph search on a kNN graph: HNSW+ / HNSW++ (ADSampling DCOs) vs HNSW (exact DCOs)",
             "value": res["hnsw_plus"]["qps"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
             "dtype": "f32", "data": "synthetic (SIFT-shaped seeded mixture)",
             "config": {"workload": wl.name, "nq": nq, "K": 10, "degree": 32, "graph_nprobe": 16,
                        "start_clusters": 8,
                        "eps0": args.eps0, "delta_d": args.delta_d, "graph_build_s": build_s,
                        "l2": "256 MB flush between steps"},
-            "hnsw_plus": res["hnsw_plus"], "hnsw": res["hnsw"],
+            "hnsw_plus": res["hnsw_plus"], "hnsw_pp": res["hnsw_pp"], "hnsw": res["hnsw"],
             "speedup_vs_hnsw": res["hnsw"]["ms"] / res["hnsw_plus"]["ms"],
+            "speedup_pp_vs_hnsw": res["hnsw"]["ms"] / res["hnsw_pp"]["ms"],
             "dims_fraction_vs_hnsw": res["hnsw_plus"]["dims"] / res["hnsw"]["dims"]}
     print(json.dumps(line), flush=True)
     g.close()

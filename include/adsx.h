@@ -427,6 +427,11 @@ int adsx_graph_export(const adsx_graph *graph, int32_t *neighbors, int64_t *entr
  * (distance, id) below R's largest, joins R, which keeps its ef smallest.
  * The search stops when every entry of R is expanded, or after 4 ef
  * expansions.  The K smallest entries of R are returned, by (distance, id).
+ * decoupled = 1 runs HNSW++ (Sec. 5.1) instead: R's two roles are split --
+ * a set R1 of the K smallest exact distances gives every DCO its threshold
+ * (R1's largest) and is returned, while R (size ef) and the expansions use
+ * each DCO's observed distance (exact at d = D, else (D/d) S_d where
+ * Algorithm 1 stopped).
  *   Qv, nq, ids, dists, dims_read, eps0, delta_d   as adsx_search
  *                (eps0 = +INF: exact DCOs, i.e. HNSW's own search).
  *   K          1..ef.     ef 1..ADSX_MAX_EF.
@@ -436,9 +441,9 @@ int adsx_graph_export(const adsx_graph *graph, int32_t *neighbors, int64_t *entr
  * Errors: ADSX_EINVAL, ADSX_ENOMEM, ADSX_ECUDA.
  */
 int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const float *Qv,
-                      int64_t nq, int32_t K, int32_t ef, int32_t n_entry, float eps0,
-                      int32_t delta_d, int64_t *ids, float *dists, int64_t *dims_read,
-                      void *stream);
+                      int64_t nq, int32_t K, int32_t ef, int32_t n_entry, int32_t decoupled,
+                      float eps0, int32_t delta_d, int64_t *ids, float *dists,
+                      int64_t *dims_read, void *stream);
 
 #ifdef __cplusplus
 }

@@ -56,7 +56,7 @@ def load():
     lib.adsx_free_graph.argtypes = [V]
     lib.adsx_graph_info.argtypes = [V, V, V, V]
     lib.adsx_graph_export.argtypes = [V, V, V]
-    lib.adsx_search_graph.argtypes = [V, V, V, i64, i32, i32, i32, f32, i32, V, V, V, V]
+    lib.adsx_search_graph.argtypes = [V, V, V, i64, i32, i32, i32, i32, f32, i32, V, V, V, V]
     lib.adsx_build_index_kac.argtypes = [V, i64, i32, V, V, i32, V, i32, V, i32, i32, V,
                                          ctypes.POINTER(V)]
     lib.adsx_free_index.argtypes = [V]
@@ -254,9 +254,9 @@ class Graph:
             pass
 
     def search(self, Q, K, ef, eps0=2.1, delta_d=32, return_dims=False, stream=None,
-               n_entry=4):
+               n_entry=4, decoupled=False):
         return search_graph(self.index, self, Q, K, ef, eps0, delta_d, return_dims, stream,
-                            n_entry)
+                            n_entry, decoupled)
 
 
 def build_graph(index: Index, X, degree: int = 32, nprobe: int = 16, stream=None) -> Graph:
@@ -287,16 +287,18 @@ def graph_export(graph: Graph):
 
 
 def search_graph(index: Index, graph: Graph, Q, K: int, ef: int, eps0: float = 2.1,
-                 delta_d: int = 32, return_dims: bool = False, stream=None, n_entry: int = 4):
-    """adsx_search_graph (HNSW+): returns (ids, squared dists[, dims]); the search
-    starts from the entry vertices of each query's n_entry nearest clusters."""
+                 delta_d: int = 32, return_dims: bool = False, stream=None, n_entry: int = 4,
+                 decoupled: bool = False):
+    """adsx_search_graph (HNSW+, or HNSW++ with decoupled=True): returns (ids,
+    squared dists[, dims]); the search starts from the entry vertices of each
+    query's n_entry nearest clusters."""
     Q = _prep_queries(Q)
     nq = Q.shape[0]
     ids = _out(Q, (nq, K), np.int64, "int64")
     d2 = _out(Q, (nq, K), np.float32, "float32")
     dims = _out(Q, (nq,), np.int64, "int64") if return_dims else None
     _check(load().adsx_search_graph(index.handle, graph.handle, _ptr(Q), nq, int(K), int(ef),
-                                    int(n_entry), float(eps0) if math.isfinite(eps0) else float("inf"),
+                                    int(n_entry), int(bool(decoupled)), float(eps0) if math.isfinite(eps0) else float("inf"),
                                     int(delta_d), _ptr(ids), _ptr(d2), _ptr(dims),
                                     _stream_of(Q, stream)))
     return (ids, d2, dims) if return_dims else (ids, d2)

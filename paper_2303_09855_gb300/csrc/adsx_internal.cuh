@@ -347,6 +347,7 @@ struct GraphArgs {
     const float *ftab;          // nblk + 1 test factors
     int64_t nq;
     int32_t D, Dp, nblk, db, test_on, K, ef, max_iter;
+    int32_t pp;                 // 0: HNSW+, 1: HNSW++ (Sec. 5.1)
     int64_t *out_ids;
     float *out_d2;
     int64_t *out_dims;          // may be NULL
@@ -356,7 +357,7 @@ struct GraphArgs {
     int64_t vcap;               // >= n_entry + 1 + max_iter * degree
     int32_t warps;
 };
-size_t graph_search_smem(int Dp, int ef);
+size_t graph_search_smem(int Dp, int ef, int K);
 int graph_search_warps_per_block();
 cudaError_t launch_knn_to_graph(const int64_t *knn, int64_t N, int64_t row0, int Kk, int degree,
                                 int32_t *nbr, cudaStream_t s);

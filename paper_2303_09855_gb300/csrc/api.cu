@@ -1127,9 +1127,9 @@ int adsx_graph_info(const adsx_graph *graph, int64_t *N, int32_t *degree, int32_
 }
 
 int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const float *Qv,
-                      int64_t nq, int32_t K, int32_t ef, int32_t n_entry, float eps0,
-                      int32_t delta_d, int64_t *ids, float *dists, int64_t *dims_read,
-                      void *stream)
+                      int64_t nq, int32_t K, int32_t ef, int32_t n_entry, int32_t decoupled,
+                      float eps0, int32_t delta_d, int64_t *ids, float *dists,
+                      int64_t *dims_read, void *stream)
 {
     const Index *ix = reinterpret_cast<const Index *>(index);
     Graph *g = const_cast<Graph *>(reinterpret_cast<const Graph *>(graph));
@@ -1141,6 +1141,7 @@ int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const fl
     if (nq < 0 || (nq > 0 && (!Qv || !ids || !dists))) return fail(ADSX_EINVAL, "bad query arguments");
     if (ef < 1 || ef > ADSX_MAX_EF) return fail(ADSX_EINVAL, "ef out of range (1..%d)", ADSX_MAX_EF);
     if (K < 1 || K > ef) return fail(ADSX_EINVAL, "K out of range (1..ef)");
+    if (decoupled != 0 && decoupled != 1) return fail(ADSX_EINVAL, "decoupled must be 0 or 1");
     if (n_entry < 1 || n_entry > ADSX_MAX_GRAPH_ENTRIES || n_entry > ix->nlist)
         return fail(ADSX_EINVAL, "n_entry out of range (1..min(nlist, %d))", ADSX_MAX_GRAPH_ENTRIES);
     if (delta_d == 0) delta_d = ix->tuned_delta_d;
@@ -1214,6 +1215,7 @@ int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const fl
     a.K = K;
     a.ef = ef;
     a.max_iter = max_iter;
+    a.pp = decoupled;
     a.out_ids = oi.dev;
     a.out_d2 = od.dev;
     a.out_dims = odims.dev;

@@ -8,7 +8,9 @@
 // only find a start vertex; here each query starts from the entry vertices
 // (members nearest to the centroids) of its n_entry nearest clusters.
 //
-// graph_search_kernel: one warp per query, persistent.  R (capacity ef) is a
+// graph_search_kernel: one warp per query, persistent (HNSW+; with pp set,
+// HNSW++ of Sec. 5.1: an exact K-set R1 gives the DCO threshold and the
+// output, the beam keeps each DCO's observed distance).  R (capacity ef) is a
 // sorted array of (distance, id) with an "expanded" flag; the search set S is
 // R's unexpanded entries (an entry evicted from R cannot matter again).  Each
 // iteration expands the first unexpanded entry: its neighbours (one per lane)
@@ -111,10 +113,77 @@ __global__ void cluster_entry_kernel(const float *__restrict__ data, const int64
     }
 }
 
-__host__ __device__ __forceinline__ size_t graph_warp_bytes(int Dp, int ef)
+// One warp's shared memory: the query, the beam R (two buffers of distance,
+// id and expanded flag), the exact K-set R1 of HNSW++ (two buffers) and two
+// 32-entry staging areas for sorted additions.
+__host__ __device__ __forceinline__ size_t graph_warp_bytes(int Dp, int ef, int K)
 {
-    const size_t cap = (size_t)ef + 32;
-    return (((size_t)Dp * 4 + cap * 4 * 6 + 32 * 8) + 15) & ~(size_t)15;
+    const size_t cap = (size_t)ef + 32, cap1 = (size_t)K + 32;
+    return (((size_t)Dp * 4 + cap * 4 * 6 + cap1 * 4 * 4 + 32 * 8 * 2) + 15) & ~(size_t)15;
+}
+
+// Ascending bitonic sort of one 64-bit key per lane.
+__device__ __forceinline__ unsigned long long warp_sort32(unsigned long long key, int lane)
+{
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(FULL, key, stride);
+            const bool lower = (lane & stride) == 0;
+            const bool up = (lane & size) == 0;
+            key = (lower == up) ? (o < key ? o : key) : (o > key ? o : key);
+        }
+    }
+    return key;
+}
+
+__device__ __forceinline__ unsigned long long dkey(float d, int id)
+{
+    return ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)id;   // d >= 0
+}
+
+// Merges the sorted (cd, ci[, cx])[0..n) and the sorted additions (ad, ai)[0..na)
+// into (nd, ni[, nx]), keeping the first `keep`; additions get flag 0.  Returns
+// the new count.  Entries are distinct, so every position is written once.
+__device__ __forceinline__ int warp_merge(const float *cd, const int *ci, const int *cx, int n,
+                                          const float *ad, const int *ai, int na, float *nd,
+                                          int *ni, int *nx, int keep, int lane)
+{
+    for (int k = lane; k < n; k += 32) {
+        const int pos = k + rank_in(ad, ai, na, cd[k], ci[k]);
+        if (pos < keep) {
+            nd[pos] = cd[k];
+            ni[pos] = ci[k];
+            if (nx) nx[pos] = cx[k];
+        }
+    }
+    if (lane < na) {
+        const int pos = lane + rank_in(cd, ci, n, ad[lane], ai[lane]);
+        if (pos < keep) {
+            nd[pos] = ad[lane];
+            ni[pos] = ai[lane];
+            if (nx) nx[pos] = 0;
+        }
+    }
+    __syncwarp();
+    return n + na < keep ? n + na : keep;
+}
+
+// Stages the lanes' keys with `take` sorted into (ad, ai); returns their count.
+__device__ __forceinline__ int stage_sorted(bool take, float d, int id, float *ad, int *ai,
+                                            int lane)
+{
+    const int na = __popc(__ballot_sync(FULL, take));
+    if (na) {
+        const unsigned long long key = warp_sort32(take ? dkey(d, id) : ~0ull, lane);
+        if (lane < na) {
+            ad[lane] = __uint_as_float((unsigned)(key >> 32));
+            ai[lane] = (int)(key & 0xffffffffu);
+        }
+        __syncwarp();
+    }
+    return na;
 }
 
 __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
@@ -122,14 +191,18 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
     extern __shared__ __align__(16) unsigned char smraw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned below = (1u << lane) - 1u;
-    const int cap = g.ef + 32;
-    unsigned char *base = smraw + graph_warp_bytes(g.Dp, g.ef) * warp;
+    const int cap = g.ef + 32, cap1 = g.K + 32;
+    unsigned char *base = smraw + graph_warp_bytes(g.Dp, g.ef, g.K) * warp;
     float *qv = reinterpret_cast<float *>(base);
     float *rd = qv + g.Dp, *nd = rd + cap;
     int *ri = reinterpret_cast<int *>(nd + cap), *ni = ri + cap;
     int *rx = ni + cap, *nx = rx + cap;
-    float *ad = reinterpret_cast<float *>(nx + cap);
+    float *kd = reinterpret_cast<float *>(nx + cap), *kd2 = kd + cap1;
+    int *ki = reinterpret_cast<int *>(kd2 + cap1), *ki2 = ki + cap1;
+    float *ad = reinterpret_cast<float *>(ki2 + cap1);
     int *ai = reinterpret_cast<int *>(ad + 32);
+    float *ad1 = reinterpret_cast<float *>(ai + 32);
+    int *ai1 = reinterpret_cast<int *>(ad1 + 32);
     const int64_t gw = (int64_t)blockIdx.x * GW + warp;
     if (gw >= g.warps) return;
     unsigned *bm = g.bitmap + gw * g.bm_words;
@@ -141,7 +214,7 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
         // Start vertices: the entries of the query's n_entry nearest clusters
         // (distinct, exact distances), sorted by (distance, id), ef kept.
         unsigned long long dims = 0ull;
-        int vcount = 0, nR = 0;
+        int vcount = 0, nR = 0, n1 = 0;
         for (int k = 0; k <= g.n_entry; ++k) {
             int64_t e;
             if (k < g.n_entry) e = g.entry[g.probes[q * g.n_entry + k]];
@@ -170,25 +243,19 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
         }
         __syncwarp();
         {
-            // nR <= n_entry + 1 <= 17: one warp bitonic sort of (distance, id)
-            unsigned long long key = lane < nR
-                ? ((unsigned long long)__float_as_uint(rd[lane]) << 32) | (unsigned)ri[lane] : ~0ull;
-#pragma unroll
-            for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-                for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                    const unsigned long long o = __shfl_xor_sync(FULL, key, stride);
-                    const bool lower = (lane & stride) == 0;
-                    const bool up = (lane & size) == 0;
-                    key = (lower == up) ? (o < key ? o : key) : (o > key ? o : key);
-                }
-            }
+            // nR <= n_entry + 1 <= 17 start vertices: one warp sort
+            const unsigned long long key = warp_sort32(lane < nR ? dkey(rd[lane], ri[lane]) : ~0ull, lane);
             __syncwarp();
             if (lane < nR) {
                 rd[lane] = __uint_as_float((unsigned)(key >> 32));
                 ri[lane] = (int)(key & 0xffffffffu);
                 rx[lane] = 0;
+                if (lane < g.K) {           // HNSW++: R1 starts as the K nearest (exact)
+                    kd[lane] = rd[lane];
+                    ki[lane] = ri[lane];
+                }
             }
+            n1 = nR < g.K ? nR : g.K;
             if (nR > g.ef) nR = g.ef;
         }
         __syncwarp();
@@ -204,9 +271,12 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
             }
             if (u < 0) break;
             const int node = ri[u];
-            const bool full = nR == g.ef;
-            const float r2 = full ? rd[nR - 1] : INFINITY;
+            const bool full = nR == g.ef, full1 = n1 == g.K;
+            const float rmax = full ? rd[nR - 1] : INFINITY;
             const int rid = full ? ri[nR - 1] : INT_MAX;
+            const float r1max = full1 ? kd[n1 - 1] : INFINITY;
+            const int r1id = full1 ? ki[n1 - 1] : INT_MAX;
+            const float r2 = g.pp ? r1max : rmax;           // the DCO threshold
             __syncwarp();
             if (lane == 0) rx[u] = 1;
             // neighbours, one per lane, exact visited test
@@ -223,7 +293,7 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
             // Algorithm 1 per fresh neighbour against r2 (squared test of Sec. 3.2)
             float S = 0.f;
             int blk = 0;
-            bool alive = fresh, acc = false;
+            bool alive = fresh, atD = false;
             const float *x = g.data + (fresh ? g.vbase[v] : 0);
             const int64_t st = fresh ? g.vstride[v] : 0;
             while (__ballot_sync(FULL, alive)) {
@@ -233,62 +303,51 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
                     blk = e2;
                     if (blk >= g.nblk) {
                         alive = false;
+                        atD = true;
                         dims += (unsigned long long)g.D;
-                        acc = S <= r2 && (!full || pless(S, v, r2, rid));
                     } else if (g.test_on && S > r2 * g.ftab[blk]) {
                         alive = false;
                         dims += (unsigned long long)(blk * BLK < g.D ? blk * BLK : g.D);
                     }
                 }
             }
-            const int na = __popc(__ballot_sync(FULL, acc));
+            const bool positive = atD && S <= r2;
+            bool take_r, take_1 = false;
+            float key_r = S;
+            if (!g.pp) {
+                // HNSW+: exact distances enter R when below its largest
+                take_r = positive && (!full || pless(S, v, rmax, rid));
+            } else {
+                // HNSW++: positives enter R1; R and S keep the observed
+                // distance (exact at d = D, else (D/d) S_d)
+                const int d = blk * BLK < g.D ? blk * BLK : g.D;
+                key_r = atD ? S : S * ((float)g.D / (float)d);
+                take_1 = positive && (!full1 || pless(S, v, r1max, r1id));
+                take_r = fresh && (!full || pless(key_r, v, rmax, rid));
+            }
+            const int na = stage_sorted(take_r, key_r, v, ad, ai, lane);
             if (na) {
-                // warp bitonic sort of the accepted (distance, id) as 64-bit keys
-                unsigned long long key = acc ? ((unsigned long long)__float_as_uint(S) << 32) | (unsigned)v
-                                             : ~0ull;
-#pragma unroll
-                for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-                    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                        const unsigned long long o = __shfl_xor_sync(FULL, key, stride);
-                        const bool lower = (lane & stride) == 0;
-                        const bool up = (lane & size) == 0;
-                        key = (lower == up) ? (o < key ? o : key) : (o > key ? o : key);
-                    }
-                }
-                if (lane < na) {
-                    ad[lane] = __uint_as_float((unsigned)(key >> 32));
-                    ai[lane] = (int)(key & 0xffffffffu);
-                }
-                __syncwarp();
-                // merge by rank into the other buffer, keeping the first ef
-                for (int k = lane; k < nR; k += 32) {
-                    const int pos = k + rank_in(ad, ai, na, rd[k], ri[k]);
-                    if (pos < g.ef) {
-                        nd[pos] = rd[k];
-                        ni[pos] = ri[k];
-                        nx[pos] = rx[k];
-                    }
-                }
-                if (lane < na) {
-                    const int pos = lane + rank_in(rd, ri, nR, ad[lane], ai[lane]);
-                    if (pos < g.ef) {
-                        nd[pos] = ad[lane];
-                        ni[pos] = ai[lane];
-                        nx[pos] = 0;
-                    }
-                }
-                __syncwarp();
+                nR = warp_merge(rd, ri, rx, nR, ad, ai, na, nd, ni, nx, g.ef, lane);
                 float *tf = rd; rd = nd; nd = tf;
                 int *ti = ri; ri = ni; ni = ti;
                 ti = rx; rx = nx; nx = ti;
-                nR = nR + na < g.ef ? nR + na : g.ef;
+            }
+            if (g.pp) {
+                const int n1a = stage_sorted(take_1, S, v, ad1, ai1, lane);
+                if (n1a) {
+                    n1 = warp_merge(kd, ki, nullptr, n1, ad1, ai1, n1a, kd2, ki2, nullptr, g.K, lane);
+                    float *tf = kd; kd = kd2; kd2 = tf;
+                    int *ti = ki; ki = ki2; ki2 = ti;
+                }
             }
         }
+        const float *od = g.pp ? kd : rd;
+        const int *oi = g.pp ? ki : ri;
+        const int no = g.pp ? n1 : nR;
         for (int k = lane; k < g.K; k += 32) {
-            const bool has = k < nR;
-            g.out_ids[q * g.K + k] = has ? (int64_t)ri[k] : (int64_t)-1;
-            g.out_d2[q * g.K + k] = has ? rd[k] : INFINITY;
+            const bool has = k < no;
+            g.out_ids[q * g.K + k] = has ? (int64_t)oi[k] : (int64_t)-1;
+            g.out_d2[q * g.K + k] = has ? od[k] : INFINITY;
         }
 #pragma unroll
         for (int s = 16; s > 0; s >>= 1) dims += __shfl_xor_sync(FULL, dims, s);
@@ -302,7 +361,7 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
 
 }  // namespace
 
-size_t graph_search_smem(int Dp, int ef) { return graph_warp_bytes(Dp, ef) * GW; }
+size_t graph_search_smem(int Dp, int ef, int K) { return graph_warp_bytes(Dp, ef, K) * GW; }
 int graph_search_warps_per_block() { return GW; }
 
 cudaError_t launch_knn_to_graph(const int64_t *knn, int64_t N, int64_t row0, int Kk, int degree,
@@ -336,7 +395,7 @@ cudaError_t launch_cluster_entries(const float *data, const int64_t *off, const 
 cudaError_t launch_graph_search(const GraphArgs &g, cudaStream_t s)
 {
     if (g.nq <= 0) return cudaSuccess;
-    const size_t smem = graph_search_smem(g.Dp, g.ef);
+    const size_t smem = graph_search_smem(g.Dp, g.ef, g.K);
     cudaError_t e = cudaFuncSetAttribute(graph_search_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

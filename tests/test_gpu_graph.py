@@ -4,10 +4,11 @@ the same algorithm on the same (exported) graph and start vertices:
   - the kNN graph: every vertex's neighbour list equals the oracle's exact
     IVF list (self excluded) except near-ties; the entry vertex of a cluster
     is its member nearest to the centroid;
-  - eps0 = inf (exact DCOs: HNSW's own search) and eps0 = 2.1: returned
-    distances exact to 1e-5, no duplicates, results identical to the
-    oracle's for most queries (a beam search can take another path after one
-    FP32 near-tie), recall no worse than the oracle's minus 0.02;
+  - eps0 = inf (exact DCOs: HNSW's own search) and eps0 = 2.1, for HNSW+
+    and HNSW++ (Sec. 5.1): returned distances exact to 1e-5, no duplicates,
+    results identical to the oracle's for most queries (a beam search can
+    take another path after one FP32 near-tie), recall no worse than the
+    oracle's minus 0.02; HNSW++ with exact DCOs equals HNSW bit for bit;
   - argument checks (K > ef, a 16-bit index).
 """
 import math
@@ -64,14 +65,17 @@ def test_graph_lists_and_entries_match_oracle(gr):
         assert ent[c] == mem[order[0]], c
 
 
-@pytest.mark.parametrize("eps0,dd,min_same", [(math.inf, 32, 0.95), (2.1, 32, 0.9), (2.1, 16, 0.9)])
-def test_graph_search_matches_oracle(gr, eps0, dd, min_same):
+@pytest.mark.parametrize("eps0,dd,pp,min_same", [(math.inf, 32, False, 0.95),
+                                                  (2.1, 32, False, 0.9), (2.1, 16, False, 0.9),
+                                                  (math.inf, 32, True, 0.95), (2.1, 32, True, 0.85)])
+def test_graph_search_matches_oracle(gr, eps0, dd, pp, min_same):
     adsx, wl, ix, g, Y, Cr, Qr, nbr, ent = gr
-    ids, d2, dims = g.search(wl.Q, K, EF, eps0=eps0, delta_d=dd, return_dims=True, n_entry=NE)
+    ids, d2, dims = g.search(wl.Q, K, EF, eps0=eps0, delta_d=dd, return_dims=True, n_entry=NE,
+                             decoupled=pp)
     probes, _ = oracle.probe(Cr, Qr, NE)
     starts = ent[probes]
     oids, od2, odims, iters = oracle.graph_search(Y, nbr, starts, Qr, K, EF, eps0, dd,
-                                                  max_iter=4 * EF)
+                                                  max_iter=4 * EF, pp=pp)
     ok = ~near_tie_queries(Cr, Qr, NE)
     same = 0
     for q in range(wl.Q.shape[0]):
@@ -90,6 +94,9 @@ def test_graph_search_matches_oracle(gr, eps0, dd, min_same):
     if math.isfinite(eps0):
         _, _, fdims = g.search(wl.Q, K, EF, eps0=math.inf, return_dims=True, n_entry=NE)
         assert dims.sum() < fdims.sum()                      # early rejections happen
+    if pp and not math.isfinite(eps0):                       # HNSW++ with exact DCOs is HNSW
+        h_ids, h_d2 = g.search(wl.Q, K, EF, eps0=math.inf, n_entry=NE)
+        assert np.array_equal(ids, h_ids) and np.array_equal(d2, h_d2)
 
 
 def test_graph_argument_checks(gr):
