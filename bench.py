@@ -49,6 +49,12 @@ def parse():
                     help="headline = the SIFT-shaped QPS@recall metric (default); the others "
                          "measure the batched uneven, serving and precision forms")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--start-clusters", type=int, default=8,
+                    help="graph mode: clusters whose entry vertices start a search")
+    ap.add_argument("--graph-nprobe", type=int, default=16,
+                    help="graph mode: clusters searched for each vertex's neighbours")
+    ap.add_argument("--cluster-entries", type=int, default=4,
+                    help="graph mode: entry vertices per cluster (farthest-point samples)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -575,7 +581,8 @@ def run_graph(args):
         wl = W.gen_sift_like(N=int(1_000_000 * args.scale), nq=int(10_000 * args.scale), device=dev)
     ix = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign)
     t0 = time.perf_counter()
-    g = adsx.build_graph(ix, wl.X, degree=32, nprobe=16)
+    g = adsx.build_graph(ix, wl.X, degree=32, nprobe=args.graph_nprobe,
+                         entries_per_cluster=args.cluster_entries)
     build_s = time.perf_counter() - t0
     gt = ground_truth(wl.X, wl.Q, 10, dev)
     Qd = torch.from_numpy(wl.Q).to(dev)
@@ -586,8 +593,8 @@ def run_graph(args):
                            ("hnsw", math.inf, False)):
         sweep, ef_sel = [], None
         for ef in (16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512):
-            ids, _ = g.search(Qd, 10, ef, eps0=eps0, delta_d=args.delta_d, n_entry=8,
-                              decoupled=pp)
+            ids, _ = g.search(Qd, 10, ef, eps0=eps0, delta_d=args.delta_d,
+                              n_entry=args.start_clusters, decoupled=pp)
             r = recall10(ids.cpu().numpy(), gt)
             sweep.append({"ef": ef, "recall10": r})
             if r >= TARGET_RECALL:
@@ -601,7 +608,7 @@ def run_graph(args):
             torch.cuda.synchronize()
             e0.record()
             ids, _, dims = g.search(Qd, 10, ef_sel, eps0=eps0, delta_d=args.delta_d,
-                                    return_dims=True, n_entry=8, decoupled=pp)
+                                    return_dims=True, n_entry=args.start_clusters, decoupled=pp)
             e1.record()
             torch.cuda.synchronize()
             if st >= args.warmup:
@@ -611,9 +618,12 @@ def run_graph(args):
                      "sweep": sweep}
     line = {"metric": "QPS at recall@10>=0.95, graph search on a kNN graph: HNSW+ / HNSW++ (ADSampling DCOs) vs HNSW (exact DCOs)",
             "value": res["hnsw_plus"]["qps"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
-            "dtype": "f32", "data": "synthetic (SIFT-shaped seeded mixture)",
-            "config": {"workload": wl.name, "nq": nq, "K": 10, "degree": 32, "graph_nprobe": 16,
-                       "start_clusters": 8,
+            "dtype": "f32",
+            "data": "synthetic (%s-shaped seeded mixture)" % ("GIST" if args.workload == "gist" else "SIFT"),
+            "config": {"workload": wl.name, "nq": nq, "K": 10, "degree": 32,
+                       "graph_nprobe": args.graph_nprobe,
+                       "start_clusters": args.start_clusters,
+                       "entries_per_cluster": args.cluster_entries,
                        "eps0": args.eps0, "delta_d": args.delta_d, "graph_build_s": build_s,
                        "l2": "256 MB flush between steps"},
             "hnsw_plus": res["hnsw_plus"], "hnsw_pp": res["hnsw_pp"], "hnsw": res["hnsw"],

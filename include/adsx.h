@@ -71,7 +71,8 @@ typedef enum { ADSX_L2 = 0, ADSX_IP = 1, ADSX_COSINE = 2 } adsx_metric;
 #define ADSX_MAX_KAC_LAYERS 1024  /* layers of a Kac-walk rotation           */
 #define ADSX_MAX_DEGREE 32    /* neighbours per vertex of a proximity graph  */
 #define ADSX_MAX_EF 512       /* result-set size of a graph search           */
-#define ADSX_MAX_GRAPH_ENTRIES 16  /* start vertices of a graph search        */
+#define ADSX_MAX_GRAPH_ENTRIES 16  /* start clusters of a graph search        */
+#define ADSX_MAX_CLUSTER_ENTRIES 64 /* entry vertices per cluster of a graph  */
 
 /*
  * adsx_build_index -- index phase (Sec. 6.1 "Implementation", Sec. 4, Sec. 5.2).
@@ -391,35 +392,46 @@ typedef struct adsx_graph adsx_graph;
 /*
  * adsx_build_graph -- vertex x's neighbours are its `degree` nearest other
  * vectors among the members of its nprobe nearest clusters (ties by id),
- * found with the library's own exact IVF search (adsx_search, eps0 = +INF);
- * each cluster's entry vertex is its member nearest to the centroid.  HNSW's
- * upper layers only locate a start vertex: a search starts from the entries
- * of the query's nearest clusters instead.  The vectors themselves are read in
- * place from the index, which must outlive the graph.
+ * found with the library's own exact IVF search (adsx_search, eps0 = +INF).
+ * HNSW's upper layers only locate a start vertex: a search starts from the
+ * entry vertices of the query's nearest clusters instead.  A cluster's E =
+ * entries_per_cluster entries are chosen by farthest-point sampling: entry 0
+ * is its member nearest to the centroid, entry e its member whose squared
+ * distance to the nearest of entries 0..e-1 is largest (ties by id; -1 once
+ * that distance is 0, and for an empty cluster).  A k-means cluster can hold
+ * parts of the kNN graph that no edge joins; E > 1 gives each a start, and a
+ * larger E makes the entries a small upper layer (the query starts from the
+ * nearest of them).  The
+ * vectors themselves are read in place from the index, which must outlive
+ * the graph.
  *   index    an FP32 index built with the L2 metric (ADSX_EINVAL otherwise).
  *   X        host or device, N x D float32: the vectors the index was built from.
  *   degree   1..ADSX_MAX_DEGREE.   nprobe 1..min(nlist, ADSX_MAX_NPROBE).
+ *   entries_per_cluster   1..ADSX_MAX_CLUSTER_ENTRIES.
  *   out      receives the graph (owns its device memory).
  * Errors: ADSX_EINVAL, ADSX_ENOMEM, ADSX_ECUDA.
  */
 int adsx_build_graph(const adsx_index *index, const float *X, int32_t degree,
-                     int32_t nprobe, void *stream, adsx_graph **out);
+                     int32_t nprobe, int32_t entries_per_cluster, void *stream,
+                     adsx_graph **out);
 
 /* Frees the graph and its device memory (synchronises the device). */
 int adsx_free_graph(adsx_graph *graph);
 
 /* Shape of a graph: any output pointer may be NULL. */
-int adsx_graph_info(const adsx_graph *graph, int64_t *N, int32_t *degree, int32_t *nlist);
+int adsx_graph_info(const adsx_graph *graph, int64_t *N, int32_t *degree, int32_t *nlist,
+                    int32_t *entries_per_cluster);
 
-/* Copies the neighbour lists (N x degree int32, -1 = none) and the per-cluster
- * entry vertices (nlist int64, -1 = empty cluster) to host or device memory
- * (either pointer may be NULL). */
+/* Copies the neighbour lists (N x degree int32, -1 = none) and the entry
+ * vertices (nlist x entries_per_cluster int64, row-major, -1 = none) to host
+ * or device memory (either pointer may be NULL). */
 int adsx_graph_export(const adsx_graph *graph, int32_t *neighbors, int64_t *entries);
 
 /*
  * adsx_search_graph -- HNSW+: greedy beam search with a result set R of ef
  * entries (Sec. 2.2.1).  R starts as the entry vertices of the query's
- * n_entry nearest clusters (exact distances, the ef nearest kept).  Then
+ * n_entry nearest clusters (all of their entries: distinct, exact distances,
+ * the ef nearest kept; vertex 0 if none exists).  Then
  * repeatedly expand the
  * nearest not-yet-expanded entry of R: every neighbour not visited before
  * runs Algorithm 1 against r = the largest distance in R (+INF while R holds

@@ -26,6 +26,9 @@ Functions (each follows the passage named in its docstring):
   kac_matrix(pairs, cs, D)          rotation, and its dense matrix
   graph_search(...)                 Sec. 2.2.1 / Sec. 4 (HNSW+): beam search on a
                                     proximity graph with Algorithm 1 DCOs
+  cluster_entries(Y, Cr, assign, E) start vertices of the graph search (stand-in
+                                    for HNSW's upper layers, Sec. 2.2.1):
+                                    farthest-point samples per cluster
 """
 from __future__ import annotations
 
@@ -252,6 +255,35 @@ def graph_search(Y, graph, entries, Qr, K: int, ef: int, eps0: float, delta_d: i
                              int(delta_d), int(bool(pp)), _p(ids), _p(d2), _p(dims), _p(iters),
                              nthreads)
     return ids, d2, dims, iters
+
+
+def cluster_entries(Y, Cr, assign, E: int):
+    """Start vertices of the graph search, E per cluster (HNSW's upper layers
+    only deliver a start vertex to the base layer, Sec. 2.2.1; clusters stand
+    in for them).  Entry 0 of cluster c is its member nearest to the centroid
+    Cr[c]; entry e is the member whose squared distance to the nearest of
+    entries 0..e-1 is largest (farthest-point sampling); ties go to the lower
+    id.  -1 once that largest distance is 0 (every member coincides with a
+    chosen entry) and for an empty cluster.  FP64; returns nlist x E int64."""
+    Y = np.asarray(Y, np.float64)
+    Cr = np.asarray(Cr, np.float64)
+    assign = np.asarray(assign)
+    out = np.full((Cr.shape[0], E), -1, np.int64)
+    for c in range(Cr.shape[0]):
+        mem = np.nonzero(assign == c)[0]                 # ascending ids
+        if len(mem) == 0:
+            continue
+        to_c = np.sum((Y[mem] - Cr[c]) ** 2, axis=1)
+        pick = int(np.argmin(to_c))                      # first minimum = lowest id
+        out[c, 0] = mem[pick]
+        nearest = np.full(len(mem), np.inf)
+        for e in range(1, E):
+            nearest = np.minimum(nearest, np.sum((Y[mem] - Y[mem[pick]]) ** 2, axis=1))
+            pick = int(np.argmax(nearest))               # first maximum = lowest id
+            if not nearest[pick] > 0.0:
+                break
+            out[c, e] = mem[pick]
+    return out
 
 
 # ------------------------------------------------------ Kac's walk

@@ -52,9 +52,9 @@ def load():
     lib.adsx_build_index_metric.argtypes = [V, i64, i32, V, V, i32, V, i32, i32, V,
                                             ctypes.POINTER(V)]
     lib.adsx_index_metric.argtypes = [V, V]
-    lib.adsx_build_graph.argtypes = [V, V, i32, i32, V, ctypes.POINTER(V)]
+    lib.adsx_build_graph.argtypes = [V, V, i32, i32, i32, V, ctypes.POINTER(V)]
     lib.adsx_free_graph.argtypes = [V]
-    lib.adsx_graph_info.argtypes = [V, V, V, V]
+    lib.adsx_graph_info.argtypes = [V, V, V, V, V]
     lib.adsx_graph_export.argtypes = [V, V, V]
     lib.adsx_search_graph.argtypes = [V, V, V, i64, i32, i32, i32, i32, f32, i32, V, V, V, V]
     lib.adsx_build_index_kac.argtypes = [V, i64, i32, V, V, i32, V, i32, V, i32, i32, V,
@@ -238,9 +238,11 @@ class Graph:
     def __init__(self, handle, index):
         self.handle = handle
         self.index = index                 # the graph reads the index's vectors
-        N, deg, nl = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
-        _check(load().adsx_graph_info(handle, ctypes.byref(N), ctypes.byref(deg), ctypes.byref(nl)))
+        N, deg, nl, ne = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().adsx_graph_info(handle, ctypes.byref(N), ctypes.byref(deg), ctypes.byref(nl),
+                                      ctypes.byref(ne)))
         self.N, self.degree, self.nlist = N.value, deg.value, nl.value
+        self.entries_per_cluster = ne.value
 
     def close(self):
         if self.handle:
@@ -259,13 +261,16 @@ class Graph:
                             n_entry, decoupled)
 
 
-def build_graph(index: Index, X, degree: int = 32, nprobe: int = 16, stream=None) -> Graph:
+def build_graph(index: Index, X, degree: int = 32, nprobe: int = 16,
+                entries_per_cluster: int = 4, stream=None) -> Graph:
     """adsx_build_graph: a kNN proximity graph over the index's vectors (X: the
-    raw vectors the index was built from)."""
+    raw vectors the index was built from) with entries_per_cluster
+    farthest-point entry vertices per cluster."""
     X = _host(X, np.float32) if not _is_torch_cuda(X) else X.contiguous()
     h = ctypes.c_void_p()
     _check(load().adsx_build_graph(index.handle, _ptr(X), int(degree), int(nprobe),
-                                   _stream_of(None, stream), ctypes.byref(h)))
+                                   int(entries_per_cluster), _stream_of(None, stream),
+                                   ctypes.byref(h)))
     return Graph(h, index)
 
 
@@ -274,14 +279,15 @@ def free_graph(graph: Graph):
 
 
 def graph_info(graph: Graph):
-    """adsx_graph_info: (N, degree, nlist)."""
-    return graph.N, graph.degree, graph.nlist
+    """adsx_graph_info: (N, degree, nlist, entries_per_cluster)."""
+    return graph.N, graph.degree, graph.nlist, graph.entries_per_cluster
 
 
 def graph_export(graph: Graph):
-    """adsx_graph_export: (neighbours N x degree int32, entries nlist int64) as numpy."""
+    """adsx_graph_export: (neighbours N x degree int32, entries nlist x
+    entries_per_cluster int64) as numpy."""
     nbr = np.empty((graph.N, graph.degree), np.int32)
-    ent = np.empty(graph.nlist, np.int64)
+    ent = np.empty((graph.nlist, graph.entries_per_cluster), np.int64)
     _check(load().adsx_graph_export(graph.handle, _ptr(nbr), _ptr(ent)))
     return nbr, ent
 

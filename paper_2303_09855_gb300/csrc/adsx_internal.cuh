@@ -340,7 +340,8 @@ struct GraphArgs {
     const int32_t *vstride;     // per vertex: block stride (16 * cluster size)
     const int32_t *nbr;         // N x degree neighbour ids (-1 = none)
     int32_t degree;
-    const int64_t *entry;       // per cluster: start vertex (-1 = empty)
+    const int64_t *entry;       // nlist x n_ce start vertices (-1 = none)
+    int32_t n_ce;               // entries per cluster
     const float *qrot;          // nq x Dp rotated queries
     const int32_t *probes;      // nq x n_entry nearest clusters
     int32_t n_entry;
@@ -354,17 +355,20 @@ struct GraphArgs {
     unsigned *bitmap;           // warps x bm_words visited bits (all zero between queries)
     int64_t bm_words;
     int32_t *vlist;             // warps x vcap visited ids of the current query
-    int64_t vcap;               // >= n_entry + 1 + max_iter * degree
-    int32_t warps;
+    int64_t vcap;               // >= n_entry n_ce + 1 + max_iter * degree
+    int32_t warps;              // resident warps launched
+    unsigned long long *qnext;  // next query to take (zeroed by the launcher)
 };
 size_t graph_search_smem(int Dp, int ef, int K);
-int graph_search_warps_per_block();
+// warps of graph_search_kernel resident at once on nsm SMs (0: does not fit)
+int graph_search_resident_warps(int Dp, int ef, int K, int nsm);
 cudaError_t launch_knn_to_graph(const int64_t *knn, int64_t N, int64_t row0, int Kk, int degree,
                                 int32_t *nbr, cudaStream_t s);
 cudaError_t launch_vertex_map(const int64_t *off, int nlist, const int32_t *ids, int Dp,
                               int64_t *vbase, int32_t *vstride, cudaStream_t s);
 cudaError_t launch_cluster_entries(const float *data, const int64_t *off, const int32_t *ids,
-                                   const float *cents, int nlist, int Dp, int64_t *entry,
+                                   const float *cents, int nlist, int Dp, int E, float *mind,
+                                   int64_t *entry,
                                    cudaStream_t s);
 cudaError_t launch_graph_search(const GraphArgs &g, cudaStream_t s);
 

@@ -1002,15 +1002,16 @@ int adsx_stream_status(const adsx_index *index, void *stream)
 // per-warp scratch of the visited test (reused by later searches).
 struct Graph {
     int64_t N = 0;
-    int32_t degree = 0, nlist = 0, device = 0;
+    int32_t degree = 0, nlist = 0, device = 0, n_ce = 1;
     int32_t *nbr = nullptr;      // N x degree
-    int64_t *entry = nullptr;    // nlist
+    int64_t *entry = nullptr;    // nlist x n_ce
     int64_t *vbase = nullptr;    // N
     int32_t *vstride = nullptr;  // N
     unsigned *bitmap = nullptr;  // warps x bm_words (all zero between queries)
     int32_t *vlist = nullptr;    // warps x vcap
+    unsigned long long *qnext = nullptr;  // the search's query counter
     int64_t bm_words = 0, vcap = 0;
-    int32_t warps = 0;
+    int32_t warps = 0;           // warps the scratch holds
 };
 
 extern "C" {
@@ -1027,12 +1028,13 @@ int adsx_free_graph(adsx_graph *graph)
     cudaFree(g->vstride);
     cudaFree(g->bitmap);
     cudaFree(g->vlist);
+    cudaFree(g->qnext);
     delete g;
     return ADSX_OK;
 }
 
 int adsx_build_graph(const adsx_index *index, const float *X, int32_t degree, int32_t nprobe,
-                     void *stream, adsx_graph **out)
+                     int32_t entries_per_cluster, void *stream, adsx_graph **out)
 {
     const Index *ix = reinterpret_cast<const Index *>(index);
     if (!out) return fail(ADSX_EINVAL, "out is NULL");
@@ -1046,8 +1048,11 @@ int adsx_build_graph(const adsx_index *index, const float *X, int32_t degree, in
         return fail(ADSX_EINVAL, "degree out of range (1..%d)", ADSX_MAX_DEGREE);
     if (nprobe < 1 || nprobe > ix->nlist || nprobe > ADSX_MAX_NPROBE)
         return fail(ADSX_EINVAL, "nprobe out of range (1..min(nlist, %d))", ADSX_MAX_NPROBE);
+    if (entries_per_cluster < 1 || entries_per_cluster > ADSX_MAX_CLUSTER_ENTRIES)
+        return fail(ADSX_EINVAL, "entries_per_cluster out of range (1..%d)", ADSX_MAX_CLUSTER_ENTRIES);
     cudaStream_t s = (cudaStream_t)stream;
     Graph *g = new Graph();
+    g->n_ce = entries_per_cluster;
     g->N = ix->N;
     g->degree = degree;
     g->nlist = ix->nlist;
@@ -1063,7 +1068,7 @@ int adsx_build_graph(const adsx_index *index, const float *X, int32_t degree, in
         if (e != cudaSuccess) return cleanup(cuda_fail(e, what)); \
     } while (0)
     GCK(cudaMalloc(&g->nbr, sizeof(int32_t) * (size_t)g->N * degree), "alloc graph");
-    GCK(cudaMalloc(&g->entry, sizeof(int64_t) * (size_t)g->nlist), "alloc graph");
+    GCK(cudaMalloc(&g->entry, sizeof(int64_t) * (size_t)g->nlist * g->n_ce), "alloc graph");
     GCK(cudaMalloc(&g->vbase, sizeof(int64_t) * (size_t)g->N), "alloc graph");
     GCK(cudaMalloc(&g->vstride, sizeof(int32_t) * (size_t)g->N), "alloc graph");
     {
@@ -1095,9 +1100,16 @@ int adsx_build_graph(const adsx_index *index, const float *X, int32_t degree, in
         if (rc) return cleanup(rc);
     }
     GCK(adsx::launch_vertex_map(ix->off, ix->nlist, ix->ids, ix->Dp, g->vbase, g->vstride, s), "vertex map");
-    GCK(adsx::launch_cluster_entries(static_cast<const float *>(ix->data), ix->off, ix->ids, ix->cents,
-                                     ix->nlist, ix->Dp, g->entry, s), "cluster entries");
-    GCK(cudaStreamSynchronize(s), "graph sync");
+    {
+        float *mind = nullptr;
+        GCK(cudaMalloc(&mind, sizeof(float) * (size_t)std::max<int64_t>(g->N, 1)), "alloc entry scratch");
+        e = adsx::launch_cluster_entries(static_cast<const float *>(ix->data), ix->off, ix->ids, ix->cents,
+                                         ix->nlist, ix->Dp, g->n_ce, mind, g->entry, s);
+        const cudaError_t e2 = cudaStreamSynchronize(s);
+        cudaFree(mind);
+        if (e == cudaSuccess) e = e2;
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "cluster entries"));
+    }
 #undef GCK
     *out = reinterpret_cast<adsx_graph *>(g);
     return ADSX_OK;
@@ -1112,17 +1124,19 @@ int adsx_graph_export(const adsx_graph *graph, int32_t *neighbors, int64_t *entr
     if (neighbors)
         e = cudaMemcpy(neighbors, g->nbr, sizeof(int32_t) * (size_t)g->N * g->degree, cudaMemcpyDefault);
     if (e == cudaSuccess && entries)
-        e = cudaMemcpy(entries, g->entry, sizeof(int64_t) * (size_t)g->nlist, cudaMemcpyDefault);
+        e = cudaMemcpy(entries, g->entry, sizeof(int64_t) * (size_t)g->nlist * g->n_ce, cudaMemcpyDefault);
     return e == cudaSuccess ? ADSX_OK : cuda_fail(e, "graph export");
 }
 
-int adsx_graph_info(const adsx_graph *graph, int64_t *N, int32_t *degree, int32_t *nlist)
+int adsx_graph_info(const adsx_graph *graph, int64_t *N, int32_t *degree, int32_t *nlist,
+                    int32_t *entries_per_cluster)
 {
     const Graph *g = reinterpret_cast<const Graph *>(graph);
     if (!g) return fail(ADSX_EINVAL, "graph is NULL");
     if (N) *N = g->N;
     if (degree) *degree = g->degree;
     if (nlist) *nlist = g->nlist;
+    if (entries_per_cluster) *entries_per_cluster = g->n_ce;
     return ADSX_OK;
 }
 
@@ -1149,28 +1163,37 @@ int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const fl
     if (nq == 0) return ADSX_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const int max_iter = 4 * ef;
-    // per-warp scratch of the visited test, kept with the graph
+    // per-warp scratch of the visited test, kept with the graph (grown,
+    // never shrunk: a search uses the first `warps` slots)
+    int32_t warps = 0;
     {
         int nsm = 0;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ix->device);
-        const int32_t warps = nsm * 16;
+        warps = adsx::graph_search_resident_warps(ix->Dp, ef, K, nsm);
+        if (warps <= 0) return fail(ADSX_EINVAL, "graph search: ef and D need more shared memory than an SM has");
         const int64_t bm_words = (g->N + 31) / 32;
-        const int64_t vcap = 1 + ADSX_MAX_GRAPH_ENTRIES + (int64_t)max_iter * g->degree;
-        if (g->warps != warps || g->bm_words != bm_words || g->vcap < vcap) {
+        const int64_t vcap = 1 + (int64_t)ADSX_MAX_GRAPH_ENTRIES * ADSX_MAX_CLUSTER_ENTRIES +
+                             (int64_t)max_iter * g->degree;
+        if (g->warps < warps || g->bm_words != bm_words || g->vcap < vcap || !g->qnext) {
             cudaStreamSynchronize(s);
             cudaFree(g->bitmap);
             cudaFree(g->vlist);
+            cudaFree(g->qnext);
             g->bitmap = nullptr;
             g->vlist = nullptr;
+            g->qnext = nullptr;
             g->warps = 0;
             cudaError_t e = cudaMalloc(&g->bitmap, sizeof(unsigned) * (size_t)warps * bm_words);
             if (e == cudaSuccess) e = cudaMalloc(&g->vlist, sizeof(int32_t) * (size_t)warps * vcap);
+            if (e == cudaSuccess) e = cudaMalloc(&g->qnext, sizeof(unsigned long long));
             if (e == cudaSuccess) e = cudaMemset(g->bitmap, 0, sizeof(unsigned) * (size_t)warps * bm_words);
             if (e != cudaSuccess) {
                 cudaFree(g->bitmap);
                 cudaFree(g->vlist);
+                cudaFree(g->qnext);
                 g->bitmap = nullptr;
                 g->vlist = nullptr;
+                g->qnext = nullptr;
                 return cuda_fail(e, "alloc graph search scratch");
             }
             g->warps = warps;
@@ -1200,6 +1223,7 @@ int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const fl
     a.nbr = g->nbr;
     a.degree = g->degree;
     a.entry = g->entry;
+    a.n_ce = g->n_ce;
     a.qrot = qrot;
     a.probes = probes;
     a.n_entry = n_entry;
@@ -1223,7 +1247,8 @@ int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const fl
     a.bm_words = g->bm_words;
     a.vlist = g->vlist;
     a.vcap = g->vcap;
-    a.warps = g->warps;
+    a.warps = warps;
+    a.qnext = g->qnext;
     CK(adsx::launch_test_factors(ftab, nblk, ix->D, a.test_on ? eps0 : 0.f, s, 0), "test factors");
     CK(adsx::launch_graph_search(a, s), "graph search");
     CK(copy_back(oi, s), "copy back");

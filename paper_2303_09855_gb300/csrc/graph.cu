@@ -6,9 +6,12 @@
 // lane) over the vectors of an FP32 index, read in place from its
 // dim-blocked layout through a per-vertex address map.  HNSW's upper layers
 // only find a start vertex; here each query starts from the entry vertices
-// (members nearest to the centroids) of its n_entry nearest clusters.
+// of its n_entry nearest clusters (per cluster, the member nearest to the
+// centroid, then farthest-point samples: a k-means cluster can hold several
+// mutually unreachable parts of a kNN graph).
 //
-// graph_search_kernel: one warp per query, persistent (HNSW+; with pp set,
+// graph_search_kernel: one warp per query, persistent, as many warps as fit
+// on the SMs, each taking the next query from a counter (HNSW+; with pp set,
 // HNSW++ of Sec. 5.1: an exact K-set R1 gives the DCO threshold and the
 // output, the beam keeps each DCO's observed distance).  R (capacity ef) is a
 // sorted array of (distance, id) with an "expanded" flag; the search set S is
@@ -76,11 +79,15 @@ __global__ void vertex_map_kernel(const int64_t *__restrict__ off, int nlist,
     }
 }
 
-// One warp per cluster: the member nearest to the (rotated) centroid, ties
-// by id; -1 for an empty cluster.
+// One warp per cluster, E start vertices chosen by farthest-point sampling:
+// entry 0 is the member nearest to the (rotated) centroid; entry e is the
+// member whose distance to the nearest of entries 0..e-1 is largest (ties by
+// id; -1 once every member coincides with a chosen one, or for an empty
+// cluster).  mind[o + m] keeps member m's distance to the chosen set.
 __global__ void cluster_entry_kernel(const float *__restrict__ data, const int64_t *__restrict__ off,
                                      const int32_t *__restrict__ ids, const float *__restrict__ cents,
-                                     int nlist, int Dp, int64_t *__restrict__ entry)
+                                     int nlist, int Dp, int E, float *__restrict__ mind,
+                                     int64_t *__restrict__ entry)
 {
     const int lane = threadIdx.x & 31;
     const int nblk = Dp / BLK;
@@ -91,6 +98,7 @@ __global__ void cluster_entry_kernel(const float *__restrict__ data, const int64
         const float *cq = cents + c * Dp;
         float best = INFINITY;
         int bid = INT_MAX;
+        int64_t bm = 0;
         for (int64_t m = lane; m < n; m += 32) {
             float S = 0.f;
             for (int b = 0; b < nblk; ++b) S = accum_block_f32(cb + b * n * BLK + m * BLK, cq + b * BLK, S);
@@ -98,18 +106,57 @@ __global__ void cluster_entry_kernel(const float *__restrict__ data, const int64
             if (pless(S, id, best, bid)) {
                 best = S;
                 bid = id;
+                bm = m;
             }
         }
 #pragma unroll
         for (int s = 16; s > 0; s >>= 1) {
             const float ob = __shfl_xor_sync(FULL, best, s);
             const int oi = __shfl_xor_sync(FULL, bid, s);
+            const int64_t om = __shfl_xor_sync(FULL, bm, s);
             if (pless(ob, oi, best, bid)) {
                 best = ob;
                 bid = oi;
+                bm = om;
             }
         }
-        if (lane == 0) entry[c] = n > 0 ? (int64_t)bid : -1;
+        if (lane == 0) entry[c * E] = n > 0 ? (int64_t)bid : -1;
+        bool done = n == 0;
+        for (int e = 1; e < E; ++e) {
+            float far = -1.f;
+            int fid = INT_MAX;
+            int64_t fm = 0;
+            if (!done) {
+                const float *xs = cb + bm * BLK;            // the entry chosen last
+                for (int64_t m = lane; m < n; m += 32) {
+                    float S = 0.f;
+                    for (int b = 0; b < nblk; ++b)
+                        S = accum_block_f32(cb + b * n * BLK + m * BLK, xs + b * n * BLK, S);
+                    const float md = e == 1 ? S : fminf(mind[o + m], S);
+                    mind[o + m] = md;
+                    const int id = ids[o + m];
+                    if (md > far || (md == far && id < fid)) {
+                        far = md;
+                        fid = id;
+                        fm = m;
+                    }
+                }
+            }
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) {
+                const float of = __shfl_xor_sync(FULL, far, s);
+                const int oi = __shfl_xor_sync(FULL, fid, s);
+                const int64_t om = __shfl_xor_sync(FULL, fm, s);
+                if (of > far || (of == far && oi < fid)) {
+                    far = of;
+                    fid = oi;
+                    fm = om;
+                }
+            }
+            done = done || !(far > 0.f);
+            if (lane == 0) entry[c * E + e] = done ? (int64_t)-1 : (int64_t)fid;
+            bm = fm;
+        }
     }
 }
 
@@ -208,55 +255,61 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
     unsigned *bm = g.bitmap + gw * g.bm_words;
     int32_t *vl = g.vlist + gw * g.vcap;
 
-    for (int64_t q = gw; q < g.nq; q += g.warps) {
+    // queries are taken one at a time from a shared counter: search lengths
+    // vary, so a static split would leave warps idle at the end
+    auto next_query = [&]() {
+        unsigned long long t = 0ull;
+        if (lane == 0) t = atomicAdd(g.qnext, 1ull);
+        return (int64_t)__shfl_sync(FULL, t, 0);
+    };
+    for (int64_t q = next_query(); q < g.nq; q = next_query()) {
         for (int i = lane; i < g.Dp; i += 32) qv[i] = g.qrot[q * g.Dp + i];
         __syncwarp();
-        // Start vertices: the entries of the query's n_entry nearest clusters
-        // (distinct, exact distances), sorted by (distance, id), ef kept.
+        // Start vertices: the n_ce entries of each of the query's n_entry
+        // nearest clusters (distinct; exact distances, one vertex per lane,
+        // blocks in order as in a DCO), merged into R 32 at a time by
+        // (distance, id), ef kept; vertex 0 when no cluster has an entry.
         unsigned long long dims = 0ull;
         int vcount = 0, nR = 0, n1 = 0;
-        for (int k = 0; k <= g.n_entry; ++k) {
-            int64_t e;
-            if (k < g.n_entry) e = g.entry[g.probes[q * g.n_entry + k]];
-            else e = nR == 0 ? 0 : -1;      // no entry at all: vertex 0
-            if (e < 0) continue;
+        const int ns = g.n_entry * g.n_ce;
+        for (int c0 = 0; c0 < ns + 32; c0 += 32) {
+            const bool tail = c0 >= ns;         // the pass after the entries
+            if (tail && nR > 0) break;
+            int64_t e = -1;
+            if (!tail) {
+                const int k = c0 + lane;
+                if (k < ns) e = g.entry[(int64_t)g.probes[q * g.n_entry + k / g.n_ce] * g.n_ce + k % g.n_ce];
+            } else if (lane == 0) {
+                e = 0;
+            }
             bool fresh = false;
-            if (lane == 0) {
+            if (e >= 0) {
                 const unsigned bit = 1u << (e & 31);
                 fresh = !(atomicOr(bm + (e >> 5), bit) & bit);
             }
-            if (!__shfl_sync(FULL, fresh, 0)) continue;
-            float part = 0.f;
-            const float *x = g.data + g.vbase[e];
-            const int64_t st = g.vstride[e];
-            for (int b = lane; b < g.nblk; b += 32) part = accum_block_f32(x + b * st, qv + b * BLK, part);
-#pragma unroll
-            for (int s = 16; s > 0; s >>= 1) part += __shfl_xor_sync(FULL, part, s);
-            if (lane == 0) {
-                vl[vcount] = (int32_t)e;
-                rd[nR] = part;
-                ri[nR] = (int)e;
+            const unsigned fb = __ballot_sync(FULL, fresh);
+            if (!fb) continue;
+            if (fresh) vl[vcount + __popc(fb & below)] = (int32_t)e;
+            vcount += __popc(fb);
+            float S = 0.f;
+            if (fresh) {
+                const float *x = g.data + g.vbase[e];
+                const int64_t st = g.vstride[e];
+#pragma unroll 1
+                for (int b = 0; b < g.nblk; ++b) S = accum_block_f32(x + b * st, qv + b * BLK, S);
                 dims += (unsigned long long)g.D;
             }
-            ++vcount;
-            ++nR;
+            const int na = stage_sorted(fresh, S, (int)e, ad, ai, lane);
+            nR = warp_merge(rd, ri, rx, nR, ad, ai, na, nd, ni, nx, g.ef, lane);
+            float *tf = rd; rd = nd; nd = tf;
+            int *ti = ri; ri = ni; ni = ti;
+            ti = rx; rx = nx; nx = ti;
         }
-        __syncwarp();
-        {
-            // nR <= n_entry + 1 <= 17 start vertices: one warp sort
-            const unsigned long long key = warp_sort32(lane < nR ? dkey(rd[lane], ri[lane]) : ~0ull, lane);
-            __syncwarp();
-            if (lane < nR) {
-                rd[lane] = __uint_as_float((unsigned)(key >> 32));
-                ri[lane] = (int)(key & 0xffffffffu);
-                rx[lane] = 0;
-                if (lane < g.K) {           // HNSW++: R1 starts as the K nearest (exact)
-                    kd[lane] = rd[lane];
-                    ki[lane] = ri[lane];
-                }
-            }
-            n1 = nR < g.K ? nR : g.K;
-            if (nR > g.ef) nR = g.ef;
+        // HNSW++: R1 starts as the K nearest start vertices (exact)
+        n1 = nR < g.K ? nR : g.K;
+        for (int k = lane; k < n1; k += 32) {
+            kd[k] = rd[k];
+            ki[k] = ri[k];
         }
         __syncwarp();
         for (int it = 0; it < g.max_iter; ++it) {
@@ -362,7 +415,19 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
 }  // namespace
 
 size_t graph_search_smem(int Dp, int ef, int K) { return graph_warp_bytes(Dp, ef, K) * GW; }
-int graph_search_warps_per_block() { return GW; }
+
+int graph_search_resident_warps(int Dp, int ef, int K, int nsm)
+{
+    const size_t smem = graph_search_smem(Dp, ef, K);
+    if (cudaFuncSetAttribute(graph_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, graph_search_kernel, GW * 32, smem) !=
+        cudaSuccess)
+        return 0;
+    return nb * GW * nsm;
+}
 
 cudaError_t launch_knn_to_graph(const int64_t *knn, int64_t N, int64_t row0, int Kk, int degree,
                                 int32_t *nbr, cudaStream_t s)
@@ -383,12 +448,12 @@ cudaError_t launch_vertex_map(const int64_t *off, int nlist, const int32_t *ids,
 }
 
 cudaError_t launch_cluster_entries(const float *data, const int64_t *off, const int32_t *ids,
-                                   const float *cents, int nlist, int Dp, int64_t *entry,
-                                   cudaStream_t s)
+                                   const float *cents, int nlist, int Dp, int E, float *mind,
+                                   int64_t *entry, cudaStream_t s)
 {
     const int blocks = (nlist + 7) / 8;
     cluster_entry_kernel<<<blocks < 152 * 16 ? blocks : 152 * 16, 256, 0, s>>>(data, off, ids, cents,
-                                                                               nlist, Dp, entry);
+                                                                               nlist, Dp, E, mind, entry);
     return cudaGetLastError();
 }
 
@@ -398,6 +463,8 @@ cudaError_t launch_graph_search(const GraphArgs &g, cudaStream_t s)
     const size_t smem = graph_search_smem(g.Dp, g.ef, g.K);
     cudaError_t e = cudaFuncSetAttribute(graph_search_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(g.qnext, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const int blocks = (g.warps + GW - 1) / GW;
     graph_search_kernel<<<blocks, GW * 32, smem, s>>>(g);

@@ -2,14 +2,20 @@
 beam search of Sec. 2.2.1) through the C ABI, against the FP64 oracle running
 the same algorithm on the same (exported) graph and start vertices:
   - the kNN graph: every vertex's neighbour list equals the oracle's exact
-    IVF list (self excluded) except near-ties; the entry vertex of a cluster
-    is its member nearest to the centroid;
+    IVF list (self excluded) except near-ties; a cluster's entry vertices
+    equal the oracle's farthest-point samples, and where an FP32 near-tie
+    let them part, each GPU entry is still a valid farthest-point step given
+    the GPU's earlier ones;
   - eps0 = inf (exact DCOs: HNSW's own search) and eps0 = 2.1, for HNSW+
     and HNSW++ (Sec. 5.1): returned distances exact to 1e-5, no duplicates,
     results identical to the oracle's for most queries (a beam search can
     take another path after one FP32 near-tie), recall no worse than the
     oracle's minus 0.02; HNSW++ with exact DCOs equals HNSW bit for bit;
-  - argument checks (K > ef, a 16-bit index).
+  - many entries per cluster (a small upper layer: 72 start vertices, more
+    than ef, merged into R 32 at a time) against the oracle given the same
+    starts;
+  - argument checks (K > ef, entries per cluster out of range, a 16-bit
+    index).
 """
 import math
 
@@ -21,7 +27,7 @@ from gpu_helpers import REL, kth_near_tie, near_tie_queries
 
 pytestmark = pytest.mark.gpu
 
-K, EF, NE = 10, 64, 3
+K, EF, NE, EPC = 10, 64, 3, 3
 
 
 @pytest.fixture(scope="module")
@@ -31,7 +37,7 @@ def gr():
     build.build()
     wl = W.gen_gaussian_mixture()
     ix = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign)
-    g = adsx.build_graph(ix, wl.X, degree=32, nprobe=10)
+    g = adsx.build_graph(ix, wl.X, degree=32, nprobe=10, entries_per_cluster=EPC)
     Y, Cr, Qr = (oracle.rotate(wl.P, a) for a in (wl.X, wl.centroids, wl.Q))
     nbr, ent = adsx.graph_export(g)
     yield adsx, wl, ix, g, Y, Cr, Qr, nbr, ent
@@ -53,16 +59,28 @@ def test_graph_lists_and_entries_match_oracle(gr):
         assert set(nbr[r].tolist()) == set(want), r
         checked += 1
     assert checked >= 250
+    assert ent.shape == (wl.nlist, EPC)
+    want = oracle.cluster_entries(Y, Cr, wl.assign, EPC)
+    same = 0
     for c in range(wl.nlist):
         mem = np.nonzero(wl.assign == c)[0]
         if len(mem) == 0:
-            assert ent[c] == -1
+            assert np.all(ent[c] == -1)
             continue
+        same += np.array_equal(ent[c], want[c])
+        assert set(ent[c][ent[c] >= 0].tolist()) <= set(mem.tolist()), c
         d = np.sum((Y[mem] - Cr[c]) ** 2, axis=1)
-        order = np.lexsort((mem, d))
-        if len(mem) > 1 and d[order[1]] - d[order[0]] <= REL * d[order[1]]:
-            continue
-        assert ent[c] == mem[order[0]], c
+        e0 = float(np.sum((Y[ent[c, 0]] - Cr[c]) ** 2))
+        assert e0 <= d.min() * (1 + REL) + 1e-6, c
+        nearest = np.full(len(mem), np.inf)
+        for e in range(1, EPC):
+            nearest = np.minimum(nearest, np.sum((Y[mem] - Y[ent[c, e - 1]]) ** 2, axis=1))
+            if ent[c, e] < 0:
+                assert nearest.max() <= 1e-6 and np.all(ent[c, e:] == -1), c
+                break
+            got = nearest[np.searchsorted(mem, ent[c, e])]
+            assert got >= nearest.max() * (1 - REL) - 1e-6, (c, e)
+    assert same >= 0.9 * wl.nlist
 
 
 @pytest.mark.parametrize("eps0,dd,pp,min_same", [(math.inf, 32, False, 0.95),
@@ -73,7 +91,7 @@ def test_graph_search_matches_oracle(gr, eps0, dd, pp, min_same):
     ids, d2, dims = g.search(wl.Q, K, EF, eps0=eps0, delta_d=dd, return_dims=True, n_entry=NE,
                              decoupled=pp)
     probes, _ = oracle.probe(Cr, Qr, NE)
-    starts = ent[probes]
+    starts = ent[probes].reshape(len(Qr), -1)
     oids, od2, odims, iters = oracle.graph_search(Y, nbr, starts, Qr, K, EF, eps0, dd,
                                                   max_iter=4 * EF, pp=pp)
     ok = ~near_tie_queries(Cr, Qr, NE)
@@ -99,6 +117,38 @@ def test_graph_search_matches_oracle(gr, eps0, dd, pp, min_same):
         assert np.array_equal(ids, h_ids) and np.array_equal(d2, h_d2)
 
 
+@pytest.mark.parametrize("pp", [False, True])
+def test_graph_many_entries_match_oracle(gr, pp):
+    adsx, wl, ix, g, Y, Cr, Qr, nbr, ent = gr
+    g24 = adsx.build_graph(ix, wl.X, degree=32, nprobe=10, entries_per_cluster=24)
+    try:
+        nbr24, ent24 = adsx.graph_export(g24)
+        assert np.array_equal(nbr24, nbr)                    # same kNN lists
+        assert np.array_equal(ent24[:, :EPC], ent)           # sampling extends the shorter one
+        ef = 48                                              # < 3 x 24 start vertices
+        ids, d2, dims = g24.search(wl.Q, K, ef, eps0=2.1, delta_d=32, return_dims=True,
+                                   n_entry=NE, decoupled=pp)
+        probes, _ = oracle.probe(Cr, Qr, NE)
+        starts = ent24[probes].reshape(len(Qr), -1)
+        oids, od2, odims, _ = oracle.graph_search(Y, nbr24, starts, Qr, K, ef, 2.1, 32,
+                                                  max_iter=4 * ef, pp=pp)
+        ok = ~near_tie_queries(Cr, Qr, NE)
+        same = sum(1 for q in range(len(Qr)) if ok[q] and np.array_equal(ids[q], oids[q]))
+        assert same >= 0.85 * ok.sum(), (same, int(ok.sum()))
+        for q in range(len(Qr)):
+            for i, d in zip(ids[q], d2[q]):
+                if i >= 0:
+                    ex = float(np.sum((Y[i] - Qr[q]) ** 2))
+                    assert abs(d - ex) <= REL * ex + 1e-6, (q, i, d, ex)
+        # every distinct start vertex costs D dims before the first expansion
+        nstart = np.array([len(set(s[s >= 0].tolist())) for s in starts])
+        assert np.all(dims >= nstart * wl.D)
+        gt, _ = oracle.knn_exact(Y, Qr, K)
+        assert oracle.recall_at(ids, gt, K) >= oracle.recall_at(oids, gt, K) - 0.02
+    finally:
+        g24.close()
+
+
 def test_graph_argument_checks(gr):
     adsx, wl, ix, g, Y, Cr, Qr, nbr, ent = gr
     with pytest.raises(adsx.AdsxError):
@@ -107,6 +157,9 @@ def test_graph_argument_checks(gr):
         g.search(wl.Q, 10, 10_000)                           # ef > ADSX_MAX_EF
     with pytest.raises(adsx.AdsxError):
         g.search(wl.Q, 10, 64, n_entry=17)                   # n_entry > ADSX_MAX_GRAPH_ENTRIES
+    for bad in (0, 65):                                      # 1..ADSX_MAX_CLUSTER_ENTRIES
+        with pytest.raises(adsx.AdsxError):
+            adsx.build_graph(ix, wl.X, entries_per_cluster=bad)
     ix16 = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign, storage=adsx.BF16)
     try:
         with pytest.raises(adsx.AdsxError):

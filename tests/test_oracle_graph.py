@@ -8,8 +8,16 @@ base-layer search of Sec. 2.2.1 with Algorithm 1 as its DCO, Sec. 4):
     exact KNN (brute force) for any ef >= K;
   - eps0 = inf and delta_d >= D give identical results (exact DCOs);
   - with ADSampling every returned distance is the exact distance of that id
-    and the result has no duplicates.
+    and the result has no duplicates;
+  - the start vertices per cluster (farthest-point sampling): a hand-worked
+    line example whose third step tells the min-distance rule from a
+    max-distance one, duplicates and empty clusters, every member chosen once
+    when E reaches the cluster size, and the 2-approximation bound of greedy
+    k-center against brute force over all E-subsets;
+  - a cluster holding two blobs that no kNN edge joins: one entry reaches one
+    blob only, two entries give the exact KNN.
 """
+import itertools
 import math
 
 import numpy as np
@@ -106,3 +114,71 @@ def test_hnsw_pp_reduces_to_hnsw_and_samples_fewer_dims():
         for i, d in zip(ids[q], d2[q]):
             if i >= 0:
                 assert abs(d - float(np.sum((Y[i] - Q[q]) ** 2))) <= 1e-12 * (1 + d)
+
+
+def test_cluster_entries_hand_worked_line():
+    # members of cluster 0 at 0, 4, 5, 10, 11 (ids 0..4), centroid at 5.9:
+    # entry 0 = 5 (id 2); farthest from it 11 (id 4); then 0 (id 0, at 5 from
+    # {5, 11}); then 4 and 10 both sit at 1 from the chosen set: the tie goes
+    # to id 1 (with max instead of min distances it would be 10, id 3); last
+    # id 3; nothing is left for the sixth entry.
+    Y = np.array([0.0, 4.0, 5.0, 10.0, 11.0, 3.0])[:, None]
+    assign = np.array([0, 0, 0, 0, 0, 1])
+    Cr = np.array([[5.9], [100.0]])
+    ent = oracle.cluster_entries(Y, Cr, assign, 6)
+    assert ent[0].tolist() == [2, 4, 0, 1, 3, -1]
+    assert ent[1].tolist() == [5, -1, -1, -1, -1, -1]
+    assert oracle.cluster_entries(Y, Cr, assign, 1).tolist() == [[2], [5]]
+
+
+def test_cluster_entries_duplicates_empty_and_full():
+    Y = np.zeros((4, 3))
+    Y[3] = 1.0
+    assign = np.array([1, 1, 1, 2])                      # cluster 0 empty
+    ent = oracle.cluster_entries(Y, np.zeros((3, 3)), assign, 3)
+    assert ent[0].tolist() == [-1, -1, -1]
+    assert ent[1].tolist() == [0, -1, -1]                # three equal points: lowest id, then none
+    assert ent[2].tolist() == [3, -1, -1]
+    rng = np.random.default_rng(11)
+    Y = rng.normal(size=(12, 5))
+    ent = oracle.cluster_entries(Y, Y.mean(0, keepdims=True), np.zeros(12, int), 12)
+    assert sorted(ent[0].tolist()) == list(range(12))
+
+
+def test_cluster_entries_greedy_k_center_bound():
+    """Farthest-point sampling is greedy k-center: its covering radius
+    max_m min_e ||y_m - y_e|| is at most twice the best over all E-subsets."""
+    rng = np.random.default_rng(12)
+    for trial in range(6):
+        n, E = 10, 3
+        Y = rng.normal(size=(n, 4)) * rng.uniform(0.5, 3.0, size=4)
+        ent = oracle.cluster_entries(Y, rng.normal(size=(1, 4)), np.zeros(n, int), E)[0]
+        dist = np.sqrt(np.sum((Y[:, None, :] - Y[None, :, :]) ** 2, axis=2))
+        greedy = dist[:, ent].min(axis=1).max()
+        best = min(dist[:, list(sub)].min(axis=1).max() for sub in itertools.combinations(range(n), E))
+        assert best <= greedy <= 2 * best + 1e-12, (trial, greedy, best)
+        # each step takes a point at the largest distance from the earlier ones
+        for e in range(1, E):
+            nearest = dist[:, ent[:e]].min(axis=1) ** 2
+            assert nearest[ent[e]] == nearest.max()
+
+
+def test_two_blobs_in_one_cluster_need_two_entries():
+    rng = np.random.default_rng(13)
+    D = 8
+    a = rng.normal(size=(60, D))
+    b = rng.normal(size=(60, D)) + 40.0                   # far apart: no kNN edge between them
+    Y = np.concatenate([a, b])
+    assign = np.zeros(120, int)                           # one cluster holds both
+    Cr = Y.mean(0, keepdims=True)
+    graph = _knn_graph(Y, 8)
+    assert not np.any((graph[:60] >= 60)) and not np.any((graph[60:] < 60))
+    Q = np.concatenate([a[:3] + 0.1, b[:3] + 0.1])
+    gt, gd = oracle.knn_exact(Y, Q, 5)
+    one = oracle.cluster_entries(Y, Cr, assign, 1)
+    two = oracle.cluster_entries(Y, Cr, assign, 2)
+    assert (one[0, 0] < 60) != (two[0, 1] < 60)          # the second entry is in the other blob
+    ids1, _, _, _ = oracle.graph_search(Y, graph, np.repeat(one, 6, axis=0), Q, 5, 20, math.inf, 8)
+    ids2, d2, _, _ = oracle.graph_search(Y, graph, np.repeat(two, 6, axis=0), Q, 5, 20, math.inf, 8)
+    assert oracle.recall_at(ids1, gt, 5) == 0.5
+    assert np.array_equal(ids2, gt) and np.allclose(d2, gd, rtol=1e-12)
