@@ -53,7 +53,7 @@ def parse():
                     help="graph mode: clusters whose entry vertices start a search")
     ap.add_argument("--graph-nprobe", type=int, default=16,
                     help="graph mode: clusters searched for each vertex's neighbours")
-    ap.add_argument("--cluster-entries", type=int, default=4,
+    ap.add_argument("--cluster-entries", type=int, default=64,
                     help="graph mode: entry vertices per cluster (farthest-point samples)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()

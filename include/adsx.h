@@ -429,14 +429,15 @@ int adsx_graph_export(const adsx_graph *graph, int32_t *neighbors, int64_t *entr
 
 /*
  * adsx_search_graph -- HNSW+: greedy beam search with a result set R of ef
- * entries (Sec. 2.2.1).  R starts as the entry vertices of the query's
- * n_entry nearest clusters (all of their entries: distinct, exact distances,
- * the ef nearest kept; vertex 0 if none exists).  Then
- * repeatedly expand the
- * nearest not-yet-expanded entry of R: every neighbour not visited before
- * runs Algorithm 1 against r = the largest distance in R (+INF while R holds
- * fewer than ef; fixed during one expansion) and, if it reaches d = D with
- * (distance, id) below R's largest, joins R, which keeps its ef smallest.
+ * entries (Sec. 2.2.1).  The start vertices are all entry vertices of the
+ * query's n_entry nearest clusters (vertex 0 if there are none), nearest
+ * cluster first.  Every vertex not visited before, start vertex or
+ * neighbour, runs Algorithm 1 against r = the largest distance in R (+INF
+ * while R holds fewer than ef) and, if it reaches d = D with (distance, id)
+ * below R's largest, joins R, which keeps its ef smallest; r stays fixed
+ * during one batch: 32 consecutive positions of the start list, then the
+ * neighbour list of each expansion.  The search repeatedly expands the
+ * nearest not-yet-expanded entry of R.
  * The search stops when every entry of R is expanded, or after 4 ef
  * expansions.  The K smallest entries of R are returned, by (distance, id).
  * decoupled = 1 runs HNSW++ (Sec. 5.1) instead: R's two roles are split --

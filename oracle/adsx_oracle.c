@@ -665,11 +665,14 @@ void orc_ivf_ads_ip(const double *Y, int64_t N, int32_t D, const double *Cr,
 /* set R (size N_ef).  The search set S is the set of R's entries not yet */
 /* expanded (an entry leaving R can never be expanded usefully again).    */
 /* Reading of batch semantics: the threshold r is the largest distance in */
-/* R when a node's expansion starts and stays fixed while its neighbours  */
-/* are tested (in adjacency order, skipping visited ones); the neighbours */
-/* that pass and precede R's maximum in (distance, id) order then merge   */
-/* into R, which keeps its N_ef smallest.  The search stops when every    */
-/* entry of R has been expanded (or after max_iter expansions).           */
+/* R when a batch starts and stays fixed while its vertices are tested    */
+/* (in order, skipping -1 and visited ones); the vertices that pass and   */
+/* precede R's maximum in (distance, id) order then merge into R, which   */
+/* keeps its N_ef smallest.  A batch is the neighbour list of the node    */
+/* being expanded, or 32 consecutive positions of the start list (the     */
+/* start vertices are tested like neighbours of a virtual root; with     */
+/* exact DCOs R starts as the N_ef nearest of them).  The search stops    */
+/* when every entry of R has been expanded (or after max_iter expansions). */
 /*   graph     N x Rg int32 neighbour ids (-1 = none), by original id      */
 /*   entries   nq x E int64 start vertices (-1 = none)                    */
 /* Outputs ids/d2 (K smallest of R by (distance, id); -1/+inf padded),    */
@@ -679,6 +682,88 @@ void orc_ivf_ads_ip(const double *Y, int64_t N, int32_t D, const double *Cr,
 /* largest distance); R (size N_ef) and S are kept with the observed      */
 /* distance of each DCO: exact if it reached d = D, else the estimate     */
 /* (D/d) S_d at the d where Algorithm 1 stopped.  The output is R1.       */
+#define ORC_START_BATCH 32
+
+typedef struct {
+    const double *Y, *qr;
+    int32_t D, K, ef, delta_d, pp;
+    double eps0;
+    unsigned char *visited, *expd;
+    orc_pair *R, *R1, *cand, *add1;
+    int32_t nR, n1;
+    int64_t dims_sum;
+} orc_beam;
+
+/* One batch: DCOs of the listed vertices against thresholds fixed at the
+   batch's start, then the merges into R (and R1). */
+static void orc_beam_batch(orc_beam *b, const int64_t *verts, int32_t nv)
+{
+    const int full = b->nR == b->ef;
+    const double rmax = full ? b->R[b->nR - 1].d : INFINITY;
+    const int64_t rid = full ? b->R[b->nR - 1].id : INT64_MAX;
+    const int full1 = b->n1 == b->K;
+    const double r1max = full1 ? b->R1[b->n1 - 1].d : INFINITY;
+    const int64_t r1id = full1 ? b->R1[b->n1 - 1].id : INT64_MAX;
+    const double r2 = b->pp ? r1max : rmax;        /* the DCO threshold */
+    const int32_t D = b->D;
+    int32_t nc = 0, nc1 = 0;
+    for (int32_t j = 0; j < nv; ++j) {
+        const int64_t v = verts[j];
+        if (v < 0 || b->visited[v]) continue;
+        b->visited[v] = 1;
+        int32_t dims = 0;
+        double S = 0.0;
+        const int res = orc_dco(b->Y + v * D, b->qr, D, r2, b->eps0, b->delta_d, &dims, &S, NULL);
+        b->dims_sum += dims;
+        if (!b->pp) {
+            if (res == ORC_POSITIVE && (!full || pair_less(S, v, rmax, rid))) {
+                b->cand[nc].d = S;
+                b->cand[nc].id = v;
+                ++nc;
+            }
+        } else {
+            const double obs = dims == D ? S : S * (double)D / (double)dims;
+            if (res == ORC_POSITIVE && (!full1 || pair_less(S, v, r1max, r1id))) {
+                b->add1[nc1].d = S;
+                b->add1[nc1].id = v;
+                ++nc1;
+            }
+            if (!full || pair_less(obs, v, rmax, rid)) {
+                b->cand[nc].d = obs;
+                b->cand[nc].id = v;
+                ++nc;
+            }
+        }
+    }
+    if (b->pp && nc1) {            /* R1: the K smallest exact distances */
+        for (int32_t k = 0; k < nc1; ++k) b->R1[b->n1 + k] = b->add1[k];
+        qsort(b->R1, (size_t)(b->n1 + nc1), sizeof(orc_pair), pair_cmp);
+        b->n1 = b->n1 + nc1 < b->K ? b->n1 + nc1 : b->K;
+    }
+    /* merge: R and the candidates, keep the ef smallest by (d, id) */
+    orc_pair *R = b->R;
+    unsigned char *expd = b->expd;
+    for (int32_t k = 0; k < nc; ++k) {
+        R[b->nR + k] = b->cand[k];
+        expd[b->nR + k] = 0;
+    }
+    const int32_t tot = b->nR + nc;
+    /* insertion sort carrying the expanded flags (tot <= ef + batch size) */
+    for (int32_t a = 1; a < tot; ++a) {
+        orc_pair x = R[a];
+        unsigned char fx = expd[a];
+        int32_t c = a - 1;
+        while (c >= 0 && pair_less(x.d, x.id, R[c].d, R[c].id)) {
+            R[c + 1] = R[c];
+            expd[c + 1] = expd[c];
+            --c;
+        }
+        R[c + 1] = x;
+        expd[c + 1] = fx;
+    }
+    b->nR = tot < b->ef ? tot : b->ef;
+}
+
 void orc_graph_search(const double *Y, int64_t N, int32_t D, const int32_t *graph,
                       int32_t Rg, const int64_t *entries, int32_t E, const double *Qr,
                       int64_t nq, int32_t K, int32_t ef, int32_t max_iter, double eps0,
@@ -686,103 +771,48 @@ void orc_graph_search(const double *Y, int64_t N, int32_t D, const int32_t *grap
                       int64_t *dims_total, int64_t *iters_out, int nthreads)
 {
     set_threads(nthreads);
+    const int32_t bmax = Rg > ORC_START_BATCH ? Rg : ORC_START_BATCH;
 #pragma omp parallel for schedule(dynamic)
     for (int64_t q = 0; q < nq; ++q) {
-        const double *qr = Qr + q * D;
-        unsigned char *visited = (unsigned char *)calloc((size_t)(N > 0 ? N : 1), 1);
-        const int32_t cap = ef + (Rg > E ? Rg : E);
-        orc_pair *R = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)cap);
-        unsigned char *expd = (unsigned char *)malloc((size_t)cap);
-        orc_pair *cand = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(Rg > 0 ? Rg : 1));
-        orc_pair *R1 = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(K + (Rg > E ? Rg : E)));
-        orc_pair *add1 = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(Rg > 0 ? Rg : 1));
-        int32_t nR = 0, n1 = 0, it = 0;
-        int64_t dims_sum = 0;
-        /* the start vertices (exact distances, duplicates and -1 skipped),
-           sorted by (distance, id), the ef smallest kept */
-        for (int32_t k = 0; k < E; ++k) {
-            const int64_t e = entries[q * E + k];
-            if (e < 0 || visited[e]) continue;
-            visited[e] = 1;
-            R[nR].d = sqdist(Y + e * D, qr, D);
-            R[nR].id = e;
-            expd[nR] = 0;
-            ++nR;
-            dims_sum += D;
+        orc_beam b;
+        b.Y = Y;
+        b.qr = Qr + q * D;
+        b.D = D;
+        b.K = K;
+        b.ef = ef;
+        b.delta_d = delta_d;
+        b.pp = pp;
+        b.eps0 = eps0;
+        b.visited = (unsigned char *)calloc((size_t)(N > 0 ? N : 1), 1);
+        b.R = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(ef + bmax));
+        b.expd = (unsigned char *)malloc((size_t)(ef + bmax));
+        b.cand = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)bmax);
+        b.R1 = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(K + bmax));
+        b.add1 = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)bmax);
+        int64_t *verts = (int64_t *)malloc(sizeof(int64_t) * (size_t)bmax);
+        b.nR = 0;
+        b.n1 = 0;
+        b.dims_sum = 0;
+        int32_t it = 0;
+        /* the start vertices, ORC_START_BATCH list positions per batch */
+        for (int32_t k0 = 0; k0 < E; k0 += ORC_START_BATCH) {
+            const int32_t nv = E - k0 < ORC_START_BATCH ? E - k0 : ORC_START_BATCH;
+            orc_beam_batch(&b, entries + q * E + k0, nv);
         }
-        qsort(R, (size_t)nR, sizeof(orc_pair), pair_cmp);
-        for (int32_t k = 0; k < nR && k < K; ++k) R1[n1++] = R[k];   /* exact already */
-        if (nR > ef) nR = ef;
         while (it < max_iter) {
             int32_t u = -1;
-            for (int32_t k = 0; k < nR; ++k)
-                if (!expd[k]) { u = k; break; }
+            for (int32_t k = 0; k < b.nR; ++k)
+                if (!b.expd[k]) { u = k; break; }
             if (u < 0) break;
-            expd[u] = 1;
-            const int64_t node = R[u].id;
-            const int full = nR == ef;
-            const double rmax = full ? R[nR - 1].d : INFINITY;
-            const int64_t rid = full ? R[nR - 1].id : INT64_MAX;
-            const int full1 = n1 == K;
-            const double r1max = full1 ? R1[n1 - 1].d : INFINITY;
-            const int64_t r1id = full1 ? R1[n1 - 1].id : INT64_MAX;
-            const double r2 = pp ? r1max : rmax;        /* the DCO threshold */
-            int32_t nc = 0, nc1 = 0;
-            for (int32_t j = 0; j < Rg; ++j) {
-                const int32_t v = graph[node * Rg + j];
-                if (v < 0 || visited[v]) continue;
-                visited[v] = 1;
-                int32_t dims = 0;
-                double S = 0.0;
-                const int res = orc_dco(Y + (int64_t)v * D, qr, D, r2, eps0, delta_d, &dims, &S, NULL);
-                dims_sum += dims;
-                if (!pp) {
-                    if (res == ORC_POSITIVE && (!full || pair_less(S, v, rmax, rid))) {
-                        cand[nc].d = S;
-                        cand[nc].id = v;
-                        ++nc;
-                    }
-                } else {
-                    const double obs = dims == D ? S : S * (double)D / (double)dims;
-                    if (res == ORC_POSITIVE && (!full1 || pair_less(S, v, r1max, r1id))) {
-                        add1[nc1].d = S;
-                        add1[nc1].id = v;
-                        ++nc1;
-                    }
-                    if (!full || pair_less(obs, v, rmax, rid)) {
-                        cand[nc].d = obs;
-                        cand[nc].id = v;
-                        ++nc;
-                    }
-                }
-            }
-            if (pp && nc1) {            /* R1: the K smallest exact distances */
-                for (int32_t k = 0; k < nc1; ++k) R1[n1 + k] = add1[k];
-                qsort(R1, (size_t)(n1 + nc1), sizeof(orc_pair), pair_cmp);
-                n1 = n1 + nc1 < K ? n1 + nc1 : K;
-            }
-            /* merge: R and the candidates, keep the ef smallest by (d, id) */
-            for (int32_t k = 0; k < nc; ++k) {
-                R[nR + k] = cand[k];
-                expd[nR + k] = 0;
-            }
-            const int32_t tot = nR + nc;
-            /* insertion sort carrying the expanded flags (tot <= ef + Rg) */
-            for (int32_t a = 1; a < tot; ++a) {
-                orc_pair x = R[a];
-                unsigned char fx = expd[a];
-                int32_t b = a - 1;
-                while (b >= 0 && pair_less(x.d, x.id, R[b].d, R[b].id)) {
-                    R[b + 1] = R[b];
-                    expd[b + 1] = expd[b];
-                    --b;
-                }
-                R[b + 1] = x;
-                expd[b + 1] = fx;
-            }
-            nR = tot < ef ? tot : ef;
+            b.expd[u] = 1;
+            const int64_t node = b.R[u].id;
+            for (int32_t j = 0; j < Rg; ++j) verts[j] = graph[node * Rg + j];
+            orc_beam_batch(&b, verts, Rg);
             ++it;
         }
+        orc_pair *R = b.R, *R1 = b.R1;
+        const int32_t nR = b.nR, n1 = b.n1;
+        const int64_t dims_sum = b.dims_sum;
         const orc_pair *res = pp ? R1 : R;
         const int32_t nres = pp ? n1 : nR;
         for (int32_t k = 0; k < K; ++k) {
@@ -791,11 +821,12 @@ void orc_graph_search(const double *Y, int64_t N, int32_t D, const int32_t *grap
         }
         if (dims_total) dims_total[q] = dims_sum;
         if (iters_out) iters_out[q] = it;
-        free(add1);
-        free(R1);
-        free(cand);
-        free(expd);
-        free(R);
-        free(visited);
+        free(verts);
+        free(b.add1);
+        free(b.R1);
+        free(b.cand);
+        free(b.expd);
+        free(b.R);
+        free(b.visited);
     }
 }

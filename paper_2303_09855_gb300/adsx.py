@@ -262,7 +262,7 @@ class Graph:
 
 
 def build_graph(index: Index, X, degree: int = 32, nprobe: int = 16,
-                entries_per_cluster: int = 4, stream=None) -> Graph:
+                entries_per_cluster: int = 64, stream=None) -> Graph:
     """adsx_build_graph: a kNN proximity graph over the index's vectors (X: the
     raw vectors the index was built from) with entries_per_cluster
     farthest-point entry vertices per cluster."""

@@ -265,85 +265,18 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
     for (int64_t q = next_query(); q < g.nq; q = next_query()) {
         for (int i = lane; i < g.Dp; i += 32) qv[i] = g.qrot[q * g.Dp + i];
         __syncwarp();
-        // Start vertices: the n_ce entries of each of the query's n_entry
-        // nearest clusters (distinct; exact distances, one vertex per lane,
-        // blocks in order as in a DCO), merged into R 32 at a time by
-        // (distance, id), ef kept; vertex 0 when no cluster has an entry.
         unsigned long long dims = 0ull;
         int vcount = 0, nR = 0, n1 = 0;
-        const int ns = g.n_entry * g.n_ce;
-        for (int c0 = 0; c0 < ns + 32; c0 += 32) {
-            const bool tail = c0 >= ns;         // the pass after the entries
-            if (tail && nR > 0) break;
-            int64_t e = -1;
-            if (!tail) {
-                const int k = c0 + lane;
-                if (k < ns) e = g.entry[(int64_t)g.probes[q * g.n_entry + k / g.n_ce] * g.n_ce + k % g.n_ce];
-            } else if (lane == 0) {
-                e = 0;
-            }
-            bool fresh = false;
-            if (e >= 0) {
-                const unsigned bit = 1u << (e & 31);
-                fresh = !(atomicOr(bm + (e >> 5), bit) & bit);
-            }
-            const unsigned fb = __ballot_sync(FULL, fresh);
-            if (!fb) continue;
-            if (fresh) vl[vcount + __popc(fb & below)] = (int32_t)e;
-            vcount += __popc(fb);
-            float S = 0.f;
-            if (fresh) {
-                const float *x = g.data + g.vbase[e];
-                const int64_t st = g.vstride[e];
-#pragma unroll 1
-                for (int b = 0; b < g.nblk; ++b) S = accum_block_f32(x + b * st, qv + b * BLK, S);
-                dims += (unsigned long long)g.D;
-            }
-            const int na = stage_sorted(fresh, S, (int)e, ad, ai, lane);
-            nR = warp_merge(rd, ri, rx, nR, ad, ai, na, nd, ni, nx, g.ef, lane);
-            float *tf = rd; rd = nd; nd = tf;
-            int *ti = ri; ri = ni; ni = ti;
-            ti = rx; rx = nx; nx = ti;
-        }
-        // HNSW++: R1 starts as the K nearest start vertices (exact)
-        n1 = nR < g.K ? nR : g.K;
-        for (int k = lane; k < n1; k += 32) {
-            kd[k] = rd[k];
-            ki[k] = ri[k];
-        }
-        __syncwarp();
-        for (int it = 0; it < g.max_iter; ++it) {
-            int u = -1;
-            for (int b0 = 0; b0 < nR; b0 += 32) {
-                const int k = b0 + lane;
-                const unsigned bb = __ballot_sync(FULL, k < nR && rx[k] == 0);
-                if (bb) {
-                    u = b0 + __ffs(bb) - 1;
-                    break;
-                }
-            }
-            if (u < 0) break;
-            const int node = ri[u];
+        // One batch of DCOs (one vertex per lane, fresh ones only) against
+        // thresholds fixed for the batch, then the merges into R (and R1).
+        auto dco_batch = [&](int v, bool fresh) {
             const bool full = nR == g.ef, full1 = n1 == g.K;
             const float rmax = full ? rd[nR - 1] : INFINITY;
             const int rid = full ? ri[nR - 1] : INT_MAX;
             const float r1max = full1 ? kd[n1 - 1] : INFINITY;
             const int r1id = full1 ? ki[n1 - 1] : INT_MAX;
             const float r2 = g.pp ? r1max : rmax;           // the DCO threshold
-            __syncwarp();
-            if (lane == 0) rx[u] = 1;
-            // neighbours, one per lane, exact visited test
-            int v = -1;
-            if (lane < g.degree) v = g.nbr[(int64_t)node * g.degree + lane];
-            bool fresh = false;
-            if (v >= 0) {
-                const unsigned bit = 1u << (v & 31);
-                fresh = !(atomicOr(bm + (v >> 5), bit) & bit);
-            }
-            const unsigned fb = __ballot_sync(FULL, fresh);
-            if (fresh) vl[vcount + __popc(fb & below)] = v;
-            vcount += __popc(fb);
-            // Algorithm 1 per fresh neighbour against r2 (squared test of Sec. 3.2)
+            // Algorithm 1 against r2 (squared test of Sec. 3.2)
             float S = 0.f;
             int blk = 0;
             bool alive = fresh, atD = false;
@@ -393,6 +326,59 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
                     int *ti = ki; ki = ki2; ki2 = ti;
                 }
             }
+        };
+        // Start vertices: the n_ce entries of each of the query's n_entry
+        // nearest clusters, 32 list positions per batch, tested like the
+        // neighbours of one expansion (distinct; -1 skipped); vertex 0 when
+        // no cluster has an entry.
+        const int ns = g.n_entry * g.n_ce;
+        for (int c0 = 0; c0 < ns + 32; c0 += 32) {
+            const bool tail = c0 >= ns;         // the pass after the entries
+            if (tail && nR > 0) break;
+            int64_t e = -1;
+            if (!tail) {
+                const int k = c0 + lane;
+                if (k < ns) e = g.entry[(int64_t)g.probes[q * g.n_entry + k / g.n_ce] * g.n_ce + k % g.n_ce];
+            } else if (lane == 0) {
+                e = 0;
+            }
+            bool fresh = false;
+            if (e >= 0) {
+                const unsigned bit = 1u << (e & 31);
+                fresh = !(atomicOr(bm + (e >> 5), bit) & bit);
+            }
+            const unsigned fb = __ballot_sync(FULL, fresh);
+            if (!fb) continue;
+            if (fresh) vl[vcount + __popc(fb & below)] = (int32_t)e;
+            vcount += __popc(fb);
+            dco_batch((int)e, fresh);
+        }
+        for (int it = 0; it < g.max_iter; ++it) {
+            int u = -1;
+            for (int b0 = 0; b0 < nR; b0 += 32) {
+                const int k = b0 + lane;
+                const unsigned bb = __ballot_sync(FULL, k < nR && rx[k] == 0);
+                if (bb) {
+                    u = b0 + __ffs(bb) - 1;
+                    break;
+                }
+            }
+            if (u < 0) break;
+            const int node = ri[u];
+            __syncwarp();
+            if (lane == 0) rx[u] = 1;
+            // neighbours, one per lane, exact visited test
+            int v = -1;
+            if (lane < g.degree) v = g.nbr[(int64_t)node * g.degree + lane];
+            bool fresh = false;
+            if (v >= 0) {
+                const unsigned bit = 1u << (v & 31);
+                fresh = !(atomicOr(bm + (v >> 5), bit) & bit);
+            }
+            const unsigned fb = __ballot_sync(FULL, fresh);
+            if (fresh) vl[vcount + __popc(fb & below)] = v;
+            vcount += __popc(fb);
+            dco_batch(v, fresh);
         }
         const float *od = g.pp ? kd : rd;
         const int *oi = g.pp ? ki : ri;

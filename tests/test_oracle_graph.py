@@ -15,7 +15,10 @@ base-layer search of Sec. 2.2.1 with Algorithm 1 as its DCO, Sec. 4):
     when E reaches the cluster size, and the 2-approximation bound of greedy
     k-center against brute force over all E-subsets;
   - a cluster holding two blobs that no kNN edge joins: one entry reaches one
-    blob only, two entries give the exact KNN.
+    blob only, two entries give the exact KNN;
+  - start vertices are tested 32 list positions at a time like the
+    neighbours of an expansion: the first 32 face no threshold (exact, D
+    dims each), later ones face the best distance of the earlier batches.
 """
 import itertools
 import math
@@ -182,3 +185,28 @@ def test_two_blobs_in_one_cluster_need_two_entries():
     ids2, d2, _, _ = oracle.graph_search(Y, graph, np.repeat(two, 6, axis=0), Q, 5, 20, math.inf, 8)
     assert oracle.recall_at(ids1, gt, 5) == 0.5
     assert np.array_equal(ids2, gt) and np.allclose(d2, gd, rtol=1e-12)
+
+
+def test_start_vertices_are_tested_in_batches_of_32():
+    rng = np.random.default_rng(14)
+    D = 64
+    q = rng.normal(size=(1, D))
+    near = q + rng.normal(size=(32, D)) * 0.1
+    far = q + 100.0                                       # S_16 alone exceeds any threshold
+    Y = np.concatenate([near, far])                       # ids 0..31 near, 32..39 far
+    graph = np.full((40, 1), -1, np.int32)                # no edges: no expansion adds anything
+    starts = np.arange(40, dtype=np.int64)[None, :]
+    for pp in (False, True):
+        ids, d2, dims, iters = oracle.graph_search(Y, graph, starts, q, 1, 1, 2.1, 16, pp=pp)
+        best = int(np.argmin(np.sum((near - q) ** 2, axis=1)))
+        assert ids[0, 0] == best and iters[0] == 1
+        # first batch exact, the 8 far starts of the second batch stop at d = 16
+        assert dims[0] == 32 * D + 8 * 16
+        _, _, dims_exact, _ = oracle.graph_search(Y, graph, starts, q, 1, 1, math.inf, 16, pp=pp)
+        assert dims_exact[0] == 40 * D
+    # with exact DCOs R starts as the ef nearest of all starts, whatever the batching
+    rev = starts[:, ::-1].copy()
+    a = oracle.graph_search(Y, graph, starts, q, 5, 5, math.inf, 16)
+    b = oracle.graph_search(Y, graph, rev, q, 5, 5, math.inf, 16)
+    order = np.argsort(np.sum((Y - q) ** 2, axis=1))[:5]
+    assert np.array_equal(a[0][0], order) and np.array_equal(b[0][0], order)
