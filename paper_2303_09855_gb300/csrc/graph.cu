@@ -31,6 +31,13 @@ namespace {
 constexpr int GW = 4;                       // warps per block
 constexpr unsigned FULL = 0xffffffffu;
 
+// Asks L2 for the line holding p (a global address); no register result.
+__device__ __forceinline__ void prefetch_l2(const float *p)
+{
+    asm volatile("{\n\t.reg .u64 ga;\n\tcvta.to.global.u64 ga, %0;\n\tprefetch.global.L2 [ga];\n\t}"
+                 :: "l"(p));
+}
+
 __device__ __forceinline__ bool pless(float d1, int i1, float d2, int i2)
 {
     return d1 < d2 || (d1 == d2 && i1 < i2);
@@ -285,6 +292,10 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
             while (__ballot_sync(FULL, alive)) {
                 if (alive) {
                     const int e2 = blk + g.db < g.nblk ? blk + g.db : g.nblk;
+                    // the next step's blocks head for L2 while this step's
+                    // test is pending (wasted only if the test rejects)
+                    const int e3 = e2 + g.db < g.nblk ? e2 + g.db : g.nblk;
+                    for (int b = e2; b < e3; ++b) prefetch_l2(x + b * st);
                     for (int b = blk; b < e2; ++b) S = accum_block_f32(x + b * st, qv + b * BLK, S);
                     blk = e2;
                     if (blk >= g.nblk) {
