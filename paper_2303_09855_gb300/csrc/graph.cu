@@ -15,12 +15,15 @@
 // HNSW++ of Sec. 5.1: an exact K-set R1 gives the DCO threshold and the
 // output, the beam keeps each DCO's observed distance).  R (capacity ef) is a
 // sorted array of (distance, id) with an "expanded" flag; the search set S is
-// R's unexpanded entries (an entry evicted from R cannot matter again).  Each
-// iteration expands the first unexpanded entry: its neighbours (one per lane)
-// pass an exact visited test (a per-warp bitmap over all vertices, its set
-// bits cleared after the query), then the fresh ones run Algorithm 1 against
-// r = R's largest distance, fixed for the expansion; the accepted ones are
-// sorted by a warp bitonic network and merged into R by rank.
+// R's unexpanded entries (an entry evicted from R cannot matter again).  The
+// start vertices (32 list positions at a time), then each expansion's
+// neighbours, form batches of one vertex per lane: they pass an exact visited
+// test (a per-warp bitmap over all vertices, its set bits cleared after the
+// query), the fresh ones run Algorithm 1 against r = R's largest distance,
+// fixed for the batch (the next step's blocks prefetched into L2 while a
+// step's test is pending), and the accepted ones are sorted by a warp
+// bitonic network and merged into R by rank.  Each iteration expands R's
+// first unexpanded entry.
 #include <climits>
 
 #include "adsx_internal.cuh"
