@@ -14,6 +14,9 @@ the same algorithm on the same (exported) graph and start vertices:
   - many entries per cluster (a small upper layer: 72 start vertices, more
     than ef, tested 32 list positions at a time like an expansion's
     neighbours) against the oracle given the same starts;
+  - edge cases: fewer vertices than degree + 1 (padded neighbour lists),
+    D not a multiple of 16, an empty cluster, more entries asked than a
+    cluster has, K = ef above N (padded results), no queries;
   - argument checks (K > ef, entries per cluster out of range, a 16-bit
     index).
 """
@@ -170,3 +173,44 @@ def test_graph_argument_checks(gr):
             adsx.build_graph(ix16, wl.X)
     finally:
         ix16.close()
+
+
+@pytest.mark.parametrize("pp", [False, True])
+def test_graph_tiny_edge_cases(pp):
+    from paper_2303_09855_gb300 import adsx
+    from paper_2303_09855_gb300 import workloads as W
+    rng = np.random.default_rng(21)
+    N, D, nlist = 20, 20, 3                               # Dp = 32; 19 others < degree 32
+    X = rng.normal(size=(N, D)).astype(np.float32)
+    assign = (np.arange(N) % 2).astype(np.int32)         # 10 members each, cluster 2 empty
+    C = np.stack([X[assign == 0].mean(0), X[assign == 1].mean(0), X[0] + 50.0]).astype(np.float32)
+    P = W.make_P(D, 22).astype(np.float32)
+    ix = adsx.build_index(X, P, C, assign)
+    g = adsx.build_graph(ix, X, degree=32, nprobe=3, entries_per_cluster=30)
+    try:
+        nbr, ent = adsx.graph_export(g)
+        Y, Cr = oracle.rotate(P, X), oracle.rotate(P, C)
+        assert nbr.shape == (N, 32)
+        assert np.all((nbr >= 0).sum(1) == N - 1) and np.all(nbr[:, N - 1:] == -1)
+        for v in range(N):
+            assert sorted(nbr[v, :N - 1].tolist()) == [u for u in range(N) if u != v]
+        assert ent.shape == (nlist, 30) and np.all(ent[2] == -1) and np.all(ent[:2, 10:] == -1)
+        for c in range(2):                               # distinct points: every member once
+            assert sorted(ent[c, :10].tolist()) == np.nonzero(assign == c)[0].tolist()
+        Q = rng.normal(size=(6, D)).astype(np.float32)
+        Qr = oracle.rotate(P, Q)
+        K = ef = 50                                      # above N: padded results
+        ids, d2 = g.search(Q, K, ef, eps0=math.inf, n_entry=3, decoupled=pp)
+        probes, _ = oracle.probe(Cr, Qr, 3)
+        oids, od2, _, _ = oracle.graph_search(Y, nbr, ent[probes].reshape(6, -1), Qr, K, ef,
+                                              math.inf, 32, max_iter=4 * ef, pp=pp)
+        assert np.array_equal(ids, oids)
+        assert np.all(ids[:, N:] == -1) and np.all(np.isinf(d2[:, N:]))
+        assert np.array_equal(np.sort(ids[:, :N], axis=1), np.tile(np.arange(N), (6, 1)))
+        fin = ids >= 0
+        assert np.allclose(d2[fin], od2[fin], rtol=1e-5, atol=1e-6)
+        e_ids, e_d2 = g.search(Q[:0], 10, 16, n_entry=2)
+        assert e_ids.shape == (0, 10) and e_d2.shape == (0, 10)
+    finally:
+        g.close()
+        ix.close()
