@@ -1,0 +1,117 @@
+"""CPU checks of the C ABI's host-side argument validation: every case here
+is rejected with ADSX_EINVAL (and a message naming the problem) before the
+library touches a device, so it runs without a GPU.  Covers the index build
+(metric, sizes, storage type, assignments, malformed Kac walks), NULL
+handles and output pointers, the graph and server entry points, and the
+thread-local error message of adsx_last_error."""
+import ctypes
+import threading
+
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def A():
+    from paper_2303_09855_gb300 import adsx, build
+    build.build()
+    return adsx
+
+
+def _small(N=12, D=8, nlist=3, seed=0):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(N, D)).astype(np.float32)
+    P = np.eye(D, dtype=np.float32)
+    C = X[:nlist].copy()
+    assign = (np.arange(N) % nlist).astype(np.int32)
+    return X, P, C, assign
+
+
+def _rejects(A, fn, needle):
+    with pytest.raises(A.AdsxError) as ei:
+        fn()
+    assert ei.value.code == A.EINVAL, str(ei.value)
+    assert needle in str(ei.value), str(ei.value)
+
+
+def test_build_index_rejects_bad_arguments(A):
+    X, P, C, a = _small()
+    _rejects(A, lambda: A.build_index_metric(X, P, C, a, metric=7), "metric 7 not supported")
+    _rejects(A, lambda: A.build_index(X, P, C, a, storage=9), "storage type 9 not supported")
+    _rejects(A, lambda: A.build_index(X[:0], P, C, a[:0]), "N out of range")
+    _rejects(A, lambda: A.build_index(np.zeros((12, 0), np.float32), P, C, a), "D out of range")
+    big = np.zeros((2, 4081), np.float32)                 # above ADSX_MAX_D
+    _rejects(A, lambda: A.build_index(big, np.eye(1, dtype=np.float32), big, np.zeros(2, np.int32)),
+             "D out of range")
+    _rejects(A, lambda: A.build_index(X[:2], P, C, a[:2]), "nlist out of range")   # nlist > N
+    bad = a.copy()
+    bad[5] = 3                                            # cluster ids are 0..nlist-1
+    _rejects(A, lambda: A.build_index(X, P, C, bad), "assign[5] = 3 out of range")
+    bad[5] = -1
+    _rejects(A, lambda: A.build_index(X, P, C, bad), "assign[5] = -1 out of range")
+
+
+def test_build_index_kac_rejects_malformed_walks(A):
+    from paper_2303_09855_gb300 import workloads as W
+    X, _, C, a = _small(D=8)
+    pairs, cs = W.make_kac_walk(8, 3, 5)
+    rep = pairs.copy()
+    rep[1, 2] = rep[1, 3]                                 # an index twice in one layer
+    _rejects(A, lambda: A.build_index_kac(X, rep, cs, C, a), "layer 1")
+    oob = pairs.copy()
+    oob[0, 0] = 8                                         # dims are 0..D-1
+    _rejects(A, lambda: A.build_index_kac(X, oob, cs, C, a), "out of range or repeated")
+    rot = cs.copy()
+    rot[2, 0], rot[2, 1] = 0.6, 0.6                       # c^2 + s^2 = 0.72
+    _rejects(A, lambda: A.build_index_kac(X, pairs, rot, C, a), "c^2 + s^2 != 1")
+    many = np.tile(pairs[:1], (1025, 1))                  # above ADSX_MAX_KAC_LAYERS
+    _rejects(A, lambda: A.build_index_kac(X, many, np.tile(cs[:1], (1025, 1)), C, a),
+             "Kac walk layers out of range")
+
+
+def test_null_handles_and_outputs(A):
+    lib = A.load()
+    V = ctypes.c_void_p
+    ids = np.empty((1, 1), np.int64)
+    d2 = np.empty((1, 1), np.float32)
+    q = np.zeros((1, 8), np.float32)
+    rc = lib.adsx_search(None, V(q.ctypes.data), 1, 1, 1, ctypes.c_float(2.1), 32,
+                         V(ids.ctypes.data), V(d2.ctypes.data), None, None)
+    assert rc == A.EINVAL and "index is NULL" in A.last_error()
+    assert lib.adsx_free_index(None) == A.OK
+    assert lib.adsx_free_graph(None) == A.OK
+    assert lib.adsx_graph_info(None, None, None, None, None) == A.EINVAL
+    assert lib.adsx_graph_export(None, None, None) == A.EINVAL
+    assert "graph is NULL" in A.last_error()
+    X = np.zeros((4, 8), np.float32)
+    assert lib.adsx_build_graph(None, V(X.ctypes.data), 32, 1, 4, None, None) == A.EINVAL
+    assert "out is NULL" in A.last_error()
+    h = V()
+    assert lib.adsx_build_graph(None, V(X.ctypes.data), 32, 1, 4, None, ctypes.byref(h)) == A.EINVAL
+    assert "index is NULL" in A.last_error() and not h.value
+    out = V()
+    assert lib.adsx_server_create(None, 4, 4, 1, 1 << 20, 10, 4, ctypes.byref(out)) == A.EINVAL
+    assert not out.value
+
+
+def test_last_error_is_per_thread(A):
+    X, P, C, a = _small()
+    with pytest.raises(A.AdsxError):
+        A.build_index(X, P, C, a, storage=9)
+    mine = A.last_error()
+    assert "storage type 9" in mine
+    seen = {}
+
+    def other():
+        seen["before"] = A.last_error()                   # a fresh thread has no message
+        try:
+            A.build_index_metric(X, P, C, a, metric=5)
+        except A.AdsxError:
+            pass
+        seen["after"] = A.last_error()
+
+    t = threading.Thread(target=other)
+    t.start()
+    t.join()
+    assert seen["before"] == "" and "metric 5" in seen["after"]
+    assert A.last_error() == mine                         # untouched by the other thread
