@@ -120,7 +120,8 @@ int adsx_build_index(const float *X, int64_t N, int32_t D, const float *P,
  *                return inner products, largest first.
  * For both, padding slots hold -INF (ids -1); ties are ordered by id.  Other
  * arguments and errors as adsx_build_index.  adsx_dco_fixed_r and
- * adsx_search_noalloc accept ADSX_L2 indexes only (ADSX_EINVAL otherwise).
+ * adsx_search_noalloc accept ADSX_L2 indexes only, the graph search L2 and
+ * COSINE indexes (ADSX_EINVAL otherwise).
  */
 int adsx_build_index_metric(const float *X, int64_t N, int32_t D, const float *P,
                             const float *centroids, int32_t nlist,
@@ -385,7 +386,8 @@ const char *adsx_last_error(void);
 /* ------------------------------------------------------------------------
  * Graph-based search with ADSampling DCOs: HNSW+ (Sec. 4) -- the greedy beam
  * search HNSW runs on its base layer (Sec. 2.2.1) with Algorithm 1 as every
- * DCO -- on a kNN proximity graph over the vectors of an FP32 L2 index.
+ * DCO -- on a kNN proximity graph over the vectors of an FP32 L2 (or cosine)
+ * index.
  * ---------------------------------------------------------------------- */
 typedef struct adsx_graph adsx_graph;
 
@@ -404,7 +406,9 @@ typedef struct adsx_graph adsx_graph;
  * nearest of them).  The
  * vectors themselves are read in place from the index, which must outlive
  * the graph.
- *   index    an FP32 index built with the L2 metric (ADSX_EINVAL otherwise).
+ *   index    an FP32 index built with the L2 or the COSINE metric (ADSX_EINVAL
+ *            otherwise); with COSINE the graph is the Euclidean one over the
+ *            normalised vectors.
  *   X        host or device, N x D float32: the vectors the index was built from.
  *   degree   1..ADSX_MAX_DEGREE.   nprobe 1..min(nlist, ADSX_MAX_NPROBE).
  *   entries_per_cluster   1..ADSX_MAX_CLUSTER_ENTRIES.
@@ -446,7 +450,9 @@ int adsx_graph_export(const adsx_graph *graph, int32_t *neighbors, int64_t *entr
  * each DCO's observed distance (exact at d = D, else (D/d) S_d where
  * Algorithm 1 stopped).
  *   Qv, nq, ids, dists, dims_read, eps0, delta_d   as adsx_search
- *                (eps0 = +INF: exact DCOs, i.e. HNSW's own search).
+ *                (eps0 = +INF: exact DCOs, i.e. HNSW's own search); on a
+ *                COSINE index queries are normalised and dists are cosine
+ *                similarities 1 - d^2/2, largest first (-INF padding).
  *   K          1..ef.     ef 1..ADSX_MAX_EF.
  *   n_entry    1..min(nlist, ADSX_MAX_GRAPH_ENTRIES).
  * The graph keeps per-warp scratch for the visited test: searches on one

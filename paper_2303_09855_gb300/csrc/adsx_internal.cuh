@@ -349,6 +349,7 @@ struct GraphArgs {
     int64_t nq;
     int32_t D, Dp, nblk, db, test_on, K, ef, max_iter;
     int32_t pp;                 // 0: HNSW+, 1: HNSW++ (Sec. 5.1)
+    int32_t metric;             // ADSX_L2, or ADSX_COSINE (output 1 - d^2/2)
     int64_t *out_ids;
     float *out_d2;
     int64_t *out_dims;          // may be NULL

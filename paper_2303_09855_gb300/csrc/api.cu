@@ -997,7 +997,7 @@ int adsx_stream_status(const adsx_index *index, void *stream)
 }  // extern "C"
 
 // ---------------------------------------------------------------- graph search
-// HNSW+ (Sec. 4) on a kNN proximity graph over an FP32 L2 index; kernels in
+// HNSW+ (Sec. 4) on a kNN proximity graph over an FP32 L2 or cosine index; kernels in
 // graph.cu.  The graph owns its device memory and, once a search has run, the
 // per-warp scratch of the visited test (reused by later searches).
 struct Graph {
@@ -1041,8 +1041,8 @@ int adsx_build_graph(const adsx_index *index, const float *X, int32_t degree, in
     *out = nullptr;
     int rc = check_index(ix);
     if (rc) return rc;
-    if (ix->storage != ADSX_F32 || ix->metric != ADSX_L2)
-        return fail(ADSX_EINVAL, "graph search needs an FP32 L2 index");
+    if (ix->storage != ADSX_F32 || (ix->metric != ADSX_L2 && ix->metric != ADSX_COSINE))
+        return fail(ADSX_EINVAL, "graph search needs an FP32 L2 or cosine index");
     if (!X) return fail(ADSX_EINVAL, "X is NULL");
     if (degree < 1 || degree > ADSX_MAX_DEGREE)
         return fail(ADSX_EINVAL, "degree out of range (1..%d)", ADSX_MAX_DEGREE);
@@ -1150,8 +1150,8 @@ int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const fl
     int rc = check_index(ix);
     if (rc) return rc;
     if (!g || g->N != ix->N || g->nlist != ix->nlist) return fail(ADSX_EINVAL, "graph does not match the index");
-    if (ix->storage != ADSX_F32 || ix->metric != ADSX_L2)
-        return fail(ADSX_EINVAL, "graph search needs an FP32 L2 index");
+    if (ix->storage != ADSX_F32 || (ix->metric != ADSX_L2 && ix->metric != ADSX_COSINE))
+        return fail(ADSX_EINVAL, "graph search needs an FP32 L2 or cosine index");
     if (nq < 0 || (nq > 0 && (!Qv || !ids || !dists))) return fail(ADSX_EINVAL, "bad query arguments");
     if (ef < 1 || ef > ADSX_MAX_EF) return fail(ADSX_EINVAL, "ef out of range (1..%d)", ADSX_MAX_EF);
     if (K < 1 || K > ef) return fail(ADSX_EINVAL, "K out of range (1..ef)");
@@ -1215,6 +1215,7 @@ int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const fl
     CK(sc.get(&probes, (size_t)nq * n_entry), "alloc probes");
     CK(sc.get(&ftab, (size_t)nblk + 1), "alloc test factors");
     CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
+    CK(queries_before_probe(ix, qrot, nq, s), "normalise queries");
     CK(probe_queries(ix, qrot, nq, n_entry, probes, nullptr, sc), "entry clusters");
     adsx::GraphArgs a;
     a.data = static_cast<const float *>(ix->data);
@@ -1240,6 +1241,7 @@ int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const fl
     a.ef = ef;
     a.max_iter = max_iter;
     a.pp = decoupled;
+    a.metric = ix->metric;
     a.out_ids = oi.dev;
     a.out_d2 = od.dev;
     a.out_dims = odims.dev;

@@ -397,10 +397,13 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
         const float *od = g.pp ? kd : rd;
         const int *oi = g.pp ? ki : ri;
         const int no = g.pp ? n1 : nR;
+        const bool cosine = g.metric == ADSX_COSINE;
         for (int k = lane; k < g.K; k += 32) {
             const bool has = k < no;
             g.out_ids[q * g.K + k] = has ? (int64_t)oi[k] : (int64_t)-1;
-            g.out_d2[q * g.K + k] = has ? od[k] : INFINITY;
+            // cosine similarity of unit vectors: 1 - d^2/2, largest first
+            g.out_d2[q * g.K + k] = has ? (cosine ? fmaf(-0.5f, od[k], 1.f) : od[k])
+                                        : (cosine ? -INFINITY : INFINITY);
         }
 #pragma unroll
         for (int s = 16; s > 0; s >>= 1) dims += __shfl_xor_sync(FULL, dims, s);

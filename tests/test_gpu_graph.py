@@ -17,8 +17,10 @@ the same algorithm on the same (exported) graph and start vertices:
   - edge cases: fewer vertices than degree + 1 (padded neighbour lists),
     D not a multiple of 16, an empty cluster, more entries asked than a
     cluster has, K = ef above N (padded results), no queries;
+  - a cosine index: the graph over the normalised vectors, similarities
+    1 - d^2/2 of the oracle's search on normalised rows (HNSW+ and HNSW++);
   - argument checks (K > ef, entries per cluster out of range, a 16-bit
-    index).
+    index, an inner-product index).
 """
 import math
 
@@ -173,6 +175,12 @@ def test_graph_argument_checks(gr):
             adsx.build_graph(ix16, wl.X)
     finally:
         ix16.close()
+    ixip = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign, metric=adsx.IP)
+    try:
+        with pytest.raises(adsx.AdsxError):
+            adsx.build_graph(ixip, wl.X)
+    finally:
+        ixip.close()
 
 
 @pytest.mark.parametrize("pp", [False, True])
@@ -214,3 +222,35 @@ def test_graph_tiny_edge_cases(pp):
     finally:
         g.close()
         ix.close()
+
+
+@pytest.mark.parametrize("pp", [False, True])
+def test_graph_cosine_matches_oracle(gr, pp):
+    adsx, wl, ix, g, Y, Cr, Qr, nbr, ent = gr
+    Yn, Cn, Qn = oracle.normalize_rows(Y), oracle.normalize_rows(Cr), oracle.normalize_rows(Qr)
+    ixc = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign, metric=adsx.COSINE)
+    gc = adsx.build_graph(ixc, wl.X, degree=32, nprobe=10, entries_per_cluster=8)
+    try:
+        nbrc, entc = adsx.graph_export(gc)
+        ef = 64
+        ids, cs, dims = gc.search(wl.Q, K, ef, eps0=2.1, delta_d=32, return_dims=True,
+                                  n_entry=NE, decoupled=pp)
+        probes, _ = oracle.probe(Cn, Qn, NE)
+        starts = entc[probes].reshape(len(Qn), -1)
+        oids, od2, _, _ = oracle.graph_search(Yn, nbrc, starts, Qn, K, ef, 2.1, 32,
+                                              max_iter=4 * ef, pp=pp)
+        ok = ~near_tie_queries(Cn, Qn, NE)
+        same = sum(1 for q in range(len(Qn)) if ok[q] and np.array_equal(ids[q], oids[q]))
+        assert same >= 0.85 * ok.sum(), (same, int(ok.sum()))
+        for q in range(len(Qn)):
+            row = ids[q][ids[q] >= 0]
+            assert len(set(row.tolist())) == len(row)
+            for i, v in zip(ids[q], cs[q]):
+                if i >= 0:
+                    assert abs(v - float(Yn[i] @ Qn[q])) <= 1e-5, (q, i, v)
+            assert np.all(np.diff(cs[q][ids[q] >= 0]) <= 1e-6)      # largest first
+        gt, _ = oracle.knn_exact(Yn, Qn, K)
+        assert oracle.recall_at(ids, gt, K) >= oracle.recall_at(oids, gt, K) - 0.02
+    finally:
+        gc.close()
+        ixc.close()
