@@ -2,8 +2,9 @@
 is rejected with ADSX_EINVAL (and a message naming the problem) before the
 library touches a device, so it runs without a GPU.  Covers the index build
 (metric, sizes, storage type, assignments, malformed Kac walks), NULL
-handles and output pointers, the graph and server entry points, and the
-thread-local error message of adsx_last_error."""
+handles and output pointers, the graph and server entry points (create,
+submit, wait, cancel, stats reset), and the thread-local error message of
+adsx_last_error."""
 import ctypes
 import threading
 
@@ -91,7 +92,15 @@ def test_null_handles_and_outputs(A):
     assert "index is NULL" in A.last_error() and not h.value
     out = V()
     assert lib.adsx_server_create(None, 4, 4, 1, 1 << 20, 10, 4, ctypes.byref(out)) == A.EINVAL
-    assert not out.value
+    assert not out.value and "index is NULL" in A.last_error()
+    assert lib.adsx_server_create(None, 4, 4, 1, 1 << 20, 10, 4, None) == A.EINVAL
+    t = ctypes.c_int64()
+    assert lib.adsx_server_submit(None, V(q.ctypes.data), 10, 4, ctypes.c_float(2.1), 32,
+                                  ctypes.byref(t)) == A.EINVAL
+    assert lib.adsx_server_wait(None, 0, 10, None, None, None) == A.EINVAL
+    assert lib.adsx_server_cancel(None, 0) == A.EINVAL
+    assert lib.adsx_server_reset_stats(None) == A.EINVAL
+    assert "server is NULL" in A.last_error()
 
 
 def test_last_error_is_per_thread(A):
