@@ -356,7 +356,7 @@ struct GraphArgs {
     unsigned *bitmap;           // warps x bm_words visited bits (all zero between queries)
     int64_t bm_words;
     int32_t *vlist;             // warps x vcap visited ids of the current query
-    int64_t vcap;               // >= n_entry n_ce + 1 + max_iter * degree
+    int64_t vcap;               // >= min(n_entry n_ce + 1 + max_iter * degree, N)
     int32_t warps;              // resident warps launched
     unsigned long long *qnext;  // next query to take (zeroed by the launcher)
 };

@@ -1172,8 +1172,10 @@ int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const fl
         warps = adsx::graph_search_resident_warps(ix->Dp, ef, K, nsm);
         if (warps <= 0) return fail(ADSX_EINVAL, "graph search: ef and D need more shared memory than an SM has");
         const int64_t bm_words = (g->N + 31) / 32;
-        const int64_t vcap = 1 + (int64_t)ADSX_MAX_GRAPH_ENTRIES * ADSX_MAX_CLUSTER_ENTRIES +
-                             (int64_t)max_iter * g->degree;
+        // visited ids are distinct: never more than N of them
+        const int64_t vcap = std::min<int64_t>(1 + (int64_t)ADSX_MAX_GRAPH_ENTRIES * ADSX_MAX_CLUSTER_ENTRIES +
+                                                   (int64_t)max_iter * g->degree,
+                                               g->N);
         if (g->warps < warps || g->bm_words != bm_words || g->vcap < vcap || !g->qnext) {
             cudaStreamSynchronize(s);
             cudaFree(g->bitmap);

@@ -14,6 +14,7 @@ the same algorithm on the same (exported) graph and start vertices:
   - many entries per cluster (a small upper layer: 72 start vertices, more
     than ef, tested 32 list positions at a time like an expansion's
     neighbours) against the oracle given the same starts;
+  - maximum sizes: ef = K = 512, 1024 start vertices (16 clusters x 64);
   - edge cases: fewer vertices than degree + 1 (padded neighbour lists),
     D not a multiple of 16, an empty cluster, more entries asked than a
     cluster has, K = ef above N (padded results), no queries;
@@ -254,3 +255,30 @@ def test_graph_cosine_matches_oracle(gr, pp):
     finally:
         gc.close()
         ixc.close()
+
+
+def test_graph_maximum_sizes(gr):
+    """ef = K = ADSX_MAX_EF, 16 start clusters x 64 entries (1024 start
+    vertices, 32 start batches), exact DCOs, against the oracle on the same
+    graph and starts."""
+    adsx, wl, ix, g, Y, Cr, Qr, nbr, ent = gr
+    g64 = adsx.build_graph(ix, wl.X, degree=32, nprobe=10, entries_per_cluster=64)
+    try:
+        nbr64, ent64 = adsx.graph_export(g64)
+        nq = 40
+        ids, d2 = g64.search(wl.Q[:nq], 512, 512, eps0=math.inf, n_entry=16)
+        probes, _ = oracle.probe(Cr, Qr[:nq], 16)
+        starts = ent64[probes].reshape(nq, -1)
+        assert starts.shape[1] == 1024
+        oids, od2, _, _ = oracle.graph_search(Y, nbr64, starts, Qr[:nq], 512, 512, math.inf, 32,
+                                              max_iter=4 * 512)
+        ok = ~near_tie_queries(Cr, Qr[:nq], 16)
+        same = sum(1 for q in range(nq) if ok[q] and set(ids[q].tolist()) == set(oids[q].tolist()))
+        assert same >= 0.9 * ok.sum(), (same, int(ok.sum()))
+        for q in range(nq):
+            fin = ids[q] >= 0
+            assert len(set(ids[q][fin].tolist())) == fin.sum()
+            ex = np.sum((Y[ids[q][fin]] - Qr[q]) ** 2, axis=1)
+            assert np.all(np.abs(d2[q][fin] - ex) <= REL * ex + 1e-6), q
+    finally:
+        g64.close()
