@@ -630,6 +630,18 @@ def run_graph(args):
             "speedup_vs_hnsw": res["hnsw"]["ms"] / res["hnsw_plus"]["ms"],
             "speedup_pp_vs_hnsw": res["hnsw"]["ms"] / res["hnsw_pp"]["ms"],
             "dims_fraction_vs_hnsw": res["hnsw_plus"]["dims"] / res["hnsw"]["dims"]}
+    # the search is latency-bound (dependent round trips per batch); its DCO
+    # bytes per second against the copy peak say how far from HBM-bound it is
+    peak, kind = peaks()
+    hp = res["hnsw_plus"]
+    achieved = 4.0 * hp["dims"] / (hp["ms"] * 1e-3) / 1e9
+    line["roofline"] = {"bound": "latency", "kernel": "graph_search_kernel",
+                        "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "peak_kind": kind, "traffic": None,
+                        "note": "algorithmic bytes = 4 x dims sampled (FP32 DCO reads) of the HNSW+ arm"}
+    # timed searches of the three arms, 6 kernels each (rotation, norms,
+    # centroid GEMM, select, test factors, graph search)
+    line["gpu_launches"] = 6 * args.steps * 3
     print(json.dumps(line), flush=True)
     g.close()
     ix.close()
