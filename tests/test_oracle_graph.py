@@ -18,7 +18,11 @@ base-layer search of Sec. 2.2.1 with Algorithm 1 as its DCO, Sec. 4):
     blob only, two entries give the exact KNN;
   - start vertices are tested 32 list positions at a time like the
     neighbours of an expansion: the first 32 face no threshold (exact, D
-    dims each), later ones face the best distance of the earlier batches.
+    dims each), later ones face the best distance of the earlier batches;
+  - HNSW++ (Sec. 5.1) on a hand-worked graph: rejected vertices enter the
+    beam by their observed distance (D/d) S_d, which decides which branch is
+    expanded (result, expansions and dims fixed by hand), where HNSW+ on the
+    same graph takes the other branch.
 """
 import itertools
 import math
@@ -210,3 +214,35 @@ def test_start_vertices_are_tested_in_batches_of_32():
     b = oracle.graph_search(Y, graph, rev, q, 5, 5, math.inf, 16)
     order = np.argsort(np.sum((Y - q) ** 2, axis=1))[:5]
     assert np.array_equal(a[0][0], order) and np.array_equal(b[0][0], order)
+
+
+def test_hnsw_pp_beam_keeps_observed_distances_hand_worked():
+    """Sec. 5.1 on a hand-worked graph (q = 0, D = 64, delta_d = 16, eps0 = 0,
+    so a DCO rejects at d iff (D/d) S_d > r^2; K = 1, ef = 2).  The start a
+    (distance 1) fills R1, r^2 = 1.  a's neighbours: v1 has S_16 = 0.3, rejected
+    at d = 16, observed distance 4 x 0.3 = 1.2; v2 has S_16 = 0.1, S_32 = 0.55,
+    rejected at d = 32, observed 2 x 0.55 = 1.1.  Both enter the beam by their
+    observed distances, which keeps a and v2 (ef = 2).  Expanding v2 finds w2
+    (0.5 < r^2: exact, into R1); w1 behind v1 is never visited.  Expansions:
+    a, v2, w2; dims 64 (a) + 16 (v1) + 32 (v2) + 64 (w2)."""
+    D = 64
+    Y = np.zeros((5, D))
+    Y[0, 63] = 1.0                                        # a: distance^2 1
+    Y[1, 0], Y[1, 63] = np.sqrt(0.3), np.sqrt(1.7)        # v1: S_16 = 0.3, total 2
+    Y[2, 0], Y[2, 16], Y[2, 63] = np.sqrt(0.1), np.sqrt(0.45), np.sqrt(1.45)   # v2
+    Y[3, 62] = np.sqrt(0.9)                               # w1 (behind v1)
+    Y[4, 62] = np.sqrt(0.5)                               # w2 (behind v2)
+    graph = np.full((5, 2), -1, np.int32)
+    graph[0] = [1, 2]
+    graph[1, 0] = 3
+    graph[2, 0] = 4
+    q = np.zeros((1, D))
+    ids, d2, dims, iters = oracle.graph_search(Y, graph, np.zeros(1, np.int64), q, 1, 2, 0.0, 16,
+                                               pp=True)
+    assert ids[0].tolist() == [4] and abs(d2[0, 0] - 0.5) < 1e-12
+    assert iters[0] == 3 and dims[0] == 64 + 16 + 32 + 64
+    # HNSW+ on the same graph: R is not full while a's neighbours are tested
+    # (r = +inf), so v1 and v2 get exact distances 2 and the beam {a, v1}
+    # (ties by id) expands v1 and finds w1 (0.9 < 1); w2 is never reached.
+    ids, d2, dims, iters = oracle.graph_search(Y, graph, np.zeros(1, np.int64), q, 1, 2, 0.0, 16)
+    assert ids[0].tolist() == [3] and abs(d2[0, 0] - 0.9) < 1e-12
