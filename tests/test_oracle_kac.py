@@ -4,6 +4,8 @@ O(D log D) by Kac's walk instead of a dense matrix product):
   - a hand-worked layer (a quarter turn on one pair, identity on the other);
   - layers apply in order (two layers equal the second applied to the
     first's output);
+  - with D odd, the coordinate a layer leaves unpaired passes through it
+    unchanged, and each pair's 2-vector keeps its length;
   - the walk is orthogonal to within the rounding of its FP32 cosines and
     sines, and the dense matrix equals the walk applied to each vector;
   - after 3 log2(D) layers the walk mixes like a Haar rotation for the
@@ -35,6 +37,21 @@ def test_layers_apply_in_order():
     assert np.allclose(both, one_then_two, atol=0, rtol=0)
     other_order = oracle.kac_apply(pairs[:1], cs[:1], oracle.kac_apply(pairs[1:], cs[1:], X))
     assert not np.allclose(both, other_order)
+
+
+def test_odd_dimension_rests_one_coordinate_per_layer():
+    D = 9
+    pairs, cs = W.make_kac_walk(D, 5, 8)
+    X = np.random.default_rng(1).normal(size=(4, D))
+    for l in range(5):
+        y = oracle.kac_apply(pairs[l:l + 1], cs[l:l + 1], X)
+        rest = sorted(set(range(D)) - set(pairs[l].tolist()))
+        assert len(rest) == 1
+        assert np.array_equal(y[:, rest[0]], X[:, rest[0]])
+        for t in range(D // 2):
+            i, j = pairs[l, 2 * t], pairs[l, 2 * t + 1]
+            assert np.allclose(y[:, i] ** 2 + y[:, j] ** 2, X[:, i] ** 2 + X[:, j] ** 2,
+                               rtol=1e-6)
 
 
 def test_walk_is_orthogonal_and_matrix_matches():
