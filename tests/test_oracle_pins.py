@@ -146,6 +146,29 @@ def test_dco_hand_worked_cases():
         assert (dec, dims, S) == (c["decision"], c["dims"], c["S"]), c["name"]
 
 
+def test_dco_margin_is_the_closest_comparison_hand_worked():
+    """The margin the GPU tests use to set boundary cases aside: the smallest
+    |lhs / rhs - 1| over every comparison Algorithm 1 made (D S_d against
+    r^2 d (1 + eps0/sqrt(d))^2 at each d < D, then S_D against r^2)."""
+    q = np.zeros(4)
+    o = np.array([1.0, 1.0, 1.0, 0.0])                   # S_2 = 2, S_4 = 3
+    # eps0 = 0, r^2 = 5: d = 2: 8 vs 10 (0.2); d = 4: 3 vs 5 (0.4) -> 0.2
+    assert oracle.dco(o, q, 5.0, 0.0, 2) == (oracle.POSITIVE, 4, 3.0, pytest.approx(0.2))
+    # r^2 = 4: d = 2 sits on the boundary (8 vs 8, not rejected) -> margin 0
+    assert oracle.dco(o, q, 4.0, 0.0, 2) == (oracle.POSITIVE, 4, 3.0, 0.0)
+    # r^2 = 2.5: d = 2: 8 > 5, rejected there with margin 0.6
+    assert oracle.dco(o, q, 2.5, 0.0, 2) == (oracle.REJECTED, 2, 2.0, pytest.approx(0.6))
+    # eps0 = 1, r^2 = 5: d = 2: 8 vs 10 (1 + 1/sqrt 2)^2 = 29.14.. (0.7255..); d = 4: 0.4
+    g2 = (1.0 + 1.0 / np.sqrt(2.0)) ** 2
+    res, dims, S, m = oracle.dco(o, q, 5.0, 1.0, 2)
+    assert (res, dims, S) == (oracle.POSITIVE, 4, 3.0)
+    assert m == pytest.approx(min(abs(8.0 / (10.0 * g2) - 1.0), 0.4))
+    # r^2 = 2.9: no rejection (8 vs 5.8 g2), negative at d = D: 3 vs 2.9
+    res, dims, S, m = oracle.dco(o, q, 2.9, 1.0, 2)
+    assert (res, dims, S) == (oracle.NEGATIVE_AT_D, 4, 3.0)
+    assert m == pytest.approx(min(abs(8.0 / (5.8 * g2) - 1.0), abs(3.0 / 2.9 - 1.0)))
+
+
 def test_dco_full_scan_is_exact_distance():
     rng = np.random.default_rng(3)
     o, q = rng.standard_normal(37), rng.standard_normal(37)
