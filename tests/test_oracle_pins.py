@@ -231,6 +231,27 @@ def small_wl():
     return wl, Y, Cr, Qr
 
 
+def test_ivf_ads_visit_order_hand_worked():
+    """Sequential IVF+ visits clusters by (centroid distance, id) and members
+    by ascending id; r^2 tightens along that order, so the dims it samples
+    pin the order.  eps0 = 0 (reject at d iff (D/d) S_d > r^2), K = 1, q = 0."""
+    q = np.zeros((1, 4))
+    # A: cluster 0 (nearer centroid) holds id 0 at distance 1; cluster 1 holds
+    # id 1 (S_2 = 4, distance 4) and id 2 (distance 0.25).  Cluster 0 first:
+    # id 0 exact (4 dims, r^2 = 1), id 1 rejected at d = 2, id 2 exact -> 10.
+    # (Cluster 1 first would sample 4 + 4 + 4 = 12.)
+    Y = np.array([[0, 0, 0, 1.0], [2.0, 0, 0, 0], [0, 0, 0, 0.5]])
+    C = np.array([[0, 0, 0, 0.9], [1.0, 0, 0, 0.3]])
+    ids, d2, dims, ncand = oracle.ivf_ads(Y, C, np.array([0, 1, 1]), q, 1, 2, 0.0, 2)
+    assert ids[0, 0] == 2 and d2[0, 0] == 0.25 and ncand[0] == 3 and dims[0] == 10
+    # B: one cluster, id 0 at distance 0.25, id 1 with S_2 = 0.36 (distance
+    # 0.36).  Ascending ids: id 0 exact (r^2 = 0.25), id 1 rejected at d = 2
+    # (2 x 0.36 > 0.25) -> 6 dims.  (Id 1 first would sample 8.)
+    Y = np.array([[0, 0, 0, 0.5], [0.6, 0, 0, 0]])
+    ids, d2, dims, ncand = oracle.ivf_ads(Y, np.zeros((1, 4)), np.array([0, 0]), q, 1, 1, 0.0, 2)
+    assert ids[0, 0] == 0 and dims[0] == 6
+
+
 def test_ivf_ads_with_infinite_eps0_is_ivf(small_wl):
     wl, Y, Cr, Qr = small_wl
     e_ids, e_d = oracle.ivf_exact(Y, Cr, wl.assign, Qr, 10, 6)
