@@ -4,7 +4,8 @@ library touches a device, so it runs without a GPU.  Covers the index build
 (metric, sizes, storage type, assignments, malformed Kac walks), NULL
 handles and output pointers, the graph and server entry points (create,
 submit, wait, cancel, stats reset), and the thread-local error message of
-adsx_last_error."""
+adsx_last_error.  Without a device, valid arguments fail with ADSX_ECUDA:
+there is no host fallback."""
 import ctypes
 import threading
 
@@ -124,3 +125,15 @@ def test_last_error_is_per_thread(A):
     t.join()
     assert seen["before"] == "" and "metric 5" in seen["after"]
     assert A.last_error() == mine                         # untouched by the other thread
+
+
+def test_no_cpu_fallback_without_a_device(A):
+    """With valid arguments and no GPU the library fails with ADSX_ECUDA: it
+    never computes a result on the host."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    X, P, C, a = _small()
+    with pytest.raises(A.AdsxError) as ei:
+        A.build_index(X, P, C, a)
+    assert ei.value.code == A.ECUDA, str(ei.value)
