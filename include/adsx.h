@@ -257,8 +257,11 @@ int adsx_rotate(const adsx_index *index, const float *Qv, int64_t nq,
 /*
  * adsx_dco_fixed_r -- Algorithm 1 for every (query, indexed vector) pair with
  * a FIXED squared threshold per query: the verification protocol of
- * Sec. 6.2.5 (linear scan, independent DCOs), run by the same device DCO
- * code as adsx_search.
+ * Sec. 6.2.5 (linear scan, independent DCOs), run by adsx_search's own scan
+ * kernel in a fixed-threshold mode (every cluster scanned, no KNN set), so
+ * each decision comes from the same per-step FP32 accumulation order, test
+ * and (16-bit storage) exact recheck as in a search.  The test is off for
+ * eps0 = +INF or delta_d >= D (one full-width step, as in a search).
  *   r2         host or device, nq float32 squared thresholds (+INF allowed).
  *   decisions  host or device, nq x N uint8, indexed by original vector id:
  *              0 = rejected at some d < D (Case 1), 1 = reached d = D with
@@ -314,8 +317,9 @@ int adsx_stage_ms(const adsx_index *index, float *ms);
  * cudaMalloc / cudaMallocAsync would fail, or would lock or synchronise and
  * stall other work.  The paper has no counterpart; this is an interface
  * variant of adsx_search, computing the same results.
- *   - Same arguments and results as adsx_search, but Qv, ids, dists and
- *     dims_read must all be DEVICE pointers (ADSX_EINVAL otherwise); the call
+ *   - Same arguments and results as adsx_search (delta_d = 0 too: the
+ *     index's tuned step), but Qv, ids, dists and dims_read must all be
+ *     DEVICE pointers on the index's GPU (ADSX_EINVAL otherwise); the call
  *     only enqueues work on `stream` and never synchronises.
  *   - No device memory is allocated or freed: every temporary buffer is cut
  *     from one fixed array of ADSX_NOALLOC_SCRATCH_BYTES that the library
@@ -324,7 +328,10 @@ int adsx_stage_ms(const adsx_index *index, float *ms);
  *     4*nprobe) bytes, plus partial top-K lists when nq is small) returns
  *     ADSX_EINVAL with the size it needed; split the batch.
  *   - The first call on each device looks up the array's device address on
- *     that device; make that first call before any stream capture.
+ *     that device and keeps it; make that first call before any stream
+ *     capture.  The address belongs to the device's primary context: after
+ *     cudaDeviceReset (which destroys it) this entry point must not be called
+ *     again in the process.
  *   - All calls share the one array: calls whose work overlaps on the GPU
  *     (different streams, or host threads) race on it and give wrong
  *     results.  Serialise them, e.g. on one stream.

@@ -14,6 +14,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <string>
@@ -331,6 +332,17 @@ struct ScanArgs {
     int32_t metric = ADSX_L2;
     const float *onorm = nullptr;
     const float *qnorm = nullptr;
+    // fixed-threshold mode (the verification protocol of Sec. 6.2.5,
+    // adsx_dco_fixed_r): decisions != NULL makes every item test all members
+    // of every cluster (probe slot p is cluster p; probes unused) against the
+    // fixed r2fixed[q], with the same accumulation, test and recheck code as
+    // a search but no KNN set; each candidate's decision (0 rejected at
+    // d < D, 1 positive, 2 negative at d = D) and dims go to
+    // decisions / dec_dims[q * N + original id]
+    const float *r2fixed = nullptr;
+    uint8_t *decisions = nullptr;
+    int32_t *dec_dims = nullptr;
+    int64_t N = 0;
 };
 
 // Graph search with ADSampling DCOs (HNSW+, graph.cu).
@@ -399,6 +411,60 @@ inline int32_t uniform_splits(int64_t nq, int nprobe, int K, int64_t target,
     return (int32_t)(S > 1 ? S : 1);
 }
 
+
+// Candidate-buffer capacity of a warp's KNN set for K: a power of two
+// >= max(2 next_pow2(K), K + 32).
+inline int32_t knn_buffer_capacity(int K)
+{
+    int Kp = 1;
+    while (Kp < K) Kp <<= 1;
+    const int need = 2 * Kp > K + 32 ? 2 * Kp : K + 32;
+    int C = 1;
+    while (C < need) C <<= 1;
+    return C;
+}
+
+// The fields of a uniform search's scan (one K and one nprobe for every
+// query) that every entry point sets the same way: the index's arrays and
+// shapes, the buffer capacity, the splits per query, the step and whether the
+// test runs (eps0 = +inf, delta_d >= D: FDScanning, one full-width step; pd:
+// PDScanning's f(d) = 1).  The caller sets the per-call buffers (queries,
+// probes, test factors, outputs, counters and split scratch).  Returns
+// false when nq * S does not fit the item counter.
+inline bool fill_uniform_scan(ScanArgs &a, const Index *ix, int64_t nq, int K, int nprobe,
+                              float eps0, int delta_d, int pd)
+{
+    a.metric = ix->metric;
+    a.onorm = ix->onorm;
+    a.data = ix->data;
+    a.rows32 = ix->rows32;
+    a.norms = ix->norms;
+    a.storage = ix->storage;
+    a.ids = ix->ids;
+    a.off = ix->off;
+    a.nq = nq;
+    a.D = ix->D;
+    a.Dp = ix->Dp;
+    a.nblk = ix->Dp / BLK;
+    a.nprobe = nprobe;
+    a.K = K;
+    a.C = knn_buffer_capacity(K);
+    a.S = uniform_splits(nq, nprobe, K, scan_items_target(ix->device, ix->items_per_sm),
+                         ix->N / ix->nlist);
+    if (nq * (int64_t)a.S >= ((int64_t)1 << 31)) return false;
+    a.n_items = (int32_t)(nq * a.S);
+    a.db = delta_d / BLK;
+    a.test_on = (isinf(eps0) && !pd) ? 0 : 1;
+    if (a.db >= a.nblk) a.test_on = 0;
+    if (!a.test_on) a.db = a.nblk;   // FDScanning: the whole vector in one step
+    a.out_dims = nullptr;
+    a.part_d = nullptr;
+    a.part_i = nullptr;
+    a.r2g = nullptr;
+    a.err = ix->err;
+    return true;
+}
+
 // Batched form: validates per-query K / nprobe, chooses splits, orders the
 // queries longest-first and writes the item list (capacity nq * 64 items).
 cudaError_t launch_plan_batched(const int32_t *Kq, const int32_t *nprobe_q, int64_t nq,
@@ -412,24 +478,6 @@ constexpr unsigned ERR_ZERO_ROW = 16u;    // a zero-norm row where a unit row is
 constexpr int BATCH_MAX_SPLITS = 16;
 int ads_scan_grid(const ScanArgs &a, int device);
 
-struct FixedRArgs {
-    const void *data;
-    const float *rows32;
-    int32_t storage;
-    const int32_t *ids;
-    const int64_t *off;
-    const int32_t *tile_off;
-    int32_t nlist, total_tiles;
-    int64_t N;
-    const float *qrot;
-    const float *r2;
-    int64_t nq;
-    int32_t D, Dp, nblk, db;
-    float eps0;
-    int32_t test_on;
-    uint8_t *decisions;
-    int32_t *dims;
-};
-cudaError_t launch_dco_fixed_r(const FixedRArgs &a, cudaStream_t s);
+
 
 }  // namespace adsx

@@ -592,47 +592,15 @@ static int search_impl(const adsx_index *index, const float *Qv, int64_t nq, int
     CK(queries_after_probe(ix, qrot, nq, sc, &qnorm), "normalise queries");
 
     adsx::ScanArgs a;
-    a.metric = ix->metric;
-    a.onorm = ix->onorm;
+    if (!adsx::fill_uniform_scan(a, ix, nq, K, nprobe, eps0, delta_d, pd))
+        return fail(ADSX_EINVAL, "too many queries in one call");
     a.qnorm = qnorm;
-    a.data = ix->data;
-    a.rows32 = ix->rows32;
-    a.norms = ix->norms;
-    a.storage = ix->storage;
-    a.ids = ix->ids;
-    a.off = ix->off;
     a.qrot = qrot;
     a.probes = probes;
-    a.nq = nq;
-    a.D = ix->D;
-    a.Dp = ix->Dp;
-    a.nblk = ix->Dp / adsx::BLK;
-    a.nprobe = nprobe;
-    a.K = K;
-    {
-        int Kp = 1;
-        while (Kp < K) Kp <<= 1;
-        int need = std::max(2 * Kp, K + 32);
-        a.C = 1;
-        while (a.C < need) a.C <<= 1;
-        a.S = adsx::uniform_splits(nq, nprobe, K,
-                                   adsx::scan_items_target(ix->device, ix->items_per_sm),
-                                   ix->N / ix->nlist);
-    }
-    if (nq * (int64_t)a.S >= ((int64_t)1 << 31)) return fail(ADSX_EINVAL, "too many queries in one call");
-    a.n_items = (int32_t)(nq * a.S);
-    a.db = delta_d / adsx::BLK;
-    a.test_on = (isinf(eps0) && !pd) ? 0 : 1;
-    if (a.db >= a.nblk) a.test_on = 0;
-    if (!a.test_on) a.db = a.nblk;   // FDScanning: the whole vector in one step
     a.out_ids = oi.dev;
     a.out_d2 = od.dev;
     a.out_dims = odims.dev;
-    a.part_d = nullptr;
-    a.part_i = nullptr;
-    a.r2g = nullptr;
     a.work_counter = counter;
-    a.err = ix->err;
     float *ftab = nullptr;
     CK(sc.get(&ftab, (size_t)a.nblk + 1), "alloc test factors");
     a.ftab = ftab;
@@ -843,7 +811,6 @@ int adsx_dco_fixed_r(const adsx_index *index, const float *Qv, int64_t nq, const
     if (rc) return rc;
     if (ix->metric != ADSX_L2) return fail(ADSX_EINVAL, "adsx_dco_fixed_r supports L2 indexes only");
     if (nq < 0 || (nq > 0 && (!Qv || !r2 || !decisions))) return fail(ADSX_EINVAL, "bad arguments");
-    if (nq > 65535) return fail(ADSX_EINVAL, "nq > 65535 in one fixed-r call");
     if ((rc = check_blocks(delta_d, eps0))) return rc;
     if (nq == 0) return ADSX_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -851,36 +818,34 @@ int adsx_dco_fixed_r(const adsx_index *index, const float *Qv, int64_t nq, const
     Buf<float> q, rr;
     Buf<uint8_t> dec;
     Buf<int32_t> dm;
-    float *qrot = nullptr;
+    float *qrot = nullptr, *ftab = nullptr;
+    unsigned *counter = nullptr;
     CK(stage_in(sc, Qv, (size_t)nq * ix->D, q), "stage queries");
     CK(stage_in(sc, r2, (size_t)nq, rr), "stage r2");
     CK(stage_out(sc, decisions, (size_t)nq * ix->N, dec), "stage decisions");
     CK(stage_out(sc, dims, (size_t)nq * ix->N, dm), "stage dims");
     CK(sc.get(&qrot, (size_t)nq * ix->Dp), "alloc q'");
+    CK(sc.get(&counter, 1), "alloc counter");
     CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
-    adsx::FixedRArgs a;
-    a.data = ix->data;
-    a.rows32 = ix->rows32;
-    a.storage = ix->storage;
-    a.ids = ix->ids;
-    a.off = ix->off;
-    a.tile_off = ix->tile_off;
-    a.nlist = ix->nlist;
-    a.total_tiles = ix->total_tiles;
-    a.N = ix->N;
+    // The search's own scan kernel in its fixed-threshold mode: every
+    // cluster is a probe slot, r^2 stays r2[q], no KNN set.
+    adsx::ScanArgs a;
+    if (!adsx::fill_uniform_scan(a, ix, nq, 1, ix->nlist, eps0, delta_d, 0))
+        return fail(ADSX_EINVAL, "too many queries in one call");
     a.qrot = qrot;
-    a.r2 = rr.dev;
-    a.nq = nq;
-    a.D = ix->D;
-    a.Dp = ix->Dp;
-    a.nblk = ix->Dp / adsx::BLK;
-    a.db = delta_d / adsx::BLK;
-    a.test_on = isinf(eps0) ? 0 : 1;
-    if (a.db >= a.nblk) a.test_on = 0;
-    a.eps0 = a.test_on ? eps0 : 0.f;
+    a.probes = nullptr;
+    a.out_ids = nullptr;
+    a.out_d2 = nullptr;
+    a.work_counter = counter;
+    a.r2fixed = rr.dev;
     a.decisions = dec.dev;
-    a.dims = dm.dev;
-    CK(adsx::launch_dco_fixed_r(a, s), "fixed-r scan");
+    a.dec_dims = dm.dev;
+    a.N = ix->N;
+    CK(sc.get(&ftab, (size_t)a.nblk + 1), "alloc test factors");
+    a.ftab = ftab;
+    CK(adsx::launch_test_factors(ftab, a.nblk, a.D, a.test_on ? eps0 : 0.f, s), "test factors");
+    CK(cudaMemsetAsync(counter, 0, sizeof(unsigned), s), "clear counter");
+    CK(adsx::launch_ads_scan(a, adsx::ads_scan_grid(a, ix->device), s), "fixed-r scan");
     CK(copy_back(dec, s), "copy back");
     CK(copy_back(dm, s), "copy back");
     return finish(s, dec.host || dm.host, "fixed-r");

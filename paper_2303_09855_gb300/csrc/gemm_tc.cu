@@ -15,8 +15,8 @@
 // FP32 accumulator in tensor memory and commits them to an mbarrier; after
 // the last step each warp reads its 32 accumulator rows with tcgen05.ld and
 // writes the epilogue.  The mbarrier wait is bounded: on time-out the kernel
-// sets the error word, waits (bounded) once more, frees its tensor memory and
-// returns.
+// sets the error word, waits (bounded by 1 s of device time) for the batch
+// already committed to arrive, frees its tensor memory and returns.
 #include "adsx_internal.cuh"
 
 namespace adsx {
@@ -31,6 +31,8 @@ constexpr int SMEM_BYTES = OPER_BYTES > STAGE_BYTES ? OPER_BYTES : STAGE_BYTES;
 constexpr uint32_t TMEM_COLS = 128;
 constexpr unsigned WAIT_LIMIT = 1u << 22;
 constexpr unsigned ERR_MMA_TIMEOUT = 8u;
+constexpr unsigned ERR_MMA_DRAIN = 32u;
+constexpr uint64_t DRAIN_NS = 1000000000ull;   // 1 s
 
 // Instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
 // (bits 7-9 = bits 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at
@@ -86,6 +88,26 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase)
         if (ok) return true;
     }
     return false;
+}
+
+// The same wait bounded by time (%globaltimer nanoseconds) instead of a
+// count: used to drain MMAs already committed after a timed-out wait.
+__device__ __forceinline__ bool mbar_wait_ns(uint32_t bar, uint32_t phase, uint64_t limit_ns)
+{
+    uint64_t t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (ok) return true;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > limit_ns) return false;
+    }
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc)
@@ -191,8 +213,15 @@ __global__ void __launch_bounds__(128, 1)
         ok = __syncthreads_and(ok);
     }
     if (!ok) {
+        // The MMAs of the last batch were committed to the barrier and will
+        // arrive on it: wait for that arrival (up to DRAIN_NS, far beyond the
+        // duration of one batch) so that tensor memory is not released under
+        // them.  Should even that wait give up (the device is not making
+        // progress), ERR_MMA_DRAIN records it; the allocation is released
+        // regardless, as a CTA must not exit holding tensor memory.
         if (tid == 0) atomicOr(err, ERR_MMA_TIMEOUT);
-        mbar_wait(bar, phase ^ 1u);            // bounded: let in-flight MMAs drain
+        const bool drained = mbar_wait_ns(bar, phase ^ 1u, DRAIN_NS);
+        if (!__syncthreads_and(drained) && tid == 0) atomicOr(err, ERR_MMA_DRAIN);
     } else {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // Each warp reads its 32 accumulator rows (lane = row) and stages the

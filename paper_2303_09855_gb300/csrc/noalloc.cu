@@ -38,7 +38,9 @@ int nerr(int code, const std::string &msg)
     return code;
 }
 
-bool is_device_ptr(const void *p)
+// Device (or managed) memory that lives on `device`: the kernels read and
+// write these buffers directly.
+bool is_device_ptr_on(const void *p, int device)
 {
     if (!p) return false;
     cudaPointerAttributes at;
@@ -46,7 +48,8 @@ bool is_device_ptr(const void *p)
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == device;
 }
 
 // Device address of the scratch array on the current device (looked up once).
@@ -97,39 +100,19 @@ extern "C" int adsx_search_noalloc(const adsx_index *index, const float *Qv, int
     if (K < 1 || K > ADSX_MAX_K) return nerr(ADSX_EINVAL, "K out of range");
     if (nprobe < 1 || nprobe > ix->nlist || nprobe > ADSX_MAX_NPROBE)
         return nerr(ADSX_EINVAL, "nprobe out of range");
+    if (delta_d == 0) delta_d = ix->tuned_delta_d;   // as adsx_search: the tuned step
     if (delta_d < 16 || delta_d % 16) return nerr(ADSX_EINVAL, "delta_d must be a positive multiple of 16");
     if (!(eps0 >= 0.f)) return nerr(ADSX_EINVAL, "eps0 must be >= 0");
     if (nq == 0) return ADSX_OK;
-    if (!is_device_ptr(Qv) || !is_device_ptr(ids) || !is_device_ptr(dists) ||
-        (dims_read && !is_device_ptr(dims_read)))
-        return nerr(ADSX_EINVAL, "adsx_search_noalloc takes device pointers only");
+    if (!is_device_ptr_on(Qv, ix->device) || !is_device_ptr_on(ids, ix->device) ||
+        !is_device_ptr_on(dists, ix->device) ||
+        (dims_read && !is_device_ptr_on(dims_read, ix->device)))
+        return nerr(ADSX_EINVAL, "adsx_search_noalloc takes device pointers of the index's GPU only");
 
     const int Dp = ix->Dp, nblk = Dp / adsx::BLK;
     adsx::ScanArgs a;
-    a.data = ix->data;
-    a.rows32 = ix->rows32;
-    a.norms = ix->norms;
-    a.storage = ix->storage;
-    a.ids = ix->ids;
-    a.off = ix->off;
-    a.nq = nq;
-    a.D = ix->D;
-    a.Dp = Dp;
-    a.nblk = nblk;
-    a.nprobe = nprobe;
-    a.K = K;
-    int Kp = 1;
-    while (Kp < K) Kp <<= 1;
-    a.C = 1;
-    while (a.C < std::max(2 * Kp, K + 32)) a.C <<= 1;
-    a.S = adsx::uniform_splits(nq, nprobe, K, adsx::scan_items_target(ix->device, ix->items_per_sm),
-                               ix->N / ix->nlist);
-    if (nq * (int64_t)a.S >= ((int64_t)1 << 31)) return nerr(ADSX_EINVAL, "too many queries");
-    a.n_items = (int32_t)(nq * a.S);
-    a.db = delta_d / adsx::BLK;
-    a.test_on = isinf(eps0) ? 0 : 1;
-    if (a.db >= nblk) a.test_on = 0;
-    if (!a.test_on) a.db = nblk;
+    if (!adsx::fill_uniform_scan(a, ix, nq, K, nprobe, eps0, delta_d, 0))
+        return nerr(ADSX_EINVAL, "too many queries");
 
     // Size check before touching the array.
     auto rup = [](size_t b) { return (std::max<size_t>(b, 1) + 255) & ~size_t(255); };
@@ -159,10 +142,6 @@ extern "C" int adsx_search_noalloc(const adsx_index *index, const float *Qv, int
     a.out_ids = ids;
     a.out_d2 = dists;
     a.out_dims = dims_read;
-    a.err = ix->err;
-    a.r2g = nullptr;
-    a.part_d = nullptr;
-    a.part_i = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
     // The array keeps the previous call's contents: clear what must start
     // from a known value.

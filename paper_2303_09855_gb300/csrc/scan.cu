@@ -1,7 +1,9 @@
 // scan.cu -- the IVF+ candidate scan: Algorithm 1 (ADSampling) as the DCO of
 // every member of a query's probed clusters (Sec. 4), against the query's
-// current K-th distance (Sec. 2.2.2), plus the fixed-threshold linear scan of
-// the verification protocol (Sec. 6.2.5).
+// current K-th distance (Sec. 2.2.2).  The same kernel, instantiated with a
+// fixed threshold per query and every cluster as a probe slot, is the linear
+// scan of the verification protocol (Sec. 6.2.5): its decisions come from
+// exactly the accumulation, test and recheck code of a search.
 //
 // ads_scan_kernel is persistent and warp-centric.  A work item is (query q,
 // split s): the probe slots s, s+S, s+2S, ... of q, or with more splits than
@@ -101,7 +103,7 @@ __device__ __forceinline__ float out_value(int metric, float key, bool has)
     return metric == ADSX_COSINE ? fmaf(-0.5f, key, 1.f) : -key;
 }
 
-template <typename T, bool IP>
+template <typename T, bool IP, bool FIXED>
 struct Warp {
     const ScanArgs *a;
     float *qv;
@@ -126,8 +128,8 @@ struct Warp {
 
 // Sorts the candidate buffer by (distance, id), keeps the first K and sets
 // r^2 to the K-th distance once K are held.
-template <typename T, bool IP>
-__device__ void compact(Warp<T, IP> &w)
+template <typename T, bool IP, bool FIXED>
+__device__ void compact(Warp<T, IP, FIXED> &w)
 {
     const int C = w.C, K = w.K;
     for (int k = w.count + w.lane; k < C; k += 32) {
@@ -165,11 +167,11 @@ __device__ void compact(Warp<T, IP> &w)
     __syncwarp();
 }
 
-template <typename T, bool IP>
-__device__ __forceinline__ float current_r2(const Warp<T, IP> &w)
+template <typename T, bool IP, bool FIXED>
+__device__ __forceinline__ float current_r2(const Warp<T, IP, FIXED> &w)
 {
     float r2 = w.r2;
-    if (w.S > 1) {
+    if (!FIXED && w.S > 1) {
         const unsigned g = *((volatile const unsigned *)(w.a->r2g + w.q));
         if (g != 0xffffffffu) r2 = fminf(r2, ord_to_key(g));
     }
@@ -179,8 +181,8 @@ __device__ __forceinline__ float current_r2(const Warp<T, IP> &w)
 // 16-bit storage: exact FP32 distance of every lane with `need`, recomputed
 // from the FP32 row copy, one candidate at a time by the whole warp (each lane
 // a 4-dim slice, then a butterfly sum whose result is the same on all lanes).
-template <typename T, bool IP>
-__device__ __forceinline__ float recheck_exact(const Warp<T, IP> &w, bool need, int pos, float S)
+template <typename T, bool IP, bool FIXED>
+__device__ __forceinline__ float recheck_exact(const Warp<T, IP, FIXED> &w, bool need, int pos, float S)
 {
     const ScanArgs &a = *w.a;
     unsigned mask = __ballot_sync(FULL, need);
@@ -206,9 +208,21 @@ __device__ __forceinline__ float recheck_exact(const Warp<T, IP> &w, bool need, 
     return S;
 }
 
+// Fixed-threshold mode: the decision of candidate `pos` (CSR row) for the
+// item's query, by original id.
+template <typename T, bool IP, bool FIXED>
+__device__ __forceinline__ void record_decision(const Warp<T, IP, FIXED> &w, int pos, int dec,
+                                                int dims)
+{
+    const ScanArgs &a = *w.a;
+    const int64_t o = w.q * a.N + a.ids[pos];
+    a.decisions[o] = (uint8_t)dec;
+    if (a.dec_dims) a.dec_dims[o] = dims;
+}
+
 // Appends the lanes with `surv` to the pending ring (lane order).
-template <typename T, bool IP>
-__device__ __forceinline__ void enqueue(Warp<T, IP> &w, bool surv, float S, int blk, int pos,
+template <typename T, bool IP, bool FIXED>
+__device__ __forceinline__ void enqueue(Warp<T, IP, FIXED> &w, bool surv, float S, int blk, int pos,
                                         long long off, int st)
 {
     const unsigned sm = __ballot_sync(FULL, surv);
@@ -228,8 +242,8 @@ __device__ __forceinline__ void enqueue(Warp<T, IP> &w, bool surv, float S, int 
 // `pos` is the candidate's CSR row, `off` the element offset of its block
 // `blk` and `st` its block stride.  Returns whether the candidate continues;
 // with `push` it is also queued.
-template <typename T, bool IP>
-__device__ __forceinline__ bool after_step(Warp<T, IP> &w, bool valid, float S, int blk, int pos,
+template <typename T, bool IP, bool FIXED>
+__device__ __forceinline__ bool after_step(Warp<T, IP, FIXED> &w, bool valid, float S, int blk, int pos,
                                            long long off, int st, float r2, bool push)
 {
     const ScanArgs &a = *w.a;
@@ -248,6 +262,7 @@ __device__ __forceinline__ bool after_step(Warp<T, IP> &w, bool valid, float S, 
         if (a.test_on && S > thr * w.ftab[blk]) {
             const int d = blk * BLK;
             w.dims += (unsigned)(d < a.D ? d : a.D);
+            if constexpr (FIXED) record_decision(w, pos, 0, d < a.D ? d : a.D);
         } else {
             surv = true;
         }
@@ -270,6 +285,11 @@ __device__ __forceinline__ bool after_step(Warp<T, IP> &w, bool valid, float S, 
         }
         S = recheck_exact(w, need, pos, S);
         cand = need;
+    }
+    if constexpr (FIXED) {
+        // positive iff the (exact FP32) distance at d = D is <= r^2
+        if (fin) record_decision(w, pos, (cand && S <= r2) ? 1 : 2, a.D);
+        return surv;
     }
     // Case 3 positives into the candidate buffer; the key is the squared
     // distance, or -<o,q> = -||o|| ||q|| (1 - S/2) for inner products.
@@ -457,8 +477,8 @@ __device__ __forceinline__ float tile_step(const T *cb, int64_t stride, int m0, 
 
 // Advances the first nb (<= 32) pending candidates by one delta_d step each,
 // NL lanes per candidate, then tests them (after_step) one per lane.
-template <typename T, bool IP>
-__device__ __forceinline__ void process_pending(Warp<T, IP> &w, int nb)
+template <typename T, bool IP, bool FIXED>
+__device__ __forceinline__ void process_pending(Warp<T, IP, FIXED> &w, int nb)
 {
     constexpr int NL = Split<T>::NL, NG = 32 / NL, PW = BLK / NL;
     typedef typename Split<T>::V V;
@@ -542,7 +562,7 @@ __device__ __forceinline__ void process_pending(Warp<T, IP> &w, int nb)
 template <typename T> struct MinBlocks { static constexpr int value = ADSX_SCAN_MINBLOCKS_H; };
 template <> struct MinBlocks<float> { static constexpr int value = ADSX_SCAN_MINBLOCKS; };
 
-template <typename T, bool IP>
+template <typename T, bool IP, bool FIXED>
 __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(ScanArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -552,7 +572,7 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
     __shared__ float s_ftab[256];
     for (int b = threadIdx.x; b <= a.nblk && b < 256; b += THREADS) s_ftab[b] = a.ftab[b];
     __syncthreads();
-    Warp<T, IP> w;
+    Warp<T, IP, FIXED> w;
     w.a = &a;
     w.ftab = s_ftab;
     w.qv = base + wc.qv;
@@ -599,7 +619,7 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
         for (int i = lane; i < a.Dp; i += 32) w.qv[i] = a.qrot[q * a.Dp + i];
         w.head = w.cnt = 0;
         w.count = 0;
-        w.r2 = INFINITY;
+        w.r2 = FIXED ? a.r2fixed[q] : INFINITY;
         w.qn = IP ? a.qnorm[q] : 1.f;
         w.dims = 0u;
         __syncwarp();
@@ -612,7 +632,7 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
         // (Two inlined copies: the common one has constant tile steps.)
         const int pstride = a.probe_stride ? a.probe_stride : a.nprobe;
         auto scan_slot = [&](int p, int j0, int js) {
-            const int c = a.probes[q * pstride + p];
+            const int c = FIXED ? p : a.probes[q * pstride + p];
             const int o = (int)a.off[c];
             const int n = (int)(a.off[c + 1] - o);
             const T *cb = static_cast<const T *>(a.data) + (int64_t)o * a.Dp;
@@ -651,6 +671,7 @@ __global__ void __launch_bounds__(THREADS, MinBlocks<T>::value) ads_scan_kernel(
             scan_slot(p0, s / nprobe, (S - 1 - p0) / nprobe + 1);
         }
         while (w.cnt > 0) process_pending(w, w.cnt < 32 ? w.cnt : 32);
+        if constexpr (FIXED) continue;       // decisions only, no KNN set
         compact(w);
 
         unsigned long long wd = w.dims;
@@ -752,88 +773,6 @@ __global__ void test_factor_kernel(float *ftab, int nblk, int D, float eps0, int
         ftab[b] = (b == 0) ? 0.f : (pd ? 1.f : test_factor(b, D, eps0));
 }
 
-// Verification protocol (Sec. 6.2.5): every (query, indexed vector) pair,
-// fixed threshold r2[q].  One warp per 32-member tile of one cluster, one
-// lane per member; the same block accumulation and test as the search scan
-// (and, for 16-bit storage, the exact FP32 distance at d = D).
-template <typename T>
-__global__ void __launch_bounds__(256) dco_fixed_r_kernel(FixedRArgs a)
-{
-    extern __shared__ __align__(16) unsigned char smraw[];
-    float *qv = reinterpret_cast<float *>(smraw);
-    float *ftab = qv + a.Dp;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t q = blockIdx.y;
-    for (int i = tid; i < a.Dp; i += 256) qv[i] = a.qrot[q * a.Dp + i];
-    for (int b = tid; b <= a.nblk; b += 256)
-        ftab[b] = (b == 0) ? 0.f : test_factor(b, a.D, a.eps0);
-    __syncthreads();
-    const int t = blockIdx.x * 8 + warp;
-    if (t >= a.total_tiles) return;      // whole warp
-    int lo = 0, hi = a.nlist - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.tile_off[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    const int c = lo;
-    const int64_t o = a.off[c];
-    const int64_t n = a.off[c + 1] - o;
-    const int64_t m = (int64_t)(t - a.tile_off[c]) * 32 + lane;
-    const bool valid = m < n;
-    const float r2 = a.r2[q];
-    const T *base = static_cast<const T *>(a.data) + o * a.Dp;
-    float S = 0.f;
-    int blk = 0;
-    uint8_t dec = 0;
-    int dims = 0;
-    bool at_D = false;
-    if (valid) {
-        for (;;) {
-            int e = blk + a.db;
-            if (e > a.nblk) e = a.nblk;
-            S = accum_range(base, n, m, blk, e, qv, S);
-            blk = e;
-            if (blk >= a.nblk) {
-                at_D = true;
-                dims = a.D;
-                break;
-            }
-            if (a.test_on && S > r2 * ftab[blk]) {
-                dec = 0;
-                dims = blk * BLK < a.D ? blk * BLK : a.D;
-                break;
-            }
-        }
-    }
-    if constexpr (Roundoff<T>::u > 0.f) {
-        unsigned mask = __ballot_sync(0xffffffffu, at_D);
-        while (mask) {
-            const int src = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const int64_t p = o + __shfl_sync(0xffffffffu, (int)m, src);
-            const float *row = a.rows32 + p * a.Dp;
-            float part = 0.f;
-            for (int j = lane * 4; j < a.Dp; j += 128) {
-                const float4 x = __ldg(reinterpret_cast<const float4 *>(row + j));
-                const float4 qq = *reinterpret_cast<const float4 *>(qv + j);
-                float d;
-                d = x.x - qq.x; part = fmaf(d, d, part);
-                d = x.y - qq.y; part = fmaf(d, d, part);
-                d = x.z - qq.z; part = fmaf(d, d, part);
-                d = x.w - qq.w; part = fmaf(d, d, part);
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-            if (lane == src) S = part;
-        }
-    }
-    if (!valid) return;
-    if (at_D) dec = (S <= r2) ? 1 : 2;
-    const int64_t id = a.ids[o + m];
-    a.decisions[q * a.N + id] = dec;
-    if (a.dims) a.dims[q * a.N + id] = dims;
-}
-
 }  // namespace
 
 size_t scan_smem_bytes(const ScanArgs &a)
@@ -848,14 +787,20 @@ int scan_items_target(int device, int items_per_sm)
     return nsm * items_per_sm;   // default 48: about one item per resident warp slot
 }
 
+// The instantiation a launch runs: storage type, inner-product thresholds,
+// fixed-threshold mode (L2 / cosine only).
+typedef void (*ScanKernel)(ScanArgs);
 template <typename T>
-static int occupancy(size_t smem, bool ip)
+static ScanKernel scan_kernel_for(const ScanArgs &a)
 {
-    int per = 0;
-    auto k = ip ? ads_scan_kernel<T, true> : ads_scan_kernel<T, false>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, THREADS, smem);
-    return per;
+    if (a.decisions) return ads_scan_kernel<T, false, true>;
+    return a.metric == ADSX_IP ? ads_scan_kernel<T, true, false> : ads_scan_kernel<T, false, false>;
+}
+static ScanKernel scan_kernel_for_args(const ScanArgs &a)
+{
+    if (a.storage == ADSX_F32) return scan_kernel_for<float>(a);
+    if (a.storage == ADSX_BF16) return scan_kernel_for<__nv_bfloat16>(a);
+    return scan_kernel_for<__half>(a);
 }
 
 int ads_scan_grid(const ScanArgs &a, int device)
@@ -863,9 +808,9 @@ int ads_scan_grid(const ScanArgs &a, int device)
     int nsm = 0, per = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
     size_t smem = scan_smem_bytes(a);
-    const bool ip = a.metric == ADSX_IP;
-    per = a.storage == ADSX_F32 ? occupancy<float>(smem, ip)
-        : a.storage == ADSX_BF16 ? occupancy<__nv_bfloat16>(smem, ip) : occupancy<__half>(smem, ip);
+    const ScanKernel k = scan_kernel_for_args(a);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, THREADS, smem);
     if (per < 1) per = 1;
     int64_t g = (int64_t)nsm * per;
     const int64_t need = ((int64_t)a.n_items + WARPS - 1) / WARPS;
@@ -883,12 +828,7 @@ cudaError_t launch_ads_scan(const ScanArgs &a, int grid, cudaStream_t s)
 {
     if (a.n_items <= 0) return cudaSuccess;
     size_t smem = scan_smem_bytes(a);
-    const bool ip = a.metric == ADSX_IP;
-    void (*k)(ScanArgs);
-    if (a.storage == ADSX_F32) k = ip ? ads_scan_kernel<float, true> : ads_scan_kernel<float, false>;
-    else if (a.storage == ADSX_BF16)
-        k = ip ? ads_scan_kernel<__nv_bfloat16, true> : ads_scan_kernel<__nv_bfloat16, false>;
-    else k = ip ? ads_scan_kernel<__half, true> : ads_scan_kernel<__half, false>;
+    const ScanKernel k = scan_kernel_for_args(a);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, THREADS, smem, s>>>(a);
@@ -909,21 +849,6 @@ cudaError_t launch_finalize_topk(const ScanArgs &a, cudaStream_t s)
     if (e != cudaSuccess) return e;
     int64_t grid = a.nq < 152 * 8 ? a.nq : 152 * 8;
     finalize_topk_kernel<<<(unsigned)grid, 256, smem, s>>>(b);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_dco_fixed_r(const FixedRArgs &a, cudaStream_t s)
-{
-    if (a.nq <= 0 || a.total_tiles <= 0) return cudaSuccess;
-    size_t smem = sizeof(float) * (a.Dp + a.nblk + 1);
-    if (a.nq > 65535) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)((a.total_tiles + 7) / 8), (unsigned)a.nq);
-    if (a.storage == ADSX_F32)
-        dco_fixed_r_kernel<float><<<grid, 256, smem, s>>>(a);
-    else if (a.storage == ADSX_BF16)
-        dco_fixed_r_kernel<__nv_bfloat16><<<grid, 256, smem, s>>>(a);
-    else
-        dco_fixed_r_kernel<__half><<<grid, 256, smem, s>>>(a);
     return cudaGetLastError();
 }
 
