@@ -61,6 +61,13 @@ typedef enum { ADSX_F32 = 0, ADSX_BF16 = 1, ADSX_F16 = 2 } adsx_dtype;
 /* Similarity of an index (adsx_build_index_metric; Sec. 8, extension (1)). */
 typedef enum { ADSX_L2 = 0, ADSX_IP = 1, ADSX_COSINE = 2 } adsx_metric;
 
+/* Scan schedules (adsx_set_scan_schedule). */
+typedef enum {
+    ADSX_SCHED_AUTO = 0,     /* cluster-major for large batches, else query-major */
+    ADSX_SCHED_QUERY = 1,    /* one warp per (query, split): every query apart    */
+    ADSX_SCHED_CLUSTER = 2   /* one warp per (cluster, query group), in rounds    */
+} adsx_schedule;
+
 /* Limits of the current kernels (checked; ADSX_EINVAL beyond them). */
 #define ADSX_MAX_D 4080       /* dimensions (padded to a multiple of 16)   */
 #define ADSX_MAX_K 1024       /* neighbours per query                        */
@@ -279,6 +286,35 @@ int adsx_dco_fixed_r(const adsx_index *index, const float *Qv, int64_t nq,
  * ADSX_OK, ADSX_EINVAL (argument check), ADSX_ETIMEOUT or ADSX_ECUDA.
  */
 int adsx_stream_status(const adsx_index *index, void *stream);
+
+/*
+ * adsx_set_scan_schedule -- how adsx_search and adsx_search_pdscan (and, when
+ * forced to ADSX_SCHED_CLUSTER, adsx_dco_fixed_r) organise the candidate
+ * scan on the GPU.  Results follow the same method either way; only the
+ * order of work, and with it which r each DCO sees, differs.
+ *   ADSX_SCHED_QUERY    a work item is one query (or a split of one): its
+ *                       warp visits the probed clusters in order and
+ *                       tightens r after every KNN-set update (Sec. 2.2.2).
+ *   ADSX_SCHED_CLUSTER  a work item is one cluster and up to
+ *                       queries_per_item of the queries probing it: each
+ *                       Delta_d step of a 32-member tile is read once and
+ *                       tested against all of them.  The probe ranks are
+ *                       covered in rounds -- the nearest 2 clusters of each
+ *                       query query-major, then rank ranges growing 3x --
+ *                       each round testing against the K-th distance of the
+ *                       rounds before it (a valid r: the K-th of a subset of
+ *                       exact candidate distances), so results do not depend
+ *                       on scheduling.  Needs delta_d <= 64 (or the test
+ *                       off) and an L2 or cosine index; other searches run
+ *                       query-major.
+ *   ADSX_SCHED_AUTO     cluster-major when it applies to a large batch
+ *                       (nq >= 2048, nprobe >= 8, nq * nprobe >= 8 nlist: each
+ *                       cluster probed 8 times on average), else query-major.
+ *                       The initial setting.
+ *   queries_per_item    1..64, or 0 to keep the current value (16 initially).
+ * Not thread-safe with other calls on the same index.
+ */
+int adsx_set_scan_schedule(adsx_index *index, int32_t schedule, int32_t queries_per_item);
 
 /*
  * adsx_autotune -- picks the step delta_d (Sec. 6.2.4: 16..64 give the best

@@ -79,6 +79,7 @@ def load():
     lib.adsx_server_reset_stats.argtypes = [V]
     lib.adsx_server_destroy.argtypes = [V]
     lib.adsx_set_stage_timing.argtypes = [V, i32]
+    lib.adsx_set_scan_schedule.argtypes = [V, i32, i32]
     lib.adsx_stage_ms.argtypes = [V, V]
     lib.adsx_last_error.restype = ctypes.c_char_p
     for fn in ("adsx_build_index", "adsx_build_index_metric", "adsx_index_metric",
@@ -87,6 +88,7 @@ def load():
                "adsx_free_index", "adsx_index_info", "adsx_search",
                "adsx_probe", "adsx_rotate", "adsx_dco_fixed_r", "adsx_stream_status",
                "adsx_set_stage_timing", "adsx_stage_ms", "adsx_search_noalloc",
+               "adsx_set_scan_schedule",
                "adsx_search_batched", "adsx_search_pdscan", "adsx_autotune",
                "adsx_server_create",
                "adsx_server_submit", "adsx_server_submit_many", "adsx_server_wait",
@@ -188,6 +190,9 @@ class Index:
 
     def dco_fixed_r(self, Q, r2, eps0, delta_d, stream=None):
         return dco_fixed_r(self, Q, r2, eps0, delta_d, stream)
+
+    def set_scan_schedule(self, schedule, queries_per_item=0):
+        return set_scan_schedule(self, schedule, queries_per_item)
 
 
 def build_index(X, P, centroids, assign, storage=F32, stream=None, metric=L2) -> Index:
@@ -468,6 +473,16 @@ def autotune(index: Index, Q, K: int, nprobe: int, eps0: float = 2.1, stream=Non
                                 ctypes.byref(dd), ctypes.byref(ip), ctypes.byref(ms),
                                 _stream_of(Q, stream)))
     return dd.value, ip.value, ms.value
+
+
+SCHED_AUTO, SCHED_QUERY, SCHED_CLUSTER = 0, 1, 2
+
+
+def set_scan_schedule(index: Index, schedule: int, queries_per_item: int = 0):
+    """adsx_set_scan_schedule: SCHED_AUTO, SCHED_QUERY (one warp per query)
+    or SCHED_CLUSTER (one warp per cluster and query group, in rounds);
+    queries_per_item 1..64 (0 keeps the current value)."""
+    _check(load().adsx_set_scan_schedule(index.handle, int(schedule), int(queries_per_item)))
 
 
 def set_stage_timing(index: Index, enable: bool = True):

@@ -25,6 +25,11 @@
 namespace adsx {
 
 constexpr int BLK = 16;                 // dims per layout block
+// With the test off (eps0 = +inf, delta_d >= D: FDScanning) partial sums are
+// still accumulated in steps of this many blocks (32 dims), so that every
+// scan schedule and every way of turning the test off sums a candidate's
+// distance in the same order.
+constexpr int FD_STEP_BLOCKS = 2;
 constexpr unsigned ERR_LOCK_TIMEOUT = 1u;  // device error word bits
 
 struct Index {
@@ -51,6 +56,13 @@ struct Index {
     int64_t bytes = 0;
     int32_t tuned_delta_d = 32;   // used when a search passes delta_d = 0
     int32_t items_per_sm = 48;    // work items per SM targeted when splitting queries
+    // scan schedule (adsx_set_scan_schedule / adsx_autotune): ADSX_SCHED_AUTO,
+    // _QUERY or _CLUSTER; queries per cluster-major work item; probe ranks of
+    // the query-major round 0 and the growth factor of later rounds' ranges
+    int32_t sched = ADSX_SCHED_AUTO;
+    int32_t cm_G = 16;
+    int32_t cm_r0 = 2;
+    int32_t cm_growth = 3;
     // stage timing (adsx_set_stage_timing): events between search stages
     bool timing = false;
     bool timed_once = false;
@@ -456,7 +468,7 @@ inline bool fill_uniform_scan(ScanArgs &a, const Index *ix, int64_t nq, int K, i
     a.db = delta_d / BLK;
     a.test_on = (isinf(eps0) && !pd) ? 0 : 1;
     if (a.db >= a.nblk) a.test_on = 0;
-    if (!a.test_on) a.db = a.nblk;   // FDScanning: the whole vector in one step
+    if (!a.test_on) a.db = FD_STEP_BLOCKS < a.nblk ? FD_STEP_BLOCKS : a.nblk;   // FDScanning
     a.out_dims = nullptr;
     a.part_d = nullptr;
     a.part_i = nullptr;
@@ -477,6 +489,64 @@ constexpr unsigned ERR_OUT_RANGE = 4u;    // an output offset + K exceeded the o
 constexpr unsigned ERR_ZERO_ROW = 16u;    // a zero-norm row where a unit row is required
 constexpr int BATCH_MAX_SPLITS = 16;
 int ads_scan_grid(const ScanArgs &a, int device);
+
+// ---- cluster-major schedule (cmscan.cu)
+constexpr int CM_MAX_DB = 4;     // blocks per step (delta_d <= 64)
+constexpr int CM_MAX_G = 64;     // queries per work item
+struct CmArgs {
+    const void *data;
+    const float *rows32;
+    const float *norms;
+    int32_t storage;
+    const int32_t *ids;
+    const int64_t *off;
+    const float *qrot;
+    int32_t D, Dp, nblk, db, test_on;
+    const float *ftab;
+    const float *r2;            // per query: the round's r^2 (+inf: none yet)
+    const int32_t *coff;        // nlist + 1 offsets into qlist
+    const int32_t *qlist;       // queries of each cluster in this round
+    const int2 *items;          // (cluster, first query slot of the item)
+    const int32_t *n_items;     // device count of items
+    int32_t items_cap;          // upper bound of *n_items (grid sizing)
+    int32_t G;                  // queries per item
+    unsigned *work_counter;
+    float *app_d;               // nq x cap appended (distance, id)
+    int32_t *app_i;
+    unsigned *app_n;            // nq appended counts
+    int32_t cap;
+    int64_t *out_dims;          // may be NULL: dims sampled, added per query
+    // fixed-threshold mode (decisions != NULL), as ScanArgs
+    const float *r2fixed = nullptr;
+    uint8_t *decisions = nullptr;
+    int32_t *dec_dims = nullptr;
+    int64_t N = 0;
+};
+struct CmMergeArgs {
+    int64_t nq;
+    int32_t K, cap, T;
+    int64_t *ids;               // nq x K running top-K ids (-1 padded)
+    float *d2;                  // nq x K keys (values after the final pass)
+    const float *app_d;
+    const int32_t *app_i;
+    unsigned *app_n;            // may be NULL (nothing appended)
+    float *r2;
+    int32_t *ovf;
+    int32_t metric;
+    int32_t final_pass;
+};
+struct CmPlan {
+    int32_t *cnt, *coff, *ioff, *cur, *qlist, *n_items;
+    int2 *items;
+};
+size_t cm_smem_bytes(int G);
+cudaError_t launch_cm_plan(const int32_t *probes, int64_t nq, int pstride, int r0, int r1, int nlist,
+                           int G, CmPlan &pl, cudaStream_t s);
+cudaError_t launch_cm_scan(const CmArgs &a, int device, cudaStream_t s);
+cudaError_t launch_cm_merge(const CmMergeArgs &m, cudaStream_t s);
+cudaError_t launch_cm_overflow_items(const int32_t *ovf, int64_t nq, int2 *items, int32_t *n_items,
+                                     cudaStream_t s);
+cudaError_t launch_cm_all_clusters(int32_t *probes, int64_t nq, int nlist, cudaStream_t s);
 
 
 

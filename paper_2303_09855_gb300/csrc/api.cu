@@ -554,6 +554,192 @@ int adsx_probe(const adsx_index *index, const float *Qv, int64_t nq, int32_t npr
 
 }  // extern "C"
 
+// ---------------------------------------------------------------- scan schedules
+// The query-major scan of `a` (scan.cu), with the shared bounds, partial
+// lists and their merge when queries are split (S > 1).
+static cudaError_t qm_scan(const Index *ix, adsx::ScanArgs a, Scratch &sc)
+{
+    cudaStream_t s = sc.s;
+    unsigned *counter = nullptr;
+    cudaError_t e = sc.get(&counter, 1);
+    if (e != cudaSuccess) return e;
+    a.work_counter = counter;
+    if (a.S > 1) {
+        if ((e = sc.get(&a.part_d, (size_t)a.n_items * a.K)) != cudaSuccess) return e;
+        if ((e = sc.get(&a.part_i, (size_t)a.n_items * a.K)) != cudaSuccess) return e;
+        if ((e = sc.get(&a.r2g, (size_t)a.nq)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(a.r2g, 0xff, sizeof(unsigned) * a.nq, s)) != cudaSuccess) return e;
+        if (a.out_dims &&
+            (e = cudaMemsetAsync(a.out_dims, 0, sizeof(int64_t) * a.nq, s)) != cudaSuccess)
+            return e;
+    }
+    if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+    if ((e = adsx::launch_ads_scan(a, adsx::ads_scan_grid(a, ix->device), s)) != cudaSuccess)
+        return e;
+    return adsx::launch_finalize_topk(a, s);
+}
+
+// Whether the uniform search set up in `a` runs cluster-major (cmscan.cu).
+static bool use_cluster_major(const Index *ix, const adsx::ScanArgs &a)
+{
+    if (ix->sched == ADSX_SCHED_QUERY) return false;
+    if (a.metric == ADSX_IP || a.db > adsx::CM_MAX_DB) return false;
+    if (a.nprobe <= ix->cm_r0) return false;           // round 0 covers every probe
+    if (ix->sched == ADSX_SCHED_CLUSTER) return true;
+    // a large batch whose queries probe each cluster 8 times on average
+    return a.nq >= 2048 && a.nprobe >= 8 && a.nq * (int64_t)a.nprobe >= 8 * (int64_t)ix->nlist;
+}
+
+// The probe-rank ranges of the cluster-major rounds after round 0: each
+// `growth` times as far as where it starts; a short tail joins the last.
+static std::vector<std::pair<int, int>> cm_rounds(int r0, int nprobe, int growth)
+{
+    std::vector<std::pair<int, int>> r;
+    int lo = r0;
+    while (lo < nprobe) {
+        int hi = std::max(lo + 1, lo * growth);
+        if (hi >= nprobe || 2 * (nprobe - hi) < hi - lo) hi = nprobe;
+        r.push_back({lo, hi});
+        lo = hi;
+    }
+    return r;
+}
+
+// The fields of a cluster-major pass taken from a query-major setup.
+static adsx::CmArgs cm_args_from(const adsx::ScanArgs &a, int G)
+{
+    adsx::CmArgs c;
+    c.data = a.data;
+    c.rows32 = a.rows32;
+    c.norms = a.norms;
+    c.storage = a.storage;
+    c.ids = a.ids;
+    c.off = a.off;
+    c.qrot = a.qrot;
+    c.D = a.D;
+    c.Dp = a.Dp;
+    c.nblk = a.nblk;
+    c.db = a.db;
+    c.test_on = a.test_on;
+    c.ftab = a.ftab;
+    c.r2 = nullptr;
+    c.G = G;
+    c.app_d = nullptr;
+    c.app_i = nullptr;
+    c.app_n = nullptr;
+    c.cap = 0;
+    c.out_dims = a.out_dims;
+    return c;
+}
+
+static cudaError_t cm_plan_buffers(const Index *ix, int64_t nq, int width, int G, Scratch &sc,
+                                   adsx::CmPlan &pl, int64_t *items_cap)
+{
+    cudaError_t e;
+    const size_t nl = (size_t)ix->nlist;
+    *items_cap = nq * (int64_t)width / G + ix->nlist + 1;
+    if ((e = sc.get(&pl.cnt, nl)) != cudaSuccess) return e;
+    if ((e = sc.get(&pl.coff, nl + 1)) != cudaSuccess) return e;
+    if ((e = sc.get(&pl.ioff, nl)) != cudaSuccess) return e;
+    if ((e = sc.get(&pl.cur, nl)) != cudaSuccess) return e;
+    if ((e = sc.get(&pl.n_items, 1)) != cudaSuccess) return e;
+    if ((e = sc.get(&pl.qlist, (size_t)(nq * (int64_t)width))) != cudaSuccess) return e;
+    return sc.get(&pl.items, (size_t)*items_cap);
+}
+
+// The cluster-major schedule of a uniform search (ADSX_SCHED_CLUSTER): round
+// 0 query-major over each query's nearest cm_r0 clusters, then the later
+// probe ranks in rounds, each scanned cluster-major against the K-th
+// distance of the rounds before it and merged into the query's top-K; a
+// query whose round list overflowed is searched again query-major.  `a` is
+// the query-major setup of the whole search.
+static cudaError_t cm_scan(const Index *ix, const adsx::ScanArgs &a, Scratch &sc)
+{
+    cudaStream_t s = sc.s;
+    cudaError_t e;
+    const int64_t nq = a.nq;
+    const int K = a.K, nprobe = a.nprobe, G = ix->cm_G;
+    const int r0 = std::min(ix->cm_r0, nprobe);
+    adsx::ScanArgs a0 = a;
+    a0.metric = ADSX_L2;                 // keys (squared distances) until the last merge
+    a0.nprobe = r0;
+    a0.probe_stride = nprobe;
+    a0.S = adsx::uniform_splits(nq, r0, K, adsx::scan_items_target(ix->device, ix->items_per_sm),
+                                ix->N / ix->nlist);
+    a0.n_items = (int32_t)(nq * a0.S);
+    if ((e = qm_scan(ix, a0, sc)) != cudaSuccess) return e;
+
+    const int cap = std::max(4 * K, 512);
+    float *r2 = nullptr, *app_d = nullptr;
+    int32_t *app_i = nullptr, *ovf = nullptr;
+    unsigned *app_n = nullptr, *counter = nullptr;
+    if ((e = sc.get(&r2, (size_t)nq)) != cudaSuccess) return e;
+    if ((e = sc.get(&app_n, (size_t)nq)) != cudaSuccess) return e;
+    if ((e = sc.get(&ovf, (size_t)nq)) != cudaSuccess) return e;
+    if ((e = sc.get(&app_d, (size_t)nq * cap)) != cudaSuccess) return e;
+    if ((e = sc.get(&app_i, (size_t)nq * cap)) != cudaSuccess) return e;
+    if ((e = sc.get(&counter, 1)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(app_n, 0, sizeof(unsigned) * nq, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ovf, 0, sizeof(int32_t) * nq, s)) != cudaSuccess) return e;
+    adsx::CmMergeArgs m;
+    m.nq = nq;
+    m.K = K;
+    m.cap = cap;
+    m.T = 0;
+    m.ids = a.out_ids;
+    m.d2 = a.out_d2;
+    m.app_d = app_d;
+    m.app_i = app_i;
+    m.app_n = app_n;
+    m.r2 = r2;
+    m.ovf = ovf;
+    m.metric = a.metric;
+    m.final_pass = 0;
+    if ((e = adsx::launch_cm_merge(m, s)) != cudaSuccess) return e;   // r from round 0
+
+    const auto rounds = cm_rounds(r0, nprobe, ix->cm_growth);
+    int width = 1;
+    for (const auto &r : rounds) width = std::max(width, r.second - r.first);
+    adsx::CmPlan pl;
+    int64_t items_cap = 0;
+    if ((e = cm_plan_buffers(ix, nq, width, G, sc, pl, &items_cap)) != cudaSuccess) return e;
+    adsx::CmArgs c = cm_args_from(a, G);
+    c.r2 = r2;
+    c.coff = pl.coff;
+    c.qlist = pl.qlist;
+    c.items = pl.items;
+    c.n_items = pl.n_items;
+    c.items_cap = (int32_t)items_cap;
+    c.work_counter = counter;
+    c.app_d = app_d;
+    c.app_i = app_i;
+    c.app_n = app_n;
+    c.cap = cap;
+    for (size_t i = 0; i < rounds.size(); ++i) {
+        if ((e = adsx::launch_cm_plan(a.probes, nq, nprobe, rounds[i].first, rounds[i].second,
+                                      ix->nlist, G, pl, s)) != cudaSuccess)
+            return e;
+        if ((e = adsx::launch_cm_scan(c, ix->device, s)) != cudaSuccess) return e;
+        m.final_pass = i + 1 == rounds.size();
+        if ((e = adsx::launch_cm_merge(m, s)) != cudaSuccess) return e;
+    }
+    // queries whose list overflowed: the whole search again, query-major
+    int2 *fitems = nullptr;
+    int32_t *fn = nullptr;
+    if ((e = sc.get(&fitems, (size_t)nq)) != cudaSuccess) return e;
+    if ((e = sc.get(&fn, 1)) != cudaSuccess) return e;
+    if ((e = adsx::launch_cm_overflow_items(ovf, nq, fitems, fn, s)) != cudaSuccess) return e;
+    adsx::ScanArgs af = a;
+    af.items = fitems;
+    af.n_items_dev = fn;
+    af.n_items = (int32_t)nq;
+    af.S = 1;
+    af.probe_stride = nprobe;
+    af.work_counter = counter;
+    if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+    return adsx::launch_ads_scan(af, adsx::ads_scan_grid(af, ix->device), s);
+}
+
 static int search_impl(const adsx_index *index, const float *Qv, int64_t nq, int32_t K,
                        int32_t nprobe, float eps0, int32_t delta_d, int64_t *ids, float *dists,
                        int64_t *dims_read, void *stream, int pd)
@@ -574,14 +760,12 @@ static int search_impl(const adsx_index *index, const float *Qv, int64_t nq, int
     Buf<int64_t> oi, odims;
     float *qrot = nullptr;
     int32_t *probes = nullptr;
-    unsigned *counter = nullptr;
     CK(stage_in(sc, Qv, (size_t)nq * ix->D, q), "stage queries");
     CK(stage_out(sc, ids, (size_t)nq * K, oi), "stage ids");
     CK(stage_out(sc, dists, (size_t)nq * K, od), "stage dists");
     CK(stage_out(sc, dims_read, (size_t)nq, odims), "stage dims");
     CK(sc.get(&qrot, (size_t)nq * ix->Dp), "alloc q'");
     CK(sc.get(&probes, (size_t)nq * nprobe), "alloc probes");
-    CK(sc.get(&counter, 1), "alloc counter");
     CK(mark(ix, 0, s), "event");
     CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
     CK(mark(ix, 1, s), "event");
@@ -600,22 +784,13 @@ static int search_impl(const adsx_index *index, const float *Qv, int64_t nq, int
     a.out_ids = oi.dev;
     a.out_d2 = od.dev;
     a.out_dims = odims.dev;
-    a.work_counter = counter;
     float *ftab = nullptr;
     CK(sc.get(&ftab, (size_t)a.nblk + 1), "alloc test factors");
     a.ftab = ftab;
     CK(adsx::launch_test_factors(ftab, a.nblk, a.D, (a.test_on && !pd) ? eps0 : 0.f, s, pd),
        "test factors");
-    if (a.S > 1) {
-        CK(sc.get(&a.part_d, (size_t)a.n_items * K), "alloc partial lists");
-        CK(sc.get(&a.part_i, (size_t)a.n_items * K), "alloc partial lists");
-        CK(sc.get(&a.r2g, (size_t)nq), "alloc r2 bounds");
-        CK(cudaMemsetAsync(a.r2g, 0xff, sizeof(unsigned) * nq, s), "clear r2 bounds");
-        if (a.out_dims) CK(cudaMemsetAsync(a.out_dims, 0, sizeof(int64_t) * nq, s), "clear dims");
-    }
-    CK(cudaMemsetAsync(counter, 0, sizeof(unsigned), s), "clear counter");
-    CK(adsx::launch_ads_scan(a, adsx::ads_scan_grid(a, ix->device), s), "scan");
-    CK(adsx::launch_finalize_topk(a, s), "finalize");
+    if (use_cluster_major(ix, a)) CK(cm_scan(ix, a, sc), "cluster-major scan");
+    else CK(qm_scan(ix, a, sc), "scan");
     CK(mark(ix, 4, s), "event");
     if (ix->timing) const_cast<Index *>(ix)->timed_once = true;
     CK(copy_back(oi, s), "copy back");
@@ -756,7 +931,7 @@ int adsx_search_batched(const adsx_index *index, const float *Qv, int64_t nq, co
     a.db = delta_d / adsx::BLK;
     a.test_on = isinf(eps0) ? 0 : 1;
     if (a.db >= a.nblk) a.test_on = 0;
-    if (!a.test_on) a.db = a.nblk;
+    if (!a.test_on) a.db = adsx::FD_STEP_BLOCKS < a.nblk ? adsx::FD_STEP_BLOCKS : a.nblk;
     a.out_ids = oi.dev;
     a.out_d2 = od.dev;
     a.out_dims = odims.dev;
@@ -844,8 +1019,34 @@ int adsx_dco_fixed_r(const adsx_index *index, const float *Qv, int64_t nq, const
     CK(sc.get(&ftab, (size_t)a.nblk + 1), "alloc test factors");
     a.ftab = ftab;
     CK(adsx::launch_test_factors(ftab, a.nblk, a.D, a.test_on ? eps0 : 0.f, s), "test factors");
-    CK(cudaMemsetAsync(counter, 0, sizeof(unsigned), s), "clear counter");
-    CK(adsx::launch_ads_scan(a, adsx::ads_scan_grid(a, ix->device), s), "fixed-r scan");
+    if (ix->sched == ADSX_SCHED_CLUSTER && a.db <= adsx::CM_MAX_DB) {
+        // the cluster-major kernel's fixed-threshold mode: every query
+        // probes every cluster, one round
+        int32_t *probes = nullptr;
+        CK(sc.get(&probes, (size_t)nq * ix->nlist), "alloc probe lists");
+        CK(adsx::launch_cm_all_clusters(probes, nq, ix->nlist, s), "probe lists");
+        adsx::CmPlan pl;
+        int64_t items_cap = 0;
+        CK(cm_plan_buffers(ix, nq, ix->nlist, ix->cm_G, sc, pl, &items_cap), "alloc plan");
+        CK(adsx::launch_cm_plan(probes, nq, ix->nlist, 0, ix->nlist, ix->nlist, ix->cm_G, pl, s),
+           "plan");
+        adsx::CmArgs c = cm_args_from(a, ix->cm_G);
+        c.coff = pl.coff;
+        c.qlist = pl.qlist;
+        c.items = pl.items;
+        c.n_items = pl.n_items;
+        c.items_cap = (int32_t)items_cap;
+        c.work_counter = counter;
+        c.r2fixed = rr.dev;
+        c.decisions = dec.dev;
+        c.dec_dims = dm.dev;
+        c.N = ix->N;
+        c.out_dims = nullptr;
+        CK(adsx::launch_cm_scan(c, ix->device, s), "fixed-r scan (cluster-major)");
+    } else {
+        CK(cudaMemsetAsync(counter, 0, sizeof(unsigned), s), "clear counter");
+        CK(adsx::launch_ads_scan(a, adsx::ads_scan_grid(a, ix->device), s), "fixed-r scan");
+    }
     CK(copy_back(dec, s), "copy back");
     CK(copy_back(dm, s), "copy back");
     return finish(s, dec.host || dm.host, "fixed-r");
@@ -916,6 +1117,20 @@ int adsx_autotune(adsx_index *index, const float *Qv, int64_t nq, int32_t K, int
     if (best_delta_d) *best_delta_d = bdd;
     if (best_items_per_sm) *best_items_per_sm = bip;
     if (best_ms) *best_ms = best;
+    return ADSX_OK;
+}
+
+int adsx_set_scan_schedule(adsx_index *index, int32_t schedule, int32_t queries_per_item)
+{
+    Index *ix = reinterpret_cast<Index *>(index);
+    if (!ix) return fail(ADSX_EINVAL, "index is NULL");
+    if (schedule != ADSX_SCHED_AUTO && schedule != ADSX_SCHED_QUERY &&
+        schedule != ADSX_SCHED_CLUSTER)
+        return fail(ADSX_EINVAL, "unknown scan schedule %d", schedule);
+    if (queries_per_item < 0 || queries_per_item > adsx::CM_MAX_G)
+        return fail(ADSX_EINVAL, "queries_per_item out of range (0..%d)", adsx::CM_MAX_G);
+    ix->sched = schedule;
+    if (queries_per_item) ix->cm_G = queries_per_item;
     return ADSX_OK;
 }
 

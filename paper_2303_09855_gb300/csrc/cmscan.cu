@@ -1,0 +1,529 @@
+// cmscan.cu -- the cluster-major schedule of the IVF+ candidate scan (Sec. 4
+// with Algorithm 1 DCOs), for large query batches.
+//
+// The query-major scan (scan.cu) gives each warp one query and reads every
+// probed cluster once per query that probes it.  On a large batch each
+// cluster is probed by many queries (about nq * nprobe / nlist), so here the
+// work is grouped by cluster instead: a work item is (cluster c, up to G of
+// the queries that probe c), and one warp loads each Delta_d step of a
+// 32-member tile of c ONCE into registers and tests it against all of its
+// queries.  One load instruction of the warp then feeds G queries' FMAs.
+//
+// The running threshold r of a query cannot be shared between the warps
+// that serve it without a global KNN set, so the probe ranks are processed
+// in rounds: round 0 (the query-major kernel over each query's nearest
+// R0 clusters) gives every query its K-th distance r among those clusters;
+// each following round scans a range of probe ranks cluster-major against
+// the r of the rounds before it, appending every candidate that reaches
+// d = D with S_D <= r^2 to a per-query list; cm_merge_kernel then merges the
+// list into the query's top-K and tightens r.  A fixed r per round is a
+// valid threshold (the K-th of a subset of exact candidate distances is
+// never below the exact K-th of all of them), so every returned distance is
+// exact and the bracket property of the query-major scan holds; and as r is
+// fixed within a round, the result does not depend on the schedule.
+//
+// Every partial distance is accumulated with the shared per-candidate code
+// of scan_common.cuh, in the same order as the query-major kernel, so both
+// schedules compute the same FP32 value of S_d for every (query, candidate,
+// step); with a fixed threshold (the verification protocol of Sec. 6.2.5)
+// their decisions are identical.
+//
+// A query whose list overflows its capacity in some round is flagged and,
+// after the last round, searched again by the query-major kernel.
+#include <float.h>
+
+#include "scan_common.cuh"
+
+namespace adsx {
+namespace {
+
+using namespace scan;
+
+constexpr int CM_WARPS = 4;
+constexpr int CM_THREADS = CM_WARPS * 32;
+#ifndef ADSX_CM_MINBLOCKS
+#define ADSX_CM_MINBLOCKS 4
+#endif
+
+// Per-warp shared memory: query slots, their thresholds and live masks,
+// dims counters and the partial distance of each lane's member per query.
+struct CmCarve {
+    int qg, r2, live, dg, S, bytes;
+    __host__ __device__ explicit CmCarve(int G)
+    {
+        int o = 0;
+        dg = o; o += 8 * G;           // unsigned long long, 8-byte aligned first
+        qg = o; o += 4 * G;
+        r2 = o; o += 4 * G;
+        live = o; o += 4 * G;
+        S = o; o += 4 * 32 * G;
+        bytes = (o + 15) & ~15;
+    }
+};
+
+__device__ __forceinline__ float4 ldg4(const float *p)
+{
+    return __ldg(reinterpret_cast<const float4 *>(p));
+}
+template <int NL>
+__device__ __forceinline__ QPiece<NL> ld_qpiece_ro(const float *q)
+{
+    QPiece<NL> r;
+    r.a = ldg4(q);
+    if constexpr (NL == 2) r.b = ldg4(q + 4);
+    return r;
+}
+
+template <typename T, int DB, bool FIXED>
+__global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(CmArgs a)
+{
+    constexpr int NL = Split<T>::NL, NG = 32 / NL, PW = BLK / NL;
+    typedef typename Split<T>::V V;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ float s_ftab[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const CmCarve cc(a.G);
+    unsigned char *base = smraw + (size_t)warp * cc.bytes;
+    unsigned long long *dg = reinterpret_cast<unsigned long long *>(base + cc.dg);
+    int *qg = reinterpret_cast<int *>(base + cc.qg);
+    float *r2g = reinterpret_cast<float *>(base + cc.r2);
+    unsigned *live = reinterpret_cast<unsigned *>(base + cc.live);
+    float *Sv = reinterpret_cast<float *>(base + cc.S);
+    for (int b = threadIdx.x; b <= a.nblk && b < 256; b += CM_THREADS) s_ftab[b] = a.ftab[b];
+    __syncthreads();
+
+    const int gi = lane / NL, jo = (lane % NL) * PW;
+    const int own = own_slot<NL>(lane);
+    const int n_items = *a.n_items;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = (int)atomicAdd(a.work_counter, 1u);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= n_items) break;
+        const int2 it = a.items[item];
+        const int c = it.x;
+        const int q0 = a.coff[c] + it.y;
+        const int ngq = a.coff[c + 1] - q0 < a.G ? a.coff[c + 1] - q0 : a.G;
+        for (int g = lane; g < ngq; g += 32) {
+            const int q = a.qlist[q0 + g];
+            qg[g] = q;
+            r2g[g] = FIXED ? a.r2fixed[q] : a.r2[q];
+            dg[g] = 0ull;
+        }
+        __syncwarp();
+        const int64_t o = a.off[c];
+        const int n = (int)(a.off[c + 1] - o);
+        const T *cb = static_cast<const T *>(a.data) + o * a.Dp;
+        const int64_t stride = (int64_t)n * BLK;
+        for (int m0 = 0; m0 < n; m0 += 32) {
+            const int m = m0 + own;
+            const unsigned vm = __ballot_sync(FULL, m < n);
+            for (int g = lane; g < ngq; g += 32) live[g] = vm;
+            __syncwarp();
+            int blk = 0;
+            for (;;) {
+                unsigned U = 0u;                  // members live for some query
+                for (int g = 0; g < ngq; ++g) U |= live[g];
+                if (U == 0u) break;
+                const int e = blk + a.db < a.nblk ? blk + a.db : a.nblk;
+                const int nb = e - blk;
+                // this step's blocks of the tile: loaded once, used by every query
+                V v[DB][NL];
+                const T *x = cb + (int64_t)blk * stride + (int64_t)(m0 + gi) * BLK + jo;
+#pragma unroll
+                for (int b = 0; b < DB; ++b) {
+#pragma unroll
+                    for (int k = 0; k < NL; ++k) {
+                        zero_piece(v[b][k]);
+                        if (b < nb && ((U >> owner_lane<NL>(gi, k)) & 1u))
+                            v[b][k] = ld_piece(x + b * stride + k * NG * BLK);
+                    }
+                }
+                const bool fin = e >= a.nblk;
+                const float fe = s_ftab[e];
+                const int dstep = e * BLK < a.D ? e * BLK : a.D;
+                const int pos = (int)o + m;
+                for (int g = 0; g < ngq; ++g) {
+                    const unsigned lv = live[g];
+                    if (lv == 0u) continue;
+                    const float *qv = a.qrot + (int64_t)qg[g] * a.Dp;
+                    float2 p[NL];
+#pragma unroll
+                    for (int k = 0; k < NL; ++k) p[k] = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int b = 0; b < DB; ++b) {
+                        if (b < nb) {
+                            const QPiece<NL> qp = ld_qpiece_ro<NL>(qv + (blk + b) * BLK + jo);
+#pragma unroll
+                            for (int k = 0; k < NL; ++k) p[k] = add_piece(v[b][k], qp, p[k], T());
+                        }
+                    }
+                    float S = (blk == 0 ? 0.f : Sv[g * 32 + lane]) + group_sum<NL>(p, lane);
+                    const bool alive = (lv >> lane) & 1u;
+                    const float r2 = r2g[g];
+                    if (!fin) {
+                        // Case 1 / Case 2 of Algorithm 1 (squared test of Sec. 3.2)
+                        const bool rej = a.test_on && alive && S > r2 * fe;
+                        const unsigned rm = __ballot_sync(FULL, rej);
+                        if (FIXED && rej) {
+                            const int64_t off = (int64_t)qg[g] * a.N + a.ids[pos];
+                            a.decisions[off] = 0;
+                            if (a.dec_dims) a.dec_dims[off] = dstep;
+                        }
+                        Sv[g * 32 + lane] = S;
+                        if (lane == 0) {
+                            live[g] = lv & ~rm;
+                            dg[g] += (unsigned long long)__popc(rm) * (unsigned)dstep;
+                        }
+                    } else {
+                        // Case 3: the exact compare at d = D
+                        bool cand = alive;
+                        if constexpr (Roundoff<T>::u > 0.f) {
+                            // 16-bit storage: only candidates with sqrt(S~) <=
+                            // r + u ||x|| can have S_D <= r^2; their exact FP32
+                            // distance comes from the FP32 row copy
+                            bool need = false;
+                            if (alive) {
+                                need = !(r2 < INFINITY);
+                                if (!need && r2 >= 0.f) {
+                                    const float bound =
+                                        (sqrtf(r2) + Roundoff<T>::u * a.norms[pos]) * 1.0001f;
+                                    need = sqrtf(S) <= bound;
+                                }
+                            }
+                            S = recheck_rows(a.rows32, a.Dp, qv, need, pos, S, lane);
+                            cand = need;
+                        }
+                        const bool posv = cand && S <= r2;
+                        if constexpr (FIXED) {
+                            if (alive) {
+                                const int64_t off = (int64_t)qg[g] * a.N + a.ids[pos];
+                                a.decisions[off] = posv ? 1 : 2;
+                                if (a.dec_dims) a.dec_dims[off] = a.D;
+                            }
+                        } else {
+                            const unsigned pm = __ballot_sync(FULL, posv);
+                            if (pm) {
+                                const int q = qg[g];
+                                unsigned b0 = 0u;
+                                if (lane == 0) b0 = atomicAdd(a.app_n + q, (unsigned)__popc(pm));
+                                b0 = __shfl_sync(FULL, b0, 0);
+                                if (posv) {
+                                    const unsigned idx = b0 + __popc(pm & ((1u << lane) - 1u));
+                                    if (idx < (unsigned)a.cap) {
+                                        a.app_d[(int64_t)q * a.cap + idx] = S;
+                                        a.app_i[(int64_t)q * a.cap + idx] = a.ids[pos];
+                                    }
+                                }
+                            }
+                        }
+                        if (lane == 0) {
+                            live[g] = 0u;
+                            dg[g] += (unsigned long long)__popc(lv) * (unsigned)a.D;
+                        }
+                    }
+                }
+                __syncwarp();
+                blk = e;
+            }
+        }
+        if (a.out_dims)
+            for (int g = lane; g < ngq; g += 32)
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.out_dims + qg[g]), dg[g]);
+        __syncwarp();
+    }
+}
+
+// ---- round planning: the (query, probe rank) pairs of ranks [r0, r1) grouped
+// by cluster.  cnt[c] counts them; cm_plan_offsets turns the counts into
+// offsets of each cluster's query list and of its work items (one per G
+// queries); cm_plan_scatter fills the lists and the items.
+__global__ void cm_plan_count_kernel(const int32_t *__restrict__ probes, int64_t nq, int pstride,
+                                     int r0, int r1, int *__restrict__ cnt)
+{
+    const int w = r1 - r0;
+    const int64_t total = nq * w;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = i / w;
+        const int p = r0 + (int)(i - q * w);
+        atomicAdd(cnt + probes[q * pstride + p], 1);
+    }
+}
+
+// One block: exclusive prefix sums of cnt (-> coff) and of ceil(cnt / G)
+// (-> ioff), the item total, and the cursors cleared.
+__global__ void __launch_bounds__(1024) cm_plan_offsets_kernel(const int *__restrict__ cnt,
+                                                               int nlist, int G,
+                                                               int *__restrict__ coff,
+                                                               int *__restrict__ ioff,
+                                                               int *__restrict__ cur,
+                                                               int *__restrict__ n_items)
+{
+    __shared__ int s_a[32], s_b[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int per = (nlist + 1023) / 1024;
+    const int c0 = t * per, c1 = c0 + per < nlist ? c0 + per : nlist;
+    int sa = 0, sb = 0;
+    for (int c = c0; c < c1; ++c) {
+        sa += cnt[c];
+        sb += (cnt[c] + G - 1) / G;
+    }
+    int xa = sa, xb = sb;                 // inclusive warp scans
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int ya = __shfl_up_sync(FULL, xa, d), yb = __shfl_up_sync(FULL, xb, d);
+        if (lane >= d) {
+            xa += ya;
+            xb += yb;
+        }
+    }
+    if (lane == 31) {
+        s_a[warp] = xa;
+        s_b[warp] = xb;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int ya = s_a[lane], yb = s_b[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int za = __shfl_up_sync(FULL, ya, d), zb = __shfl_up_sync(FULL, yb, d);
+            if (lane >= d) {
+                ya += za;
+                yb += zb;
+            }
+        }
+        s_a[lane] = ya;
+        s_b[lane] = yb;
+    }
+    __syncthreads();
+    int ea = xa - sa + (warp > 0 ? s_a[warp - 1] : 0);
+    int eb = xb - sb + (warp > 0 ? s_b[warp - 1] : 0);
+    for (int c = c0; c < c1; ++c) {
+        coff[c] = ea;
+        ioff[c] = eb;
+        cur[c] = 0;
+        ea += cnt[c];
+        eb += (cnt[c] + G - 1) / G;
+    }
+    if (t == 1023) {
+        coff[nlist] = ea;
+        *n_items = eb;
+    }
+}
+
+__global__ void cm_plan_scatter_kernel(const int32_t *__restrict__ probes, int64_t nq, int pstride,
+                                       int r0, int r1, int G, const int *__restrict__ coff,
+                                       const int *__restrict__ ioff, int *__restrict__ cur,
+                                       int *__restrict__ qlist, int2 *__restrict__ items)
+{
+    const int w = r1 - r0;
+    const int64_t total = nq * w;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = i / w;
+        const int p = r0 + (int)(i - q * w);
+        const int c = probes[q * pstride + p];
+        const int slot = atomicAdd(cur + c, 1);
+        qlist[coff[c] + slot] = (int)q;
+        if (slot % G == 0) items[ioff[c] + slot / G] = make_int2(c, slot);
+    }
+}
+
+// Per query: the top-K so far (ids / keys, -1 padded) and the candidates the
+// round appended are sorted by (distance, id) and cut to K; r^2 becomes the
+// K-th key (+inf while fewer than K are known).  A list beyond its capacity
+// flags the query.  With `final_pass` the keys are written as the values the
+// search returns.
+__global__ void __launch_bounds__(256) cm_merge_kernel(CmMergeArgs m)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float *sd = reinterpret_cast<float *>(smraw);
+    int *si = reinterpret_cast<int *>(sd + m.T);
+    const int K = m.K;
+    for (int64_t q = blockIdx.x; q < m.nq; q += gridDim.x) {
+        unsigned na = m.app_n ? m.app_n[q] : 0u;
+        if (na > (unsigned)m.cap) {
+            if (threadIdx.x == 0) m.ovf[q] = 1;
+            na = (unsigned)m.cap;
+        }
+        int64_t *ids = m.ids + q * K;
+        float *dk = m.d2 + q * K;
+        if (na == 0u && !m.final_pass) {
+            if (threadIdx.x == 0) m.r2[q] = ids[K - 1] >= 0 ? dk[K - 1] : INFINITY;
+            continue;
+        }
+        int T = 1;
+        while (T < K + (int)na) T <<= 1;
+        for (int i = threadIdx.x; i < T; i += blockDim.x) {
+            float d = INFINITY;
+            int id = 0x7fffffff;
+            if (i < K) {
+                if (ids[i] >= 0) {
+                    d = dk[i];
+                    id = (int)ids[i];
+                }
+            } else if (i < K + (int)na) {
+                d = m.app_d[q * m.cap + (i - K)];
+                id = m.app_i[q * m.cap + (i - K)];
+            }
+            sd[i] = d;
+            si[i] = id;
+        }
+        __syncthreads();
+        for (int size = 2; size <= T; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = threadIdx.x; i < T; i += blockDim.x) {
+                    const int j = i ^ stride;
+                    if (j > i) {
+                        const float di = sd[i], dj = sd[j];
+                        const int ii = si[i], ij = si[j];
+                        const bool up = (i & size) == 0;
+                        if (pair_less(dj, ij, di, ii) == up) {
+                            sd[i] = dj;
+                            si[i] = ij;
+                            sd[j] = di;
+                            si[j] = ii;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            const bool has = si[k] != 0x7fffffff;
+            ids[k] = has ? (int64_t)si[k] : (int64_t)-1;
+            dk[k] = m.final_pass ? out_value(m.metric, sd[k], has) : (has ? sd[k] : INFINITY);
+        }
+        if (threadIdx.x == 0) {
+            m.r2[q] = si[K - 1] != 0x7fffffff ? sd[K - 1] : INFINITY;
+            if (m.app_n) m.app_n[q] = 0u;
+        }
+        __syncthreads();
+    }
+}
+
+// Items (query, one split) of the queries whose lists overflowed, for a
+// query-major re-run.
+__global__ void cm_overflow_items_kernel(const int *__restrict__ ovf, int64_t nq,
+                                         int2 *__restrict__ items, int *__restrict__ n_items)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
+         q += (int64_t)gridDim.x * blockDim.x)
+        if (ovf[q]) items[atomicAdd(n_items, 1)] = make_int2((int)q, (0 << 16) | 1);
+}
+
+// Probe slot p of every query is cluster p (the fixed-threshold scan of all
+// clusters).
+__global__ void cm_all_clusters_kernel(int32_t *__restrict__ probes, int64_t nq, int nlist)
+{
+    const int64_t total = nq * nlist;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x)
+        probes[i] = (int32_t)(i % nlist);
+}
+
+typedef void (*CmKernel)(CmArgs);
+
+template <typename T, bool FIXED>
+CmKernel cm_kernel_db(int db)
+{
+    switch (db) {
+    case 1: return cm_scan_kernel<T, 1, FIXED>;
+    case 2: return cm_scan_kernel<T, 2, FIXED>;
+    case 3: return cm_scan_kernel<T, 3, FIXED>;
+    default: return cm_scan_kernel<T, 4, FIXED>;
+    }
+}
+
+template <typename T>
+CmKernel cm_kernel_t(const CmArgs &a)
+{
+    return a.decisions ? cm_kernel_db<T, true>(a.db) : cm_kernel_db<T, false>(a.db);
+}
+
+CmKernel cm_kernel_for(const CmArgs &a)
+{
+    if (a.storage == ADSX_F32) return cm_kernel_t<float>(a);
+    if (a.storage == ADSX_BF16) return cm_kernel_t<__nv_bfloat16>(a);
+    return cm_kernel_t<__half>(a);
+}
+
+unsigned grid_for(int64_t work, int threads)
+{
+    int64_t b = (work + threads - 1) / threads;
+    if (b > 152 * 16) b = 152 * 16;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+size_t cm_smem_bytes(int G) { return (size_t)CmCarve(G).bytes * CM_WARPS; }
+
+cudaError_t launch_cm_plan(const int32_t *probes, int64_t nq, int pstride, int r0, int r1, int nlist,
+                           int G, CmPlan &pl, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(pl.cnt, 0, sizeof(int) * nlist, s);
+    if (e != cudaSuccess) return e;
+    const int64_t work = nq * (int64_t)(r1 - r0);
+    cm_plan_count_kernel<<<grid_for(work, 256), 256, 0, s>>>(probes, nq, pstride, r0, r1, pl.cnt);
+    cm_plan_offsets_kernel<<<1, 1024, 0, s>>>(pl.cnt, nlist, G, pl.coff, pl.ioff, pl.cur, pl.n_items);
+    cm_plan_scatter_kernel<<<grid_for(work, 256), 256, 0, s>>>(probes, nq, pstride, r0, r1, G,
+                                                                pl.coff, pl.ioff, pl.cur, pl.qlist,
+                                                                pl.items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cm_scan(const CmArgs &a, int device, cudaStream_t s)
+{
+    if (a.db < 1 || a.db > CM_MAX_DB || a.G < 1 || a.G > CM_MAX_G) return cudaErrorInvalidValue;
+    const CmKernel k = cm_kernel_for(a);
+    const size_t smem = cm_smem_bytes(a.G);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int nsm = 0, per = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, CM_THREADS, smem);
+    if (per < 1) per = 1;
+    int64_t grid = (int64_t)nsm * per;
+    const int64_t need = ((int64_t)a.items_cap + CM_WARPS - 1) / CM_WARPS;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    e = cudaMemsetAsync(a.work_counter, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    k<<<(unsigned)grid, CM_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cm_merge(const CmMergeArgs &m, cudaStream_t s)
+{
+    if (m.nq <= 0) return cudaSuccess;
+    CmMergeArgs b = m;
+    int T = 1;
+    while (T < m.K + m.cap) T <<= 1;
+    b.T = T;
+    const size_t smem = (size_t)T * 8;
+    cudaError_t e = cudaFuncSetAttribute(cm_merge_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = m.nq < 152 * 16 ? m.nq : 152 * 16;
+    cm_merge_kernel<<<(unsigned)grid, 256, smem, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cm_overflow_items(const int *ovf, int64_t nq, int2 *items, int *n_items,
+                                     cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(n_items, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    cm_overflow_items_kernel<<<grid_for(nq, 256), 256, 0, s>>>(ovf, nq, items, n_items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cm_all_clusters(int32_t *probes, int64_t nq, int nlist, cudaStream_t s)
+{
+    cm_all_clusters_kernel<<<grid_for(nq * nlist, 256), 256, 0, s>>>(probes, nq, nlist);
+    return cudaGetLastError();
+}
+
+}  // namespace adsx

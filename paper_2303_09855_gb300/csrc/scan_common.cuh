@@ -1,0 +1,189 @@
+// scan_common.cuh -- the per-candidate arithmetic shared by the two scan
+// schedules of libadsx.so (internal): ads_scan_kernel (query-major, scan.cu)
+// and cm_scan_kernel (cluster-major, cmscan.cu).  Both accumulate a
+// candidate's partial distance S_d (Algorithm 1) with exactly these
+// functions, in the same order, so both give the same FP32 value for every
+// (query, candidate, step) and hence the same decisions at a given r.
+#pragma once
+
+#include "adsx_internal.cuh"
+
+namespace adsx {
+namespace scan {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ bool pair_less(float d1, int i1, float d2, int i2)
+{
+    return d1 < d2 || (d1 == d2 && i1 < i2);
+}
+
+// Order-preserving map of a float key to unsigned (inner-product keys are
+// negative), for the atomicMin that shares r between the splits of a query;
+// 0xffffffff (the cleared value) means "no bound yet".
+__device__ __forceinline__ unsigned key_to_ord(float k)
+{
+    const unsigned u = __float_as_uint(k);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord_to_key(unsigned m)
+{
+    return __uint_as_float((m & 0x80000000u) ? (m & 0x7fffffffu) : ~m);
+}
+
+// The value returned for a key: L2 the squared distance; cosine the
+// similarity 1 - ||x^ - q^||^2 / 2; inner product <o,q> (key = -<o,q>).
+// Empty slots: +inf for L2, -inf for similarities.
+__device__ __forceinline__ float out_value(int metric, float key, bool has)
+{
+    if (metric == ADSX_L2) return has ? key : INFINITY;
+    if (!has) return -INFINITY;
+    return metric == ADSX_COSINE ? fmaf(-0.5f, key, 1.f) : -key;
+}
+
+// ---- several lanes per candidate.  One 16-dim block of a candidate is 64
+// bytes (FP32) or 32 bytes (16-bit); NL = 4 or 2 lanes split it into 16-byte
+// pieces.  The warp is 32/NL groups of NL lanes, and lane l (group g = l / NL,
+// piece j = l % NL) works on the NL candidates g + (32/NL) k, k < NL, of a set
+// of 32.  One load instruction of the warp thus reads whole blocks of 32/NL
+// candidates -- a single contiguous 512-byte run when they are consecutive
+// members -- instead of 16-byte slices of 32 candidates spread over 16 or more
+// cache lines.  Each lane keeps a partial sum per candidate (its piece, two
+// FP32 chains: even and odd dims); group_sum then combines the NL pieces so
+// that lane l holds the complete sum of candidate own_slot(l).
+template <typename T> struct Split {           // 16-bit: 2 lanes x 8 values
+    static constexpr int NL = 2;
+    typedef uint4 V;
+};
+template <> struct Split<float> {              // FP32: 4 lanes x 4 values
+    static constexpr int NL = 4;
+    typedef float4 V;
+};
+
+__device__ __forceinline__ float4 ld_piece(const float *p)
+{
+    return __ldg(reinterpret_cast<const float4 *>(p));
+}
+template <typename H>
+__device__ __forceinline__ uint4 ld_piece(const H *p)
+{
+    return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+__device__ __forceinline__ void zero_piece(float4 &v) { v = make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ void zero_piece(uint4 &v) { v = make_uint4(0u, 0u, 0u, 0u); }
+
+// The query values matching a lane's piece (4 or 8 floats, shared memory).
+template <int NL> struct QPiece;
+template <> struct QPiece<4> { float4 a; };
+template <> struct QPiece<2> { float4 a, b; };
+template <int NL>
+__device__ __forceinline__ QPiece<NL> ld_qpiece(const float *q)
+{
+    QPiece<NL> r;
+    r.a = *reinterpret_cast<const float4 *>(q);
+    if constexpr (NL == 2) r.b = *reinterpret_cast<const float4 *>(q + 4);
+    return r;
+}
+
+// S + (x - q)^2 over the piece, even dims into S.x and odd dims into S.y.
+// (The packed f32x2 subtract/FMA of sm_100+ gives the same values but
+// measured about 12% slower in this loop, so the chains stay scalar.)
+__device__ __forceinline__ float2 add_piece(float4 x, const QPiece<4> &q, float2 S, float)
+{
+    float t;
+    t = x.x - q.a.x; S.x = fmaf(t, t, S.x);
+    t = x.y - q.a.y; S.y = fmaf(t, t, S.y);
+    t = x.z - q.a.z; S.x = fmaf(t, t, S.x);
+    t = x.w - q.a.w; S.y = fmaf(t, t, S.y);
+    return S;
+}
+template <typename H>
+__device__ __forceinline__ float2 add_piece(uint4 x, const QPiece<2> &q, float2 S, H h)
+{
+    float v0, v1, t;
+    unpack2(x.x, v0, v1, h);
+    t = v0 - q.a.x; S.x = fmaf(t, t, S.x);
+    t = v1 - q.a.y; S.y = fmaf(t, t, S.y);
+    unpack2(x.y, v0, v1, h);
+    t = v0 - q.a.z; S.x = fmaf(t, t, S.x);
+    t = v1 - q.a.w; S.y = fmaf(t, t, S.y);
+    unpack2(x.z, v0, v1, h);
+    t = v0 - q.b.x; S.x = fmaf(t, t, S.x);
+    t = v1 - q.b.y; S.y = fmaf(t, t, S.y);
+    unpack2(x.w, v0, v1, h);
+    t = v0 - q.b.z; S.x = fmaf(t, t, S.x);
+    t = v1 - q.b.w; S.y = fmaf(t, t, S.y);
+    return S;
+}
+
+// The candidate (of the set of 32) whose complete sum lane l receives from
+// group_sum, and the lane that receives candidate g + (32/NL) k.
+template <int NL>
+__device__ __forceinline__ int own_slot(int lane)
+{
+    if constexpr (NL == 4) return (lane >> 2) + 8 * (2 * (lane & 1) + ((lane >> 1) & 1));
+    else return (lane >> 1) + 16 * (lane & 1);
+}
+template <int NL>
+__device__ __forceinline__ int owner_lane(int g, int k)
+{
+    if constexpr (NL == 4) return 4 * g + (k >> 1) + 2 * (k & 1);
+    else return 2 * g + k;
+}
+
+// Transpose-and-add over the NL lanes of a group: lane l enters with the
+// partial sums p[k] of its piece for candidates g + (32/NL) k and leaves with
+// the sum over all pieces of candidate own_slot(l).  With NL = 4, lanes l, l^1
+// split the four candidates into {0, 1} and {2, 3}, then lanes l, l^2 split
+// each pair; with NL = 2, lanes l, l^1 split {0, 1}.
+template <int NL>
+__device__ __forceinline__ float group_sum(const float2 (&pp)[NL], int lane)
+{
+    float p[NL];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) p[k] = pp[k].x + pp[k].y;
+    const bool hi1 = lane & 1;
+    if constexpr (NL == 4) {
+        const bool hi2 = lane & 2;
+        const float u0 = (hi1 ? p[2] : p[0]) + __shfl_xor_sync(FULL, hi1 ? p[0] : p[2], 1);
+        const float u1 = (hi1 ? p[3] : p[1]) + __shfl_xor_sync(FULL, hi1 ? p[1] : p[3], 1);
+        return (hi2 ? u1 : u0) + __shfl_xor_sync(FULL, hi2 ? u0 : u1, 2);
+    } else {
+        return (hi1 ? p[1] : p[0]) + __shfl_xor_sync(FULL, hi1 ? p[0] : p[1], 1);
+    }
+}
+
+// 16-bit storage: the exact FP32 distance of the candidate at CSR row `pos`
+// for every lane with `need`, recomputed from the FP32 row copy one candidate
+// at a time by the whole warp (each lane a 4-dim slice, then a butterfly sum
+// whose result is the same on all lanes).  qv: the query (Dp floats, shared
+// or global memory).
+__device__ __forceinline__ float recheck_rows(const float *__restrict__ rows32, int Dp,
+                                              const float *qv, bool need, int pos, float S,
+                                              int lane)
+{
+    unsigned mask = __ballot_sync(FULL, need);
+    while (mask) {
+        const int src = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int p = __shfl_sync(FULL, pos, src);
+        const float *row = rows32 + (int64_t)p * Dp;
+        float part = 0.f;
+        for (int j = lane * 4; j < Dp; j += 128) {
+            const float4 x = __ldg(reinterpret_cast<const float4 *>(row + j));
+            const float4 q = *reinterpret_cast<const float4 *>(qv + j);
+            float t;
+            t = x.x - q.x; part = fmaf(t, t, part);
+            t = x.y - q.y; part = fmaf(t, t, part);
+            t = x.z - q.z; part = fmaf(t, t, part);
+            t = x.w - q.w; part = fmaf(t, t, part);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+        if (lane == src) S = part;
+    }
+    return S;
+}
+
+}  // namespace scan
+}  // namespace adsx

@@ -1,0 +1,193 @@
+"""The cluster-major scan schedule (ADSX_SCHED_CLUSTER, cmscan.cu) through the
+C ABI, against the query-major schedule and the FP64 oracle.
+
+Both schedules accumulate every candidate's partial distance with the same
+code in the same order, so:
+  - with the test off (FDScanning, eps0 = inf) their results are bit-identical,
+    and equal exact IVF (ids except near-ties, distances within 1e-5);
+  - with a fixed threshold (the verification protocol of Sec. 6.2.5) every
+    per-candidate decision and dims count is identical, and bit-exact to the
+    oracle outside the 1e-5 margin band;
+  - with ADSampling (eps0 = 2.1) the cluster-major rounds test each candidate
+    against the K-th distance of the rounds before it: every returned distance
+    is exact, the bracket invariant holds, recall@K stays within 0.002 of the
+    sequential oracle's IVF+ recall, and -- r being fixed per round -- two
+    runs give identical results, dims included;
+  - a query whose round list overflows is searched again query-major and
+    still returns exact IVF;
+  - BF16 storage, the cosine metric and PDScanning run through it too.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import REL, kth_near_tie, near_tie_queries, topk_row_mismatch
+from paper_2303_09855_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cm():
+    from paper_2303_09855_gb300 import adsx, build
+    build.build()
+    wl = W.gen_gaussian_mixture()
+    ix = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign)
+    Y, Cr, Qr = (oracle.rotate(wl.P, a) for a in (wl.X, wl.centroids, wl.Q))
+    yield adsx, wl, ix, Y, Cr, Qr
+    ix.close()
+
+
+def _both(adsx, ix, fn):
+    ix.set_scan_schedule(adsx.SCHED_QUERY)
+    a = fn()
+    ix.set_scan_schedule(adsx.SCHED_CLUSTER)
+    b = fn()
+    ix.set_scan_schedule(adsx.SCHED_AUTO)
+    return a, b
+
+
+@pytest.mark.parametrize("K,nprobe,G", [(10, 10, 16), (100, 25, 16), (1, 12, 3), (10, 100, 64)])
+def test_fd_bit_identical_across_schedules_and_exact(cm, K, nprobe, G):
+    adsx, wl, ix, Y, Cr, Qr = cm
+    ix.set_scan_schedule(adsx.SCHED_AUTO, G)
+    (a_ids, a_d, a_dims), (b_ids, b_d, b_dims) = _both(
+        adsx, ix, lambda: ix.search(wl.Q, K, nprobe, eps0=math.inf, return_dims=True))
+    assert np.array_equal(a_ids, b_ids)
+    assert np.array_equal(a_d, b_d)
+    assert np.array_equal(a_dims, b_dims)
+    eids, ed2 = oracle.ivf_exact(Y, Cr, wl.assign, Qr, K + 1, nprobe)
+    ok = ~(near_tie_queries(Cr, Qr, nprobe) | kth_near_tie(ed2, K))
+    for q in np.nonzero(ok)[0]:
+        assert not topk_row_mismatch(b_ids[q], b_d[q], eids[q, :K], ed2[q, :K]), q
+    _, _, _, ncand = oracle.ivf_ads(Y, Cr, wl.assign, Qr, K, nprobe, math.inf, 32)
+    assert np.array_equal(b_dims[ok], (ncand * wl.D)[ok])
+    ix.set_scan_schedule(adsx.SCHED_AUTO, 16)
+
+
+@pytest.mark.parametrize("scale,eps0,dd", [(1.0, 2.1, 32), (1.0, 1.0, 16), (1.5, 2.1, 48),
+                                           (0.7, 0.5, 64), (1.0, math.inf, 32)])
+def test_fixed_r_decisions_identical_across_schedules(cm, scale, eps0, dd):
+    adsx, wl, ix, Y, Cr, Qr = cm
+    _, kd = oracle.knn_exact(Y, Qr, 10)
+    r2 = (kd[:, -1] * scale).astype(np.float32)
+    (a_dec, a_dims), (b_dec, b_dims) = _both(adsx, ix,
+                                             lambda: ix.dco_fixed_r(wl.Q, r2, eps0, dd))
+    assert np.array_equal(a_dec, b_dec)
+    assert np.array_equal(a_dims, b_dims)
+    edec, edims, emar = oracle.dco_fixed_r(Y, Qr, r2.astype(np.float64), eps0, dd)
+    boundary = emar < REL
+    agree = b_dec == edec
+    assert np.all(agree | boundary), int((~agree & ~boundary).sum())
+    assert np.all(b_dims[agree] == edims[agree])
+
+
+@pytest.mark.parametrize("K,nprobe,eps0,dd", [(10, 10, 2.1, 32), (100, 25, 2.1, 32),
+                                              (10, 20, 1.0, 16), (10, 30, 2.1, 64)])
+def test_ads_exact_bracket_recall_and_deterministic(cm, K, nprobe, eps0, dd):
+    adsx, wl, ix, Y, Cr, Qr = cm
+    ix.set_scan_schedule(adsx.SCHED_CLUSTER)
+    try:
+        ids, d2, dims = ix.search(wl.Q, K, nprobe, eps0=eps0, delta_d=dd, return_dims=True)
+        ids2, d22, dims2 = ix.search(wl.Q, K, nprobe, eps0=eps0, delta_d=dd, return_dims=True)
+    finally:
+        ix.set_scan_schedule(adsx.SCHED_AUTO)
+    assert np.array_equal(ids, ids2) and np.array_equal(d2, d22) and np.array_equal(dims, dims2)
+    eids, ed2 = oracle.ivf_exact(Y, Cr, wl.assign, Qr, K + 1, nprobe)
+    oids, _, _, ncand = oracle.ivf_ads(Y, Cr, wl.assign, Qr, K, nprobe, eps0, dd)
+    ok = ~near_tie_queries(Cr, Qr, nprobe)
+    for q in np.nonzero(ok)[0]:
+        row = ids[q][ids[q] >= 0]
+        assert len(set(row.tolist())) == len(row), q
+        for i, d in zip(ids[q], d2[q]):
+            if i >= 0:
+                ex = float(np.sum((Y[i] - Qr[q]) ** 2))
+                assert abs(d - ex) <= REL * ex + 1e-6, (q, i, d, ex)
+        top = eids[q, :K][eids[q, :K] >= 0]
+        dec, _, mar = oracle.dco_fixed_r(Y[top], Qr[q:q + 1], np.array([ed2[q, K - 1]]), eps0, dd)
+        must = set(top[(dec[0] == oracle.POSITIVE) & (mar[0] >= REL)].tolist())
+        assert must <= set(ids[q].tolist()), q
+    gt, _ = oracle.knn_exact(Y, Qr, K)
+    r_gpu, r_orc = oracle.recall_at(ids[ok], gt[ok], K), oracle.recall_at(oids[ok], gt[ok], K)
+    assert abs(r_gpu - r_orc) <= 0.002, (r_gpu, r_orc)
+    first = min(dd, wl.D)
+    assert np.all(dims >= ncand * first) and np.all(dims <= ncand * wl.D)
+
+
+def test_auto_takes_cluster_major_on_large_batches(cm):
+    """3000 queries, nprobe 10: AUTO gives exactly the (deterministic)
+    cluster-major result, dims included; FDScanning equals query-major."""
+    adsx, wl, ix, Y, Cr, Qr = cm
+    many = np.tile(wl.Q, (30, 1))
+    auto = ix.search(many, 10, 10, eps0=2.1, return_dims=True)
+    ix.set_scan_schedule(adsx.SCHED_CLUSTER)
+    try:
+        clus = ix.search(many, 10, 10, eps0=2.1, return_dims=True)
+    finally:
+        ix.set_scan_schedule(adsx.SCHED_AUTO)
+    for x, y in zip(auto, clus):
+        assert np.array_equal(x, y)
+    # the 30 copies of a query get the same answer
+    assert np.array_equal(auto[0][:100], auto[0][2900:])
+    (a_ids, a_d), (b_ids, b_d) = _both(adsx, ix,
+                                       lambda: ix.search(many, 10, 10, eps0=math.inf))
+    assert np.array_equal(a_ids, b_ids) and np.array_equal(a_d, b_d)
+
+
+def test_overflowing_round_list_falls_back_to_query_major():
+    """Every vector equal: after round 0 every later candidate ties r, so each
+    round list overflows; the query is searched again query-major and the
+    result is exact IVF (smallest ids among equal distances)."""
+    from paper_2303_09855_gb300 import adsx
+    rng = np.random.default_rng(5)
+    N, D, nlist = 3000, 32, 6
+    X = np.tile(rng.standard_normal(D).astype(np.float32), (N, 1))
+    assign = (np.arange(N) % nlist).astype(np.int32)
+    C = rng.standard_normal((nlist, D)).astype(np.float32)
+    P = W.make_P(D, 11).astype(np.float32)
+    Q = rng.standard_normal((4, D)).astype(np.float32)
+    ix = adsx.build_index(X, P, C, assign)
+    try:
+        ix.set_scan_schedule(adsx.SCHED_CLUSTER)
+        for eps0 in (math.inf, 2.1):
+            ids, d2, dims = ix.search(Q, 3, nlist, eps0=eps0, return_dims=True)
+            assert np.array_equal(ids, np.tile(np.arange(3), (4, 1))), ids
+            ex = ((X[0].astype(np.float64) - Q.astype(np.float64)) ** 2).sum(1)
+            assert np.allclose(d2, ex[:, None], rtol=1e-5)
+            assert np.all(dims == N * D)
+    finally:
+        ix.close()
+
+
+def test_bf16_and_cosine_and_pdscan_across_schedules(cm):
+    adsx, wl, ix, Y, Cr, Qr = cm
+    bf = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign, storage=adsx.BF16)
+    co = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign, metric=adsx.COSINE)
+    try:
+        for idx in (bf, co):
+            (a, b) = _both(adsx, idx, lambda: idx.search(wl.Q, 10, 12, eps0=math.inf,
+                                                         return_dims=True))
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y)
+        _, kd = oracle.knn_exact(Y, Qr, 10)
+        r2 = (kd[:, -1] * 1.2).astype(np.float32)
+        (a_dec, a_dims), (b_dec, b_dims) = _both(adsx, bf,
+                                                 lambda: bf.dco_fixed_r(wl.Q, r2, 2.1, 32))
+        assert np.array_equal(a_dec, b_dec) and np.array_equal(a_dims, b_dims)
+        # BF16 ADSampling, cluster-major: exact FP32 distances from the recheck
+        bf.set_scan_schedule(adsx.SCHED_CLUSTER)
+        ids, d2 = bf.search(wl.Q, 10, 12, eps0=2.1)
+        for q in range(0, 100, 9):
+            for i, d in zip(ids[q], d2[q]):
+                if i >= 0:
+                    ex = float(np.sum((Y[i] - Qr[q]) ** 2))
+                    assert abs(d - ex) <= REL * ex + 1e-6
+        # PDScanning is exact under either schedule
+        (p_ids, p_d), (c_ids, c_d) = _both(adsx, ix,
+                                           lambda: adsx.search_pdscan(ix, wl.Q, 10, 12, 32))
+        assert np.array_equal(p_ids, c_ids) and np.array_equal(p_d, c_d)
+    finally:
+        bf.close()
+        co.close()

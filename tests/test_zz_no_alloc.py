@@ -27,6 +27,9 @@ def setup():
     build.build()
     wl = W.gen_gaussian_mixture()
     ix = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign)
+    # the no-alloc entry point runs the query-major scan; pin adsx_search to
+    # the same schedule so that large batches compare like with like
+    ix.set_scan_schedule(adsx.SCHED_QUERY)
     yield adsx, torch, wl, ix
     ix.close()
 
@@ -109,6 +112,7 @@ def test_noalloc_tuned_step_after_autotune():
     wl = W.gen_gaussian_mixture()
     ix = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign)
     try:
+        ix.set_scan_schedule(adsx.SCHED_QUERY)
         adsx.autotune(ix, wl.Q, 10, 10, eps0=2.1)
         Qd = torch.from_numpy(np.tile(wl.Q, (80, 1))).cuda()
         ref_ids, ref_d, ref_dims = (t.cpu().numpy() for t in
