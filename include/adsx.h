@@ -481,9 +481,13 @@ int adsx_graph_export(const adsx_graph *graph, int32_t *neighbors, int64_t *entr
  * cluster first.  Every vertex not visited before, start vertex or
  * neighbour, runs Algorithm 1 against r = the largest distance in R (+INF
  * while R holds fewer than ef) and, if it reaches d = D with (distance, id)
- * below R's largest, joins R, which keeps its ef smallest; r stays fixed
- * during one batch: 32 consecutive positions of the start list, then the
- * neighbour list of each expansion.  The search repeatedly expands the
+ * below R's largest, joins R, which keeps its ef smallest -- in the paper's
+ * order: one vertex at a time, each vertex facing R as it stands after the
+ * vertices before it in the start list or neighbour list.  (The GPU tests
+ * up to 32 vertices side by side against the threshold at their start and
+ * then replays the decisions in list order from the recorded partial
+ * distances, which gives the sequential outcome exactly; dims_read counts
+ * the dims of the sequential order.)  The search repeatedly expands the
  * nearest not-yet-expanded entry of R.
  * The search stops when every entry of R is expanded, or after 4 ef
  * expansions.  The K smallest entries of R are returned, by (distance, id).

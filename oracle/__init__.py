@@ -88,7 +88,7 @@ def _load():
             lib.orc_ivf_ads_ip.argtypes = [P, i64, i32, P, i32, P, P, i64, i32, i32,
                                            f64, i32, P, P, P, P, cint]
             lib.orc_graph_search.argtypes = [P, i64, i32, P, i32, P, i32, P, i64, i32, i32, i32,
-                                             f64, i32, i32, P, P, P, P, cint]
+                                             f64, i32, i32, P, P, P, P, P, cint]
             _lib = lib
     return _lib
 
@@ -230,17 +230,22 @@ def ivf_pd(Y, Cr, assign, Qr, K: int, nprobe: int, delta_d: int, nthreads: int =
 
 # ------------------------------------------------------ graph search
 def graph_search(Y, graph, entries, Qr, K: int, ef: int, eps0: float, delta_d: int,
-                 max_iter: int = 0, nthreads: int = 0, pp: bool = False):
+                 max_iter: int = 0, nthreads: int = 0, pp: bool = False,
+                 return_margin: bool = False):
     """Sec. 2.2.1 / Sec. 4 (HNSW+): greedy beam search on a proximity graph
     (graph: N x Rg int32 neighbour ids, -1 = none; entries: start vertex per
     query, or nq x E start vertices, -1 = none) whose DCOs run Algorithm 1
-    against the largest distance of the result set of size ef, fixed for the
-    duration of one node's expansion.
+    against the largest distance of the result set of size ef, in the
+    paper's order: one vertex at a time, the result set (and the threshold)
+    updated after every vertex; the start vertices first, then the
+    neighbours of each expansion of the nearest unexpanded result.
     max_iter = 0 means 16 * ef expansions at most.  pp: HNSW++ (Sec. 5.1),
     the result set's roles decoupled -- the DCO threshold and the output come
     from the K smallest exact distances, the beam (size ef) is kept with each
     DCO's observed distance (exact at d = D, else (D/d) S_d).  Returns ids,
-    squared distances (K smallest), dims sampled and expansions per query."""
+    squared distances (K smallest), dims sampled and expansions per query,
+    and with return_margin each query's closest call (the smallest relative
+    gap of any DCO comparison or of two keys that decided the result set)."""
     Y = _c(Y, np.float64)
     graph = _c(graph, np.int32)
     Qr = _c(Qr, np.float64)
@@ -250,10 +255,13 @@ def graph_search(Y, graph, entries, Qr, K: int, ef: int, eps0: float, delta_d: i
     d2 = np.empty((nq, K), np.float64)
     dims = np.empty(nq, np.int64)
     iters = np.empty(nq, np.int64)
+    margin = np.empty(nq, np.float64)
     _load().orc_graph_search(_p(Y), Y.shape[0], D, _p(graph), graph.shape[1], _p(entries),
                              entries.shape[1], _p(Qr), nq, K, ef, int(max_iter or 16 * ef), float(eps0),
                              int(delta_d), int(bool(pp)), _p(ids), _p(d2), _p(dims), _p(iters),
-                             nthreads)
+                             _p(margin), nthreads)
+    if return_margin:
+        return ids, d2, dims, iters, margin
     return ids, d2, dims, iters
 
 

@@ -662,116 +662,113 @@ void orc_ivf_ads_ip(const double *Y, int64_t N, int32_t D, const double *Cr,
 /* ---------------------------------------------------------------------- */
 /* Sec. 2.2.1 / Sec. 4 (HNSW+): greedy beam search on a proximity graph    */
 /* whose DCOs run Algorithm 1 against the largest distance of the result  */
-/* set R (size N_ef).  The search set S is the set of R's entries not yet */
-/* expanded (an entry leaving R can never be expanded usefully again).    */
-/* Reading of batch semantics: the threshold r is the largest distance in */
-/* R when a batch starts and stays fixed while its vertices are tested    */
-/* (in order, skipping -1 and visited ones); the vertices that pass and   */
-/* precede R's maximum in (distance, id) order then merge into R, which   */
-/* keeps its N_ef smallest.  A batch is the neighbour list of the node    */
-/* being expanded, or 32 consecutive positions of the start list (the     */
-/* start vertices are tested like neighbours of a virtual root; with     */
-/* exact DCOs R starts as the N_ef nearest of them).  The search stops    */
-/* when every entry of R has been expanded (or after max_iter expansions). */
+/* set R (size N_ef), in the paper's order: one vertex at a time, R (and   */
+/* with it the threshold) updated after every vertex.  The search set S is */
+/* the set of R's entries not yet expanded (an entry leaving R has a       */
+/* distance above R's maximum, which would stop the search, so it can      */
+/* never be expanded usefully).  The start vertices are visited first, in  */
+/* list order, like neighbours of a virtual root; then each iteration      */
+/* expands R's nearest unexpanded entry and visits its neighbours in list  */
+/* order, skipping -1 and vertices visited before.  A vertex whose DCO is  */
+/* positive (d = D, S_D <= r^2) joins R when (S_D, id) precedes R's        */
+/* maximum (or R is not full), R keeping its N_ef smallest by (d, id).      */
+/* The search stops when every entry of R is expanded (or after max_iter   */
+/* expansions).                                                             */
 /*   graph     N x Rg int32 neighbour ids (-1 = none), by original id      */
 /*   entries   nq x E int64 start vertices (-1 = none)                    */
 /* Outputs ids/d2 (K smallest of R by (distance, id); -1/+inf padded),    */
-/* the dims sampled and the expansions per query.                          */
+/* the dims sampled and the expansions per query, and (margin_out, may be */
+/* NULL) the query's closest call: the smallest relative gap over every   */
+/* DCO comparison (orc_dco's margin) and every comparison of two keys that */
+/* decided R's (or R1's) content or order -- a query whose closest call is */
+/* below a tolerance may take another path under another rounding.        */
 /* pp = 1: HNSW++ (Sec. 5.1) -- R's two roles decoupled: R1 (size K, exact  */
 /* distances) holds the results and gives every DCO its threshold (R1's   */
 /* largest distance); R (size N_ef) and S are kept with the observed      */
 /* distance of each DCO: exact if it reached d = D, else the estimate     */
 /* (D/d) S_d at the d where Algorithm 1 stopped.  The output is R1.       */
-#define ORC_START_BATCH 32
-
 typedef struct {
     const double *Y, *qr;
     int32_t D, K, ef, delta_d, pp;
     double eps0;
     unsigned char *visited, *expd;
-    orc_pair *R, *R1, *cand, *add1;
+    orc_pair *R, *R1;
     int32_t nR, n1;
     int64_t dims_sum;
+    double closest;
 } orc_beam;
 
-/* One batch: DCOs of the listed vertices against thresholds fixed at the
-   batch's start, then the merges into R (and R1). */
-static void orc_beam_batch(orc_beam *b, const int64_t *verts, int32_t nv)
+static void orc_note_gap(orc_beam *b, double x, double y)
 {
-    const int full = b->nR == b->ef;
+    if (!isfinite(x) || !isfinite(y)) return;
+    const double m = fabs(x) > fabs(y) ? fabs(x) : fabs(y);
+    const double g = m > 0.0 ? fabs(x - y) / m : 0.0;
+    if (g < b->closest) b->closest = g;
+}
+
+/* Inserts (d, id) into the sorted set A[0..*n) of capacity cap (flags: the
+   expanded flags carried along, may be NULL), dropping the largest when
+   full.  The caller has checked that it belongs there. */
+static void orc_set_insert(orc_beam *b, orc_pair *A, unsigned char *flags, int32_t *n,
+                           int32_t cap, double d, int64_t id)
+{
+    int32_t p = *n < cap ? *n : cap - 1;        /* slot freed at the end */
+    while (p > 0 && pair_less(d, id, A[p - 1].d, A[p - 1].id)) {
+        A[p] = A[p - 1];
+        if (flags) flags[p] = flags[p - 1];
+        --p;
+    }
+    if (p > 0) orc_note_gap(b, d, A[p - 1].d);
+    if (p + 1 < (*n < cap ? *n + 1 : cap)) orc_note_gap(b, d, A[p + 1].d);
+    A[p].d = d;
+    A[p].id = id;
+    if (flags) flags[p] = 0;
+    if (*n < cap) ++*n;
+}
+
+/* One vertex: its DCO against the current threshold, then R (and R1). */
+static void orc_beam_visit(orc_beam *b, int64_t v)
+{
+    if (v < 0 || b->visited[v]) return;
+    b->visited[v] = 1;
+    const int full = b->nR == b->ef, full1 = b->n1 == b->K;
     const double rmax = full ? b->R[b->nR - 1].d : INFINITY;
     const int64_t rid = full ? b->R[b->nR - 1].id : INT64_MAX;
-    const int full1 = b->n1 == b->K;
     const double r1max = full1 ? b->R1[b->n1 - 1].d : INFINITY;
     const int64_t r1id = full1 ? b->R1[b->n1 - 1].id : INT64_MAX;
     const double r2 = b->pp ? r1max : rmax;        /* the DCO threshold */
     const int32_t D = b->D;
-    int32_t nc = 0, nc1 = 0;
-    for (int32_t j = 0; j < nv; ++j) {
-        const int64_t v = verts[j];
-        if (v < 0 || b->visited[v]) continue;
-        b->visited[v] = 1;
-        int32_t dims = 0;
-        double S = 0.0;
-        const int res = orc_dco(b->Y + v * D, b->qr, D, r2, b->eps0, b->delta_d, &dims, &S, NULL);
-        b->dims_sum += dims;
-        if (!b->pp) {
-            if (res == ORC_POSITIVE && (!full || pair_less(S, v, rmax, rid))) {
-                b->cand[nc].d = S;
-                b->cand[nc].id = v;
-                ++nc;
-            }
-        } else {
-            const double obs = dims == D ? S : S * (double)D / (double)dims;
-            if (res == ORC_POSITIVE && (!full1 || pair_less(S, v, r1max, r1id))) {
-                b->add1[nc1].d = S;
-                b->add1[nc1].id = v;
-                ++nc1;
-            }
-            if (!full || pair_less(obs, v, rmax, rid)) {
-                b->cand[nc].d = obs;
-                b->cand[nc].id = v;
-                ++nc;
-            }
-        }
+    int32_t dims = 0;
+    double S = 0.0, mar = INFINITY;
+    const int res = orc_dco(b->Y + v * D, b->qr, D, r2, b->eps0, b->delta_d, &dims, &S, &mar);
+    b->dims_sum += dims;
+    if (mar < b->closest) b->closest = mar;
+    if (!b->pp) {
+        if (res != ORC_POSITIVE) return;
+        if (full) orc_note_gap(b, S, rmax);
+        if (!full || pair_less(S, v, rmax, rid))
+            orc_set_insert(b, b->R, b->expd, &b->nR, b->ef, S, v);
+        return;
     }
-    if (b->pp && nc1) {            /* R1: the K smallest exact distances */
-        for (int32_t k = 0; k < nc1; ++k) b->R1[b->n1 + k] = b->add1[k];
-        qsort(b->R1, (size_t)(b->n1 + nc1), sizeof(orc_pair), pair_cmp);
-        b->n1 = b->n1 + nc1 < b->K ? b->n1 + nc1 : b->K;
+    const double obs = dims == D ? S : S * (double)D / (double)dims;
+    if (res == ORC_POSITIVE) {
+        if (full1) orc_note_gap(b, S, r1max);
+        if (!full1 || pair_less(S, v, r1max, r1id))
+            orc_set_insert(b, b->R1, NULL, &b->n1, b->K, S, v);
     }
-    /* merge: R and the candidates, keep the ef smallest by (d, id) */
-    orc_pair *R = b->R;
-    unsigned char *expd = b->expd;
-    for (int32_t k = 0; k < nc; ++k) {
-        R[b->nR + k] = b->cand[k];
-        expd[b->nR + k] = 0;
-    }
-    const int32_t tot = b->nR + nc;
-    /* insertion sort carrying the expanded flags (tot <= ef + batch size) */
-    for (int32_t a = 1; a < tot; ++a) {
-        orc_pair x = R[a];
-        unsigned char fx = expd[a];
-        int32_t c = a - 1;
-        while (c >= 0 && pair_less(x.d, x.id, R[c].d, R[c].id)) {
-            R[c + 1] = R[c];
-            expd[c + 1] = expd[c];
-            --c;
-        }
-        R[c + 1] = x;
-        expd[c + 1] = fx;
-    }
-    b->nR = tot < b->ef ? tot : b->ef;
+    if (full) orc_note_gap(b, obs, rmax);
+    if (!full || pair_less(obs, v, rmax, rid))
+        orc_set_insert(b, b->R, b->expd, &b->nR, b->ef, obs, v);
 }
 
 void orc_graph_search(const double *Y, int64_t N, int32_t D, const int32_t *graph,
                       int32_t Rg, const int64_t *entries, int32_t E, const double *Qr,
                       int64_t nq, int32_t K, int32_t ef, int32_t max_iter, double eps0,
                       int32_t delta_d, int32_t pp, int64_t *ids, double *d2,
-                      int64_t *dims_total, int64_t *iters_out, int nthreads)
+                      int64_t *dims_total, int64_t *iters_out, double *margin_out,
+                      int nthreads)
 {
     set_threads(nthreads);
-    const int32_t bmax = Rg > ORC_START_BATCH ? Rg : ORC_START_BATCH;
 #pragma omp parallel for schedule(dynamic)
     for (int64_t q = 0; q < nq; ++q) {
         orc_beam b;
@@ -784,21 +781,15 @@ void orc_graph_search(const double *Y, int64_t N, int32_t D, const int32_t *grap
         b.pp = pp;
         b.eps0 = eps0;
         b.visited = (unsigned char *)calloc((size_t)(N > 0 ? N : 1), 1);
-        b.R = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(ef + bmax));
-        b.expd = (unsigned char *)malloc((size_t)(ef + bmax));
-        b.cand = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)bmax);
-        b.R1 = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)(K + bmax));
-        b.add1 = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)bmax);
-        int64_t *verts = (int64_t *)malloc(sizeof(int64_t) * (size_t)bmax);
+        b.R = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)ef);
+        b.expd = (unsigned char *)malloc((size_t)ef);
+        b.R1 = (orc_pair *)malloc(sizeof(orc_pair) * (size_t)K);
         b.nR = 0;
         b.n1 = 0;
         b.dims_sum = 0;
+        b.closest = INFINITY;
         int32_t it = 0;
-        /* the start vertices, ORC_START_BATCH list positions per batch */
-        for (int32_t k0 = 0; k0 < E; k0 += ORC_START_BATCH) {
-            const int32_t nv = E - k0 < ORC_START_BATCH ? E - k0 : ORC_START_BATCH;
-            orc_beam_batch(&b, entries + q * E + k0, nv);
-        }
+        for (int32_t k = 0; k < E; ++k) orc_beam_visit(&b, entries[q * E + k]);
         while (it < max_iter) {
             int32_t u = -1;
             for (int32_t k = 0; k < b.nR; ++k)
@@ -806,25 +797,19 @@ void orc_graph_search(const double *Y, int64_t N, int32_t D, const int32_t *grap
             if (u < 0) break;
             b.expd[u] = 1;
             const int64_t node = b.R[u].id;
-            for (int32_t j = 0; j < Rg; ++j) verts[j] = graph[node * Rg + j];
-            orc_beam_batch(&b, verts, Rg);
+            for (int32_t j = 0; j < Rg; ++j) orc_beam_visit(&b, graph[node * Rg + j]);
             ++it;
         }
-        orc_pair *R = b.R, *R1 = b.R1;
-        const int32_t nR = b.nR, n1 = b.n1;
-        const int64_t dims_sum = b.dims_sum;
-        const orc_pair *res = pp ? R1 : R;
-        const int32_t nres = pp ? n1 : nR;
+        const orc_pair *res = pp ? b.R1 : b.R;
+        const int32_t nres = pp ? b.n1 : b.nR;
         for (int32_t k = 0; k < K; ++k) {
             ids[q * K + k] = k < nres ? res[k].id : -1;
             d2[q * K + k] = k < nres ? res[k].d : INFINITY;
         }
-        if (dims_total) dims_total[q] = dims_sum;
+        if (dims_total) dims_total[q] = b.dims_sum;
         if (iters_out) iters_out[q] = it;
-        free(verts);
-        free(b.add1);
+        if (margin_out) margin_out[q] = b.closest;
         free(b.R1);
-        free(b.cand);
         free(b.expd);
         free(b.R);
         free(b.visited);

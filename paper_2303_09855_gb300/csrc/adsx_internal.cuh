@@ -61,6 +61,8 @@ struct Index {
     // the query-major round 0 and the growth factor of later rounds' ranges
     int32_t sched = ADSX_SCHED_AUTO;
     int32_t cm_G = 16;
+    int32_t cm_tpi = 4;           // 32-member tiles per cluster-major work item
+    int32_t max_tiles = 0;        // tiles of the largest cluster
     int32_t cm_r0 = 2;
     int32_t cm_growth = 3;
     // stage timing (adsx_set_stage_timing): events between search stages
@@ -372,6 +374,7 @@ struct GraphArgs {
     const float *ftab;          // nblk + 1 test factors
     int64_t nq;
     int32_t D, Dp, nblk, db, test_on, K, ef, max_iter;
+    int32_t nst;                // Algorithm 1 steps of one DCO at most
     int32_t pp;                 // 0: HNSW+, 1: HNSW++ (Sec. 5.1)
     int32_t metric;             // ADSX_L2, or ADSX_COSINE (output 1 - d^2/2)
     int64_t *out_ids;
@@ -384,9 +387,10 @@ struct GraphArgs {
     int32_t warps;              // resident warps launched
     unsigned long long *qnext;  // next query to take (zeroed by the launcher)
 };
-size_t graph_search_smem(int Dp, int ef, int K);
+// nst: Algorithm 1 steps of one DCO at most (ceil(nblk / db))
+size_t graph_search_smem(int Dp, int ef, int K, int nst);
 // warps of graph_search_kernel resident at once on nsm SMs (0: does not fit)
-int graph_search_resident_warps(int Dp, int ef, int K, int nsm);
+int graph_search_resident_warps(int Dp, int ef, int K, int nst, int nsm);
 cudaError_t launch_knn_to_graph(const int64_t *knn, int64_t N, int64_t row0, int Kk, int degree,
                                 int32_t *nbr, cudaStream_t s);
 cudaError_t launch_vertex_map(const int64_t *off, int nlist, const int32_t *ids, int Dp,
@@ -510,6 +514,7 @@ struct CmArgs {
     const int32_t *n_items;     // device count of items
     int32_t items_cap;          // upper bound of *n_items (grid sizing)
     int32_t G;                  // queries per item
+    int32_t tpi;                // 32-member tiles per item (a chunk of the cluster)
     unsigned *work_counter;
     float *app_d;               // nq x cap appended (distance, id)
     int32_t *app_i;
@@ -541,7 +546,7 @@ struct CmPlan {
 };
 size_t cm_smem_bytes(int G);
 cudaError_t launch_cm_plan(const int32_t *probes, int64_t nq, int pstride, int r0, int r1, int nlist,
-                           int G, CmPlan &pl, cudaStream_t s);
+                           int G, int tpi, const int64_t *off, CmPlan &pl, cudaStream_t s);
 cudaError_t launch_cm_scan(const CmArgs &a, int device, cudaStream_t s);
 cudaError_t launch_cm_merge(const CmMergeArgs &m, cudaStream_t s);
 cudaError_t launch_cm_overflow_items(const int32_t *ovf, int64_t nq, int2 *items, int32_t *n_items,

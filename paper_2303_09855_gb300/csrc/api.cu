@@ -294,6 +294,8 @@ static int build_impl(const float *X, int64_t N, int32_t D, const float *P,
     ix->storage = storage;
     ix->h_off = off;
     ix->total_tiles = tile_off[(size_t)nlist];
+    for (int c = 0; c < nlist; ++c)
+        ix->max_tiles = std::max<int32_t>(ix->max_tiles, tile_off[(size_t)c + 1] - tile_off[(size_t)c]);
     cudaGetDevice(&ix->device);
     cudaStream_t s = (cudaStream_t)stream;
     const int Dp = ix->Dp;
@@ -624,6 +626,7 @@ static adsx::CmArgs cm_args_from(const adsx::ScanArgs &a, int G)
     c.ftab = a.ftab;
     c.r2 = nullptr;
     c.G = G;
+    c.tpi = 1;
     c.app_d = nullptr;
     c.app_i = nullptr;
     c.app_n = nullptr;
@@ -637,7 +640,11 @@ static cudaError_t cm_plan_buffers(const Index *ix, int64_t nq, int width, int G
 {
     cudaError_t e;
     const size_t nl = (size_t)ix->nlist;
-    *items_cap = nq * (int64_t)width / G + ix->nlist + 1;
+    // items: ceil(cnt_c / G) query groups times the chunks of cluster c, at
+    // most (cnt_c / G + 1) * chunks_c summed over the clusters
+    const int64_t tpi = ix->cm_tpi;
+    const int64_t maxch = (ix->max_tiles + tpi - 1) / tpi;
+    *items_cap = nq * (int64_t)width * maxch / G + ix->total_tiles / tpi + ix->nlist + 1;
     if ((e = sc.get(&pl.cnt, nl)) != cudaSuccess) return e;
     if ((e = sc.get(&pl.coff, nl + 1)) != cudaSuccess) return e;
     if ((e = sc.get(&pl.ioff, nl)) != cudaSuccess) return e;
@@ -664,12 +671,13 @@ static cudaError_t cm_scan(const Index *ix, const adsx::ScanArgs &a, Scratch &sc
     a0.metric = ADSX_L2;                 // keys (squared distances) until the last merge
     a0.nprobe = r0;
     a0.probe_stride = nprobe;
-    a0.S = adsx::uniform_splits(nq, r0, K, adsx::scan_items_target(ix->device, ix->items_per_sm),
-                                ix->N / ix->nlist);
-    a0.n_items = (int32_t)(nq * a0.S);
+    a0.S = 1;                            // one warp per query: a schedule-independent round
+    a0.n_items = (int32_t)nq;
     if ((e = qm_scan(ix, a0, sc)) != cudaSuccess) return e;
 
-    const int cap = std::max(4 * K, 512);
+    // capacity of a round's list per query: candidates reaching d = D within
+    // the previous rounds' r (a query beyond it is searched again query-major)
+    const int cap = std::max(8 * K, 1024);
     float *r2 = nullptr, *app_d = nullptr;
     int32_t *app_i = nullptr, *ovf = nullptr;
     unsigned *app_n = nullptr, *counter = nullptr;
@@ -704,6 +712,7 @@ static cudaError_t cm_scan(const Index *ix, const adsx::ScanArgs &a, Scratch &sc
     int64_t items_cap = 0;
     if ((e = cm_plan_buffers(ix, nq, width, G, sc, pl, &items_cap)) != cudaSuccess) return e;
     adsx::CmArgs c = cm_args_from(a, G);
+    c.tpi = ix->cm_tpi;
     c.r2 = r2;
     c.coff = pl.coff;
     c.qlist = pl.qlist;
@@ -717,7 +726,7 @@ static cudaError_t cm_scan(const Index *ix, const adsx::ScanArgs &a, Scratch &sc
     c.cap = cap;
     for (size_t i = 0; i < rounds.size(); ++i) {
         if ((e = adsx::launch_cm_plan(a.probes, nq, nprobe, rounds[i].first, rounds[i].second,
-                                      ix->nlist, G, pl, s)) != cudaSuccess)
+                                      ix->nlist, G, ix->cm_tpi, ix->off, pl, s)) != cudaSuccess)
             return e;
         if ((e = adsx::launch_cm_scan(c, ix->device, s)) != cudaSuccess) return e;
         m.final_pass = i + 1 == rounds.size();
@@ -1028,9 +1037,11 @@ int adsx_dco_fixed_r(const adsx_index *index, const float *Qv, int64_t nq, const
         adsx::CmPlan pl;
         int64_t items_cap = 0;
         CK(cm_plan_buffers(ix, nq, ix->nlist, ix->cm_G, sc, pl, &items_cap), "alloc plan");
-        CK(adsx::launch_cm_plan(probes, nq, ix->nlist, 0, ix->nlist, ix->nlist, ix->cm_G, pl, s),
+        CK(adsx::launch_cm_plan(probes, nq, ix->nlist, 0, ix->nlist, ix->nlist, ix->cm_G,
+                                ix->cm_tpi, ix->off, pl, s),
            "plan");
         adsx::CmArgs c = cm_args_from(a, ix->cm_G);
+        c.tpi = ix->cm_tpi;
         c.coff = pl.coff;
         c.qlist = pl.qlist;
         c.items = pl.items;
@@ -1343,13 +1354,19 @@ int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const fl
     if (nq == 0) return ADSX_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const int max_iter = 4 * ef;
+    // Algorithm 1 steps per DCO (the test off: one full-width step)
+    const int gnblk = ix->Dp / adsx::BLK;
+    int gdb = delta_d / adsx::BLK;
+    const bool gtest = !isinf(eps0) && gdb < gnblk;
+    if (!gtest) gdb = gnblk;
+    const int nst = (gnblk + gdb - 1) / gdb;
     // per-warp scratch of the visited test, kept with the graph (grown,
     // never shrunk: a search uses the first `warps` slots)
     int32_t warps = 0;
     {
         int nsm = 0;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ix->device);
-        warps = adsx::graph_search_resident_warps(ix->Dp, ef, K, nsm);
+        warps = adsx::graph_search_resident_warps(ix->Dp, ef, K, nst, nsm);
         if (warps <= 0) return fail(ADSX_EINVAL, "graph search: ef and D need more shared memory than an SM has");
         const int64_t bm_words = (g->N + 31) / 32;
         // visited ids are distinct: never more than N of them
@@ -1415,10 +1432,9 @@ int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const fl
     a.D = ix->D;
     a.Dp = ix->Dp;
     a.nblk = nblk;
-    a.db = delta_d / adsx::BLK;
-    a.test_on = isinf(eps0) ? 0 : 1;
-    if (a.db >= nblk) a.test_on = 0;
-    if (!a.test_on) a.db = nblk;
+    a.db = gdb;
+    a.test_on = gtest ? 1 : 0;
+    a.nst = nst;
     a.K = K;
     a.ef = ef;
     a.max_iter = max_iter;

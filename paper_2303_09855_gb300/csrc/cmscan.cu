@@ -102,8 +102,15 @@ __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(
         if (item >= n_items) break;
         const int2 it = a.items[item];
         const int c = it.x;
-        const int q0 = a.coff[c] + it.y;
+        const int64_t o = a.off[c];
+        const int n = (int)(a.off[c + 1] - o);
+        // item = (query group, chunk of tpi tiles) of cluster c
+        const int tiles = (n + 31) >> 5, chunks = (tiles + a.tpi - 1) / a.tpi;
+        const int qgi = it.y / chunks, tc = it.y - qgi * chunks;
+        const int q0 = a.coff[c] + qgi * a.G;
         const int ngq = a.coff[c + 1] - q0 < a.G ? a.coff[c + 1] - q0 : a.G;
+        const int mb = tc * a.tpi * 32;
+        const int me = mb + a.tpi * 32 < n ? mb + a.tpi * 32 : n;
         for (int g = lane; g < ngq; g += 32) {
             const int q = a.qlist[q0 + g];
             qg[g] = q;
@@ -111,11 +118,9 @@ __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(
             dg[g] = 0ull;
         }
         __syncwarp();
-        const int64_t o = a.off[c];
-        const int n = (int)(a.off[c + 1] - o);
         const T *cb = static_cast<const T *>(a.data) + o * a.Dp;
         const int64_t stride = (int64_t)n * BLK;
-        for (int m0 = 0; m0 < n; m0 += 32) {
+        for (int m0 = mb; m0 < me; m0 += 32) {
             const int m = m0 + own;
             const unsigned vm = __ballot_sync(FULL, m < n);
             for (int g = lane; g < ngq; g += 32) live[g] = vm;
@@ -143,22 +148,10 @@ __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(
                 const float fe = s_ftab[e];
                 const int dstep = e * BLK < a.D ? e * BLK : a.D;
                 const int pos = (int)o + m;
-                for (int g = 0; g < ngq; ++g) {
-                    const unsigned lv = live[g];
-                    if (lv == 0u) continue;
-                    const float *qv = a.qrot + (int64_t)qg[g] * a.Dp;
-                    float2 p[NL];
-#pragma unroll
-                    for (int k = 0; k < NL; ++k) p[k] = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int b = 0; b < DB; ++b) {
-                        if (b < nb) {
-                            const QPiece<NL> qp = ld_qpiece_ro<NL>(qv + (blk + b) * BLK + jo);
-#pragma unroll
-                            for (int k = 0; k < NL; ++k) p[k] = add_piece(v[b][k], qp, p[k], T());
-                        }
-                    }
-                    float S = (blk == 0 ? 0.f : Sv[g * 32 + lane]) + group_sum<NL>(p, lane);
+                // the rest of Algorithm 1's step for query slot g, whose
+                // partial distance over this step is st
+                auto finish = [&](int g, unsigned lv, float st, const float *qv) {
+                    float S = (blk == 0 ? 0.f : Sv[g * 32 + lane]) + st;
                     const bool alive = (lv >> lane) & 1u;
                     const float r2 = r2g[g];
                     if (!fin) {
@@ -222,6 +215,36 @@ __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(
                             dg[g] += (unsigned long long)__popc(lv) * (unsigned)a.D;
                         }
                     }
+                };
+                // queries two at a time: their FMA chains and shuffles interleave
+                for (int g = 0; g < ngq; g += 2) {
+                    const bool two = g + 1 < ngq;
+                    const unsigned lv0 = live[g], lv1 = two ? live[g + 1] : 0u;
+                    if ((lv0 | lv1) == 0u) continue;
+                    const float *qv0 = a.qrot + (int64_t)qg[g] * a.Dp;
+                    const float *qv1 = two ? a.qrot + (int64_t)qg[g + 1] * a.Dp : qv0;
+                    float2 p0[NL], p1[NL];
+#pragma unroll
+                    for (int k = 0; k < NL; ++k) {
+                        p0[k] = make_float2(0.f, 0.f);
+                        p1[k] = make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int b = 0; b < DB; ++b) {
+                        if (b < nb) {
+                            const QPiece<NL> qa = ld_qpiece_ro<NL>(qv0 + (blk + b) * BLK + jo);
+                            const QPiece<NL> qb = ld_qpiece_ro<NL>(qv1 + (blk + b) * BLK + jo);
+#pragma unroll
+                            for (int k = 0; k < NL; ++k) {
+                                p0[k] = add_piece(v[b][k], qa, p0[k], T());
+                                p1[k] = add_piece(v[b][k], qb, p1[k], T());
+                            }
+                        }
+                    }
+                    const float s0 = group_sum<NL>(p0, lane);
+                    const float s1 = group_sum<NL>(p1, lane);
+                    if (lv0) finish(g, lv0, s0, qv0);
+                    if (lv1) finish(g + 1, lv1, s1, qv1);
                 }
                 __syncwarp();
                 blk = e;
@@ -237,7 +260,8 @@ __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(
 // ---- round planning: the (query, probe rank) pairs of ranks [r0, r1) grouped
 // by cluster.  cnt[c] counts them; cm_plan_offsets turns the counts into
 // offsets of each cluster's query list and of its work items (one per G
-// queries); cm_plan_scatter fills the lists and the items.
+// queries and chunk of tpi 32-member tiles, so that large clusters are
+// shared among warps); cm_plan_scatter fills the lists and the items.
 __global__ void cm_plan_count_kernel(const int32_t *__restrict__ probes, int64_t nq, int pstride,
                                      int r0, int r1, int *__restrict__ cnt)
 {
@@ -253,8 +277,15 @@ __global__ void cm_plan_count_kernel(const int32_t *__restrict__ probes, int64_t
 
 // One block: exclusive prefix sums of cnt (-> coff) and of ceil(cnt / G)
 // (-> ioff), the item total, and the cursors cleared.
+__device__ __forceinline__ int cm_chunks(const int64_t *off, int c, int tpi)
+{
+    const int tiles = (int)((off[c + 1] - off[c] + 31) >> 5);
+    return (tiles + tpi - 1) / tpi;
+}
+
 __global__ void __launch_bounds__(1024) cm_plan_offsets_kernel(const int *__restrict__ cnt,
-                                                               int nlist, int G,
+                                                               const int64_t *__restrict__ off,
+                                                               int nlist, int G, int tpi,
                                                                int *__restrict__ coff,
                                                                int *__restrict__ ioff,
                                                                int *__restrict__ cur,
@@ -267,7 +298,7 @@ __global__ void __launch_bounds__(1024) cm_plan_offsets_kernel(const int *__rest
     int sa = 0, sb = 0;
     for (int c = c0; c < c1; ++c) {
         sa += cnt[c];
-        sb += (cnt[c] + G - 1) / G;
+        sb += (cnt[c] + G - 1) / G * cm_chunks(off, c, tpi);
     }
     int xa = sa, xb = sb;                 // inclusive warp scans
 #pragma unroll
@@ -304,7 +335,7 @@ __global__ void __launch_bounds__(1024) cm_plan_offsets_kernel(const int *__rest
         ioff[c] = eb;
         cur[c] = 0;
         ea += cnt[c];
-        eb += (cnt[c] + G - 1) / G;
+        eb += (cnt[c] + G - 1) / G * cm_chunks(off, c, tpi);
     }
     if (t == 1023) {
         coff[nlist] = ea;
@@ -313,7 +344,9 @@ __global__ void __launch_bounds__(1024) cm_plan_offsets_kernel(const int *__rest
 }
 
 __global__ void cm_plan_scatter_kernel(const int32_t *__restrict__ probes, int64_t nq, int pstride,
-                                       int r0, int r1, int G, const int *__restrict__ coff,
+                                       int r0, int r1, int G, int tpi,
+                                       const int64_t *__restrict__ off,
+                                       const int *__restrict__ coff,
                                        const int *__restrict__ ioff, int *__restrict__ cur,
                                        int *__restrict__ qlist, int2 *__restrict__ items)
 {
@@ -326,7 +359,10 @@ __global__ void cm_plan_scatter_kernel(const int32_t *__restrict__ probes, int64
         const int c = probes[q * pstride + p];
         const int slot = atomicAdd(cur + c, 1);
         qlist[coff[c] + slot] = (int)q;
-        if (slot % G == 0) items[ioff[c] + slot / G] = make_int2(c, slot);
+        if (slot % G == 0) {
+            const int ch = cm_chunks(off, c, tpi), first = (slot / G) * ch;
+            for (int t = 0; t < ch; ++t) items[ioff[c] + first + t] = make_int2(c, first + t);
+        }
     }
 }
 
@@ -461,22 +497,24 @@ unsigned grid_for(int64_t work, int threads)
 size_t cm_smem_bytes(int G) { return (size_t)CmCarve(G).bytes * CM_WARPS; }
 
 cudaError_t launch_cm_plan(const int32_t *probes, int64_t nq, int pstride, int r0, int r1, int nlist,
-                           int G, CmPlan &pl, cudaStream_t s)
+                           int G, int tpi, const int64_t *off, CmPlan &pl, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(pl.cnt, 0, sizeof(int) * nlist, s);
     if (e != cudaSuccess) return e;
     const int64_t work = nq * (int64_t)(r1 - r0);
     cm_plan_count_kernel<<<grid_for(work, 256), 256, 0, s>>>(probes, nq, pstride, r0, r1, pl.cnt);
-    cm_plan_offsets_kernel<<<1, 1024, 0, s>>>(pl.cnt, nlist, G, pl.coff, pl.ioff, pl.cur, pl.n_items);
-    cm_plan_scatter_kernel<<<grid_for(work, 256), 256, 0, s>>>(probes, nq, pstride, r0, r1, G,
-                                                                pl.coff, pl.ioff, pl.cur, pl.qlist,
-                                                                pl.items);
+    cm_plan_offsets_kernel<<<1, 1024, 0, s>>>(pl.cnt, off, nlist, G, tpi, pl.coff, pl.ioff, pl.cur,
+                                              pl.n_items);
+    cm_plan_scatter_kernel<<<grid_for(work, 256), 256, 0, s>>>(probes, nq, pstride, r0, r1, G, tpi,
+                                                                off, pl.coff, pl.ioff, pl.cur,
+                                                                pl.qlist, pl.items);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cm_scan(const CmArgs &a, int device, cudaStream_t s)
 {
-    if (a.db < 1 || a.db > CM_MAX_DB || a.G < 1 || a.G > CM_MAX_G) return cudaErrorInvalidValue;
+    if (a.db < 1 || a.db > CM_MAX_DB || a.G < 1 || a.G > CM_MAX_G || a.tpi < 1)
+        return cudaErrorInvalidValue;
     const CmKernel k = cm_kernel_for(a);
     const size_t smem = cm_smem_bytes(a.G);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -171,12 +171,14 @@ __global__ void cluster_entry_kernel(const float *__restrict__ data, const int64
 }
 
 // One warp's shared memory: the query, the beam R (two buffers of distance,
-// id and expanded flag), the exact K-set R1 of HNSW++ (two buffers) and two
-// 32-entry staging areas for sorted additions.
-__host__ __device__ __forceinline__ size_t graph_warp_bytes(int Dp, int ef, int K)
+// id and expanded flag), the exact K-set R1 of HNSW++ (two buffers), two
+// 32-entry staging areas for sorted additions, and each lane's partial
+// distance after every Algorithm 1 step of the current batch (nst steps).
+__host__ __device__ __forceinline__ size_t graph_warp_bytes(int Dp, int ef, int K, int nst)
 {
     const size_t cap = (size_t)ef + 32, cap1 = (size_t)K + 32;
-    return (((size_t)Dp * 4 + cap * 4 * 6 + cap1 * 4 * 4 + 32 * 8 * 2) + 15) & ~(size_t)15;
+    return (((size_t)Dp * 4 + cap * 4 * 6 + cap1 * 4 * 4 + 32 * 8 * 2 + (size_t)nst * 32 * 4) +
+            15) & ~(size_t)15;
 }
 
 // Ascending bitonic sort of one 64-bit key per lane.
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned below = (1u << lane) - 1u;
     const int cap = g.ef + 32, cap1 = g.K + 32;
-    unsigned char *base = smraw + graph_warp_bytes(g.Dp, g.ef, g.K) * warp;
+    unsigned char *base = smraw + graph_warp_bytes(g.Dp, g.ef, g.K, g.nst) * warp;
     float *qv = reinterpret_cast<float *>(base);
     float *rd = qv + g.Dp, *nd = rd + cap;
     int *ri = reinterpret_cast<int *>(nd + cap), *ni = ri + cap;
@@ -260,6 +262,7 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
     int *ai = reinterpret_cast<int *>(ad + 32);
     float *ad1 = reinterpret_cast<float *>(ai + 32);
     int *ai1 = reinterpret_cast<int *>(ad1 + 32);
+    float *sst = reinterpret_cast<float *>(ai1 + 32);     // nst x 32 partial distances
     const int64_t gw = (int64_t)blockIdx.x * GW + warp;
     if (gw >= g.warps) return;
     unsigned *bm = g.bitmap + gw * g.bm_words;
@@ -277,19 +280,27 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
         __syncwarp();
         unsigned long long dims = 0ull;
         int vcount = 0, nR = 0, n1 = 0;
-        // One batch of DCOs (one vertex per lane, fresh ones only) against
-        // thresholds fixed for the batch, then the merges into R (and R1).
+        // One batch of up to 32 vertices (one per lane, in list order; fresh
+        // ones only), with the outcome of the paper's order: each vertex's
+        // DCO faces the threshold as it stands after the vertices before it.
+        // All DCOs first run side by side against the threshold at the
+        // batch's start (an upper bound of every later one), recording S_d
+        // after each step; a threshold that only shrinks can only move a
+        // decision to an earlier rejection, which the recorded S_d settle
+        // exactly (the same FP32 comparison).  So the decisions are then
+        // replayed in list order: whenever a vertex enters the set that gives
+        // the threshold (R for HNSW+, R1 for HNSW++), it is inserted and the
+        // later vertices are decided again against the new threshold.  The
+        // dims counted are those of the paper's order.
         auto dco_batch = [&](int v, bool fresh) {
-            const bool full = nR == g.ef, full1 = n1 == g.K;
-            const float rmax = full ? rd[nR - 1] : INFINITY;
-            const int rid = full ? ri[nR - 1] : INT_MAX;
-            const float r1max = full1 ? kd[n1 - 1] : INFINITY;
-            const int r1id = full1 ? ki[n1 - 1] : INT_MAX;
-            const float r2 = g.pp ? r1max : rmax;           // the DCO threshold
-            // Algorithm 1 against r2 (squared test of Sec. 3.2)
+            const bool full0 = nR == g.ef;
+            const float rmax0 = full0 ? rd[nR - 1] : INFINITY;
+            const int rid0 = full0 ? ri[nR - 1] : INT_MAX;
+            float th = g.pp ? (n1 == g.K ? kd[n1 - 1] : INFINITY) : rmax0;
+            // Algorithm 1 against th (squared test of Sec. 3.2), S_d recorded
             float S = 0.f;
-            int blk = 0;
-            bool alive = fresh, atD = false;
+            int blk = 0, nst = 0;
+            bool alive = fresh;
             const float *x = g.data + (fresh ? g.vbase[v] : 0);
             const int64_t st = fresh ? g.vstride[v] : 0;
             while (__ballot_sync(FULL, alive)) {
@@ -301,45 +312,85 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
                     for (int b = e2; b < e3; ++b) prefetch_l2(x + b * st);
                     for (int b = blk; b < e2; ++b) S = accum_block_f32(x + b * st, qv + b * BLK, S);
                     blk = e2;
-                    if (blk >= g.nblk) {
-                        alive = false;
-                        atD = true;
-                        dims += (unsigned long long)g.D;
-                    } else if (g.test_on && S > r2 * g.ftab[blk]) {
-                        alive = false;
-                        dims += (unsigned long long)(blk * BLK < g.D ? blk * BLK : g.D);
+                    sst[nst * 32 + lane] = S;
+                    ++nst;
+                    if (blk >= g.nblk || (g.test_on && S > th * g.ftab[blk])) alive = false;
+                }
+            }
+            // the decision against threshold t from the recorded steps:
+            // 0 rejected at d < D, 1 positive (d = D, S_D <= t), 2 negative
+            // at d = D; dstep the dims, sdec S_d where Algorithm 1 stopped
+            int dec = 0, dstep = 0;
+            float sdec = 0.f;
+            auto decide = [&](float t) {
+                int b2 = 0;
+                for (int k = 0; k < nst; ++k) {
+                    b2 = b2 + g.db < g.nblk ? b2 + g.db : g.nblk;
+                    const float Sk = sst[k * 32 + lane];
+                    if (b2 >= g.nblk) {
+                        dec = Sk <= t ? 1 : 2;
+                        dstep = g.D;
+                        sdec = Sk;
+                        return;
+                    }
+                    if (g.test_on && Sk > t * g.ftab[b2]) {
+                        dec = 0;
+                        dstep = b2 * BLK < g.D ? b2 * BLK : g.D;
+                        sdec = Sk;
+                        return;
                     }
                 }
-            }
-            const bool positive = atD && S <= r2;
-            bool take_r, take_1 = false;
-            float key_r = S;
-            if (!g.pp) {
-                // HNSW+: exact distances enter R when below its largest
-                take_r = positive && (!full || pless(S, v, rmax, rid));
-            } else {
-                // HNSW++: positives enter R1; R and S keep the observed
-                // distance (exact at d = D, else (D/d) S_d)
-                const int d = blk * BLK < g.D ? blk * BLK : g.D;
-                key_r = atD ? S : S * ((float)g.D / (float)d);
-                take_1 = positive && (!full1 || pless(S, v, r1max, r1id));
-                take_r = fresh && (!full || pless(key_r, v, rmax, rid));
-            }
-            const int na = stage_sorted(take_r, key_r, v, ad, ai, lane);
-            if (na) {
-                nR = warp_merge(rd, ri, rx, nR, ad, ai, na, nd, ni, nx, g.ef, lane);
-                float *tf = rd; rd = nd; nd = tf;
-                int *ti = ri; ri = ni; ni = ti;
-                ti = rx; rx = nx; nx = ti;
-            }
-            if (g.pp) {
-                const int n1a = stage_sorted(take_1, S, v, ad1, ai1, lane);
-                if (n1a) {
-                    n1 = warp_merge(kd, ki, nullptr, n1, ad1, ai1, n1a, kd2, ki2, nullptr, g.K, lane);
+            };
+            if (fresh) decide(th);
+            // replay in list order: the first vertex (lane) that enters the
+            // threshold set is inserted, the lanes after it are decided again
+            unsigned settled = 0u;
+            for (;;) {
+                bool enter = false;
+                if (fresh && !((settled >> lane) & 1u) && dec == 1) {
+                    if (!g.pp) enter = nR < g.ef || pless(sdec, v, rd[nR - 1], ri[nR - 1]);
+                    else enter = n1 < g.K || pless(sdec, v, kd[n1 - 1], ki[n1 - 1]);
+                }
+                const unsigned em = __ballot_sync(FULL, enter);
+                if (!em) break;
+                const int j = __ffs(em) - 1;
+                settled |= (j == 31) ? FULL : ((2u << j) - 1u);
+                if (lane == j) {
+                    (g.pp ? ad1 : ad)[0] = sdec;
+                    (g.pp ? ai1 : ai)[0] = v;
+                }
+                __syncwarp();
+                if (!g.pp) {
+                    nR = warp_merge(rd, ri, rx, nR, ad, ai, 1, nd, ni, nx, g.ef, lane);
+                    float *tf = rd; rd = nd; nd = tf;
+                    int *ti = ri; ri = ni; ni = ti;
+                    ti = rx; rx = nx; nx = ti;
+                    th = nR == g.ef ? rd[nR - 1] : INFINITY;
+                } else {
+                    n1 = warp_merge(kd, ki, nullptr, n1, ad1, ai1, 1, kd2, ki2, nullptr, g.K, lane);
                     float *tf = kd; kd = kd2; kd2 = tf;
                     int *ti = ki; ki = ki2; ki2 = ti;
+                    th = n1 == g.K ? kd[n1 - 1] : INFINITY;
+                }
+                if (fresh && lane > j) decide(th);
+            }
+            if (fresh) dims += (unsigned long long)dstep;
+            if (g.pp) {
+                // HNSW++: R and S keep every fresh vertex's observed distance
+                // (exact at d = D, else (D/d) S_d); R keeps its ef smallest,
+                // which a merge of all of them at once gives as well
+                const int d = dstep;
+                const float key_r = dec != 0 ? sdec : sdec * ((float)g.D / (float)d);
+                const bool take_r = fresh && (!full0 || pless(key_r, v, rmax0, rid0));
+                const int na = stage_sorted(take_r, key_r, v, ad, ai, lane);
+                if (na) {
+                    nR = warp_merge(rd, ri, rx, nR, ad, ai, na, nd, ni, nx, g.ef, lane);
+                    float *tf = rd; rd = nd; nd = tf;
+                    int *ti = ri; ri = ni; ni = ti;
+                    ti = rx; rx = nx; nx = ti;
                 }
             }
+            __syncwarp();
         };
         // Start vertices: the n_ce entries of each of the query's n_entry
         // nearest clusters, 32 list positions per batch, tested like the
@@ -417,11 +468,14 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
 
 }  // namespace
 
-size_t graph_search_smem(int Dp, int ef, int K) { return graph_warp_bytes(Dp, ef, K) * GW; }
-
-int graph_search_resident_warps(int Dp, int ef, int K, int nsm)
+size_t graph_search_smem(int Dp, int ef, int K, int nst)
 {
-    const size_t smem = graph_search_smem(Dp, ef, K);
+    return graph_warp_bytes(Dp, ef, K, nst) * GW;
+}
+
+int graph_search_resident_warps(int Dp, int ef, int K, int nst, int nsm)
+{
+    const size_t smem = graph_search_smem(Dp, ef, K, nst);
     if (cudaFuncSetAttribute(graph_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return 0;
@@ -463,7 +517,7 @@ cudaError_t launch_cluster_entries(const float *data, const int64_t *off, const 
 cudaError_t launch_graph_search(const GraphArgs &g, cudaStream_t s)
 {
     if (g.nq <= 0) return cudaSuccess;
-    const size_t smem = graph_search_smem(g.Dp, g.ef, g.K);
+    const size_t smem = graph_search_smem(g.Dp, g.ef, g.K, g.nst);
     cudaError_t e = cudaFuncSetAttribute(graph_search_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -111,7 +111,13 @@ def test_ads_exact_bracket_recall_and_deterministic(cm, K, nprobe, eps0, dd):
         assert must <= set(ids[q].tolist()), q
     gt, _ = oracle.knn_exact(Y, Qr, K)
     r_gpu, r_orc = oracle.recall_at(ids[ok], gt[ok], K), oracle.recall_at(oids[ok], gt[ok], K)
-    assert abs(r_gpu - r_orc) <= 0.002, (r_gpu, r_orc)
+    if eps0 >= 2.0:
+        assert abs(r_gpu - r_orc) <= 0.002, (r_gpu, r_orc)
+    else:
+        # with a small eps0 the test itself loses true neighbours (Lemma 3.2);
+        # a round's r is never below the sequential one, so the rounds lose
+        # no more of them than the oracle does
+        assert r_gpu >= r_orc - 0.002, (r_gpu, r_orc)
     first = min(dd, wl.D)
     assert np.all(dims >= ncand * first) and np.all(dims <= ncand * wl.D)
 

@@ -6,14 +6,17 @@ the same algorithm on the same (exported) graph and start vertices:
     equal the oracle's farthest-point samples, and where an FP32 near-tie
     let them part, each GPU entry is still a valid farthest-point step given
     the GPU's earlier ones;
-  - eps0 = inf (exact DCOs: HNSW's own search) and eps0 = 2.1, for HNSW+
-    and HNSW++ (Sec. 5.1): returned distances exact to 1e-5, no duplicates,
-    results identical to the oracle's for most queries (a beam search can
-    take another path after one FP32 near-tie), recall no worse than the
-    oracle's minus 0.02; HNSW++ with exact DCOs equals HNSW bit for bit;
+  - eps0 = inf (exact DCOs: HNSW's own search), eps0 = 2.1 and 1.0, for
+    HNSW+ and HNSW++ (Sec. 5.1), against the oracle's search in the paper's
+    sequential order (one vertex at a time, the threshold updated after
+    every vertex): the GPU tests a batch of 32 vertices side by side and then
+    replays the decisions in list order, so every query whose oracle run has
+    no comparison closer than 1e-5 relative returns the oracle's ids and
+    samples the oracle's dims exactly (the others, counted, are a small
+    minority); returned distances exact to 1e-5, no duplicates; HNSW++ with
+    exact DCOs equals HNSW bit for bit;
   - many entries per cluster (a small upper layer: 72 start vertices, more
-    than ef, tested 32 list positions at a time like an expansion's
-    neighbours) against the oracle given the same starts;
+    than ef) against the oracle given the same starts;
   - maximum sizes: ef = K = 512, 1024 start vertices (16 clusters x 64);
   - edge cases: fewer vertices than degree + 1 (padded neighbour lists),
     D not a multiple of 16, an empty cluster, more entries asked than a
@@ -34,6 +37,31 @@ from gpu_helpers import REL, kth_near_tie, near_tie_queries
 pytestmark = pytest.mark.gpu
 
 K, EF, NE, EPC = 10, 64, 3, 3
+
+
+def _match_sequential(ids, d2, dims, Y, Qr, oids, odims, margin, ok, min_frac=0.8):
+    """The GPU search replays each batch in list order, so it follows the
+    paper's sequential order (the oracle) exactly up to rounding: every
+    query whose probe set is not a near-tie and whose closest call in the
+    oracle (smallest relative gap of any comparison that decided the search)
+    is at least REL returns the oracle's ids and samples the oracle's number
+    of dims; the others are counted and must be a small minority.  Every
+    returned distance is exact and the ids of a query are distinct."""
+    good = ok & (margin >= REL)
+    for q in np.nonzero(good)[0]:
+        assert np.array_equal(ids[q], oids[q]), (q, ids[q], oids[q])
+        if dims is not None:
+            assert dims[q] == odims[q], (q, dims[q], odims[q])
+    for q in range(len(Qr)):
+        row = ids[q][ids[q] >= 0]
+        assert len(set(row.tolist())) == len(row), q
+        for i, d in zip(ids[q], d2[q]):
+            if i >= 0:
+                ex = float(np.sum((Y[i] - Qr[q]) ** 2))
+                assert abs(d - ex) <= REL * ex + 1e-6, (q, i, d, ex)
+    print("graph parity: %d of %d queries checked exactly (%d near a tie)"
+          % (int(good.sum()), len(good), int((~good).sum())))
+    assert good.mean() >= min_frac, good.mean()
 
 
 @pytest.fixture(scope="module")
@@ -89,32 +117,20 @@ def test_graph_lists_and_entries_match_oracle(gr):
     assert same >= 0.9 * wl.nlist
 
 
-@pytest.mark.parametrize("eps0,dd,pp,min_same", [(math.inf, 32, False, 0.95),
-                                                  (2.1, 32, False, 0.9), (2.1, 16, False, 0.9),
-                                                  (math.inf, 32, True, 0.95), (2.1, 32, True, 0.85)])
-def test_graph_search_matches_oracle(gr, eps0, dd, pp, min_same):
+@pytest.mark.parametrize("eps0,dd,pp", [(math.inf, 32, False), (2.1, 32, False), (2.1, 16, False),
+                                         (math.inf, 32, True), (2.1, 32, True), (1.0, 16, True)])
+def test_graph_search_matches_oracle(gr, eps0, dd, pp):
     adsx, wl, ix, g, Y, Cr, Qr, nbr, ent = gr
     ids, d2, dims = g.search(wl.Q, K, EF, eps0=eps0, delta_d=dd, return_dims=True, n_entry=NE,
                              decoupled=pp)
     probes, _ = oracle.probe(Cr, Qr, NE)
     starts = ent[probes].reshape(len(Qr), -1)
-    oids, od2, odims, iters = oracle.graph_search(Y, nbr, starts, Qr, K, EF, eps0, dd,
-                                                  max_iter=4 * EF, pp=pp)
+    oids, od2, odims, iters, margin = oracle.graph_search(Y, nbr, starts, Qr, K, EF, eps0, dd,
+                                                          max_iter=4 * EF, pp=pp,
+                                                          return_margin=True)
     ok = ~near_tie_queries(Cr, Qr, NE)
-    same = 0
-    for q in range(wl.Q.shape[0]):
-        row = ids[q][ids[q] >= 0]
-        assert len(set(row.tolist())) == len(row), q
-        for i, d in zip(ids[q], d2[q]):
-            if i >= 0:
-                ex = float(np.sum((Y[i] - Qr[q]) ** 2))
-                assert abs(d - ex) <= REL * ex + 1e-6, (q, i, d, ex)
-        assert np.all(np.diff(d2[q][ids[q] >= 0]) >= -1e-6 * (1 + d2[q][0]))
-        if ok[q] and np.array_equal(ids[q], oids[q]):
-            same += 1
-    assert same >= min_same * ok.sum(), (same, int(ok.sum()))
-    gt, _ = oracle.knn_exact(Y, Qr, K)
-    assert oracle.recall_at(ids, gt, K) >= oracle.recall_at(oids, gt, K) - 0.02
+    _match_sequential(ids, d2, dims, Y, Qr, oids, odims, margin, ok)
+    assert np.all(np.diff(np.where(ids >= 0, d2, np.inf), axis=1) >= -1e-6 * (1 + d2[:, :1]))
     if math.isfinite(eps0):
         _, _, fdims = g.search(wl.Q, K, EF, eps0=math.inf, return_dims=True, n_entry=NE)
         assert dims.sum() < fdims.sum()                      # early rejections happen
@@ -136,25 +152,17 @@ def test_graph_many_entries_match_oracle(gr, pp):
                                    n_entry=NE, decoupled=pp)
         probes, _ = oracle.probe(Cr, Qr, NE)
         starts = ent24[probes].reshape(len(Qr), -1)
-        oids, od2, odims, _ = oracle.graph_search(Y, nbr24, starts, Qr, K, ef, 2.1, 32,
-                                                  max_iter=4 * ef, pp=pp)
+        oids, od2, odims, _, margin = oracle.graph_search(Y, nbr24, starts, Qr, K, ef, 2.1, 32,
+                                                          max_iter=4 * ef, pp=pp,
+                                                          return_margin=True)
         ok = ~near_tie_queries(Cr, Qr, NE)
-        same = sum(1 for q in range(len(Qr)) if ok[q] and np.array_equal(ids[q], oids[q]))
-        assert same >= 0.85 * ok.sum(), (same, int(ok.sum()))
-        for q in range(len(Qr)):
-            for i, d in zip(ids[q], d2[q]):
-                if i >= 0:
-                    ex = float(np.sum((Y[i] - Qr[q]) ** 2))
-                    assert abs(d - ex) <= REL * ex + 1e-6, (q, i, d, ex)
-        assert np.array_equal(dims, odims) or abs(int(dims.sum()) - int(odims.sum())) <= 0.05 * odims.sum()
+        _match_sequential(ids, d2, dims, Y, Qr, oids, odims, margin, ok)
         # exact DCOs: every distinct start vertex costs D dims; ADSampling
         # rejects some of the later start batches early
         _, _, xdims = g24.search(wl.Q, K, ef, eps0=math.inf, return_dims=True, n_entry=NE,
                                  decoupled=pp)
         nstart = np.array([len(set(s[s >= 0].tolist())) for s in starts])
         assert np.all(xdims >= nstart * wl.D) and dims.sum() < xdims.sum()
-        gt, _ = oracle.knn_exact(Y, Qr, K)
-        assert oracle.recall_at(ids, gt, K) >= oracle.recall_at(oids, gt, K) - 0.02
     finally:
         g24.close()
 
@@ -238,11 +246,14 @@ def test_graph_cosine_matches_oracle(gr, pp):
                                   n_entry=NE, decoupled=pp)
         probes, _ = oracle.probe(Cn, Qn, NE)
         starts = entc[probes].reshape(len(Qn), -1)
-        oids, od2, _, _ = oracle.graph_search(Yn, nbrc, starts, Qn, K, ef, 2.1, 32,
-                                              max_iter=4 * ef, pp=pp)
+        oids, od2, odims, _, margin = oracle.graph_search(Yn, nbrc, starts, Qn, K, ef, 2.1, 32,
+                                                          max_iter=4 * ef, pp=pp,
+                                                          return_margin=True)
         ok = ~near_tie_queries(Cn, Qn, NE)
-        same = sum(1 for q in range(len(Qn)) if ok[q] and np.array_equal(ids[q], oids[q]))
-        assert same >= 0.85 * ok.sum(), (same, int(ok.sum()))
+        good = ok & (margin >= REL)
+        for q in np.nonzero(good)[0]:
+            assert np.array_equal(ids[q], oids[q]) and dims[q] == odims[q], q
+        assert good.mean() >= 0.8, good.mean()
         for q in range(len(Qn)):
             row = ids[q][ids[q] >= 0]
             assert len(set(row.tolist())) == len(row)
@@ -250,8 +261,6 @@ def test_graph_cosine_matches_oracle(gr, pp):
                 if i >= 0:
                     assert abs(v - float(Yn[i] @ Qn[q])) <= 1e-5, (q, i, v)
             assert np.all(np.diff(cs[q][ids[q] >= 0]) <= 1e-6)      # largest first
-        gt, _ = oracle.knn_exact(Yn, Qn, K)
-        assert oracle.recall_at(ids, gt, K) >= oracle.recall_at(oids, gt, K) - 0.02
     finally:
         gc.close()
         ixc.close()
@@ -270,15 +279,10 @@ def test_graph_maximum_sizes(gr):
         probes, _ = oracle.probe(Cr, Qr[:nq], 16)
         starts = ent64[probes].reshape(nq, -1)
         assert starts.shape[1] == 1024
-        oids, od2, _, _ = oracle.graph_search(Y, nbr64, starts, Qr[:nq], 512, 512, math.inf, 32,
-                                              max_iter=4 * 512)
+        oids, od2, _, _, margin = oracle.graph_search(Y, nbr64, starts, Qr[:nq], 512, 512,
+                                                      math.inf, 32, max_iter=4 * 512,
+                                                      return_margin=True)
         ok = ~near_tie_queries(Cr, Qr[:nq], 16)
-        same = sum(1 for q in range(nq) if ok[q] and set(ids[q].tolist()) == set(oids[q].tolist()))
-        assert same >= 0.9 * ok.sum(), (same, int(ok.sum()))
-        for q in range(nq):
-            fin = ids[q] >= 0
-            assert len(set(ids[q][fin].tolist())) == fin.sum()
-            ex = np.sum((Y[ids[q][fin]] - Qr[q]) ** 2, axis=1)
-            assert np.all(np.abs(d2[q][fin] - ex) <= REL * ex + 1e-6), q
+        _match_sequential(ids, d2, None, Y, Qr[:nq], oids, None, margin, ok, min_frac=0.5)
     finally:
         g64.close()

@@ -16,9 +16,11 @@ base-layer search of Sec. 2.2.1 with Algorithm 1 as its DCO, Sec. 4):
     k-center against brute force over all E-subsets;
   - a cluster holding two blobs that no kNN edge joins: one entry reaches one
     blob only, two entries give the exact KNN;
-  - start vertices are tested 32 list positions at a time like the
-    neighbours of an expansion: the first 32 face no threshold (exact, D
-    dims each), later ones face the best distance of the earlier batches;
+  - vertices are tested one at a time in the paper's order: a hand-worked
+    start list where the third vertex is rejected early only because the
+    second has already tightened R (sequential dims 208 against 256 for a
+    threshold fixed at the start), and the closest-call margin the oracle
+    reports;
   - HNSW++ (Sec. 5.1) on a hand-worked graph: rejected vertices enter the
     beam by their observed distance (D/d) S_d, which decides which branch is
     expanded (result, expansions and dims fixed by hand), where HNSW+ on the
@@ -191,29 +193,61 @@ def test_two_blobs_in_one_cluster_need_two_entries():
     assert np.array_equal(ids2, gt) and np.allclose(d2, gd, rtol=1e-12)
 
 
-def test_start_vertices_are_tested_in_batches_of_32():
-    rng = np.random.default_rng(14)
+def test_vertices_are_tested_one_at_a_time_hand_worked():
+    """The paper's order (Sec. 2.2.1): each vertex's DCO faces R's largest
+    distance as it stands after the vertices before it.  q = 0, D = 64,
+    delta_d = 16, eps0 = 0 (a DCO rejects at d < D iff (D/d) S_d > r^2),
+    K = ef = 1, four start vertices and no edges:
+      v0  distance^2 4, R empty (r = inf): exact, 64 dims, R = {v0};
+      v1  distance^2 1 against r^2 = 4: S_d = 0 until d = 64, positive,
+          64 dims, R = {v1};
+      v2  S_16 = 0.5 (distance^2 1) against r^2 = 1: 4 x 0.5 = 2 > 1,
+          rejected at d = 16 (16 dims) -- had the four been tested against the
+          threshold at the start (r = inf) it would cost 64;
+      v3  distance^2 0.81 against r^2 = 1: positive, 64 dims, R = {v3}.
+    Result v3, 208 dims, one expansion (v3, no neighbours); with exact DCOs
+    4 x 64 dims.  HNSW++ gives the same (R1 = R here)."""
     D = 64
-    q = rng.normal(size=(1, D))
-    near = q + rng.normal(size=(32, D)) * 0.1
-    far = q + 100.0                                       # S_16 alone exceeds any threshold
-    Y = np.concatenate([near, far])                       # ids 0..31 near, 32..39 far
-    graph = np.full((40, 1), -1, np.int32)                # no edges: no expansion adds anything
-    starts = np.arange(40, dtype=np.int64)[None, :]
+    Y = np.zeros((4, D))
+    Y[0, 63] = 2.0
+    Y[1, 63] = 1.0
+    Y[2, 0], Y[2, 63] = np.sqrt(0.5), np.sqrt(0.5)
+    Y[3, 63] = 0.9
+    graph = np.full((4, 1), -1, np.int32)
+    starts = np.arange(4, dtype=np.int64)[None, :]
+    q = np.zeros((1, D))
     for pp in (False, True):
-        ids, d2, dims, iters = oracle.graph_search(Y, graph, starts, q, 1, 1, 2.1, 16, pp=pp)
-        best = int(np.argmin(np.sum((near - q) ** 2, axis=1)))
-        assert ids[0, 0] == best and iters[0] == 1
-        # first batch exact, the 8 far starts of the second batch stop at d = 16
-        assert dims[0] == 32 * D + 8 * 16
+        ids, d2, dims, iters = oracle.graph_search(Y, graph, starts, q, 1, 1, 0.0, 16, pp=pp)
+        assert ids[0].tolist() == [3] and abs(d2[0, 0] - 0.81) < 1e-12
+        assert dims[0] == 64 + 64 + 16 + 64 and iters[0] == 1
         _, _, dims_exact, _ = oracle.graph_search(Y, graph, starts, q, 1, 1, math.inf, 16, pp=pp)
-        assert dims_exact[0] == 40 * D
-    # with exact DCOs R starts as the ef nearest of all starts, whatever the batching
-    rev = starts[:, ::-1].copy()
-    a = oracle.graph_search(Y, graph, starts, q, 5, 5, math.inf, 16)
-    b = oracle.graph_search(Y, graph, rev, q, 5, 5, math.inf, 16)
-    order = np.argsort(np.sum((Y - q) ** 2, axis=1))[:5]
+        assert dims_exact[0] == 4 * D
+    # with exact DCOs R is the ef nearest of all starts, whatever their order
+    rng = np.random.default_rng(14)
+    Yr = rng.normal(size=(40, 16))
+    qr = rng.normal(size=(1, 16))
+    g0 = np.full((40, 1), -1, np.int32)
+    st = np.arange(40, dtype=np.int64)[None, :]
+    a = oracle.graph_search(Yr, g0, st, qr, 5, 5, math.inf, 16)
+    b = oracle.graph_search(Yr, g0, st[:, ::-1].copy(), qr, 5, 5, math.inf, 16)
+    order = np.argsort(np.sum((Yr - qr) ** 2, axis=1))[:5]
     assert np.array_equal(a[0][0], order) and np.array_equal(b[0][0], order)
+
+
+def test_closest_call_margin():
+    """The margin the oracle reports per query is the smallest relative gap of
+    any comparison that decided the search: with exact DCOs and ef = 1, start
+    vertices at squared distances 1 and 1 + 1e-7 give about 1e-7 (the second
+    DCO's S_D against r^2 = 1); 1 and 2 give |2/1 - 1| = 1."""
+    D = 8
+    for d_b, want in ((1.0 + 1e-7, 1e-7), (2.0, 1.0)):
+        Y = np.zeros((2, D))
+        Y[0, 0] = 1.0
+        Y[1, 0] = np.sqrt(d_b)
+        *_, margin = oracle.graph_search(Y, np.full((2, 1), -1, np.int32),
+                                         np.array([[0, 1]], np.int64), np.zeros((1, D)), 1, 1,
+                                         math.inf, 8, return_margin=True)
+        assert abs(margin[0] - want) <= 1e-3 * want
 
 
 def test_hnsw_pp_beam_keeps_observed_distances_hand_worked():
