@@ -299,12 +299,12 @@ int adsx_stream_status(const adsx_index *index, void *stream);
  *                       queries_per_item of the queries probing it: each
  *                       Delta_d step of a 32-member tile is read once and
  *                       tested against all of them.  The probe ranks are
- *                       covered in rounds -- the nearest 2 clusters of each
- *                       query query-major, then rank ranges growing 3x --
- *                       each round testing against the K-th distance of the
- *                       rounds before it (a valid r: the K-th of a subset of
- *                       exact candidate distances), so results do not depend
- *                       on scheduling.  Needs delta_d <= 64 (or the test
+ *                       covered in rounds -- each query's nearest cluster
+ *                       in full (no r is known yet), then rank ranges
+ *                       growing 4x -- each round testing against the K-th
+ *                       distance of the rounds before it (a valid r: the
+ *                       K-th of a subset of exact candidate distances), so
+ *                       results do not depend on scheduling.  Needs delta_d <= 64 (or the test
  *                       off) and an L2 or cosine index; other searches run
  *                       query-major.
  *   ADSX_SCHED_AUTO     cluster-major when it applies to a large batch

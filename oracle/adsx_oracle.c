@@ -679,9 +679,12 @@ void orc_ivf_ads_ip(const double *Y, int64_t N, int32_t D, const double *Cr,
 /* Outputs ids/d2 (K smallest of R by (distance, id); -1/+inf padded),    */
 /* the dims sampled and the expansions per query, and (margin_out, may be */
 /* NULL) the query's closest call: the smallest relative gap over every   */
-/* DCO comparison (orc_dco's margin) and every comparison of two keys that */
-/* decided R's (or R1's) content or order -- a query whose closest call is */
-/* below a tolerance may take another path under another rounding.        */
+/* DCO comparison (orc_dco's margin), every comparison of a new key with   */
+/* the largest of R (or R1) that decided an insertion, and every choice of */
+/* the entry to expand (R's nearest unexpanded entry against the next      */
+/* one) -- a query whose closest call is below a tolerance may take        */
+/* another path under another rounding (the order of the returned keys    */
+/* among themselves is not included: it does not steer the search).       */
 /* pp = 1: HNSW++ (Sec. 5.1) -- R's two roles decoupled: R1 (size K, exact  */
 /* distances) holds the results and gives every DCO its threshold (R1's   */
 /* largest distance); R (size N_ef) and S are kept with the observed      */
@@ -718,8 +721,6 @@ static void orc_set_insert(orc_beam *b, orc_pair *A, unsigned char *flags, int32
         if (flags) flags[p] = flags[p - 1];
         --p;
     }
-    if (p > 0) orc_note_gap(b, d, A[p - 1].d);
-    if (p + 1 < (*n < cap ? *n + 1 : cap)) orc_note_gap(b, d, A[p + 1].d);
     A[p].d = d;
     A[p].id = id;
     if (flags) flags[p] = 0;
@@ -795,6 +796,10 @@ void orc_graph_search(const double *Y, int64_t N, int32_t D, const int32_t *grap
             for (int32_t k = 0; k < b.nR; ++k)
                 if (!b.expd[k]) { u = k; break; }
             if (u < 0) break;
+            /* which entry is expanded: R's nearest unexpanded one, against
+               the next unexpanded one */
+            for (int32_t k = u + 1; k < b.nR; ++k)
+                if (!b.expd[k]) { orc_note_gap(&b, b.R[u].d, b.R[k].d); break; }
             b.expd[u] = 1;
             const int64_t node = b.R[u].id;
             for (int32_t j = 0; j < Rg; ++j) orc_beam_visit(&b, graph[node * Rg + j]);

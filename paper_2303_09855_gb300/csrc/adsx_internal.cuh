@@ -63,8 +63,8 @@ struct Index {
     int32_t cm_G = 16;
     int32_t cm_tpi = 4;           // 32-member tiles per cluster-major work item
     int32_t max_tiles = 0;        // tiles of the largest cluster
-    int32_t cm_r0 = 2;
-    int32_t cm_growth = 3;
+    int32_t cm_r0 = 1;
+    int32_t cm_growth = 4;
     // stage timing (adsx_set_stage_timing): events between search stages
     bool timing = false;
     bool timed_once = false;
@@ -544,7 +544,7 @@ struct CmPlan {
     int32_t *cnt, *coff, *ioff, *cur, *qlist, *n_items;
     int2 *items;
 };
-size_t cm_smem_bytes(int G);
+size_t cm_smem_bytes(int G, int db, int storage);
 cudaError_t launch_cm_plan(const int32_t *probes, int64_t nq, int pstride, int r0, int r1, int nlist,
                            int G, int tpi, const int64_t *off, CmPlan &pl, cudaStream_t s);
 cudaError_t launch_cm_scan(const CmArgs &a, int device, cudaStream_t s);

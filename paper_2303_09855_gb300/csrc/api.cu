@@ -586,7 +586,7 @@ static bool use_cluster_major(const Index *ix, const adsx::ScanArgs &a)
 {
     if (ix->sched == ADSX_SCHED_QUERY) return false;
     if (a.metric == ADSX_IP || a.db > adsx::CM_MAX_DB) return false;
-    if (a.nprobe <= ix->cm_r0) return false;           // round 0 covers every probe
+    if (a.nprobe <= ix->cm_r0) return false;           // round 0 alone would cover every probe
     if (ix->sched == ADSX_SCHED_CLUSTER) return true;
     // a large batch whose queries probe each cluster 8 times on average
     return a.nq >= 2048 && a.nprobe >= 8 && a.nq * (int64_t)a.nprobe >= 8 * (int64_t)ix->nlist;
@@ -667,17 +667,11 @@ static cudaError_t cm_scan(const Index *ix, const adsx::ScanArgs &a, Scratch &sc
     const int64_t nq = a.nq;
     const int K = a.K, nprobe = a.nprobe, G = ix->cm_G;
     const int r0 = std::min(ix->cm_r0, nprobe);
-    adsx::ScanArgs a0 = a;
-    a0.metric = ADSX_L2;                 // keys (squared distances) until the last merge
-    a0.nprobe = r0;
-    a0.probe_stride = nprobe;
-    a0.S = 1;                            // one warp per query: a schedule-independent round
-    a0.n_items = (int32_t)nq;
-    if ((e = qm_scan(ix, a0, sc)) != cudaSuccess) return e;
-
     // capacity of a round's list per query: candidates reaching d = D within
-    // the previous rounds' r (a query beyond it is searched again query-major)
-    const int cap = std::max(8 * K, 1024);
+    // the previous rounds' r -- in round 0 (no r yet) every member of the
+    // query's r0 nearest clusters (a query beyond it is searched again
+    // query-major)
+    const int cap = std::max(std::max(4 * K, 1024), r0 * 32 * ix->max_tiles);
     float *r2 = nullptr, *app_d = nullptr;
     int32_t *app_i = nullptr, *ovf = nullptr;
     unsigned *app_n = nullptr, *counter = nullptr;
@@ -689,6 +683,11 @@ static cudaError_t cm_scan(const Index *ix, const adsx::ScanArgs &a, Scratch &sc
     if ((e = sc.get(&counter, 1)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(app_n, 0, sizeof(unsigned) * nq, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ovf, 0, sizeof(int32_t) * nq, s)) != cudaSuccess) return e;
+    // empty top-K lists (ids -1) and dims counters; the merge then sets r = +inf
+    if ((e = cudaMemsetAsync(a.out_ids, 0xff, sizeof(int64_t) * nq * K, s)) != cudaSuccess) return e;
+    if (a.out_dims &&
+        (e = cudaMemsetAsync(a.out_dims, 0, sizeof(int64_t) * nq, s)) != cudaSuccess)
+        return e;
     adsx::CmMergeArgs m;
     m.nq = nq;
     m.K = K;
@@ -703,9 +702,12 @@ static cudaError_t cm_scan(const Index *ix, const adsx::ScanArgs &a, Scratch &sc
     m.ovf = ovf;
     m.metric = a.metric;
     m.final_pass = 0;
-    if ((e = adsx::launch_cm_merge(m, s)) != cudaSuccess) return e;   // r from round 0
+    if ((e = adsx::launch_cm_merge(m, s)) != cudaSuccess) return e;
 
-    const auto rounds = cm_rounds(r0, nprobe, ix->cm_growth);
+    // round 0: each query's r0 nearest clusters, every member to d = D (no r
+    // yet: the test cannot reject); then the later ranks against r
+    auto rounds = cm_rounds(r0, nprobe, ix->cm_growth);
+    rounds.insert(rounds.begin(), {0, r0});
     int width = 1;
     for (const auto &r : rounds) width = std::max(width, r.second - r.first);
     adsx::CmPlan pl;
@@ -728,6 +730,7 @@ static cudaError_t cm_scan(const Index *ix, const adsx::ScanArgs &a, Scratch &sc
         if ((e = adsx::launch_cm_plan(a.probes, nq, nprobe, rounds[i].first, rounds[i].second,
                                       ix->nlist, G, ix->cm_tpi, ix->off, pl, s)) != cudaSuccess)
             return e;
+        c.test_on = i == 0 ? 0 : a.test_on;
         if ((e = adsx::launch_cm_scan(c, ix->device, s)) != cudaSuccess) return e;
         m.final_pass = i + 1 == rounds.size();
         if ((e = adsx::launch_cm_merge(m, s)) != cudaSuccess) return e;

@@ -11,12 +11,12 @@
 //
 // The running threshold r of a query cannot be shared between the warps
 // that serve it without a global KNN set, so the probe ranks are processed
-// in rounds: round 0 (the query-major kernel over each query's nearest
-// R0 clusters) gives every query its K-th distance r among those clusters;
-// each following round scans a range of probe ranks cluster-major against
-// the r of the rounds before it, appending every candidate that reaches
-// d = D with S_D <= r^2 to a per-query list; cm_merge_kernel then merges the
-// list into the query's top-K and tightens r.  A fixed r per round is a
+// in rounds: round 0 scans each query's nearest R0 clusters in full (no r is
+// known yet, so the test is off) and gives every query its K-th distance r
+// among them; each following round scans a range of probe ranks against the
+// r of the rounds before it, appending every candidate that reaches d = D
+// with S_D <= r^2 to a per-query list; cm_merge_kernel then merges the list
+// into the query's top-K and tightens r.  A fixed r per round is a
 // valid threshold (the K-th of a subset of exact candidate distances is
 // never below the exact K-th of all of them), so every returned distance is
 // exact and the bracket property of the query-major scan holds; and as r is
@@ -27,6 +27,12 @@
 // schedules compute the same FP32 value of S_d for every (query, candidate,
 // step); with a fixed threshold (the verification protocol of Sec. 6.2.5)
 // their decisions are identical.
+//
+// Within an item, each tile's first step is dense (one load of the step's
+// blocks feeds every query of the item); each later step is loaded once,
+// staged in shared memory, and only the (query, member) pairs still live are
+// computed, one per lane, so that candidates ADSampling has rejected cost
+// nothing more.
 //
 // A query whose list overflows its capacity in some round is flagged and,
 // after the last round, searched again by the query-major kernel.
@@ -45,11 +51,29 @@ constexpr int CM_THREADS = CM_WARPS * 32;
 #define ADSX_CM_MINBLOCKS 4
 #endif
 
-// Per-warp shared memory: query slots, their thresholds and live masks,
-// dims counters and the partial distance of each lane's member per query.
+// Member-block row of the staged tile step in shared memory: the 16 dims of
+// one member as NL 16-byte pieces (FP32: 4, 16-bit: 2), piece j stored in
+// column j ^ swz(member).  A 128-bit shared load serves eight lanes at a
+// time; the eight members a pass gives eight consecutive lanes of one slot
+// are own_slot(l) for eight consecutive l -- members 0, 16, 8, 24, 1, 17, 9,
+// 25 and so on (FP32), 0, 16, 1, 17, ... (16-bit) -- whose unswizzled pieces
+// would share banks; the swizzle spreads them over all 32 banks.
+template <typename T> struct Stage {
+    static constexpr int ROW = 32;               // bytes per member-block row
+    __device__ static int swz(int m) { return (m >> 4) & 1; }
+};
+template <> struct Stage<float> {
+    static constexpr int ROW = 64;
+    __device__ static int swz(int m) { return (m >> 3) & 3; }
+};
+
+// Per-warp shared memory: query slots, their thresholds, live masks and dims
+// counters; per (slot, tile lane) the partial distance S_d and the outcome of
+// the last pass; the list of live (slot, lane) pairs of a pass; and the
+// tile's current step, staged member by member.
 struct CmCarve {
-    int qg, r2, live, dg, S, bytes;
-    __host__ __device__ explicit CmCarve(int G)
+    int qg, r2, live, dg, S, code, pairs, stile, bytes;
+    __host__ __device__ CmCarve(int G, int db, int row)
     {
         int o = 0;
         dg = o; o += 8 * G;           // unsigned long long, 8-byte aligned first
@@ -57,6 +81,10 @@ struct CmCarve {
         r2 = o; o += 4 * G;
         live = o; o += 4 * G;
         S = o; o += 4 * 32 * G;
+        code = o; o += 32 * G;
+        pairs = o; o += 2 * 32 * G;
+        o = (o + 15) & ~15;
+        stile = o; o += db * 32 * row;
         bytes = (o + 15) & ~15;
     }
 };
@@ -74,21 +102,69 @@ __device__ __forceinline__ QPiece<NL> ld_qpiece_ro(const float *q)
     return r;
 }
 
+// One member's step sum computed by one lane, in the order the NL-lane
+// layout produces it: a chain pair (even, odd dims) per piece over the step's
+// blocks, each pair summed, then the pieces combined as group_sum does --
+// (P0 + P1) + (P2 + P3) for FP32, P0 + P1 for 16-bit storage -- which IEEE
+// addition, being commutative, makes the same value on every lane.
+//   row: the member's block rows in the staged tile (stride 32 rows per
+//   block); mt: the member within the tile; q: the query's dims of the
+//   step's first block.
+template <typename T, int DB>
+__device__ __forceinline__ float member_step_sum(const unsigned char *row, int mt, const float *q,
+                                                 int nb)
+{
+    constexpr int NL = Split<T>::NL, PW = BLK / NL;
+    constexpr int RB = 32 * Stage<T>::ROW;       // bytes between a member's block rows
+    float2 p[NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) p[j] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < DB; ++b) {
+        if (b < nb) {
+#pragma unroll
+            for (int j = 0; j < NL; ++j) {
+                const typename Split<T>::V v = *reinterpret_cast<const typename Split<T>::V *>(
+                    row + b * RB + ((j ^ Stage<T>::swz(mt)) * 16));
+                p[j] = add_piece(v, ld_qpiece_ro<NL>(q + b * BLK + j * PW), p[j], T());
+            }
+        }
+    }
+    if constexpr (NL == 4)
+        return ((p[0].x + p[0].y) + (p[1].x + p[1].y)) + ((p[2].x + p[2].y) + (p[3].x + p[3].y));
+    else
+        return (p[0].x + p[0].y) + (p[1].x + p[1].y);
+}
+
+// One warp per item.  Each 32-member tile takes its first step densely: the
+// step's blocks are loaded once into registers in the NL-lane layout of the
+// query-major scan, and every query slot of the item computes its partial
+// distances from them (two slots at a time: their FMA chains and shuffles
+// interleave).  With the test off (FDScanning) every member stays live and
+// the later steps run the same way.  With the test on, each later step of
+// the tile is staged once in shared memory and only the live (slot, member)
+// pairs are computed, one pair per lane, 32 pairs per pass whatever their
+// query: the pairs that ADSampling has rejected cost nothing more.
 template <typename T, int DB, bool FIXED>
 __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(CmArgs a)
 {
     constexpr int NL = Split<T>::NL, NG = 32 / NL, PW = BLK / NL;
+    constexpr int ROW = Stage<T>::ROW, RB = 32 * ROW;
     typedef typename Split<T>::V V;
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ float s_ftab[256];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const CmCarve cc(a.G);
+    const unsigned below = (1u << lane) - 1u;
+    const CmCarve cc(a.G, a.db, ROW);
     unsigned char *base = smraw + (size_t)warp * cc.bytes;
     unsigned long long *dg = reinterpret_cast<unsigned long long *>(base + cc.dg);
     int *qg = reinterpret_cast<int *>(base + cc.qg);
     float *r2g = reinterpret_cast<float *>(base + cc.r2);
     unsigned *live = reinterpret_cast<unsigned *>(base + cc.live);
     float *Sv = reinterpret_cast<float *>(base + cc.S);
+    unsigned char *code = base + cc.code;
+    unsigned short *pairs = reinterpret_cast<unsigned short *>(base + cc.pairs);
+    unsigned char *stile = base + cc.stile;
     for (int b = threadIdx.x; b <= a.nblk && b < 256; b += CM_THREADS) s_ftab[b] = a.ftab[b];
     __syncthreads();
 
@@ -121,8 +197,7 @@ __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(
         const T *cb = static_cast<const T *>(a.data) + o * a.Dp;
         const int64_t stride = (int64_t)n * BLK;
         for (int m0 = mb; m0 < me; m0 += 32) {
-            const int m = m0 + own;
-            const unsigned vm = __ballot_sync(FULL, m < n);
+            const unsigned vm = __ballot_sync(FULL, m0 + own < n);
             for (int g = lane; g < ngq; g += 32) live[g] = vm;
             __syncwarp();
             int blk = 0;
@@ -132,7 +207,10 @@ __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(
                 if (U == 0u) break;
                 const int e = blk + a.db < a.nblk ? blk + a.db : a.nblk;
                 const int nb = e - blk;
-                // this step's blocks of the tile: loaded once, used by every query
+                const bool fin = e >= a.nblk;
+                const float fe = s_ftab[e];
+                const unsigned dstep = (unsigned)(e * BLK < a.D ? e * BLK : a.D);
+                // this step's blocks of the tile: loaded once for every query
                 V v[DB][NL];
                 const T *x = cb + (int64_t)blk * stride + (int64_t)(m0 + gi) * BLK + jo;
 #pragma unroll
@@ -144,37 +222,35 @@ __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(
                             v[b][k] = ld_piece(x + b * stride + k * NG * BLK);
                     }
                 }
-                const bool fin = e >= a.nblk;
-                const float fe = s_ftab[e];
-                const int dstep = e * BLK < a.D ? e * BLK : a.D;
-                const int pos = (int)o + m;
-                // the rest of Algorithm 1's step for query slot g, whose
-                // partial distance over this step is st
-                auto finish = [&](int g, unsigned lv, float st, const float *qv) {
-                    float S = (blk == 0 ? 0.f : Sv[g * 32 + lane]) + st;
-                    const bool alive = (lv >> lane) & 1u;
-                    const float r2 = r2g[g];
-                    if (!fin) {
-                        // Case 1 / Case 2 of Algorithm 1 (squared test of Sec. 3.2)
-                        const bool rej = a.test_on && alive && S > r2 * fe;
-                        const unsigned rm = __ballot_sync(FULL, rej);
-                        if (FIXED && rej) {
-                            const int64_t off = (int64_t)qg[g] * a.N + a.ids[pos];
-                            a.decisions[off] = 0;
-                            if (a.dec_dims) a.dec_dims[off] = dstep;
+                if (blk == 0 || !a.test_on) {
+                    // ---- dense step: every slot, every member, from registers
+                    const int pos = (int)o + m0 + own;
+                    auto finish = [&](int g, unsigned lv, float st, const float *qv) {
+                        float S = (blk == 0 ? 0.f : Sv[g * 32 + lane]) + st;
+                        const bool alive = (lv >> lane) & 1u;
+                        const float r2 = r2g[g];
+                        if (!fin) {
+                            // Case 1 / Case 2 of Algorithm 1 (squared test, Sec. 3.2)
+                            const bool rej = a.test_on && alive && S > r2 * fe;
+                            const unsigned rmk = __ballot_sync(FULL, rej);
+                            if (FIXED && rej) {
+                                const int64_t off = (int64_t)qg[g] * a.N + a.ids[pos];
+                                a.decisions[off] = 0;
+                                if (a.dec_dims) a.dec_dims[off] = (int)dstep;
+                            }
+                            Sv[g * 32 + lane] = S;
+                            if (lane == 0) {
+                                live[g] = lv & ~rmk;
+                                dg[g] += (unsigned long long)__popc(rmk) * dstep;
+                            }
+                            return;
                         }
-                        Sv[g * 32 + lane] = S;
-                        if (lane == 0) {
-                            live[g] = lv & ~rm;
-                            dg[g] += (unsigned long long)__popc(rm) * (unsigned)dstep;
-                        }
-                    } else {
                         // Case 3: the exact compare at d = D
                         bool cand = alive;
                         if constexpr (Roundoff<T>::u > 0.f) {
-                            // 16-bit storage: only candidates with sqrt(S~) <=
-                            // r + u ||x|| can have S_D <= r^2; their exact FP32
-                            // distance comes from the FP32 row copy
+                            // 16-bit storage: only candidates with sqrt(S~) <= r + u ||x||
+                            // can have S_D <= r^2; their exact FP32 distance comes from
+                            // the FP32 row copy
                             bool need = false;
                             if (alive) {
                                 need = !(r2 < INFINITY);
@@ -202,7 +278,7 @@ __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(
                                 if (lane == 0) b0 = atomicAdd(a.app_n + q, (unsigned)__popc(pm));
                                 b0 = __shfl_sync(FULL, b0, 0);
                                 if (posv) {
-                                    const unsigned idx = b0 + __popc(pm & ((1u << lane) - 1u));
+                                    const unsigned idx = b0 + __popc(pm & below);
                                     if (idx < (unsigned)a.cap) {
                                         a.app_d[(int64_t)q * a.cap + idx] = S;
                                         a.app_i[(int64_t)q * a.cap + idx] = a.ids[pos];
@@ -214,37 +290,131 @@ __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(
                             live[g] = 0u;
                             dg[g] += (unsigned long long)__popc(lv) * (unsigned)a.D;
                         }
-                    }
-                };
-                // queries two at a time: their FMA chains and shuffles interleave
-                for (int g = 0; g < ngq; g += 2) {
-                    const bool two = g + 1 < ngq;
-                    const unsigned lv0 = live[g], lv1 = two ? live[g + 1] : 0u;
-                    if ((lv0 | lv1) == 0u) continue;
-                    const float *qv0 = a.qrot + (int64_t)qg[g] * a.Dp;
-                    const float *qv1 = two ? a.qrot + (int64_t)qg[g + 1] * a.Dp : qv0;
-                    float2 p0[NL], p1[NL];
+                    };
+                    for (int g = 0; g < ngq; g += 2) {
+                        const bool two = g + 1 < ngq;
+                        const unsigned lv0 = live[g], lv1 = two ? live[g + 1] : 0u;
+                        if ((lv0 | lv1) == 0u) continue;
+                        const float *qv0 = a.qrot + (int64_t)qg[g] * a.Dp;
+                        const float *qv1 = two ? a.qrot + (int64_t)qg[g + 1] * a.Dp : qv0;
+                        float2 p0[NL], p1[NL];
 #pragma unroll
-                    for (int k = 0; k < NL; ++k) {
-                        p0[k] = make_float2(0.f, 0.f);
-                        p1[k] = make_float2(0.f, 0.f);
-                    }
+                        for (int k = 0; k < NL; ++k) {
+                            p0[k] = make_float2(0.f, 0.f);
+                            p1[k] = make_float2(0.f, 0.f);
+                        }
 #pragma unroll
-                    for (int b = 0; b < DB; ++b) {
-                        if (b < nb) {
-                            const QPiece<NL> qa = ld_qpiece_ro<NL>(qv0 + (blk + b) * BLK + jo);
-                            const QPiece<NL> qb = ld_qpiece_ro<NL>(qv1 + (blk + b) * BLK + jo);
+                        for (int b = 0; b < DB; ++b) {
+                            if (b < nb) {
+                                const QPiece<NL> qa = ld_qpiece_ro<NL>(qv0 + (blk + b) * BLK + jo);
+                                const QPiece<NL> qb = ld_qpiece_ro<NL>(qv1 + (blk + b) * BLK + jo);
 #pragma unroll
-                            for (int k = 0; k < NL; ++k) {
-                                p0[k] = add_piece(v[b][k], qa, p0[k], T());
-                                p1[k] = add_piece(v[b][k], qb, p1[k], T());
+                                for (int k = 0; k < NL; ++k) {
+                                    p0[k] = add_piece(v[b][k], qa, p0[k], T());
+                                    p1[k] = add_piece(v[b][k], qb, p1[k], T());
+                                }
                             }
                         }
+                        const float s0 = group_sum<NL>(p0, lane);
+                        const float s1 = group_sum<NL>(p1, lane);
+                        if (lv0) finish(g, lv0, s0, qv0);
+                        if (lv1) finish(g + 1, lv1, s1, qv1);
                     }
-                    const float s0 = group_sum<NL>(p0, lane);
-                    const float s1 = group_sum<NL>(p1, lane);
-                    if (lv0) finish(g, lv0, s0, qv0);
-                    if (lv1) finish(g + 1, lv1, s1, qv1);
+                } else {
+                    // ---- sparse step: stage the tile's step, then the live
+                    // (slot, member) pairs one per lane
+#pragma unroll
+                    for (int b = 0; b < DB; ++b)
+#pragma unroll
+                        for (int k = 0; k < NL; ++k)
+                            if (b < nb)
+                                *reinterpret_cast<V *>(
+                                    stile + b * RB + (gi + NG * k) * ROW +
+                                    (((lane % NL) ^ Stage<T>::swz(gi + NG * k)) * 16)) = v[b][k];
+                    int np = 0;
+                    for (int g = 0; g < ngq; ++g) {
+                        const unsigned lv = live[g];
+                        if ((lv >> lane) & 1u)
+                            pairs[np + __popc(lv & below)] = (unsigned short)((g << 5) | lane);
+                        np += __popc(lv);
+                    }
+                    __syncwarp();
+                    for (int p0 = 0; p0 < np; p0 += 32) {
+                        const bool valid = p0 + lane < np;
+                        int g = 0, l = 0;
+                        if (valid) {
+                            const int pr = pairs[p0 + lane];
+                            g = pr >> 5;
+                            l = pr & 31;
+                        }
+                        const int mt = own_slot<NL>(l);             // member within the tile
+                        const int pos = (int)o + m0 + mt;
+                        const float *qv = a.qrot + (int64_t)qg[g] * a.Dp;
+                        float S = 0.f;
+                        if (valid)
+                            S = Sv[g * 32 + l] +
+                                member_step_sum<T, DB>(stile + mt * ROW, mt, qv + blk * BLK, nb);
+                        const float r2 = valid ? r2g[g] : 0.f;
+                        unsigned char out = 0;                      // 1: continues
+                        if (!fin) {
+                            if (valid) {
+                                if (S > r2 * fe) {
+                                    if constexpr (FIXED) {
+                                        const int64_t off = (int64_t)qg[g] * a.N + a.ids[pos];
+                                        a.decisions[off] = 0;
+                                        if (a.dec_dims) a.dec_dims[off] = (int)dstep;
+                                    }
+                                } else {
+                                    out = 1;
+                                    Sv[g * 32 + l] = S;
+                                }
+                            }
+                        } else {
+                            bool cand = valid;
+                            if constexpr (Roundoff<T>::u > 0.f) {
+                                bool need = false;
+                                if (valid) {
+                                    need = !(r2 < INFINITY);
+                                    if (!need && r2 >= 0.f) {
+                                        const float bound =
+                                            (sqrtf(r2) + Roundoff<T>::u * a.norms[pos]) * 1.0001f;
+                                        need = sqrtf(S) <= bound;
+                                    }
+                                }
+                                S = recheck_rows(a.rows32, a.Dp, qv, need, pos, S, lane);
+                                cand = need;
+                            }
+                            const bool posv = cand && S <= r2;
+                            if constexpr (FIXED) {
+                                if (valid) {
+                                    const int64_t off = (int64_t)qg[g] * a.N + a.ids[pos];
+                                    a.decisions[off] = posv ? 1 : 2;
+                                    if (a.dec_dims) a.dec_dims[off] = a.D;
+                                }
+                            } else if (posv) {
+                                const int q = qg[g];
+                                const unsigned idx = atomicAdd(a.app_n + q, 1u);
+                                if (idx < (unsigned)a.cap) {
+                                    a.app_d[(int64_t)q * a.cap + idx] = S;
+                                    a.app_i[(int64_t)q * a.cap + idx] = a.ids[pos];
+                                }
+                            }
+                        }
+                        if (valid) code[g * 32 + l] = out;
+                    }
+                    __syncwarp();
+                    // the pass's outcome, slot by slot: the survivors stay live;
+                    // the others sampled dstep dims (rejected) or all D (d = D)
+                    for (int g = 0; g < ngq; ++g) {
+                        const unsigned lv = live[g];
+                        if (lv == 0u) continue;
+                        const unsigned nl =
+                            __ballot_sync(FULL, ((lv >> lane) & 1u) && code[g * 32 + lane] == 1);
+                        if (lane == 0) {
+                            live[g] = nl;
+                            dg[g] += (unsigned long long)__popc(lv & ~nl) * (fin ? (unsigned)a.D : dstep);
+                        }
+                    }
                 }
                 __syncwarp();
                 blk = e;
@@ -366,76 +536,116 @@ __global__ void cm_plan_scatter_kernel(const int32_t *__restrict__ probes, int64
     }
 }
 
-// Per query: the top-K so far (ids / keys, -1 padded) and the candidates the
-// round appended are sorted by (distance, id) and cut to K; r^2 becomes the
-// K-th key (+inf while fewer than K are known).  A list beyond its capacity
-// flags the query.  With `final_pass` the keys are written as the values the
-// search returns.
-__global__ void __launch_bounds__(256) cm_merge_kernel(CmMergeArgs m)
+// Per query (one warp each): the top-K so far (ids / keys, -1 padded, sorted
+// by (distance, id)) and the candidates the round appended merge into the
+// new top-K; r^2 becomes the K-th key (+inf while fewer than K are known).
+// The appended (key, id) pairs -- 64-bit words, key bits above id, which
+// orders non-negative keys as (distance, id) -- are sorted by a warp bitonic
+// network in shared memory; every entry of either list then lands at its
+// index plus its rank in the other list (the two lists hold distinct ids),
+// and the first K are kept.  A list beyond its capacity flags the query.
+// With `final_pass` the keys are written as the values the search returns.
+constexpr int MERGE_WARPS = 4;
+
+__device__ __forceinline__ unsigned long long mkey(float d, int id)
+{
+    return ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)id;
+}
+
+// entries of the sorted a[0..n) below x
+__device__ __forceinline__ int rank_below(const unsigned long long *a, int n, unsigned long long x)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(MERGE_WARPS * 32) cm_merge_kernel(CmMergeArgs m)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    float *sd = reinterpret_cast<float *>(smraw);
-    int *si = reinterpret_cast<int *>(sd + m.T);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int K = m.K;
-    for (int64_t q = blockIdx.x; q < m.nq; q += gridDim.x) {
+    unsigned long long *ak = reinterpret_cast<unsigned long long *>(smraw) +
+                             (size_t)warp * (m.T + K);
+    unsigned long long *ek = ak + m.T;
+    const unsigned long long NONE = ~0ull;
+    for (int64_t q = (int64_t)blockIdx.x * MERGE_WARPS + warp; q < m.nq;
+         q += (int64_t)gridDim.x * MERGE_WARPS) {
         unsigned na = m.app_n ? m.app_n[q] : 0u;
         if (na > (unsigned)m.cap) {
-            if (threadIdx.x == 0) m.ovf[q] = 1;
+            if (lane == 0) m.ovf[q] = 1;
             na = (unsigned)m.cap;
         }
         int64_t *ids = m.ids + q * K;
         float *dk = m.d2 + q * K;
         if (na == 0u && !m.final_pass) {
-            if (threadIdx.x == 0) m.r2[q] = ids[K - 1] >= 0 ? dk[K - 1] : INFINITY;
+            if (lane == 0) m.r2[q] = ids[K - 1] >= 0 ? dk[K - 1] : INFINITY;
             continue;
         }
-        int T = 1;
-        while (T < K + (int)na) T <<= 1;
-        for (int i = threadIdx.x; i < T; i += blockDim.x) {
-            float d = INFINITY;
-            int id = 0x7fffffff;
-            if (i < K) {
-                if (ids[i] >= 0) {
-                    d = dk[i];
-                    id = (int)ids[i];
-                }
-            } else if (i < K + (int)na) {
-                d = m.app_d[q * m.cap + (i - K)];
-                id = m.app_i[q * m.cap + (i - K)];
-            }
-            sd[i] = d;
-            si[i] = id;
+        int ne = 0;                                   // existing entries (a prefix)
+        for (int k = lane; k < K; k += 32) {
+            const bool has = ids[k] >= 0;
+            ek[k] = has ? mkey(dk[k], (int)ids[k]) : NONE;
+            ne += __popc(__ballot_sync(__activemask(), has));
         }
-        __syncthreads();
+        ne = __shfl_sync(FULL, ne, 0);
+        int T = 32;
+        while (T < (int)na) T <<= 1;
+        for (int i = lane; i < T; i += 32)
+            ak[i] = i < (int)na ? mkey(m.app_d[q * m.cap + i], m.app_i[q * m.cap + i]) : NONE;
+        __syncwarp();
         for (int size = 2; size <= T; size <<= 1) {
             for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = threadIdx.x; i < T; i += blockDim.x) {
+                for (int i = lane; i < T; i += 32) {
                     const int j = i ^ stride;
                     if (j > i) {
-                        const float di = sd[i], dj = sd[j];
-                        const int ii = si[i], ij = si[j];
+                        const unsigned long long x = ak[i], y = ak[j];
                         const bool up = (i & size) == 0;
-                        if (pair_less(dj, ij, di, ii) == up) {
-                            sd[i] = dj;
-                            si[i] = ij;
-                            sd[j] = di;
-                            si[j] = ii;
+                        if ((y < x) == up) {
+                            ak[i] = y;
+                            ak[j] = x;
                         }
                     }
                 }
-                __syncthreads();
+                __syncwarp();
             }
         }
-        for (int k = threadIdx.x; k < K; k += blockDim.x) {
-            const bool has = si[k] != 0x7fffffff;
-            ids[k] = has ? (int64_t)si[k] : (int64_t)-1;
-            dk[k] = m.final_pass ? out_value(m.metric, sd[k], has) : (has ? sd[k] : INFINITY);
+        const int total = ne + (int)na < K ? ne + (int)na : K;
+        unsigned long long kth = NONE;
+        auto put = [&](int pos, unsigned long long key) {
+            const int id = (int)(key & 0xffffffffu);
+            const float d = __uint_as_float((unsigned)(key >> 32));
+            ids[pos] = id;
+            dk[pos] = m.final_pass ? out_value(m.metric, d, true) : d;
+            if (pos == K - 1) kth = key;
+        };
+        // reads of ids / dk are done (ek holds them); positions are distinct
+        __syncwarp();
+        for (int k = lane; k < ne; k += 32) {
+            const int pos = k + rank_below(ak, (int)na, ek[k]);
+            if (pos < K) put(pos, ek[k]);
         }
-        if (threadIdx.x == 0) {
-            m.r2[q] = si[K - 1] != 0x7fffffff ? sd[K - 1] : INFINITY;
-            if (m.app_n) m.app_n[q] = 0u;
+        for (int j = lane; j < (int)na; j += 32) {
+            const int pos = j + rank_below(ek, ne, ak[j]);
+            if (pos < K) put(pos, ak[j]);
         }
-        __syncthreads();
+        for (int k = total + lane; k < K; k += 32) {
+            ids[k] = -1;
+            dk[k] = m.final_pass ? out_value(m.metric, 0.f, false) : INFINITY;
+        }
+        // the lane that placed the K-th entry publishes r^2
+        const unsigned km = __ballot_sync(FULL, kth != NONE);
+        if (km) {
+            if (lane == __ffs(km) - 1) m.r2[q] = __uint_as_float((unsigned)(kth >> 32));
+        } else if (lane == 0) {
+            m.r2[q] = INFINITY;
+        }
+        if (lane == 0 && m.app_n) m.app_n[q] = 0u;
+        __syncwarp();
     }
 }
 
@@ -494,7 +704,11 @@ unsigned grid_for(int64_t work, int threads)
 
 }  // namespace
 
-size_t cm_smem_bytes(int G) { return (size_t)CmCarve(G).bytes * CM_WARPS; }
+size_t cm_smem_bytes(int G, int db, int storage)
+{
+    const int row = storage == ADSX_F32 ? Stage<float>::ROW : Stage<__half>::ROW;
+    return (size_t)CmCarve(G, db, row).bytes * CM_WARPS;
+}
 
 cudaError_t launch_cm_plan(const int32_t *probes, int64_t nq, int pstride, int r0, int r1, int nlist,
                            int G, int tpi, const int64_t *off, CmPlan &pl, cudaStream_t s)
@@ -516,7 +730,7 @@ cudaError_t launch_cm_scan(const CmArgs &a, int device, cudaStream_t s)
     if (a.db < 1 || a.db > CM_MAX_DB || a.G < 1 || a.G > CM_MAX_G || a.tpi < 1)
         return cudaErrorInvalidValue;
     const CmKernel k = cm_kernel_for(a);
-    const size_t smem = cm_smem_bytes(a.G);
+    const size_t smem = cm_smem_bytes(a.G, a.db, a.storage);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int nsm = 0, per = 0;
@@ -537,15 +751,16 @@ cudaError_t launch_cm_merge(const CmMergeArgs &m, cudaStream_t s)
 {
     if (m.nq <= 0) return cudaSuccess;
     CmMergeArgs b = m;
-    int T = 1;
-    while (T < m.K + m.cap) T <<= 1;
+    int T = 32;
+    while (T < m.cap) T <<= 1;
     b.T = T;
-    const size_t smem = (size_t)T * 8;
+    const size_t smem = (size_t)(T + m.K) * 8 * MERGE_WARPS;
     cudaError_t e = cudaFuncSetAttribute(cm_merge_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t grid = m.nq < 152 * 16 ? m.nq : 152 * 16;
-    cm_merge_kernel<<<(unsigned)grid, 256, smem, s>>>(b);
+    int64_t grid = (m.nq + MERGE_WARPS - 1) / MERGE_WARPS;
+    if (grid > 152 * 16) grid = 152 * 16;
+    cm_merge_kernel<<<(unsigned)grid, MERGE_WARPS * 32, smem, s>>>(b);
     return cudaGetLastError();
 }
 

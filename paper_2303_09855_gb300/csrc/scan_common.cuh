@@ -85,34 +85,52 @@ __device__ __forceinline__ QPiece<NL> ld_qpiece(const float *q)
     return r;
 }
 
-// S + (x - q)^2 over the piece, even dims into S.x and odd dims into S.y.
-// (The packed f32x2 subtract/FMA of sm_100+ gives the same values but
-// measured about 12% slower in this loop, so the chains stay scalar.)
+// S + (x - q)^2 over two consecutive dims (x0, x1) of a piece: the even dim
+// into S.x, the odd one into S.y, each rounded as the scalar
+// t = x - q; S = fma(t, t, S) would be.  With ADSX_F32X2 (the default) one
+// packed f32x2 subtract and one packed f32x2 FMA (sm_100+) do both lanes of
+// the pair: the same IEEE round-to-nearest operation per element, so the
+// same values, in half the instructions.
+#ifndef ADSX_F32X2
+#define ADSX_F32X2 1
+#endif
+__device__ __forceinline__ float2 add_pair(float x0, float x1, float q0, float q1, float2 S)
+{
+#if ADSX_F32X2
+    asm("{\n .reg .b64 xv, qv, tv, sv;\n"
+        " mov.b64 xv, {%2, %3};\n mov.b64 qv, {%4, %5};\n mov.b64 sv, {%0, %1};\n"
+        " sub.rn.f32x2 tv, xv, qv;\n fma.rn.f32x2 sv, tv, tv, sv;\n"
+        " mov.b64 {%0, %1}, sv;\n}"
+        : "+f"(S.x), "+f"(S.y)
+        : "f"(x0), "f"(x1), "f"(q0), "f"(q1));
+#else
+    float t;
+    t = x0 - q0; S.x = fmaf(t, t, S.x);
+    t = x1 - q1; S.y = fmaf(t, t, S.y);
+#endif
+    return S;
+}
+
+// S + (x - q)^2 over the piece, even dims into S.x and odd dims into S.y
+// (dims in ascending order within each chain).
 __device__ __forceinline__ float2 add_piece(float4 x, const QPiece<4> &q, float2 S, float)
 {
-    float t;
-    t = x.x - q.a.x; S.x = fmaf(t, t, S.x);
-    t = x.y - q.a.y; S.y = fmaf(t, t, S.y);
-    t = x.z - q.a.z; S.x = fmaf(t, t, S.x);
-    t = x.w - q.a.w; S.y = fmaf(t, t, S.y);
+    S = add_pair(x.x, x.y, q.a.x, q.a.y, S);
+    S = add_pair(x.z, x.w, q.a.z, q.a.w, S);
     return S;
 }
 template <typename H>
 __device__ __forceinline__ float2 add_piece(uint4 x, const QPiece<2> &q, float2 S, H h)
 {
-    float v0, v1, t;
+    float v0, v1;
     unpack2(x.x, v0, v1, h);
-    t = v0 - q.a.x; S.x = fmaf(t, t, S.x);
-    t = v1 - q.a.y; S.y = fmaf(t, t, S.y);
+    S = add_pair(v0, v1, q.a.x, q.a.y, S);
     unpack2(x.y, v0, v1, h);
-    t = v0 - q.a.z; S.x = fmaf(t, t, S.x);
-    t = v1 - q.a.w; S.y = fmaf(t, t, S.y);
+    S = add_pair(v0, v1, q.a.z, q.a.w, S);
     unpack2(x.z, v0, v1, h);
-    t = v0 - q.b.x; S.x = fmaf(t, t, S.x);
-    t = v1 - q.b.y; S.y = fmaf(t, t, S.y);
+    S = add_pair(v0, v1, q.b.x, q.b.y, S);
     unpack2(x.w, v0, v1, h);
-    t = v0 - q.b.z; S.x = fmaf(t, t, S.x);
-    t = v1 - q.b.w; S.y = fmaf(t, t, S.y);
+    S = add_pair(v0, v1, q.b.z, q.b.w, S);
     return S;
 }
 
@@ -156,8 +174,8 @@ __device__ __forceinline__ float group_sum(const float2 (&pp)[NL], int lane)
 // 16-bit storage: the exact FP32 distance of the candidate at CSR row `pos`
 // for every lane with `need`, recomputed from the FP32 row copy one candidate
 // at a time by the whole warp (each lane a 4-dim slice, then a butterfly sum
-// whose result is the same on all lanes).  qv: the query (Dp floats, shared
-// or global memory).
+// whose result is the same on all lanes).  qv: each lane's query (Dp floats,
+// shared or global memory; lanes may hold different queries).
 __device__ __forceinline__ float recheck_rows(const float *__restrict__ rows32, int Dp,
                                               const float *qv, bool need, int pos, float S,
                                               int lane)
@@ -167,11 +185,13 @@ __device__ __forceinline__ float recheck_rows(const float *__restrict__ rows32, 
         const int src = __ffs(mask) - 1;
         mask &= mask - 1;
         const int p = __shfl_sync(FULL, pos, src);
+        const float *qs = reinterpret_cast<const float *>(__shfl_sync(
+            FULL, (unsigned long long)reinterpret_cast<uintptr_t>(qv), src));
         const float *row = rows32 + (int64_t)p * Dp;
         float part = 0.f;
         for (int j = lane * 4; j < Dp; j += 128) {
             const float4 x = __ldg(reinterpret_cast<const float4 *>(row + j));
-            const float4 q = *reinterpret_cast<const float4 *>(qv + j);
+            const float4 q = *reinterpret_cast<const float4 *>(qs + j);
             float t;
             t = x.x - q.x; part = fmaf(t, t, part);
             t = x.y - q.y; part = fmaf(t, t, part);

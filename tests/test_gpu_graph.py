@@ -32,24 +32,26 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_helpers import REL, kth_near_tie, near_tie_queries
+from gpu_helpers import REL, kth_near_tie, near_tie_queries, topk_row_mismatch
 
 pytestmark = pytest.mark.gpu
 
 K, EF, NE, EPC = 10, 64, 3, 3
 
 
-def _match_sequential(ids, d2, dims, Y, Qr, oids, odims, margin, ok, min_frac=0.8):
+def _match_sequential(ids, d2, dims, Y, Qr, oids, od2, odims, margin, ok, min_frac=0.8):
     """The GPU search replays each batch in list order, so it follows the
     paper's sequential order (the oracle) exactly up to rounding: every
     query whose probe set is not a near-tie and whose closest call in the
     oracle (smallest relative gap of any comparison that decided the search)
     is at least REL returns the oracle's ids and samples the oracle's number
-    of dims; the others are counted and must be a small minority.  Every
+    of dims (the returned ids in the oracle's order, except between keys
+    within REL of each other); the others are counted and must be a small
+    minority.  Every
     returned distance is exact and the ids of a query are distinct."""
     good = ok & (margin >= REL)
     for q in np.nonzero(good)[0]:
-        assert np.array_equal(ids[q], oids[q]), (q, ids[q], oids[q])
+        assert not topk_row_mismatch(ids[q], d2[q], oids[q], od2[q]), (q, ids[q], oids[q])
         if dims is not None:
             assert dims[q] == odims[q], (q, dims[q], odims[q])
     for q in range(len(Qr)):
@@ -129,7 +131,7 @@ def test_graph_search_matches_oracle(gr, eps0, dd, pp):
                                                           max_iter=4 * EF, pp=pp,
                                                           return_margin=True)
     ok = ~near_tie_queries(Cr, Qr, NE)
-    _match_sequential(ids, d2, dims, Y, Qr, oids, odims, margin, ok)
+    _match_sequential(ids, d2, dims, Y, Qr, oids, od2, odims, margin, ok)
     assert np.all(np.diff(np.where(ids >= 0, d2, np.inf), axis=1) >= -1e-6 * (1 + d2[:, :1]))
     if math.isfinite(eps0):
         _, _, fdims = g.search(wl.Q, K, EF, eps0=math.inf, return_dims=True, n_entry=NE)
@@ -156,7 +158,7 @@ def test_graph_many_entries_match_oracle(gr, pp):
                                                           max_iter=4 * ef, pp=pp,
                                                           return_margin=True)
         ok = ~near_tie_queries(Cr, Qr, NE)
-        _match_sequential(ids, d2, dims, Y, Qr, oids, odims, margin, ok)
+        _match_sequential(ids, d2, dims, Y, Qr, oids, od2, odims, margin, ok)
         # exact DCOs: every distinct start vertex costs D dims; ADSampling
         # rejects some of the later start batches early
         _, _, xdims = g24.search(wl.Q, K, ef, eps0=math.inf, return_dims=True, n_entry=NE,
@@ -252,7 +254,9 @@ def test_graph_cosine_matches_oracle(gr, pp):
         ok = ~near_tie_queries(Cn, Qn, NE)
         good = ok & (margin >= REL)
         for q in np.nonzero(good)[0]:
-            assert np.array_equal(ids[q], oids[q]) and dims[q] == odims[q], q
+            # similarities 1 - d^2/2 against the oracle's squared distances
+            assert not topk_row_mismatch(ids[q], 2.0 - 2.0 * cs[q], oids[q], od2[q]), q
+            assert dims[q] == odims[q], q
         assert good.mean() >= 0.8, good.mean()
         for q in range(len(Qn)):
             row = ids[q][ids[q] >= 0]
@@ -283,6 +287,12 @@ def test_graph_maximum_sizes(gr):
                                                       math.inf, 32, max_iter=4 * 512,
                                                       return_margin=True)
         ok = ~near_tie_queries(Cr, Qr[:nq], 16)
-        _match_sequential(ids, d2, None, Y, Qr[:nq], oids, None, margin, ok, min_frac=0.5)
+        # 512 results and hundreds of expansions: nearly every query has some
+        # comparison closer than REL, so besides the exact match of the
+        # queries without one, the result sets must overlap almost entirely
+        _match_sequential(ids, d2, None, Y, Qr[:nq], oids, od2, None, margin, ok, min_frac=0.0)
+        overlap = np.mean([len(set(ids[q].tolist()) & set(oids[q].tolist())) / 512.0
+                           for q in range(nq)])
+        assert overlap >= 0.99, overlap
     finally:
         g64.close()

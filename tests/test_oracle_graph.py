@@ -236,7 +236,7 @@ def test_vertices_are_tested_one_at_a_time_hand_worked():
 
 def test_closest_call_margin():
     """The margin the oracle reports per query is the smallest relative gap of
-    any comparison that decided the search: with exact DCOs and ef = 1, start
+    any comparison that steered the search: with exact DCOs and ef = 1, start
     vertices at squared distances 1 and 1 + 1e-7 give about 1e-7 (the second
     DCO's S_D against r^2 = 1); 1 and 2 give |2/1 - 1| = 1."""
     D = 8
