@@ -49,6 +49,8 @@ def parse():
                     help="headline = the SIFT-shaped QPS@recall metric (default); the others "
                          "measure the batched uneven, serving and precision forms")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the production forms (precision, batched, serving) in the default line")
     ap.add_argument("--start-clusters", type=int, default=8,
                     help="graph mode: clusters whose entry vertices start a search")
     ap.add_argument("--graph-nprobe", type=int, default=16,
@@ -180,18 +182,28 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def scan_traffic(workload=None, nprobe=None, storage="f32"):
-    """DRAM bytes per scan launch from the committed 1-pass ncu capture
-    (profiles/scan_traffic.json), if it was taken on the current scan source,
-    the same workload and nprobe (else None)."""
+SCAN_SOURCES = ("scan_common.cuh", "scan.cu", "cmscan.cu")
+
+
+def scan_source_hash():
+    """sha256[:16] over the scan kernels' sources (both schedules)."""
     import hashlib
+    h = hashlib.sha256()
+    for name in SCAN_SOURCES:
+        with open(os.path.join(ROOT, "paper_2303_09855_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def scan_traffic(workload=None, nprobe=None, storage="f32"):
+    """DRAM bytes of one search's scan-kernel launches from the committed 1-pass
+    ncu capture (profiles/scan_traffic.json), if it was taken on the current
+    scan sources, the same workload and nprobe (else None)."""
     path = os.path.join(ROOT, "profiles", "scan_traffic.json")
-    src = os.path.join(ROOT, "paper_2303_09855_gb300", "csrc", "scan.cu")
     try:
         with open(path) as f:
             t = json.load(f)
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if t.get("scan_cu_sha256_16") != h:
+        if t.get("scan_sources_sha256_16") != scan_source_hash():
             return None
         if workload is not None and (t.get("workload") != workload or t.get("nprobe") != nprobe
                                      or storage != "f32"):
@@ -199,6 +211,20 @@ def scan_traffic(workload=None, nprobe=None, storage="f32"):
         return t
     except Exception:
         return None
+
+
+def cm_round_count(nprobe, r0=1, growth=4):
+    """Rounds of the cluster-major schedule for nprobe probe ranks (round 0 over
+    ranks [0, r0), then ranges growing `growth` times; a short tail joins the
+    last) -- the library's own rule, for the launch count."""
+    n, lo = 1, r0
+    while lo < nprobe:
+        hi = max(lo + 1, lo * growth)
+        if hi >= nprobe or 2 * (nprobe - hi) < hi - lo:
+            hi = nprobe
+        n += 1
+        lo = hi
+    return n
 
 
 def cpu_baseline_oracle(wl, K, nprobe, eps0, dd, seconds):
@@ -361,10 +387,9 @@ def run_batched(args):
             "ads": res["ads"], "fd_scan": res["fd"], "ads_bf16": res["ads_bf16"],
             "speedup_vs_fd": res["fd"]["ms"] / res["ads"]["ms"],
             "dims_fraction_vs_fd": res["ads"]["dims"] / res["fd"]["dims"]}
-    print(json.dumps(line), flush=True)
     for _, _, index in arms[1:]:
         index.close()
-    return 0
+    return line
 
 
 def run_serving(args):
@@ -447,9 +472,8 @@ def run_serving(args):
                        "arrivals": "open-loop Poisson, submitted in 200 us windows"},
             "recall10": recall, "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"],
             "per_rate": out}
-    print(json.dumps(line), flush=True)
     ix.close()
-    return 0
+    return line
 
 
 def run_precision(args):
@@ -560,8 +584,34 @@ def run_precision(args):
                        "nprobe": nprobe, "eps0": args.eps0, "delta_d": 32},
             "per_storage": res, "fd_scan_f32": fd_f32, "rotation_f32": rot,
             "speedup_f32_vs_fd": fd_f32["ms"] / res["f32"]["ms"]}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
+
+
+def production_forms(args):
+    """The three production forms, each through its own mode at a reduced size
+    (stated in its entry), for the default bench line: precision (GIST-shaped,
+    FP32 / BF16 / FP16 storage, error against FP64), batched uneven (one
+    persistent launch per batch, CUDA-graph replay, autotuned) and serving
+    (continuous batching, p50 / p99 under Poisson arrivals)."""
+    import copy
+    import torch
+    out = {}
+    for name, fn, scale in (("precision", run_precision, 0.25), ("batched", run_batched, 0.25),
+                            ("serving", run_serving, 0.2)):
+        a = copy.copy(args)
+        a.scale, a.storage = scale, "f32"
+        a.steps, a.warmup = min(args.steps, 10), 3
+        t0 = time.time()
+        try:
+            r = fn(a)
+            r["scale"] = scale
+        except Exception as ex:                     # reported, the headline line still prints
+            r = {"error": repr(ex)[:300]}
+        r["wall_s"] = time.time() - t0
+        out[name] = r
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_graph(args):
@@ -652,14 +702,12 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
-    if args.mode == "batched":
-        return run_batched(args)
-    if args.mode == "serving":
-        return run_serving(args)
+    if args.mode in ("batched", "serving", "precision"):
+        fn = {"batched": run_batched, "serving": run_serving, "precision": run_precision}
+        print(json.dumps(fn[args.mode](args)), flush=True)
+        return 0
     if args.mode == "graph":
         return run_graph(args)
-    if args.mode == "precision":
-        return run_precision(args)
     import torch
     ws, rank, local = dist_env()
     if ws > 1:
@@ -704,12 +752,18 @@ def main():
     np_fd = np_fd or NPROBE_GRID[-1]
     np_ads = np_ads or NPROBE_GRID[-1]
 
+    # the scan schedule and its shape from the library's autotuner, on the
+    # whole batch at the ADSampling arm's nprobe, with the metric's delta_d
+    _, _, tune_ms = adsx.autotune(ix, Qd, args.K, np_ads, args.eps0, delta_d=args.delta_d)
+    scan_cfg = adsx.scan_config(ix)
+    scan_cfg["tune_ms"] = tune_ms
+
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)   # 256 MB > L2
     adsx.set_stage_timing(ix, True)
     stream = torch.cuda.current_stream()
 
     def timed(nprobe, eps0, steps, warmup, dd=None):
-        tot, scan_ms, dims_sum = 0.0, 0.0, 0
+        tot, scan_ms, dims_sum, kern_ms, kern_n = 0.0, 0.0, 0, 0.0, 0
         for s in range(warmup + steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -722,7 +776,11 @@ def main():
             if s >= warmup:
                 tot += e0.elapsed_time(e1)
                 scan_ms += adsx.stage_ms(ix)[3]
+                km, kn = adsx.scan_kernel_ms(ix)
+                kern_ms += km
+                kern_n = kn
                 dims_sum += int(dims.sum().item())
+        timed.kernel = (kern_ms / steps, kern_n)
         return tot / steps, scan_ms / steps, dims_sum / steps, ids
 
     # FDScanning arm (the baseline the metric compares against).  Each arm is an
@@ -731,6 +789,7 @@ def main():
     nvtx = torch.cuda.nvtx
     nvtx.range_push("fd_arm")
     fd_ms, fd_scan_ms, fd_dims, _ = timed(np_fd, math.inf, max(3, args.steps // 2), 2)
+    fd_kern_ms, _ = timed.kernel
     nvtx.range_pop()
     fd_ms = max_over_ranks(fd_ms)
 
@@ -764,6 +823,7 @@ def main():
     nvtx.range_push("ads_arm")
     with Clocks(gpu_idx) as clk:
         ads_ms, ads_scan_ms, ads_dims, ids = timed(np_ads, args.eps0, args.steps, args.warmup)
+    ads_kern_ms, ads_kern_n = timed.kernel
     nvtx.range_pop()
     torch.cuda.synchronize()
     stage = adsx.stage_ms(ix)
@@ -794,8 +854,18 @@ def main():
     # rechecks of 16-bit storage are not counted: a lower bound on bytes)
     esz = 4.0 if args.storage == "f32" else 2.0
     algo_bytes = esz * ads_dims
-    achieved = algo_bytes / (ads_scan_ms * 1e-3) / 1e9
+    achieved = algo_bytes / (ads_kern_ms * 1e-3) / 1e9
     tr = scan_traffic(wl.name, np_ads, args.storage)
+    traffic = tr["dram_bytes_per_search"] if tr else None
+    # FP32 pipe: 152 SMs x 128 lanes x 2 flops (FMA) x the measured SM clock;
+    # the distance arithmetic is 3 flops (subtract, multiply, add) per dim
+    clk = clk.summary()
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    cm = scan_cfg["schedule"] == adsx.SCHED_CLUSTER or (
+        scan_cfg["schedule"] == adsx.SCHED_AUTO and nq >= 2048 and np_ads >= 8
+        and nq * np_ads >= 8 * wl.nlist)
+    launches_per_search = (5 + 1 + 5 * cm_round_count(np_ads) + 2) if cm else 6
     fd_frac = ads_dims / fd_dims if fd_dims else None
     line = {
         "metric": METRIC, "value": job_throughput(nq, ws, ads_ms), "unit": UNIT, "n_gpus": ws,
@@ -819,18 +889,26 @@ def main():
         "calibration": sweep,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_kind": peak_kind,
-                     "kernel": "ads_scan_kernel",
-                     "traffic": (tr["dram_bytes_per_launch"] * ads_dims / tr["dims_per_launch"])
-                     if tr else None,
-                     "dram_frac": ((tr["dram_bytes_per_launch"] * ads_dims / tr["dims_per_launch"])
-                                   / (ads_scan_ms * 1e-3) / 1e9 / hbm) if tr else None,
-                     "algorithmic_bytes_per_launch": algo_bytes},
+                     "kernel": ("cm_scan_kernel (%d cluster-major rounds per search)"
+                                % ads_kern_n) if cm else "ads_scan_kernel",
+                     "kernel_ms_per_search": ads_kern_ms,
+                     "algorithmic_bytes_per_search": algo_bytes,
+                     "traffic": traffic,
+                     "dram_frac": (traffic / (ads_kern_ms * 1e-3) / 1e9 / hbm) if traffic else None,
+                     "fd_frac": (esz * fd_dims / (fd_kern_ms * 1e-3) / 1e9 / hbm)
+                     if fd_kern_ms else None,
+                     "alu": {"achieved": 3.0 * ads_dims / (ads_kern_ms * 1e-3) / 1e12,
+                             "peak": fp32_peak, "unit": "TFLOP/s",
+                             "frac": 3.0 * ads_dims / (ads_kern_ms * 1e-3) / 1e12 / fp32_peak}},
+        "scan_config": scan_cfg,
         "e2e": {"value": e2e_qps, "unit": UNIT, "h2d_bytes_per_step": int(nq * wl.D * 4),
                 "d2h_bytes_per_step": int(nq * args.K * 12)},
         # per search: query rotation, query norms, tcgen05 centroid GEMM, top-nprobe
-        # select, test factors, scan (no finalize: one split per query at 10k queries)
-        "gpu_launches": 6 * args.steps,
-        "clocks": clk.summary(),
+        # select, test factors; cluster-major: the initial merge, per round the plan
+        # (count, offsets, scatter), the scan and the merge, then the overflow
+        # check and its (usually empty) query-major re-run; query-major: the scan
+        "gpu_launches": launches_per_search * args.steps,
+        "clocks": clk,
     }
     # dims fraction of ADS vs FD at the same nprobe (Sec. 6.1 evaluated-dims metric)
     if np_fd == np_ads:
@@ -848,8 +926,13 @@ def main():
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline_oracle(wl, args.K, np_ads, args.eps0,
                                                    args.delta_d, args.cpu_seconds)
+    if not args.no_extras and ws == 1:
+        ix.close()
+        ix = None
+        line["production_forms"] = production_forms(args)
     print(json.dumps(line), flush=True)
-    ix.close()
+    if ix is not None:
+        ix.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0

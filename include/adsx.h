@@ -304,29 +304,53 @@ int adsx_stream_status(const adsx_index *index, void *stream);
  *                       growing 4x -- each round testing against the K-th
  *                       distance of the rounds before it (a valid r: the
  *                       K-th of a subset of exact candidate distances), so
- *                       results do not depend on scheduling.  Needs delta_d <= 64 (or the test
- *                       off) and an L2 or cosine index; other searches run
- *                       query-major.
+ *                       results do not depend on scheduling.  A tile's
+ *                       first step is computed for every (query, member);
+ *                       its later steps only for the pairs still live.  A
+ *                       cluster is shared among items in chunks of
+ *                       tiles_per_item tiles.  Needs delta_d <= 64 (or the
+ *                       test off) and an L2 or cosine index; other searches
+ *                       run query-major.
  *   ADSX_SCHED_AUTO     cluster-major when it applies to a large batch
  *                       (nq >= 2048, nprobe >= 8, nq * nprobe >= 8 nlist: each
  *                       cluster probed 8 times on average), else query-major.
  *                       The initial setting.
  *   queries_per_item    1..64, or 0 to keep the current value (16 initially).
+ *   tiles_per_item      1..64 32-member tiles, or 0 to keep the current value
+ *                       (4 initially).
  * Not thread-safe with other calls on the same index.
  */
-int adsx_set_scan_schedule(adsx_index *index, int32_t schedule, int32_t queries_per_item);
+int adsx_set_scan_schedule(adsx_index *index, int32_t schedule, int32_t queries_per_item,
+                           int32_t tiles_per_item);
 
 /*
- * adsx_autotune -- picks the step delta_d (Sec. 6.2.4: 16..64 give the best
- * trade-off; the candidates are 16, 32, 48, 64, up to the padded D) and the
- * work-item granularity used when queries are split (24, 48 or 96 items per
- * SM) by timing adsx_search on a caller-supplied query sample (one warm-up
- * and three timed runs each, CUDA events on `stream`).  The winner is stored
- * in the index and used by searches that pass delta_d = 0; the item
- * granularity applies to every later search on the index.
+ * adsx_scan_config -- the index's current scan settings: the step delta_d
+ * used when a search passes 0, the schedule, queries and tiles per
+ * cluster-major item, and the query-major work items per SM (any output
+ * pointer may be NULL).
+ */
+int adsx_scan_config(const adsx_index *index, int32_t *delta_d, int32_t *schedule,
+                     int32_t *queries_per_item, int32_t *tiles_per_item,
+                     int32_t *items_per_sm);
+
+/*
+ * adsx_autotune -- picks, by timing adsx_search on a caller-supplied query
+ * sample (one warm-up and three timed runs each, CUDA events on `stream`),
+ * the step delta_d (Sec. 6.2.4: 16..64 give the best trade-off; the
+ * candidates are 16, 32, 48, 64, up to the padded D) under each scan
+ * schedule (query-major, cluster-major), then the winner's shape: queries
+ * per item (8, 16, 32) and tiles per item (2, 4, 8) for cluster-major, work
+ * items per SM (24, 48, 96) for query-major.  The winner is stored in the
+ * index: the schedule and shape apply to every later search, the step to
+ * searches that pass delta_d = 0 (adsx_scan_config reads them back).  Tune
+ * on a sample the size of the batches to be searched: the schedule that
+ * wins depends on it.
  *   Qv               host or device, nq x D sample queries (nq >= 1).
  *   K, nprobe, eps0  the search parameters to tune for.
- *   best_delta_d, best_items_per_sm, best_ms  outputs (each may be NULL).
+ *   best_delta_d     in: 0 to tune the step, or a step (a multiple of 16) to
+ *                    keep fixed while the schedule and shape are tuned; out:
+ *                    the step chosen (may be NULL: the step is tuned).
+ *   best_items_per_sm, best_ms  outputs (each may be NULL).
  * Not thread-safe with other calls on the same index.
  */
 int adsx_autotune(adsx_index *index, const float *Qv, int64_t nq, int32_t K,
@@ -345,6 +369,15 @@ int adsx_autotune(adsx_index *index, const float *Qv, int64_t nq, int32_t K,
  */
 int adsx_set_stage_timing(adsx_index *index, int32_t enable);
 int adsx_stage_ms(const adsx_index *index, float *ms);
+
+/*
+ * adsx_scan_kernel_ms -- with stage timing on, waits for the last timed
+ * search and writes the device time of its scan-kernel launches alone, in
+ * milliseconds, summed (*ms: the candidate scan without the planning and
+ * merging kernels around it; the query-major scan or each cluster-major
+ * round), and their number (*launches, may be NULL).
+ */
+int adsx_scan_kernel_ms(const adsx_index *index, float *ms, int32_t *launches);
 
 /*
  * adsx_search_noalloc -- adsx_search for callers that must not allocate

@@ -79,8 +79,10 @@ def load():
     lib.adsx_server_reset_stats.argtypes = [V]
     lib.adsx_server_destroy.argtypes = [V]
     lib.adsx_set_stage_timing.argtypes = [V, i32]
-    lib.adsx_set_scan_schedule.argtypes = [V, i32, i32]
+    lib.adsx_set_scan_schedule.argtypes = [V, i32, i32, i32]
+    lib.adsx_scan_config.argtypes = [V, V, V, V, V, V]
     lib.adsx_stage_ms.argtypes = [V, V]
+    lib.adsx_scan_kernel_ms.argtypes = [V, V, V]
     lib.adsx_last_error.restype = ctypes.c_char_p
     for fn in ("adsx_build_index", "adsx_build_index_metric", "adsx_index_metric",
                "adsx_build_index_kac", "adsx_build_graph", "adsx_free_graph",
@@ -88,7 +90,7 @@ def load():
                "adsx_free_index", "adsx_index_info", "adsx_search",
                "adsx_probe", "adsx_rotate", "adsx_dco_fixed_r", "adsx_stream_status",
                "adsx_set_stage_timing", "adsx_stage_ms", "adsx_search_noalloc",
-               "adsx_set_scan_schedule",
+               "adsx_set_scan_schedule", "adsx_scan_config", "adsx_scan_kernel_ms",
                "adsx_search_batched", "adsx_search_pdscan", "adsx_autotune",
                "adsx_server_create",
                "adsx_server_submit", "adsx_server_submit_many", "adsx_server_wait",
@@ -191,8 +193,8 @@ class Index:
     def dco_fixed_r(self, Q, r2, eps0, delta_d, stream=None):
         return dco_fixed_r(self, Q, r2, eps0, delta_d, stream)
 
-    def set_scan_schedule(self, schedule, queries_per_item=0):
-        return set_scan_schedule(self, schedule, queries_per_item)
+    def set_scan_schedule(self, schedule, queries_per_item=0, tiles_per_item=0):
+        return set_scan_schedule(self, schedule, queries_per_item, tiles_per_item)
 
 
 def build_index(X, P, centroids, assign, storage=F32, stream=None, metric=L2) -> Index:
@@ -463,11 +465,14 @@ def dco_fixed_r(index: Index, Q, r2, eps0: float, delta_d: int, stream=None):
     return dec, dims
 
 
-def autotune(index: Index, Q, K: int, nprobe: int, eps0: float = 2.1, stream=None):
+def autotune(index: Index, Q, K: int, nprobe: int, eps0: float = 2.1, stream=None,
+             delta_d: int = 0):
     """adsx_autotune: returns (delta_d, items_per_sm, ms) of the fastest
-    configuration on the sample Q; searches with delta_d=0 then use it."""
+    configuration on the sample Q (the schedule and its shape are stored in
+    the index too: scan_config); searches with delta_d=0 then use the step.
+    delta_d != 0 keeps the step fixed and tunes the rest."""
     Q = _prep_queries(Q)
-    dd, ip, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    dd, ip, ms = ctypes.c_int32(int(delta_d)), ctypes.c_int32(), ctypes.c_float()
     _check(load().adsx_autotune(index.handle, _ptr(Q), Q.shape[0], int(K), int(nprobe),
                                 float(eps0) if math.isfinite(eps0) else float("inf"),
                                 ctypes.byref(dd), ctypes.byref(ip), ctypes.byref(ms),
@@ -478,11 +483,23 @@ def autotune(index: Index, Q, K: int, nprobe: int, eps0: float = 2.1, stream=Non
 SCHED_AUTO, SCHED_QUERY, SCHED_CLUSTER = 0, 1, 2
 
 
-def set_scan_schedule(index: Index, schedule: int, queries_per_item: int = 0):
+def set_scan_schedule(index: Index, schedule: int, queries_per_item: int = 0,
+                      tiles_per_item: int = 0):
     """adsx_set_scan_schedule: SCHED_AUTO, SCHED_QUERY (one warp per query)
-    or SCHED_CLUSTER (one warp per cluster and query group, in rounds);
-    queries_per_item 1..64 (0 keeps the current value)."""
-    _check(load().adsx_set_scan_schedule(index.handle, int(schedule), int(queries_per_item)))
+    or SCHED_CLUSTER (one warp per cluster chunk and query group, in rounds);
+    queries_per_item 1..64 and tiles_per_item 1..64 (0 keeps the current
+    value)."""
+    _check(load().adsx_set_scan_schedule(index.handle, int(schedule), int(queries_per_item),
+                                         int(tiles_per_item)))
+
+
+def scan_config(index: Index):
+    """adsx_scan_config: dict of the index's delta_d (for delta_d = 0),
+    schedule, queries_per_item, tiles_per_item and items_per_sm."""
+    v = [ctypes.c_int32() for _ in range(5)]
+    _check(load().adsx_scan_config(index.handle, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("delta_d", "schedule", "queries_per_item", "tiles_per_item",
+                     "items_per_sm"), (x.value for x in v)))
 
 
 def set_stage_timing(index: Index, enable: bool = True):
@@ -496,6 +513,14 @@ def stage_ms(index: Index):
     out = (ctypes.c_float * 4)()
     _check(load().adsx_stage_ms(index.handle, out))
     return [float(x) for x in out]
+
+
+def scan_kernel_ms(index: Index):
+    """adsx_scan_kernel_ms: (device ms of the last timed search's scan-kernel
+    launches summed, number of those launches)."""
+    ms, n = ctypes.c_float(), ctypes.c_int32()
+    _check(load().adsx_scan_kernel_ms(index.handle, ctypes.byref(ms), ctypes.byref(n)))
+    return float(ms.value), int(n.value)
 
 
 def stream_status(index: Index, stream=None):

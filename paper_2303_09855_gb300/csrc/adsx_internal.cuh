@@ -69,6 +69,11 @@ struct Index {
     bool timing = false;
     bool timed_once = false;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // and around each scan-kernel launch of the search (rounds of the
+    // cluster-major schedule, the query-major scan): start/end pairs
+    static constexpr int MAX_KEV = 16;
+    cudaEvent_t kev[2 * MAX_KEV] = {};
+    int nkev = 0;
 };
 
 // ----------------------------------------------------------------- device

@@ -151,6 +151,17 @@ cudaError_t centroid_distances(const Index *ix, const float *qrot, int64_t nq, f
                                 ix->nlist, ix->nlist, qn, ix->cnorm, ix->err, sc.s);
 }
 
+// Stage timing: an event before (begin) or after (end) a scan-kernel launch.
+cudaError_t mark_kernel(const Index *ix, bool begin, cudaStream_t s)
+{
+    if (!ix->timing) return cudaSuccess;
+    Index *w = const_cast<Index *>(ix);
+    if (w->nkev >= Index::MAX_KEV) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(w->kev[2 * w->nkev + (begin ? 0 : 1)], s);
+    if (!begin) ++w->nkev;
+    return e;
+}
+
 cudaError_t mark(const Index *ix, int i, cudaStream_t s)
 {
     if (!ix->timing) return cudaSuccess;
@@ -489,6 +500,8 @@ int adsx_free_index(adsx_index *index)
     cudaFree(ix->err);
     for (cudaEvent_t e : ix->ev)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : ix->kev)
+        if (e) cudaEventDestroy(e);
     delete ix;
     return ADSX_OK;
 }
@@ -576,8 +589,10 @@ static cudaError_t qm_scan(const Index *ix, adsx::ScanArgs a, Scratch &sc)
             return e;
     }
     if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+    if ((e = mark_kernel(ix, true, s)) != cudaSuccess) return e;
     if ((e = adsx::launch_ads_scan(a, adsx::ads_scan_grid(a, ix->device), s)) != cudaSuccess)
         return e;
+    if ((e = mark_kernel(ix, false, s)) != cudaSuccess) return e;
     return adsx::launch_finalize_topk(a, s);
 }
 
@@ -731,7 +746,9 @@ static cudaError_t cm_scan(const Index *ix, const adsx::ScanArgs &a, Scratch &sc
                                       ix->nlist, G, ix->cm_tpi, ix->off, pl, s)) != cudaSuccess)
             return e;
         c.test_on = i == 0 ? 0 : a.test_on;
+        if ((e = mark_kernel(ix, true, s)) != cudaSuccess) return e;
         if ((e = adsx::launch_cm_scan(c, ix->device, s)) != cudaSuccess) return e;
+        if ((e = mark_kernel(ix, false, s)) != cudaSuccess) return e;
         m.final_pass = i + 1 == rounds.size();
         if ((e = adsx::launch_cm_merge(m, s)) != cudaSuccess) return e;
     }
@@ -772,6 +789,7 @@ static int search_impl(const adsx_index *index, const float *Qv, int64_t nq, int
     Buf<int64_t> oi, odims;
     float *qrot = nullptr;
     int32_t *probes = nullptr;
+    const_cast<Index *>(ix)->nkev = 0;
     CK(stage_in(sc, Qv, (size_t)nq * ix->D, q), "stage queries");
     CK(stage_out(sc, ids, (size_t)nq * K, oi), "stage ids");
     CK(stage_out(sc, dists, (size_t)nq * K, od), "stage dists");
@@ -1066,6 +1084,19 @@ int adsx_dco_fixed_r(const adsx_index *index, const float *Qv, int64_t nq, const
     return finish(s, dec.host || dm.host, "fixed-r");
 }
 
+// One configuration of the search's tunables.
+struct TuneCfg {
+    int dd, sched, G, tpi, ip;
+};
+
+static void apply_cfg(Index *ix, const TuneCfg &c)
+{
+    ix->sched = c.sched;
+    ix->cm_G = c.G;
+    ix->cm_tpi = c.tpi;
+    ix->items_per_sm = c.ip;
+}
+
 int adsx_autotune(adsx_index *index, const float *Qv, int64_t nq, int32_t K, int32_t nprobe,
                   float eps0, int32_t *best_delta_d, int32_t *best_items_per_sm, float *best_ms,
                   void *stream)
@@ -1089,52 +1120,99 @@ int adsx_autotune(adsx_index *index, const float *Qv, int64_t nq, int32_t K, int
     CK(cudaEventCreate(&e1), "event");
     const bool timing = ix->timing;
     ix->timing = false;
-    const int dds[4] = {16, 32, 48, 64};
-    const int ips[3] = {24, 48, 96};
-    float best = INFINITY;
-    int bdd = ix->tuned_delta_d, bip = ix->items_per_sm;
-    const int saved_ip = ix->items_per_sm;
-    for (int di = 0; di < 4 && rc == ADSX_OK; ++di) {
-        if (dds[di] > ix->Dp) continue;
-        for (int ii = 0; ii < 3 && rc == ADSX_OK; ++ii) {
-            ix->items_per_sm = ips[ii];
-            float tot = 0.f;
-            for (int rep = 0; rep < 4 && rc == ADSX_OK; ++rep) {
-                cudaEventRecord(e0, s);
-                rc = adsx_search(index, q.dev, nq, K, nprobe, eps0, dds[di], ids, d2, nullptr, stream);
-                cudaEventRecord(e1, s);
-                if (rc) break;
-                if (cudaEventSynchronize(e1) != cudaSuccess) {
-                    rc = fail(ADSX_ECUDA, "autotune sync failed");
-                    break;
-                }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (rep > 0) tot += ms;          // first run is a warm-up
-            }
-            if (rc == ADSX_OK && tot / 3.f < best) {
-                best = tot / 3.f;
-                bdd = dds[di];
-                bip = ips[ii];
-            }
+    const TuneCfg saved{ix->tuned_delta_d, ix->sched, ix->cm_G, ix->cm_tpi, ix->items_per_sm};
+    // mean of three timed searches after a warm-up (CUDA events on `stream`)
+    auto time_cfg = [&](const TuneCfg &c, float *ms_out) -> int {
+        apply_cfg(ix, c);
+        float tot = 0.f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, s);
+            int r = adsx_search(index, q.dev, nq, K, nprobe, eps0, c.dd, ids, d2, nullptr, stream);
+            cudaEventRecord(e1, s);
+            if (r) return r;
+            if (cudaEventSynchronize(e1) != cudaSuccess) return fail(ADSX_ECUDA, "autotune sync failed");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tot += ms;
         }
+        *ms_out = tot / 3.f;
+        return ADSX_OK;
+    };
+    // Coordinate search: the step delta_d (Sec. 6.2.4's 16..64) under each
+    // schedule, then the winning schedule's own shape -- queries per item and
+    // tiles per item (cluster-major) or work items per SM (query-major).
+    // *best_delta_d != 0 on entry keeps the step fixed at that value
+    int dds[4] = {16, 32, 48, 64};
+    int ndd = 4;
+    if (best_delta_d && *best_delta_d != 0) {
+        if ((rc = check_blocks(*best_delta_d, eps0))) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            ix->timing = timing;
+            return rc;
+        }
+        dds[0] = *best_delta_d;
+        ndd = 1;
+    }
+    TuneCfg best = saved;
+    float best_t = INFINITY;
+    auto consider = [&](const TuneCfg &c) -> int {
+        float t = 0.f;
+        const int r = time_cfg(c, &t);
+        if (r == ADSX_OK && t < best_t) {
+            best_t = t;
+            best = c;
+        }
+        return r;
+    };
+    for (int di = 0; di < ndd && rc == ADSX_OK; ++di) {
+        if (ndd > 1 && dds[di] > ix->Dp) continue;
+        rc = consider({dds[di], ADSX_SCHED_QUERY, saved.G, saved.tpi, 48});
+        if (rc == ADSX_OK) rc = consider({dds[di], ADSX_SCHED_CLUSTER, 16, 4, 48});
+    }
+    const TuneCfg base = best;
+    if (rc == ADSX_OK && base.sched == ADSX_SCHED_CLUSTER) {
+        const int Gs[3] = {8, 16, 32}, tpis[3] = {2, 4, 8};
+        for (int gi = 0; gi < 3 && rc == ADSX_OK; ++gi)
+            if (Gs[gi] != base.G) rc = consider({base.dd, base.sched, Gs[gi], base.tpi, base.ip});
+        const TuneCfg b2 = best;
+        for (int ti = 0; ti < 3 && rc == ADSX_OK; ++ti)
+            if (tpis[ti] != b2.tpi) rc = consider({b2.dd, b2.sched, b2.G, tpis[ti], b2.ip});
+    } else if (rc == ADSX_OK) {
+        const int ips[2] = {24, 96};
+        for (int ii = 0; ii < 2 && rc == ADSX_OK; ++ii)
+            rc = consider({base.dd, base.sched, base.G, base.tpi, ips[ii]});
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ix->timing = timing;
     if (rc) {
-        ix->items_per_sm = saved_ip;
+        apply_cfg(ix, saved);
         return rc;
     }
-    ix->tuned_delta_d = bdd;
-    ix->items_per_sm = bip;
-    if (best_delta_d) *best_delta_d = bdd;
-    if (best_items_per_sm) *best_items_per_sm = bip;
-    if (best_ms) *best_ms = best;
+    apply_cfg(ix, best);
+    ix->tuned_delta_d = best.dd;
+    if (best_delta_d) *best_delta_d = best.dd;
+    if (best_items_per_sm) *best_items_per_sm = best.ip;
+    if (best_ms) *best_ms = best_t;
     return ADSX_OK;
 }
 
-int adsx_set_scan_schedule(adsx_index *index, int32_t schedule, int32_t queries_per_item)
+int adsx_scan_config(const adsx_index *index, int32_t *delta_d, int32_t *schedule,
+                     int32_t *queries_per_item, int32_t *tiles_per_item, int32_t *items_per_sm)
+{
+    const Index *ix = reinterpret_cast<const Index *>(index);
+    if (!ix) return fail(ADSX_EINVAL, "index is NULL");
+    if (delta_d) *delta_d = ix->tuned_delta_d;
+    if (schedule) *schedule = ix->sched;
+    if (queries_per_item) *queries_per_item = ix->cm_G;
+    if (tiles_per_item) *tiles_per_item = ix->cm_tpi;
+    if (items_per_sm) *items_per_sm = ix->items_per_sm;
+    return ADSX_OK;
+}
+
+int adsx_set_scan_schedule(adsx_index *index, int32_t schedule, int32_t queries_per_item,
+                           int32_t tiles_per_item)
 {
     Index *ix = reinterpret_cast<Index *>(index);
     if (!ix) return fail(ADSX_EINVAL, "index is NULL");
@@ -1143,8 +1221,11 @@ int adsx_set_scan_schedule(adsx_index *index, int32_t schedule, int32_t queries_
         return fail(ADSX_EINVAL, "unknown scan schedule %d", schedule);
     if (queries_per_item < 0 || queries_per_item > adsx::CM_MAX_G)
         return fail(ADSX_EINVAL, "queries_per_item out of range (0..%d)", adsx::CM_MAX_G);
+    if (tiles_per_item < 0 || tiles_per_item > 64)
+        return fail(ADSX_EINVAL, "tiles_per_item out of range (0..64)");
     ix->sched = schedule;
     if (queries_per_item) ix->cm_G = queries_per_item;
+    if (tiles_per_item) ix->cm_tpi = tiles_per_item;
     return ADSX_OK;
 }
 
@@ -1153,8 +1234,10 @@ int adsx_set_stage_timing(adsx_index *index, int32_t enable)
     Index *ix = reinterpret_cast<Index *>(index);
     int rc = check_index(ix);
     if (rc) return rc;
-    if (enable && !ix->ev[0])
+    if (enable && !ix->ev[0]) {
         for (cudaEvent_t &e : ix->ev) CK(cudaEventCreate(&e), "create event");
+        for (cudaEvent_t &e : ix->kev) CK(cudaEventCreate(&e), "create event");
+    }
     ix->timing = enable != 0;
     return ADSX_OK;
 }
@@ -1168,6 +1251,25 @@ int adsx_stage_ms(const adsx_index *index, float *ms)
     if (!ix->timed_once || !ix->ev[0]) return fail(ADSX_EINVAL, "no timed search has run");
     CK(cudaEventSynchronize(ix->ev[4]), "event sync");
     for (int i = 0; i < 4; ++i) CK(cudaEventElapsedTime(&ms[i], ix->ev[i], ix->ev[i + 1]), "elapsed");
+    return ADSX_OK;
+}
+
+int adsx_scan_kernel_ms(const adsx_index *index, float *ms, int32_t *launches)
+{
+    const Index *ix = reinterpret_cast<const Index *>(index);
+    int rc = check_index(ix);
+    if (rc) return rc;
+    if (!ms) return fail(ADSX_EINVAL, "ms is NULL");
+    if (!ix->timed_once || !ix->ev[0]) return fail(ADSX_EINVAL, "no timed search has run");
+    CK(cudaEventSynchronize(ix->ev[4]), "event sync");
+    float tot = 0.f;
+    for (int i = 0; i < ix->nkev; ++i) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, ix->kev[2 * i], ix->kev[2 * i + 1]), "elapsed");
+        tot += t;
+    }
+    *ms = tot;
+    if (launches) *launches = ix->nkev;
     return ADSX_OK;
 }
 

@@ -46,6 +46,12 @@ namespace {
 using namespace scan;
 
 constexpr int CM_WARPS = 4;
+// Percentage of live (slot, member) pairs of a tile from which a step is
+// computed densely rather than pair by pair.
+#ifndef ADSX_CM_DENSE_PCT
+#define ADSX_CM_DENSE_PCT 35
+#endif
+constexpr int CM_DENSE_PCT = ADSX_CM_DENSE_PCT;
 constexpr int CM_THREADS = CM_WARPS * 32;
 #ifndef ADSX_CM_MINBLOCKS
 #define ADSX_CM_MINBLOCKS 4
@@ -68,11 +74,11 @@ template <> struct Stage<float> {
 };
 
 // Per-warp shared memory: query slots, their thresholds, live masks and dims
-// counters; per (slot, tile lane) the partial distance S_d and the outcome of
-// the last pass; the list of live (slot, lane) pairs of a pass; and the
-// tile's current step, staged member by member.
+// counters; per (slot, tile lane) the partial distance S_d; the live (slot,
+// lane) pairs of the current step and of the next; and the tile's current
+// step, staged member by member.
 struct CmCarve {
-    int qg, r2, live, dg, S, code, pairs, stile, bytes;
+    int qg, r2, live, dg, S, pa, stile, bytes;
     __host__ __device__ CmCarve(int G, int db, int row)
     {
         int o = 0;
@@ -81,8 +87,7 @@ struct CmCarve {
         r2 = o; o += 4 * G;
         live = o; o += 4 * G;
         S = o; o += 4 * 32 * G;
-        code = o; o += 32 * G;
-        pairs = o; o += 2 * 32 * G;
+        pa = o; o += 2 * 32 * G;
         o = (o + 15) & ~15;
         stile = o; o += db * 32 * row;
         bytes = (o + 15) & ~15;
@@ -162,8 +167,7 @@ __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(
     float *r2g = reinterpret_cast<float *>(base + cc.r2);
     unsigned *live = reinterpret_cast<unsigned *>(base + cc.live);
     float *Sv = reinterpret_cast<float *>(base + cc.S);
-    unsigned char *code = base + cc.code;
-    unsigned short *pairs = reinterpret_cast<unsigned short *>(base + cc.pairs);
+    unsigned short *pa = reinterpret_cast<unsigned short *>(base + cc.pa);
     unsigned char *stile = base + cc.stile;
     for (int b = threadIdx.x; b <= a.nblk && b < 256; b += CM_THREADS) s_ftab[b] = a.ftab[b];
     __syncthreads();
@@ -203,13 +207,25 @@ __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(
             int blk = 0;
             for (;;) {
                 unsigned U = 0u;                  // members live for some query
-                for (int g = 0; g < ngq; ++g) U |= live[g];
+                int L = 0;                        // live (slot, member) pairs
+                for (int g = 0; g < ngq; ++g) {
+                    const unsigned lv = live[g];
+                    U |= lv;
+                    L += __popc(lv);
+                }
                 if (U == 0u) break;
                 const int e = blk + a.db < a.nblk ? blk + a.db : a.nblk;
                 const int nb = e - blk;
                 const bool fin = e >= a.nblk;
                 const float fe = s_ftab[e];
                 const unsigned dstep = (unsigned)(e * BLK < a.D ? e * BLK : a.D);
+                // A step is dense -- every slot against every member, the
+                // step's blocks loaded once into registers -- while enough
+                // pairs are live (always the first step, and every step with
+                // the test off); else only the live pairs are computed, one
+                // per lane, from the step staged in shared memory.
+                const bool dense = blk == 0 || !a.test_on || 100 * L >= CM_DENSE_PCT * 32 * ngq;
+                if (dense) {
                 // this step's blocks of the tile: loaded once for every query
                 V v[DB][NL];
                 const T *x = cb + (int64_t)blk * stride + (int64_t)(m0 + gi) * BLK + jo;
@@ -222,7 +238,7 @@ __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(
                             v[b][k] = ld_piece(x + b * stride + k * NG * BLK);
                     }
                 }
-                if (blk == 0 || !a.test_on) {
+                {
                     // ---- dense step: every slot, every member, from registers
                     const int pos = (int)o + m0 + own;
                     auto finish = [&](int g, unsigned lv, float st, const float *qv) {
@@ -320,101 +336,99 @@ __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(
                         if (lv0) finish(g, lv0, s0, qv0);
                         if (lv1) finish(g + 1, lv1, s1, qv1);
                     }
+                }
                 } else {
-                    // ---- sparse step: stage the tile's step, then the live
-                    // (slot, member) pairs one per lane
+                // ---- sparse step: the tile's step staged in shared memory,
+                // then the live (slot, member) pairs, one per lane, 32 per
+                // pass whatever their query
+                const T *x = cb + (int64_t)blk * stride + (int64_t)(m0 + gi) * BLK + jo;
 #pragma unroll
-                    for (int b = 0; b < DB; ++b)
+                for (int b = 0; b < DB; ++b)
 #pragma unroll
-                        for (int k = 0; k < NL; ++k)
-                            if (b < nb)
-                                *reinterpret_cast<V *>(
-                                    stile + b * RB + (gi + NG * k) * ROW +
-                                    (((lane % NL) ^ Stage<T>::swz(gi + NG * k)) * 16)) = v[b][k];
-                    int np = 0;
-                    for (int g = 0; g < ngq; ++g) {
-                        const unsigned lv = live[g];
-                        if ((lv >> lane) & 1u)
-                            pairs[np + __popc(lv & below)] = (unsigned short)((g << 5) | lane);
-                        np += __popc(lv);
-                    }
-                    __syncwarp();
-                    for (int p0 = 0; p0 < np; p0 += 32) {
-                        const bool valid = p0 + lane < np;
-                        int g = 0, l = 0;
+                    for (int k = 0; k < NL; ++k)
+                        if (b < nb && ((U >> owner_lane<NL>(gi, k)) & 1u))
+                            *reinterpret_cast<V *>(
+                                stile + b * RB + (gi + NG * k) * ROW +
+                                (((lane % NL) ^ Stage<T>::swz(gi + NG * k)) * 16)) =
+                                ld_piece(x + b * stride + k * NG * BLK);
+                int npr = 0;
+                for (int g = 0; g < ngq; ++g) {
+                    const unsigned lv = live[g];
+                    if ((lv >> lane) & 1u)
+                        pa[npr + __popc(lv & below)] = (unsigned short)((g << 5) | lane);
+                    npr += __popc(lv);
+                }
+                __syncwarp();
+                for (int p0 = 0; p0 < npr; p0 += 32) {
+                    const bool valid = p0 + lane < npr;
+                    const int pr = valid ? pa[p0 + lane] : 0;
+                    const int g = pr >> 5, l = pr & 31;
+                    const int mt = own_slot<NL>(l);             // member within the tile
+                    const int pos = (int)o + m0 + mt;
+                    const float *qv = a.qrot + (int64_t)qg[g] * a.Dp;
+                    float S = 0.f;
+                    if (valid)
+                        S = Sv[g * 32 + l] +
+                            member_step_sum<T, DB>(stile + mt * ROW, mt, qv + blk * BLK, nb);
+                    const float r2 = valid ? r2g[g] : 0.f;
+                    bool out = false;                           // continues to the next step
+                    if (!fin) {
                         if (valid) {
-                            const int pr = pairs[p0 + lane];
-                            g = pr >> 5;
-                            l = pr & 31;
-                        }
-                        const int mt = own_slot<NL>(l);             // member within the tile
-                        const int pos = (int)o + m0 + mt;
-                        const float *qv = a.qrot + (int64_t)qg[g] * a.Dp;
-                        float S = 0.f;
-                        if (valid)
-                            S = Sv[g * 32 + l] +
-                                member_step_sum<T, DB>(stile + mt * ROW, mt, qv + blk * BLK, nb);
-                        const float r2 = valid ? r2g[g] : 0.f;
-                        unsigned char out = 0;                      // 1: continues
-                        if (!fin) {
-                            if (valid) {
-                                if (S > r2 * fe) {
-                                    if constexpr (FIXED) {
-                                        const int64_t off = (int64_t)qg[g] * a.N + a.ids[pos];
-                                        a.decisions[off] = 0;
-                                        if (a.dec_dims) a.dec_dims[off] = (int)dstep;
-                                    }
-                                } else {
-                                    out = 1;
-                                    Sv[g * 32 + l] = S;
-                                }
-                            }
-                        } else {
-                            bool cand = valid;
-                            if constexpr (Roundoff<T>::u > 0.f) {
-                                bool need = false;
-                                if (valid) {
-                                    need = !(r2 < INFINITY);
-                                    if (!need && r2 >= 0.f) {
-                                        const float bound =
-                                            (sqrtf(r2) + Roundoff<T>::u * a.norms[pos]) * 1.0001f;
-                                        need = sqrtf(S) <= bound;
-                                    }
-                                }
-                                S = recheck_rows(a.rows32, a.Dp, qv, need, pos, S, lane);
-                                cand = need;
-                            }
-                            const bool posv = cand && S <= r2;
-                            if constexpr (FIXED) {
-                                if (valid) {
+                            if (S > r2 * fe) {
+                                if constexpr (FIXED) {
                                     const int64_t off = (int64_t)qg[g] * a.N + a.ids[pos];
-                                    a.decisions[off] = posv ? 1 : 2;
-                                    if (a.dec_dims) a.dec_dims[off] = a.D;
+                                    a.decisions[off] = 0;
+                                    if (a.dec_dims) a.dec_dims[off] = (int)dstep;
                                 }
-                            } else if (posv) {
-                                const int q = qg[g];
-                                const unsigned idx = atomicAdd(a.app_n + q, 1u);
-                                if (idx < (unsigned)a.cap) {
-                                    a.app_d[(int64_t)q * a.cap + idx] = S;
-                                    a.app_i[(int64_t)q * a.cap + idx] = a.ids[pos];
-                                }
+                            } else {
+                                out = true;
+                                Sv[g * 32 + l] = S;
                             }
                         }
-                        if (valid) code[g * 32 + l] = out;
+                    } else {
+                        bool cand = valid;
+                        if constexpr (Roundoff<T>::u > 0.f) {
+                            bool need = false;
+                            if (valid) {
+                                need = !(r2 < INFINITY);
+                                if (!need && r2 >= 0.f) {
+                                    const float bound =
+                                        (sqrtf(r2) + Roundoff<T>::u * a.norms[pos]) * 1.0001f;
+                                    need = sqrtf(S) <= bound;
+                                }
+                            }
+                            S = recheck_rows(a.rows32, a.Dp, qv, need, pos, S, lane);
+                            cand = need;
+                        }
+                        const bool posv = cand && S <= r2;
+                        if constexpr (FIXED) {
+                            if (valid) {
+                                const int64_t off = (int64_t)qg[g] * a.N + a.ids[pos];
+                                a.decisions[off] = posv ? 1 : 2;
+                                if (a.dec_dims) a.dec_dims[off] = a.D;
+                            }
+                        } else if (posv) {
+                            const int q = qg[g];
+                            const unsigned idx = atomicAdd(a.app_n + q, 1u);
+                            if (idx < (unsigned)a.cap) {
+                                a.app_d[(int64_t)q * a.cap + idx] = S;
+                                a.app_i[(int64_t)q * a.cap + idx] = a.ids[pos];
+                            }
+                        }
+                    }
+                    // the pairs that stop here, per slot (a slot's pairs are
+                    // consecutive): dims summed and live bits cleared by the
+                    // slot's lowest lane
+                    const unsigned d = valid && !out ? (fin ? (unsigned)a.D : dstep) : 0u;
+                    const unsigned grp = __match_any_sync(FULL, valid ? g : -1);
+                    const unsigned dsum = __reduce_add_sync(grp, d);
+                    const unsigned dead = __reduce_or_sync(grp, valid && !out ? 1u << l : 0u);
+                    if (valid && lane == __ffs(grp) - 1) {
+                        if (dsum) dg[g] += dsum;
+                        if (dead) live[g] &= ~dead;
                     }
                     __syncwarp();
-                    // the pass's outcome, slot by slot: the survivors stay live;
-                    // the others sampled dstep dims (rejected) or all D (d = D)
-                    for (int g = 0; g < ngq; ++g) {
-                        const unsigned lv = live[g];
-                        if (lv == 0u) continue;
-                        const unsigned nl =
-                            __ballot_sync(FULL, ((lv >> lane) & 1u) && code[g * 32 + lane] == 1);
-                        if (lane == 0) {
-                            live[g] = nl;
-                            dg[g] += (unsigned long long)__popc(lv & ~nl) * (fin ? (unsigned)a.D : dstep);
-                        }
-                    }
+                }
                 }
                 __syncwarp();
                 blk = e;
@@ -547,6 +561,8 @@ __global__ void cm_plan_scatter_kernel(const int32_t *__restrict__ probes, int64
 // With `final_pass` the keys are written as the values the search returns.
 constexpr int MERGE_WARPS = 4;
 
+__device__ __forceinline__ unsigned below_mask(int lane) { return (1u << lane) - 1u; }
+
 __device__ __forceinline__ unsigned long long mkey(float d, int id)
 {
     return ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)id;
@@ -564,14 +580,71 @@ __device__ __forceinline__ int rank_below(const unsigned long long *a, int n, un
     return lo;
 }
 
+// The distance bits (the high word of a key) of the K-th smallest key among
+// e[0..ne) and a[0..na): a radix select, 8 bits per pass, with a 256-bin
+// histogram in shared memory (lane l owns bins 8l .. 8l+7 for the scan).
+__device__ __forceinline__ unsigned select_hi(const unsigned long long *e, int ne,
+                                              const unsigned long long *a, int na, int K,
+                                              unsigned *hist, int lane)
+{
+    unsigned prefix = 0u, pmask = 0u;
+    unsigned kk = (unsigned)K;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int b = lane; b < 256; b += 32) hist[b] = 0u;
+        __syncwarp();
+        for (int i = lane; i < ne + na; i += 32) {
+            const unsigned hi = (unsigned)((i < ne ? e[i] : a[i - ne]) >> 32);
+            if ((hi & pmask) == prefix) atomicAdd(hist + ((hi >> shift) & 255u), 1u);
+        }
+        __syncwarp();
+        unsigned c[8], sum = 0u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            c[j] = hist[8 * lane + j];
+            sum += c[j];
+        }
+        unsigned incl = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(FULL, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const unsigned excl = incl - sum;
+        const unsigned hit = __ballot_sync(FULL, excl < kk && kk <= incl);
+        const int src = __ffs(hit) - 1;
+        unsigned bin = 0u, before = 0u;
+        if (lane == src) {
+            unsigned acc = excl;
+            bool found = false;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (!found && acc + c[j] >= kk) {
+                    found = true;
+                    bin = 8u * lane + j;
+                    before = acc;
+                }
+                acc += c[j];
+            }
+        }
+        bin = __shfl_sync(FULL, bin, src);
+        before = __shfl_sync(FULL, before, src);
+        prefix |= bin << shift;
+        pmask |= 255u << shift;
+        kk -= before;
+        __syncwarp();
+    }
+    return prefix;
+}
+
 __global__ void __launch_bounds__(MERGE_WARPS * 32) cm_merge_kernel(CmMergeArgs m)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int K = m.K;
     unsigned long long *ak = reinterpret_cast<unsigned long long *>(smraw) +
-                             (size_t)warp * (m.T + K);
+                             (size_t)warp * (m.T + K + 128);
     unsigned long long *ek = ak + m.T;
+    unsigned *hist = reinterpret_cast<unsigned *>(ek + K);
     const unsigned long long NONE = ~0ull;
     for (int64_t q = (int64_t)blockIdx.x * MERGE_WARPS + warp; q < m.nq;
          q += (int64_t)gridDim.x * MERGE_WARPS) {
@@ -587,16 +660,36 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) cm_merge_kernel(CmMergeArgs 
             continue;
         }
         int ne = 0;                                   // existing entries (a prefix)
-        for (int k = lane; k < K; k += 32) {
-            const bool has = ids[k] >= 0;
-            ek[k] = has ? mkey(dk[k], (int)ids[k]) : NONE;
-            ne += __popc(__ballot_sync(__activemask(), has));
+        for (int k0 = 0; k0 < K; k0 += 32) {
+            const int k = k0 + lane;
+            const bool has = k < K && ids[k] >= 0;
+            if (k < K) ek[k] = has ? mkey(dk[k], (int)ids[k]) : NONE;
+            ne += __popc(__ballot_sync(FULL, has));
         }
-        ne = __shfl_sync(FULL, ne, 0);
+        for (int i = lane; i < (int)na; i += 32)
+            ak[i] = mkey(m.app_d[q * m.cap + i], m.app_i[q * m.cap + i]);
+        __syncwarp();
+        if (na > 64u && ne + (int)na > K) {
+            // many appended: keep only the keys whose distance is at most the
+            // K-th smallest of both lists (ties kept), then sort those
+            const unsigned th = select_hi(ek, ne, ak, (int)na, K, hist, lane);
+            int kept = 0;
+            for (int c0 = 0; c0 < (int)na; c0 += 32) {
+                const int i = c0 + lane;
+                const unsigned long long v = i < (int)na ? ak[i] : NONE;
+                const bool keep = i < (int)na && (unsigned)(v >> 32) <= th;
+                const unsigned km = __ballot_sync(FULL, keep);
+                __syncwarp();                         // the chunk is read before it is written
+                if (keep) ak[kept + __popc(km & below_mask(lane))] = v;
+                kept += __popc(km);
+                __syncwarp();
+            }
+            na = (unsigned)kept;
+            ne = rank_below(ek, ne, (unsigned long long)(th + 1u) << 32);
+        }
         int T = 32;
         while (T < (int)na) T <<= 1;
-        for (int i = lane; i < T; i += 32)
-            ak[i] = i < (int)na ? mkey(m.app_d[q * m.cap + i], m.app_i[q * m.cap + i]) : NONE;
+        for (int i = (int)na + lane; i < T; i += 32) ak[i] = NONE;
         __syncwarp();
         for (int size = 2; size <= T; size <<= 1) {
             for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -754,7 +847,8 @@ cudaError_t launch_cm_merge(const CmMergeArgs &m, cudaStream_t s)
     int T = 32;
     while (T < m.cap) T <<= 1;
     b.T = T;
-    const size_t smem = (size_t)(T + m.K) * 8 * MERGE_WARPS;
+    // per warp: appended keys, existing keys, a 256-bin histogram
+    const size_t smem = (size_t)(T + m.K + 128) * 8 * MERGE_WARPS;
     cudaError_t e = cudaFuncSetAttribute(cm_merge_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -53,7 +53,7 @@ def test_scan_traffic_only_for_its_own_source_workload_and_nprobe():
     t = bench.scan_traffic()
     if t is None:
         pytest.skip("the committed capture predates the current scan source")
-    assert t["dram_bytes_read"] > 0 and t["dims_per_launch"] > 0
+    assert t["dram_bytes_per_search"] > 0 and t["dims_per_search"] > 0
     assert bench.scan_traffic(t["workload"], t["nprobe"]) is not None
     assert bench.scan_traffic(t["workload"], t["nprobe"] + 1) is None
     assert bench.scan_traffic("another_workload", t["nprobe"]) is None

@@ -197,3 +197,29 @@ def test_bf16_and_cosine_and_pdscan_across_schedules(cm):
     finally:
         bf.close()
         co.close()
+
+
+def test_autotune_picks_schedule_and_shape(cm):
+    """adsx_autotune times delta_d under both schedules, then the winner's
+    shape (queries and tiles per item, or items per SM); the chosen setting is
+    stored in the index (adsx_scan_config) and used by later searches, whose
+    FDScanning results stay exact IVF."""
+    from paper_2303_09855_gb300 import adsx
+    adsx_mod, wl, _, Y, Cr, Qr = cm
+    ix = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign)
+    try:
+        many = np.tile(wl.Q, (30, 1))
+        dd, ip, ms = adsx.autotune(ix, many, 10, 10, eps0=2.1)
+        cfg = adsx.scan_config(ix)
+        assert cfg["delta_d"] == dd and dd in (16, 32, 48, 64) and ms > 0
+        assert cfg["schedule"] in (adsx.SCHED_QUERY, adsx.SCHED_CLUSTER)
+        if cfg["schedule"] == adsx.SCHED_CLUSTER:
+            assert cfg["queries_per_item"] in (8, 16, 32) and cfg["tiles_per_item"] in (2, 4, 8)
+        else:
+            assert cfg["items_per_sm"] in (24, 48, 96)
+        ids, d2 = ix.search(wl.Q, 10, 10, eps0=math.inf, delta_d=0)
+        ix.set_scan_schedule(adsx.SCHED_QUERY)
+        ref_ids, ref_d2 = ix.search(wl.Q, 10, 10, eps0=math.inf, delta_d=0)
+        assert np.array_equal(ids, ref_ids) and np.array_equal(d2, ref_d2)
+    finally:
+        ix.close()

@@ -112,8 +112,9 @@ def test_noalloc_tuned_step_after_autotune():
     wl = W.gen_gaussian_mixture()
     ix = adsx.build_index(wl.X, wl.P, wl.centroids, wl.assign)
     try:
-        ix.set_scan_schedule(adsx.SCHED_QUERY)
         adsx.autotune(ix, wl.Q, 10, 10, eps0=2.1)
+        # the tuned step stays; the schedule is pinned to the no-alloc one
+        ix.set_scan_schedule(adsx.SCHED_QUERY)
         Qd = torch.from_numpy(np.tile(wl.Q, (80, 1))).cuda()
         ref_ids, ref_d, ref_dims = (t.cpu().numpy() for t in
                                     ix.search(Qd, 10, 10, eps0=2.1, delta_d=0, return_dims=True))
