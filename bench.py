@@ -48,6 +48,8 @@ def parse():
                     choices=["headline", "batched", "serving", "precision", "graph"],
                     help="headline = the SIFT-shaped QPS@recall metric (default); the others "
                          "measure the batched uneven, serving and precision forms")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "query", "cluster"],
+                    help="scan schedule of the headline search (auto: the autotuner's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the production forms (precision, batched, serving) in the default line")
@@ -755,6 +757,8 @@ def main():
     # the scan schedule and its shape from the library's autotuner, on the
     # whole batch at the ADSampling arm's nprobe, with the metric's delta_d
     _, _, tune_ms = adsx.autotune(ix, Qd, args.K, np_ads, args.eps0, delta_d=args.delta_d)
+    if args.schedule != "auto":
+        ix.set_scan_schedule(adsx.SCHED_QUERY if args.schedule == "query" else adsx.SCHED_CLUSTER)
     scan_cfg = adsx.scan_config(ix)
     scan_cfg["tune_ms"] = tune_ms
 

@@ -670,7 +670,7 @@ static cudaError_t cm_plan_buffers(const Index *ix, int64_t nq, int width, int G
 }
 
 // The cluster-major schedule of a uniform search (ADSX_SCHED_CLUSTER): round
-// 0 query-major over each query's nearest cm_r0 clusters, then the later
+// 0 over each query's nearest cm_r0 clusters with the test off, then the later
 // probe ranks in rounds, each scanned cluster-major against the K-th
 // distance of the rounds before it and merged into the query's top-K; a
 // query whose round list overflowed is searched again query-major.  `a` is

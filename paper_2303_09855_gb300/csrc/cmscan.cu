@@ -53,9 +53,21 @@ constexpr int CM_WARPS = 4;
 #endif
 constexpr int CM_DENSE_PCT = ADSX_CM_DENSE_PCT;
 constexpr int CM_THREADS = CM_WARPS * 32;
+// Resident blocks per SM the register allocation is bounded for (4 warps
+// each).  The scan is latency-bound, so occupancy pays for a few spilled
+// registers: measured on the SIFT-shaped 1M x 128 benchmark (10k queries,
+// nprobe 64, K 100), scan kernel ms per search for 4 / 5 / 6 / 7 / 8 blocks:
+// FP32 4.56 / 4.05 / 3.75 / 4.05 / 5.29 (118 / 96 / 80 / 72 / 64 registers),
+// BF16 storage 5.60 (at 5) / 5.18 / 4.96 / 5.25 (6 / 7 / 8); with the live
+// state in registers, FP32 at 6: 3.72 (FDScanning 4.04), BF16 at 7: 5.24.
 #ifndef ADSX_CM_MINBLOCKS
-#define ADSX_CM_MINBLOCKS 4
+#define ADSX_CM_MINBLOCKS 6
 #endif
+#ifndef ADSX_CM_MINBLOCKS_H
+#define ADSX_CM_MINBLOCKS_H 7
+#endif
+template <typename T> struct CmMinBlocks { static constexpr int value = ADSX_CM_MINBLOCKS_H; };
+template <> struct CmMinBlocks<float> { static constexpr int value = ADSX_CM_MINBLOCKS; };
 
 // Member-block row of the staged tile step in shared memory: the 16 dims of
 // one member as NL 16-byte pieces (FP32: 4, 16-bit: 2), piece j stored in
@@ -73,16 +85,15 @@ template <> struct Stage<float> {
     __device__ static int swz(int m) { return (m >> 3) & 3; }
 };
 
-// Per-warp shared memory: query slots, their thresholds, live masks and dims
-// counters; per (slot, tile lane) the partial distance S_d; the live (slot,
-// lane) pairs of the current step and of the next; and the tile's current
+// Per-warp shared memory: query slots and their thresholds; the slots' live
+// masks while a sparse step runs; per (slot, tile lane) the partial distance
+// S_d; the live (slot, lane) pairs of a sparse step; and the tile's current
 // step, staged member by member.
 struct CmCarve {
-    int qg, r2, live, dg, S, pa, stile, bytes;
+    int qg, r2, live, S, pa, stile, bytes;
     __host__ __device__ CmCarve(int G, int db, int row)
     {
         int o = 0;
-        dg = o; o += 8 * G;           // unsigned long long, 8-byte aligned first
         qg = o; o += 4 * G;
         r2 = o; o += 4 * G;
         live = o; o += 4 * G;
@@ -151,7 +162,7 @@ __device__ __forceinline__ float member_step_sum(const unsigned char *row, int m
 // pairs are computed, one pair per lane, 32 pairs per pass whatever their
 // query: the pairs that ADSampling has rejected cost nothing more.
 template <typename T, int DB, bool FIXED>
-__global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(CmArgs a)
+__global__ void __launch_bounds__(CM_THREADS, CmMinBlocks<T>::value) cm_scan_kernel(CmArgs a)
 {
     constexpr int NL = Split<T>::NL, NG = 32 / NL, PW = BLK / NL;
     constexpr int ROW = Stage<T>::ROW, RB = 32 * ROW;
@@ -162,7 +173,6 @@ __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(
     const unsigned below = (1u << lane) - 1u;
     const CmCarve cc(a.G, a.db, ROW);
     unsigned char *base = smraw + (size_t)warp * cc.bytes;
-    unsigned long long *dg = reinterpret_cast<unsigned long long *>(base + cc.dg);
     int *qg = reinterpret_cast<int *>(base + cc.qg);
     float *r2g = reinterpret_cast<float *>(base + cc.r2);
     unsigned *live = reinterpret_cast<unsigned *>(base + cc.live);
@@ -195,70 +205,87 @@ __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(
             const int q = a.qlist[q0 + g];
             qg[g] = q;
             r2g[g] = FIXED ? a.r2fixed[q] : a.r2[q];
-            dg[g] = 0ull;
         }
         __syncwarp();
+        // dims sampled in this item by slots lane and lane + 32
+        unsigned dga = 0u, dgb = 0u;
+        const unsigned long long slots = ngq >= 64 ? ~0ull : (1ull << ngq) - 1ull;
         const T *cb = static_cast<const T *>(a.data) + o * a.Dp;
         const int64_t stride = (int64_t)n * BLK;
         for (int m0 = mb; m0 < me; m0 += 32) {
-            const unsigned vm = __ballot_sync(FULL, m0 + own < n);
-            for (int g = lane; g < ngq; g += 32) live[g] = vm;
-            __syncwarp();
+            // The tile's live state, in registers: la / lb are the live
+            // members of slots lane and lane + 32 (bit l: member
+            // own_slot(l)); am holds the slots for which this lane's own
+            // member is live.
+            const bool mine = m0 + own < n;
+            const unsigned vm = __ballot_sync(FULL, mine);
+            unsigned la = lane < ngq ? vm : 0u, lb = lane + 32 < ngq ? vm : 0u;
+            unsigned long long am = mine ? slots : 0ull;
             int blk = 0;
             for (;;) {
-                unsigned U = 0u;                  // members live for some query
-                int L = 0;                        // live (slot, member) pairs
-                for (int g = 0; g < ngq; ++g) {
-                    const unsigned lv = live[g];
-                    U |= lv;
-                    L += __popc(lv);
-                }
+                const unsigned U = __ballot_sync(FULL, am != 0ull);   // members live for some slot
                 if (U == 0u) break;
+                const int L = (int)__reduce_add_sync(FULL, (unsigned)(__popc(la) + __popc(lb)));
+                // bit g: slot g has a live member
+                const unsigned long long sl =
+                    ((unsigned long long)__ballot_sync(FULL, lb != 0u) << 32) |
+                    __ballot_sync(FULL, la != 0u);
                 const int e = blk + a.db < a.nblk ? blk + a.db : a.nblk;
                 const int nb = e - blk;
                 const bool fin = e >= a.nblk;
                 const float fe = s_ftab[e];
                 const unsigned dstep = (unsigned)(e * BLK < a.D ? e * BLK : a.D);
+                // Every pair live when the step starts samples its width: a
+                // pair stopped at d_j has sampled the widths of steps 1..j.
+                const unsigned width = dstep - (unsigned)(blk * BLK);
+                dga += (unsigned)__popc(la) * width;
+                dgb += (unsigned)__popc(lb) * width;
                 // A step is dense -- every slot against every member, the
                 // step's blocks loaded once into registers -- while enough
                 // pairs are live (always the first step, and every step with
                 // the test off); else only the live pairs are computed, one
                 // per lane, from the step staged in shared memory.
                 const bool dense = blk == 0 || !a.test_on || 100 * L >= CM_DENSE_PCT * 32 * ngq;
-                if (dense) {
-                // this step's blocks of the tile: loaded once for every query
-                V v[DB][NL];
                 const T *x = cb + (int64_t)blk * stride + (int64_t)(m0 + gi) * BLK + jo;
+                if (dense) {
+                    // this step's blocks of the tile: loaded once for every query
+                    V v[DB][NL];
 #pragma unroll
-                for (int b = 0; b < DB; ++b) {
+                    for (int b = 0; b < DB; ++b) {
 #pragma unroll
-                    for (int k = 0; k < NL; ++k) {
-                        zero_piece(v[b][k]);
-                        if (b < nb && ((U >> owner_lane<NL>(gi, k)) & 1u))
-                            v[b][k] = ld_piece(x + b * stride + k * NG * BLK);
+                        for (int k = 0; k < NL; ++k) {
+                            zero_piece(v[b][k]);
+                            if (b < nb && ((U >> owner_lane<NL>(gi, k)) & 1u))
+                                v[b][k] = ld_piece(x + b * stride + k * NG * BLK);
+                        }
                     }
-                }
-                {
-                    // ---- dense step: every slot, every member, from registers
                     const int pos = (int)o + m0 + own;
-                    auto finish = [&](int g, unsigned lv, float st, const float *qv) {
+                    // slot g's live mask loses the members m (lane g % 32 holds it)
+                    auto drop = [&](int g, unsigned m) {
+                        const unsigned cm = lane == (g & 31) ? m : 0u;
+                        if (g < 32) la &= ~cm;
+                        else lb &= ~cm;
+                    };
+                    auto finish = [&](int g, float st, const float *qv) {
                         float S = (blk == 0 ? 0.f : Sv[g * 32 + lane]) + st;
-                        const bool alive = (lv >> lane) & 1u;
+                        const bool alive = (am >> g) & 1ull;
                         const float r2 = r2g[g];
                         if (!fin) {
-                            // Case 1 / Case 2 of Algorithm 1 (squared test, Sec. 3.2)
-                            const bool rej = a.test_on && alive && S > r2 * fe;
-                            const unsigned rmk = __ballot_sync(FULL, rej);
-                            if (FIXED && rej) {
-                                const int64_t off = (int64_t)qg[g] * a.N + a.ids[pos];
-                                a.decisions[off] = 0;
-                                if (a.dec_dims) a.dec_dims[off] = (int)dstep;
+                            if (a.test_on) {
+                                // Case 1 / Case 2 of Algorithm 1 (squared test, Sec. 3.2)
+                                const bool rej = alive && S > r2 * fe;
+                                const unsigned rmk = __ballot_sync(FULL, rej);
+                                if (rmk) {
+                                    if (rej) am &= ~(1ull << g);
+                                    drop(g, rmk);
+                                    if (FIXED && rej) {
+                                        const int64_t off = (int64_t)qg[g] * a.N + a.ids[pos];
+                                        a.decisions[off] = 0;
+                                        if (a.dec_dims) a.dec_dims[off] = (int)dstep;
+                                    }
+                                }
                             }
                             Sv[g * 32 + lane] = S;
-                            if (lane == 0) {
-                                live[g] = lv & ~rmk;
-                                dg[g] += (unsigned long long)__popc(rmk) * dstep;
-                            }
                             return;
                         }
                         // Case 3: the exact compare at d = D
@@ -302,15 +329,15 @@ __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(
                                 }
                             }
                         }
-                        if (lane == 0) {
-                            live[g] = 0u;
-                            dg[g] += (unsigned long long)__popc(lv) * (unsigned)a.D;
-                        }
+                        am &= ~(1ull << g);
+                        drop(g, ~0u);
                     };
+                    // ---- dense step: the live slots, two at a time, every
+                    // member, from registers
                     for (int g = 0; g < ngq; g += 2) {
                         const bool two = g + 1 < ngq;
-                        const unsigned lv0 = live[g], lv1 = two ? live[g + 1] : 0u;
-                        if ((lv0 | lv1) == 0u) continue;
+                        const unsigned s2 = (unsigned)(sl >> g) & (two ? 3u : 1u);
+                        if (s2 == 0u) continue;
                         const float *qv0 = a.qrot + (int64_t)qg[g] * a.Dp;
                         const float *qv1 = two ? a.qrot + (int64_t)qg[g + 1] * a.Dp : qv0;
                         float2 p0[NL], p1[NL];
@@ -333,110 +360,117 @@ __global__ void __launch_bounds__(CM_THREADS, ADSX_CM_MINBLOCKS) cm_scan_kernel(
                         }
                         const float s0 = group_sum<NL>(p0, lane);
                         const float s1 = group_sum<NL>(p1, lane);
-                        if (lv0) finish(g, lv0, s0, qv0);
-                        if (lv1) finish(g + 1, lv1, s1, qv1);
+                        if (s2 & 1u) finish(g, s0, qv0);
+                        if (s2 & 2u) finish(g + 1, s1, qv1);
                     }
-                }
                 } else {
-                // ---- sparse step: the tile's step staged in shared memory,
-                // then the live (slot, member) pairs, one per lane, 32 per
-                // pass whatever their query
-                const T *x = cb + (int64_t)blk * stride + (int64_t)(m0 + gi) * BLK + jo;
+                    // ---- sparse step: the tile's step staged in shared
+                    // memory, then the live (slot, member) pairs, one per
+                    // lane, 32 per pass whatever their query
+                    if (lane < ngq) live[lane] = la;
+                    if (lane + 32 < ngq) live[lane + 32] = lb;
 #pragma unroll
-                for (int b = 0; b < DB; ++b)
+                    for (int b = 0; b < DB; ++b)
 #pragma unroll
-                    for (int k = 0; k < NL; ++k)
-                        if (b < nb && ((U >> owner_lane<NL>(gi, k)) & 1u))
-                            *reinterpret_cast<V *>(
-                                stile + b * RB + (gi + NG * k) * ROW +
-                                (((lane % NL) ^ Stage<T>::swz(gi + NG * k)) * 16)) =
-                                ld_piece(x + b * stride + k * NG * BLK);
-                int npr = 0;
-                for (int g = 0; g < ngq; ++g) {
-                    const unsigned lv = live[g];
-                    if ((lv >> lane) & 1u)
-                        pa[npr + __popc(lv & below)] = (unsigned short)((g << 5) | lane);
-                    npr += __popc(lv);
-                }
-                __syncwarp();
-                for (int p0 = 0; p0 < npr; p0 += 32) {
-                    const bool valid = p0 + lane < npr;
-                    const int pr = valid ? pa[p0 + lane] : 0;
-                    const int g = pr >> 5, l = pr & 31;
-                    const int mt = own_slot<NL>(l);             // member within the tile
-                    const int pos = (int)o + m0 + mt;
-                    const float *qv = a.qrot + (int64_t)qg[g] * a.Dp;
-                    float S = 0.f;
-                    if (valid)
-                        S = Sv[g * 32 + l] +
-                            member_step_sum<T, DB>(stile + mt * ROW, mt, qv + blk * BLK, nb);
-                    const float r2 = valid ? r2g[g] : 0.f;
-                    bool out = false;                           // continues to the next step
-                    if (!fin) {
-                        if (valid) {
-                            if (S > r2 * fe) {
-                                if constexpr (FIXED) {
-                                    const int64_t off = (int64_t)qg[g] * a.N + a.ids[pos];
-                                    a.decisions[off] = 0;
-                                    if (a.dec_dims) a.dec_dims[off] = (int)dstep;
-                                }
-                            } else {
-                                out = true;
-                                Sv[g * 32 + l] = S;
-                            }
-                        }
-                    } else {
-                        bool cand = valid;
-                        if constexpr (Roundoff<T>::u > 0.f) {
-                            bool need = false;
-                            if (valid) {
-                                need = !(r2 < INFINITY);
-                                if (!need && r2 >= 0.f) {
-                                    const float bound =
-                                        (sqrtf(r2) + Roundoff<T>::u * a.norms[pos]) * 1.0001f;
-                                    need = sqrtf(S) <= bound;
-                                }
-                            }
-                            S = recheck_rows(a.rows32, a.Dp, qv, need, pos, S, lane);
-                            cand = need;
-                        }
-                        const bool posv = cand && S <= r2;
-                        if constexpr (FIXED) {
-                            if (valid) {
-                                const int64_t off = (int64_t)qg[g] * a.N + a.ids[pos];
-                                a.decisions[off] = posv ? 1 : 2;
-                                if (a.dec_dims) a.dec_dims[off] = a.D;
-                            }
-                        } else if (posv) {
-                            const int q = qg[g];
-                            const unsigned idx = atomicAdd(a.app_n + q, 1u);
-                            if (idx < (unsigned)a.cap) {
-                                a.app_d[(int64_t)q * a.cap + idx] = S;
-                                a.app_i[(int64_t)q * a.cap + idx] = a.ids[pos];
-                            }
-                        }
-                    }
-                    // the pairs that stop here, per slot (a slot's pairs are
-                    // consecutive): dims summed and live bits cleared by the
-                    // slot's lowest lane
-                    const unsigned d = valid && !out ? (fin ? (unsigned)a.D : dstep) : 0u;
-                    const unsigned grp = __match_any_sync(FULL, valid ? g : -1);
-                    const unsigned dsum = __reduce_add_sync(grp, d);
-                    const unsigned dead = __reduce_or_sync(grp, valid && !out ? 1u << l : 0u);
-                    if (valid && lane == __ffs(grp) - 1) {
-                        if (dsum) dg[g] += dsum;
-                        if (dead) live[g] &= ~dead;
+                        for (int k = 0; k < NL; ++k)
+                            if (b < nb && ((U >> owner_lane<NL>(gi, k)) & 1u))
+                                *reinterpret_cast<V *>(
+                                    stile + b * RB + (gi + NG * k) * ROW +
+                                    (((lane % NL) ^ Stage<T>::swz(gi + NG * k)) * 16)) =
+                                    ld_piece(x + b * stride + k * NG * BLK);
+                    __syncwarp();
+                    int npr = 0;
+                    for (int g = 0; g < ngq; ++g) {
+                        const unsigned lv = live[g];
+                        if ((lv >> lane) & 1u)
+                            pa[npr + __popc(lv & below)] = (unsigned short)((g << 5) | lane);
+                        npr += __popc(lv);
                     }
                     __syncwarp();
-                }
+                    for (int p0 = 0; p0 < npr; p0 += 32) {
+                        const bool valid = p0 + lane < npr;
+                        const int pr = valid ? pa[p0 + lane] : 0;
+                        const int g = pr >> 5, l = pr & 31;
+                        const int mt = own_slot<NL>(l);             // member within the tile
+                        const int pos = (int)o + m0 + mt;
+                        const float *qv = a.qrot + (int64_t)qg[g] * a.Dp;
+                        float S = 0.f;
+                        if (valid)
+                            S = Sv[g * 32 + l] +
+                                member_step_sum<T, DB>(stile + mt * ROW, mt, qv + blk * BLK, nb);
+                        const float r2 = valid ? r2g[g] : 0.f;
+                        bool out = false;                           // continues to the next step
+                        if (!fin) {
+                            if (valid) {
+                                if (S > r2 * fe) {
+                                    if constexpr (FIXED) {
+                                        const int64_t off = (int64_t)qg[g] * a.N + a.ids[pos];
+                                        a.decisions[off] = 0;
+                                        if (a.dec_dims) a.dec_dims[off] = (int)dstep;
+                                    }
+                                } else {
+                                    out = true;
+                                    Sv[g * 32 + l] = S;
+                                }
+                            }
+                        } else {
+                            bool cand = valid;
+                            if constexpr (Roundoff<T>::u > 0.f) {
+                                bool need = false;
+                                if (valid) {
+                                    need = !(r2 < INFINITY);
+                                    if (!need && r2 >= 0.f) {
+                                        const float bound =
+                                            (sqrtf(r2) + Roundoff<T>::u * a.norms[pos]) * 1.0001f;
+                                        need = sqrtf(S) <= bound;
+                                    }
+                                }
+                                S = recheck_rows(a.rows32, a.Dp, qv, need, pos, S, lane);
+                                cand = need;
+                            }
+                            const bool posv = cand && S <= r2;
+                            if constexpr (FIXED) {
+                                if (valid) {
+                                    const int64_t off = (int64_t)qg[g] * a.N + a.ids[pos];
+                                    a.decisions[off] = posv ? 1 : 2;
+                                    if (a.dec_dims) a.dec_dims[off] = a.D;
+                                }
+                            } else if (posv) {
+                                const int q = qg[g];
+                                const unsigned idx = atomicAdd(a.app_n + q, 1u);
+                                if (idx < (unsigned)a.cap) {
+                                    a.app_d[(int64_t)q * a.cap + idx] = S;
+                                    a.app_i[(int64_t)q * a.cap + idx] = a.ids[pos];
+                                }
+                            }
+                        }
+                        // the pairs that stop here, per slot (a slot's pairs
+                        // are consecutive): live bits cleared by the slot's
+                        // lowest lane
+                        const unsigned grp = __match_any_sync(FULL, valid ? g : -1);
+                        const unsigned dead = __reduce_or_sync(grp, valid && !out ? 1u << l : 0u);
+                        if (valid && dead && lane == __ffs(grp) - 1) live[g] &= ~dead;
+                        __syncwarp();
+                    }
+                    // the registers again from the shared masks
+                    la = lane < ngq ? live[lane] : 0u;
+                    lb = lane + 32 < ngq ? live[lane + 32] : 0u;
+                    am = 0ull;
+                    for (int g = 0; g < ngq; ++g)
+                        am |= (unsigned long long)((live[g] >> lane) & 1u) << g;
                 }
                 __syncwarp();
                 blk = e;
             }
         }
-        if (a.out_dims)
-            for (int g = lane; g < ngq; g += 32)
-                atomicAdd(reinterpret_cast<unsigned long long *>(a.out_dims + qg[g]), dg[g]);
+        if (a.out_dims) {
+            if (lane < ngq)
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.out_dims + qg[lane]),
+                          (unsigned long long)dga);
+            if (lane + 32 < ngq)
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.out_dims + qg[lane + 32]),
+                          (unsigned long long)dgb);
+        }
         __syncwarp();
     }
 }

@@ -2,13 +2,16 @@
 times, on outputs sampled for the oracle.
 
 SIFT-shaped 1M x 128, 10k queries, nlist 4096, nprobe 64, K 100, eps0 2.1,
-delta_d 32 (one warp per query): for a sample of queries the oracle computes
+delta_d 32 (the schedule the library picks for this batch, cluster-major, in
+its default shape and in the shape the bench's autotuner picked, 16 queries
+and 2 tiles per item: the results are the same): for a sample of queries the oracle computes
 exact IVF and the DCO decisions of the true top-K at the exact K-th distance;
 FDScanning must return exact IVF, ADSampling every returned distance exact and
 the bracket invariant, and recall@10 over 500 sampled queries within 0.002
 (both ways) of the sequential oracle's IVF+; and, for 8 of the sampled queries, every
 per-candidate decision of the scan kernel's fixed-threshold mode over all 1M
-vectors is bit-exact to the oracle's outside the 1e-5 margin band.  GIST-shaped 1M x 960 in BF16 storage (1000 queries,
+vectors is bit-exact to the oracle's outside the 1e-5 margin band, through
+the query-major and the cluster-major kernels alike.  GIST-shaped 1M x 960 in BF16 storage (1000 queries,
 nprobe 16, K 10): the same checks with the 16-bit allowance (recall over 60
 queries); the oracle rotates only the sampled queries' candidates (other rows
 are never read)."""
@@ -72,6 +75,12 @@ def test_sift_shaped_1M_headline_configuration():
         K, nprobe, eps0, dd = 100, 64, 2.1, 32
         ids, d2 = (t.cpu().numpy() for t in ix.search(Qd, K, nprobe, eps0=eps0, delta_d=dd))
         fd_ids, fd_d2 = (t.cpu().numpy() for t in ix.search(Qd, K, nprobe, eps0=math.inf))
+        ix.set_scan_schedule(adsx.SCHED_CLUSTER, 16, 2)
+        try:
+            ids2, d22 = (t.cpu().numpy() for t in ix.search(Qd, K, nprobe, eps0=eps0, delta_d=dd))
+        finally:
+            ix.set_scan_schedule(adsx.SCHED_AUTO)
+        assert np.array_equal(ids, ids2) and np.array_equal(d2, d22)
         qs = np.random.default_rng(0).choice(wl.Q.shape[0], size=24, replace=False)
         threads = oracle.max_threads()
         Y = oracle.rotate(wl.P, wl.X, threads)
@@ -91,6 +100,14 @@ def test_sift_shaped_1M_headline_configuration():
         dec, dims = ix.dco_fixed_r(Qd[torch.as_tensor(qf, device="cuda")],
                                    torch.from_numpy(r2).cuda(), eps0, dd)
         dec, dims = dec.cpu().numpy(), dims.cpu().numpy()
+        ix.set_scan_schedule(adsx.SCHED_CLUSTER)
+        try:
+            dec_cm, dims_cm = ix.dco_fixed_r(Qd[torch.as_tensor(qf, device="cuda")],
+                                             torch.from_numpy(r2).cuda(), eps0, dd)
+        finally:
+            ix.set_scan_schedule(adsx.SCHED_AUTO)
+        assert np.array_equal(dec, dec_cm.cpu().numpy())
+        assert np.array_equal(dims, dims_cm.cpu().numpy())
         edec, edims, emar = oracle.dco_fixed_r(Y, Qr[:8], r2.astype(np.float64), eps0, dd,
                                                threads)
         boundary = emar < REL
