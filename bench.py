@@ -215,20 +215,6 @@ def scan_traffic(workload=None, nprobe=None, storage="f32"):
         return None
 
 
-def cm_round_count(nprobe, r0=1, growth=4):
-    """Rounds of the cluster-major schedule for nprobe probe ranks (round 0 over
-    ranks [0, r0), then ranges growing `growth` times; a short tail joins the
-    last) -- the library's own rule, for the launch count."""
-    n, lo = 1, r0
-    while lo < nprobe:
-        hi = max(lo + 1, lo * growth)
-        if hi >= nprobe or 2 * (nprobe - hi) < hi - lo:
-            hi = nprobe
-        n += 1
-        lo = hi
-    return n
-
-
 def cpu_baseline_oracle(wl, K, nprobe, eps0, dd, seconds):
     """The FP64 oracle's IVF+ (sequential Algorithm 1) on the host cores, on a
     bounded sample of the same queries; index-phase rotation untimed."""
@@ -866,10 +852,13 @@ def main():
     clk = clk.summary()
     sm_mhz = clk.get("sm_mhz") or 2070.0
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    cm = scan_cfg["schedule"] == adsx.SCHED_CLUSTER or (
-        scan_cfg["schedule"] == adsx.SCHED_AUTO and nq >= 2048 and np_ads >= 8
-        and nq * np_ads >= 8 * wl.nlist)
-    launches_per_search = (5 + 1 + 5 * cm_round_count(np_ads) + 2) if cm else 6
+    # the scan kernel launches of one search: one query-major launch, or one
+    # per cluster-major round
+    cm = ads_kern_n > 1
+    # rotation, centroid norms, GEMM, select, test factors; cluster-major adds
+    # the first merge, per round three planning kernels, the scan and a merge,
+    # and the overflow check with its (usually empty) query-major launch
+    launches_per_search = (5 + 1 + 5 * ads_kern_n + 2) if cm else 6
     fd_frac = ads_dims / fd_dims if fd_dims else None
     line = {
         "metric": METRIC, "value": job_throughput(nq, ws, ads_ms), "unit": UNIT, "n_gpus": ws,

@@ -63,7 +63,8 @@ typedef enum { ADSX_L2 = 0, ADSX_IP = 1, ADSX_COSINE = 2 } adsx_metric;
 
 /* Scan schedules (adsx_set_scan_schedule). */
 typedef enum {
-    ADSX_SCHED_AUTO = 0,     /* cluster-major for large batches, else query-major */
+    ADSX_SCHED_AUTO = 0,     /* cluster-major for batches probing each cluster    */
+                             /* about once or more, else query-major              */
     ADSX_SCHED_QUERY = 1,    /* one warp per (query, split): every query apart    */
     ADSX_SCHED_CLUSTER = 2   /* one warp per (cluster, query group), in rounds    */
 } adsx_schedule;
@@ -311,13 +312,17 @@ int adsx_stream_status(const adsx_index *index, void *stream);
  *                       tiles_per_item tiles.  Needs delta_d <= 64 (or the
  *                       test off) and an L2 or cosine index; other searches
  *                       run query-major.
- *   ADSX_SCHED_AUTO     cluster-major when it applies to a large batch
- *                       (nq >= 2048, nprobe >= 8, nq * nprobe >= 8 nlist: each
- *                       cluster probed 8 times on average), else query-major.
+ *   ADSX_SCHED_AUTO     cluster-major when it applies and the batch probes
+ *                       each cluster about once or more on average (nq >=
+ *                       128, nq * nprobe >= nlist; with 16-bit storage and
+ *                       D >= 512, nq * nprobe >= 8 nlist), else query-major.
  *                       The initial setting.
- *   queries_per_item    1..64, or 0 to keep the current value (16 initially).
+ *   queries_per_item    1..64; 0 keeps the current setting; -1 returns to
+ *                       the initial one, chosen per batch from q = nq *
+ *                       nprobe / nlist: 16 from q = 24, 8 from q = 6, else 4
+ *                       (at D >= 512 at most 8, and 4 with 16-bit storage).
  *   tiles_per_item      1..64 32-member tiles, or 0 to keep the current value
- *                       (4 initially).
+ *                       (2 initially).
  * Not thread-safe with other calls on the same index.
  */
 int adsx_set_scan_schedule(adsx_index *index, int32_t schedule, int32_t queries_per_item,
@@ -325,9 +330,9 @@ int adsx_set_scan_schedule(adsx_index *index, int32_t schedule, int32_t queries_
 
 /*
  * adsx_scan_config -- the index's current scan settings: the step delta_d
- * used when a search passes 0, the schedule, queries and tiles per
- * cluster-major item, and the query-major work items per SM (any output
- * pointer may be NULL).
+ * used when a search passes 0, the schedule, queries (0: chosen per batch)
+ * and tiles per cluster-major item, and the query-major work items per SM
+ * (any output pointer may be NULL).
  */
 int adsx_scan_config(const adsx_index *index, int32_t *delta_d, int32_t *schedule,
                      int32_t *queries_per_item, int32_t *tiles_per_item,
@@ -339,8 +344,8 @@ int adsx_scan_config(const adsx_index *index, int32_t *delta_d, int32_t *schedul
  * the step delta_d (Sec. 6.2.4: 16..64 give the best trade-off; the
  * candidates are 16, 32, 48, 64, up to the padded D) under each scan
  * schedule (query-major, cluster-major), then the winner's shape: queries
- * per item (8, 16, 32) and tiles per item (2, 4, 8) for cluster-major, work
- * items per SM (24, 48, 96) for query-major.  The winner is stored in the
+ * per item (chosen per batch, 4, 8, 16, 32) and tiles per item (1, 2, 4) for
+ * cluster-major, work items per SM (24, 48, 96) for query-major.  The winner is stored in the
  * index: the schedule and shape apply to every later search, the step to
  * searches that pass delta_d = 0 (adsx_scan_config reads them back).  Tune
  * on a sample the size of the batches to be searched: the schedule that

@@ -487,15 +487,16 @@ def set_scan_schedule(index: Index, schedule: int, queries_per_item: int = 0,
                       tiles_per_item: int = 0):
     """adsx_set_scan_schedule: SCHED_AUTO, SCHED_QUERY (one warp per query)
     or SCHED_CLUSTER (one warp per cluster chunk and query group, in rounds);
-    queries_per_item 1..64 and tiles_per_item 1..64 (0 keeps the current
-    value)."""
+    queries_per_item 1..64 (0 keeps the current value, -1 chooses it per
+    batch) and tiles_per_item 1..64 (0 keeps the current value)."""
     _check(load().adsx_set_scan_schedule(index.handle, int(schedule), int(queries_per_item),
                                          int(tiles_per_item)))
 
 
 def scan_config(index: Index):
     """adsx_scan_config: dict of the index's delta_d (for delta_d = 0),
-    schedule, queries_per_item, tiles_per_item and items_per_sm."""
+    schedule, queries_per_item (0: chosen per batch), tiles_per_item and
+    items_per_sm."""
     v = [ctypes.c_int32() for _ in range(5)]
     _check(load().adsx_scan_config(index.handle, *[ctypes.byref(x) for x in v]))
     return dict(zip(("delta_d", "schedule", "queries_per_item", "tiles_per_item",

@@ -57,11 +57,12 @@ struct Index {
     int32_t tuned_delta_d = 32;   // used when a search passes delta_d = 0
     int32_t items_per_sm = 48;    // work items per SM targeted when splitting queries
     // scan schedule (adsx_set_scan_schedule / adsx_autotune): ADSX_SCHED_AUTO,
-    // _QUERY or _CLUSTER; queries per cluster-major work item; probe ranks of
-    // the query-major round 0 and the growth factor of later rounds' ranges
+    // _QUERY or _CLUSTER; queries per cluster-major work item (0: chosen per
+    // batch); probe ranks of round 0 and the growth factor of later rounds'
+    // ranges
     int32_t sched = ADSX_SCHED_AUTO;
-    int32_t cm_G = 16;
-    int32_t cm_tpi = 4;           // 32-member tiles per cluster-major work item
+    int32_t cm_G = 0;
+    int32_t cm_tpi = 2;           // 32-member tiles per cluster-major work item
     int32_t max_tiles = 0;        // tiles of the largest cluster
     int32_t cm_r0 = 1;
     int32_t cm_growth = 4;

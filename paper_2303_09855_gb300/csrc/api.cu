@@ -603,8 +603,29 @@ static bool use_cluster_major(const Index *ix, const adsx::ScanArgs &a)
     if (a.metric == ADSX_IP || a.db > adsx::CM_MAX_DB) return false;
     if (a.nprobe <= ix->cm_r0) return false;           // round 0 alone would cover every probe
     if (ix->sched == ADSX_SCHED_CLUSTER) return true;
-    // a large batch whose queries probe each cluster 8 times on average
-    return a.nq >= 2048 && a.nprobe >= 8 && a.nq * (int64_t)a.nprobe >= 8 * (int64_t)ix->nlist;
+    // Measured on GB300 (SIFT-shaped 1M x 128, GIST-shaped 250k and 1M x 960,
+    // 125..10k queries): cluster-major is faster once a batch probes each
+    // cluster about once on average (from 1.1x at 250 SIFT-shaped queries to
+    // 1.6x for 1000 GIST-shaped ones in FP32), except with 16-bit storage at
+    // high D, where query-major stays ahead below about 8 queries per cluster.
+    const int64_t probes = a.nq * (int64_t)a.nprobe, nl = ix->nlist;
+    if (a.nq < 128 || probes < nl) return false;
+    if (a.storage != ADSX_F32 && ix->D >= 512 && probes < 8 * nl) return false;
+    return true;
+}
+
+// Queries per cluster-major work item: the index's setting, or chosen by
+// the batch from the mean number of queries probing a cluster, q = nq *
+// nprobe / nlist: 16 from q = 24, 8 from q = 6, else 4 (at D >= 512 at most 8,
+// and 4 with 16-bit storage: there most candidates stop at the first steps
+// and a slot's per-step bookkeeping outweighs the shared tile loads).
+static int cm_queries_per_item(const Index *ix, int64_t nq, int nprobe)
+{
+    if (ix->cm_G > 0) return ix->cm_G;
+    const double q = (double)nq * nprobe / ix->nlist;
+    int G = q >= 24.0 ? 16 : (q >= 6.0 ? 8 : 4);
+    if (ix->D >= 512) G = std::min(G, ix->storage == ADSX_F32 ? 8 : 4);
+    return G;
 }
 
 // The probe-rank ranges of the cluster-major rounds after round 0: each
@@ -680,7 +701,7 @@ static cudaError_t cm_scan(const Index *ix, const adsx::ScanArgs &a, Scratch &sc
     cudaStream_t s = sc.s;
     cudaError_t e;
     const int64_t nq = a.nq;
-    const int K = a.K, nprobe = a.nprobe, G = ix->cm_G;
+    const int K = a.K, nprobe = a.nprobe, G = cm_queries_per_item(ix, nq, a.nprobe);
     const int r0 = std::min(ix->cm_r0, nprobe);
     // capacity of a round's list per query: candidates reaching d = D within
     // the previous rounds' r -- in round 0 (no r yet) every member of the
@@ -1057,11 +1078,12 @@ int adsx_dco_fixed_r(const adsx_index *index, const float *Qv, int64_t nq, const
         CK(adsx::launch_cm_all_clusters(probes, nq, ix->nlist, s), "probe lists");
         adsx::CmPlan pl;
         int64_t items_cap = 0;
-        CK(cm_plan_buffers(ix, nq, ix->nlist, ix->cm_G, sc, pl, &items_cap), "alloc plan");
-        CK(adsx::launch_cm_plan(probes, nq, ix->nlist, 0, ix->nlist, ix->nlist, ix->cm_G,
+        const int G = cm_queries_per_item(ix, nq, ix->nlist);
+        CK(cm_plan_buffers(ix, nq, ix->nlist, G, sc, pl, &items_cap), "alloc plan");
+        CK(adsx::launch_cm_plan(probes, nq, ix->nlist, 0, ix->nlist, ix->nlist, G,
                                 ix->cm_tpi, ix->off, pl, s),
            "plan");
-        adsx::CmArgs c = cm_args_from(a, ix->cm_G);
+        adsx::CmArgs c = cm_args_from(a, G);
         c.tpi = ix->cm_tpi;
         c.coff = pl.coff;
         c.qlist = pl.qlist;
@@ -1168,12 +1190,13 @@ int adsx_autotune(adsx_index *index, const float *Qv, int64_t nq, int32_t K, int
     for (int di = 0; di < ndd && rc == ADSX_OK; ++di) {
         if (ndd > 1 && dds[di] > ix->Dp) continue;
         rc = consider({dds[di], ADSX_SCHED_QUERY, saved.G, saved.tpi, 48});
-        if (rc == ADSX_OK) rc = consider({dds[di], ADSX_SCHED_CLUSTER, 16, 4, 48});
+        if (rc == ADSX_OK) rc = consider({dds[di], ADSX_SCHED_CLUSTER, 0, 2, 48});
     }
     const TuneCfg base = best;
     if (rc == ADSX_OK && base.sched == ADSX_SCHED_CLUSTER) {
-        const int Gs[3] = {8, 16, 32}, tpis[3] = {2, 4, 8};
-        for (int gi = 0; gi < 3 && rc == ADSX_OK; ++gi)
+        // queries per item (0: chosen per batch), then tiles per item
+        const int Gs[4] = {4, 8, 16, 32}, tpis[3] = {1, 2, 4};
+        for (int gi = 0; gi < 4 && rc == ADSX_OK; ++gi)
             if (Gs[gi] != base.G) rc = consider({base.dd, base.sched, Gs[gi], base.tpi, base.ip});
         const TuneCfg b2 = best;
         for (int ti = 0; ti < 3 && rc == ADSX_OK; ++ti)
@@ -1219,12 +1242,12 @@ int adsx_set_scan_schedule(adsx_index *index, int32_t schedule, int32_t queries_
     if (schedule != ADSX_SCHED_AUTO && schedule != ADSX_SCHED_QUERY &&
         schedule != ADSX_SCHED_CLUSTER)
         return fail(ADSX_EINVAL, "unknown scan schedule %d", schedule);
-    if (queries_per_item < 0 || queries_per_item > adsx::CM_MAX_G)
-        return fail(ADSX_EINVAL, "queries_per_item out of range (0..%d)", adsx::CM_MAX_G);
+    if (queries_per_item < -1 || queries_per_item > adsx::CM_MAX_G)
+        return fail(ADSX_EINVAL, "queries_per_item out of range (-1..%d)", adsx::CM_MAX_G);
     if (tiles_per_item < 0 || tiles_per_item > 64)
         return fail(ADSX_EINVAL, "tiles_per_item out of range (0..64)");
     ix->sched = schedule;
-    if (queries_per_item) ix->cm_G = queries_per_item;
+    if (queries_per_item) ix->cm_G = queries_per_item < 0 ? 0 : queries_per_item;
     if (tiles_per_item) ix->cm_tpi = tiles_per_item;
     return ADSX_OK;
 }

@@ -591,7 +591,10 @@ __global__ void cm_plan_scatter_kernel(const int32_t *__restrict__ probes, int64
 // orders non-negative keys as (distance, id) -- are sorted by a warp bitonic
 // network in shared memory; every entry of either list then lands at its
 // index plus its rank in the other list (the two lists hold distinct ids),
-// and the first K are kept.  A list beyond its capacity flags the query.
+// and the first K are kept.  A long list is first cut, in global memory, to
+// the keys whose distance is at most the K-th smallest of both lists; the
+// shared memory holds T >= 2K of them.  A list beyond its capacity, or one
+// whose cut still exceeds T (ties at the K-th distance), flags the query.
 // With `final_pass` the keys are written as the values the search returns.
 constexpr int MERGE_WARPS = 4;
 
@@ -617,9 +620,9 @@ __device__ __forceinline__ int rank_below(const unsigned long long *a, int n, un
 // The distance bits (the high word of a key) of the K-th smallest key among
 // e[0..ne) and a[0..na): a radix select, 8 bits per pass, with a 256-bin
 // histogram in shared memory (lane l owns bins 8l .. 8l+7 for the scan).
-__device__ __forceinline__ unsigned select_hi(const unsigned long long *e, int ne,
-                                              const unsigned long long *a, int na, int K,
-                                              unsigned *hist, int lane)
+template <typename AK>
+__device__ __forceinline__ unsigned select_hi(const unsigned long long *e, int ne, AK akey,
+                                              int na, int K, unsigned *hist, int lane)
 {
     unsigned prefix = 0u, pmask = 0u;
     unsigned kk = (unsigned)K;
@@ -627,7 +630,7 @@ __device__ __forceinline__ unsigned select_hi(const unsigned long long *e, int n
         for (int b = lane; b < 256; b += 32) hist[b] = 0u;
         __syncwarp();
         for (int i = lane; i < ne + na; i += 32) {
-            const unsigned hi = (unsigned)((i < ne ? e[i] : a[i - ne]) >> 32);
+            const unsigned hi = (unsigned)((i < ne ? e[i] : akey(i - ne)) >> 32);
             if ((hi & pmask) == prefix) atomicAdd(hist + ((hi >> shift) & 255u), 1u);
         }
         __syncwarp();
@@ -700,27 +703,39 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) cm_merge_kernel(CmMergeArgs 
             if (k < K) ek[k] = has ? mkey(dk[k], (int)ids[k]) : NONE;
             ne += __popc(__ballot_sync(FULL, has));
         }
-        for (int i = lane; i < (int)na; i += 32)
-            ak[i] = mkey(m.app_d[q * m.cap + i], m.app_i[q * m.cap + i]);
-        __syncwarp();
+        const float *gd = m.app_d + q * m.cap;
+        const int32_t *gi = m.app_i + q * m.cap;
+        auto akey = [&](int i) { return mkey(gd[i], gi[i]); };
         if (na > 64u && ne + (int)na > K) {
             // many appended: keep only the keys whose distance is at most the
             // K-th smallest of both lists (ties kept), then sort those
-            const unsigned th = select_hi(ek, ne, ak, (int)na, K, hist, lane);
+            const unsigned th = select_hi(ek, ne, akey, (int)na, K, hist, lane);
             int kept = 0;
             for (int c0 = 0; c0 < (int)na; c0 += 32) {
                 const int i = c0 + lane;
-                const unsigned long long v = i < (int)na ? ak[i] : NONE;
+                const unsigned long long v = i < (int)na ? akey(i) : NONE;
                 const bool keep = i < (int)na && (unsigned)(v >> 32) <= th;
                 const unsigned km = __ballot_sync(FULL, keep);
-                __syncwarp();                         // the chunk is read before it is written
-                if (keep) ak[kept + __popc(km & below_mask(lane))] = v;
+                const int at = kept + __popc(km & below_mask(lane));
+                if (keep && at < m.T) ak[at] = v;
                 kept += __popc(km);
+            }
+            if (kept > m.T) {
+                // ties at the K-th distance beyond the sort capacity: the
+                // query is searched again (query-major); its list is dropped
+                if (lane == 0) {
+                    m.ovf[q] = 1;
+                    if (m.app_n) m.app_n[q] = 0u;
+                }
                 __syncwarp();
+                continue;
             }
             na = (unsigned)kept;
             ne = rank_below(ek, ne, (unsigned long long)(th + 1u) << 32);
+        } else {
+            for (int i = lane; i < (int)na; i += 32) ak[i] = akey(i);
         }
+        __syncwarp();
         int T = 32;
         while (T < (int)na) T <<= 1;
         for (int i = (int)na + lane; i < T; i += 32) ak[i] = NONE;
@@ -878,8 +893,10 @@ cudaError_t launch_cm_merge(const CmMergeArgs &m, cudaStream_t s)
 {
     if (m.nq <= 0) return cudaSuccess;
     CmMergeArgs b = m;
-    int T = 32;
-    while (T < m.cap) T <<= 1;
+    // the sort capacity: every list of at most 64 or whose merge cannot
+    // exceed K (na <= K) fits, and the cut of a longer one (K plus ties)
+    int T = 128;
+    while (T < 2 * m.K) T <<= 1;
     b.T = T;
     // per warp: appended keys, existing keys, a 256-bin histogram
     const size_t smem = (size_t)(T + m.K + 128) * 8 * MERGE_WARPS;

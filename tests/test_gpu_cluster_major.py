@@ -214,7 +214,7 @@ def test_autotune_picks_schedule_and_shape(cm):
         assert cfg["delta_d"] == dd and dd in (16, 32, 48, 64) and ms > 0
         assert cfg["schedule"] in (adsx.SCHED_QUERY, adsx.SCHED_CLUSTER)
         if cfg["schedule"] == adsx.SCHED_CLUSTER:
-            assert cfg["queries_per_item"] in (8, 16, 32) and cfg["tiles_per_item"] in (2, 4, 8)
+            assert cfg["queries_per_item"] in (0, 4, 8, 16, 32) and cfg["tiles_per_item"] in (1, 2, 4)
         else:
             assert cfg["items_per_sm"] in (24, 48, 96)
         ids, d2 = ix.search(wl.Q, 10, 10, eps0=math.inf, delta_d=0)
