@@ -618,20 +618,42 @@ __device__ __forceinline__ int rank_below(const unsigned long long *a, int n, un
 }
 
 // The distance bits (the high word of a key) of the K-th smallest key among
-// e[0..ne) and a[0..na): a radix select, 8 bits per pass, with a 256-bin
-// histogram in shared memory (lane l owns bins 8l .. 8l+7 for the scan).
+// e[0..ne) and the appended keys 0..na (akey(i)): a radix select over the
+// bits below the prefix all of them share, 8 bits per pass, with a 256-bin
+// histogram in shared memory (lane l owns bins 8l .. 8l+7 for the scan);
+// lanes voting for the same bin merge into one atomic.
 template <typename AK>
 __device__ __forceinline__ unsigned select_hi(const unsigned long long *e, int ne, AK akey,
                                               int na, int K, unsigned *hist, int lane)
 {
-    unsigned prefix = 0u, pmask = 0u;
+    unsigned lo = 0xffffffffu, hi = 0u;
+    for (int i = lane; i < ne + na; i += 32) {
+        const unsigned h = (unsigned)((i < ne ? e[i] : akey(i - ne)) >> 32);
+        lo = min(lo, h);
+        hi = max(hi, h);
+    }
+    lo = __reduce_min_sync(FULL, lo);
+    hi = __reduce_max_sync(FULL, hi);
+    if (lo == hi) return lo;
+    const int hb = 31 - __clz(lo ^ hi);                  // highest differing bit
+    unsigned pmask = hb == 31 ? 0u : ~((2u << hb) - 1u);  // bits already fixed
+    unsigned prefix = lo & pmask;
     unsigned kk = (unsigned)K;
-    for (int shift = 24; shift >= 0; shift -= 8) {
-        for (int b = lane; b < 256; b += 32) hist[b] = 0u;
+    for (int top = hb; top >= 0; top -= 8) {
+        const int shift = top >= 7 ? top - 7 : 0;
+        const unsigned dmask = (2u << (top - shift)) - 1u;   // <= 8 bits
+#pragma unroll
+        for (int j = 0; j < 8; ++j) hist[lane * 8 + j] = 0u;
         __syncwarp();
-        for (int i = lane; i < ne + na; i += 32) {
-            const unsigned hi = (unsigned)((i < ne ? e[i] : akey(i - ne)) >> 32);
-            if ((hi & pmask) == prefix) atomicAdd(hist + ((hi >> shift) & 255u), 1u);
+        for (int i0 = 0; i0 < ne + na; i0 += 32) {
+            const int i = i0 + lane;
+            unsigned bin = 256u;                              // no vote
+            if (i < ne + na) {
+                const unsigned h = (unsigned)((i < ne ? e[i] : akey(i - ne)) >> 32);
+                if ((h & pmask) == prefix) bin = (h >> shift) & dmask;
+            }
+            const unsigned peers = __match_any_sync(FULL, bin);
+            if (bin < 256u && lane == __ffs(peers) - 1) atomicAdd(hist + bin, (unsigned)__popc(peers));
         }
         __syncwarp();
         unsigned c[8], sum = 0u;
@@ -666,9 +688,10 @@ __device__ __forceinline__ unsigned select_hi(const unsigned long long *e, int n
         bin = __shfl_sync(FULL, bin, src);
         before = __shfl_sync(FULL, before, src);
         prefix |= bin << shift;
-        pmask |= 255u << shift;
+        pmask |= dmask << shift;
         kk -= before;
         __syncwarp();
+        if (shift == 0) break;
     }
     return prefix;
 }

@@ -6,7 +6,9 @@
 // nprobe <= 64 a bound-and-gather path is taken (see the kernel); otherwise,
 // or when ties overflow it, a radix select runs: the row's
 // distances become order-preserving 32-bit keys (bit patterns of non-negative
-// floats) in the warp's shared memory; the row's smallest and largest key
+// floats), re-read from the row (an L2 hit: the warp has just read it) on
+// every pass, so a warp needs shared memory only for its winners and a
+// histogram; the row's smallest and largest key
 // give the high bits every key shares, and radix passes of up to 8 bits over
 // the remaining bits (warp-aggregated shared-memory histograms) find the
 // exact key T of the nprobe-th smallest distance and how many keys equal to T
@@ -19,7 +21,7 @@
 namespace adsx {
 namespace {
 
-constexpr int MAXW = 4;                 // warps per block (fewer for large rows)
+constexpr int MAXW = 8;                 // warps per block (fewer for large nprobe)
 constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ unsigned dist_key(float v)
@@ -62,17 +64,16 @@ __device__ __forceinline__ void warp_sort(K *v, int n, int lane)
     }
 }
 
-// One warp's shared-memory region: winners (P2 x 8 bytes), histogram
-// (256 x 4), keys (nlist x 4); each part starts on a 16-byte boundary (the
-// keys are written with 16-byte stores).
+// One warp's shared-memory region: winners (P2 x 8 bytes, at least the
+// 128 of the bound-and-gather path) and a 256-bin histogram.
 constexpr int FAST_CAP = 128;   // candidate capacity of the bound-and-gather path (nprobe <= 64)
 __host__ __device__ inline size_t sel_bytes(int P2)
 {
     return ((size_t)(P2 > FAST_CAP ? P2 : FAST_CAP) * 8 + 15) & ~(size_t)15;
 }
-__host__ __device__ inline size_t warp_region(int nlist, int P2)
+__host__ __device__ inline size_t warp_region(int P2)
 {
-    return sel_bytes(P2) + 1024 + (size_t)((nlist + 3) & ~3) * 4;
+    return sel_bytes(P2) + 1024;
 }
 
 __global__ void __launch_bounds__(MAXW * 32) select_nprobe_kernel(
@@ -81,10 +82,9 @@ __global__ void __launch_bounds__(MAXW * 32) select_nprobe_kernel(
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned char *base = smraw + warp_region(nlist, P2) * warp;
+    unsigned char *base = smraw + warp_region(P2) * warp;
     unsigned long long *sel = reinterpret_cast<unsigned long long *>(base);
     unsigned *hist = reinterpret_cast<unsigned *>(base + sel_bytes(P2));
-    unsigned *key = hist + 256;
     const unsigned below = (1u << lane) - 1u;
 
     for (int64_t q = (int64_t)blockIdx.x * W + warp; q < nq; q += (int64_t)gridDim.x * W) {
@@ -116,7 +116,6 @@ __global__ void __launch_bounds__(MAXW * 32) select_nprobe_kernel(
                     if (i < n4) {
                         const uint4 k4 = make_uint4(dist_key(v[u].x), dist_key(v[u].y),
                                                     dist_key(v[u].z), dist_key(v[u].w));
-                        reinterpret_cast<uint4 *>(key)[i] = k4;
                         kmin = min(min(kmin, min(k4.x, k4.y)), min(k4.z, k4.w));
                         kmax = max(max(kmax, max(k4.x, k4.y)), max(k4.z, k4.w));
                         if (fast) {
@@ -139,7 +138,6 @@ __global__ void __launch_bounds__(MAXW * 32) select_nprobe_kernel(
                     const int i = i0 + 32 * u;
                     if (i < nlist) {
                         const unsigned k = dist_key(v[u]);
-                        key[i] = k;
                         kmin = k < kmin ? k : kmin;
                         kmax = k > kmax ? k : kmax;
                         if (fast) keep4(k, t0, t1, t2, t3);
@@ -158,16 +156,27 @@ __global__ void __launch_bounds__(MAXW * 32) select_nprobe_kernel(
             __syncwarp();
             warp_sort(hist, 128, lane);
             const unsigned Tb = hist[nprobe - 1];
+            // gather every key <= Tb (any order: sorted below), the row read
+            // again 8 x 32 keys at a time
             unsigned c = 0;
-            for (int i0 = 0; i0 < nlist && c <= (unsigned)FAST_CAP; i0 += 32) {
-                const int i = i0 + lane;
-                const unsigned u = i < nlist ? key[i] : 0xffffffffu;
-                const bool take = i < nlist && u <= Tb;
-                const unsigned bt = __ballot_sync(FULL, take);
-                const unsigned at = c + __popc(bt & below);
-                if (take && at < (unsigned)FAST_CAP)
-                    sel[at] = ((unsigned long long)u << 32) | (unsigned)i;
-                c += __popc(bt);
+            for (int i0 = 0; i0 < nlist && c <= (unsigned)FAST_CAP; i0 += 32 * 8) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = i0 + 32 * u + lane;
+                    v[u] = i < nlist ? __ldg(row + i) : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = i0 + 32 * u + lane;
+                    const unsigned k = dist_key(v[u]);
+                    const bool take = i < nlist && k <= Tb;
+                    const unsigned bt = __ballot_sync(FULL, take);
+                    const unsigned at = c + __popc(bt & below);
+                    if (take && at < (unsigned)FAST_CAP)
+                        sel[at] = ((unsigned long long)k << 32) | (unsigned)i;
+                    c += __popc(bt);
+                }
             }
             if (c <= (unsigned)FAST_CAP) {
                 int n2 = 32;
@@ -203,7 +212,7 @@ __global__ void __launch_bounds__(MAXW * 32) select_nprobe_kernel(
                     const int i = i0 + lane;
                     unsigned bin = 256u;                        // no vote
                     if (i < nlist) {
-                        const unsigned u = key[i];
+                        const unsigned u = dist_key(__ldg(row + i));
                         if ((u & mask) == prefix) bin = (u >> shift) & dmask;
                     }
                     // lanes with the same digit merge into one atomic
@@ -261,7 +270,7 @@ __global__ void __launch_bounds__(MAXW * 32) select_nprobe_kernel(
         unsigned nsel = 0, eq_seen = 0;
         for (int i0 = 0; i0 < nlist; i0 += 32) {
             const int i = i0 + lane;
-            const unsigned u = i < nlist ? key[i] : 0xffffffffu;
+            const unsigned u = i < nlist ? dist_key(__ldg(row + i)) : 0xffffffffu;
             const bool lt = i < nlist && (cut >= 0 ? (u >> cut) <= (T >> cut) : u < T);
             const bool eq = i < nlist && cut < 0 && u == T;
             const unsigned be = __ballot_sync(FULL, eq);
@@ -292,15 +301,15 @@ cudaError_t launch_select_nprobe(const float *dist, int64_t nq, int nlist, int n
     if (nq <= 0) return cudaSuccess;
     int P2 = 1;
     while (P2 < nprobe) P2 <<= 1;
-    const size_t per = warp_region(nlist, P2);
-    int W = (int)((200u << 10) / per);
+    const size_t per = warp_region(P2);
+    int W = (int)((48u << 10) / per);
     W = W > MAXW ? MAXW : (W < 1 ? 1 : W);
     const size_t smem = per * W;
     cudaError_t e = cudaFuncSetAttribute(select_nprobe_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int64_t grid = (nq + W - 1) / W;
-    if (grid > 152 * 16) grid = 152 * 16;
+    if (grid > 152 * 8) grid = 152 * 8;
     select_nprobe_kernel<<<(unsigned)grid, W * 32, smem, s>>>(dist, nq, nlist, nprobe, P2, W, probes,
                                                               probe_d2, nprobe_q);
     return cudaGetLastError();
