@@ -546,13 +546,24 @@ struct CmMergeArgs {
     int32_t metric;
     int32_t final_pass;
 };
+// The rounds of a cluster-major search: probe ranks [lo[r], lo[r + 1]) form
+// round r; its work items start at ibase[r] of the plan's item array.
+constexpr int CM_MAX_ROUNDS = 8;
+struct CmRounds {
+    int32_t n;
+    int32_t lo[CM_MAX_ROUNDS + 1];
+    int64_t ibase[CM_MAX_ROUNDS];
+};
+// Plans of all rounds: cnt, ioff and cur are n x nlist, coff n x (nlist + 1),
+// n_items n; round r's query lists start at qlist + nq * (lo[r] - lo[0]).
 struct CmPlan {
     int32_t *cnt, *coff, *ioff, *cur, *qlist, *n_items;
     int2 *items;
 };
 size_t cm_smem_bytes(int G, int db, int storage);
-cudaError_t launch_cm_plan(const int32_t *probes, int64_t nq, int pstride, int r0, int r1, int nlist,
-                           int G, int tpi, const int64_t *off, CmPlan &pl, cudaStream_t s);
+cudaError_t launch_cm_plan(const int32_t *probes, int64_t nq, int pstride, const CmRounds &R,
+                           int nlist, int G, int tpi, const int64_t *off, CmPlan &pl,
+                           cudaStream_t s);
 cudaError_t launch_cm_scan(const CmArgs &a, int device, cudaStream_t s);
 cudaError_t launch_cm_merge(const CmMergeArgs &m, cudaStream_t s);
 cudaError_t launch_cm_overflow_items(const int32_t *ovf, int64_t nq, int2 *items, int32_t *n_items,

@@ -671,23 +671,43 @@ static adsx::CmArgs cm_args_from(const adsx::ScanArgs &a, int G)
     return c;
 }
 
-static cudaError_t cm_plan_buffers(const Index *ix, int64_t nq, int width, int G, Scratch &sc,
-                                   adsx::CmPlan &pl, int64_t *items_cap)
+// Plan buffers of the rounds R (probe ranks already set in R.lo): per round
+// its item capacity -- ceil(cnt_c / G) query groups times the chunks of
+// cluster c, at most (cnt_c / G + 1) * chunks_c summed over the clusters --
+// and the offset of its items (R.ibase).
+static cudaError_t cm_plan_buffers(const Index *ix, int64_t nq, int G, adsx::CmRounds &R,
+                                   Scratch &sc, adsx::CmPlan &pl, int64_t *icap)
 {
     cudaError_t e;
-    const size_t nl = (size_t)ix->nlist;
-    // items: ceil(cnt_c / G) query groups times the chunks of cluster c, at
-    // most (cnt_c / G + 1) * chunks_c summed over the clusters
+    const size_t nl = (size_t)ix->nlist, nr = (size_t)R.n;
     const int64_t tpi = ix->cm_tpi;
     const int64_t maxch = (ix->max_tiles + tpi - 1) / tpi;
-    *items_cap = nq * (int64_t)width * maxch / G + ix->total_tiles / tpi + ix->nlist + 1;
-    if ((e = sc.get(&pl.cnt, nl)) != cudaSuccess) return e;
-    if ((e = sc.get(&pl.coff, nl + 1)) != cudaSuccess) return e;
-    if ((e = sc.get(&pl.ioff, nl)) != cudaSuccess) return e;
-    if ((e = sc.get(&pl.cur, nl)) != cudaSuccess) return e;
-    if ((e = sc.get(&pl.n_items, 1)) != cudaSuccess) return e;
-    if ((e = sc.get(&pl.qlist, (size_t)(nq * (int64_t)width))) != cudaSuccess) return e;
-    return sc.get(&pl.items, (size_t)*items_cap);
+    int64_t total = 0;
+    for (int r = 0; r < R.n; ++r) {
+        const int64_t w = R.lo[r + 1] - R.lo[r];
+        icap[r] = nq * w * maxch / G + ix->total_tiles / tpi + ix->nlist + 1;
+        R.ibase[r] = total;
+        total += icap[r];
+    }
+    if ((e = sc.get(&pl.cnt, nr * nl)) != cudaSuccess) return e;
+    if ((e = sc.get(&pl.coff, nr * (nl + 1))) != cudaSuccess) return e;
+    if ((e = sc.get(&pl.ioff, nr * nl)) != cudaSuccess) return e;
+    if ((e = sc.get(&pl.cur, nr * nl)) != cudaSuccess) return e;
+    if ((e = sc.get(&pl.n_items, nr)) != cudaSuccess) return e;
+    if ((e = sc.get(&pl.qlist, (size_t)(nq * (int64_t)(R.lo[R.n] - R.lo[0])))) != cudaSuccess)
+        return e;
+    return sc.get(&pl.items, (size_t)total);
+}
+
+// The scan fields of round r of the plan.
+static void cm_round_args(adsx::CmArgs &c, const adsx::CmPlan &pl, const adsx::CmRounds &R,
+                          const int64_t *icap, int64_t nq, int nlist, int r)
+{
+    c.coff = pl.coff + (size_t)r * (nlist + 1);
+    c.qlist = pl.qlist + nq * (int64_t)(R.lo[r] - R.lo[0]);
+    c.items = pl.items + R.ibase[r];
+    c.n_items = pl.n_items + r;
+    c.items_cap = (int32_t)std::min<int64_t>(icap[r], INT32_MAX);
 }
 
 // The cluster-major schedule of a uniform search (ADSX_SCHED_CLUSTER): round
@@ -741,36 +761,36 @@ static cudaError_t cm_scan(const Index *ix, const adsx::ScanArgs &a, Scratch &sc
     if ((e = adsx::launch_cm_merge(m, s)) != cudaSuccess) return e;
 
     // round 0: each query's r0 nearest clusters, every member to d = D (no r
-    // yet: the test cannot reject); then the later ranks against r
+    // yet: the test cannot reject); then the later ranks against r.  All
+    // rounds are planned at once (the probe lists are known).
     auto rounds = cm_rounds(r0, nprobe, ix->cm_growth);
     rounds.insert(rounds.begin(), {0, r0});
-    int width = 1;
-    for (const auto &r : rounds) width = std::max(width, r.second - r.first);
+    if ((int)rounds.size() > adsx::CM_MAX_ROUNDS) return cudaErrorInvalidValue;
+    adsx::CmRounds R;
+    R.n = (int32_t)rounds.size();
+    for (int r = 0; r < R.n; ++r) R.lo[r] = rounds[r].first;
+    R.lo[R.n] = nprobe;
     adsx::CmPlan pl;
-    int64_t items_cap = 0;
-    if ((e = cm_plan_buffers(ix, nq, width, G, sc, pl, &items_cap)) != cudaSuccess) return e;
+    int64_t icap[adsx::CM_MAX_ROUNDS];
+    if ((e = cm_plan_buffers(ix, nq, G, R, sc, pl, icap)) != cudaSuccess) return e;
+    if ((e = adsx::launch_cm_plan(a.probes, nq, nprobe, R, ix->nlist, G, ix->cm_tpi, ix->off, pl,
+                                  s)) != cudaSuccess)
+        return e;
     adsx::CmArgs c = cm_args_from(a, G);
     c.tpi = ix->cm_tpi;
     c.r2 = r2;
-    c.coff = pl.coff;
-    c.qlist = pl.qlist;
-    c.items = pl.items;
-    c.n_items = pl.n_items;
-    c.items_cap = (int32_t)items_cap;
     c.work_counter = counter;
     c.app_d = app_d;
     c.app_i = app_i;
     c.app_n = app_n;
     c.cap = cap;
-    for (size_t i = 0; i < rounds.size(); ++i) {
-        if ((e = adsx::launch_cm_plan(a.probes, nq, nprobe, rounds[i].first, rounds[i].second,
-                                      ix->nlist, G, ix->cm_tpi, ix->off, pl, s)) != cudaSuccess)
-            return e;
+    for (int i = 0; i < R.n; ++i) {
+        cm_round_args(c, pl, R, icap, nq, ix->nlist, i);
         c.test_on = i == 0 ? 0 : a.test_on;
         if ((e = mark_kernel(ix, true, s)) != cudaSuccess) return e;
         if ((e = adsx::launch_cm_scan(c, ix->device, s)) != cudaSuccess) return e;
         if ((e = mark_kernel(ix, false, s)) != cudaSuccess) return e;
-        m.final_pass = i + 1 == rounds.size();
+        m.final_pass = i + 1 == R.n;
         if ((e = adsx::launch_cm_merge(m, s)) != cudaSuccess) return e;
     }
     // queries whose list overflowed: the whole search again, query-major
@@ -1077,19 +1097,18 @@ int adsx_dco_fixed_r(const adsx_index *index, const float *Qv, int64_t nq, const
         CK(sc.get(&probes, (size_t)nq * ix->nlist), "alloc probe lists");
         CK(adsx::launch_cm_all_clusters(probes, nq, ix->nlist, s), "probe lists");
         adsx::CmPlan pl;
-        int64_t items_cap = 0;
+        adsx::CmRounds R;
+        R.n = 1;
+        R.lo[0] = 0;
+        R.lo[1] = ix->nlist;
+        int64_t icap[1];
         const int G = cm_queries_per_item(ix, nq, ix->nlist);
-        CK(cm_plan_buffers(ix, nq, ix->nlist, G, sc, pl, &items_cap), "alloc plan");
-        CK(adsx::launch_cm_plan(probes, nq, ix->nlist, 0, ix->nlist, ix->nlist, G,
-                                ix->cm_tpi, ix->off, pl, s),
+        CK(cm_plan_buffers(ix, nq, G, R, sc, pl, icap), "alloc plan");
+        CK(adsx::launch_cm_plan(probes, nq, ix->nlist, R, ix->nlist, G, ix->cm_tpi, ix->off, pl, s),
            "plan");
         adsx::CmArgs c = cm_args_from(a, G);
         c.tpi = ix->cm_tpi;
-        c.coff = pl.coff;
-        c.qlist = pl.qlist;
-        c.items = pl.items;
-        c.n_items = pl.n_items;
-        c.items_cap = (int32_t)items_cap;
+        cm_round_args(c, pl, R, icap, nq, ix->nlist, 0);
         c.work_counter = counter;
         c.r2fixed = rr.dev;
         c.decisions = dec.dev;

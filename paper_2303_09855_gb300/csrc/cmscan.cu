@@ -249,14 +249,17 @@ __global__ void __launch_bounds__(CM_THREADS, CmMinBlocks<T>::value) cm_scan_ker
                 const T *x = cb + (int64_t)blk * stride + (int64_t)(m0 + gi) * BLK + jo;
                 if (dense) {
                     // this step's blocks of the tile: loaded once for every query
-                    V v[DB][NL];
+                    // (16-bit storage: converted to FP32 once, not per query)
+                    typename Unpacked<T>::U v[DB][NL];
 #pragma unroll
                     for (int b = 0; b < DB; ++b) {
 #pragma unroll
                         for (int k = 0; k < NL; ++k) {
-                            zero_piece(v[b][k]);
+                            V w;
+                            zero_piece(w);
                             if (b < nb && ((U >> owner_lane<NL>(gi, k)) & 1u))
-                                v[b][k] = ld_piece(x + b * stride + k * NG * BLK);
+                                w = ld_piece(x + b * stride + k * NG * BLK);
+                            v[b][k] = unpack_piece(w, T());
                         }
                     }
                     const int pos = (int)o + m0 + own;
@@ -353,8 +356,8 @@ __global__ void __launch_bounds__(CM_THREADS, CmMinBlocks<T>::value) cm_scan_ker
                                 const QPiece<NL> qb = ld_qpiece_ro<NL>(qv1 + (blk + b) * BLK + jo);
 #pragma unroll
                                 for (int k = 0; k < NL; ++k) {
-                                    p0[k] = add_piece(v[b][k], qa, p0[k], T());
-                                    p1[k] = add_piece(v[b][k], qb, p1[k], T());
+                                    p0[k] = add_piece_u(v[b][k], qa, p0[k]);
+                                    p1[k] = add_piece_u(v[b][k], qb, p1[k]);
                                 }
                             }
                         }
@@ -475,41 +478,54 @@ __global__ void __launch_bounds__(CM_THREADS, CmMinBlocks<T>::value) cm_scan_ker
     }
 }
 
-// ---- round planning: the (query, probe rank) pairs of ranks [r0, r1) grouped
-// by cluster.  cnt[c] counts them; cm_plan_offsets turns the counts into
-// offsets of each cluster's query list and of its work items (one per G
-// queries and chunk of tpi 32-member tiles, so that large clusters are
-// shared among warps); cm_plan_scatter fills the lists and the items.
-__global__ void cm_plan_count_kernel(const int32_t *__restrict__ probes, int64_t nq, int pstride,
-                                     int r0, int r1, int *__restrict__ cnt)
+// ---- round planning, every round in one pass: the (query, probe rank)
+// pairs of each round grouped by cluster.  cnt[r][c] counts them;
+// cm_plan_offsets (one block per round) turns the counts into offsets of each
+// cluster's query list and of its work items (one per G queries and chunk of
+// tpi 32-member tiles, so that large clusters are shared among warps);
+// cm_plan_scatter fills the lists and the items.
+__device__ __forceinline__ int cm_round_of(const CmRounds &R, int p)
 {
-    const int w = r1 - r0;
+    int r = 0;
+    while (r + 1 < R.n && p >= R.lo[r + 1]) ++r;
+    return r;
+}
+
+__global__ void cm_plan_count_kernel(const int32_t *__restrict__ probes, int64_t nq, int pstride,
+                                     CmRounds R, int nlist, int *__restrict__ cnt)
+{
+    const int w = R.lo[R.n] - R.lo[0];
     const int64_t total = nq * w;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = i / w;
-        const int p = r0 + (int)(i - q * w);
-        atomicAdd(cnt + probes[q * pstride + p], 1);
+        const int p = R.lo[0] + (int)(i - q * w);
+        atomicAdd(cnt + (size_t)cm_round_of(R, p) * nlist + probes[q * pstride + p], 1);
     }
 }
 
-// One block: exclusive prefix sums of cnt (-> coff) and of ceil(cnt / G)
-// (-> ioff), the item total, and the cursors cleared.
+// One block per round: exclusive prefix sums of cnt (-> coff) and of
+// ceil(cnt / G) * chunks (-> ioff), the item total, and the cursors cleared.
 __device__ __forceinline__ int cm_chunks(const int64_t *off, int c, int tpi)
 {
     const int tiles = (int)((off[c + 1] - off[c] + 31) >> 5);
     return (tiles + tpi - 1) / tpi;
 }
 
-__global__ void __launch_bounds__(1024) cm_plan_offsets_kernel(const int *__restrict__ cnt,
+__global__ void __launch_bounds__(1024) cm_plan_offsets_kernel(const int *__restrict__ cnt_all,
                                                                const int64_t *__restrict__ off,
                                                                int nlist, int G, int tpi,
-                                                               int *__restrict__ coff,
-                                                               int *__restrict__ ioff,
-                                                               int *__restrict__ cur,
+                                                               int *__restrict__ coff_all,
+                                                               int *__restrict__ ioff_all,
+                                                               int *__restrict__ cur_all,
                                                                int *__restrict__ n_items)
 {
     __shared__ int s_a[32], s_b[32];
+    const int r = blockIdx.x;
+    const int *cnt = cnt_all + (size_t)r * nlist;
+    int *coff = coff_all + (size_t)r * (nlist + 1);
+    int *ioff = ioff_all + (size_t)r * nlist;
+    int *cur = cur_all + (size_t)r * nlist;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int per = (nlist + 1023) / 1024;
     const int c0 = t * per, c1 = c0 + per < nlist ? c0 + per : nlist;
@@ -557,29 +573,31 @@ __global__ void __launch_bounds__(1024) cm_plan_offsets_kernel(const int *__rest
     }
     if (t == 1023) {
         coff[nlist] = ea;
-        *n_items = eb;
+        n_items[r] = eb;
     }
 }
 
 __global__ void cm_plan_scatter_kernel(const int32_t *__restrict__ probes, int64_t nq, int pstride,
-                                       int r0, int r1, int G, int tpi,
+                                       CmRounds R, int nlist, int G, int tpi,
                                        const int64_t *__restrict__ off,
-                                       const int *__restrict__ coff,
-                                       const int *__restrict__ ioff, int *__restrict__ cur,
+                                       const int *__restrict__ coff_all,
+                                       const int *__restrict__ ioff_all, int *__restrict__ cur_all,
                                        int *__restrict__ qlist, int2 *__restrict__ items)
 {
-    const int w = r1 - r0;
+    const int w = R.lo[R.n] - R.lo[0];
     const int64_t total = nq * w;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = i / w;
-        const int p = r0 + (int)(i - q * w);
+        const int p = R.lo[0] + (int)(i - q * w);
+        const int r = cm_round_of(R, p);
         const int c = probes[q * pstride + p];
-        const int slot = atomicAdd(cur + c, 1);
-        qlist[coff[c] + slot] = (int)q;
+        const int slot = atomicAdd(cur_all + (size_t)r * nlist + c, 1);
+        qlist[nq * (R.lo[r] - R.lo[0]) + coff_all[(size_t)r * (nlist + 1) + c] + slot] = (int)q;
         if (slot % G == 0) {
             const int ch = cm_chunks(off, c, tpi), first = (slot / G) * ch;
-            for (int t = 0; t < ch; ++t) items[ioff[c] + first + t] = make_int2(c, first + t);
+            int2 *it = items + R.ibase[r] + ioff_all[(size_t)r * nlist + c] + first;
+            for (int t = 0; t < ch; ++t) it[t] = make_int2(c, first + t);
         }
     }
 }
@@ -617,21 +635,59 @@ __device__ __forceinline__ int rank_below(const unsigned long long *a, int n, un
     return lo;
 }
 
-// The distance bits (the high word of a key) of the K-th smallest key among
-// e[0..ne) and the appended keys 0..na (akey(i)): a radix select over the
-// bits below the prefix all of them share, 8 bits per pass, with a 256-bin
-// histogram in shared memory (lane l owns bins 8l .. 8l+7 for the scan);
-// lanes voting for the same bin merge into one atomic.
-template <typename AK>
-__device__ __forceinline__ unsigned select_hi(const unsigned long long *e, int ne, AK akey,
-                                              int na, int K, unsigned *hist, int lane)
+// Appended distance bits a lane keeps in registers (keys lane + 32 j): lists
+// of up to 32 * MERGE_RK entries are read from global memory once.
+constexpr int MERGE_RK = 16;
+
+// Calls f(h, valid) on every lane for each distance bit pattern h (the high
+// word of a key) of e[0..ne) and of the appended list -- from the registers
+// hv when `inreg`, else from gd 8 x 32 at a time -- with warp-uniform control
+// flow (f may use warp collectives).
+template <typename F>
+__device__ __forceinline__ void visit_hi(const unsigned long long *e, int ne, const float *gd,
+                                         int na, const unsigned (&hv)[MERGE_RK], bool inreg,
+                                         int lane, F f)
+{
+    for (int i0 = 0; i0 < ne; i0 += 32) {
+        const int i = i0 + lane;
+        f(i < ne ? (unsigned)(e[i] >> 32) : 0u, i < ne);
+    }
+    if (inreg) {
+#pragma unroll
+        for (int j = 0; j < MERGE_RK; ++j)
+            if (32 * j < na) f(hv[j], lane + 32 * j < na);
+    } else {
+        for (int i0 = 0; i0 < na; i0 += 32 * 8) {
+            unsigned h[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + 32 * u + lane;
+                h[u] = i < na ? __float_as_uint(__ldg(gd + i)) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (i0 + 32 * u < na) f(h[u], i0 + 32 * u + lane < na);
+        }
+    }
+}
+
+// The distance bits of the K-th smallest key among e[0..ne) and the
+// appended list (distances gd[0..na), their bits in hv when `inreg`): a radix
+// select over the bits below the prefix all of them share, 8 bits per pass,
+// with a 256-bin histogram in shared memory (lane l owns bins 8l .. 8l+7 for
+// the scan); lanes voting for the same bin merge into one atomic.
+__device__ __forceinline__ unsigned select_hi(const unsigned long long *e, int ne,
+                                              const float *gd, int na,
+                                              const unsigned (&hv)[MERGE_RK], bool inreg, int K,
+                                              unsigned *hist, int lane)
 {
     unsigned lo = 0xffffffffu, hi = 0u;
-    for (int i = lane; i < ne + na; i += 32) {
-        const unsigned h = (unsigned)((i < ne ? e[i] : akey(i - ne)) >> 32);
-        lo = min(lo, h);
-        hi = max(hi, h);
-    }
+    visit_hi(e, ne, gd, na, hv, inreg, lane, [&](unsigned h, bool v) {
+        if (v) {
+            lo = min(lo, h);
+            hi = max(hi, h);
+        }
+    });
     lo = __reduce_min_sync(FULL, lo);
     hi = __reduce_max_sync(FULL, hi);
     if (lo == hi) return lo;
@@ -645,16 +701,11 @@ __device__ __forceinline__ unsigned select_hi(const unsigned long long *e, int n
 #pragma unroll
         for (int j = 0; j < 8; ++j) hist[lane * 8 + j] = 0u;
         __syncwarp();
-        for (int i0 = 0; i0 < ne + na; i0 += 32) {
-            const int i = i0 + lane;
-            unsigned bin = 256u;                              // no vote
-            if (i < ne + na) {
-                const unsigned h = (unsigned)((i < ne ? e[i] : akey(i - ne)) >> 32);
-                if ((h & pmask) == prefix) bin = (h >> shift) & dmask;
-            }
+        visit_hi(e, ne, gd, na, hv, inreg, lane, [&](unsigned h, bool v) {
+            const unsigned bin = v && (h & pmask) == prefix ? (h >> shift) & dmask : 256u;
             const unsigned peers = __match_any_sync(FULL, bin);
             if (bin < 256u && lane == __ffs(peers) - 1) atomicAdd(hist + bin, (unsigned)__popc(peers));
-        }
+        });
         __syncwarp();
         unsigned c[8], sum = 0u;
 #pragma unroll
@@ -696,7 +747,7 @@ __device__ __forceinline__ unsigned select_hi(const unsigned long long *e, int n
     return prefix;
 }
 
-__global__ void __launch_bounds__(MERGE_WARPS * 32) cm_merge_kernel(CmMergeArgs m)
+__global__ void __launch_bounds__(MERGE_WARPS * 32, 8) cm_merge_kernel(CmMergeArgs m)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -732,16 +783,32 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) cm_merge_kernel(CmMergeArgs 
         if (na > 64u && ne + (int)na > K) {
             // many appended: keep only the keys whose distance is at most the
             // K-th smallest of both lists (ties kept), then sort those
-            const unsigned th = select_hi(ek, ne, akey, (int)na, K, hist, lane);
+            const int n = (int)na;
+            const bool inreg = n <= 32 * MERGE_RK;
+            unsigned hv[MERGE_RK];
+#pragma unroll
+            for (int j = 0; j < MERGE_RK; ++j) {
+                const int i = lane + 32 * j;
+                hv[j] = inreg && i < n ? __float_as_uint(__ldg(gd + i)) : 0u;
+            }
+            const unsigned th = select_hi(ek, ne, gd, n, hv, inreg, K, hist, lane);
             int kept = 0;
-            for (int c0 = 0; c0 < (int)na; c0 += 32) {
-                const int i = c0 + lane;
-                const unsigned long long v = i < (int)na ? akey(i) : NONE;
-                const bool keep = i < (int)na && (unsigned)(v >> 32) <= th;
-                const unsigned km = __ballot_sync(FULL, keep);
-                const int at = kept + __popc(km & below_mask(lane));
-                if (keep && at < m.T) ak[at] = v;
-                kept += __popc(km);
+            for (int i0 = 0; i0 < n; i0 += 32 * 8) {
+                unsigned long long v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = i0 + 32 * u + lane;
+                    v[u] = i < n ? akey(i) : NONE;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (i0 + 32 * u >= n) break;
+                    const bool keep = i0 + 32 * u + lane < n && (unsigned)(v[u] >> 32) <= th;
+                    const unsigned km = __ballot_sync(FULL, keep);
+                    const int at = kept + __popc(km & below_mask(lane));
+                    if (keep && at < m.T) ak[at] = v[u];
+                    kept += __popc(km);
+                }
             }
             if (kept > m.T) {
                 // ties at the K-th distance beyond the sort capacity: the
@@ -875,16 +942,18 @@ size_t cm_smem_bytes(int G, int db, int storage)
     return (size_t)CmCarve(G, db, row).bytes * CM_WARPS;
 }
 
-cudaError_t launch_cm_plan(const int32_t *probes, int64_t nq, int pstride, int r0, int r1, int nlist,
-                           int G, int tpi, const int64_t *off, CmPlan &pl, cudaStream_t s)
+cudaError_t launch_cm_plan(const int32_t *probes, int64_t nq, int pstride, const CmRounds &R,
+                           int nlist, int G, int tpi, const int64_t *off, CmPlan &pl,
+                           cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(pl.cnt, 0, sizeof(int) * nlist, s);
+    if (R.n < 1 || R.n > CM_MAX_ROUNDS) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(pl.cnt, 0, sizeof(int) * (size_t)R.n * nlist, s);
     if (e != cudaSuccess) return e;
-    const int64_t work = nq * (int64_t)(r1 - r0);
-    cm_plan_count_kernel<<<grid_for(work, 256), 256, 0, s>>>(probes, nq, pstride, r0, r1, pl.cnt);
-    cm_plan_offsets_kernel<<<1, 1024, 0, s>>>(pl.cnt, off, nlist, G, tpi, pl.coff, pl.ioff, pl.cur,
-                                              pl.n_items);
-    cm_plan_scatter_kernel<<<grid_for(work, 256), 256, 0, s>>>(probes, nq, pstride, r0, r1, G, tpi,
+    const int64_t work = nq * (int64_t)(R.lo[R.n] - R.lo[0]);
+    cm_plan_count_kernel<<<grid_for(work, 256), 256, 0, s>>>(probes, nq, pstride, R, nlist, pl.cnt);
+    cm_plan_offsets_kernel<<<R.n, 1024, 0, s>>>(pl.cnt, off, nlist, G, tpi, pl.coff, pl.ioff, pl.cur,
+                                                pl.n_items);
+    cm_plan_scatter_kernel<<<grid_for(work, 256), 256, 0, s>>>(probes, nq, pstride, R, nlist, G, tpi,
                                                                 off, pl.coff, pl.ioff, pl.cur,
                                                                 pl.qlist, pl.items);
     return cudaGetLastError();

@@ -353,6 +353,37 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
                 }
                 const unsigned em = __ballot_sync(FULL, enter);
                 if (!em) break;
+                // With exact DCOs (test off) the order does not matter: a
+                // bounded set fed one vertex at a time ends as the smallest
+                // of all it was offered, so every entering vertex goes in at
+                // once.  With the test on, while the set has room its
+                // threshold stays +inf, so the first `room` entering vertices
+                // all enter: one merge for all of them; the lanes after the
+                // last one are decided again if the set is now full.
+                const int room = !g.test_on ? 32 : (g.pp ? g.K - n1 : g.ef - nR);
+                if (room > 1 && __popc(em) > 1) {
+                    const int cnt = room < __popc(em) ? room : __popc(em);
+                    const bool take = enter && __popc(em & below) < cnt;
+                    const unsigned tm = __ballot_sync(FULL, take);
+                    const int jl = 31 - __clz(tm);
+                    settled |= (jl == 31) ? FULL : ((2u << jl) - 1u);
+                    if (!g.pp) {
+                        const int na = stage_sorted(take, sdec, v, ad, ai, lane);
+                        nR = warp_merge(rd, ri, rx, nR, ad, ai, na, nd, ni, nx, g.ef, lane);
+                        float *tf = rd; rd = nd; nd = tf;
+                        int *ti = ri; ri = ni; ni = ti;
+                        ti = rx; rx = nx; nx = ti;
+                        th = nR == g.ef ? rd[nR - 1] : INFINITY;
+                    } else {
+                        const int na = stage_sorted(take, sdec, v, ad1, ai1, lane);
+                        n1 = warp_merge(kd, ki, nullptr, n1, ad1, ai1, na, kd2, ki2, nullptr, g.K, lane);
+                        float *tf = kd; kd = kd2; kd2 = tf;
+                        int *ti = ki; ki = ki2; ki2 = ti;
+                        th = n1 == g.K ? kd[n1 - 1] : INFINITY;
+                    }
+                    if (fresh && lane > jl) decide(th);
+                    continue;
+                }
                 const int j = __ffs(em) - 1;
                 settled |= (j == 31) ? FULL : ((2u << j) - 1u);
                 if (lane == j) {

@@ -134,6 +134,41 @@ __device__ __forceinline__ float2 add_piece(uint4 x, const QPiece<2> &q, float2 
     return S;
 }
 
+// A piece held unpacked in FP32 registers (16-bit storage: its 8 values;
+// FP32: the piece itself), for a piece used against many queries: the
+// conversion is exact, and add_piece_u adds in add_piece's order, so the
+// sums are the same.
+template <typename T> struct Unpacked {
+    struct U { float4 a, b; };
+};
+template <> struct Unpacked<float> {
+    typedef float4 U;
+};
+__device__ __forceinline__ float4 unpack_piece(float4 x, float) { return x; }
+template <typename H>
+__device__ __forceinline__ typename Unpacked<H>::U unpack_piece(uint4 x, H h)
+{
+    typename Unpacked<H>::U u;
+    unpack2(x.x, u.a.x, u.a.y, h);
+    unpack2(x.y, u.a.z, u.a.w, h);
+    unpack2(x.z, u.b.x, u.b.y, h);
+    unpack2(x.w, u.b.z, u.b.w, h);
+    return u;
+}
+__device__ __forceinline__ float2 add_piece_u(float4 x, const QPiece<4> &q, float2 S)
+{
+    return add_piece(x, q, S, 0.f);
+}
+template <typename U>
+__device__ __forceinline__ float2 add_piece_u(const U &x, const QPiece<2> &q, float2 S)
+{
+    S = add_pair(x.a.x, x.a.y, q.a.x, q.a.y, S);
+    S = add_pair(x.a.z, x.a.w, q.a.z, q.a.w, S);
+    S = add_pair(x.b.x, x.b.y, q.b.x, q.b.y, S);
+    S = add_pair(x.b.z, x.b.w, q.b.z, q.b.w, S);
+    return S;
+}
+
 // The candidate (of the set of 32) whose complete sum lane l receives from
 // group_sum, and the lane that receives candidate g + (32/NL) k.
 template <int NL>
