@@ -527,6 +527,10 @@ struct CmArgs {
     unsigned *app_n;            // nq appended counts
     int32_t cap;
     int64_t *out_dims;          // may be NULL: dims sampled, added per query
+    // 16-bit storage, round 0 (no r yet): append the approximate S_D and the
+    // CSR row of every member instead of rechecking each one; the exact
+    // distances of the few that can reach the top-K follow (cm_recheck0)
+    int32_t defer_recheck = 0;
     // fixed-threshold mode (decisions != NULL), as ScanArgs
     const float *r2fixed = nullptr;
     uint8_t *decisions = nullptr;
@@ -546,6 +550,20 @@ struct CmMergeArgs {
     int32_t metric;
     int32_t final_pass;
 };
+// Round 0 of a 16-bit cluster-major search, per query: the appended
+// (approximate S_D, CSR row) pairs become the exact (S_D, id) pairs of every
+// member that can be among the K nearest (the others are dropped).
+struct CmRecheck0Args {
+    int64_t nq;
+    int32_t K, cap, Dp;
+    float u;                    // unit roundoff of the storage type
+    const float *rows32, *norms, *qrot;
+    const int32_t *ids;
+    float *app_d;
+    int32_t *app_i;
+    unsigned *app_n;
+};
+cudaError_t launch_cm_recheck0(const CmRecheck0Args &r, cudaStream_t s);
 // The rounds of a cluster-major search: probe ranks [lo[r], lo[r + 1]) form
 // round r; its work items start at ibase[r] of the plan's item array.
 constexpr int CM_MAX_ROUNDS = 8;

@@ -784,12 +784,30 @@ static cudaError_t cm_scan(const Index *ix, const adsx::ScanArgs &a, Scratch &sc
     c.app_i = app_i;
     c.app_n = app_n;
     c.cap = cap;
+    // 16-bit storage: round 0 appends approximate distances, and only the
+    // members that can be among the K nearest are rechecked in FP32
+    const bool defer = ix->storage != ADSX_F32;
+    adsx::CmRecheck0Args rc0;
+    rc0.nq = nq;
+    rc0.K = K;
+    rc0.cap = cap;
+    rc0.Dp = ix->Dp;
+    rc0.u = ix->storage == ADSX_BF16 ? 1.0f / 256.0f : 1.0f / 2048.0f;
+    rc0.rows32 = ix->rows32;
+    rc0.norms = ix->norms;
+    rc0.qrot = a.qrot;
+    rc0.ids = ix->ids;
+    rc0.app_d = app_d;
+    rc0.app_i = app_i;
+    rc0.app_n = app_n;
     for (int i = 0; i < R.n; ++i) {
         cm_round_args(c, pl, R, icap, nq, ix->nlist, i);
         c.test_on = i == 0 ? 0 : a.test_on;
+        c.defer_recheck = defer && i == 0;
         if ((e = mark_kernel(ix, true, s)) != cudaSuccess) return e;
         if ((e = adsx::launch_cm_scan(c, ix->device, s)) != cudaSuccess) return e;
         if ((e = mark_kernel(ix, false, s)) != cudaSuccess) return e;
+        if (c.defer_recheck && (e = adsx::launch_cm_recheck0(rc0, s)) != cudaSuccess) return e;
         m.final_pass = i + 1 == R.n;
         if ((e = adsx::launch_cm_merge(m, s)) != cudaSuccess) return e;
     }

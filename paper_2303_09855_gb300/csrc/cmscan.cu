@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(CM_THREADS, CmMinBlocks<T>::value) cm_scan_ker
                         }
                         // Case 3: the exact compare at d = D
                         bool cand = alive;
-                        if constexpr (Roundoff<T>::u > 0.f) {
+                        if (Roundoff<T>::u > 0.f && !a.defer_recheck) {
                             // 16-bit storage: only candidates with sqrt(S~) <= r + u ||x||
                             // can have S_D <= r^2; their exact FP32 distance comes from
                             // the FP32 row copy
@@ -327,7 +327,8 @@ __global__ void __launch_bounds__(CM_THREADS, CmMinBlocks<T>::value) cm_scan_ker
                                     const unsigned idx = b0 + __popc(pm & below);
                                     if (idx < (unsigned)a.cap) {
                                         a.app_d[(int64_t)q * a.cap + idx] = S;
-                                        a.app_i[(int64_t)q * a.cap + idx] = a.ids[pos];
+                                        a.app_i[(int64_t)q * a.cap + idx] =
+                                            a.defer_recheck ? pos : a.ids[pos];
                                     }
                                 }
                             }
@@ -881,6 +882,109 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32, 8) cm_merge_kernel(CmMergeAr
     }
 }
 
+// Round 0 of a 16-bit search: per query (one warp) the list holds every
+// member of the nearest cluster with its approximate distance a_i = sqrt(S~_i)
+// and CSR row.  The exact distance e_i differs from a_i by at most
+// ||y~_i - y_i|| <= u ||y_i||, so B, the K-th smallest of a_i + u ||y_i||, is at
+// least the exact K-th distance, and only members with a_i <= B + u ||y_i||
+// can be among the K nearest.  B is taken as the K-th smallest of the lanes'
+// four smallest bounds (the K-th of a subset: never below the K-th of all,
+// so still valid); with K > 128 every member is kept.  The kept members get
+// their exact FP32 distances from the FP32 rows (recheck_rows, the same
+// arithmetic as every other recheck) and their ids; the list is compacted.
+__global__ void __launch_bounds__(MERGE_WARPS * 32) cm_recheck0_kernel(CmRecheck0Args r)
+{
+    __shared__ unsigned s_w[MERGE_WARPS][128];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned *w4 = s_w[warp];
+    for (int64_t q = (int64_t)blockIdx.x * MERGE_WARPS + warp; q < r.nq;
+         q += (int64_t)gridDim.x * MERGE_WARPS) {
+        unsigned na = r.app_n[q];
+        if (na > (unsigned)r.cap) na = (unsigned)r.cap;   // the merge flags the overflow
+        const int n = (int)na;
+        float *gd = r.app_d + q * r.cap;
+        int32_t *gi = r.app_i + q * r.cap;
+        float B = INFINITY;
+        if (n > r.K && r.K <= 128) {
+            // each lane's four smallest bounds a_i + u ||y_i|| (as float bits:
+            // non-negative floats order like their bit patterns)
+            unsigned t0 = ~0u, t1 = ~0u, t2 = ~0u, t3 = ~0u;
+            for (int i0 = 0; i0 < n; i0 += 32 * 8) {
+                float sd[8];
+                int pr[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int i = i0 + 32 * k + lane;
+                    sd[k] = i < n ? gd[i] : 0.f;
+                    pr[k] = i < n ? gi[i] : 0;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    if (i0 + 32 * k + lane < n) {
+                        unsigned x = __float_as_uint(sqrtf(sd[k]) + r.u * r.norms[pr[k]]);
+                        unsigned m;
+                        m = min(t0, x); x = max(t0, x); t0 = m;
+                        m = min(t1, x); x = max(t1, x); t1 = m;
+                        m = min(t2, x); x = max(t2, x); t2 = m;
+                        t3 = min(t3, x);
+                    }
+                }
+            }
+            w4[lane * 4 + 0] = t0;
+            w4[lane * 4 + 1] = t1;
+            w4[lane * 4 + 2] = t2;
+            w4[lane * 4 + 3] = t3;
+            __syncwarp();
+            for (int size = 2; size <= 128; size <<= 1) {
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    for (int i = lane; i < 128; i += 32) {
+                        const int j = i ^ stride;
+                        if (j > i) {
+                            const unsigned x = w4[i], y = w4[j];
+                            if ((x > y) == ((i & size) == 0)) {
+                                w4[i] = y;
+                                w4[j] = x;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+            const unsigned kb = w4[r.K - 1];
+            B = kb == ~0u ? INFINITY : __uint_as_float(kb) * 1.0001f;
+            __syncwarp();
+        }
+        // keep (in list order, compacted in place) the members that can be
+        // among the K nearest, then their exact distances, 32 at a time
+        int kept = 0;
+        const float *qv = r.qrot + q * r.Dp;
+        for (int i0 = 0; i0 < n; i0 += 32) {
+            const int i = i0 + lane;
+            float sd = 0.f;
+            int pr = 0;
+            bool keep = false;
+            if (i < n) {
+                sd = gd[i];
+                pr = gi[i];
+                keep = !(B < INFINITY) ||
+                       sqrtf(sd) <= (B + r.u * r.norms[pr]) * 1.0001f;
+            }
+            const unsigned km = __ballot_sync(FULL, keep);
+            // exact FP32 distances of the kept members of this chunk
+            const float S = recheck_rows(r.rows32, r.Dp, qv, keep, pr, sd, lane);
+            __syncwarp();                     // the chunk is read before it is written
+            if (keep) {
+                const int at = kept + __popc(km & below_mask(lane));
+                gd[at] = S;
+                gi[at] = r.ids[pr];
+            }
+            kept += __popc(km);
+        }
+        __syncwarp();
+        if (lane == 0 && r.app_n[q] <= (unsigned)r.cap) r.app_n[q] = (unsigned)kept;
+    }
+}
+
 // Items (query, one split) of the queries whose lists overflowed, for a
 // query-major re-run.
 __global__ void cm_overflow_items_kernel(const int *__restrict__ ovf, int64_t nq,
@@ -998,6 +1102,15 @@ cudaError_t launch_cm_merge(const CmMergeArgs &m, cudaStream_t s)
     int64_t grid = (m.nq + MERGE_WARPS - 1) / MERGE_WARPS;
     if (grid > 152 * 16) grid = 152 * 16;
     cm_merge_kernel<<<(unsigned)grid, MERGE_WARPS * 32, smem, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cm_recheck0(const CmRecheck0Args &r, cudaStream_t s)
+{
+    if (r.nq <= 0) return cudaSuccess;
+    int64_t grid = (r.nq + MERGE_WARPS - 1) / MERGE_WARPS;
+    if (grid > 152 * 16) grid = 152 * 16;
+    cm_recheck0_kernel<<<(unsigned)grid, MERGE_WARPS * 32, 0, s>>>(r);
     return cudaGetLastError();
 }
 

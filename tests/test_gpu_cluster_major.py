@@ -177,6 +177,15 @@ def test_bf16_and_cosine_and_pdscan_across_schedules(cm):
                                                          return_dims=True))
             for x, y in zip(a, b):
                 assert np.array_equal(x, y)
+        # 16-bit round 0 rechecks only the members that can be among the K
+        # nearest (a bound from the lanes' four smallest; every member when
+        # K > 128): FDScanning stays identical to query-major, for K below,
+        # near and above that limit and for lists shorter than K
+        for K in (1, 100, 128, 150, 400):
+            (a, b) = _both(adsx, bf, lambda: bf.search(wl.Q, K, 12, eps0=math.inf,
+                                                       return_dims=True))
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y), K
         _, kd = oracle.knn_exact(Y, Qr, 10)
         r2 = (kd[:, -1] * 1.2).astype(np.float32)
         (a_dec, a_dims), (b_dec, b_dims) = _both(adsx, bf,
