@@ -128,31 +128,81 @@ namespace {
 // r = fma(a, b, -h)), the running sum by TwoSum (Knuth), and the errors are
 // summed separately, so y is as accurate as if computed in twice the working
 // precision and then rounded once to FP32.
-// 64 x 64 output tile per 256-thread block, 4 x 4 per thread, k-steps of 16.
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+// 64 x 64 (or 32 x 32) output tile per 256-thread block, 4 x 4 (2 x 2) per
+// thread, k-steps of 16; neighbouring outputs of a thread go through the
+// same operations as packed FP32 pairs.
+
+// Packed FP32 pair arithmetic (sm_100+ f32x2: each element rounded as the
+// scalar instruction would be, two elements per instruction).
+__device__ __forceinline__ float2 f2_op_add(float2 a, float2 b)
 {
-    s = a + b;
-    const float z = s - a;
-    e = (a - (s - z)) + (b - z);
+    float2 r;
+    asm("{\n .reg .b64 av, bv, rv;\n mov.b64 av, {%2, %3};\n mov.b64 bv, {%4, %5};\n"
+        " add.rn.f32x2 rv, av, bv;\n mov.b64 {%0, %1}, rv;\n}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 f2_op_sub(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n .reg .b64 av, bv, rv;\n mov.b64 av, {%2, %3};\n mov.b64 bv, {%4, %5};\n"
+        " sub.rn.f32x2 rv, av, bv;\n mov.b64 {%0, %1}, rv;\n}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 f2_op_mul(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n .reg .b64 av, bv, rv;\n mov.b64 av, {%2, %3};\n mov.b64 bv, {%4, %5};\n"
+        " mul.rn.f32x2 rv, av, bv;\n mov.b64 {%0, %1}, rv;\n}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 f2_op_fma(float2 a, float2 b, float2 c)
+{
+    float2 r;
+    asm("{\n .reg .b64 av, bv, cv, rv;\n mov.b64 av, {%2, %3};\n mov.b64 bv, {%4, %5};\n"
+        " mov.b64 cv, {%6, %7};\n fma.rn.f32x2 rv, av, bv, cv;\n mov.b64 {%0, %1}, rv;\n}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
 }
 
+// One Dot2 step for two outputs sharing the factor a: the products a*b.x and
+// a*b.y split exactly (TwoProduct: h = a*b, r = fma(a, b, -h), taken here as
+// r = -fma(-a, b, h), the same value), h added to hi by TwoSum, the errors
+// q + r into lo -- element by element the scalar sequence.
+__device__ __forceinline__ void dot2_pair(float a, float2 b, float2 &hi, float2 &lo)
+{
+    const float2 aa = make_float2(a, a), na = make_float2(-a, -a);
+    const float2 h = f2_op_mul(aa, b);
+    const float2 t = f2_op_fma(na, b, h);          // -r
+    const float2 s = f2_op_add(hi, h);
+    const float2 z = f2_op_sub(s, hi);
+    const float2 e = f2_op_add(f2_op_sub(hi, f2_op_sub(s, z)), f2_op_sub(h, z));
+    hi = s;
+    lo = f2_op_add(lo, f2_op_sub(e, t));           // lo + (q + r)
+}
+
+template <int T>
 __global__ void __launch_bounds__(256) rotate_dot2_kernel(const float *__restrict__ X, int64_t N,
                                                           int D, const float *__restrict__ P,
                                                           int ldp, float *__restrict__ Y, int Dp)
 {
-    __shared__ float Xs[16][64 + 4];
-    __shared__ float Ps[16][64 + 4];
+    constexpr int TM = T / 16;          // outputs per thread along each side
+    __shared__ float Xs[16][T + 4];
+    __shared__ float Ps[16][T + 4];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t r0 = (int64_t)blockIdx.x * 64;
-    const int c0 = blockIdx.y * 64;
-    float hi[4][4], lo[4][4];
+    const int64_t r0 = (int64_t)blockIdx.x * T;
+    const int c0 = blockIdx.y * T;
+    float2 hi[TM][TM / 2], lo[TM][TM / 2];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) hi[i][j] = lo[i][j] = 0.f;
+        for (int j = 0; j < TM / 2; ++j) hi[i][j] = lo[i][j] = make_float2(0.f, 0.f);
     for (int k0 = 0; k0 < D; k0 += 16) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < TM; ++i) {
             const int e = tid + i * 256, r = e >> 4, kk = e & 15;
             const int64_t gr = r0 + r;
             const int gk = k0 + kk, gc = c0 + r;
@@ -162,33 +212,28 @@ __global__ void __launch_bounds__(256) rotate_dot2_kernel(const float *__restric
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < 16; ++kk) {
-            float a[4], b[4];
+            float a[TM], b[TM];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = Xs[kk][ty * 4 + i];
+            for (int i = 0; i < TM; ++i) a[i] = Xs[kk][ty * TM + i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Ps[kk][tx * 4 + j];
+            for (int j = 0; j < TM; ++j) b[j] = Ps[kk][tx * TM + j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float h = a[i] * b[j];
-                    const float r = fmaf(a[i], b[j], -h);
-                    float s, q;
-                    two_sum(hi[i][j], h, s, q);
-                    hi[i][j] = s;
-                    lo[i][j] += q + r;
-                }
+                for (int j = 0; j < TM / 2; ++j)
+                    dot2_pair(a[i], make_float2(b[2 * j], b[2 * j + 1]), hi[i][j], lo[i][j]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int64_t gr = r0 + ty * 4 + i;
+    for (int i = 0; i < TM; ++i) {
+        const int64_t gr = r0 + ty * TM + i;
         if (gr >= N) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int gc = c0 + tx * 4 + j;
-            if (gc < Dp) Y[gr * Dp + gc] = hi[i][j] + lo[i][j];
+        for (int j = 0; j < TM; ++j) {
+            const int gc = c0 + tx * TM + j;
+            const float2 h = hi[i][j / 2], l = lo[i][j / 2];
+            if (gc < Dp) Y[gr * Dp + gc] = (j & 1) ? h.y + l.y : h.x + l.x;
         }
     }
 }
@@ -200,8 +245,17 @@ cudaError_t launch_rotate(const float *X, int64_t N, int D, const float *P, int 
 {
     if (N <= 0) return cudaSuccess;
     if ((N + 63) / 64 > 0x7fffffffLL) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)((N + 63) / 64), (unsigned)((Dp + 63) / 64));
-    rotate_dot2_kernel<<<grid, 256, 0, s>>>(X, N, D, P, ldp, Y, Dp);
+    // 64 x 64 output tiles, or 32 x 32 ones when the former would give fewer
+    // than about 8 blocks per SM (a query batch; each output is summed in the
+    // same order either way)
+    const int64_t b64 = ((N + 63) / 64) * ((Dp + 63) / 64);
+    if (b64 >= 8 * 152) {
+        dim3 grid((unsigned)((N + 63) / 64), (unsigned)((Dp + 63) / 64));
+        rotate_dot2_kernel<64><<<grid, 256, 0, s>>>(X, N, D, P, ldp, Y, Dp);
+    } else {
+        dim3 grid((unsigned)((N + 31) / 32), (unsigned)((Dp + 31) / 32));
+        rotate_dot2_kernel<32><<<grid, 256, 0, s>>>(X, N, D, P, ldp, Y, Dp);
+    }
     return cudaGetLastError();
 }
 
