@@ -46,6 +46,22 @@ __device__ __forceinline__ bool pless(float d1, int i1, float d2, int i2)
     return d1 < d2 || (d1 == d2 && i1 < i2);
 }
 
+// The least t >= 0 with fl(t f) >= S (f > 0), i.e. the least threshold under
+// which the squared test "S > t f" passes: fl(t f) does not decrease as t
+// grows, so the correctly rounded S / f is moved to the boundary (in practice
+// one float step at most; the loops are bounded).
+__device__ __forceinline__ float pass_bound(float S, float f)
+{
+    float t = __fdiv_rn(S, f);
+    for (int it = 0; it < 64 && __fmul_rn(t, f) < S; ++it) t = nextafterf(t, INFINITY);
+    for (int it = 0; it < 64 && t > 0.f; ++it) {
+        const float pt = nextafterf(t, 0.f);
+        if (__fmul_rn(pt, f) >= S) t = pt;
+        else break;
+    }
+    return t;
+}
+
 // number of entries of the sorted (d, i)[0..n) that precede (x, xi)
 __device__ __forceinline__ int rank_in(const float *d, const int *i, int n, float x, int xi)
 {
@@ -288,10 +304,12 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
         // after each step; a threshold that only shrinks can only move a
         // decision to an earlier rejection, which the recorded S_d settle
         // exactly (the same FP32 comparison).  So the decisions are then
-        // replayed in list order: whenever a vertex enters the set that gives
-        // the threshold (R for HNSW+, R1 for HNSW++), it is inserted and the
-        // later vertices are decided again against the new threshold.  The
-        // dims counted are those of the paper's order.
+        // replayed in list order: each vertex knows the least threshold under
+        // which it is positive, the vertices that enter the set giving the
+        // threshold (R for HNSW+, R1 for HNSW++) are found one after another
+        // in registers, and each vertex is finally decided against the
+        // threshold of its turn.  The dims counted are those of the paper's
+        // order.
         auto dco_batch = [&](int v, bool fresh) {
             const bool full0 = nR == g.ef;
             const float rmax0 = full0 ? rd[nR - 1] : INFINITY;
@@ -341,69 +359,90 @@ __global__ void __launch_bounds__(GW * 32) graph_search_kernel(GraphArgs g)
                     }
                 }
             };
-            if (fresh) decide(th);
-            // replay in list order: the first vertex (lane) that enters the
-            // threshold set is inserted, the lanes after it are decided again
+            // tpos: the smallest threshold under which this vertex is positive
+            // (every recorded step passes and S_D <= t): the larger of S_D
+            // and, per earlier step, the least t with fl(t f) >= S_d; +inf if
+            // th already rejects it (a smaller threshold rejects it too)
+            float tpos = INFINITY, sD = 0.f;
+            if (fresh) {
+                decide(th);
+                if (dec == 1) {
+                    sD = sdec;
+                    tpos = sdec;
+                    int b2 = 0;
+                    for (int k = 0; k + 1 < nst; ++k) {
+                        b2 = b2 + g.db < g.nblk ? b2 + g.db : g.nblk;
+                        tpos = fmaxf(tpos, pass_bound(sst[k * 32 + lane], g.ftab[b2]));
+                    }
+                }
+            }
+            // Replay in list order.  T is the set that gives the threshold (R
+            // for HNSW+, R1 for HNSW++, C entries at most); E holds the keys of
+            // this batch's vertices that entered it so far, sorted, lane e the
+            // e-th; thk is the C-th smallest key of T and E (~0: T and E hold
+            // fewer), the threshold for the vertices after the last one that
+            // entered.  The first vertex still positive under thk with a key
+            // below it enters next; each vertex keeps the thk of its turn.
+            const int C = g.pp ? g.K : g.ef;
+            const int nT = g.pp ? n1 : nR;
+            const float *Td = g.pp ? kd : rd;
+            const int *Ti = g.pp ? ki : ri;
+            unsigned long long thk = nT == C ? dkey(Td[C - 1], Ti[C - 1]) : ~0ull;
+            unsigned long long E = ~0ull, mythk = thk;
+            const unsigned long long mykey = dkey(sD, v);
+            int m = 0;
             unsigned settled = 0u;
             for (;;) {
-                bool enter = false;
-                if (fresh && !((settled >> lane) & 1u) && dec == 1) {
-                    if (!g.pp) enter = nR < g.ef || pless(sdec, v, rd[nR - 1], ri[nR - 1]);
-                    else enter = n1 < g.K || pless(sdec, v, kd[n1 - 1], ki[n1 - 1]);
-                }
+                const float thd = thk == ~0ull ? INFINITY : __uint_as_float((unsigned)(thk >> 32));
+                const bool enter = fresh && !((settled >> lane) & 1u) && thd >= tpos && mykey < thk;
                 const unsigned em = __ballot_sync(FULL, enter);
                 if (!em) break;
-                // With exact DCOs (test off) the order does not matter: a
-                // bounded set fed one vertex at a time ends as the smallest
-                // of all it was offered, so every entering vertex goes in at
-                // once.  With the test on, while the set has room its
-                // threshold stays +inf, so the first `room` entering vertices
-                // all enter: one merge for all of them; the lanes after the
-                // last one are decided again if the set is now full.
-                const int room = !g.test_on ? 32 : (g.pp ? g.K - n1 : g.ef - nR);
-                if (room > 1 && __popc(em) > 1) {
-                    const int cnt = room < __popc(em) ? room : __popc(em);
-                    const bool take = enter && __popc(em & below) < cnt;
-                    const unsigned tm = __ballot_sync(FULL, take);
-                    const int jl = 31 - __clz(tm);
-                    settled |= (jl == 31) ? FULL : ((2u << jl) - 1u);
-                    if (!g.pp) {
-                        const int na = stage_sorted(take, sdec, v, ad, ai, lane);
-                        nR = warp_merge(rd, ri, rx, nR, ad, ai, na, nd, ni, nx, g.ef, lane);
-                        float *tf = rd; rd = nd; nd = tf;
-                        int *ti = ri; ri = ni; ni = ti;
-                        ti = rx; rx = nx; nx = ti;
-                        th = nR == g.ef ? rd[nR - 1] : INFINITY;
-                    } else {
-                        const int na = stage_sorted(take, sdec, v, ad1, ai1, lane);
-                        n1 = warp_merge(kd, ki, nullptr, n1, ad1, ai1, na, kd2, ki2, nullptr, g.K, lane);
-                        float *tf = kd; kd = kd2; kd2 = tf;
-                        int *ti = ki; ki = ki2; ki2 = ti;
-                        th = n1 == g.K ? kd[n1 - 1] : INFINITY;
-                    }
-                    if (fresh && lane > jl) decide(th);
-                    continue;
-                }
                 const int j = __ffs(em) - 1;
                 settled |= (j == 31) ? FULL : ((2u << j) - 1u);
-                if (lane == j) {
-                    (g.pp ? ad1 : ad)[0] = sdec;
-                    (g.pp ? ai1 : ai)[0] = v;
+                const unsigned long long kj = __shfl_sync(FULL, mykey, j);
+                const int p = __popc(__ballot_sync(FULL, lane < m && E < kj));
+                const unsigned long long up = __shfl_up_sync(FULL, E, 1);
+                if (lane == p) E = kj;
+                else if (lane > p && lane <= m) E = up;
+                ++m;
+                if (nT + m >= C) {
+                    // the C smallest of T and E: the ts smallest of E and the
+                    // C - ts smallest of T, ts the largest t <= min(m, C) with
+                    // E[t-1] below T[C-t] (or T shorter than C - t + 1)
+                    const int t = lane + 1, hi_t = m < C ? m : C;
+                    const bool P = t <= hi_t && (C - t >= nT || E < dkey(Td[C - t], Ti[C - t]));
+                    const int ts = __popc(__ballot_sync(FULL, P));
+                    const unsigned long long ea = __shfl_sync(FULL, E, ts > 0 ? ts - 1 : 0);
+                    const unsigned long long k1 = ts > 0 ? ea : 0ull;
+                    const unsigned long long k2 =
+                        C - ts - 1 >= 0 ? dkey(Td[C - ts - 1], Ti[C - ts - 1]) : 0ull;
+                    thk = k1 > k2 ? k1 : k2;
+                }
+                if (lane > j) mythk = thk;
+            }
+            // every vertex's own outcome, against the threshold of its turn
+            if (fresh)
+                decide(mythk == ~0ull ? INFINITY : __uint_as_float((unsigned)(mythk >> 32)));
+            // the entered keys join T (a bounded set fed one at a time ends
+            // as the smallest of all it was offered)
+            if (m > 0) {
+                float *sd_ = g.pp ? ad1 : ad;
+                int *si_ = g.pp ? ai1 : ai;
+                if (lane < m) {
+                    sd_[lane] = __uint_as_float((unsigned)(E >> 32));
+                    si_[lane] = (int)(E & 0xffffffffu);
                 }
                 __syncwarp();
                 if (!g.pp) {
-                    nR = warp_merge(rd, ri, rx, nR, ad, ai, 1, nd, ni, nx, g.ef, lane);
+                    nR = warp_merge(rd, ri, rx, nR, ad, ai, m, nd, ni, nx, g.ef, lane);
                     float *tf = rd; rd = nd; nd = tf;
                     int *ti = ri; ri = ni; ni = ti;
                     ti = rx; rx = nx; nx = ti;
-                    th = nR == g.ef ? rd[nR - 1] : INFINITY;
                 } else {
-                    n1 = warp_merge(kd, ki, nullptr, n1, ad1, ai1, 1, kd2, ki2, nullptr, g.K, lane);
+                    n1 = warp_merge(kd, ki, nullptr, n1, ad1, ai1, m, kd2, ki2, nullptr, g.K, lane);
                     float *tf = kd; kd = kd2; kd2 = tf;
                     int *ti = ki; ki = ki2; ki2 = ti;
-                    th = n1 == g.K ? kd[n1 - 1] : INFINITY;
                 }
-                if (fresh && lane > j) decide(th);
             }
             if (fresh) dims += (unsigned long long)dstep;
             if (g.pp) {
