@@ -328,6 +328,36 @@ int adsx_stream_status(const adsx_index *index, void *stream);
 int adsx_set_scan_schedule(adsx_index *index, int32_t schedule, int32_t queries_per_item,
                            int32_t tiles_per_item);
 
+/* Query rotation modes (adsx_set_query_rotation). */
+#define ADSX_ROT_FP32 0      /* compensated FP32 dot products (Dot2)                */
+#define ADSX_ROT_TENSOR 1    /* tcgen05 tensor cores, exact digit products           */
+
+/*
+ * adsx_set_query_rotation -- how searches on this index rotate their queries,
+ * q' = P q (Sec. 3.1).  ADSX_ROT_TENSOR, available on every index with a
+ * dense P and a padded D of at most 1024: every query value and every
+ * entry of P is split into T signed integer digits of b bits (with a power
+ * of two per row; bT >= 28), the digit products are summed on the tensor
+ * cores (tcgen05.mma kind::tf32), where every partial sum of a level is an
+ * integer held exactly in FP32 (T Dp (2^b - 1)^2 < 2^24), and the levels
+ * are added by compensated summation (as if in twice the precision) and
+ * rounded once to FP32: q' is the FP64 product of the
+ * FP32 inputs, rounded to FP32, up to the digits' truncated tails (below
+ * 2^(-bT) of each row's largest value) -- the error-free splitting of
+ * Ozaki, Ogita, Oishi and Rump (2012).  ADSX_ROT_FP32: compensated FP32 dot
+ * products on the CUDA cores, as accurate as twice the working precision:
+ * the initial mode, measured faster on GB300 for query batches (0.21 vs
+ * 0.27 ms for 10k queries at D = 128, 0.47 vs 0.79 ms for 1000 at D = 960)
+ * and the only one for D > 1024 (Kac-walk indexes use their walk).  The digits
+ * of P take (about half of T^2) Dp^2 floats of device memory per index
+ * (122 MB at D = 960), a search (units + T) Dp floats of scratch per query
+ * (units, the work units of one output tile: 5 to 6 for D <= 128, 19 for
+ * D = 960; T = 4 to 6).  Returns ADSX_EINVAL for an
+ * unknown mode or ADSX_ROT_TENSOR where it is not available.  Not
+ * thread-safe with other calls on the same index.
+ */
+int adsx_set_query_rotation(adsx_index *index, int32_t mode);
+
 /*
  * adsx_scan_config -- the index's current scan settings: the step delta_d
  * used when a search passes 0, the schedule, queries (0: chosen per batch)
@@ -399,8 +429,12 @@ int adsx_scan_kernel_ms(const adsx_index *index, float *ms, int32_t *launches);
  *     from one fixed array of ADSX_NOALLOC_SCRATCH_BYTES that the library
  *     holds on every GPU that loads it, until the process exits.  A call
  *     whose temporaries would not fit (roughly nq * (4*D + 4*nlist +
- *     4*nprobe) bytes, plus partial top-K lists when nq is small) returns
- *     ADSX_EINVAL with the size it needed; split the batch.
+ *     4*nprobe) bytes -- with the tensor-core query rotation the 4*nlist
+ *     part is at least the rotation's digits and partial sums of
+ *     min(nq, 1024) queries, 4 * (units + T) * Dp each (see
+ *     adsx_set_query_rotation) --
+ *     plus partial top-K lists when nq is small) returns ADSX_EINVAL with the
+ *     size it needed; split the batch.
  *   - The first call on each device looks up the array's device address on
  *     that device and keeps it; make that first call before any stream
  *     capture.  The address belongs to the device's primary context: after

@@ -80,6 +80,7 @@ def load():
     lib.adsx_server_destroy.argtypes = [V]
     lib.adsx_set_stage_timing.argtypes = [V, i32]
     lib.adsx_set_scan_schedule.argtypes = [V, i32, i32, i32]
+    lib.adsx_set_query_rotation.argtypes = [V, i32]
     lib.adsx_scan_config.argtypes = [V, V, V, V, V, V]
     lib.adsx_stage_ms.argtypes = [V, V]
     lib.adsx_scan_kernel_ms.argtypes = [V, V, V]
@@ -91,6 +92,7 @@ def load():
                "adsx_probe", "adsx_rotate", "adsx_dco_fixed_r", "adsx_stream_status",
                "adsx_set_stage_timing", "adsx_stage_ms", "adsx_search_noalloc",
                "adsx_set_scan_schedule", "adsx_scan_config", "adsx_scan_kernel_ms",
+               "adsx_set_query_rotation",
                "adsx_search_batched", "adsx_search_pdscan", "adsx_autotune",
                "adsx_server_create",
                "adsx_server_submit", "adsx_server_submit_many", "adsx_server_wait",
@@ -195,6 +197,9 @@ class Index:
 
     def set_scan_schedule(self, schedule, queries_per_item=0, tiles_per_item=0):
         return set_scan_schedule(self, schedule, queries_per_item, tiles_per_item)
+
+    def set_query_rotation(self, mode):
+        return set_query_rotation(self, mode)
 
 
 def build_index(X, P, centroids, assign, storage=F32, stream=None, metric=L2) -> Index:
@@ -491,6 +496,15 @@ def set_scan_schedule(index: Index, schedule: int, queries_per_item: int = 0,
     batch) and tiles_per_item 1..64 (0 keeps the current value)."""
     _check(load().adsx_set_scan_schedule(index.handle, int(schedule), int(queries_per_item),
                                          int(tiles_per_item)))
+
+
+ROT_FP32, ROT_TENSOR = 0, 1
+
+
+def set_query_rotation(index: Index, mode: int):
+    """adsx_set_query_rotation: ROT_TENSOR (tensor cores, exact digit
+    products) or ROT_FP32 (compensated FP32 dot products, the default)."""
+    _check(load().adsx_set_query_rotation(index.handle, int(mode)))
 
 
 def scan_config(index: Index):

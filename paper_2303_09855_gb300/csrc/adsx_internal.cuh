@@ -66,6 +66,15 @@ struct Index {
     int32_t max_tiles = 0;        // tiles of the largest cluster
     int32_t cm_r0 = 1;
     int32_t cm_growth = 4;
+    // query rotation on the tensor cores (rot_tc, adsx_set_query_rotation):
+    // P's rows split into rot_T integer slices of rot_b bits (rot_F: each
+    // row's exponent), laid out per level L = 2..T+1 at rot_B + rot_boff[L]
+    // as Dp x (L - 1) Dp matrices; rot_ok when they exist
+    bool rot_ok = false, rot_tc = false;
+    int32_t rot_b = 0, rot_T = 0, rot_Lmax = 0;
+    float *rot_B = nullptr;
+    int32_t *rot_F = nullptr;
+    int64_t rot_boff[16] = {};
     // stage timing (adsx_set_stage_timing): events between search stages
     bool timing = false;
     bool timed_once = false;
@@ -266,6 +275,17 @@ cudaError_t launch_tc_gemm(const float *A, int64_t M, int lda, const float *B, i
                            int Kd, float *C, int ldc, int Nout, const float *an, const float *bn,
                            unsigned *err, cudaStream_t s);
 cudaError_t launch_row_sqnorm(const float *X, int64_t M, int ld, int K, float *out, cudaStream_t s);
+
+// Query rotation Y = X P^T on the tensor cores, FP32-accurate (gemm_tc.cu):
+// digit width b, digits T and kept levels for a padded dimension Dp (T = 0:
+// not available, Dp > 1024); the partial-sum scratch (floats) that lets a
+// batch of nq rows run in one pass of up to 1024 rows; and the rotation
+// itself (part: part_floats of scratch, at least one row's worth; xexp: nq
+// ints).
+void tc_rot_params(int Dp, int *b, int *T, int *Lmax);
+int64_t tc_rot_scratch_floats(const Index *ix, int64_t nq);
+cudaError_t rotate_queries_tc(const Index *ix, const float *X, int64_t nq, float *Y, float *part,
+                              int64_t part_floats, int32_t *xexp, cudaStream_t s);
 
 // Rotation Y = X P^T (N x D times D x D, P row stride ldp) with compensated
 // (Dot2) FP32 dot products, written as N x Dp FP32 (columns >= D are 0).

@@ -132,10 +132,22 @@ int check_index(const Index *ix)
 }
 
 // q' = P q for nq raw queries into a Dp-strided buffer (zero padded dims).
+// Query rotation q' = P q (Sec. 3.1): on the tensor cores, exactly up to the
+// final rounding, when the index has P's digits and that mode is on
+// (adsx_set_query_rotation); else the compensated FP32 (or Kac) rotation.
 cudaError_t rotate_queries(const Index *ix, const float *q_dev, int64_t nq, float *qrot,
-                           cudaStream_t s)
+                           Scratch &sc)
 {
-    return adsx::rotate_rows(ix, q_dev, nq, qrot, s);
+    if (ix->rot_tc && nq > 0) {
+        float *part = nullptr;
+        int32_t *xexp = nullptr;
+        const int64_t pf = adsx::tc_rot_scratch_floats(ix, nq);
+        cudaError_t e = sc.get(&part, (size_t)pf);
+        if (e == cudaSuccess) e = sc.get(&xexp, (size_t)nq);
+        if (e != cudaSuccess) return e;
+        return adsx::rotate_queries_tc(ix, q_dev, nq, qrot, part, pf, xexp, sc.s);
+    }
+    return adsx::rotate_rows(ix, q_dev, nq, qrot, sc.s);
 }
 
 // ||q'-c'||^2 for every (query, centroid) as ||q'||^2 + ||c'||^2 - 2 q'.c'.
@@ -227,6 +239,54 @@ extern "C" {
 const char *adsx_last_error(void) { return g_last_error.c_str(); }
 
 // The rotation is either a dense P (kac_L = 0) or a layered Kac walk.
+// The P side of the tensor-core query rotation (gemm_tc.cu): every row c of
+// P split into T signed b-bit digits of V = trunc(P[c][k] 2^(bT - F_c)) (F_c
+// the exponent of the row's largest |P[c][k]|), laid out per level
+// L = 2..Lmax as a Dp x n_L Dp matrix whose row c holds, in block j, digit
+// L - t of the row for t = max(1, L - T) + j (n_L = the level's digit pairs).
+// Host code, once per index.
+static void rot_slices_host(const float *P, int D, int Dp, int b, int T, int Lmax,
+                            std::vector<float> &B, std::vector<int32_t> &F, int64_t *boff)
+{
+    const long long mask = (1ll << b) - 1;
+    std::vector<int32_t> dig((size_t)T * Dp * Dp, 0);
+    F.assign((size_t)Dp, 0);
+    for (int c = 0; c < D; ++c) {
+        double m = 0.0;
+        for (int k = 0; k < D; ++k) m = std::max(m, fabs((double)P[(size_t)c * D + k]));
+        int E = 0;
+        if (m > 0.0) frexp(m, &E);
+        F[c] = E;
+        for (int k = 0; k < D; ++k) {
+            const long long V = (long long)trunc(ldexp((double)P[(size_t)c * D + k], b * T - E));
+            const long long av = V < 0 ? -V : V;
+            for (int u = 1; u <= T; ++u) {
+                const long long d = (av >> (b * (T - u))) & mask;
+                dig[((size_t)(u - 1) * Dp + c) * Dp + k] = (int32_t)(V < 0 ? -d : d);
+            }
+        }
+    }
+    int64_t total = 0;
+    for (int L = 0; L < 16; ++L) boff[L] = 0;
+    for (int L = 2; L <= Lmax; ++L) {
+        const int lo = std::max(1, L - T), hi = std::min(T, L - 1);
+        boff[L] = total;
+        total += (int64_t)(hi - lo + 1) * Dp * Dp;
+    }
+    B.assign((size_t)total, 0.f);
+    for (int L = 2; L <= Lmax; ++L) {
+        const int lo = std::max(1, L - T), hi = std::min(T, L - 1);
+        const int64_t ld = (int64_t)(hi - lo + 1) * Dp;
+        for (int c = 0; c < Dp; ++c)
+            for (int t = lo; t <= hi; ++t) {
+                const int u = L - t;
+                for (int k = 0; k < Dp; ++k)
+                    B[(size_t)(boff[L] + c * ld + (int64_t)(t - lo) * Dp + k)] =
+                        (float)dig[((size_t)(u - 1) * Dp + c) * Dp + k];
+            }
+    }
+}
+
 static int build_impl(const float *X, int64_t N, int32_t D, const float *P,
                       const int32_t *kac_pairs, const float *kac_cs, int32_t kac_L,
                       const float *centroids, int32_t nlist, const int32_t *assign,
@@ -387,6 +447,27 @@ static int build_impl(const float *X, int64_t N, int32_t D, const float *P,
             if (!(worst <= 1e-4))
                 return cleanup(fail(ADSX_EINVAL, "P is not orthogonal (max|P P^T - I| = %g)", worst));
         }
+        // the digits of P for the tensor-core query rotation (Dp <= 1024)
+        int rb = 0, rT = 0, rL = 0;
+        adsx::tc_rot_params(Dp, &rb, &rT, &rL);
+        if (rT > 0) {
+            std::vector<float> RB;
+            std::vector<int32_t> RF;
+            rot_slices_host(P, D, Dp, rb, rT, rL, RB, RF, ix->rot_boff);
+            BCK(dalloc((void **)&ix->rot_B, sizeof(float) * RB.size()), "alloc rotation digits");
+            BCK(dalloc((void **)&ix->rot_F, sizeof(int32_t) * RF.size()), "alloc rotation digits");
+            BCK(cudaMemcpyAsync(ix->rot_B, RB.data(), sizeof(float) * RB.size(), cudaMemcpyHostToDevice, s),
+                "copy rotation digits");
+            BCK(cudaMemcpyAsync(ix->rot_F, RF.data(), sizeof(int32_t) * RF.size(), cudaMemcpyHostToDevice, s),
+                "copy rotation digits");
+            BCK(cudaStreamSynchronize(s), "sync");
+            ix->rot_b = rb;
+            ix->rot_T = rT;
+            ix->rot_Lmax = rL;
+            // available; the compensated FP32 rotation stays the initial
+            // mode (measured faster at these shapes)
+            ix->rot_ok = true;
+        }
     }
     BCK(cudaMemcpyAsync(ix->ids, ids.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, s), "copy ids");
     BCK(cudaMemcpyAsync(ix->off, off.data(), sizeof(int64_t) * (nlist + 1), cudaMemcpyHostToDevice, s), "copy off");
@@ -494,6 +575,8 @@ int adsx_free_index(adsx_index *index)
     cudaFree(ix->onorm);
     cudaFree(ix->kac_pairs);
     cudaFree(ix->kac_cs);
+    cudaFree(ix->rot_B);
+    cudaFree(ix->rot_F);
     cudaFree(ix->ids);
     cudaFree(ix->off);
     cudaFree(ix->tile_off);
@@ -533,7 +616,7 @@ int adsx_rotate(const adsx_index *index, const float *Qv, int64_t nq, float *out
     CK(stage_in(sc, Qv, (size_t)nq * ix->D, q), "stage queries");
     CK(stage_out(sc, out, (size_t)nq * ix->D, o), "stage output");
     CK(sc.get(&qrot, (size_t)nq * ix->Dp), "alloc q'");
-    CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
+    CK(rotate_queries(ix, q.dev, nq, qrot, sc), "rotate");
     CK(cudaMemcpy2DAsync(o.dev, sizeof(float) * ix->D, qrot, sizeof(float) * ix->Dp,
                          sizeof(float) * ix->D, (size_t)nq, cudaMemcpyDeviceToDevice, s), "copy q'");
     CK(copy_back(o, s), "copy back");
@@ -559,7 +642,7 @@ int adsx_probe(const adsx_index *index, const float *Qv, int64_t nq, int32_t npr
     CK(stage_out(sc, probes, (size_t)nq * nprobe, pr), "stage probes");
     CK(stage_out(sc, probe_d2, (size_t)nq * nprobe, pd), "stage probe distances");
     CK(sc.get(&qrot, (size_t)nq * ix->Dp), "alloc q'");
-    CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
+    CK(rotate_queries(ix, q.dev, nq, qrot, sc), "rotate");
     CK(queries_before_probe(ix, qrot, nq, s), "normalise queries");
     CK(probe_queries(ix, qrot, nq, nprobe, pr.dev, pd.dev, sc), "probe");
     CK(copy_back(pr, s), "copy back");
@@ -856,7 +939,7 @@ static int search_impl(const adsx_index *index, const float *Qv, int64_t nq, int
     CK(sc.get(&qrot, (size_t)nq * ix->Dp), "alloc q'");
     CK(sc.get(&probes, (size_t)nq * nprobe), "alloc probes");
     CK(mark(ix, 0, s), "event");
-    CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
+    CK(rotate_queries(ix, q.dev, nq, qrot, sc), "rotate");
     CK(mark(ix, 1, s), "event");
     CK(queries_before_probe(ix, qrot, nq, s), "normalise queries");
     CK(probe_queries(ix, qrot, nq, nprobe, probes, nullptr, sc), "probe");
@@ -972,7 +1055,7 @@ int adsx_search_batched(const adsx_index *index, const float *Qv, int64_t nq, co
     CK(sc.get(&out_off, (size_t)nq), "alloc offsets");
     CK(sc.get(&counter, 1), "alloc counter");
     CK(mark(ix, 0, s), "event");
-    CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
+    CK(rotate_queries(ix, q.dev, nq, qrot, sc), "rotate");
     CK(mark(ix, 1, s), "event");
     CK(queries_before_probe(ix, qrot, nq, s), "normalise queries");
     {
@@ -1090,7 +1173,7 @@ int adsx_dco_fixed_r(const adsx_index *index, const float *Qv, int64_t nq, const
     CK(stage_out(sc, dims, (size_t)nq * ix->N, dm), "stage dims");
     CK(sc.get(&qrot, (size_t)nq * ix->Dp), "alloc q'");
     CK(sc.get(&counter, 1), "alloc counter");
-    CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
+    CK(rotate_queries(ix, q.dev, nq, qrot, sc), "rotate");
     // The search's own scan kernel in its fixed-threshold mode: every
     // cluster is a probe slot, r^2 stays r2[q], no KNN set.
     adsx::ScanArgs a;
@@ -1286,6 +1369,19 @@ int adsx_set_scan_schedule(adsx_index *index, int32_t schedule, int32_t queries_
     ix->sched = schedule;
     if (queries_per_item) ix->cm_G = queries_per_item < 0 ? 0 : queries_per_item;
     if (tiles_per_item) ix->cm_tpi = tiles_per_item;
+    return ADSX_OK;
+}
+
+int adsx_set_query_rotation(adsx_index *index, int32_t mode)
+{
+    Index *ix = reinterpret_cast<Index *>(index);
+    int rc = check_index(ix);
+    if (rc) return rc;
+    if (mode != ADSX_ROT_FP32 && mode != ADSX_ROT_TENSOR)
+        return fail(ADSX_EINVAL, "unknown query rotation mode %d", mode);
+    if (mode == ADSX_ROT_TENSOR && !ix->rot_ok)
+        return fail(ADSX_EINVAL, "tensor-core rotation needs a dense P and a padded D <= 1024");
+    ix->rot_tc = mode == ADSX_ROT_TENSOR;
     return ADSX_OK;
 }
 
@@ -1578,7 +1674,7 @@ int adsx_search_graph(const adsx_index *index, const adsx_graph *graph, const fl
     CK(sc.get(&qrot, (size_t)nq * ix->Dp), "alloc q'");
     CK(sc.get(&probes, (size_t)nq * n_entry), "alloc probes");
     CK(sc.get(&ftab, (size_t)nblk + 1), "alloc test factors");
-    CK(rotate_queries(ix, q.dev, nq, qrot, s), "rotate");
+    CK(rotate_queries(ix, q.dev, nq, qrot, sc), "rotate");
     CK(queries_before_probe(ix, qrot, nq, s), "normalise queries");
     CK(probe_queries(ix, qrot, nq, n_entry, probes, nullptr, sc), "entry clusters");
     adsx::GraphArgs a;

@@ -327,4 +327,372 @@ cudaError_t launch_row_sqnorm(const float *X, int64_t M, int ld, int K, float *o
     return cudaGetLastError();
 }
 
+namespace {
+
+// ---- query rotation Y = X P^T on the tensor cores, FP32-accurate.
+//
+// Each value x of a row becomes the integer V = trunc(x 2^(bT - E)), E the
+// exponent of the row's largest |x| (so |V| < 2^(bT)), and V is written as T
+// signed digits of b bits, s_1 (most significant) .. s_T:
+// x = sum_t s_t 2^(E - bt) up to the truncated remainder (below 2^(E - bT)).
+// P's rows are split the same way once, at index build (digits p_u,
+// exponents F).  Then
+//   (X P^T)[r][c] = 2^(E_r + F_c) sum_L 2^(-bL) sum_{t + u = L} sum_k s_t[r][k] p_u[c][k],
+// and each inner sum adds products of integers below 2^b in magnitude: with
+// T Dp (2^b - 1)^2 < 2^24 every partial sum of a level is an integer an FP32
+// accumulator holds exactly, in whatever order the tensor core adds.  The
+// digit pairs of one level L are laid side by side along K (digits t of X
+// against digits L - t of P), so one exact accumulation serves a level.
+// Levels 2..Lmax are kept, Lmax chosen so that the others weigh below
+// 2^(-bT) of the row and column scales (bT >= 28); each level is split along
+// K into work units for parallelism.  The units' exact sums, each times its
+// level's power of two (still exact in FP32), are added by compensated
+// summation and the total is scaled by 2^(E_r + F_c).  The
+// approach is the error-free splitting of matrix products of Ozaki, Ogita,
+// Oishi and Rump (Numer. Algorithms, 2012), with one digit width.
+constexpr int ROT_MAX_UNITS = 64;
+constexpr int ROT_MAX_LEVEL = 16;
+
+struct TcRot {
+    const float *dig;          // M x T x Dp digits of X (rot_digits_kernel)
+    int64_t M;
+    int D, Dp;
+    const int32_t *xexp;
+    int b, T;
+    const float *B;
+    int64_t boff[ROT_MAX_LEVEL];
+    int nz;
+    int zL[ROT_MAX_UNITS], zk0[ROT_MAX_UNITS], zk1[ROT_MAX_UNITS];
+    float *part;
+    unsigned *err;
+};
+
+// Work units of the levels 2..Lmax (K' of level L: its digit pairs times Dp);
+// returns their number (at most 24 units, by the K' per unit).
+int rot_plan(int Dp, int T, int Lmax, TcRot &r)
+{
+    for (int kc = 512;; kc *= 2) {
+        int n = 0;
+        bool over = false;
+        for (int L = 2; L <= Lmax && !over; ++L) {
+            const int lo = L - T > 1 ? L - T : 1, hi = L - 1 < T ? L - 1 : T;
+            const int kl = (hi - lo + 1) * Dp;
+            for (int k0 = 0; k0 < kl; k0 += kc) {
+                if (n >= ROT_MAX_UNITS) {
+                    over = true;
+                    break;
+                }
+                r.zL[n] = L;
+                r.zk0[n] = k0;
+                r.zk1[n] = k0 + kc < kl ? k0 + kc : kl;
+                ++n;
+            }
+        }
+        if (!over && n <= 24) {
+            r.nz = n;
+            return n;
+        }
+        if (kc > (1 << 20)) return -1;
+    }
+}
+
+// Per row (one warp): E, the exponent of its largest |x| (x = m 2^E, m in
+// [0.5, 1); 0 for a zero row), and its T digits, dig[r][(t - 1) Dp + k]
+// (FP32 values of small integers; 0 for k >= D).
+__global__ void rot_digits_kernel(const float *__restrict__ X, int64_t M, int D, int Dp, int b,
+                                  int T, int32_t *__restrict__ xexp, float *__restrict__ dig)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long mask = (1ull << b) - 1ull;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < M;
+         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        float m = 0.f;
+        for (int k = lane; k < D; k += 32) m = fmaxf(m, fabsf(X[r * D + k]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        int E = 0;
+        if (m > 0.f) frexpf(m, &E);
+        if (lane == 0) xexp[r] = E;
+        const int sh = b * T - E;
+        // 2^sh as two exact factors (sh may exceed the FP32 exponent range)
+        const float s1 = ldexpf(1.f, sh < 127 ? sh : 127), s2 = ldexpf(1.f, sh > 127 ? sh - 127 : 0);
+        float *dr = dig + r * (int64_t)T * Dp;
+        for (int k = lane; k < Dp; k += 32) {
+            // |V| < 2^(bT) <= 2^32: 64-bit
+            const long long V = k < D ? __float2ll_rz((X[r * D + k] * s1) * s2) : 0ll;
+            const unsigned long long av = (unsigned long long)(V < 0 ? -V : V);
+            for (int t = 1; t <= T; ++t) {
+                const int d = (int)((av >> (b * (T - t))) & mask);
+                dr[(int64_t)(t - 1) * Dp + k] = (float)(V < 0 ? -d : d);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool full)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(full ? 16 : 0)
+                 : "memory");
+}
+
+// One work unit (blockIdx.z: a level L and a K' range) of a 128 x 128 output
+// tile: the digits t of X (K' block j holds digit max(1, L - T) + j, read
+// from the precomputed digits) against digits L - t of P, one tcgen05.mma
+// (kind::tf32; the digits are small integers, exact in TF32) per 8-wide K
+// slab, with the exact partial sums written to part[z].  Operands reach
+// shared memory by cp.async in a ROT_STAGES-deep ring, so the copies of the
+// next k-steps overlap the MMAs of the current one.
+constexpr int ROT_STAGES = 3;
+constexpr int ROT_STAGE_BYTES = 2 * OPER;                 // A and B of one 32-wide k-step
+constexpr int ROT_SMEM = ROT_STAGES * ROT_STAGE_BYTES > STAGE_BYTES ? ROT_STAGES * ROT_STAGE_BYTES
+                                                                    : STAGE_BYTES;
+
+__global__ void __launch_bounds__(128, 1) tc_rot_kernel(TcRot r)
+{
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ __align__(8) uint64_t mbar[ROT_STAGES];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t m0 = (int64_t)blockIdx.x * TM;
+    const int n0 = blockIdx.y * TN;
+    const int z = blockIdx.z;
+    const int L = r.zL[z], kb = r.zk0[z], ke = r.zk1[z];
+    const int tlo = L - r.T > 1 ? L - r.T : 1, thi = L - 1 < r.T ? L - 1 : r.T;
+    const int ldb = (thi - tlo + 1) * r.Dp;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :
+                     : "r"(smem_addr(&tmem_slot)), "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < ROT_STAGES; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" : : "r"(smem_addr(&mbar[i])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    // A k-step moves 128 rows x 32 values of A (digits of queries m0..) and
+    // of B (the level's digits of P rows n0..) as 16-byte chunks: chunk
+    // c = tid + 128 j is row c / 8, values 4 (c % 8) .. +3, so the lanes of a
+    // warp read 4 rows x 128 contiguous bytes per instruction.
+    const int rsub = tid >> 3, csub = tid & 7;
+    const float *asrc = r.dig + (int64_t)(tlo - 1) * r.Dp;
+    const float *bsrc = r.B + r.boff[L];
+    const int64_t astride = (int64_t)r.T * r.Dp;
+    const int nsteps = (ke - kb + BK - 1) / BK;
+    auto issue = [&](int step) {
+        if (step < nsteps) {
+            const int k = kb + step * BK + 4 * csub;      // K' ends on a multiple of 16
+            const bool in = k < ke;
+            uint8_t *Ab = sm + (step % ROT_STAGES) * ROT_STAGE_BYTES, *Bb = Ab + OPER;
+            const uint32_t co = (uint32_t)(csub >> 1) * SLAB;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int row = rsub + 16 * j;
+                const uint32_t o = co + slab_off(row, (4 * csub) & 7);
+                const int64_t ar = m0 + row;
+                const bool av = in && ar < r.M, bv = in && n0 + row < r.Dp;
+                cp_async16(smem_addr(Ab + o), asrc + (av ? ar * astride + k : 0), av);
+                cp_async16(smem_addr(Bb + o), bsrc + (bv ? (int64_t)(n0 + row) * ldb + k : 0), bv);
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    for (int i = 0; i < ROT_STAGES - 1; ++i) issue(i);
+
+    uint32_t phases = 0;                                  // bit b: phase of mbar[b]
+    int last = 0;                                         // buffer of the last commit
+    bool ok = true;
+    for (int i = 0; i < nsteps && ok; ++i) {
+        asm volatile("cp.async.wait_group %0;" ::"n"(ROT_STAGES - 2) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        const int buf = i % ROT_STAGES;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint8_t *Ab = sm + buf * ROT_STAGE_BYTES, *Bb = Ab + OPER;
+#pragma unroll
+            for (int s = 0; s < BK / 8; ++s)
+                mma_tf32(tmem, make_desc(smem_addr(Ab + s * SLAB)), make_desc(smem_addr(Bb + s * SLAB)),
+                         (i > 0 || s > 0) ? 1u : 0u);
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                :
+                : "r"(smem_addr(&mbar[buf]))
+                : "memory");
+        }
+        last = buf;
+        // the buffer of step i - 1 is refilled with step i + ROT_STAGES - 1
+        // once its MMAs are done
+        if (i > 0) {
+            const int pb = (i - 1) % ROT_STAGES;
+            ok = __syncthreads_and(mbar_wait(smem_addr(&mbar[pb]), (phases >> pb) & 1u));
+            if (ok) phases ^= 1u << pb;
+        }
+        if (ok) issue(i + ROT_STAGES - 1);
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (ok) {
+        // the last step's MMAs
+        ok = __syncthreads_and(mbar_wait(smem_addr(&mbar[last]), (phases >> last) & 1u));
+        if (ok) phases ^= 1u << last;
+    }
+    if (!ok) {
+        // as in tc_gemm_kernel: flag, then wait (bounded by time) for the
+        // last committed batch -- MMAs complete in order, so every earlier
+        // one is done when it is -- before tensor memory is released
+        if (tid == 0) atomicOr(r.err, ERR_MMA_TIMEOUT);
+        const bool drained = mbar_wait_ns(smem_addr(&mbar[last]), (phases >> last) & 1u, DRAIN_NS);
+        if (!__syncthreads_and(drained) && tid == 0) atomicOr(r.err, ERR_MMA_DRAIN);
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // each warp stages its 32 accumulator rows, then writes them row by
+        // row as coalesced runs
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        float *stage = reinterpret_cast<float *>(sm) + warp * 32 * (TN + 4);
+#pragma unroll 1
+        for (int c0 = 0; c0 < TN; c0 += 16) {
+            uint32_t v[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+                "%12,%13,%14,%15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                  "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                  "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(trow + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+                *reinterpret_cast<float4 *>(stage + lane * (TN + 4) + c0 + j) =
+                    make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                                __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+        }
+        __syncwarp();
+        float *pz = r.part + (int64_t)z * r.M * r.Dp;
+        for (int rr = 0; rr < 32; ++rr) {
+            const int64_t grow = m0 + warp * 32 + rr;
+            if (grow >= r.M) break;
+            for (int c = lane; c < TN; c += 32)
+                if (n0 + c < r.Dp) pz[grow * r.Dp + n0 + c] = stage[rr * (TN + 4) + c];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     :
+                     : "r"(tmem), "r"(TMEM_COLS)
+                     : "memory");
+}
+
+// Y[r][c] = 2^(E_r + F_c) sum_z part[z][r][c] 2^(-b L_z).  Each term is an
+// integer below 2^24 times a power of two, so exact in FP32; the terms are
+// added by Sum2 (TwoSum on the running sum, the errors added apart: as
+// accurate as twice the working precision, Ogita, Rump and Oishi 2005), the
+// two parts added and the total scaled by 2^(E_r + F_c) (0 for c >= D).
+__global__ void rot_combine_kernel(TcRot r, const int32_t *__restrict__ fexp, float *__restrict__ Y)
+{
+    const int64_t total = r.M * r.Dp;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / r.Dp;
+        const int c = (int)(i - row * r.Dp);
+        float hi = 0.f, lo = 0.f;
+        for (int z = 0; z < r.nz; ++z) {
+            const float v = ldexpf(r.part[(int64_t)z * total + i], -r.b * r.zL[z]);
+            const float sum = hi + v, zz = sum - hi;
+            lo += (hi - (sum - zz)) + (v - zz);
+            hi = sum;
+        }
+        Y[i] = c < r.D ? ldexpf(hi + lo, r.xexp[row] + fexp[c]) : 0.f;
+    }
+}
+
+}  // namespace
+
+void tc_rot_params(int Dp, int *b, int *T, int *Lmax)
+{
+    *b = 0;
+    *T = 0;
+    *Lmax = 0;
+    if (Dp > 1024) return;
+    for (int bb = 8; bb >= 3; --bb) {
+        const int tt = (28 + bb - 1) / bb;
+        const int64_t lim = (int64_t)tt * Dp * ((1ll << bb) - 1) * ((1ll << bb) - 1);
+        if (lim < (1ll << 24)) {
+            // dropped levels weigh at most T Dp 2^(2b - b(Lmax + 1)) <= 2^(-bT)
+            int lg = 0;
+            while ((1ll << lg) < (int64_t)tt * Dp) ++lg;
+            int lm = tt + 1 + (lg + bb - 1) / bb;
+            if (lm > 2 * tt) lm = 2 * tt;
+            *b = bb;
+            *T = tt;
+            *Lmax = lm;
+            return;
+        }
+    }
+}
+
+int64_t tc_rot_scratch_floats(const Index *ix, int64_t rows)
+{
+    if (!ix->rot_ok) return 0;
+    TcRot r;
+    const int nz = rot_plan(ix->Dp, ix->rot_T, ix->rot_Lmax, r);
+    return nz > 0 ? (int64_t)(nz + ix->rot_T) * rows * ix->Dp : 0;
+}
+
+cudaError_t rotate_queries_tc(const Index *ix, const float *X, int64_t nq, float *Y, float *part,
+                              int64_t part_floats, int32_t *xexp, cudaStream_t s)
+{
+    if (nq <= 0) return cudaSuccess;
+    if (!ix->rot_ok || (nq + TM - 1) / TM > 0x7fffffffLL) return cudaErrorInvalidValue;
+    TcRot r;
+    r.D = ix->D;
+    r.Dp = ix->Dp;
+    r.b = ix->rot_b;
+    r.T = ix->rot_T;
+    r.B = ix->rot_B;
+    for (int i = 0; i < ROT_MAX_LEVEL; ++i) r.boff[i] = ix->rot_boff[i];
+    r.err = ix->err;
+    const int nz = rot_plan(ix->Dp, ix->rot_T, ix->rot_Lmax, r);
+    if (nz <= 0) return cudaErrorInvalidValue;
+    // rows per pass: as many as the scratch holds (digits and partial sums)
+    const int64_t per_row = (int64_t)(nz + ix->rot_T) * ix->Dp;
+    int64_t chunk = part_floats / per_row;
+    if (chunk < 1) return cudaErrorInvalidValue;
+    if (chunk > TM && chunk < nq) chunk -= chunk % TM;
+    cudaError_t e = cudaFuncSetAttribute(tc_rot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         ROT_SMEM);
+    if (e != cudaSuccess) return e;
+    for (int64_t r0 = 0; r0 < nq; r0 += chunk) {
+        const int64_t m = nq - r0 < chunk ? nq - r0 : chunk;
+        float *dig = part + (int64_t)nz * m * ix->Dp;
+        int64_t blocks = (m * 32 + 255) / 256;
+        if (blocks > 152 * 32) blocks = 152 * 32;
+        rot_digits_kernel<<<(unsigned)blocks, 256, 0, s>>>(X + r0 * ix->D, m, ix->D, ix->Dp, r.b, r.T,
+                                                            xexp + r0, dig);
+        r.dig = dig;
+        r.M = m;
+        r.xexp = xexp + r0;
+        r.part = part;
+        dim3 grid((unsigned)((m + TM - 1) / TM), (unsigned)((ix->Dp + TN - 1) / TN), (unsigned)nz);
+        tc_rot_kernel<<<grid, 128, ROT_SMEM, s>>>(r);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        int64_t cb = (m * ix->Dp + 255) / 256;
+        if (cb > 152 * 32) cb = 152 * 32;
+        rot_combine_kernel<<<(unsigned)cb, 256, 0, s>>>(r, ix->rot_F, Y + r0 * ix->Dp);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace adsx

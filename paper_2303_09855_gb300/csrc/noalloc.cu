@@ -116,8 +116,14 @@ extern "C" int adsx_search_noalloc(const adsx_index *index, const float *Qv, int
 
     // Size check before touching the array.
     auto rup = [](size_t b) { return (std::max<size_t>(b, 1) + 255) & ~size_t(255); };
-    size_t need = rup((size_t)nq * Dp * 4) + rup((size_t)nq * 4) + rup((size_t)nq * ix->nlist * 4) +
-                  rup((size_t)nq * nprobe * 4) + rup((size_t)(nblk + 1) * 4) + rup(4);
+    // the centroid distances share their region with the partial sums of a
+    // tensor-core query rotation (used one after the other)
+    const size_t rot_part =
+        ix->rot_tc ? (size_t)adsx::tc_rot_scratch_floats(ix, std::min<int64_t>(nq, 1024)) * 4 : 0;
+    const size_t dist_bytes = std::max<size_t>((size_t)nq * ix->nlist * 4, rot_part);
+    size_t need = rup((size_t)nq * Dp * 4) + rup((size_t)nq * 4) + rup(dist_bytes) +
+                  rup((size_t)nq * nprobe * 4) + rup((size_t)(nblk + 1) * 4) + rup(4) +
+                  (ix->rot_tc ? rup((size_t)nq * 4) : 0);
     if (a.S > 1) need += rup((size_t)nq * 4) + 2 * rup((size_t)a.n_items * K * 4);
     if (need > (size_t)ADSX_NOALLOC_SCRATCH_BYTES)
         return nerr(ADSX_EINVAL, "adsx_search_noalloc: this call needs " + std::to_string(need) +
@@ -131,7 +137,7 @@ extern "C" int adsx_search_noalloc(const adsx_index *index, const float *Qv, int
     Carver cv{base};
     float *qrot = cv.take<float>((size_t)nq * Dp);
     float *qn = cv.take<float>((size_t)nq);
-    float *dist = cv.take<float>((size_t)nq * ix->nlist);
+    float *dist = cv.take<float>(dist_bytes / 4);
     int32_t *probes = cv.take<int32_t>((size_t)nq * nprobe);
     float *ftab = cv.take<float>((size_t)nblk + 1);
     unsigned *counter = cv.take<unsigned>(1);
@@ -154,8 +160,13 @@ extern "C" int adsx_search_noalloc(const adsx_index *index, const float *Qv, int
         if (e != cudaSuccess) return nerr(ADSX_ECUDA, cudaGetErrorString(e));
     }
     e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
-    if (e == cudaSuccess)
-        e = adsx::rotate_rows(ix, Qv, nq, qrot, s);
+    if (e == cudaSuccess) {
+        if (ix->rot_tc)
+            e = adsx::rotate_queries_tc(ix, Qv, nq, qrot, dist, (int64_t)(dist_bytes / 4),
+                                        cv.take<int32_t>((size_t)nq), s);
+        else
+            e = adsx::rotate_rows(ix, Qv, nq, qrot, s);
+    }
     if (e == cudaSuccess) e = adsx::launch_row_sqnorm(qrot, nq, Dp, Dp, qn, s);
     if (e == cudaSuccess)
         e = adsx::launch_tc_gemm(qrot, nq, Dp, ix->cents, ix->nlist, Dp, Dp, dist, ix->nlist,

@@ -74,6 +74,29 @@ def test_noalloc_matches_search_on_two_calls_in_a_row(setup, reps, K, nprobe, ep
         assert np.array_equal(dims, ref_dims)
 
 
+def test_noalloc_with_tensor_core_rotation(setup):
+    """With the index's query rotation on the tensor cores, the no-alloc call
+    rotates with the same digits, their partial sums kept in the fixed array
+    (in the space of the centroid distances): the same results as
+    adsx_search, on two calls in a row, for 100 and 8000 queries."""
+    adsx, torch, wl, ix = setup
+    ix.set_query_rotation(adsx.ROT_TENSOR)
+    try:
+        # (few queries are split over warps: exact mode keeps that deterministic)
+        for reps, eps0 in ((1, math.inf), (80, 2.1)):
+            Qd = torch.from_numpy(np.tile(wl.Q, (reps, 1))).cuda()
+            ref_ids, ref_d, ref_dims = ix.search(Qd, 10, 10, eps0=eps0, delta_d=32, return_dims=True)
+            torch.cuda.synchronize()
+            ref_ids, ref_d = ref_ids.cpu().numpy(), ref_d.cpu().numpy()
+            ref_dims = ref_dims.cpu().numpy()
+            for _ in range(2):
+                ids, d2, dims = _noalloc(adsx, torch, ix, Qd, 10, 10, eps0, 32)
+                _same(ids, d2, ref_ids, ref_d)
+                assert np.array_equal(dims, ref_dims)
+    finally:
+        ix.set_query_rotation(adsx.ROT_FP32)
+
+
 @pytest.mark.parametrize("K", [10, 100])
 def test_noalloc_split_adsampling_few_queries(setup, K):
     """100 queries: each is split over several warps that share r through the
