@@ -328,6 +328,28 @@ int adsx_stream_status(const adsx_index *index, void *stream);
 int adsx_set_scan_schedule(adsx_index *index, int32_t schedule, int32_t queries_per_item,
                            int32_t tiles_per_item);
 
+/*
+ * adsx_save_index -- writes a built index to the file `path` (the paper keeps
+ * P from index time, Sec. 6.1 "Implementation"; this keeps the whole index:
+ * the rotation (P or the Kac walk), rotated centroids, the dim-blocked
+ * vectors and, for 16-bit storage, their FP32 copy, ids and offsets, the
+ * tuned scan settings), so that another process can search it without
+ * rebuilding.  The file is in the host's byte order with an FNV-1a
+ * checksum; it is about as large as the index's device memory.
+ *   index   a built index; its stream work is finished first (`stream` is
+ *           synchronised).
+ * Errors: ADSX_EINVAL (NULL arguments, the file cannot be written),
+ * ADSX_ECUDA.
+ * adsx_load_index -- reads such a file onto the current CUDA device; the
+ * index searches exactly like the one saved (same results, bit for bit).
+ * The query-rotation mode starts as ADSX_ROT_FP32.  Synchronous.
+ * Errors: ADSX_EINVAL (no such file, not an index file, fields outside the
+ * library's limits, truncated, checksum mismatch, inconsistent offsets),
+ * ADSX_ENOMEM, ADSX_ECUDA; *out is NULL then and nothing leaks.
+ */
+int adsx_save_index(const adsx_index *index, const char *path, void *stream);
+int adsx_load_index(const char *path, void *stream, adsx_index **out);
+
 /* Query rotation modes (adsx_set_query_rotation). */
 #define ADSX_ROT_FP32 0      /* compensated FP32 dot products (Dot2)                */
 #define ADSX_ROT_TENSOR 1    /* tcgen05 tensor cores, exact digit products           */

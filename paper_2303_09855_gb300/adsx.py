@@ -81,6 +81,8 @@ def load():
     lib.adsx_set_stage_timing.argtypes = [V, i32]
     lib.adsx_set_scan_schedule.argtypes = [V, i32, i32, i32]
     lib.adsx_set_query_rotation.argtypes = [V, i32]
+    lib.adsx_save_index.argtypes = [V, ctypes.c_char_p, V]
+    lib.adsx_load_index.argtypes = [ctypes.c_char_p, V, V]
     lib.adsx_scan_config.argtypes = [V, V, V, V, V, V]
     lib.adsx_stage_ms.argtypes = [V, V]
     lib.adsx_scan_kernel_ms.argtypes = [V, V, V]
@@ -92,7 +94,7 @@ def load():
                "adsx_probe", "adsx_rotate", "adsx_dco_fixed_r", "adsx_stream_status",
                "adsx_set_stage_timing", "adsx_stage_ms", "adsx_search_noalloc",
                "adsx_set_scan_schedule", "adsx_scan_config", "adsx_scan_kernel_ms",
-               "adsx_set_query_rotation",
+               "adsx_set_query_rotation", "adsx_save_index", "adsx_load_index",
                "adsx_search_batched", "adsx_search_pdscan", "adsx_autotune",
                "adsx_server_create",
                "adsx_server_submit", "adsx_server_submit_many", "adsx_server_wait",
@@ -201,6 +203,9 @@ class Index:
     def set_query_rotation(self, mode):
         return set_query_rotation(self, mode)
 
+    def save(self, path, stream=None):
+        return save_index(self, path, stream)
+
 
 def build_index(X, P, centroids, assign, storage=F32, stream=None, metric=L2) -> Index:
     """adsx_build_index (metric L2) or adsx_build_index_metric (IP, COSINE):
@@ -219,6 +224,18 @@ def build_index(X, P, centroids, assign, storage=F32, stream=None, metric=L2) ->
         _check(load().adsx_build_index_metric(_ptr(X), X.shape[0], X.shape[1], _ptr(P), _ptr(C),
                                               C.shape[0], _ptr(a), int(storage), int(metric),
                                               _stream_of(None, stream), ctypes.byref(h)))
+    return Index(h)
+
+
+def save_index(index: Index, path: str, stream=None):
+    """adsx_save_index: the built index to a file."""
+    _check(load().adsx_save_index(index.handle, str(path).encode(), _stream_of(None, stream)))
+
+
+def load_index(path: str, stream=None) -> Index:
+    """adsx_load_index: an index saved by save_index, on the current device."""
+    h = ctypes.c_void_p()
+    _check(load().adsx_load_index(str(path).encode(), _stream_of(None, stream), ctypes.byref(h)))
     return Index(h)
 
 

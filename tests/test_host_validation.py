@@ -3,8 +3,9 @@ is rejected with ADSX_EINVAL (and a message naming the problem) before the
 library touches a device, so it runs without a GPU.  Covers the index build
 (metric, sizes, storage type, assignments, malformed Kac walks), NULL
 handles and output pointers, the graph and server entry points (create,
-submit, wait, cancel, stats reset), and the thread-local error message of
-adsx_last_error.  Without a device, valid arguments fail with ADSX_ECUDA:
+submit, wait, cancel, stats reset), index files that are missing, of
+another kind or with header fields out of range (adsx_load_index), and the
+thread-local error message of adsx_last_error.  Without a device, valid arguments fail with ADSX_ECUDA:
 there is no host fallback."""
 import ctypes
 import threading
@@ -137,3 +138,23 @@ def test_no_cpu_fallback_without_a_device(A):
     with pytest.raises(A.AdsxError) as ei:
         A.build_index(X, P, C, a)
     assert ei.value.code == A.ECUDA, str(ei.value)
+
+
+def test_load_index_rejects_bad_files(A, tmp_path):
+    """adsx_load_index checks the file's magic and header before it
+    allocates anything on a device."""
+    _rejects(A, lambda: A.load_index(tmp_path / "missing.adsx"), "cannot open")
+    p = tmp_path / "other.bin"
+    p.write_bytes(b"NOTANIDX" + bytes(400))
+    _rejects(A, lambda: A.load_index(p), "not an adsx index file")
+    p.write_bytes(b"ADSXIDX1" + bytes(40))                      # header cut short
+    _rejects(A, lambda: A.load_index(p), "not an adsx index file")
+    hdr = np.zeros(36, dtype=np.int64)                          # N = 0, ... out of range
+    p.write_bytes(b"ADSXIDX1" + hdr.tobytes())
+    _rejects(A, lambda: A.load_index(p), "header fields out of range")
+    lib = A.load()
+    out = ctypes.c_void_p(123)
+    assert lib.adsx_load_index(None, None, ctypes.byref(out)) == A.EINVAL and not out.value
+    assert lib.adsx_load_index(str(p).encode(), None, None) == A.EINVAL
+    assert lib.adsx_save_index(None, str(p).encode(), None) == A.EINVAL
+    assert "index is NULL" in A.last_error()
