@@ -35,6 +35,10 @@
  *     caller pointer after a call returns.
  *   - Thread safety: searches on one index may run concurrently on different
  *     streams; build and free must not overlap any other call on the index.
+ *   - Temporary device memory of a call comes from the library's own
+ *     stream-ordered memory pool on the current device, which keeps what it
+ *     has grown to between calls (like a caching allocator) so that repeated
+ *     searches do not map fresh memory; adsx_search_noalloc allocates none.
  */
 #ifndef ADSX_H
 #define ADSX_H

@@ -2,13 +2,15 @@
 // construction (host CSR build + device rotation and layout scatter) and the
 // search pipeline (rotate -> centroid distances -> top-nprobe -> scan), all
 // enqueued on the caller's stream.  Temporary device buffers come from the
-// stream-ordered allocator (cudaMallocAsync / cudaFreeAsync).
+// library's own stream-ordered memory pool (cudaMallocFromPoolAsync /
+// cudaFreeAsync), which keeps its memory between calls.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -58,11 +60,60 @@ bool is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// The library's stream-ordered memory pool on the current device, created
+// on first use with no release threshold: memory freed by a search stays in
+// the pool for the next one.  (The device's default pool hands freed memory
+// back to the system at every synchronisation, so each search would map its
+// temporaries -- 164 MB of centroid distances for 10k queries x 4096
+// clusters -- afresh, on the host's critical path.)  NULL if no pool can be
+// made: the default pool is used then.
+cudaMemPool_t scratch_pool()
+{
+    constexpr int MAXDEV = 64;
+    static std::mutex mu;
+    static cudaMemPool_t pools[MAXDEV] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof props);
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t mp = nullptr;
+        if (cudaMemPoolCreate(&mp, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = UINT64_MAX;
+        if (cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+            cudaGetLastError();
+            cudaMemPoolDestroy(mp);
+            return nullptr;
+        }
+        pools[dev] = mp;
+    }
+    return pools[dev];
+}
+
 // Stream-ordered scratch buffers, released on the stream when the scope ends.
+// While the stream is being captured into a CUDA graph the allocations are
+// left to the graph (cudaMallocAsync becomes a graph allocation node).
 struct Scratch {
     cudaStream_t s;
+    cudaMemPool_t pool = nullptr;
     std::vector<void *> bufs;
-    explicit Scratch(cudaStream_t st) : s(st) {}
+    explicit Scratch(cudaStream_t st) : s(st)
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) cudaGetLastError();
+        if (cs == cudaStreamCaptureStatusNone) pool = scratch_pool();
+    }
     ~Scratch()
     {
         for (void *p : bufs) cudaFreeAsync(p, s);
@@ -71,7 +122,9 @@ struct Scratch {
     cudaError_t get(T **out, size_t count)
     {
         void *p = nullptr;
-        cudaError_t e = cudaMallocAsync(&p, std::max<size_t>(count * sizeof(T), 16), s);
+        const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+        cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s)
+                             : cudaMallocAsync(&p, bytes, s);
         if (e != cudaSuccess) return e;
         bufs.push_back(p);
         *out = static_cast<T *>(p);
