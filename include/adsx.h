@@ -454,8 +454,10 @@ int adsx_scan_kernel_ms(const adsx_index *index, float *ms, int32_t *launches);
  *   - No device memory is allocated or freed: every temporary buffer is cut
  *     from one fixed array of ADSX_NOALLOC_SCRATCH_BYTES that the library
  *     holds on every GPU that loads it, until the process exits.  A call
- *     whose temporaries would not fit (roughly nq * (4*D + 4*nlist +
- *     4*nprobe) bytes -- with the tensor-core query rotation the 4*nlist
+ *     whose temporaries would not fit (roughly nq * (12*D + 4*nlist +
+ *     4*nprobe) bytes: q', its TF32 halves for the centroid GEMM, the
+ *     centroid distances and the probes -- with the tensor-core query
+ *     rotation the 4*nlist
  *     part is at least the rotation's digits and partial sums of
  *     min(nq, 1024) queries, 4 * (units + T) * Dp each (see
  *     adsx_set_query_rotation) --

@@ -39,6 +39,7 @@ struct Index {
     float *P = nullptr;        // Dp x Dp, zero padded, row-major (y = P x)
     float *cents = nullptr;    // nlist x Dp rotated centroids
     float *cnorm = nullptr;    // nlist ||c'||^2
+    uint32_t *cents_split = nullptr;  // TF32 halves of cents for the centroid GEMM (tf32_split)
     void *data = nullptr;      // N x Dp of the storage type, dim-blocked per cluster
     float *rows32 = nullptr;   // N x Dp FP32 rotated rows in CSR order (16-bit storage only)
     float *norms = nullptr;    // N FP32 norms ||y|| in CSR order (16-bit storage only)
@@ -266,14 +267,49 @@ __device__ __forceinline__ float test_factor(int blk, int D, float eps0)
 // Sets the message returned by adsx_last_error() on the calling thread.
 void set_last_error(const std::string &msg);
 
+// ---- probe selection (gemm_tc.cu epilogue, select.cu)
+// Ordering key of a query-centroid distance: the bit pattern of a positive
+// float orders like the float; zero, negative rounding residue and NaN map
+// to 0 / +inf.
+__device__ __forceinline__ unsigned dist_key(float v)
+{
+    if (!(v > 0.f)) return (v != v) ? 0x7f800000u : 0u;
+    return __float_as_uint(v);
+}
+
+// Keeps t0 <= t1 <= t2 <= t3, the four smallest words seen so far.
+__device__ __forceinline__ void keep4(unsigned x, unsigned &t0, unsigned &t1, unsigned &t2,
+                                      unsigned &t3)
+{
+    unsigned m;
+    m = min(t0, x); x = max(t0, x); t0 = m;
+    m = min(t1, x); x = max(t1, x); t1 = m;
+    m = min(t2, x); x = max(t2, x); t2 = m;
+    t3 = min(t3, x);
+}
+
+// The tile summary of the distance matrix: for every query row and every
+// 128-column tile, the tile's four smallest entries, ascending, each as
+// (dist_key & ~127) | column within the tile; a tile narrower than four
+// columns pads with ~0u.  Row q's tiles are SUMMARY_TILE-wide and stored at
+// summary + (q * ntiles + tile) * 4.
+constexpr int SUMMARY_TILE = 128;
+constexpr unsigned SUMMARY_LOW = SUMMARY_TILE - 1;
+
 // ----------------------------------------------------------------- launches
 // C[i][j] = max(an[i] + bn[j] - 2 (A B^T)[i][j], 0) on tcgen05 tensor cores
 // (3-term TF32 split, FP32 accumulation in TMEM): A M x Kd (row stride lda),
 // B Nb x Kd (row stride ldb; rows >= Nb read as 0), C M x Nout (row stride
 // ldc), an / bn the squared row norms of A / B.
-cudaError_t launch_tc_gemm(const float *A, int64_t M, int lda, const float *B, int Nb, int ldb,
-                           int Kd, float *C, int ldc, int Nout, const float *an, const float *bn,
-                           unsigned *err, cudaStream_t s);
+// TF32 hi/lo halves of the rows of X (R x K, K a multiple of 16) in the
+// layout launch_tc_gemm streams; `out` holds tf32_split_words(R, K) words.
+int64_t tf32_split_words(int64_t rows, int K);
+cudaError_t launch_tf32_split(const float *X, int64_t R, int ld, int K, uint32_t *out, cudaStream_t s);
+// C = max(an + bn - 2 A B^T, 0) (M x Nout, row stride ldc) from split A and B
+// (K = Kd), and the probe select's tile summary when `summary` is not NULL.
+cudaError_t launch_tc_gemm(const uint32_t *As, int64_t M, const uint32_t *Bs, int Kd, float *C,
+                           int ldc, int Nout, const float *an, const float *bn, unsigned *err,
+                           cudaStream_t s, unsigned *summary = nullptr);
 cudaError_t launch_row_sqnorm(const float *X, int64_t M, int ld, int K, float *out, cudaStream_t s);
 
 // Query rotation Y = X P^T on the tensor cores, FP32-accurate (gemm_tc.cu):
@@ -328,7 +364,8 @@ cudaError_t launch_scatter_layout(const float *Y, int64_t N, int Dp, const int32
 
 cudaError_t launch_select_nprobe(const float *dist, int64_t nq, int nlist, int nprobe,
                                  int32_t *probes, float *probe_d2, cudaStream_t s,
-                                 const int32_t *nprobe_q = nullptr);
+                                 const int32_t *nprobe_q = nullptr,
+                                 const unsigned *summary = nullptr);
 
 struct ScanArgs {
     const void *data;          // storage type per `storage`

@@ -203,17 +203,33 @@ cudaError_t rotate_queries(const Index *ix, const float *q_dev, int64_t nq, floa
     return adsx::rotate_rows(ix, q_dev, nq, qrot, sc.s);
 }
 
-// ||q'-c'||^2 for every (query, centroid) as ||q'||^2 + ||c'||^2 - 2 q'.c'.
+// ||q'-c'||^2 for every (query, centroid) as ||q'||^2 + ||c'||^2 - 2 q'.c',
+// with the tile summary of the result for the top-nprobe select when
+// `summary` is not NULL.
 cudaError_t centroid_distances(const Index *ix, const float *qrot, int64_t nq, float *dist,
-                               Scratch &sc)
+                               Scratch &sc, unsigned *summary = nullptr)
 {
     float *qn = nullptr;
+    uint32_t *qs = nullptr;
     cudaError_t e = sc.get(&qn, (size_t)nq);
+    if (e == cudaSuccess) e = sc.get(&qs, (size_t)adsx::tf32_split_words(nq, ix->Dp));
     if (e != cudaSuccess) return e;
     e = adsx::launch_row_sqnorm(qrot, nq, ix->Dp, ix->Dp, qn, sc.s);
+    if (e == cudaSuccess) e = adsx::launch_tf32_split(qrot, nq, ix->Dp, ix->Dp, qs, sc.s);
     if (e != cudaSuccess) return e;
-    return adsx::launch_tc_gemm(qrot, nq, ix->Dp, ix->cents, ix->nlist, ix->Dp, ix->Dp, dist,
-                                ix->nlist, ix->nlist, qn, ix->cnorm, ix->err, sc.s);
+    return adsx::launch_tc_gemm(qs, nq, ix->cents_split, ix->Dp, dist, ix->nlist, ix->nlist, qn,
+                                ix->cnorm, ix->err, sc.s, summary);
+}
+
+// The tile summary (four entries per 128 centroids) is written for the
+// select when it can bound the nprobe-th distance of a row from at least
+// twice nprobe entries; the select uses it for rows with nprobe <= 64.
+cudaError_t probe_summary(const Index *ix, int64_t nq, int nprobe, Scratch &sc, unsigned **summary)
+{
+    *summary = nullptr;
+    const int64_t ntiles = (ix->nlist + adsx::SUMMARY_TILE - 1) / adsx::SUMMARY_TILE;
+    if (4 * ntiles < 2 * (int64_t)std::min(nprobe, 64)) return cudaSuccess;
+    return sc.get(summary, (size_t)(nq * ntiles * 4));
 }
 
 // Stage timing: an event before (begin) or after (end) a scan-kernel launch.
@@ -237,12 +253,14 @@ cudaError_t probe_queries(const Index *ix, const float *qrot, int64_t nq, int np
                           int32_t *probes, float *pd2, Scratch &sc)
 {
     float *dist = nullptr;
+    unsigned *summ = nullptr;
     cudaError_t e = sc.get(&dist, (size_t)nq * ix->nlist);
+    if (e == cudaSuccess) e = probe_summary(ix, nq, nprobe, sc, &summ);
     if (e != cudaSuccess) return e;
-    e = centroid_distances(ix, qrot, nq, dist, sc);
+    e = centroid_distances(ix, qrot, nq, dist, sc, summ);
     if (e != cudaSuccess) return e;
     if ((e = mark(ix, 2, sc.s)) != cudaSuccess) return e;
-    return adsx::launch_select_nprobe(dist, nq, ix->nlist, nprobe, probes, pd2, sc.s);
+    return adsx::launch_select_nprobe(dist, nq, ix->nlist, nprobe, probes, pd2, sc.s, nullptr, summ);
 }
 
 // Sec. 8, extension (1): cosine queries are scaled to unit norm before the
@@ -559,6 +577,11 @@ static int build_impl(const float *X, int64_t N, int32_t D, const float *P,
         BCK(adsx::rotate_rows(ix, xd, N, yd, s), "rotate data");
         BCK(adsx::rotate_rows(ix, cd, nlist, ix->cents, s), "rotate centroids");
         BCK(adsx::launch_row_sqnorm(ix->cents, nlist, Dp, Dp, ix->cnorm, s), "centroid norms");
+        // the centroids' TF32 halves for the centroid-distance GEMM
+        BCK(dalloc((void **)&ix->cents_split,
+                   sizeof(uint32_t) * (size_t)adsx::tf32_split_words(nlist, Dp)),
+            "alloc split centroids");
+        BCK(adsx::launch_tf32_split(ix->cents, nlist, Dp, Dp, ix->cents_split, s), "split centroids");
         // inner product: ||q'||^2 + max ||c'||^2 - 2 q'.c' >= 0 ranks clusters
         // by the largest <c, q> with the distance GEMM unchanged
         if (metric == ADSX_IP) BCK(adsx::launch_fill_max(ix->cnorm, nlist, s), "centroid term");
@@ -621,6 +644,7 @@ int adsx_free_index(adsx_index *index)
     cudaDeviceSynchronize();
     cudaFree(ix->P);
     cudaFree(ix->cents);
+    cudaFree(ix->cents_split);
     cudaFree(ix->cnorm);
     cudaFree(ix->data);
     cudaFree(ix->rows32);
@@ -1113,10 +1137,13 @@ int adsx_search_batched(const adsx_index *index, const float *Qv, int64_t nq, co
     CK(queries_before_probe(ix, qrot, nq, s), "normalise queries");
     {
         float *dist = nullptr;
+        unsigned *summ = nullptr;
         CK(sc.get(&dist, (size_t)nq * ix->nlist), "alloc distances");
-        CK(centroid_distances(ix, qrot, nq, dist, sc), "centroid distances");
+        CK(probe_summary(ix, nq, max_nprobe, sc, &summ), "alloc tile summary");
+        CK(centroid_distances(ix, qrot, nq, dist, sc, summ), "centroid distances");
         CK(mark(ix, 2, s), "event");
-        CK(adsx::launch_select_nprobe(dist, nq, ix->nlist, max_nprobe, probes, nullptr, s, pq.dev),
+        CK(adsx::launch_select_nprobe(dist, nq, ix->nlist, max_nprobe, probes, nullptr, s, pq.dev,
+                                      summ),
            "select");
     }
     const int target = adsx::scan_items_target(ix->device, ix->items_per_sm);

@@ -7,16 +7,19 @@
 //   D2[q][c] = ||q'||^2 + ||c'||^2 - 2 q'.c'  (clamped at 0),
 // a dense nq x nlist x Dp contraction.
 //
-// One 128-thread CTA computes a 128 x 128 output tile.  Per 32-wide k-step
-// every thread converts one row of A and one row of B (fp32 from global) into
-// hi/lo TF32 halves in shared memory, in the canonical K-major no-swizzle
-// layout of the tensor core (8-row x 16-byte core matrices); one thread then
-// issues 4 x 3 tcgen05.mma (M = 128, N = 128, K = 8 each) into a 128-column
-// FP32 accumulator in tensor memory and commits them to an mbarrier; after
-// the last step each warp reads its 32 accumulator rows with tcgen05.ld and
-// writes the epilogue.  The mbarrier wait is bounded: on time-out the kernel
-// sets the error word, waits (bounded by 1 s of device time) for the batch
-// already committed to arrive, frees its tensor memory and returns.
+// The operands are split once into hi/lo TF32 halves (tf32_split_kernel:
+// the queries per search, the centroids at index build), already in the
+// canonical K-major no-swizzle layout of the tensor core (8-row x 16-byte
+// core matrices), so that a 128-row block's K = 16 step is one contiguous
+// 16 KB run per operand.  One 128-thread CTA computes a 128 x 128 output
+// tile: one thread streams the steps into a 3-deep shared-memory ring with
+// bulk copies (the TMA engine) and issues 2 x 3 tcgen05.mma (M = 128,
+// N = 128, K = 8 each) per step into a 128-column FP32 accumulator in tensor
+// memory; two CTAs share an SM, so one's epilogue overlaps the other's
+// MMAs.  After the last step each warp reads its 32 accumulator rows with
+// tcgen05.ld and writes the epilogue: the distances, and for the probe
+// select the tile's four smallest entries per row (one thread owns a row, so
+// this costs a compare-exchange chain per value and no communication).
 #include "adsx_internal.cuh"
 
 namespace adsx {
@@ -25,9 +28,14 @@ namespace {
 constexpr int TM = 128, TN = 128, BK = 32;
 constexpr int SLAB = 4096;                     // bytes of one K = 8 slab of 128 rows
 constexpr int OPER = (BK / 8) * SLAB;          // bytes of one operand (hi or lo) per k-step
-constexpr int OPER_BYTES = 4 * OPER;           // A_hi, A_lo, B_hi, B_lo
 constexpr int STAGE_BYTES = 4 * 32 * (TN + 4) * 4;  // epilogue: 4 warps x 32 rows x 132 floats
-constexpr int SMEM_BYTES = OPER_BYTES > STAGE_BYTES ? OPER_BYTES : STAGE_BYTES;
+// the centroid GEMM's ring: stages of K = 16 (two slabs), A and B halves
+constexpr int GEMM_KS = 2;                              // slabs per stage
+constexpr int GEMM_OPND_BYTES = GEMM_KS * 2 * SLAB;      // one operand's hi + lo per stage
+constexpr int GEMM_STAGE_BYTES = 2 * GEMM_OPND_BYTES;    // A and B: 32 KB
+constexpr int GEMM_STAGES = 3;
+constexpr int GEMM_RING = GEMM_STAGES * GEMM_STAGE_BYTES;
+constexpr int SMEM_BYTES = GEMM_RING > STAGE_BYTES ? GEMM_RING : STAGE_BYTES;
 constexpr uint32_t TMEM_COLS = 128;
 constexpr unsigned WAIT_LIMIT = 1u << 22;
 constexpr unsigned ERR_MMA_TIMEOUT = 8u;
@@ -120,50 +128,94 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd
         : "memory");
 }
 
-// Loads row `r` of a 128-row tile (rows >= rows_valid or k >= Kd read as 0)
-// for the 32-wide k-step k0, splits it and stores hi/lo into their slabs.
-__device__ __forceinline__ void stage_row(const float *__restrict__ src, bool valid,
-                                          int k0, int Kd, int r, uint8_t *hi, uint8_t *lo)
+// Bulk copy (the TMA engine's linear form) of `bytes` from global to shared
+// memory, completing as transaction bytes on the mbarrier `bar`; both
+// addresses 16-byte aligned, `bytes` a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
 {
-    const bool vec = valid && (k0 + BK <= Kd) && ((reinterpret_cast<uintptr_t>(src) & 15) == 0);
-    float x[BK];
-    if (vec) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        :
+        : "r"(dst), "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" : : "r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :
+                 : "r"(bar)
+                 : "memory");
+}
+
+// Rows of X (R x K, row stride ld floats, K a multiple of 16, rows 16-byte
+// aligned) split into TF32 halves in the order tc_gemm_kernel streams them:
+// per 128-row block and K = 8 slab, the block's 4 KB of hi words, then its
+// 4 KB of lo words, each in the canonical core-matrix order of slab_off.
+// Rows R .. Rpad - 1 (Rpad a multiple of 128) are written as zeros.
+__global__ void tf32_split_kernel(const float *__restrict__ X, int64_t R, int ld, int K,
+                                  int64_t Rpad, uint32_t *__restrict__ out)
+{
+    const int kq = K / 4;
+    const int nslab = K / 8;
+    uint8_t *ob = reinterpret_cast<uint8_t *>(out);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Rpad * kq;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / kq;
+        const int k = (int)(i - r * kq) * 4;
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r < R) x = __ldg(reinterpret_cast<const float4 *>(X + r * ld + k));
+        const float v[4] = {x.x, x.y, x.z, x.w};
+        uint32_t h[4], l[4];
 #pragma unroll
-        for (int i = 0; i < BK / 4; ++i) {
-            const float4 t = __ldg(reinterpret_cast<const float4 *>(src) + i);
-            x[4 * i] = t.x;
-            x[4 * i + 1] = t.y;
-            x[4 * i + 2] = t.z;
-            x[4 * i + 3] = t.w;
+        for (int j = 0; j < 4; ++j) {
+            h[j] = to_tf32(v[j]);
+            l[j] = to_tf32(v[j] - __uint_as_float(h[j]));
         }
-    } else {
-#pragma unroll
-        for (int k = 0; k < BK; ++k) x[k] = (valid && k0 + k < Kd) ? src[k] : 0.f;
-    }
-#pragma unroll
-    for (int k = 0; k < BK; ++k) {
-        const uint32_t h = to_tf32(x[k]);
-        const uint32_t l = to_tf32(x[k] - __uint_as_float(h));
-        const uint32_t o = (uint32_t)(k >> 3) * SLAB + slab_off(r, k & 7);
-        *reinterpret_cast<uint32_t *>(hi + o) = h;
-        *reinterpret_cast<uint32_t *>(lo + o) = l;
+        uint8_t *o = ob + ((r >> 7) * nslab + (k >> 3)) * 2 * SLAB + slab_off((int)(r & 127), k & 7);
+        *reinterpret_cast<uint4 *>(o) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4 *>(o + SLAB) = make_uint4(l[0], l[1], l[2], l[3]);
     }
 }
 
-// C[i][j] = max(an[i] + bn[j] - 2 (A B^T)[i][j], 0).
+// C[i][j] = max(an[i] + bn[j] - 2 (A B^T)[i][j], 0) from the TF32 halves of
+// A (M rows) and B laid out by tf32_split_kernel, and (summary != NULL) the
+// tile summary of C used by the top-nprobe select: per row of the 128 x 128
+// output tile its four smallest entries, packed as dist_key with the column
+// within the tile in the low 7 bits (SUMMARY_TILE = TN).
+//
+// Thread 0 drives a ring of GEMM_STAGES stages of K = 16: it bulk-copies a
+// stage's A and B halves (16 KB each, contiguous in the split layout) onto
+// the stage's `full` barrier, waits for them, issues the stage's 2 x 3 MMAs
+// (per K = 8 slab: lo*hi, hi*lo, hi*hi, the order of the FP32 accumulation)
+// and commits them to the stage's `empty` barrier; the stage the previous
+// step used is refilled as soon as its MMAs have completed, so that the
+// tensor pipe always has the next step's operands.  A final commit to `done`
+// releases the epilogue.  Every wait is bounded; on time-out the kernel sets
+// the error word, waits (bounded by 1 s of device time) for the copies and
+// MMAs already issued, frees its tensor memory and returns.
 __global__ void __launch_bounds__(128, 1)
-    tc_gemm_kernel(const float *__restrict__ A, int64_t M, int lda, const float *__restrict__ B,
-                   int Nb, int ldb, int Kd, float *__restrict__ C, int ldc, int Nout,
-                   const float *__restrict__ an, const float *__restrict__ bn, unsigned *err)
+    tc_gemm_kernel(const uint32_t *__restrict__ As, int64_t M, const uint32_t *__restrict__ Bs,
+                   int Kd, float *__restrict__ C, int ldc, int Nout, const float *__restrict__ an,
+                   const float *__restrict__ bn, unsigned *err, unsigned *__restrict__ summary)
 {
+    static_assert(TN == SUMMARY_TILE, "one summary tile per output tile");
     extern __shared__ __align__(1024) uint8_t sm[];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t full[GEMM_STAGES], empty[GEMM_STAGES], done;
     __shared__ uint32_t tmem_slot;
+    __shared__ int s_ok;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t m0 = (int64_t)blockIdx.x * TM;
     const int n0 = blockIdx.y * TN;
-    uint8_t *Ah = sm, *Al = sm + OPER, *Bh = sm + 2 * OPER, *Bl = sm + 3 * OPER;
-    const uint32_t bar = smem_addr(&mbar);
+    const int nslab = Kd / 8, nsteps = nslab / GEMM_KS;
+    const uint8_t *ga = reinterpret_cast<const uint8_t *>(As) + (size_t)blockIdx.x * nslab * 2 * SLAB;
+    const uint8_t *gb = reinterpret_cast<const uint8_t *>(Bs) + (size_t)blockIdx.y * nslab * 2 * SLAB;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -173,65 +225,92 @@ __global__ void __launch_bounds__(128, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" : : "r"(bar) : "memory");
+        for (int i = 0; i < GEMM_STAGES; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" : : "r"(smem_addr(&full[i])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" : : "r"(smem_addr(&empty[i])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" : : "r"(smem_addr(&done)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_ok = 1;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_slot;
 
-    uint32_t phase = 0;
-    bool ok = true;
-    const int64_t arow = m0 + tid;
-    const int brow = n0 + tid;
-    for (int k0 = 0; k0 < Kd && ok; k0 += BK) {
-        stage_row(A + arow * lda + k0, arow < M, k0, Kd, tid, Ah, Al);
-        stage_row(B + (int64_t)brow * ldb + k0, brow < Nb, k0, Kd, tid, Bh, Bl);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+    if (tid == 0) {
+        auto produce = [&](int step) {
+            const int st = step % GEMM_STAGES;
+            const uint32_t fb = smem_addr(&full[st]);
+            const uint32_t dst = smem_addr(sm + st * GEMM_STAGE_BYTES);
+            mbar_expect(fb, GEMM_STAGE_BYTES);
+            bulk_g2s(dst, ga + (size_t)step * GEMM_OPND_BYTES, GEMM_OPND_BYTES, fb);
+            bulk_g2s(dst + GEMM_OPND_BYTES, gb + (size_t)step * GEMM_OPND_BYTES, GEMM_OPND_BYTES, fb);
+        };
+        int produced = nsteps < GEMM_STAGES ? nsteps : GEMM_STAGES;
+        for (int p = 0; p < produced; ++p) produce(p);
+        int consumed = 0;            // steps whose copies have been waited for
+        bool ok = true;
+        for (int step = 0; step < nsteps && ok; ++step) {
+            const int st = step % GEMM_STAGES;
+            if (!mbar_wait(smem_addr(&full[st]), (uint32_t)(step / GEMM_STAGES) & 1u)) {
+                ok = false;
+                break;
+            }
+            consumed = step + 1;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint8_t *Ab = sm + st * GEMM_STAGE_BYTES, *Bb = Ab + GEMM_OPND_BYTES;
 #pragma unroll
-            for (int s = 0; s < BK / 8; ++s) {
-                const uint64_t ah = make_desc(smem_addr(Ah + s * SLAB));
-                const uint64_t al = make_desc(smem_addr(Al + s * SLAB));
-                const uint64_t bh = make_desc(smem_addr(Bh + s * SLAB));
-                const uint64_t bl = make_desc(smem_addr(Bl + s * SLAB));
-                mma_tf32(tmem, al, bh, (k0 > 0 || s > 0) ? 1u : 0u);
+            for (int j = 0; j < GEMM_KS; ++j) {
+                const uint64_t ah = make_desc(smem_addr(Ab + j * 2 * SLAB));
+                const uint64_t al = make_desc(smem_addr(Ab + j * 2 * SLAB + SLAB));
+                const uint64_t bh = make_desc(smem_addr(Bb + j * 2 * SLAB));
+                const uint64_t bl = make_desc(smem_addr(Bb + j * 2 * SLAB + SLAB));
+                mma_tf32(tmem, al, bh, (step > 0 || j > 0) ? 1u : 0u);
                 mma_tf32(tmem, ah, bl, 1u);
                 mma_tf32(tmem, ah, bh, 1u);
             }
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                :
-                : "r"(bar)
-                : "memory");
+            mma_commit(smem_addr(&empty[st]));
+            // refill the stage of the previous step once its MMAs are done
+            if (step >= 1 && produced < nsteps) {
+                const int prev = step - 1;
+                if (!mbar_wait(smem_addr(&empty[prev % GEMM_STAGES]),
+                               (uint32_t)(prev / GEMM_STAGES) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                produce(produced);
+                ++produced;
+            }
         }
-        ok = mbar_wait(bar, phase);
-        phase ^= 1u;
-        ok = __syncthreads_and(ok);
+        mma_commit(smem_addr(&done));        // every MMA issued above
+        if (!ok) {
+            s_ok = 0;
+            atomicOr(err, ERR_MMA_TIMEOUT);
+            // copies still in flight write into this block's shared memory:
+            // wait for them before anyone leaves
+            for (int step = consumed; step < produced; ++step)
+                if (!mbar_wait_ns(smem_addr(&full[step % GEMM_STAGES]),
+                                  (uint32_t)(step / GEMM_STAGES) & 1u, DRAIN_NS))
+                    atomicOr(err, ERR_MMA_DRAIN);
+        }
     }
-    if (!ok) {
-        // The MMAs of the last batch were committed to the barrier and will
-        // arrive on it: wait for that arrival (up to DRAIN_NS, far beyond the
-        // duration of one batch) so that tensor memory is not released under
-        // them.  Should even that wait give up (the device is not making
-        // progress), ERR_MMA_DRAIN records it; the allocation is released
-        // regardless, as a CTA must not exit holding tensor memory.
-        if (tid == 0) atomicOr(err, ERR_MMA_TIMEOUT);
-        const bool drained = mbar_wait_ns(bar, phase ^ 1u, DRAIN_NS);
-        if (!__syncthreads_and(drained) && tid == 0) atomicOr(err, ERR_MMA_DRAIN);
-    } else {
+    // every thread: the accumulator is final once `done` completes
+    bool ok = mbar_wait_ns(smem_addr(&done), 0u, DRAIN_NS);
+    __syncthreads();
+    if (!ok && tid == 0) atomicOr(err, ERR_MMA_DRAIN);
+    ok = __syncthreads_and(ok && s_ok);
+    if (ok) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         // Each warp reads its 32 accumulator rows (lane = row) and stages the
-        // finished 32 x 128 distances in the (now idle) operand shared memory,
-        // rows 132 floats apart (float4 writes of 8 lanes hit distinct banks),
+        // finished 32 x 128 distances in the (now idle) operand ring, rows
+        // 132 floats apart (float4 writes of 8 lanes hit distinct banks),
         // then writes every row as one coalesced 512-byte run.
         const int64_t row = m0 + warp * 32 + lane;
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         const float rn = (row < M) ? an[row] : 0.f;
         float *stage = reinterpret_cast<float *>(sm) + warp * 32 * (TN + 4);
+        unsigned t0 = ~0u, t1 = ~0u, t2 = ~0u, t3 = ~0u;   // the row's four smallest
 #pragma unroll 1
         for (int c0 = 0; c0 < TN; c0 += 16) {
             uint32_t v[16];
@@ -250,11 +329,22 @@ __global__ void __launch_bounds__(128, 1)
                 const float cn = (col < Nout) ? bn[col] : 0.f;
                 o[j] = fmaxf(rn + cn - 2.f * __uint_as_float(v[j]), 0.f);
             }
+            if (summary) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int cl = c0 + j;
+                    keep4(n0 + cl < Nout ? (dist_key(o[j]) & ~SUMMARY_LOW) | (unsigned)cl : ~0u,
+                          t0, t1, t2, t3);
+                }
+            }
 #pragma unroll
             for (int j = 0; j < 16; j += 4)
                 *reinterpret_cast<float4 *>(stage + lane * (TN + 4) + c0 + j) =
                     make_float4(o[j], o[j + 1], o[j + 2], o[j + 3]);
         }
+        if (summary && row < M)
+            *reinterpret_cast<uint4 *>(summary + ((size_t)row * gridDim.y + blockIdx.y) * 4) =
+                make_uint4(t0, t1, t2, t3);
         __syncwarp();
         const int col = n0 + lane * 4;
         const bool vec_ok = (ldc % 4 == 0) && (col + 4 <= Nout);
@@ -303,18 +393,38 @@ __global__ void row_sqnorm_kernel(const float *__restrict__ X, int64_t M, int ld
 
 }  // namespace
 
-cudaError_t launch_tc_gemm(const float *A, int64_t M, int lda, const float *B, int Nb, int ldb,
-                           int Kd, float *C, int ldc, int Nout, const float *an, const float *bn,
-                           unsigned *err, cudaStream_t s)
+int64_t tf32_split_words(int64_t rows, int K)
+{
+    return (rows + TM - 1) / TM * TM * (int64_t)K * 2;
+}
+
+cudaError_t launch_tf32_split(const float *X, int64_t R, int ld, int K, uint32_t *out, cudaStream_t s)
+{
+    if (R <= 0) return cudaSuccess;
+    if (K % 16 != 0 || ld % 4 != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0 ||
+        (reinterpret_cast<uintptr_t>(out) & 15) != 0)
+        return cudaErrorInvalidValue;
+    const int64_t Rpad = (R + TM - 1) / TM * TM;
+    int64_t blocks = (Rpad * (K / 4) + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    tf32_split_kernel<<<(unsigned)blocks, 256, 0, s>>>(X, R, ld, K, Rpad, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_gemm(const uint32_t *As, int64_t M, const uint32_t *Bs, int Kd, float *C,
+                           int ldc, int Nout, const float *an, const float *bn, unsigned *err,
+                           cudaStream_t s, unsigned *summary)
 {
     if (M <= 0 || Nout <= 0) return cudaSuccess;
     if ((M + TM - 1) / TM > 0x7fffffffLL) return cudaErrorInvalidValue;
-    if (!an || !bn) return cudaErrorInvalidValue;
+    if (!an || !bn || Kd <= 0 || Kd % (8 * GEMM_KS) != 0) return cudaErrorInvalidValue;
+    if ((reinterpret_cast<uintptr_t>(As) & 15) != 0 || (reinterpret_cast<uintptr_t>(Bs) & 15) != 0)
+        return cudaErrorInvalidValue;
     dim3 grid((unsigned)((M + TM - 1) / TM), (unsigned)((Nout + TN - 1) / TN));
     cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    tc_gemm_kernel<<<grid, 128, SMEM_BYTES, s>>>(A, M, lda, B, Nb, ldb, Kd, C, ldc, Nout, an, bn, err);
+    tc_gemm_kernel<<<grid, 128, SMEM_BYTES, s>>>(As, M, Bs, Kd, C, ldc, Nout, an, bn, err, summary);
     return cudaGetLastError();
 }
 

@@ -121,7 +121,8 @@ extern "C" int adsx_search_noalloc(const adsx_index *index, const float *Qv, int
     const size_t rot_part =
         ix->rot_tc ? (size_t)adsx::tc_rot_scratch_floats(ix, std::min<int64_t>(nq, 1024)) * 4 : 0;
     const size_t dist_bytes = std::max<size_t>((size_t)nq * ix->nlist * 4, rot_part);
-    size_t need = rup((size_t)nq * Dp * 4) + rup((size_t)nq * 4) + rup(dist_bytes) +
+    const size_t split_bytes = (size_t)adsx::tf32_split_words(nq, Dp) * 4;
+    size_t need = rup((size_t)nq * Dp * 4) + rup((size_t)nq * 4) + rup(split_bytes) + rup(dist_bytes) +
                   rup((size_t)nq * nprobe * 4) + rup((size_t)(nblk + 1) * 4) + rup(4) +
                   (ix->rot_tc ? rup((size_t)nq * 4) : 0);
     if (a.S > 1) need += rup((size_t)nq * 4) + 2 * rup((size_t)a.n_items * K * 4);
@@ -137,6 +138,7 @@ extern "C" int adsx_search_noalloc(const adsx_index *index, const float *Qv, int
     Carver cv{base};
     float *qrot = cv.take<float>((size_t)nq * Dp);
     float *qn = cv.take<float>((size_t)nq);
+    uint32_t *qs = cv.take<uint32_t>(split_bytes / 4);
     float *dist = cv.take<float>(dist_bytes / 4);
     int32_t *probes = cv.take<int32_t>((size_t)nq * nprobe);
     float *ftab = cv.take<float>((size_t)nblk + 1);
@@ -168,9 +170,10 @@ extern "C" int adsx_search_noalloc(const adsx_index *index, const float *Qv, int
             e = adsx::rotate_rows(ix, Qv, nq, qrot, s);
     }
     if (e == cudaSuccess) e = adsx::launch_row_sqnorm(qrot, nq, Dp, Dp, qn, s);
+    if (e == cudaSuccess) e = adsx::launch_tf32_split(qrot, nq, Dp, Dp, qs, s);
     if (e == cudaSuccess)
-        e = adsx::launch_tc_gemm(qrot, nq, Dp, ix->cents, ix->nlist, Dp, Dp, dist, ix->nlist,
-                                 ix->nlist, qn, ix->cnorm, ix->err, s);
+        e = adsx::launch_tc_gemm(qs, nq, ix->cents_split, Dp, dist, ix->nlist, ix->nlist, qn,
+                                 ix->cnorm, ix->err, s);
     if (e == cudaSuccess)
         e = adsx::launch_select_nprobe(dist, nq, ix->nlist, nprobe, probes, nullptr, s);
     if (e == cudaSuccess)

@@ -323,6 +323,19 @@ extern "C" int adsx_load_index(const char *path, void *stream, adsx_index **out)
         adsx_free_index(reinterpret_cast<adsx_index *>(ix));
         return perr(ADSX_EINVAL, "%s: %s", path, bad.c_str());
     }
+    // the centroids' TF32 halves for the centroid GEMM, derived, not stored
+    const size_t sw = (size_t)adsx::tf32_split_words(ix->nlist, ix->Dp);
+    e = cudaMalloc((void **)&ix->cents_split, sizeof(uint32_t) * sw);
+    if (e == cudaSuccess) {
+        ix->bytes += (int64_t)(sizeof(uint32_t) * sw);
+        e = adsx::launch_tf32_split(ix->cents, ix->nlist, ix->Dp, ix->Dp, ix->cents_split, nullptr);
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        adsx_free_index(reinterpret_cast<adsx_index *>(ix));
+        return perr(e == cudaErrorMemoryAllocation ? ADSX_ENOMEM : ADSX_ECUDA, "split centroids: %s",
+                    cudaGetErrorString(e));
+    }
     (void)stream;
     *out = reinterpret_cast<adsx_index *>(ix);
     return ADSX_OK;

@@ -2,8 +2,15 @@
 // N_probe clusters whose centroids are nearest to the query), ordered by
 // (squared centroid distance, cluster id).
 //
-// One warp per query row, several per block, no block barriers.  For
-// nprobe <= 64 a bound-and-gather path is taken (see the kernel); otherwise,
+// One warp per query row, several per block, no block barriers.  When the
+// centroid GEMM has written the tile summary (four smallest entries of every
+// 128-column tile of the row, adsx_internal.cuh) and nprobe <= 64, the row
+// is mostly not read at all: the nprobe-th smallest summary word bounds the
+// nprobe-th smallest distance, a tile whose fourth word lies above the bound
+// contributes exactly its summary words below it (their exact values read
+// one by one), and only the other tiles are read whole
+// (select_by_summary).  Else, for nprobe <= 64, a bound-and-gather path over
+// the whole row is taken (see the kernel); otherwise,
 // or when ties overflow it, a radix select runs: the row's
 // distances become order-preserving 32-bit keys (bit patterns of non-negative
 // floats), re-read from the row (an L2 hit: the warp has just read it) on
@@ -23,25 +30,6 @@ namespace {
 
 constexpr int MAXW = 8;                 // warps per block (fewer for large nprobe)
 constexpr unsigned FULL = 0xffffffffu;
-
-__device__ __forceinline__ unsigned dist_key(float v)
-{
-    // non-negative floats order like their bit patterns; -0, tiny negative
-    // rounding residue and NaN are mapped to 0 / +inf.
-    if (!(v > 0.f)) return (v != v) ? 0x7f800000u : 0u;
-    return __float_as_uint(v);
-}
-
-// Keeps t0 <= t1 <= t2 <= t3, the lane's four smallest keys so far.
-__device__ __forceinline__ void keep4(unsigned x, unsigned &t0, unsigned &t1, unsigned &t2,
-                                      unsigned &t3)
-{
-    unsigned m;
-    m = min(t0, x); x = max(t0, x); t0 = m;
-    m = min(t1, x); x = max(t1, x); t1 = m;
-    m = min(t2, x); x = max(t2, x); t2 = m;
-    t3 = min(t3, x);
-}
 
 // Bitonic sort of n (a power of two) entries of `v` by the warp.
 template <typename K>
@@ -76,9 +64,134 @@ __host__ __device__ inline size_t warp_region(int P2)
     return sel_bytes(P2) + 1024;
 }
 
-__global__ void __launch_bounds__(MAXW * 32) select_nprobe_kernel(
+// The sorted (key, id) words sel[0 .. c) padded to a power of two, sorted,
+// and the first nprobe written out.
+__device__ __forceinline__ void emit_sorted(unsigned long long *sel, unsigned c, int nprobe,
+                                            int lane, int32_t *prow, float *drow)
+{
+    int n2 = 32;
+    while (n2 < (int)c) n2 <<= 1;
+    for (int i = (int)c + lane; i < n2; i += 32) sel[i] = ~0ull;
+    __syncwarp();
+    warp_sort(sel, n2, lane);
+    for (int p = lane; p < nprobe; p += 32) {
+        const unsigned long long v = sel[p];
+        prow[p] = (int32_t)(v & 0xffffffffu);
+        if (drow) drow[p] = __uint_as_float((unsigned)(v >> 32));
+    }
+    __syncwarp();
+}
+
+// nprobe <= 64 from the tile summary `srow` (ntiles x 4 words of this row).
+// Each lane keeps the four smallest words of its tiles; the nprobe-th
+// smallest of those 128 words, pb, is at least the packed word of the
+// nprobe-th smallest distance (a subset's order statistic), so with
+// tb = pb & ~127 every distance among the nprobe smallest has a key
+// <= Tb = tb | 127.  A tile whose fourth word has (word & ~127) > tb holds
+// no other key <= Tb than those of its summary words with (word & ~127) <= tb,
+// whose exact keys are read from the row; every other tile is read whole.
+// Everything <= Tb is gathered and sorted by (key, id): the exact answer.
+// Returns false (nothing written) when the summary holds fewer than nprobe
+// entries or more than FAST_CAP keys reach the bound.
+__device__ bool select_by_summary(const float *__restrict__ row, const unsigned *__restrict__ srow,
+                                  int ntiles, int nlist, int nprobe, unsigned long long *sel,
+                                  int lane, int32_t *prow, float *drow)
+{
+    const unsigned below = (1u << lane) - 1u;
+    unsigned t0 = ~0u, t1 = ~0u, t2 = ~0u, t3 = ~0u;
+    uint4 w0 = make_uint4(~0u, ~0u, ~0u, ~0u);      // this lane's first tile, kept for the gather
+    for (int t = lane; t < ntiles; t += 32) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(srow) + t);
+        if (t == lane) w0 = w;
+        keep4(w.x, t0, t1, t2, t3);
+        keep4(w.y, t0, t1, t2, t3);
+        keep4(w.z, t0, t1, t2, t3);
+        keep4(w.w, t0, t1, t2, t3);
+    }
+    // tb = (nprobe-th smallest of the 128 kept words) & ~127, bit by bit from
+    // the top: bit b of tb is 0 iff at least nprobe words lie at or below
+    // the prefix found so far with bit b clear and every lower bit set.
+    unsigned tb = 0u;
+    for (int b = 31; b >= 7; --b) {
+        const unsigned x = tb | ((1u << b) - 1u);
+        const unsigned n = (t0 <= x) + (t1 <= x) + (t2 <= x) + (t3 <= x);
+        if (__reduce_add_sync(FULL, n) < (unsigned)nprobe) tb |= 1u << b;
+    }
+    if (tb == (~0u & ~SUMMARY_LOW)) return false;   // fewer than nprobe summary entries
+    const unsigned Tb = tb | SUMMARY_LOW;
+    unsigned c = 0;
+    for (int g0 = 0; g0 < ntiles && c <= (unsigned)FAST_CAP; g0 += 32) {
+        const int t = g0 + lane;
+        uint4 w = w0;
+        if (g0 > 0) w = t < ntiles ? __ldg(reinterpret_cast<const uint4 *>(srow) + t)
+                                   : make_uint4(~0u, ~0u, ~0u, ~0u);
+        const bool whole = t < ntiles && (w.w & ~SUMMARY_LOW) <= tb;
+        const unsigned e4[4] = {w.x, w.y, w.z, w.w};
+        // the exact values of the summary words below the bound, loaded together
+        float xv[4];
+        unsigned needm = 0u;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const bool need = !whole && (e4[e] & ~SUMMARY_LOW) <= tb;   // padding never passes
+            needm |= (need ? 1u : 0u) << e;
+            xv[e] = need ? __ldg(row + t * SUMMARY_TILE + (int)(e4[e] & SUMMARY_LOW)) : 0.f;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const unsigned k = dist_key(xv[e]);
+            const bool take = ((needm >> e) & 1u) && k <= Tb;
+            const unsigned bt = __ballot_sync(FULL, take);
+            const unsigned at = c + __popc(bt & below);
+            if (take && at < (unsigned)FAST_CAP)
+                sel[at] = ((unsigned long long)k << 32) |
+                          (unsigned)(t * SUMMARY_TILE + (int)(e4[e] & SUMMARY_LOW));
+            c += __popc(bt);
+        }
+        // tiles that may hold more keys <= Tb than their summary shows, two
+        // at a time
+        unsigned wm = __ballot_sync(FULL, whole);
+        while (wm) {
+            const int ta = g0 + __ffs(wm) - 1;
+            wm &= wm - 1u;
+            int tz = -1;
+            if (wm) {
+                tz = g0 + __ffs(wm) - 1;
+                wm &= wm - 1u;
+            }
+            constexpr int U = SUMMARY_TILE / 32;
+            float x[2 * U];
+#pragma unroll
+            for (int u = 0; u < 2 * U; ++u) {
+                const int tt = u < U ? ta : tz;
+                const int col = tt * SUMMARY_TILE + (u % U) * 32 + lane;
+                x[u] = (tt >= 0 && col < nlist) ? __ldg(row + col) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 2 * U; ++u) {
+                const int tt = u < U ? ta : tz;
+                const int col = tt * SUMMARY_TILE + (u % U) * 32 + lane;
+                const unsigned k = dist_key(x[u]);
+                const bool take = tt >= 0 && col < nlist && k <= Tb;
+                const unsigned bt = __ballot_sync(FULL, take);
+                const unsigned at = c + __popc(bt & below);
+                if (take && at < (unsigned)FAST_CAP)
+                    sel[at] = ((unsigned long long)k << 32) | (unsigned)col;
+                c += __popc(bt);
+            }
+        }
+    }
+    if (c > (unsigned)FAST_CAP) {
+        __syncwarp();
+        return false;
+    }
+    emit_sorted(sel, c, nprobe, lane, prow, drow);
+    return true;
+}
+
+__global__ void __launch_bounds__(MAXW * 32, 3) select_nprobe_kernel(
     const float *__restrict__ dist, int64_t nq, int nlist, int pstride, int P2, int W,
-    int32_t *__restrict__ probes, float *__restrict__ pd2, const int32_t *__restrict__ nprobe_q)
+    int32_t *__restrict__ probes, float *__restrict__ pd2, const int32_t *__restrict__ nprobe_q,
+    const unsigned *__restrict__ summary, int ntiles)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -94,6 +207,10 @@ __global__ void __launch_bounds__(MAXW * 32) select_nprobe_kernel(
             nprobe = nprobe < 1 ? 1 : (nprobe > pstride ? pstride : nprobe);
         }
         const float *row = dist + q * nlist;
+        if (summary && nprobe <= 64 &&
+            select_by_summary(row, summary + (size_t)q * ntiles * 4, ntiles, nlist, nprobe, sel,
+                              lane, probes + q * pstride, pd2 ? pd2 + q * pstride : nullptr))
+            continue;
         unsigned kmin = 0xffffffffu, kmax = 0u;
         // nprobe <= 64: the nprobe-th smallest of the 128 lane-wise four
         // smallest keys bounds the nprobe-th smallest key from above (it is
@@ -179,17 +296,8 @@ __global__ void __launch_bounds__(MAXW * 32) select_nprobe_kernel(
                 }
             }
             if (c <= (unsigned)FAST_CAP) {
-                int n2 = 32;
-                while (n2 < (int)c) n2 <<= 1;
-                for (int i = (int)c + lane; i < n2; i += 32) sel[i] = ~0ull;
-                __syncwarp();
-                warp_sort(sel, n2, lane);
-                for (int p = lane; p < nprobe; p += 32) {
-                    const unsigned long long v = sel[p];
-                    probes[q * pstride + p] = (int32_t)(v & 0xffffffffu);
-                    if (pd2) pd2[q * pstride + p] = __uint_as_float((unsigned)(v >> 32));
-                }
-                __syncwarp();
+                emit_sorted(sel, c, nprobe, lane, probes + q * pstride,
+                            pd2 ? pd2 + q * pstride : nullptr);
                 continue;
             }
             __syncwarp();                   // too many ties: the radix path below
@@ -296,7 +404,7 @@ __global__ void __launch_bounds__(MAXW * 32) select_nprobe_kernel(
 
 cudaError_t launch_select_nprobe(const float *dist, int64_t nq, int nlist, int nprobe,
                                  int32_t *probes, float *probe_d2, cudaStream_t s,
-                                 const int32_t *nprobe_q)
+                                 const int32_t *nprobe_q, const unsigned *summary)
 {
     if (nq <= 0) return cudaSuccess;
     int P2 = 1;
@@ -310,8 +418,9 @@ cudaError_t launch_select_nprobe(const float *dist, int64_t nq, int nlist, int n
     if (e != cudaSuccess) return e;
     int64_t grid = (nq + W - 1) / W;
     if (grid > 152 * 8) grid = 152 * 8;
+    const int ntiles = (nlist + SUMMARY_TILE - 1) / SUMMARY_TILE;
     select_nprobe_kernel<<<(unsigned)grid, W * 32, smem, s>>>(dist, nq, nlist, nprobe, P2, W, probes,
-                                                              probe_d2, nprobe_q);
+                                                              probe_d2, nprobe_q, summary, ntiles);
     return cudaGetLastError();
 }
 
