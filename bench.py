@@ -677,9 +677,9 @@ def run_graph(args):
                         "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "peak_kind": kind, "traffic": None,
                         "note": "algorithmic bytes = 4 x dims sampled (FP32 DCO reads) of the HNSW+ arm"}
-    # timed searches of the three arms, 6 kernels each (rotation, norms,
-    # centroid GEMM, select, test factors, graph search)
-    line["gpu_launches"] = 6 * args.steps * 3
+    # timed searches of the three arms, 7 kernels each (rotation, norms, TF32
+    # split of the queries, centroid GEMM, select, test factors, graph search)
+    line["gpu_launches"] = 7 * args.steps * 3
     print(json.dumps(line), flush=True)
     g.close()
     ix.close()
@@ -855,10 +855,12 @@ def main():
     # the scan kernel launches of one search: one query-major launch, or one
     # per cluster-major round
     cm = ads_kern_n > 1
-    # rotation, centroid norms, GEMM, select, test factors; cluster-major adds
-    # the first merge, per round three planning kernels, the scan and a merge,
-    # and the overflow check with its (usually empty) query-major launch
-    launches_per_search = (5 + 1 + 5 * ads_kern_n + 2) if cm else 6
+    # rotation, query norms, TF32 split of the queries, centroid GEMM,
+    # select, test factors; then the query-major scan, or (cluster-major) the
+    # three planning kernels of all rounds, per round the scan and a merge,
+    # the first merge, and the overflow check with its (usually empty)
+    # query-major launch
+    launches_per_search = (6 + 3 + 2 * ads_kern_n + 1 + 2) if cm else 7
     fd_frac = ads_dims / fd_dims if fd_dims else None
     line = {
         "metric": METRIC, "value": job_throughput(nq, ws, ads_ms), "unit": UNIT, "n_gpus": ws,
