@@ -403,7 +403,7 @@ def run_serving(args):
     srv = adsx.Server(ix, max_slots=8192, max_batch=2048, n_streams=4,
                       mem_budget_bytes=2 << 30, max_K=10, max_nprobe=64)
     rng = np.random.default_rng(7)
-    rates = [10_000, 50_000, 100_000, 200_000, 500_000]
+    rates = [10_000, 50_000, 100_000, 200_000, 350_000, 500_000]
     out = []
     recall = None
     for rate in rates:
