@@ -85,12 +85,16 @@ struct Server {
 };
 
 // Device bytes one request needs inside adsx_search_batched: its rotated
-// query, a row of centroid distances, its probe list, plan entries, the
-// partial lists of its splits and its outputs.
+// query and that query's TF32 halves, a row of centroid distances and of
+// their tile summary, its probe list, plan entries, the partial lists of
+// its splits and its outputs.  (The TF32 halves of a batch's queries are
+// padded to a multiple of 128 rows; that padding, at most 127 * 8 * Dp
+// bytes per batch, is not charged.)
 int64_t request_cost(const adsx::Index *ix, int32_t K, int32_t max_nprobe, int32_t max_K)
 {
-    return 4LL * ix->Dp + 4LL * ix->nlist + 4LL * max_nprobe + 8LL * adsx::BATCH_MAX_SPLITS +
-           8LL * adsx::BATCH_MAX_SPLITS * max_K + 12LL * K + 64;
+    const int64_t tiles = (ix->nlist + adsx::SUMMARY_TILE - 1) / adsx::SUMMARY_TILE;
+    return 12LL * ix->Dp + 4LL * ix->nlist + 16LL * tiles + 4LL * max_nprobe +
+           8LL * adsx::BATCH_MAX_SPLITS + 8LL * adsx::BATCH_MAX_SPLITS * max_K + 12LL * K + 64;
 }
 
 void free_slot(Slot &s)

@@ -97,7 +97,7 @@ def test_mix_equals_alone(c1):
 def test_admission_by_memory_and_rejection(c1):
     adsx, wl, ix, *_ = c1
     # budget for two requests: never more than two in flight
-    one = 4 * 128 + 4 * 100 + 4 * 10 + 8 * 16 + 8 * 16 * 10 + 12 * 10 + 64
+    one = 12 * 128 + 4 * 100 + 16 * 1 + 4 * 10 + 8 * 16 + 8 * 16 * 10 + 12 * 10 + 64
     srv = adsx.Server(ix, max_slots=64, max_batch=64, n_streams=4, mem_budget_bytes=2 * one + 10,
                       max_K=10, max_nprobe=10)
     try:
@@ -119,7 +119,7 @@ def test_admission_by_memory_and_rejection(c1):
 
 def test_cancel_and_bounded_wait(c1):
     adsx, wl, ix, *_ = c1
-    one = 4 * 128 + 4 * 100 + 4 * 10 + 8 * 16 + 8 * 16 * 10 + 12 * 10 + 64
+    one = 12 * 128 + 4 * 100 + 16 * 1 + 4 * 10 + 8 * 16 + 8 * 16 * 10 + 12 * 10 + 64
     # one request at a time, so later submissions are still queued
     srv = adsx.Server(ix, max_slots=1, max_batch=1, n_streams=1, mem_budget_bytes=one,
                       max_K=10, max_nprobe=10)
