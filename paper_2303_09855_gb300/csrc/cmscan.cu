@@ -100,7 +100,10 @@ struct CmCarve {
         S = o; o += 4 * 32 * G;
         pa = o; o += 2 * 32 * G;
         o = (o + 15) & ~15;
-        stile = o; o += db * 32 * row;
+        // the staged tile step of a sparse pass, or (dense steps) the step's
+        // dims of every slot's query
+        stile = o;
+        o += db * 32 * row > G * db * 16 * 4 ? db * 32 * row : G * db * 16 * 4;
         bytes = (o + 15) & ~15;
     }
 };
@@ -262,6 +265,20 @@ __global__ void __launch_bounds__(CM_THREADS, CmMinBlocks<T>::value) cm_scan_ker
                             v[b][k] = unpack_piece(w, T());
                         }
                     }
+                    // this step's dims of every slot's query, staged in the
+                    // (idle) tile buffer: the slot loop reads them from shared
+                    // memory (the same values, so the same sums)
+                    constexpr int QW = DB * BLK;
+                    float *qs = reinterpret_cast<float *>(stile);
+                    {
+                        const int per = nb * (BLK / 4);             // float4 per slot
+                        for (int i = lane; i < ngq * per; i += 32) {
+                            const int g = i / per, c = i - g * per;
+                            reinterpret_cast<float4 *>(qs + g * QW)[c] =
+                                ldg4(a.qrot + (int64_t)qg[g] * a.Dp + blk * BLK + 4 * c);
+                        }
+                        __syncwarp();
+                    }
                     const int pos = (int)o + m0 + own;
                     // slot g's live mask loses the members m (lane g % 32 holds it)
                     auto drop = [&](int g, unsigned m) {
@@ -353,8 +370,9 @@ __global__ void __launch_bounds__(CM_THREADS, CmMinBlocks<T>::value) cm_scan_ker
 #pragma unroll
                         for (int b = 0; b < DB; ++b) {
                             if (b < nb) {
-                                const QPiece<NL> qa = ld_qpiece_ro<NL>(qv0 + (blk + b) * BLK + jo);
-                                const QPiece<NL> qb = ld_qpiece_ro<NL>(qv1 + (blk + b) * BLK + jo);
+                                const QPiece<NL> qa = ld_qpiece<NL>(qs + g * QW + b * BLK + jo);
+                                const QPiece<NL> qb =
+                                    ld_qpiece<NL>(qs + (two ? g + 1 : g) * QW + b * BLK + jo);
 #pragma unroll
                                 for (int k = 0; k < NL; ++k) {
                                     p0[k] = add_piece_u(v[b][k], qa, p0[k]);
