@@ -16,7 +16,6 @@
 #include <string.h>
 
 #include <algorithm>
-#include <mutex>
 #include <string>
 
 #include "adsx_internal.cuh"
@@ -28,9 +27,6 @@ constexpr int MAX_DEVICES = 64;
 // The shared scratch of adsx_search_noalloc.  Every call uses it, and it keeps
 // whatever the last call left in it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[ADSX_NOALLOC_SCRATCH_BYTES];
-
-std::mutex g_setup_mu;
-void *g_scratch_ptr[MAX_DEVICES] = {};
 
 int nerr(int code, const std::string &msg)
 {
@@ -52,22 +48,19 @@ bool is_device_ptr_on(const void *p, int device)
     return at.type == cudaMemoryTypeDevice && at.device == device;
 }
 
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array in the current context, looked up on
+// every call (a cheap runtime query): a cached address would dangle after
+// the context is destroyed and re-created (cudaDeviceReset).
 int scratch_base(int device, unsigned char **out)
 {
     if (device < 0 || device >= MAX_DEVICES) return nerr(ADSX_EINVAL, "device id out of range");
-    std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_ptr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return nerr(ADSX_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") +
-                                        cudaGetErrorString(e));
-        }
-        g_scratch_ptr[device] = p;
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return nerr(ADSX_ECUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
     }
-    *out = static_cast<unsigned char *>(g_scratch_ptr[device]);
+    *out = static_cast<unsigned char *>(p);
     return ADSX_OK;
 }
 
