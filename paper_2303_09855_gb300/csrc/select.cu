@@ -8,21 +8,20 @@
 // is mostly not read at all: the nprobe-th smallest summary word bounds the
 // nprobe-th smallest distance, a tile whose fourth word lies above the bound
 // contributes exactly its summary words below it (their exact values read
-// one by one), and only the other tiles are read whole
-// (select_by_summary).  Else, for nprobe <= 64, a bound-and-gather path over
-// the whole row is taken (see the kernel); otherwise,
-// or when ties overflow it, a radix select runs: the row's
-// distances become order-preserving 32-bit keys (bit patterns of non-negative
-// floats), re-read from the row (an L2 hit: the warp has just read it) on
-// every pass, so a warp needs shared memory only for its winners and a
-// histogram; the row's smallest and largest key
-// give the high bits every key shares, and radix passes of up to 8 bits over
-// the remaining bits (warp-aggregated shared-memory histograms) find the
-// exact key T of the nprobe-th smallest distance and how many keys equal to T
-// are needed (or stop early when a digit's bin is needed whole).  Keys below
-// T and the needed keys equal to T (ascending cluster id) are gathered by
-// ballot in index order, and the warp bitonic-sorts the
-// nprobe winners as 64-bit (key, id) words.
+// one by one), and only the other tiles are read whole (select_by_summary).
+// Else, for nprobe <= 64, a bound-and-gather path over the whole row is
+// taken (see the kernel); otherwise, or when ties overflow it, a radix
+// select runs: the row's distances become order-preserving 32-bit keys (bit
+// patterns of non-negative floats), re-read from the row (an L2 hit: the
+// warp has just read it) on every pass, so a warp needs shared memory only
+// for its winners and a histogram; the row's smallest and largest key give
+// the high bits every key shares, and radix passes of up to 8 bits over the
+// remaining bits (warp-aggregated shared-memory histograms) find the exact
+// key T of the nprobe-th smallest distance and how many keys equal to T are
+// needed (or stop early when a digit's bin is needed whole).  Keys below T
+// and the needed keys equal to T (ascending cluster id) are gathered by
+// ballot in index order, and the warp bitonic-sorts the nprobe winners as
+// 64-bit (key, id) words.
 #include "adsx_internal.cuh"
 
 namespace adsx {
