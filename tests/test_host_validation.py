@@ -158,3 +158,47 @@ def test_load_index_rejects_bad_files(A, tmp_path):
     assert lib.adsx_load_index(str(p).encode(), None, None) == A.EINVAL
     assert lib.adsx_save_index(None, str(p).encode(), None) == A.EINVAL
     assert "index is NULL" in A.last_error()
+
+
+def _header(**kw):
+    """An adsx_load_index header (the file's int64 fields after the magic)
+    for a 12 x 8 index with 3 clusters and the digit layout of P at Dp = 16
+    (8-bit digits, T = 4, levels 2..6), with fields overridden by kw."""
+    boff = [0, 0, 0, 256, 768, 1536, 2560] + [0] * 9
+    f = dict(N=12, D=8, Dp=16, nlist=3, storage=0, metric=0, kac_L=0, total_tiles=3,
+             max_tiles=1, tuned_delta_d=32, items_per_sm=48, sched=0, cm_G=0, cm_tpi=2,
+             has_P=1, rot_ok=1, rot_b=8, rot_T=4, rot_Lmax=6, rot_floats=13 * 256)
+    f.update(kw)
+    vals = [f[k] for k in ("N", "D", "Dp", "nlist", "storage", "metric", "kac_L", "total_tiles",
+                           "max_tiles", "tuned_delta_d", "items_per_sm", "sched", "cm_G",
+                           "cm_tpi", "has_P", "rot_ok", "rot_b", "rot_T", "rot_Lmax",
+                           "rot_floats")]
+    return b"ADSXIDX1" + np.array(vals + kw.get("boff", boff), dtype=np.int64).tobytes()
+
+
+@pytest.mark.parametrize("bad", [
+    dict(rot_b=7),                      # digits not those the library derives from Dp
+    dict(rot_floats=12 * 256),          # digit array size off
+    dict(boff=[0, 0, 0, 256, 768, 1536, 2561] + [0] * 9),
+    dict(Dp=32),                        # padding of D
+    dict(has_P=0),                      # neither P nor a Kac walk
+    dict(storage=3), dict(metric=7), dict(nlist=13), dict(tuned_delta_d=24),
+    dict(sched=5), dict(kac_L=2),       # a Kac walk and P together
+])
+def test_load_index_checks_header_fields(A, tmp_path, bad):
+    """Header fields outside the library's limits or inconsistent with one
+    another are rejected before anything is allocated."""
+    p = tmp_path / "h.adsx"
+    p.write_bytes(_header(**bad))
+    _rejects(A, lambda: A.load_index(p), "header fields out of range")
+
+
+def test_load_index_valid_header_passes_the_checks(A, tmp_path):
+    """The unmodified header of the cases above is accepted: the load gets
+    past the header checks (and then fails on the missing arrays, or on the
+    missing device)."""
+    p = tmp_path / "h.adsx"
+    p.write_bytes(_header())
+    with pytest.raises(A.AdsxError) as ei:
+        A.load_index(p)
+    assert "header fields out of range" not in str(ei.value), str(ei.value)
